@@ -1,0 +1,206 @@
+/*
+ * cdf_lb.h -- C ABI of the GB300 (sm_103a) lattice Boltzmann solver for the
+ * coupled cross-diffusion-fluid (CDF) system of Zhan, Chai & Shi,
+ * "A lattice Boltzmann model for the coupled cross-diffusion-fluid system"
+ * (arXiv:2101.03055).
+ *
+ * The problem (Eqs. CDE, NS1, NS2 of Sec. 1):
+ *   d_t phi_a + div(phi_a u) = div(D_ab grad phi_b) + S_a,   a = 0..m-1
+ *   div u = 0,  d_t u + div(u u) = -grad p + div(nu grad u) + F
+ * is advanced by the model of Sec. 2 with D2Q5 scalar populations and D2Q9
+ * fluid populations (Eqs. D2Q5, D2Q9), lambda = I and varphi = 0 (Sec. 3):
+ *   Eq. evolution12 -- scalar update with the matrix collision operator
+ *                      omega_ab, the source S_i = W_i S_a (Eq. source), its
+ *                      time-derivative correction and the auxiliary source
+ *                      G_i (Eq. Gi);
+ *   Eq. evolution3  -- fluid update with the force term (Eq. force);
+ *   Eq. omega-D     -- omega = (D / cs^2 + I / 2)^-1 (dt = 1);
+ *   appendix        -- nu = (1 / omega_f - 1/2) cs^2.
+ *
+ * Conventions for every call:
+ *   - Lattice units: dx = dt = 1.  Fields are row-major [y][x] with x fastest;
+ *     a stack of fields is [field][y][x].  Moment stacks hold m + 3 fields:
+ *     phi_0 .. phi_{m-1}, u_x, u_y, p.
+ *   - Node (i, j) of an axis with walls sits half a spacing inside them
+ *     (half-way walls); on a periodic axis node i sits at x = i.
+ *   - A handle owns all the device memory it allocates.  Pointers passed in
+ *     belong to the caller and are not retained after the call returns.
+ *   - Device pointers must be on the device that was current at create time.
+ *   - Work is ordered on the caller's stream (options.cuda_stream, NULL = the
+ *     legacy default stream): each call waits for earlier work on that stream
+ *     and later work on it waits for the call.  Calls that return host data
+ *     synchronise before they return.
+ *   - Every call returns CDF_OK or an error code; cdf_lb_last_error() gives
+ *     a message for the calling thread's last failure.  After CDF_ECUDA the
+ *     handle should be destroyed.
+ */
+#ifndef CDF_LB_H
+#define CDF_LB_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define CDF_MAX_M 4 /* scalar sets supported by the kernels */
+
+typedef enum {
+    CDF_OK = 0,
+    CDF_EINVAL = 1,        /* invalid argument or parameter set */
+    CDF_ENOMEM = 2,        /* device or host allocation failed */
+    CDF_ECUDA = 3,         /* a CUDA call failed (message has the CUDA error) */
+    CDF_ENOTCONVERGED = 4, /* run_to_steady reached max_steps above tol */
+    CDF_EUNSTABLE = 5,     /* a NaN or Inf appeared in the fields */
+    CDF_ETIMEOUT = 6,      /* a bounded device-side wait ran out */
+    CDF_EIO = 7            /* checkpoint file could not be read or written */
+} cdf_status;
+
+/* Population storage.  CDF_FP32 stores populations as float.  The 16-bit modes
+ * store each population's deviation from a fixed reference (W_i phi_ref16_a
+ * for scalars, (rho0, 0, ..., 0) for the fluid) as FP16 or BF16; every
+ * collision is computed in FP32 (paper: silent on precision). */
+typedef enum { CDF_FP32 = 0, CDF_FP16_DEV = 1, CDF_BF16_DEV = 2 } cdf_storage;
+
+typedef enum { CDF_BC_PERIODIC = 0, CDF_BC_WALL = 1 } cdf_bckind;
+typedef enum { CDF_FL_NOSLIP = 0, CDF_FL_FREESLIP = 1 } cdf_fluid_bc;
+typedef enum { CDF_SC_NOFLUX = 0, CDF_SC_DIRICHLET = 1 } cdf_scalar_bc;
+
+/* Diffusion matrix D (Eq. CDE).  CDF_D_CONST: D as given.  CDF_D_CHEMOTAXIS
+ * (Sec. 3.1): D_01 gets -chi * phi_0 * r(phi_1) added at every node, with the
+ * cut-off r(c) = 1 if c >= c_star else 0 (Sec. 3.1.3), or, when
+ * r_regularised != 0, r(c) = (1 + (c - c*) / sqrt((c - c*)^2 + eps^2)) / 2
+ * (Sec. 3.1.2).  Needs m >= 2. */
+typedef enum { CDF_D_CONST = 0, CDF_D_CHEMOTAXIS = 1 } cdf_dkind;
+typedef struct {
+    int kind;                          /* cdf_dkind */
+    double D[CDF_MAX_M * CDF_MAX_M];   /* row-major m x m, lattice units */
+    double chi, c_star, eps;
+    int r_regularised;
+} cdf_diffusion;
+
+/* Source S (Eq. CDE).  CDF_S_CONST: S_a = S[a].  CDF_S_CONSUMPTION (Sec. 3.1):
+ * S_1 = -k * phi_0 * r(phi_1), other components 0 (uses the cut-off of the
+ * diffusion struct).  Its time derivative enters Eq. evolution12 as the
+ * backward difference (S_i(t) - S_i(t-1)) / 2 (Sec. 2.1, gamma = 0). */
+typedef enum { CDF_S_NONE = 0, CDF_S_CONST = 1, CDF_S_CONSUMPTION = 2 } cdf_skind;
+typedef struct {
+    int kind;                          /* cdf_skind */
+    double S[CDF_MAX_M];
+    double k;
+} cdf_source;
+
+/* Body force F = g * (F0 + sum_a beta[a] * (phi_a - phi_ref[a])) (Eq. NS2;
+ * Sec. 3.1: F = -Sc gamma n z; Sec. 3.2: F = Ra Pr (T + Nc C) z). */
+typedef struct {
+    double g[2];
+    double beta[CDF_MAX_M];
+    double phi_ref[CDF_MAX_M];
+    double F0;
+} cdf_force;
+
+/* One side of the box (Sec. 3: anti-bounce-back for scalar Dirichlet values,
+ * half-way bounce-back for no-flux and no-slip; free slip as specular
+ * reflection).  Opposite sides must both be periodic or both be walls. */
+typedef struct {
+    int kind;                          /* cdf_bckind */
+    int fluid;                         /* cdf_fluid_bc (walls) */
+    int scalar[CDF_MAX_M];             /* cdf_scalar_bc per scalar (walls) */
+    double value[CDF_MAX_M];           /* Dirichlet value per scalar */
+} cdf_side;
+typedef struct { cdf_side west, east, south, north; } cdf_boundaries;
+
+typedef struct { int nx, ny; } cdf_grid;
+
+typedef struct {
+    int storage;                       /* cdf_storage */
+    double rho0;                       /* the constant of sigma_0 in Eq. heq (> 0) */
+    void *cuda_stream;                 /* cudaStream_t of the caller, NULL = default */
+    double phi_ref16[CDF_MAX_M];       /* 16-bit modes: scalar reference values */
+    int block_x, block_y;              /* step kernel CTA shape; 0 = autotuned */
+} cdf_options;
+
+/* Facts about a handle (for benchmarks and tests). */
+typedef struct {
+    int nx, ny, m, pitch;              /* pitch: elements per stored row */
+    int storage;
+    int planes;                        /* population planes per buffer */
+    int sprev_planes;                  /* S(t-1) planes (CONSUMPTION: 1) */
+    int block_x, block_y;              /* step kernel CTA shape in use */
+    double bytes_per_lup;              /* minimal HBM bytes moved per node update */
+    long long t;                       /* time steps taken since initialisation */
+} cdf_info;
+
+typedef struct cdf_lb cdf_lb;
+
+/* Create a solver for one nx x ny lattice with m scalar sets (1 <= m <= 4).
+ * Checks: nx, ny >= 1; the relaxation matrix of Eq. omega-D exists (D / cs^2 +
+ * I / 2 invertible); nu > 0 (so 0 < omega_f < 2); opposite sides both periodic
+ * or both walls; chemotaxis and consumption need m >= 2; rho0 > 0.
+ * Allocates the device buffers; the populations hold no state until one of
+ * the init calls.  On failure *out is NULL and nothing is leaked. */
+cdf_status cdf_lb_create(const cdf_grid *grid, int m, const cdf_diffusion *diffusion, double nu,
+                         const cdf_source *source, const cdf_force *force,
+                         const cdf_boundaries *boundaries, const cdf_options *options,
+                         cdf_lb **out);
+
+/* Set the state at t = 0 from moments (host, FP64): phi [m][ny][nx],
+ * u [2][ny][nx], p [ny][nx] or NULL (p = 0).  Populations are f = f^eq(phi, u)
+ * (Eq. feq-phi), h = h^eq(u, p) - F_i / 2 (Eq. heq, Eq. force) so that the
+ * moments of Eqs. sum-phi/u/p return the inputs; S(t-1) = S(phi). */
+cdf_status cdf_lb_init_moments(cdf_lb *h, const double *phi, const double *u, const double *p);
+
+/* As cdf_lb_init_moments from a device FP32 stack [m+3][ny][nx]
+ * (phi..., u_x, u_y, p), contiguous, on the handle's device. */
+cdf_status cdf_lb_init_moments_device(cdf_lb *h, const float *dev_fields);
+
+/* Advance n >= 0 time steps of Eqs. evolution12 and evolution3 with streaming
+ * and the boundary rules, one fused kernel per step (CUDA-graph launched). */
+cdf_status cdf_lb_step(cdf_lb *h, long long n);
+
+/* Step until the relative change of every field q in {phi_0..phi_{m-1}, u_x,
+ * u_y} over `check_every` steps, R = max_q sum|q(t) - q(t - K)| / sum|q(t)|,
+ * summed in FP64, is below tol (the stop test of Sec. 3.1.1 with absolute
+ * differences).  Returns CDF_ENOTCONVERGED after max_steps more steps,
+ * CDF_EUNSTABLE on a NaN/Inf.  steps_taken and residual may be NULL. */
+cdf_status cdf_lb_run_to_steady(cdf_lb *h, double tol, long long check_every, long long max_steps,
+                                long long *steps_taken, double *residual);
+
+/* Moments at the current time (Eqs. sum-phi, sum-u, sum-p) into a host FP64
+ * stack [m+3][ny][nx]. */
+cdf_status cdf_lb_moments(cdf_lb *h, double *host_out);
+
+/* Same into a device FP32 stack [m+3][ny][nx], contiguous. */
+cdf_status cdf_lb_moments_device(cdf_lb *h, float *dev_out);
+
+/* Total of each scalar over the lattice, sum_x phi_a(x), accumulated in FP64 on
+ * the device (mass check of Eq. CDE). sums has m entries (host). */
+cdf_status cdf_lb_mass(cdf_lb *h, double *sums);
+
+/* Post-collision populations of the current time as FP64 on the host:
+ * f [m][5][ny][nx] (D2Q5 order of Eq. D2Q5), hf [9][ny][nx] (Eq. D2Q9 order),
+ * s_now [m][ny][nx] = S(phi) of the current time (zeros unless CONSUMPTION).
+ * Any pointer may be NULL. */
+cdf_status cdf_lb_populations(cdf_lb *h, double *f, double *hf, double *s_now);
+
+/* Write / read the full state (populations, S(t-1), time, moments) to a file;
+ * a restart continues bit-identically.  load checks that the file matches the
+ * handle's grid, m and storage (CDF_EINVAL otherwise, CDF_EIO on file errors). */
+cdf_status cdf_lb_save(cdf_lb *h, const char *path);
+cdf_status cdf_lb_load(cdf_lb *h, const char *path);
+
+cdf_status cdf_lb_get_info(const cdf_lb *h, cdf_info *out);
+
+/* The library's internal CUDA stream of the handle (cudaStream_t) on which the
+ * step kernels run; for timing with events.  Borrowed, do not destroy. */
+void *cdf_lb_stream(const cdf_lb *h);
+
+/* Release the handle and its device memory (NULL is a no-op). */
+void cdf_lb_destroy(cdf_lb *h);
+
+/* Message of the calling thread's last error ("" if none).  Valid until the
+ * thread's next call into the library. */
+const char *cdf_lb_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* CDF_LB_H */

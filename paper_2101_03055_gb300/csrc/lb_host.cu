@@ -1,0 +1,688 @@
+// Host runtime behind the C ABI of include/cdf_lb.h: parameter checks and
+// scaling, device buffers, stream ordering, CUDA-graph batches of fused steps,
+// the steady-state driver with FP64 device reductions, checkpoints and the
+// CTA-shape autotuner.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <new>
+#include <tuple>
+#include <vector>
+
+#include "../../include/cdf_lb.h"
+#include "lb_internal.h"
+
+using namespace cdflb;
+
+namespace {
+
+thread_local char g_err[512] = "";
+
+cdf_status fail(cdf_status st, const char *fmt, ...) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof g_err, fmt, ap);
+    va_end(ap);
+    return st;
+}
+
+#define CK(call)                                                                          \
+    do {                                                                                  \
+        cudaError_t e_ = (call);                                                          \
+        if (e_ != cudaSuccess)                                                            \
+            return fail(CDF_ECUDA, "%s failed: %s (%s:%d)", #call, cudaGetErrorString(e_), \
+                        __FILE__, __LINE__);                                              \
+    } while (0)
+
+// Keeps the caller's current device and restores it on scope exit.
+struct DeviceGuard {
+    int prev = -1;
+    explicit DeviceGuard(int dev) {
+        if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+        if (prev != dev) cudaSetDevice(dev);
+    }
+    ~DeviceGuard() {
+        int cur;
+        if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+    }
+};
+
+// Gauss-Jordan inverse with partial pivoting (double).  false if singular.
+bool invert(int n, const double *a_in, double *inv) {
+    double a[kMaxM * kMaxM];
+    for (int i = 0; i < n * n; ++i) a[i] = a_in[i];
+    for (int r = 0; r < n; ++r)
+        for (int c = 0; c < n; ++c) inv[r * n + c] = r == c ? 1.0 : 0.0;
+    for (int col = 0; col < n; ++col) {
+        int piv = col;
+        for (int r = col + 1; r < n; ++r)
+            if (std::fabs(a[r * n + col]) > std::fabs(a[piv * n + col])) piv = r;
+        if (!(std::fabs(a[piv * n + col]) > 1e-300)) return false;
+        for (int c = 0; c < n; ++c) {
+            std::swap(a[col * n + c], a[piv * n + c]);
+            std::swap(inv[col * n + c], inv[piv * n + c]);
+        }
+        const double d = a[col * n + col];
+        for (int c = 0; c < n; ++c) { a[col * n + c] /= d; inv[col * n + c] /= d; }
+        for (int r = 0; r < n; ++r) {
+            if (r == col) continue;
+            const double f = a[r * n + col];
+            for (int c = 0; c < n; ++c) { a[r * n + c] -= f * a[col * n + c]; inv[r * n + c] -= f * inv[col * n + c]; }
+        }
+    }
+    return true;
+}
+
+// Cholesky test of a symmetric matrix.
+bool positive_definite(int n, const double *s) {
+    double L[kMaxM * kMaxM] = {0};
+    for (int i = 0; i < n; ++i)
+        for (int j = 0; j <= i; ++j) {
+            double v = s[i * n + j];
+            for (int k = 0; k < j; ++k) v -= L[i * n + k] * L[j * n + k];
+            if (i == j) {
+                if (!(v > 0.0)) return false;
+                L[i * n + i] = std::sqrt(v);
+            } else {
+                L[i * n + j] = v / L[j * n + j];
+            }
+        }
+    return true;
+}
+
+size_t elem_size(int storage) { return storage == CDF_FP32 ? 4 : 2; }
+
+using TuneKey = std::tuple<int, int, int, int, int>;
+std::mutex g_tune_mu;
+std::map<TuneKey, dim3> g_tune_cache;
+
+constexpr int kGraphSteps = 32;  // steps per captured graph (even: parity returns)
+
+}  // namespace
+
+struct cdf_lb {
+    int device = 0;
+    int nx = 0, ny = 0, m = 0, pitch = 0;
+    long long plane = 0;
+    int storage = 0;
+    int planes = 0, sprev_planes = 0;
+    LbParams P{};
+    void *buf[2] = {nullptr, nullptr};
+    int cur = 0;  // buffer that holds the current post-collision populations
+    float *sprev = nullptr;
+    float *mom = nullptr, *mom_prev = nullptr;
+    float *dense = nullptr;       // dense FP32 staging (export, host init)
+    float *host_stage = nullptr;  // pinned host staging of one moment stack
+    double *partials = nullptr, *red = nullptr, *red_host = nullptr;
+    cudaStream_t s = nullptr;
+    cudaStream_t user = nullptr;
+    cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+    cudaGraphExec_t graph[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};  // [parity][moments]
+    dim3 block{64, 4, 1};
+    long long t = 0;
+    bool initialised = false;
+};
+
+namespace {
+
+void release(cdf_lb *h) {
+    if (!h) return;
+    DeviceGuard g(h->device);
+    for (auto &row : h->graph)
+        for (auto &ge : row)
+            if (ge) cudaGraphExecDestroy(ge);
+    cudaFree(h->buf[0]);
+    cudaFree(h->buf[1]);
+    cudaFree(h->sprev);
+    cudaFree(h->mom);
+    cudaFree(h->mom_prev);
+    cudaFree(h->dense);
+    cudaFree(h->partials);
+    cudaFree(h->red);
+    if (h->red_host) cudaFreeHost(h->red_host);
+    if (h->host_stage) cudaFreeHost(h->host_stage);
+    if (h->ev_in) cudaEventDestroy(h->ev_in);
+    if (h->ev_out) cudaEventDestroy(h->ev_out);
+    if (h->s) cudaStreamDestroy(h->s);
+    delete h;
+}
+
+// Order the library stream after the caller's stream, and back.
+cdf_status enter(cdf_lb *h) {
+    CK(cudaEventRecord(h->ev_in, h->user));
+    CK(cudaStreamWaitEvent(h->s, h->ev_in, 0));
+    return CDF_OK;
+}
+cdf_status leave(cdf_lb *h) {
+    CK(cudaEventRecord(h->ev_out, h->s));
+    CK(cudaStreamWaitEvent(h->user, h->ev_out, 0));
+    return CDF_OK;
+}
+
+cdf_status launch_one(cdf_lb *h, int src, bool with_moments) {
+    CK(launch_step(h->P, h->storage, h->buf[src], h->buf[src ^ 1], h->sprev,
+                   with_moments ? h->mom : nullptr, h->block, h->s));
+    return CDF_OK;
+}
+
+cdf_status get_graph(cdf_lb *h, int parity, int with_moments, cudaGraphExec_t *out) {
+    if (!h->graph[parity][with_moments]) {
+        cudaGraph_t graph = nullptr;
+        CK(cudaStreamBeginCapture(h->s, cudaStreamCaptureModeThreadLocal));
+        int src = parity;
+        for (int k = 0; k < kGraphSteps; ++k) {
+            cudaError_t e = launch_step(h->P, h->storage, h->buf[src], h->buf[src ^ 1], h->sprev,
+                                        (with_moments && k == kGraphSteps - 1) ? h->mom : nullptr,
+                                        h->block, h->s);
+            if (e != cudaSuccess) {
+                cudaStreamEndCapture(h->s, &graph);
+                if (graph) cudaGraphDestroy(graph);
+                return fail(CDF_ECUDA, "step launch during capture: %s", cudaGetErrorString(e));
+            }
+            src ^= 1;
+        }
+        CK(cudaStreamEndCapture(h->s, &graph));
+        cudaError_t e = cudaGraphInstantiate(&h->graph[parity][with_moments], graph, 0);
+        cudaGraphDestroy(graph);
+        CK(e);
+    }
+    *out = h->graph[parity][with_moments];
+    return CDF_OK;
+}
+
+// n steps on the library stream; the last one writes the moments.
+cdf_status run_steps(cdf_lb *h, long long n) {
+    while (n > 0) {
+        if (n >= kGraphSteps) {
+            cudaGraphExec_t ge;
+            cdf_status st = get_graph(h, h->cur, n == kGraphSteps, &ge);
+            if (st != CDF_OK) return st;
+            CK(cudaGraphLaunch(ge, h->s));
+            n -= kGraphSteps;
+            h->t += kGraphSteps;
+        } else {
+            for (long long j = 0; j < n; ++j) {
+                cdf_status st = launch_one(h, h->cur, j == n - 1);
+                if (st != CDF_OK) return st;
+                h->cur ^= 1;
+            }
+            h->t += n;
+            n = 0;
+        }
+    }
+    return CDF_OK;
+}
+
+cdf_status reduce(cdf_lb *h, const float *nw, const float *od, double *host_out) {
+    CK(launch_reduce(nw, od, h->nx, h->ny, h->pitch, h->plane, h->m, h->partials, h->red, h->s));
+    const int nq = reduce_quantities(h->m);
+    CK(cudaMemcpyAsync(h->red_host, h->red, nq * sizeof(double), cudaMemcpyDeviceToHost, h->s));
+    CK(cudaStreamSynchronize(h->s));
+    std::memcpy(host_out, h->red_host, nq * sizeof(double));
+    return CDF_OK;
+}
+
+// Time the step kernel for a few CTA shapes on the (zeroed) buffers and keep the
+// fastest; results are cached per (nx, ny, m, storage).
+cdf_status autotune(cdf_lb *h) {
+    TuneKey key{h->nx, h->ny, h->m, h->storage, h->P.chemotaxis};
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        auto it = g_tune_cache.find(key);
+        if (it != g_tune_cache.end()) { h->block = it->second; return CDF_OK; }
+    }
+    const dim3 cands[] = {dim3(32, 4), dim3(32, 8), dim3(64, 2), dim3(64, 4),
+                          dim3(128, 1), dim3(128, 2), dim3(256, 1)};
+    cudaEvent_t a, b;
+    CK(cudaEventCreate(&a));
+    CK(cudaEventCreate(&b));
+    float best = 1e30f;
+    dim3 best_b = h->block;
+    const long long nodes = (long long)h->nx * h->ny;
+    const int reps = nodes >= (1 << 22) ? 4 : 16;
+    for (const dim3 &c : cands) {
+        if ((int)c.x > 2 * h->nx && c.x > 32) continue;
+        h->block = c;
+        for (int w = 0; w < 2; ++w) {
+            cdf_status st = launch_one(h, 0, false);
+            if (st != CDF_OK) return st;
+        }
+        CK(cudaEventRecord(a, h->s));
+        for (int r = 0; r < reps; ++r) {
+            cdf_status st = launch_one(h, r & 1, false);
+            if (st != CDF_OK) return st;
+        }
+        CK(cudaEventRecord(b, h->s));
+        CK(cudaEventSynchronize(b));
+        float ms = 0;
+        CK(cudaEventElapsedTime(&ms, a, b));
+        if (ms < best) { best = ms; best_b = c; }
+    }
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    h->block = best_b;
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_tune_cache[key] = best_b;
+    return CDF_OK;
+}
+
+cdf_status check_side_pair(const cdf_side &a, const cdf_side &b, const char *axis) {
+    for (const cdf_side *s : {&a, &b})
+        if (s->kind != CDF_BC_PERIODIC && s->kind != CDF_BC_WALL)
+            return fail(CDF_EINVAL, "boundary kind must be CDF_BC_PERIODIC or CDF_BC_WALL");
+    if (a.kind != b.kind)
+        return fail(CDF_EINVAL, "opposite %s sides must both be periodic or both walls", axis);
+    return CDF_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *cdf_lb_last_error(void) { return g_err; }
+
+cdf_status cdf_lb_create(const cdf_grid *grid, int m, const cdf_diffusion *dif, double nu,
+                         const cdf_source *src, const cdf_force *frc, const cdf_boundaries *bc,
+                         const cdf_options *opt, cdf_lb **out) {
+    g_err[0] = 0;
+    if (!out) return fail(CDF_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (!grid || !dif || !src || !frc || !bc || !opt) return fail(CDF_EINVAL, "NULL argument");
+    if (grid->nx < 1 || grid->ny < 1) return fail(CDF_EINVAL, "grid must be at least 1 x 1");
+    if ((long long)grid->nx * grid->ny > (1LL << 31)) return fail(CDF_EINVAL, "grid too large");
+    if (m < 1 || m > CDF_MAX_M) return fail(CDF_EINVAL, "m must be in [1, %d]", CDF_MAX_M);
+    if (!(nu > 0.0) || !std::isfinite(nu)) return fail(CDF_EINVAL, "nu must be positive");
+    if (dif->kind != CDF_D_CONST && dif->kind != CDF_D_CHEMOTAXIS) return fail(CDF_EINVAL, "bad diffusion kind");
+    if (src->kind != CDF_S_NONE && src->kind != CDF_S_CONST && src->kind != CDF_S_CONSUMPTION)
+        return fail(CDF_EINVAL, "bad source kind");
+    if ((dif->kind == CDF_D_CHEMOTAXIS || src->kind == CDF_S_CONSUMPTION) && m < 2)
+        return fail(CDF_EINVAL, "chemotaxis / consumption closures need m >= 2");
+    if (opt->storage < CDF_FP32 || opt->storage > CDF_BF16_DEV) return fail(CDF_EINVAL, "bad storage");
+    if (!(opt->rho0 > 0.0)) return fail(CDF_EINVAL, "rho0 must be positive");
+    cdf_status st;
+    if ((st = check_side_pair(bc->west, bc->east, "x")) != CDF_OK) return st;
+    if ((st = check_side_pair(bc->south, bc->north, "y")) != CDF_OK) return st;
+
+    // Eq. omega-D with lambda = I, dt = 1: omega^-1 = D / cs^2 + I / 2 = 3 D + I / 2.
+    double B[kMaxM * kMaxM], Binv[kMaxM * kMaxM], Bs[kMaxM * kMaxM];
+    for (int a = 0; a < m; ++a)
+        for (int b = 0; b < m; ++b) {
+            B[a * m + b] = 3.0 * dif->D[a * m + b] + (a == b ? 0.5 : 0.0);
+            if (!std::isfinite(B[a * m + b])) return fail(CDF_EINVAL, "D has a non-finite entry");
+        }
+    for (int a = 0; a < m; ++a)
+        for (int b = 0; b < m; ++b) Bs[a * m + b] = 0.5 * (B[a * m + b] + B[b * m + a]);
+    if (!positive_definite(m, Bs))
+        return fail(CDF_EINVAL, "3 D + I/2 is not positive definite (no stable relaxation matrix)");
+    if (!invert(m, B, Binv)) return fail(CDF_EINVAL, "3 D + I/2 is singular");
+    if (dif->r_regularised && !(dif->eps > 0.0)) return fail(CDF_EINVAL, "regularised cut-off needs eps > 0");
+    const cdf_side *sides[4] = {&bc->west, &bc->east, &bc->south, &bc->north};
+    for (int s = 0; s < 4; ++s) {
+        if (sides[s]->kind == CDF_BC_WALL && sides[s]->fluid != CDF_FL_NOSLIP && sides[s]->fluid != CDF_FL_FREESLIP)
+            return fail(CDF_EINVAL, "bad fluid boundary kind");
+        for (int a = 0; a < m; ++a) {
+            if (sides[s]->scalar[a] != CDF_SC_NOFLUX && sides[s]->scalar[a] != CDF_SC_DIRICHLET)
+                return fail(CDF_EINVAL, "bad scalar boundary kind");
+            if (sides[s]->kind == CDF_BC_PERIODIC && sides[s]->scalar[a] == CDF_SC_DIRICHLET)
+                return fail(CDF_EINVAL, "Dirichlet value on a periodic side");
+        }
+    }
+    if (opt->block_x != 0 || opt->block_y != 0) {
+        if (opt->block_x <= 0 || opt->block_y <= 0 || opt->block_x * opt->block_y > 256 || opt->block_x % 32 != 0)
+            return fail(CDF_EINVAL, "block must be a multiple of 32 wide and at most 256 threads");
+    }
+
+    cdf_lb *h = new (std::nothrow) cdf_lb;
+    if (!h) return fail(CDF_ENOMEM, "host allocation failed");
+    if (cudaGetDevice(&h->device) != cudaSuccess) { delete h; return fail(CDF_ECUDA, "no CUDA device"); }
+    h->nx = grid->nx;
+    h->ny = grid->ny;
+    h->m = m;
+    h->storage = opt->storage;
+    const int align = opt->storage == CDF_FP32 ? 32 : 64;  // 128-byte rows
+    h->pitch = (grid->nx + align - 1) / align * align;
+    h->plane = (long long)h->pitch * h->ny;
+    h->planes = 9 + 5 * m;
+    h->sprev_planes = src->kind == CDF_S_CONSUMPTION ? 1 : 0;
+    h->user = static_cast<cudaStream_t>(opt->cuda_stream);
+
+    LbParams &P = h->P;
+    P.nx = h->nx;
+    P.ny = h->ny;
+    P.pitch = h->pitch;
+    P.plane = h->plane;
+    P.m = m;
+    for (int i = 0; i < m * m; ++i) P.omega[i] = (float)Binv[i];
+    P.omega_f = (float)(1.0 / (3.0 * nu + 0.5));
+    P.chemotaxis = dif->kind == CDF_D_CHEMOTAXIS;
+    P.chi3 = (float)(3.0 * dif->chi);
+    P.c_star = (float)dif->c_star;
+    P.eps2 = (float)(dif->eps * dif->eps);
+    P.r_regularised = dif->r_regularised != 0;
+    P.skind = src->kind;
+    for (int a = 0; a < m; ++a) P.S[a] = (float)src->S[a];
+    P.k = (float)src->k;
+    P.g[0] = (float)frc->g[0];
+    P.g[1] = (float)frc->g[1];
+    double Fbase = frc->F0;
+    for (int a = 0; a < m; ++a) {
+        P.beta[a] = (float)frc->beta[a];
+        Fbase -= frc->beta[a] * frc->phi_ref[a];
+        P.ref16[a] = (float)opt->phi_ref16[a];
+    }
+    P.Fbase = (float)Fbase;
+    P.rho0 = (float)opt->rho0;
+    P.periodic_x = bc->west.kind == CDF_BC_PERIODIC;
+    P.periodic_y = bc->south.kind == CDF_BC_PERIODIC;
+    for (int s = 0; s < 4; ++s) {
+        P.freeslip[s] = sides[s]->kind == CDF_BC_WALL && sides[s]->fluid == CDF_FL_FREESLIP;
+        P.dirichlet[s] = 0;
+        for (int a = 0; a < m; ++a) {
+            if (sides[s]->kind == CDF_BC_WALL && sides[s]->scalar[a] == CDF_SC_DIRICHLET) {
+                P.dirichlet[s] |= 1u << a;
+                P.abb[s][a] = (float)(sides[s]->value[a] / 3.0);  // 2 W_i phi_w, W_i = 1/6
+            }
+        }
+    }
+
+    DeviceGuard g(h->device);
+    const size_t esz = elem_size(h->storage);
+    const size_t pop_bytes = (size_t)h->planes * h->plane * esz;
+    const size_t n = (size_t)h->nx * h->ny;
+    auto alloc = [&](void **p, size_t bytes) -> bool { return cudaMalloc(p, bytes) == cudaSuccess; };
+    bool ok = alloc(&h->buf[0], pop_bytes) && alloc(&h->buf[1], pop_bytes) &&
+              alloc((void **)&h->sprev, (size_t)h->plane * 4) &&
+              alloc((void **)&h->mom, (size_t)(m + 3) * h->plane * 4) &&
+              alloc((void **)&h->mom_prev, (size_t)(m + 3) * h->plane * 4) &&
+              alloc((void **)&h->dense, (size_t)h->planes * n * 4) &&
+              alloc((void **)&h->partials, (size_t)reduce_quantities(m) * kReduceBlocks * sizeof(double)) &&
+              alloc((void **)&h->red, (size_t)reduce_quantities(m) * sizeof(double)) &&
+              cudaMallocHost((void **)&h->red_host, (size_t)reduce_quantities(m) * sizeof(double)) == cudaSuccess &&
+              cudaMallocHost((void **)&h->host_stage, (size_t)(m + 3) * n * 4) == cudaSuccess;
+    if (!ok) {
+        cudaGetLastError();
+        release(h);
+        return fail(CDF_ENOMEM, "device allocation of %.1f MB failed", 2.0 * pop_bytes / 1e6);
+    }
+    if (cudaStreamCreateWithFlags(&h->s, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&h->ev_in, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&h->ev_out, cudaEventDisableTiming) != cudaSuccess) {
+        release(h);
+        return fail(CDF_ECUDA, "stream/event creation failed");
+    }
+    if (cudaMemsetAsync(h->buf[0], 0, pop_bytes, h->s) != cudaSuccess ||
+        cudaMemsetAsync(h->buf[1], 0, pop_bytes, h->s) != cudaSuccess ||
+        cudaMemsetAsync(h->sprev, 0, (size_t)h->plane * 4, h->s) != cudaSuccess ||
+        cudaMemsetAsync(h->mom, 0, (size_t)(m + 3) * h->plane * 4, h->s) != cudaSuccess) {
+        release(h);
+        return fail(CDF_ECUDA, "memset failed");
+    }
+    if (opt->block_x > 0 && opt->block_y > 0) {
+        h->block = dim3(opt->block_x, opt->block_y);
+    } else if ((st = autotune(h)) != CDF_OK) {
+        release(h);
+        return st;
+    }
+    if (cudaStreamSynchronize(h->s) != cudaSuccess) {
+        release(h);
+        return fail(CDF_ECUDA, "set-up failed");
+    }
+    *out = h;
+    return CDF_OK;
+}
+
+void cdf_lb_destroy(cdf_lb *h) {
+    if (!h) return;
+    {
+        DeviceGuard g(h->device);
+        cudaStreamSynchronize(h->s);
+    }
+    release(h);
+}
+
+static cdf_status init_from_device_fields(cdf_lb *h, const float *fields) {
+    CK(launch_init(h->P, h->storage, fields, h->nx, h->buf[0], h->sprev, h->mom, h->s));
+    h->cur = 0;
+    h->t = 0;
+    h->initialised = true;
+    return CDF_OK;
+}
+
+cdf_status cdf_lb_init_moments(cdf_lb *h, const double *phi, const double *u, const double *p) {
+    g_err[0] = 0;
+    if (!h || !phi || !u) return fail(CDF_EINVAL, "NULL argument");
+    DeviceGuard g(h->device);
+    const size_t n = (size_t)h->nx * h->ny;
+    // The pinned staging buffer may still feed an earlier copy.
+    CK(cudaStreamSynchronize(h->s));
+    float *host = h->host_stage;
+    for (int a = 0; a < h->m; ++a)
+        for (size_t i = 0; i < n; ++i) host[a * n + i] = (float)phi[a * n + i];
+    for (size_t i = 0; i < 2 * n; ++i) host[h->m * n + i] = (float)u[i];
+    for (size_t i = 0; i < n; ++i) host[(h->m + 2) * n + i] = p ? (float)p[i] : 0.f;
+    cdf_status st = enter(h);
+    if (st != CDF_OK) return st;
+    CK(cudaMemcpyAsync(h->dense, host, (size_t)(h->m + 3) * n * 4, cudaMemcpyHostToDevice, h->s));
+    if ((st = init_from_device_fields(h, h->dense)) != CDF_OK) return st;
+    return leave(h);
+}
+
+cdf_status cdf_lb_init_moments_device(cdf_lb *h, const float *dev_fields) {
+    g_err[0] = 0;
+    if (!h || !dev_fields) return fail(CDF_EINVAL, "NULL argument");
+    DeviceGuard g(h->device);
+    cdf_status st = enter(h);
+    if (st != CDF_OK) return st;
+    if ((st = init_from_device_fields(h, dev_fields)) != CDF_OK) return st;
+    return leave(h);
+}
+
+cdf_status cdf_lb_step(cdf_lb *h, long long n) {
+    g_err[0] = 0;
+    if (!h) return fail(CDF_EINVAL, "NULL handle");
+    if (n < 0) return fail(CDF_EINVAL, "n must be >= 0");
+    if (!h->initialised) return fail(CDF_EINVAL, "state not initialised");
+    if (n == 0) return CDF_OK;
+    DeviceGuard g(h->device);
+    cdf_status st = enter(h);
+    if (st != CDF_OK) return st;
+    if ((st = run_steps(h, n)) != CDF_OK) return st;
+    return leave(h);
+}
+
+cdf_status cdf_lb_run_to_steady(cdf_lb *h, double tol, long long check_every, long long max_steps,
+                                long long *steps_taken, double *residual) {
+    g_err[0] = 0;
+    if (!h) return fail(CDF_EINVAL, "NULL handle");
+    if (!h->initialised) return fail(CDF_EINVAL, "state not initialised");
+    if (check_every < 1 || max_steps < 0 || !(tol > 0.0)) return fail(CDF_EINVAL, "bad tol / check_every / max_steps");
+    DeviceGuard g(h->device);
+    cdf_status st = enter(h);
+    if (st != CDF_OK) return st;
+    const int m = h->m;
+    const size_t mom_bytes = (size_t)(m + 3) * h->plane * 4;
+    double q[3 * kMaxM + 5];
+    long long taken = 0;
+    double R = INFINITY;
+    cdf_status result = CDF_ENOTCONVERGED;
+    while (taken < max_steps) {
+        CK(cudaMemcpyAsync(h->mom_prev, h->mom, mom_bytes, cudaMemcpyDeviceToDevice, h->s));
+        const long long k = std::min(check_every, max_steps - taken);
+        if ((st = run_steps(h, k)) != CDF_OK) return st;
+        taken += k;
+        if ((st = reduce(h, h->mom, h->mom_prev, q)) != CDF_OK) return st;
+        if (q[3 * m + 4] > 0) { result = CDF_EUNSTABLE; break; }
+        R = 0.0;
+        for (int f = 0; f < m + 2; ++f) {
+            const double den = std::max(q[2 * m + 2 + f], 1e-300);
+            R = std::max(R, q[m + f] / den);
+        }
+        if (k == check_every && R < tol) { result = CDF_OK; break; }
+    }
+    if (steps_taken) *steps_taken = taken;
+    if (residual) *residual = R;
+    if ((st = leave(h)) != CDF_OK) return st;
+    if (result == CDF_EUNSTABLE) return fail(CDF_EUNSTABLE, "non-finite moments after %lld steps", taken);
+    if (result == CDF_ENOTCONVERGED)
+        return fail(CDF_ENOTCONVERGED, "residual %.3e above tol %.3e after %lld steps", R, tol, taken);
+    return CDF_OK;
+}
+
+cdf_status cdf_lb_moments_device(cdf_lb *h, float *dev_out) {
+    g_err[0] = 0;
+    if (!h || !dev_out) return fail(CDF_EINVAL, "NULL argument");
+    if (!h->initialised) return fail(CDF_EINVAL, "state not initialised");
+    DeviceGuard g(h->device);
+    cdf_status st = enter(h);
+    if (st != CDF_OK) return st;
+    CK(launch_pack_moments(h->P, h->mom, dev_out, h->s));
+    return leave(h);
+}
+
+cdf_status cdf_lb_moments(cdf_lb *h, double *host_out) {
+    g_err[0] = 0;
+    if (!h || !host_out) return fail(CDF_EINVAL, "NULL argument");
+    if (!h->initialised) return fail(CDF_EINVAL, "state not initialised");
+    DeviceGuard g(h->device);
+    cdf_status st = enter(h);
+    if (st != CDF_OK) return st;
+    const size_t n = (size_t)h->nx * h->ny * (h->m + 3);
+    CK(launch_pack_moments(h->P, h->mom, h->dense, h->s));
+    CK(cudaMemcpyAsync(h->host_stage, h->dense, n * 4, cudaMemcpyDeviceToHost, h->s));
+    CK(cudaStreamSynchronize(h->s));
+    for (size_t i = 0; i < n; ++i) host_out[i] = h->host_stage[i];
+    return leave(h);
+}
+
+cdf_status cdf_lb_mass(cdf_lb *h, double *sums) {
+    g_err[0] = 0;
+    if (!h || !sums) return fail(CDF_EINVAL, "NULL argument");
+    if (!h->initialised) return fail(CDF_EINVAL, "state not initialised");
+    DeviceGuard g(h->device);
+    cdf_status st = enter(h);
+    if (st != CDF_OK) return st;
+    double q[3 * kMaxM + 5];
+    if ((st = reduce(h, h->mom, nullptr, q)) != CDF_OK) return st;
+    for (int a = 0; a < h->m; ++a) sums[a] = q[a];
+    return leave(h);
+}
+
+cdf_status cdf_lb_populations(cdf_lb *h, double *f, double *hf, double *s_now) {
+    g_err[0] = 0;
+    if (!h) return fail(CDF_EINVAL, "NULL handle");
+    if (!h->initialised) return fail(CDF_EINVAL, "state not initialised");
+    DeviceGuard g(h->device);
+    cdf_status st = enter(h);
+    if (st != CDF_OK) return st;
+    const size_t n = (size_t)h->nx * h->ny;
+    std::vector<float> tmp((size_t)h->planes * n), sp;
+    CK(launch_export(h->P, h->storage, h->buf[h->cur], h->dense, h->s));
+    CK(cudaMemcpyAsync(tmp.data(), h->dense, tmp.size() * 4, cudaMemcpyDeviceToHost, h->s));
+    if (s_now && h->sprev_planes) {
+        sp.resize((size_t)h->plane);
+        CK(cudaMemcpyAsync(sp.data(), h->sprev, sp.size() * 4, cudaMemcpyDeviceToHost, h->s));
+    }
+    CK(cudaStreamSynchronize(h->s));
+    if (hf)
+        for (size_t i = 0; i < 9 * n; ++i) hf[i] = tmp[i];
+    if (f)
+        for (size_t i = 0; i < (size_t)5 * h->m * n; ++i) f[i] = tmp[9 * n + i];
+    if (s_now) {
+        for (size_t i = 0; i < (size_t)h->m * n; ++i) s_now[i] = 0.0;
+        if (h->sprev_planes)
+            for (int y = 0; y < h->ny; ++y)
+                for (int x = 0; x < h->nx; ++x) s_now[n + (size_t)y * h->nx + x] = sp[(size_t)y * h->pitch + x];
+    }
+    return leave(h);
+}
+
+namespace {
+struct FileHeader {
+    char magic[8];
+    int version, nx, ny, m, storage, planes, sprev_planes, pitch;
+    long long t;
+    int cur;
+    int reserved[5];
+};
+const char kMagic[8] = {'C', 'D', 'F', 'L', 'B', '0', '0', '1'};
+}  // namespace
+
+cdf_status cdf_lb_save(cdf_lb *h, const char *path) {
+    g_err[0] = 0;
+    if (!h || !path) return fail(CDF_EINVAL, "NULL argument");
+    if (!h->initialised) return fail(CDF_EINVAL, "state not initialised");
+    DeviceGuard g(h->device);
+    cdf_status st = enter(h);
+    if (st != CDF_OK) return st;
+    const size_t pop = (size_t)h->planes * h->plane * elem_size(h->storage);
+    const size_t spb = (size_t)h->plane * 4, momb = (size_t)(h->m + 3) * h->plane * 4;
+    std::vector<char> data(pop + spb + momb);
+    CK(cudaMemcpyAsync(data.data(), h->buf[h->cur], pop, cudaMemcpyDeviceToHost, h->s));
+    CK(cudaMemcpyAsync(data.data() + pop, h->sprev, spb, cudaMemcpyDeviceToHost, h->s));
+    CK(cudaMemcpyAsync(data.data() + pop + spb, h->mom, momb, cudaMemcpyDeviceToHost, h->s));
+    CK(cudaStreamSynchronize(h->s));
+    FileHeader hd{};
+    std::memcpy(hd.magic, kMagic, 8);
+    hd.version = 1;
+    hd.nx = h->nx; hd.ny = h->ny; hd.m = h->m; hd.storage = h->storage;
+    hd.planes = h->planes; hd.sprev_planes = h->sprev_planes; hd.pitch = h->pitch; hd.t = h->t;
+    FILE *fp = std::fopen(path, "wb");
+    if (!fp) return fail(CDF_EIO, "cannot open %s for writing", path);
+    bool ok = std::fwrite(&hd, sizeof hd, 1, fp) == 1 && std::fwrite(data.data(), 1, data.size(), fp) == data.size();
+    ok = (std::fclose(fp) == 0) && ok;
+    if (!ok) return fail(CDF_EIO, "write to %s failed", path);
+    return leave(h);
+}
+
+cdf_status cdf_lb_load(cdf_lb *h, const char *path) {
+    g_err[0] = 0;
+    if (!h || !path) return fail(CDF_EINVAL, "NULL argument");
+    FILE *fp = std::fopen(path, "rb");
+    if (!fp) return fail(CDF_EIO, "cannot open %s", path);
+    FileHeader hd{};
+    if (std::fread(&hd, sizeof hd, 1, fp) != 1 || std::memcmp(hd.magic, kMagic, 8) != 0) {
+        std::fclose(fp);
+        return fail(CDF_EIO, "%s is not a cdf_lb checkpoint", path);
+    }
+    if (hd.nx != h->nx || hd.ny != h->ny || hd.m != h->m || hd.storage != h->storage ||
+        hd.planes != h->planes || hd.sprev_planes != h->sprev_planes || hd.pitch != h->pitch) {
+        std::fclose(fp);
+        return fail(CDF_EINVAL, "checkpoint does not match this solver's grid, m or storage");
+    }
+    const size_t pop = (size_t)h->planes * h->plane * elem_size(h->storage);
+    const size_t spb = (size_t)h->plane * 4, momb = (size_t)(h->m + 3) * h->plane * 4;
+    std::vector<char> data(pop + spb + momb);
+    const bool ok = std::fread(data.data(), 1, data.size(), fp) == data.size();
+    std::fclose(fp);
+    if (!ok) return fail(CDF_EIO, "%s is truncated", path);
+    DeviceGuard g(h->device);
+    cdf_status st = enter(h);
+    if (st != CDF_OK) return st;
+    CK(cudaMemcpyAsync(h->buf[0], data.data(), pop, cudaMemcpyHostToDevice, h->s));
+    CK(cudaMemcpyAsync(h->sprev, data.data() + pop, spb, cudaMemcpyHostToDevice, h->s));
+    CK(cudaMemcpyAsync(h->mom, data.data() + pop + spb, momb, cudaMemcpyHostToDevice, h->s));
+    CK(cudaStreamSynchronize(h->s));
+    h->cur = 0;
+    h->t = hd.t;
+    h->initialised = true;
+    return leave(h);
+}
+
+cdf_status cdf_lb_get_info(const cdf_lb *h, cdf_info *out) {
+    if (!h || !out) return fail(CDF_EINVAL, "NULL argument");
+    out->nx = h->nx; out->ny = h->ny; out->m = h->m; out->pitch = h->pitch;
+    out->storage = h->storage; out->planes = h->planes; out->sprev_planes = h->sprev_planes;
+    out->block_x = (int)h->block.x; out->block_y = (int)h->block.y;
+    out->bytes_per_lup = 2.0 * h->planes * (double)elem_size(h->storage) + 8.0 * h->sprev_planes;
+    out->t = h->t;
+    return CDF_OK;
+}
+
+void *cdf_lb_stream(const cdf_lb *h) { return h ? static_cast<void *>(h->s) : nullptr; }
+
+}  // extern "C"

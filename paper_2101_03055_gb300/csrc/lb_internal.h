@@ -1,0 +1,63 @@
+// Internal declarations shared by the host runtime and the kernel translation
+// units of libcdflb (not part of the C ABI).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace cdflb {
+
+constexpr int kMaxM = 4;
+
+// Everything a step / init kernel needs besides its buffers; passed by value.
+// All coefficients are in lattice units and already scaled for the kernels.
+struct LbParams {
+    int nx, ny, pitch;          // lattice size, elements per stored row
+    long long plane;            // elements per plane (pitch * ny)
+    int m;
+    // Relaxation (Eq. omega-D).  For constant D: omega itself.  For the
+    // chemotaxis closure: the inverse of the constant part B = D/cs^2 + I/2;
+    // the node value follows by a rank-one update (Sherman-Morrison).
+    float omega[kMaxM * kMaxM];
+    float omega_f;              // fluid relaxation, 1 / (3 nu + 1/2)
+    int chemotaxis;             // D_01 += -chi phi_0 r(phi_1)
+    float chi3;                 // 3 chi (the 1/cs^2 of Eq. omega-D folded in)
+    float c_star, eps2;         // cut-off and regularisation width squared
+    int r_regularised;
+    int skind;                  // 0 none, 1 const, 2 consumption (S_1 = -k phi_0 r)
+    float S[kMaxM];
+    float k;
+    float g[2];                 // F = g (Fbase + sum_a beta_a phi_a)
+    float beta[kMaxM];
+    float Fbase;
+    float rho0;
+    int periodic_x, periodic_y;
+    int freeslip[4];            // per side (west, east, south, north)
+    unsigned dirichlet[4];      // per side: bit a set -> scalar a is Dirichlet
+    float abb[4][kMaxM];        // per side and scalar: 2 W_i phi_w = phi_w / 3
+    float ref16[kMaxM];         // 16-bit storage: scalar reference values
+};
+
+enum Storage { kFP32 = 0, kFP16 = 1, kBF16 = 2 };
+
+// Launchers (lb_kernels.cu).  `in`/`out` point at the first of `planes`
+// population planes; plane k starts at base + k * plane.  Planes are ordered
+// h_0..h_8, then f_{a,0..4} for a = 0..m-1.
+cudaError_t launch_step(const LbParams &p, int storage, const void *in, void *out, float *sprev,
+                        float *moments, dim3 block, cudaStream_t s);
+cudaError_t launch_init(const LbParams &p, int storage, const float *fields, int fields_pitch,
+                        void *out, float *sprev, float *moments, cudaStream_t s);
+cudaError_t launch_export(const LbParams &p, int storage, const void *in, float *dense,
+                          cudaStream_t s);
+cudaError_t launch_pack_moments(const LbParams &p, const float *moments, float *dense,
+                                cudaStream_t s);
+
+// FP64 reductions (lb_reduce.cu).  Over `fields` stacks of (m+3) planes with the
+// given pitch: out[0..m) = sum phi_a; out[m + q] = sum |q_new - q_old| and
+// out[2m + 2 + q] = sum |q_new| for q in {phi_0..phi_{m-1}, u_x, u_y};
+// out[3m + 4] = count of non-finite values in the first m + 3 planes.
+constexpr int kReduceBlocks = 304;  // 2 x 152 SMs
+int reduce_quantities(int m);
+cudaError_t launch_reduce(const float *mom_new, const float *mom_old, int nx, int ny, int pitch,
+                          long long plane, int m, double *partials, double *out, cudaStream_t s);
+
+}  // namespace cdflb

@@ -1,0 +1,439 @@
+// Fused stream-and-collide kernels of the CDF lattice Boltzmann model
+// (Zhan, Chai & Shi, arXiv:2101.03055) for sm_103a.
+//
+// One thread owns one lattice node.  A step pulls the post-collision
+// populations of the previous step from the neighbours (x - c_i), substitutes
+// the boundary rule where the link crosses a wall, forms the moments (Eqs.
+// sum-phi, sum-u, sum-p), the closures and the relaxation matrix (Eq. omega-D),
+// collides (Eqs. evolution12, evolution3 with Eqs. feq-phi, heq, force,
+// source, Gi) and stores the new post-collision populations: one read and one
+// write of every population per step, nothing else in HBM.
+//
+// Storage is structure-of-arrays: plane k holds population k of every node,
+// rows padded to `pitch` elements (128-byte aligned rows).  Pull loads along
+// x are shifted by one element; consecutive threads still read consecutive
+// addresses, and the overlap between neighbouring warps is served from L1/L2.
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
+#include "lb_internal.h"
+
+namespace cdflb {
+namespace {
+
+// D2Q5 (Eq. D2Q5) and D2Q9 (Eq. D2Q9) weights; velocities are spelled out in
+// the pull and collision code below, direction by direction.
+__host__ __device__ constexpr float kW5(int i) { return i == 0 ? 1.f / 3.f : 1.f / 6.f; }
+__host__ __device__ constexpr float kW9(int i) { return i == 0 ? 4.f / 9.f : (i < 5 ? 1.f / 9.f : 1.f / 36.f); }
+__host__ __device__ constexpr int kC5x(int i) { return i == 1 ? 1 : (i == 3 ? -1 : 0); }
+__host__ __device__ constexpr int kC5y(int i) { return i == 2 ? 1 : (i == 4 ? -1 : 0); }
+__host__ __device__ constexpr int kC9x(int i) { return (i == 1 || i == 5 || i == 8) ? 1 : ((i == 3 || i == 6 || i == 7) ? -1 : 0); }
+__host__ __device__ constexpr int kC9y(int i) { return (i == 2 || i == 5 || i == 6) ? 1 : ((i == 4 || i == 7 || i == 8) ? -1 : 0); }
+
+// ---- storage types: FP32 values, or 16-bit deviations from a reference -------
+template <typename T> struct Store;
+template <> struct Store<float> {
+    static constexpr bool kDev = false;
+    __device__ static float load(const float *p) { return __ldg(p); }
+    __device__ static void store(float *p, float v) { *p = v; }
+};
+template <> struct Store<__half> {
+    static constexpr bool kDev = true;
+    __device__ static float load(const __half *p) { return __half2float(__ldg(p)); }
+    __device__ static void store(__half *p, float v) { *p = __float2half_rn(v); }
+};
+template <> struct Store<__nv_bfloat16> {
+    static constexpr bool kDev = true;
+    __device__ static float load(const __nv_bfloat16 *p) { return __bfloat162float(__ldg(p)); }
+    __device__ static void store(__nv_bfloat16 *p, float v) { *p = __float2bfloat16_rn(v); }
+};
+
+// Reference subtracted before a 16-bit store: (rho0, 0, ..., 0) for the fluid,
+// W_i phi_ref_a for scalar a.
+template <typename T>
+__device__ __forceinline__ float fluid_ref(const LbParams &p, int i) {
+    return (Store<T>::kDev && i == 0) ? p.rho0 : 0.f;
+}
+template <typename T>
+__device__ __forceinline__ float scalar_ref(const LbParams &p, int a, int i) {
+    return Store<T>::kDev ? kW5(i) * p.ref16[a] : 0.f;
+}
+
+__device__ __forceinline__ float cutoff(const LbParams &p, float c) {
+    // r(c): step (Sec. 3.1.3) or regularised (Sec. 3.1.2)
+    if (p.r_regularised) {
+        float d = c - p.c_star;
+        return 0.5f * (1.f + d * rsqrtf(d * d + p.eps2));
+    }
+    return c >= p.c_star ? 1.f : 0.f;
+}
+
+// Node-local moments: phi_a, u, p; plus S(t) of the consumption closure.
+template <int M>
+struct NodeOut {
+    float phi[M], ux, uy, pr, s1;
+};
+
+// Collision of one node (Eqs. evolution12, evolution3).  f, h: pre-collision
+// populations, overwritten by the post-collision ones.  sp1: S_1(t-1) of the
+// consumption closure (ignored otherwise); `first` uses S(t-1) = S(t).
+template <int M>
+__device__ __forceinline__ void collide(const LbParams &p, float (&f)[M][5], float (&h)[9],
+                                        float sp1, bool first, NodeOut<M> &o) {
+    // Eq. sum-phi and the closures of Sec. 3
+    float phi[M];
+#pragma unroll
+    for (int a = 0; a < M; ++a) phi[a] = ((f[a][0] + f[a][1]) + (f[a][2] + f[a][3])) + f[a][4];
+    float r = 0.f;
+    if (M >= 2 && (p.chemotaxis || p.skind == 2)) r = cutoff(p, phi[M >= 2 ? 1 : 0]);
+    float S[M], Sp[M];
+#pragma unroll
+    for (int a = 0; a < M; ++a) {
+        S[a] = (p.skind == 1) ? p.S[a] : 0.f;
+        Sp[a] = S[a];
+    }
+    if (M >= 2 && p.skind == 2) {
+        S[1] = -p.k * phi[0] * r;
+        Sp[1] = first ? S[1] : sp1;
+    }
+    float fm = p.Fbase;
+#pragma unroll
+    for (int a = 0; a < M; ++a) fm = fmaf(p.beta[a], phi[a], fm);
+    const float Fx = p.g[0] * fm, Fy = p.g[1] * fm;
+
+    // Eq. sum-u and Eq. sum-p (varphi = 0): p = cs^2/(1-W0) [sum_{i!=0} h_i - W0 u.u/(2 cs^2)]
+    const float jx = (h[1] - h[3]) + (h[5] - h[6]) + (h[8] - h[7]);
+    const float jy = (h[2] - h[4]) + (h[5] - h[8]) + (h[6] - h[7]);
+    const float ux = jx + 0.5f * Fx, uy = jy + 0.5f * Fy;
+    const float usq = ux * ux + uy * uy;
+    const float snr = ((h[1] + h[2]) + (h[3] + h[4])) + ((h[5] + h[6]) + (h[7] + h[8]));
+    const float pr = 0.6f * (snr - (2.f / 3.f) * usq);
+
+    // Eq. omega-D.  Constant D: omega from the host.  Chemotaxis: omega^-1 =
+    // B + delta e_0 e_1^T with delta = -3 chi phi_0 r, inverted by Sherman-Morrison.
+    float om[M][M];
+#pragma unroll
+    for (int a = 0; a < M; ++a)
+#pragma unroll
+        for (int b = 0; b < M; ++b) om[a][b] = p.omega[a * M + b];
+    if (M >= 2 && p.chemotaxis) {
+        const float delta = -p.chi3 * phi[0] * r;
+        const float den = 1.f / (1.f + delta * om[1][0]);
+        float col0[M], row1[M];
+#pragma unroll
+        for (int a = 0; a < M; ++a) { col0[a] = om[a][0]; row1[a] = om[M >= 2 ? 1 : 0][a]; }
+#pragma unroll
+        for (int a = 0; a < M; ++a)
+#pragma unroll
+            for (int b = 0; b < M; ++b) om[a][b] -= delta * den * col0[a] * row1[b];
+    }
+
+    // Eq. Gi: G_{i,a} = 3 W_i c_i . J_a,  J_a = sum_b (delta_ab - omega_ab / 2)(u S_b + phi_b F)
+    float Jx[M], Jy[M];
+#pragma unroll
+    for (int a = 0; a < M; ++a) {
+        float jxa = 0.f, jya = 0.f;
+#pragma unroll
+        for (int b = 0; b < M; ++b) {
+            const float c = (a == b ? 1.f : 0.f) - 0.5f * om[a][b];
+            jxa = fmaf(c, fmaf(ux, S[b], phi[b] * Fx), jxa);
+            jya = fmaf(c, fmaf(uy, S[b], phi[b] * Fy), jya);
+        }
+        Jx[a] = jxa;
+        Jy[a] = jya;
+    }
+
+    // Eq. evolution12 with f^eq_i = W_i phi (1 + 3 c_i.u) (Eq. feq-phi, lambda = I,
+    // vartheta = 0), source W_i S and the backward difference (S(t) - S(t-1)) / 2.
+#pragma unroll
+    for (int i = 0; i < 5; ++i) {
+        const float cu = kC5x(i) * ux + kC5y(i) * uy;
+        float neq[M];
+#pragma unroll
+        for (int b = 0; b < M; ++b) neq[b] = f[b][i] - kW5(i) * phi[b] * fmaf(3.f, cu, 1.f);
+#pragma unroll
+        for (int a = 0; a < M; ++a) {
+            float coll = 0.f;
+#pragma unroll
+            for (int b = 0; b < M; ++b) coll = fmaf(om[a][b], neq[b], coll);
+            const float src = kW5(i) * (1.5f * S[a] - 0.5f * Sp[a]);
+            const float G = 3.f * kW5(i) * (kC5x(i) * Jx[a] + kC5y(i) * Jy[a]);
+            f[a][i] = (f[a][i] - coll) + (src + G);
+        }
+    }
+
+    // Eq. evolution3 with Eq. heq (sigma_0 = rho0 - 5p/3, sigma_i = 3 W_i p) and
+    // Eq. force (varphi = 0): F_i = 3 W_i c_i.F, weighted by (1 - omega_f / 2).
+    const float wf = p.omega_f, fw = 1.f - 0.5f * wf;
+#pragma unroll
+    for (int i = 0; i < 9; ++i) {
+        const float cu = kC9x(i) * ux + kC9y(i) * uy;
+        const float sigma = (i == 0) ? (p.rho0 - (5.f / 3.f) * pr) : 3.f * kW9(i) * pr;
+        const float heq = sigma + kW9(i) * (3.f * cu + 4.5f * cu * cu - 1.5f * usq);
+        const float Fi = 3.f * kW9(i) * (kC9x(i) * Fx + kC9y(i) * Fy);
+        h[i] = h[i] - wf * (h[i] - heq) + fw * Fi;
+    }
+#pragma unroll
+    for (int a = 0; a < M; ++a) o.phi[a] = phi[a];
+    o.ux = ux;
+    o.uy = uy;
+    o.pr = pr;
+    o.s1 = (M >= 2) ? S[M >= 2 ? 1 : 0] : 0.f;
+}
+
+// ---- the fused step ------------------------------------------------------------
+template <int M, typename T>
+__global__ void __launch_bounds__(256) step_kernel(const LbParams p, const T *__restrict__ in,
+                                                   T *__restrict__ out, float *__restrict__ sprev,
+                                                   float *__restrict__ moments) {
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int y = blockIdx.y * blockDim.y + threadIdx.y;
+    if (x >= p.nx || y >= p.ny) return;
+    const long long P = p.plane;
+
+    // Neighbour coordinates (periodic wrap) and wall crossings of the pull links.
+    int xw = x - 1, xe = x + 1, ys = y - 1, yn = y + 1;
+    bool cw = false, ce = false, cs = false, cn = false;
+    if (xw < 0) { if (p.periodic_x) xw += p.nx; else cw = true; }
+    if (xe >= p.nx) { if (p.periodic_x) xe -= p.nx; else ce = true; }
+    if (ys < 0) { if (p.periodic_y) ys += p.ny; else cs = true; }
+    if (yn >= p.ny) { if (p.periodic_y) yn -= p.ny; else cn = true; }
+    const long long r0 = (long long)y * p.pitch, rs = (long long)ys * p.pitch,
+                    rn = (long long)yn * p.pitch;
+    const long long o0 = r0 + x;
+
+    // Fluid, D2Q9: h_i(x) = h*_i(x - c_i); bounce-back h*_opp(i)(x) across a
+    // no-slip wall; specular image across a free-slip wall; bounce-back at corners.
+    auto H = [&](int i, long long off) -> float {
+        return Store<T>::load(in + i * P + off) + fluid_ref<T>(p, i);
+    };
+    float h[9];
+    h[0] = H(0, o0);
+    h[1] = cw ? H(3, o0) : H(1, r0 + xw);
+    h[2] = cs ? H(4, o0) : H(2, rs + x);
+    h[3] = ce ? H(1, o0) : H(3, r0 + xe);
+    h[4] = cn ? H(2, o0) : H(4, rn + x);
+    // (1,1) from (x-1, y-1)
+    if (cw && cs) h[5] = H(7, o0);
+    else if (cw) h[5] = p.freeslip[0] ? H(6, rs + x) : H(7, o0);
+    else if (cs) h[5] = p.freeslip[2] ? H(8, r0 + xw) : H(7, o0);
+    else h[5] = H(5, rs + xw);
+    // (-1,1) from (x+1, y-1)
+    if (ce && cs) h[6] = H(8, o0);
+    else if (ce) h[6] = p.freeslip[1] ? H(5, rs + x) : H(8, o0);
+    else if (cs) h[6] = p.freeslip[2] ? H(7, r0 + xe) : H(8, o0);
+    else h[6] = H(6, rs + xe);
+    // (-1,-1) from (x+1, y+1)
+    if (ce && cn) h[7] = H(5, o0);
+    else if (ce) h[7] = p.freeslip[1] ? H(8, rn + x) : H(5, o0);
+    else if (cn) h[7] = p.freeslip[3] ? H(6, r0 + xe) : H(5, o0);
+    else h[7] = H(7, rn + xe);
+    // (1,-1) from (x-1, y+1)
+    if (cw && cn) h[8] = H(6, o0);
+    else if (cw) h[8] = p.freeslip[0] ? H(7, rn + x) : H(6, o0);
+    else if (cn) h[8] = p.freeslip[3] ? H(5, r0 + xw) : H(6, o0);
+    else h[8] = H(8, rn + xw);
+
+    // Scalars, D2Q5: bounce-back f*_opp(i)(x) (no flux) or anti-bounce-back
+    // -f*_opp(i)(x) + 2 W_i phi_w (Dirichlet) across a wall.
+    float f[M][5];
+#pragma unroll
+    for (int a = 0; a < M; ++a) {
+        const T *base = in + (9 + 5 * a) * P;
+        auto F = [&](int i, long long off) -> float {
+            return Store<T>::load(base + i * P + off) + scalar_ref<T>(p, a, i);
+        };
+        auto wall = [&](int side, float v) -> float {
+            return ((p.dirichlet[side] >> a) & 1u) ? p.abb[side][a] - v : v;
+        };
+        f[a][0] = F(0, o0);
+        f[a][1] = cw ? wall(0, F(3, o0)) : F(1, r0 + xw);
+        f[a][2] = cs ? wall(2, F(4, o0)) : F(2, rs + x);
+        f[a][3] = ce ? wall(1, F(1, o0)) : F(3, r0 + xe);
+        f[a][4] = cn ? wall(3, F(2, o0)) : F(4, rn + x);
+    }
+    const bool consume = (M >= 2 && p.skind == 2);
+    const float sp1 = consume ? sprev[o0] : 0.f;
+
+    NodeOut<M> o;
+    collide<M>(p, f, h, sp1, false, o);
+
+#pragma unroll
+    for (int i = 0; i < 9; ++i) Store<T>::store(out + i * P + o0, h[i] - fluid_ref<T>(p, i));
+#pragma unroll
+    for (int a = 0; a < M; ++a)
+#pragma unroll
+        for (int i = 0; i < 5; ++i)
+            Store<T>::store(out + (9 + 5 * a + i) * P + o0, f[a][i] - scalar_ref<T>(p, a, i));
+    if (consume) sprev[o0] = o.s1;
+    if (moments) {
+#pragma unroll
+        for (int a = 0; a < M; ++a) moments[a * P + o0] = o.phi[a];
+        moments[M * P + o0] = o.ux;
+        moments[(M + 1) * P + o0] = o.uy;
+        moments[(M + 2) * P + o0] = o.pr;
+    }
+}
+
+// ---- initialisation from moments (collide-only pass at t = 0) ------------------
+template <int M, typename T>
+__global__ void init_kernel(const LbParams p, const float *__restrict__ fields, int fpitch,
+                            T *__restrict__ out, float *__restrict__ sprev,
+                            float *__restrict__ moments) {
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int y = blockIdx.y * blockDim.y + threadIdx.y;
+    if (x >= p.nx || y >= p.ny) return;
+    const long long P = p.plane, FP = (long long)fpitch * p.ny;
+    const long long o0 = (long long)y * p.pitch + x, i0 = (long long)y * fpitch + x;
+    float phi[M];
+#pragma unroll
+    for (int a = 0; a < M; ++a) phi[a] = fields[a * FP + i0];
+    const float ux = fields[M * FP + i0], uy = fields[(M + 1) * FP + i0];
+    const float pr = fields[(M + 2) * FP + i0];
+    float fm = p.Fbase;
+#pragma unroll
+    for (int a = 0; a < M; ++a) fm = fmaf(p.beta[a], phi[a], fm);
+    const float Fx = p.g[0] * fm, Fy = p.g[1] * fm;
+    // f = f^eq(phi, u); h = h^eq(u, p) - F_i / 2 (moments then return the inputs)
+    float f[M][5], h[9];
+    const float usq = ux * ux + uy * uy;
+#pragma unroll
+    for (int i = 0; i < 5; ++i) {
+        const float cu = kC5x(i) * ux + kC5y(i) * uy;
+#pragma unroll
+        for (int a = 0; a < M; ++a) f[a][i] = kW5(i) * phi[a] * fmaf(3.f, cu, 1.f);
+    }
+#pragma unroll
+    for (int i = 0; i < 9; ++i) {
+        const float cu = kC9x(i) * ux + kC9y(i) * uy;
+        const float sigma = (i == 0) ? (p.rho0 - (5.f / 3.f) * pr) : 3.f * kW9(i) * pr;
+        const float heq = sigma + kW9(i) * (3.f * cu + 4.5f * cu * cu - 1.5f * usq);
+        h[i] = heq - 0.5f * 3.f * kW9(i) * (kC9x(i) * Fx + kC9y(i) * Fy);
+    }
+    NodeOut<M> o;
+    collide<M>(p, f, h, 0.f, true, o);
+#pragma unroll
+    for (int i = 0; i < 9; ++i) Store<T>::store(out + i * P + o0, h[i] - fluid_ref<T>(p, i));
+#pragma unroll
+    for (int a = 0; a < M; ++a)
+#pragma unroll
+        for (int i = 0; i < 5; ++i)
+            Store<T>::store(out + (9 + 5 * a + i) * P + o0, f[a][i] - scalar_ref<T>(p, a, i));
+    if (M >= 2 && p.skind == 2) sprev[o0] = o.s1;
+#pragma unroll
+    for (int a = 0; a < M; ++a) moments[a * P + o0] = o.phi[a];
+    moments[M * P + o0] = o.ux;
+    moments[(M + 1) * P + o0] = o.uy;
+    moments[(M + 2) * P + o0] = o.pr;
+}
+
+// Post-collision populations as dense FP32 planes [9 + 5m][ny][nx].
+template <int M, typename T>
+__global__ void export_kernel(const LbParams p, const T *__restrict__ in, float *__restrict__ dense) {
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int y = blockIdx.y * blockDim.y + threadIdx.y;
+    if (x >= p.nx || y >= p.ny) return;
+    const long long P = p.plane, N = (long long)p.nx * p.ny;
+    const long long o0 = (long long)y * p.pitch + x, d0 = (long long)y * p.nx + x;
+#pragma unroll
+    for (int i = 0; i < 9; ++i) dense[i * N + d0] = Store<T>::load(in + i * P + o0) + fluid_ref<T>(p, i);
+#pragma unroll
+    for (int a = 0; a < M; ++a)
+#pragma unroll
+        for (int i = 0; i < 5; ++i)
+            dense[(9 + 5 * a + i) * N + d0] =
+                Store<T>::load(in + (9 + 5 * a + i) * P + o0) + scalar_ref<T>(p, a, i);
+}
+
+__global__ void pack_kernel(const LbParams p, int nf, const float *__restrict__ mom,
+                            float *__restrict__ dense) {
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int y = blockIdx.y * blockDim.y + threadIdx.y;
+    if (x >= p.nx || y >= p.ny) return;
+    const long long P = p.plane, N = (long long)p.nx * p.ny;
+    for (int k = 0; k < nf; ++k) dense[k * N + (long long)y * p.nx + x] = mom[k * P + (long long)y * p.pitch + x];
+}
+
+template <typename T>
+cudaError_t step_dispatch(const LbParams &p, const void *in, void *out, float *sprev, float *mom,
+                          dim3 block, cudaStream_t s) {
+    dim3 grid((p.nx + block.x - 1) / block.x, (p.ny + block.y - 1) / block.y);
+    const T *i = static_cast<const T *>(in);
+    T *o = static_cast<T *>(out);
+    switch (p.m) {
+        case 1: step_kernel<1, T><<<grid, block, 0, s>>>(p, i, o, sprev, mom); break;
+        case 2: step_kernel<2, T><<<grid, block, 0, s>>>(p, i, o, sprev, mom); break;
+        case 3: step_kernel<3, T><<<grid, block, 0, s>>>(p, i, o, sprev, mom); break;
+        case 4: step_kernel<4, T><<<grid, block, 0, s>>>(p, i, o, sprev, mom); break;
+        default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t init_dispatch(const LbParams &p, const float *fields, int fpitch, void *out, float *sprev,
+                          float *mom, cudaStream_t s) {
+    dim3 block(128, 2), grid((p.nx + 127) / 128, (p.ny + 1) / 2);
+    T *o = static_cast<T *>(out);
+    switch (p.m) {
+        case 1: init_kernel<1, T><<<grid, block, 0, s>>>(p, fields, fpitch, o, sprev, mom); break;
+        case 2: init_kernel<2, T><<<grid, block, 0, s>>>(p, fields, fpitch, o, sprev, mom); break;
+        case 3: init_kernel<3, T><<<grid, block, 0, s>>>(p, fields, fpitch, o, sprev, mom); break;
+        case 4: init_kernel<4, T><<<grid, block, 0, s>>>(p, fields, fpitch, o, sprev, mom); break;
+        default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t export_dispatch(const LbParams &p, const void *in, float *dense, cudaStream_t s) {
+    dim3 block(128, 2), grid((p.nx + 127) / 128, (p.ny + 1) / 2);
+    const T *i = static_cast<const T *>(in);
+    switch (p.m) {
+        case 1: export_kernel<1, T><<<grid, block, 0, s>>>(p, i, dense); break;
+        case 2: export_kernel<2, T><<<grid, block, 0, s>>>(p, i, dense); break;
+        case 3: export_kernel<3, T><<<grid, block, 0, s>>>(p, i, dense); break;
+        case 4: export_kernel<4, T><<<grid, block, 0, s>>>(p, i, dense); break;
+        default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_step(const LbParams &p, int storage, const void *in, void *out, float *sprev,
+                        float *moments, dim3 block, cudaStream_t s) {
+    switch (storage) {
+        case kFP32: return step_dispatch<float>(p, in, out, sprev, moments, block, s);
+        case kFP16: return step_dispatch<__half>(p, in, out, sprev, moments, block, s);
+        case kBF16: return step_dispatch<__nv_bfloat16>(p, in, out, sprev, moments, block, s);
+    }
+    return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_init(const LbParams &p, int storage, const float *fields, int fields_pitch,
+                        void *out, float *sprev, float *moments, cudaStream_t s) {
+    switch (storage) {
+        case kFP32: return init_dispatch<float>(p, fields, fields_pitch, out, sprev, moments, s);
+        case kFP16: return init_dispatch<__half>(p, fields, fields_pitch, out, sprev, moments, s);
+        case kBF16: return init_dispatch<__nv_bfloat16>(p, fields, fields_pitch, out, sprev, moments, s);
+    }
+    return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_export(const LbParams &p, int storage, const void *in, float *dense, cudaStream_t s) {
+    switch (storage) {
+        case kFP32: return export_dispatch<float>(p, in, dense, s);
+        case kFP16: return export_dispatch<__half>(p, in, dense, s);
+        case kBF16: return export_dispatch<__nv_bfloat16>(p, in, dense, s);
+    }
+    return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_pack_moments(const LbParams &p, const float *moments, float *dense, cudaStream_t s) {
+    dim3 block(128, 2), grid((p.nx + 127) / 128, (p.ny + 1) / 2);
+    pack_kernel<<<grid, block, 0, s>>>(p, p.m + 3, moments, dense);
+    return cudaGetLastError();
+}
+
+}  // namespace cdflb

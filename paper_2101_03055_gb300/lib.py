@@ -1,0 +1,337 @@
+"""Thin ctypes binding of libcdflb (include/cdf_lb.h).
+
+Argument marshalling only: every step of the solver runs in the CUDA library.
+The functions keep the C names (cdf_lb_create, cdf_lb_step, ...); `Solver`
+wraps a handle for convenience.  PyTorch is used for device memory and streams
+only (device tensors are passed as raw pointers).  There is no CPU fallback:
+loading fails loudly when the library is missing or cannot be loaded.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from .inputs import Problem
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libcdflb.so")
+MAX_M = 4
+
+CDF_OK, CDF_EINVAL, CDF_ENOMEM, CDF_ECUDA, CDF_ENOTCONVERGED, CDF_EUNSTABLE, CDF_ETIMEOUT, CDF_EIO = range(8)
+STATUS_NAMES = ["CDF_OK", "CDF_EINVAL", "CDF_ENOMEM", "CDF_ECUDA", "CDF_ENOTCONVERGED",
+                "CDF_EUNSTABLE", "CDF_ETIMEOUT", "CDF_EIO"]
+STORAGE = {"fp32": 0, "fp16": 1, "bf16": 2}
+
+
+class CdfError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS_NAMES[status] if 0 <= status < 8 else status}: {msg}")
+        self.status = status
+
+
+class cdf_grid(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int)]
+
+
+class cdf_diffusion(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int), ("D", ctypes.c_double * (MAX_M * MAX_M)),
+                ("chi", ctypes.c_double), ("c_star", ctypes.c_double), ("eps", ctypes.c_double),
+                ("r_regularised", ctypes.c_int)]
+
+
+class cdf_source(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int), ("S", ctypes.c_double * MAX_M), ("k", ctypes.c_double)]
+
+
+class cdf_force(ctypes.Structure):
+    _fields_ = [("g", ctypes.c_double * 2), ("beta", ctypes.c_double * MAX_M),
+                ("phi_ref", ctypes.c_double * MAX_M), ("F0", ctypes.c_double)]
+
+
+class cdf_side(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int), ("fluid", ctypes.c_int), ("scalar", ctypes.c_int * MAX_M),
+                ("value", ctypes.c_double * MAX_M)]
+
+
+class cdf_boundaries(ctypes.Structure):
+    _fields_ = [("west", cdf_side), ("east", cdf_side), ("south", cdf_side), ("north", cdf_side)]
+
+
+class cdf_options(ctypes.Structure):
+    _fields_ = [("storage", ctypes.c_int), ("rho0", ctypes.c_double), ("cuda_stream", ctypes.c_void_p),
+                ("phi_ref16", ctypes.c_double * MAX_M), ("block_x", ctypes.c_int), ("block_y", ctypes.c_int)]
+
+
+class cdf_info(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int), ("m", ctypes.c_int), ("pitch", ctypes.c_int),
+                ("storage", ctypes.c_int), ("planes", ctypes.c_int), ("sprev_planes", ctypes.c_int),
+                ("block_x", ctypes.c_int), ("block_y", ctypes.c_int), ("bytes_per_lup", ctypes.c_double),
+                ("t", ctypes.c_longlong)]
+
+
+_DP = ctypes.POINTER(ctypes.c_double)
+_FP = ctypes.c_void_p
+_H = ctypes.c_void_p
+_lib = None
+
+# name -> (restype, argtypes); the C ABI of include/cdf_lb.h
+SIGNATURES = {
+    "cdf_lb_create": (ctypes.c_int, [ctypes.POINTER(cdf_grid), ctypes.c_int, ctypes.POINTER(cdf_diffusion),
+                                     ctypes.c_double, ctypes.POINTER(cdf_source), ctypes.POINTER(cdf_force),
+                                     ctypes.POINTER(cdf_boundaries), ctypes.POINTER(cdf_options),
+                                     ctypes.POINTER(ctypes.c_void_p)]),
+    "cdf_lb_init_moments": (ctypes.c_int, [_H, _DP, _DP, _DP]),
+    "cdf_lb_init_moments_device": (ctypes.c_int, [_H, _FP]),
+    "cdf_lb_step": (ctypes.c_int, [_H, ctypes.c_longlong]),
+    "cdf_lb_run_to_steady": (ctypes.c_int, [_H, ctypes.c_double, ctypes.c_longlong, ctypes.c_longlong,
+                                            ctypes.POINTER(ctypes.c_longlong), _DP]),
+    "cdf_lb_moments": (ctypes.c_int, [_H, _DP]),
+    "cdf_lb_moments_device": (ctypes.c_int, [_H, _FP]),
+    "cdf_lb_mass": (ctypes.c_int, [_H, _DP]),
+    "cdf_lb_populations": (ctypes.c_int, [_H, _DP, _DP, _DP]),
+    "cdf_lb_save": (ctypes.c_int, [_H, ctypes.c_char_p]),
+    "cdf_lb_load": (ctypes.c_int, [_H, ctypes.c_char_p]),
+    "cdf_lb_get_info": (ctypes.c_int, [_H, ctypes.POINTER(cdf_info)]),
+    "cdf_lb_stream": (ctypes.c_void_p, [_H]),
+    "cdf_lb_destroy": (None, [_H]),
+    "cdf_lb_last_error": (ctypes.c_char_p, []),
+}
+
+
+def load(path: str = LIB_PATH):
+    """Load libcdflb; raises if it is missing (build it with build.build())."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(path):
+            raise RuntimeError(f"libcdflb not built: {path} is missing (run paper_2101_03055_gb300.build.build())")
+        lib = ctypes.CDLL(path)
+        for name, (res, args) in SIGNATURES.items():
+            fn = getattr(lib, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = lib
+    return _lib
+
+
+def _check(status: int):
+    if status != CDF_OK:
+        raise CdfError(status, load().cdf_lb_last_error().decode())
+
+
+def _dptr(a: np.ndarray):
+    assert a.dtype == np.float64 and a.flags.c_contiguous
+    return a.ctypes.data_as(_DP)
+
+
+# ---- same-name wrappers -----------------------------------------------------------
+def cdf_lb_create(grid, m, diffusion, nu, source, force, boundaries, options):
+    h = ctypes.c_void_p()
+    _check(load().cdf_lb_create(ctypes.byref(grid), m, ctypes.byref(diffusion), nu, ctypes.byref(source),
+                                ctypes.byref(force), ctypes.byref(boundaries), ctypes.byref(options),
+                                ctypes.byref(h)))
+    return h
+
+
+def cdf_lb_init_moments(h, phi, u, p=None):
+    _check(load().cdf_lb_init_moments(h, _dptr(phi), _dptr(u), None if p is None else _dptr(p)))
+
+
+def cdf_lb_init_moments_device(h, dev_ptr: int):
+    _check(load().cdf_lb_init_moments_device(h, ctypes.c_void_p(dev_ptr)))
+
+
+def cdf_lb_step(h, n: int):
+    _check(load().cdf_lb_step(h, int(n)))
+
+
+def cdf_lb_run_to_steady(h, tol, check_every, max_steps):
+    steps = ctypes.c_longlong(0)
+    res = ctypes.c_double(0.0)
+    st = load().cdf_lb_run_to_steady(h, tol, int(check_every), int(max_steps), ctypes.byref(steps), ctypes.byref(res))
+    return st, steps.value, res.value
+
+
+def cdf_lb_moments(h, out: np.ndarray):
+    _check(load().cdf_lb_moments(h, _dptr(out)))
+
+
+def cdf_lb_moments_device(h, dev_ptr: int):
+    _check(load().cdf_lb_moments_device(h, ctypes.c_void_p(dev_ptr)))
+
+
+def cdf_lb_mass(h, out: np.ndarray):
+    _check(load().cdf_lb_mass(h, _dptr(out)))
+
+
+def cdf_lb_populations(h, f=None, hf=None, s_now=None):
+    _check(load().cdf_lb_populations(h, None if f is None else _dptr(f), None if hf is None else _dptr(hf),
+                                     None if s_now is None else _dptr(s_now)))
+
+
+def cdf_lb_save(h, path: str):
+    _check(load().cdf_lb_save(h, path.encode()))
+
+
+def cdf_lb_load(h, path: str):
+    _check(load().cdf_lb_load(h, path.encode()))
+
+
+def cdf_lb_get_info(h) -> cdf_info:
+    info = cdf_info()
+    _check(load().cdf_lb_get_info(h, ctypes.byref(info)))
+    return info
+
+
+def cdf_lb_stream(h) -> int:
+    return load().cdf_lb_stream(h) or 0
+
+
+def cdf_lb_destroy(h):
+    load().cdf_lb_destroy(h)
+
+
+def cdf_lb_last_error() -> str:
+    return load().cdf_lb_last_error().decode()
+
+
+# ---- problem description -> C structs ------------------------------------------------
+def structs_from_problem(pb: Problem, storage: str = "fp32", stream: int = 0, block=None, phi_ref16=None):
+    m = pb.m
+    if m > MAX_M:
+        raise ValueError(f"m = {m} > {MAX_M}")
+    grid = cdf_grid(pb.nx, pb.ny)
+    dif = cdf_diffusion()
+    dif.kind = {"const": 0, "chemotaxis": 1}[pb.dkind]
+    for a in range(m):
+        for b in range(m):
+            dif.D[a * m + b] = float(pb.D[a, b])
+    dif.chi, dif.c_star, dif.eps, dif.r_regularised = pb.chi, pb.c_star, pb.eps, int(pb.r_regularised)
+    src = cdf_source()
+    src.kind = {"none": 0, "const": 1, "consumption": 2}[pb.skind]
+    src.k = pb.k
+    frc = cdf_force()
+    frc.g[0], frc.g[1] = float(pb.g[0]), float(pb.g[1])
+    frc.F0 = pb.F0
+    for a in range(m):
+        src.S[a] = float(pb.S[a])
+        frc.beta[a] = float(pb.beta[a])
+        frc.phi_ref[a] = float(pb.phi_ref[a])
+    bc = cdf_boundaries()
+    for name in ("west", "east", "south", "north"):
+        side, cs = getattr(pb, name), getattr(bc, name)
+        cs.kind = {"periodic": 0, "wall": 1}[side.kind]
+        cs.fluid = {"noslip": 0, "freeslip": 1}[side.fluid]
+        for a in range(m):
+            cs.scalar[a] = {"noflux": 0, "dirichlet": 1}[side.scalar[a]]
+            cs.value[a] = float(side.value[a])
+    opt = cdf_options()
+    opt.storage = STORAGE[storage]
+    opt.rho0 = pb.rho0
+    opt.cuda_stream = stream or None
+    ref = phi_ref16 if phi_ref16 is not None else default_ref16(pb)
+    for a in range(m):
+        opt.phi_ref16[a] = float(ref[a])
+    if block is not None:
+        opt.block_x, opt.block_y = block
+    return grid, dif, src, frc, bc, opt
+
+
+def default_ref16(pb: Problem):
+    """Reference scalar values of the 16-bit deviation storage: the midpoint of the
+    initial range of each scalar, widened to include its Dirichlet values."""
+    ref = []
+    for a in range(pb.m):
+        lo, hi = float(pb.phi0[a].min()), float(pb.phi0[a].max())
+        for name in ("west", "east", "south", "north"):
+            side = getattr(pb, name)
+            if side.kind == "wall" and side.scalar[a] == "dirichlet":
+                lo, hi = min(lo, side.value[a]), max(hi, side.value[a])
+        ref.append(0.5 * (lo + hi))
+    return ref
+
+
+class Solver:
+    """One lattice on the GPU behind the C ABI."""
+
+    def __init__(self, pb: Problem, storage: str = "fp32", stream: int = 0, block=None, init: bool = True,
+                 phi_ref16=None):
+        self.pb = pb
+        self.m, self.nx, self.ny = pb.m, pb.nx, pb.ny
+        self.storage = storage
+        self._structs = structs_from_problem(pb, storage, stream, block, phi_ref16)
+        grid, dif, src, frc, bc, opt = self._structs
+        self.h = cdf_lb_create(grid, pb.m, dif, pb.nu, src, frc, bc, opt)
+        if init:
+            self.init_moments(pb.phi0, pb.u0, pb.p0)
+
+    def close(self):
+        if getattr(self, "h", None):
+            cdf_lb_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def init_moments(self, phi, u, p=None):
+        cdf_lb_init_moments(self.h, np.ascontiguousarray(phi, np.float64), np.ascontiguousarray(u, np.float64),
+                            None if p is None else np.ascontiguousarray(p, np.float64))
+
+    def init_moments_device(self, fields):
+        """fields: contiguous float32 CUDA tensor [m+3, ny, nx]."""
+        assert fields.is_cuda and fields.dtype.itemsize == 4 and fields.is_contiguous()
+        assert tuple(fields.shape) == (self.m + 3, self.ny, self.nx)
+        cdf_lb_init_moments_device(self.h, fields.data_ptr())
+
+    def step(self, n: int = 1):
+        cdf_lb_step(self.h, n)
+
+    def run_to_steady(self, tol: float, check_every: int = 1000, max_steps: int = 10 ** 7):
+        st, steps, res = cdf_lb_run_to_steady(self.h, tol, check_every, max_steps)
+        if st not in (CDF_OK, CDF_ENOTCONVERGED):
+            _check(st)
+        return st == CDF_OK, steps, res
+
+    def moments(self) -> np.ndarray:
+        out = np.empty((self.m + 3, self.ny, self.nx))
+        cdf_lb_moments(self.h, out)
+        return out
+
+    def moments_device(self, out):
+        assert out.is_cuda and out.is_contiguous() and out.dtype.itemsize == 4
+        assert tuple(out.shape) == (self.m + 3, self.ny, self.nx)
+        cdf_lb_moments_device(self.h, out.data_ptr())
+        return out
+
+    def mass(self) -> np.ndarray:
+        out = np.empty(self.m)
+        cdf_lb_mass(self.h, out)
+        return out
+
+    def populations(self):
+        f = np.empty((self.m, 5, self.ny, self.nx))
+        hf = np.empty((9, self.ny, self.nx))
+        s = np.empty((self.m, self.ny, self.nx))
+        cdf_lb_populations(self.h, f, hf, s)
+        return f, hf, s
+
+    def save(self, path: str):
+        cdf_lb_save(self.h, path)
+
+    def load(self, path: str):
+        cdf_lb_load(self.h, path)
+
+    def info(self) -> cdf_info:
+        return cdf_lb_get_info(self.h)
+
+    @property
+    def stream(self) -> int:
+        return cdf_lb_stream(self.h)
+
+    @property
+    def t(self) -> int:
+        return self.info().t

@@ -1,0 +1,278 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle.
+
+Tolerance: relative L2 <= 1e-5 per field for FP32 population storage, the
+bound the solver is specified to; every comparison is element by element on
+the same seeded inputs.  Sizes span several CTA tiles and ragged tails; the
+full-size workloads run in the launch configuration the benchmark uses
+(autotuned CTA shape, CUDA-graph batches) for a shorter window.
+"""
+import math
+import os
+
+import numpy as np
+import pytest
+
+from paper_2101_03055_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+TOL32 = 1e-5
+
+
+def rel_l2(a, b):
+    nb = np.linalg.norm(b)
+    return np.linalg.norm(a - b) / (nb if nb > 0 else 1.0)
+
+
+def field_errors(Mg, Mo, m):
+    errs = {f"phi{a}": rel_l2(Mg[a], Mo[a]) for a in range(m)}
+    errs["u"] = rel_l2(Mg[m:m + 2], Mo[m:m + 2])
+    errs["p"] = rel_l2(Mg[m + 2], Mo[m + 2])
+    return errs
+
+
+def run_pair(cdf, oracle_mod, pb, steps, storage="fp32", block=None):
+    s = cdf.Solver(pb, storage=storage, block=block)
+    o = oracle_mod.OracleSim(pb)
+    s.step(steps)
+    o.step(steps)
+    return s, o
+
+
+def assert_parity(s, o, m, tol=TOL32, populations=True, p_floor=0.0):
+    Mg, Mo = s.moments(), o.moments()
+    errs = field_errors(Mg, Mo, m)
+    if p_floor > 0:  # pressure measured against its own scale when it is tiny
+        errs["p"] = np.linalg.norm(Mg[m + 2] - Mo[m + 2]) / max(np.linalg.norm(Mo[m + 2]), p_floor)
+    bad = {k: v for k, v in errs.items() if not v <= tol}
+    assert not bad, f"relative L2 above {tol}: {bad}"
+    if populations:
+        fg, hg, _ = s.populations()
+        fo, ho = o.post_collision()
+        assert rel_l2(fg, fo) <= tol
+        assert rel_l2(hg, ho) <= tol
+    return errs
+
+
+# ---------------------------------------------------------------------------
+# the workloads
+# ---------------------------------------------------------------------------
+def test_taylor_green_cross_diffusion_64(cdf, oracle_mod):
+    """64^2 periodic, m = 2, constant cross-diffusion, Taylor-Green, 1000 steps (full size)."""
+    pb = I.cross_diffusion_taylor_green()
+    s, o = run_pair(cdf, oracle_mod, pb, 1000)
+    assert_parity(s, o, 2)
+
+
+def test_chemotaxis_plume_reduced(cdf, oracle_mod):
+    """Chemotaxis plume physics on 128 x 64 for 2000 steps: walls, free-slip top,
+    anti-bounce-back oxygen, nonlinear cross diffusion, consumption, buoyancy."""
+    pb = I.chemotaxis_plume(128, 64, seed=3)
+    s, o = run_pair(cdf, oracle_mod, pb, 2000)
+    assert_parity(s, o, 2)
+    Mo = o.moments()
+    assert np.abs(Mo[1] - pb.c_star).min() > 0.05  # the cut-off decision is far from c*
+
+
+def test_ddc_cavity_reduced(cdf, oracle_mod):
+    """Double-diffusive cavity with Soret/Dufour terms on 128^2 (same dimensionless
+    parameters as the 1024^2 workload), 2000 steps."""
+    pb = I.ddc_cavity(128, Ra=1e5, Pr=0.7, Le=2.0, Nc=1.0, Df=0.5, Sr=0.5)
+    s, o = run_pair(cdf, oracle_mod, pb, 2000)
+    assert_parity(s, o, 2)
+
+
+def test_chemotaxis_plume_full_size(cdf, oracle_mod):
+    """512 x 256 plume, the benchmark's launch configuration, 100 steps."""
+    pb = I.chemotaxis_plume(512, 256, seed=0)
+    s, o = run_pair(cdf, oracle_mod, pb, 100)
+    assert_parity(s, o, 2, populations=False, p_floor=1e-12)
+
+
+def test_ddc_cavity_full_size(cdf, oracle_mod):
+    """1024^2 cavity, 12 steps, every node compared."""
+    pb = I.ddc_cavity(1024, Df=0.5, Sr=0.5)
+    s, o = run_pair(cdf, oracle_mod, pb, 12)
+    assert_parity(s, o, 2, populations=False, p_floor=1e-12)
+
+
+# ---------------------------------------------------------------------------
+# boundaries, sizes, m
+# ---------------------------------------------------------------------------
+SIDE_CASES = {
+    "periodic": lambda m: (I.periodic_side(m), I.periodic_side(m)),
+    "noslip_noflux": lambda m: (I.wall_side(m), I.wall_side(m)),
+    "freeslip_dirichlet": lambda m: (I.wall_side(m, I.FREESLIP, [I.DIRICHLET] * m, [1.2] * m),
+                                     I.wall_side(m, I.FREESLIP, [I.DIRICHLET] * m, [0.8] * m)),
+    "mixed": lambda m: (I.wall_side(m, I.NOSLIP, [I.DIRICHLET] + [I.NOFLUX] * (m - 1), [1.1] + [0] * (m - 1)),
+                        I.wall_side(m, I.FREESLIP, [I.NOFLUX] * (m - 1) + [I.DIRICHLET], [0] * (m - 1) + [0.9])),
+}
+
+
+def _rand_problem(nx, ny, m, seed, xcase, ycase, force=True):
+    r = np.random.default_rng(seed)
+    A = r.normal(size=(m, m)) * 0.03
+    D = A @ A.T + np.diag(r.uniform(0.02, 0.2, m)) + 0.01 * r.normal(size=(m, m))
+    phi0 = 1 + 0.1 * (2 * I.uniform(seed, np.arange(m * nx * ny)) - 1).reshape(m, ny, nx)
+    u0 = 0.02 * (2 * I.uniform(seed + 1, np.arange(2 * nx * ny)) - 1).reshape(2, ny, nx)
+    p0 = 1e-3 * (2 * I.uniform(seed + 2, np.arange(nx * ny)) - 1).reshape(ny, nx)
+    w, e = SIDE_CASES[xcase](m)
+    s, n = SIDE_CASES[ycase](m)
+    kw = dict(g=(0.3, -1.0), beta=r.uniform(-1e-3, 1e-3, m), phi_ref=np.ones(m)) if force else {}
+    return I.Problem("rand", nx, ny, m, D, 0.05 + 0.1 * r.uniform(), west=w, east=e, south=s, north=n,
+                     phi0=phi0, u0=u0, p0=p0, **kw)
+
+
+@pytest.mark.parametrize("xcase", list(SIDE_CASES))
+@pytest.mark.parametrize("ycase", list(SIDE_CASES))
+def test_boundary_combinations(cdf, oracle_mod, xcase, ycase):
+    """Every pair of side types on a ragged 37 x 21 lattice (not a multiple of any
+    CTA shape), random non-symmetric D and density-dependent force, 60 steps."""
+    pb = _rand_problem(37, 21, 2, 11, xcase, ycase)
+    s, o = run_pair(cdf, oracle_mod, pb, 60)
+    assert_parity(s, o, 2)
+
+
+@pytest.mark.parametrize("nx,ny", [(1, 1), (1, 9), (9, 1), (2, 2), (33, 17), (130, 3)])
+def test_degenerate_and_ragged_sizes(cdf, oracle_mod, nx, ny):
+    pb = _rand_problem(nx, ny, 2, 5, "periodic" if nx < 3 else "noslip_noflux",
+                       "periodic" if ny < 3 else "freeslip_dirichlet")
+    s, o = run_pair(cdf, oracle_mod, pb, 25)
+    assert_parity(s, o, 2)
+
+
+@pytest.mark.parametrize("m", [1, 3, 4])
+def test_other_scalar_counts(cdf, oracle_mod, m):
+    pb = _rand_problem(29, 19, m, 7 + m, "mixed", "noslip_noflux")
+    s, o = run_pair(cdf, oracle_mod, pb, 40)
+    assert_parity(s, o, m)
+
+
+def test_regularised_cutoff_and_const_source(cdf, oracle_mod):
+    pb = I.chemotaxis_plume(40, 24, seed=2).replace(r_regularised=True, eps=0.05, c_star=0.97)
+    s, o = run_pair(cdf, oracle_mod, pb, 300)
+    assert_parity(s, o, 2)
+    pc = _rand_problem(24, 16, 2, 3, "periodic", "noslip_noflux").replace(skind="const", S=np.array([1e-4, -2e-4]))
+    s, o = run_pair(cdf, oracle_mod, pc, 100)
+    assert_parity(s, o, 2)
+
+
+def test_block_shapes_agree_bitwise(cdf):
+    pb = I.chemotaxis_plume(100, 60, seed=4)
+    ref = None
+    for blk in [(32, 4), (64, 2), (128, 1), (256, 1), (32, 8)]:
+        s = cdf.Solver(pb, block=blk)
+        s.step(77)
+        M = s.moments()
+        if ref is None:
+            ref = M
+        else:
+            assert np.array_equal(M, ref), blk
+
+
+def test_graph_batches_equal_single_steps(cdf):
+    pb = I.chemotaxis_plume(70, 50, seed=5)
+    a, b = cdf.Solver(pb), cdf.Solver(pb)
+    a.step(100)
+    for _ in range(100):
+        b.step(1)
+    assert np.array_equal(a.moments(), b.moments())
+    fa, ha, sa = a.populations()
+    fb, hb, sb = b.populations()
+    assert np.array_equal(fa, fb) and np.array_equal(ha, hb) and np.array_equal(sa, sb)
+    assert a.t == b.t == 100
+
+
+# ---------------------------------------------------------------------------
+# invariants, driver, checkpoint, device I/O
+# ---------------------------------------------------------------------------
+def test_initial_moments_round_trip(cdf):
+    pb = _rand_problem(31, 13, 2, 9, "periodic", "noslip_noflux")
+    s = cdf.Solver(pb)
+    M = s.moments()
+    np.testing.assert_allclose(M[:2], pb.phi0, rtol=2e-7)
+    np.testing.assert_allclose(M[2:4], pb.u0, atol=2e-8)
+    np.testing.assert_allclose(M[4], pb.p0, atol=2e-8)
+
+
+def test_mass_conservation_fp64_reduction(cdf):
+    pb = I.cross_diffusion_taylor_green(256, 256)
+    s = cdf.Solver(pb)
+    m0 = s.mass()
+    np.testing.assert_allclose(m0, pb.phi0.reshape(2, -1).sum(axis=1), rtol=1e-7)
+    s.step(2000)
+    np.testing.assert_allclose(s.mass(), m0, rtol=1e-6)
+
+
+def test_run_to_steady_linear_profile(cdf):
+    m, nx = 2, 16
+    hot = I.wall_side(m, I.NOSLIP, [I.DIRICHLET] * 2, [1.0, 1.0])
+    cold = I.wall_side(m, I.NOSLIP, [I.DIRICHLET] * 2, [0.0, 0.0])
+    pb = I.Problem("cond", nx, 4, m, np.array([[0.2, 0.05], [0.03, 0.1]]), 0.1, west=hot, east=cold,
+                   phi0=np.zeros((2, 4, nx)))
+    s = cdf.Solver(pb)
+    ok, steps, res = s.run_to_steady(1e-7, 500, 200_000)
+    assert ok and res < 1e-7 and steps % 500 == 0
+    M = s.moments()
+    pe = 1 - (np.arange(nx) + 0.5) / nx
+    np.testing.assert_allclose(M[0], np.broadcast_to(pe, (4, nx)), atol=1e-5)
+    ok2, steps2, res2 = cdf.Solver(pb).run_to_steady(1e-12, 100, 300)
+    assert not ok2 and steps2 == 300 and res2 > 1e-12
+
+
+def test_run_to_steady_reports_instability(cdf):
+    pb = _rand_problem(16, 16, 2, 1, "periodic", "periodic").replace(
+        nu=1e-7, u0=np.full((2, 16, 16), 0.4) * np.sin(np.arange(16))[None, None, :])
+    s = cdf.Solver(pb)
+    with pytest.raises(cdf.CdfError) as e:
+        ok, steps, res = s.run_to_steady(1e-9, 200, 200_000)
+    assert e.value.status == cdf.CDF_EUNSTABLE
+
+
+def test_checkpoint_restart_is_bitwise(cdf, tmp_path):
+    pb = I.chemotaxis_plume(96, 48, seed=6)
+    a = cdf.Solver(pb)
+    a.step(150)
+    path = str(tmp_path / "ck.bin")
+    a.save(path)
+    a.step(150)
+    b = cdf.Solver(pb, init=False)
+    b.load(path)
+    assert b.t == 150
+    b.step(150)
+    assert np.array_equal(a.moments(), b.moments())
+    fa, ha, sa = a.populations()
+    fb, hb, sb = b.populations()
+    assert np.array_equal(fa, fb) and np.array_equal(ha, hb) and np.array_equal(sa, sb)
+    other = cdf.Solver(I.chemotaxis_plume(64, 48))
+    with pytest.raises(cdf.CdfError):
+        other.load(path)
+
+
+def test_device_tensor_io_and_user_stream(cdf):
+    import torch
+    pb = _rand_problem(45, 23, 2, 8, "mixed", "periodic")
+    fields = torch.tensor(np.concatenate([pb.phi0, pb.u0, pb.p0[None]]), dtype=torch.float32, device="cuda")
+    st = torch.cuda.Stream()
+    with torch.cuda.stream(st):
+        a = cdf.Solver(pb, stream=st.cuda_stream, init=False)
+        a.init_moments_device(fields)
+        a.step(50)
+        out = torch.empty_like(fields)
+        a.moments_device(out)
+    st.synchronize()
+    b = cdf.Solver(pb)
+    b.step(50)
+    np.testing.assert_array_equal(out.cpu().numpy().astype(np.float64), b.moments())
+
+
+def test_step_zero_and_errors(cdf):
+    pb = I.cross_diffusion_taylor_green(16, 16)
+    s = cdf.Solver(pb)
+    s.step(0)
+    assert s.t == 0
+    with pytest.raises(cdf.CdfError):
+        s.step(-1)
+    u = cdf.Solver(pb, init=False)
+    with pytest.raises(cdf.CdfError):
+        u.step(1)
