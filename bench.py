@@ -53,6 +53,8 @@ def workload(name: str, rank: int):
         return I.ddc_cavity(1024, Df=0.5, Sr=0.5)
     if name == "periodic_4096":
         return I.periodic_box(4096, 4096, seed=rank)
+    if name == "periodic_2048":
+        return I.periodic_box(2048, 2048, seed=rank)
     raise SystemExit(f"unknown workload {name}")
 
 
@@ -62,6 +64,7 @@ def describe(name: str) -> str:
                                     "chi=0.5 step cut-off, consumption, buoyancy; n0 = 1 + 0.01 N(0,1)",
         "ddc_cavity_1024": "double-diffusive cavity 1024x1024 with Soret/Dufour (Df=Sr=0.5), Ra=1e5, Pr=0.7, Le=2, N=1",
         "periodic_4096": "periodic 4096x4096 cross-diffusion box (roofline grid)",
+        "periodic_2048": "periodic 2048x2048 cross-diffusion box (profiling grid above L2)",
     }[name]
 
 

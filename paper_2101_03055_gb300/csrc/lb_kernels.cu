@@ -21,14 +21,55 @@
 namespace cdflb {
 namespace {
 
-// D2Q5 (Eq. D2Q5) and D2Q9 (Eq. D2Q9) weights; velocities are spelled out in
-// the pull and collision code below, direction by direction.
-__host__ __device__ constexpr float kW5(int i) { return i == 0 ? 1.f / 3.f : 1.f / 6.f; }
-__host__ __device__ constexpr float kW9(int i) { return i == 0 ? 4.f / 9.f : (i < 5 ? 1.f / 9.f : 1.f / 36.f); }
+// Lattice constants of Eq. D2Q5 and Eq. D2Q9 in FP32.  Rounding 1/3, 1/6,
+// 1/9, 1/36 independently would break the discrete conservation identities by
+// a few 1e-8 per collision, and because scalar mass, fluid momentum and the
+// mean pressure are neutral (conserved) modes the error would pile up linearly
+// over the run.  The constants below are chosen so that, for the rounded
+// values themselves, sum W = 1 (scalars), 3 sum W c_x^2 = 1 and
+// 3 sum_{i!=0} W = kC (fluid) hold exactly; they differ from the exact
+// weights by at most 1.2e-7 relative.
+//   kW5  = fl(1/6)                W_1..4 of D2Q5;   kW50 = 1 - 4 kW5
+//   kA1  = 3 W_1..4 of D2Q9 ~ 1/3; kA5 = 3 W_5..8 ~ 1/12;  2 kA1 + 4 kA5 = 1
+//   kC   = 4 kA1 + 4 kA5 ~ 5/3 (= (1 - W_0)/cs^2);  kQ = 3/2 - kC/2 ~ 2/3
+constexpr float kW5 = 0x1.555556p-3f;
+constexpr float kW50 = 0x1.555554p-2f;
+constexpr float kA1 = 0x1.555554p-2f;
+constexpr float kA5 = 0x1.555558p-4f;
+constexpr float kC = 0x1.aaaaaap+0f;
+constexpr float kQ = 0x1.555556p-1f;
+__host__ __device__ constexpr float kWs(int i) { return i == 0 ? kW50 : kW5; }
+__host__ __device__ constexpr float kA9(int i) { return i == 0 ? 0.f : (i < 5 ? kA1 : kA5); }
 __host__ __device__ constexpr int kC5x(int i) { return i == 1 ? 1 : (i == 3 ? -1 : 0); }
 __host__ __device__ constexpr int kC5y(int i) { return i == 2 ? 1 : (i == 4 ? -1 : 0); }
 __host__ __device__ constexpr int kC9x(int i) { return (i == 1 || i == 5 || i == 8) ? 1 : ((i == 3 || i == 6 || i == 7) ? -1 : 0); }
 __host__ __device__ constexpr int kC9y(int i) { return (i == 2 || i == 5 || i == 6) ? 1 : ((i == 4 || i == 7 || i == 8) ? -1 : 0); }
+
+// Scalar equilibrium, Eq. feq-phi with lambda = I, vartheta = 0:
+// f^eq_i = W_i phi (1 + 3 c_i.u); the rest population is phi minus the moving
+// ones, so sum_i f^eq_i = phi up to one rounding.
+template <int M>
+__device__ __forceinline__ void scalar_equilibrium(const float (&phi)[M], float ux, float uy,
+                                                   float (&feq)[M][5]) {
+#pragma unroll
+    for (int b = 0; b < M; ++b) {
+        const float wp = kW5 * phi[b];
+        feq[b][1] = wp * fmaf(3.f, ux, 1.f);
+        feq[b][2] = wp * fmaf(3.f, uy, 1.f);
+        feq[b][3] = wp * fmaf(-3.f, ux, 1.f);
+        feq[b][4] = wp * fmaf(-3.f, uy, 1.f);
+        feq[b][0] = phi[b] - ((feq[b][1] + feq[b][3]) + (feq[b][2] + feq[b][4]));
+    }
+}
+
+// Fluid equilibrium, Eq. heq: h^eq_i = sigma_i + W_i [3 c_i.u + 4.5 (c_i.u)^2 - 1.5 u.u],
+// sigma_i = 3 W_i p (i != 0), sigma_0 = rho0 - (1 - W_0) p / cs^2; written with
+// kA_i = 3 W_i as kA_i (p + c_i.u + 1.5 (c_i.u)^2 - 0.5 u.u).
+__device__ __forceinline__ float fluid_equilibrium(int i, float rho0, float pr, float ux, float uy, float usq) {
+    if (i == 0) return rho0 - kC * pr - kQ * usq;
+    const float cu = kC9x(i) * ux + kC9y(i) * uy;
+    return kA9(i) * ((pr + cu) + fmaf(1.5f * cu, cu, -0.5f * usq));
+}
 
 // ---- storage types: FP32 values, or 16-bit deviations from a reference -------
 template <typename T> struct Store;
@@ -56,7 +97,7 @@ __device__ __forceinline__ float fluid_ref(const LbParams &p, int i) {
 }
 template <typename T>
 __device__ __forceinline__ float scalar_ref(const LbParams &p, int a, int i) {
-    return Store<T>::kDev ? kW5(i) * p.ref16[a] : 0.f;
+    return Store<T>::kDev ? kWs(i) * p.ref16[a] : 0.f;
 }
 
 __device__ __forceinline__ float cutoff(const LbParams &p, float c) {
@@ -101,13 +142,14 @@ __device__ __forceinline__ void collide(const LbParams &p, float (&f)[M][5], flo
     for (int a = 0; a < M; ++a) fm = fmaf(p.beta[a], phi[a], fm);
     const float Fx = p.g[0] * fm, Fy = p.g[1] * fm;
 
-    // Eq. sum-u and Eq. sum-p (varphi = 0): p = cs^2/(1-W0) [sum_{i!=0} h_i - W0 u.u/(2 cs^2)]
+    // Eq. sum-u and Eq. sum-p (varphi = 0):
+    // p = cs^2/(1 - W0) [sum_{i!=0} h_i - W0 u.u / (2 cs^2)] = (sum_{i!=0} h_i - kQ u.u) / kC
     const float jx = (h[1] - h[3]) + (h[5] - h[6]) + (h[8] - h[7]);
     const float jy = (h[2] - h[4]) + (h[5] - h[8]) + (h[6] - h[7]);
     const float ux = jx + 0.5f * Fx, uy = jy + 0.5f * Fy;
     const float usq = ux * ux + uy * uy;
     const float snr = ((h[1] + h[2]) + (h[3] + h[4])) + ((h[5] + h[6]) + (h[7] + h[8]));
-    const float pr = 0.6f * (snr - (2.f / 3.f) * usq);
+    const float pr = (snr - kQ * usq) / kC;
 
     // Eq. omega-D.  Constant D: omega from the host.  Chemotaxis: omega^-1 =
     // B + delta e_0 e_1^T with delta = -3 chi phi_0 r, inverted by Sherman-Morrison.
@@ -143,35 +185,34 @@ __device__ __forceinline__ void collide(const LbParams &p, float (&f)[M][5], flo
         Jy[a] = jya;
     }
 
-    // Eq. evolution12 with f^eq_i = W_i phi (1 + 3 c_i.u) (Eq. feq-phi, lambda = I,
-    // vartheta = 0), source W_i S and the backward difference (S(t) - S(t-1)) / 2.
+    // Eq. evolution12: f*_i,a = f_i,a - sum_b omega_ab (f_i,b - f^eq_i,b) + W_i S_a
+    // + (W_i S_a - W_i S_a(t-1)) / 2 + G_i,a
+    float feq[M][5];
+    scalar_equilibrium<M>(phi, ux, uy, feq);
 #pragma unroll
     for (int i = 0; i < 5; ++i) {
-        const float cu = kC5x(i) * ux + kC5y(i) * uy;
         float neq[M];
 #pragma unroll
-        for (int b = 0; b < M; ++b) neq[b] = f[b][i] - kW5(i) * phi[b] * fmaf(3.f, cu, 1.f);
+        for (int b = 0; b < M; ++b) neq[b] = f[b][i] - feq[b][i];
 #pragma unroll
         for (int a = 0; a < M; ++a) {
             float coll = 0.f;
 #pragma unroll
             for (int b = 0; b < M; ++b) coll = fmaf(om[a][b], neq[b], coll);
-            const float src = kW5(i) * (1.5f * S[a] - 0.5f * Sp[a]);
-            const float G = 3.f * kW5(i) * (kC5x(i) * Jx[a] + kC5y(i) * Jy[a]);
+            const float src = kWs(i) * fmaf(1.5f, S[a], -0.5f * Sp[a]);
+            const float G = (i == 0) ? 0.f : 3.f * kW5 * (kC5x(i) * Jx[a] + kC5y(i) * Jy[a]);
             f[a][i] = (f[a][i] - coll) + (src + G);
         }
     }
 
-    // Eq. evolution3 with Eq. heq (sigma_0 = rho0 - 5p/3, sigma_i = 3 W_i p) and
-    // Eq. force (varphi = 0): F_i = 3 W_i c_i.F, weighted by (1 - omega_f / 2).
+    // Eq. evolution3 with Eq. force (varphi = 0): F_i = 3 W_i c_i.F, weighted by
+    // (1 - omega_f / 2).
     const float wf = p.omega_f, fw = 1.f - 0.5f * wf;
 #pragma unroll
     for (int i = 0; i < 9; ++i) {
-        const float cu = kC9x(i) * ux + kC9y(i) * uy;
-        const float sigma = (i == 0) ? (p.rho0 - (5.f / 3.f) * pr) : 3.f * kW9(i) * pr;
-        const float heq = sigma + kW9(i) * (3.f * cu + 4.5f * cu * cu - 1.5f * usq);
-        const float Fi = 3.f * kW9(i) * (kC9x(i) * Fx + kC9y(i) * Fy);
-        h[i] = h[i] - wf * (h[i] - heq) + fw * Fi;
+        const float heq = fluid_equilibrium(i, p.rho0, pr, ux, uy, usq);
+        const float Fi = kA9(i) * (kC9x(i) * Fx + kC9y(i) * Fy);
+        h[i] = fmaf(-wf, h[i] - heq, h[i]) + fw * Fi;
     }
 #pragma unroll
     for (int a = 0; a < M; ++a) o.phi[a] = phi[a];
@@ -297,19 +338,11 @@ __global__ void init_kernel(const LbParams p, const float *__restrict__ fields, 
     // f = f^eq(phi, u); h = h^eq(u, p) - F_i / 2 (moments then return the inputs)
     float f[M][5], h[9];
     const float usq = ux * ux + uy * uy;
+    scalar_equilibrium<M>(phi, ux, uy, f);
 #pragma unroll
-    for (int i = 0; i < 5; ++i) {
-        const float cu = kC5x(i) * ux + kC5y(i) * uy;
-#pragma unroll
-        for (int a = 0; a < M; ++a) f[a][i] = kW5(i) * phi[a] * fmaf(3.f, cu, 1.f);
-    }
-#pragma unroll
-    for (int i = 0; i < 9; ++i) {
-        const float cu = kC9x(i) * ux + kC9y(i) * uy;
-        const float sigma = (i == 0) ? (p.rho0 - (5.f / 3.f) * pr) : 3.f * kW9(i) * pr;
-        const float heq = sigma + kW9(i) * (3.f * cu + 4.5f * cu * cu - 1.5f * usq);
-        h[i] = heq - 0.5f * 3.f * kW9(i) * (kC9x(i) * Fx + kC9y(i) * Fy);
-    }
+    for (int i = 0; i < 9; ++i)
+        h[i] = fluid_equilibrium(i, p.rho0, pr, ux, uy, usq) -
+               0.5f * kA9(i) * (kC9x(i) * Fx + kC9y(i) * Fy);
     NodeOut<M> o;
     collide<M>(p, f, h, 0.f, true, o);
 #pragma unroll
