@@ -54,10 +54,11 @@ typedef enum {
     CDF_EIO = 7            /* checkpoint file could not be read or written */
 } cdf_status;
 
-/* Population storage.  CDF_FP32 stores populations as float.  The 16-bit modes
- * store each population's deviation from a fixed reference (W_i phi_ref16_a
- * for scalars, (rho0, 0, ..., 0) for the fluid) as FP16 or BF16; every
- * collision is computed in FP32 (paper: silent on precision). */
+/* Population storage.  Every mode stores each population as its deviation from
+ * a reference state -- W_i phi_ref_a for scalar a; h^eq_i(p_ref(x), u = 0) for
+ * the fluid, with p_ref the hydrostatic pressure of the force at phi_ref along
+ * walled axes -- as FP32, FP16 or BF16; every collision is computed in FP32 on
+ * these deviations (paper: silent on precision). */
 typedef enum { CDF_FP32 = 0, CDF_FP16_DEV = 1, CDF_BF16_DEV = 2 } cdf_storage;
 
 typedef enum { CDF_BC_PERIODIC = 0, CDF_BC_WALL = 1 } cdf_bckind;
@@ -114,7 +115,7 @@ typedef struct {
     int storage;                       /* cdf_storage */
     double rho0;                       /* the constant of sigma_0 in Eq. heq (> 0) */
     void *cuda_stream;                 /* cudaStream_t of the caller, NULL = default */
-    double phi_ref16[CDF_MAX_M];       /* 16-bit modes: scalar reference values */
+    double phi_ref[CDF_MAX_M];         /* reference scalar values of the stored deviations */
     int block_x, block_y;              /* step kernel CTA shape; 0 = autotuned */
 } cdf_options;
 
@@ -183,7 +184,8 @@ cdf_status cdf_lb_populations(cdf_lb *h, double *f, double *hf, double *s_now);
 
 /* Write / read the full state (populations, S(t-1), time, moments) to a file;
  * a restart continues bit-identically.  load checks that the file matches the
- * handle's grid, m and storage (CDF_EINVAL otherwise, CDF_EIO on file errors). */
+ * handle's grid, m, storage and reference state (CDF_EINVAL otherwise, CDF_EIO
+ * on file errors). */
 cdf_status cdf_lb_save(cdf_lb *h, const char *path);
 cdf_status cdf_lb_load(cdf_lb *h, const char *path);
 

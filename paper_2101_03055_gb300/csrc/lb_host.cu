@@ -294,7 +294,8 @@ cdf_status cdf_lb_create(const cdf_grid *grid, int m, const cdf_diffusion *dif, 
     *out = nullptr;
     if (!grid || !dif || !src || !frc || !bc || !opt) return fail(CDF_EINVAL, "NULL argument");
     if (grid->nx < 1 || grid->ny < 1) return fail(CDF_EINVAL, "grid must be at least 1 x 1");
-    if ((long long)grid->nx * grid->ny > (1LL << 31)) return fail(CDF_EINVAL, "grid too large");
+    if ((long long)(grid->nx + 63) * grid->ny >= (1LL << 31) - 1)
+        return fail(CDF_EINVAL, "grid too large: one padded plane must hold fewer than 2^31 elements");
     if (m < 1 || m > CDF_MAX_M) return fail(CDF_EINVAL, "m must be in [1, %d]", CDF_MAX_M);
     if (!(nu > 0.0) || !std::isfinite(nu)) return fail(CDF_EINVAL, "nu must be positive");
     if (dif->kind != CDF_D_CONST && dif->kind != CDF_D_CHEMOTAXIS) return fail(CDF_EINVAL, "bad diffusion kind");
@@ -373,9 +374,17 @@ cdf_status cdf_lb_create(const cdf_grid *grid, int m, const cdf_diffusion *dif, 
     for (int a = 0; a < m; ++a) {
         P.beta[a] = (float)frc->beta[a];
         Fbase -= frc->beta[a] * frc->phi_ref[a];
-        P.ref16[a] = (float)opt->phi_ref16[a];
+        P.phi_ref[a] = (float)opt->phi_ref[a];
     }
     P.Fbase = (float)Fbase;
+    // Pressure reference of the fluid deviations: hydrostatic balance grad p = F
+    // of the force at the reference scalar values, along walled axes only.
+    double Fref = Fbase;
+    for (int a = 0; a < m; ++a) Fref += frc->beta[a] * opt->phi_ref[a];
+    P.gref[0] = bc->west.kind == CDF_BC_WALL ? (float)(frc->g[0] * Fref) : 0.f;
+    P.gref[1] = bc->south.kind == CDF_BC_WALL ? (float)(frc->g[1] * Fref) : 0.f;
+    P.xc = 0.5f * (float)(grid->nx - 1);
+    P.yc = 0.5f * (float)(grid->ny - 1);
     P.rho0 = (float)opt->rho0;
     P.periodic_x = bc->west.kind == CDF_BC_PERIODIC;
     P.periodic_y = bc->south.kind == CDF_BC_PERIODIC;
@@ -385,7 +394,7 @@ cdf_status cdf_lb_create(const cdf_grid *grid, int m, const cdf_diffusion *dif, 
         for (int a = 0; a < m; ++a) {
             if (sides[s]->kind == CDF_BC_WALL && sides[s]->scalar[a] == CDF_SC_DIRICHLET) {
                 P.dirichlet[s] |= 1u << a;
-                P.abb[s][a] = (float)(sides[s]->value[a] / 3.0);  // 2 W_i phi_w, W_i = 1/6
+                P.abb[s][a] = (float)((sides[s]->value[a] - opt->phi_ref[a]) / 3.0);  // 2 W_i (phi_w - phi_ref)
             }
         }
     }
@@ -608,6 +617,7 @@ struct FileHeader {
     long long t;
     int cur;
     int reserved[5];
+    float phi_ref[kMaxM], gref[2];
 };
 const char kMagic[8] = {'C', 'D', 'F', 'L', 'B', '0', '0', '1'};
 }  // namespace
@@ -631,6 +641,9 @@ cdf_status cdf_lb_save(cdf_lb *h, const char *path) {
     hd.version = 1;
     hd.nx = h->nx; hd.ny = h->ny; hd.m = h->m; hd.storage = h->storage;
     hd.planes = h->planes; hd.sprev_planes = h->sprev_planes; hd.pitch = h->pitch; hd.t = h->t;
+    for (int a = 0; a < kMaxM; ++a) hd.phi_ref[a] = h->P.phi_ref[a];
+    hd.gref[0] = h->P.gref[0];
+    hd.gref[1] = h->P.gref[1];
     FILE *fp = std::fopen(path, "wb");
     if (!fp) return fail(CDF_EIO, "cannot open %s for writing", path);
     bool ok = std::fwrite(&hd, sizeof hd, 1, fp) == 1 && std::fwrite(data.data(), 1, data.size(), fp) == data.size();
@@ -650,9 +663,11 @@ cdf_status cdf_lb_load(cdf_lb *h, const char *path) {
         return fail(CDF_EIO, "%s is not a cdf_lb checkpoint", path);
     }
     if (hd.nx != h->nx || hd.ny != h->ny || hd.m != h->m || hd.storage != h->storage ||
-        hd.planes != h->planes || hd.sprev_planes != h->sprev_planes || hd.pitch != h->pitch) {
+        hd.planes != h->planes || hd.sprev_planes != h->sprev_planes || hd.pitch != h->pitch ||
+        std::memcmp(hd.phi_ref, h->P.phi_ref, sizeof hd.phi_ref) != 0 || hd.gref[0] != h->P.gref[0] ||
+        hd.gref[1] != h->P.gref[1]) {
         std::fclose(fp);
-        return fail(CDF_EINVAL, "checkpoint does not match this solver's grid, m or storage");
+        return fail(CDF_EINVAL, "checkpoint does not match this solver's grid, m, storage or reference state");
     }
     const size_t pop = (size_t)h->planes * h->plane * elem_size(h->storage);
     const size_t spb = (size_t)h->plane * 4, momb = (size_t)(h->m + 3) * h->plane * 4;

@@ -33,8 +33,12 @@ struct LbParams {
     int periodic_x, periodic_y;
     int freeslip[4];            // per side (west, east, south, north)
     unsigned dirichlet[4];      // per side: bit a set -> scalar a is Dirichlet
-    float abb[4][kMaxM];        // per side and scalar: 2 W_i phi_w = phi_w / 3
-    float ref16[kMaxM];         // 16-bit storage: scalar reference values
+    float abb[4][kMaxM];        // per side and scalar: 2 W_i (phi_w - phi_ref) = (phi_w - phi_ref) / 3
+    // Reference state of the stored deviations: W_i phi_ref_a for scalar a;
+    // h^eq(p_ref(x), 0) for the fluid with p_ref(x) = gref . (x - (xc, yc)).
+    float phi_ref[kMaxM];
+    float gref[2];
+    float xc, yc;
 };
 
 enum Storage { kFP32 = 0, kFP16 = 1, kBF16 = 2 };

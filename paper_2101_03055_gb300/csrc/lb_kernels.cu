@@ -71,33 +71,32 @@ __device__ __forceinline__ float fluid_equilibrium(int i, float rho0, float pr, 
     return kA9(i) * ((pr + cu) + fmaf(1.5f * cu, cu, -0.5f * usq));
 }
 
-// ---- storage types: FP32 values, or 16-bit deviations from a reference -------
+// ---- storage types ---------------------------------------------------------------
+// Populations are stored as deviations from a reference state (below) in FP32,
+// FP16 or BF16; every collision is computed in FP32.
 template <typename T> struct Store;
 template <> struct Store<float> {
-    static constexpr bool kDev = false;
     __device__ static float load(const float *p) { return __ldg(p); }
     __device__ static void store(float *p, float v) { *p = v; }
 };
 template <> struct Store<__half> {
-    static constexpr bool kDev = true;
     __device__ static float load(const __half *p) { return __half2float(__ldg(p)); }
     __device__ static void store(__half *p, float v) { *p = __float2half_rn(v); }
 };
 template <> struct Store<__nv_bfloat16> {
-    static constexpr bool kDev = true;
     __device__ static float load(const __nv_bfloat16 *p) { return __bfloat162float(__ldg(p)); }
     __device__ static void store(__nv_bfloat16 *p, float v) { *p = __float2bfloat16_rn(v); }
 };
 
-// Reference subtracted before a 16-bit store: (rho0, 0, ..., 0) for the fluid,
-// W_i phi_ref_a for scalar a.
-template <typename T>
-__device__ __forceinline__ float fluid_ref(const LbParams &p, int i) {
-    return (Store<T>::kDev && i == 0) ? p.rho0 : 0.f;
-}
-template <typename T>
-__device__ __forceinline__ float scalar_ref(const LbParams &p, int a, int i) {
-    return Store<T>::kDev ? kWs(i) * p.ref16[a] : 0.f;
+// Reference state of the deviation variables at node x:
+//   scalars  f_ref_i,a = W_i phi_ref_a                      (constant)
+//   fluid    h_ref_i   = h^eq_i(p_ref(x), u = 0)            (Eq. heq)
+//            p_ref(x)  = G . (x - x_c), G the hydrostatic gradient of the mean force
+// The collision below is written in these variables; it is the same update as
+// Eqs. evolution12/evolution3 term by term, with phi = phi_ref + sum_i f'_i,
+// u = sum_i c_i h'_i + F/2 (sum_i c_i h_ref_i = 0) and p = p_ref(x) + p'.
+__device__ __forceinline__ float pref_at(const LbParams &p, int x, int y) {
+    return p.gref[0] * ((float)x - p.xc) + p.gref[1] * ((float)y - p.yc);
 }
 
 __device__ __forceinline__ float cutoff(const LbParams &p, float c) {
@@ -109,22 +108,50 @@ __device__ __forceinline__ float cutoff(const LbParams &p, float c) {
     return c >= p.c_star ? 1.f : 0.f;
 }
 
-// Node-local moments: phi_a, u, p; plus S(t) of the consumption closure.
 template <int M>
 struct NodeOut {
     float phi[M], ux, uy, pr, s1;
 };
 
-// Collision of one node (Eqs. evolution12, evolution3).  f, h: pre-collision
-// populations, overwritten by the post-collision ones.  sp1: S_1(t-1) of the
-// consumption closure (ignored otherwise); `first` uses S(t-1) = S(t).
+// Scalar equilibrium deviation: f^eq_i - W_i phi_ref = W_i (phi' + 3 phi c_i.u) for the
+// moving directions (Eq. feq-phi, lambda = I, vartheta = 0); the rest direction is phi'
+// minus the moving ones, so the populations' sum is phi' up to one rounding.
 template <int M>
-__device__ __forceinline__ void collide(const LbParams &p, float (&f)[M][5], float (&h)[9],
+__device__ __forceinline__ void scalar_equilibrium(const float (&phid)[M], const float (&phi)[M], float ux,
+                                                   float uy, float (&feq)[M][5]) {
+#pragma unroll
+    for (int b = 0; b < M; ++b) {
+        const float t = 3.f * phi[b];
+        feq[b][1] = kW5 * fmaf(t, ux, phid[b]);
+        feq[b][2] = kW5 * fmaf(t, uy, phid[b]);
+        feq[b][3] = kW5 * fmaf(-t, ux, phid[b]);
+        feq[b][4] = kW5 * fmaf(-t, uy, phid[b]);
+        feq[b][0] = phid[b] - ((feq[b][1] + feq[b][3]) + (feq[b][2] + feq[b][4]));
+    }
+}
+
+// Fluid equilibrium deviation (Eq. heq): h^eq_i(p, u) - h^eq_i(p_ref, 0)
+//   = kA_i (p' + c_i.u + 1.5 (c_i.u)^2 - 0.5 u.u)  (i != 0),  -kC p' - kQ u.u  (i = 0).
+__device__ __forceinline__ float fluid_equilibrium(int i, float prd, float ux, float uy, float usq) {
+    if (i == 0) return -kC * prd - kQ * usq;
+    const float cu = kC9x(i) * ux + kC9y(i) * uy;
+    return kA9(i) * ((prd + cu) + fmaf(1.5f * cu, cu, -0.5f * usq));
+}
+
+// Collision of one node (Eqs. evolution12, evolution3) in deviation variables.
+// f, h: pre-collision deviations, overwritten by the post-collision ones.  prx:
+// p_ref at the node.  sp1: S_1(t-1) of the consumption closure; `first` uses
+// S(t-1) = S(t) (initialisation).
+template <int M>
+__device__ __forceinline__ void collide(const LbParams &p, float (&f)[M][5], float (&h)[9], float prx,
                                         float sp1, bool first, NodeOut<M> &o) {
     // Eq. sum-phi and the closures of Sec. 3
-    float phi[M];
+    float phid[M], phi[M];
 #pragma unroll
-    for (int a = 0; a < M; ++a) phi[a] = ((f[a][0] + f[a][1]) + (f[a][2] + f[a][3])) + f[a][4];
+    for (int a = 0; a < M; ++a) {
+        phid[a] = ((f[a][0] + f[a][1]) + (f[a][2] + f[a][3])) + f[a][4];
+        phi[a] = p.phi_ref[a] + phid[a];
+    }
     float r = 0.f;
     if (M >= 2 && (p.chemotaxis || p.skind == 2)) r = cutoff(p, phi[M >= 2 ? 1 : 0]);
     float S[M], Sp[M];
@@ -146,10 +173,10 @@ __device__ __forceinline__ void collide(const LbParams &p, float (&f)[M][5], flo
     // p = cs^2/(1 - W0) [sum_{i!=0} h_i - W0 u.u / (2 cs^2)] = (sum_{i!=0} h_i - kQ u.u) / kC
     const float jx = (h[1] - h[3]) + (h[5] - h[6]) + (h[8] - h[7]);
     const float jy = (h[2] - h[4]) + (h[5] - h[8]) + (h[6] - h[7]);
-    const float ux = jx + 0.5f * Fx, uy = jy + 0.5f * Fy;
+    const float ux = fmaf(0.5f, Fx, jx), uy = fmaf(0.5f, Fy, jy);
     const float usq = ux * ux + uy * uy;
     const float snr = ((h[1] + h[2]) + (h[3] + h[4])) + ((h[5] + h[6]) + (h[7] + h[8]));
-    const float pr = (snr - kQ * usq) / kC;
+    const float prd = (snr - kQ * usq) / kC;
 
     // Eq. omega-D.  Constant D: omega from the host.  Chemotaxis: omega^-1 =
     // B + delta e_0 e_1^T with delta = -3 chi phi_0 r, inverted by Sherman-Morrison.
@@ -160,7 +187,7 @@ __device__ __forceinline__ void collide(const LbParams &p, float (&f)[M][5], flo
         for (int b = 0; b < M; ++b) om[a][b] = p.omega[a * M + b];
     if (M >= 2 && p.chemotaxis) {
         const float delta = -p.chi3 * phi[0] * r;
-        const float den = 1.f / (1.f + delta * om[1][0]);
+        const float den = 1.f / fmaf(delta, om[M >= 2 ? 1 : 0][0], 1.f);
         float col0[M], row1[M];
 #pragma unroll
         for (int a = 0; a < M; ++a) { col0[a] = om[a][0]; row1[a] = om[M >= 2 ? 1 : 0][a]; }
@@ -188,7 +215,7 @@ __device__ __forceinline__ void collide(const LbParams &p, float (&f)[M][5], flo
     // Eq. evolution12: f*_i,a = f_i,a - sum_b omega_ab (f_i,b - f^eq_i,b) + W_i S_a
     // + (W_i S_a - W_i S_a(t-1)) / 2 + G_i,a
     float feq[M][5];
-    scalar_equilibrium<M>(phi, ux, uy, feq);
+    scalar_equilibrium<M>(phid, phi, ux, uy, feq);
 #pragma unroll
     for (int i = 0; i < 5; ++i) {
         float neq[M];
@@ -205,12 +232,11 @@ __device__ __forceinline__ void collide(const LbParams &p, float (&f)[M][5], flo
         }
     }
 
-    // Eq. evolution3 with Eq. force (varphi = 0): F_i = 3 W_i c_i.F, weighted by
-    // (1 - omega_f / 2).
+    // Eq. evolution3 with Eq. force (varphi = 0): F_i = 3 W_i c_i.F, weighted by (1 - omega_f / 2).
     const float wf = p.omega_f, fw = 1.f - 0.5f * wf;
 #pragma unroll
     for (int i = 0; i < 9; ++i) {
-        const float heq = fluid_equilibrium(i, p.rho0, pr, ux, uy, usq);
+        const float heq = fluid_equilibrium(i, prd, ux, uy, usq);
         const float Fi = kA9(i) * (kC9x(i) * Fx + kC9y(i) * Fy);
         h[i] = fmaf(-wf, h[i] - heq, h[i]) + fw * Fi;
     }
@@ -218,11 +244,38 @@ __device__ __forceinline__ void collide(const LbParams &p, float (&f)[M][5], flo
     for (int a = 0; a < M; ++a) o.phi[a] = phi[a];
     o.ux = ux;
     o.uy = uy;
-    o.pr = pr;
+    o.pr = prx + prd;
     o.s1 = (M >= 2) ? S[M >= 2 ? 1 : 0] : 0.f;
 }
 
+template <int M>
+__device__ __forceinline__ void write_moments(float *moments, long long P, long long o0, const NodeOut<M> &o) {
+#pragma unroll
+    for (int a = 0; a < M; ++a) moments[a * P + o0] = o.phi[a];
+    moments[M * P + o0] = o.ux;
+    moments[(M + 1) * P + o0] = o.uy;
+    moments[(M + 2) * P + o0] = o.pr;
+}
+
+template <int M, typename T>
+__device__ __forceinline__ void store_node(T *out, long long P, long long o0, const float (&f)[M][5],
+                                           const float (&h)[9]) {
+#pragma unroll
+    for (int i = 0; i < 9; ++i) Store<T>::store(out + i * P + o0, h[i]);
+#pragma unroll
+    for (int a = 0; a < M; ++a)
+#pragma unroll
+        for (int i = 0; i < 5; ++i) Store<T>::store(out + (9 + 5 * a + i) * P + o0, f[a][i]);
+}
+
 // ---- the fused step ------------------------------------------------------------
+// Pull source of one fluid direction: plane j at in-plane offset `off`, with the
+// change of the pressure reference between source and node, kA_j G.(src - x).
+struct Src {
+    int plane, off;
+    float shift;
+};
+
 template <int M, typename T>
 __global__ void __launch_bounds__(256) step_kernel(const LbParams p, const T *__restrict__ in,
                                                    T *__restrict__ out, float *__restrict__ sprev,
@@ -234,86 +287,91 @@ __global__ void __launch_bounds__(256) step_kernel(const LbParams p, const T *__
 
     // Neighbour coordinates (periodic wrap) and wall crossings of the pull links.
     int xw = x - 1, xe = x + 1, ys = y - 1, yn = y + 1;
-    bool cw = false, ce = false, cs = false, cn = false;
-    if (xw < 0) { if (p.periodic_x) xw += p.nx; else cw = true; }
-    if (xe >= p.nx) { if (p.periodic_x) xe -= p.nx; else ce = true; }
-    if (ys < 0) { if (p.periodic_y) ys += p.ny; else cs = true; }
-    if (yn >= p.ny) { if (p.periodic_y) yn -= p.ny; else cn = true; }
-    const long long r0 = (long long)y * p.pitch, rs = (long long)ys * p.pitch,
-                    rn = (long long)yn * p.pitch;
-    const long long o0 = r0 + x;
+    const bool cw = xw < 0 && !p.periodic_x, ce = xe >= p.nx && !p.periodic_x;
+    const bool cs = ys < 0 && !p.periodic_y, cn = yn >= p.ny && !p.periodic_y;
+    xw = xw < 0 ? p.nx - 1 : xw;
+    xe = xe >= p.nx ? 0 : xe;
+    ys = ys < 0 ? p.ny - 1 : ys;
+    yn = yn >= p.ny ? 0 : yn;
+    const int r0 = y * p.pitch, rs = ys * p.pitch, rn = yn * p.pitch;
+    const int o0 = r0 + x;
+    const float ax = kA1 * p.gref[0], ay = kA1 * p.gref[1];  // axis-link shifts
+    const float dx5 = kA5 * p.gref[0], dy5 = kA5 * p.gref[1];  // diagonal-link shifts
+    const bool fw = p.freeslip[0], fe = p.freeslip[1], fs = p.freeslip[2], fn = p.freeslip[3];
 
-    // Fluid, D2Q9: h_i(x) = h*_i(x - c_i); bounce-back h*_opp(i)(x) across a
-    // no-slip wall; specular image across a free-slip wall; bounce-back at corners.
-    auto H = [&](int i, long long off) -> float {
-        return Store<T>::load(in + i * P + off) + fluid_ref<T>(p, i);
-    };
-    float h[9];
-    h[0] = H(0, o0);
-    h[1] = cw ? H(3, o0) : H(1, r0 + xw);
-    h[2] = cs ? H(4, o0) : H(2, rs + x);
-    h[3] = ce ? H(1, o0) : H(3, r0 + xe);
-    h[4] = cn ? H(2, o0) : H(4, rn + x);
-    // (1,1) from (x-1, y-1)
-    if (cw && cs) h[5] = H(7, o0);
-    else if (cw) h[5] = p.freeslip[0] ? H(6, rs + x) : H(7, o0);
-    else if (cs) h[5] = p.freeslip[2] ? H(8, r0 + xw) : H(7, o0);
-    else h[5] = H(5, rs + xw);
-    // (-1,1) from (x+1, y-1)
-    if (ce && cs) h[6] = H(8, o0);
-    else if (ce) h[6] = p.freeslip[1] ? H(5, rs + x) : H(8, o0);
-    else if (cs) h[6] = p.freeslip[2] ? H(7, r0 + xe) : H(8, o0);
-    else h[6] = H(6, rs + xe);
-    // (-1,-1) from (x+1, y+1)
-    if (ce && cn) h[7] = H(5, o0);
-    else if (ce) h[7] = p.freeslip[1] ? H(8, rn + x) : H(5, o0);
-    else if (cn) h[7] = p.freeslip[3] ? H(6, r0 + xe) : H(5, o0);
-    else h[7] = H(7, rn + xe);
-    // (1,-1) from (x-1, y+1)
-    if (cw && cn) h[8] = H(6, o0);
-    else if (cw) h[8] = p.freeslip[0] ? H(7, rn + x) : H(6, o0);
-    else if (cn) h[8] = p.freeslip[3] ? H(5, r0 + xw) : H(6, o0);
-    else h[8] = H(8, rn + xw);
-
-    // Scalars, D2Q5: bounce-back f*_opp(i)(x) (no flux) or anti-bounce-back
-    // -f*_opp(i)(x) + 2 W_i phi_w (Dirichlet) across a wall.
-    float f[M][5];
-#pragma unroll
-    for (int a = 0; a < M; ++a) {
-        const T *base = in + (9 + 5 * a) * P;
-        auto F = [&](int i, long long off) -> float {
-            return Store<T>::load(base + i * P + off) + scalar_ref<T>(p, a, i);
-        };
-        auto wall = [&](int side, float v) -> float {
-            return ((p.dirichlet[side] >> a) & 1u) ? p.abb[side][a] - v : v;
-        };
-        f[a][0] = F(0, o0);
-        f[a][1] = cw ? wall(0, F(3, o0)) : F(1, r0 + xw);
-        f[a][2] = cs ? wall(2, F(4, o0)) : F(2, rs + x);
-        f[a][3] = ce ? wall(1, F(1, o0)) : F(3, r0 + xe);
-        f[a][4] = cn ? wall(3, F(2, o0)) : F(4, rn + x);
+    // Fluid, D2Q9: h_i(x) = h*_j(src).  Regular link: j = i, src = x - c_i.  No-slip
+    // wall: bounce-back j = opp(i), src = x.  Free-slip wall: the specular image j
+    // from the neighbour along the wall.  Corner links: bounce-back.  Every
+    // source is chosen by selects, so all loads issue before any arithmetic.
+    Src sh[9];
+    sh[0] = {0, o0, 0.f};
+    sh[1] = cw ? Src{3, o0, 0.f} : Src{1, r0 + xw, -ax};
+    sh[2] = cs ? Src{4, o0, 0.f} : Src{2, rs + x, -ay};
+    sh[3] = ce ? Src{1, o0, 0.f} : Src{3, r0 + xe, ax};
+    sh[4] = cn ? Src{2, o0, 0.f} : Src{4, rn + x, ay};
+    {   // (1,1) from (x-1, y-1)
+        Src v{5, rs + xw, -dx5 - dy5};
+        v = (cw || cs) ? Src{7, o0, 0.f} : v;
+        v = (cw && !cs && fw) ? Src{6, rs + x, -dy5} : v;
+        v = (cs && !cw && fs) ? Src{8, r0 + xw, -dx5} : v;
+        sh[5] = v;
     }
-    const bool consume = (M >= 2 && p.skind == 2);
-    const float sp1 = consume ? sprev[o0] : 0.f;
+    {   // (-1,1) from (x+1, y-1)
+        Src v{6, rs + xe, dx5 - dy5};
+        v = (ce || cs) ? Src{8, o0, 0.f} : v;
+        v = (ce && !cs && fe) ? Src{5, rs + x, -dy5} : v;
+        v = (cs && !ce && fs) ? Src{7, r0 + xe, dx5} : v;
+        sh[6] = v;
+    }
+    {   // (-1,-1) from (x+1, y+1)
+        Src v{7, rn + xe, dx5 + dy5};
+        v = (ce || cn) ? Src{5, o0, 0.f} : v;
+        v = (ce && !cn && fe) ? Src{8, rn + x, dy5} : v;
+        v = (cn && !ce && fn) ? Src{6, r0 + xe, dx5} : v;
+        sh[7] = v;
+    }
+    {   // (1,-1) from (x-1, y+1)
+        Src v{8, rn + xw, -dx5 + dy5};
+        v = (cw || cn) ? Src{6, o0, 0.f} : v;
+        v = (cw && !cn && fw) ? Src{7, rn + x, dy5} : v;
+        v = (cn && !cw && fn) ? Src{5, r0 + xw, -dx5} : v;
+        sh[8] = v;
+    }
+    // Scalars, D2Q5: bounce-back f*_opp(i)(x) (no flux) or anti-bounce-back
+    // -f*_opp(i)(x) + 2 W_i phi_w (Dirichlet); in deviations the latter is
+    // -f'*_opp(i)(x) + 2 W_i (phi_w - phi_ref).
+    const int sp_[5] = {0, cw ? 3 : 1, cs ? 4 : 2, ce ? 1 : 3, cn ? 2 : 4};
+    const int so_[5] = {o0, cw ? o0 : r0 + xw, cs ? o0 : rs + x, ce ? o0 : r0 + xe, cn ? o0 : rn + x};
+    const int side_[5] = {-1, cw ? 0 : -1, cs ? 2 : -1, ce ? 1 : -1, cn ? 3 : -1};
 
-    NodeOut<M> o;
-    collide<M>(p, f, h, sp1, false, o);
-
+    // ---- loads
+    float h[9], f[M][5];
 #pragma unroll
-    for (int i = 0; i < 9; ++i) Store<T>::store(out + i * P + o0, h[i] - fluid_ref<T>(p, i));
+    for (int i = 0; i < 9; ++i) h[i] = Store<T>::load(in + sh[i].plane * P + sh[i].off);
 #pragma unroll
     for (int a = 0; a < M; ++a)
 #pragma unroll
-        for (int i = 0; i < 5; ++i)
-            Store<T>::store(out + (9 + 5 * a + i) * P + o0, f[a][i] - scalar_ref<T>(p, a, i));
-    if (consume) sprev[o0] = o.s1;
-    if (moments) {
+        for (int i = 0; i < 5; ++i) f[a][i] = Store<T>::load(in + (9 + 5 * a + sp_[i]) * P + so_[i]);
+    const bool consume = (M >= 2 && p.skind == 2);
+    const float sp1 = consume ? sprev[o0] : 0.f;
+
+    // ---- boundary values
 #pragma unroll
-        for (int a = 0; a < M; ++a) moments[a * P + o0] = o.phi[a];
-        moments[M * P + o0] = o.ux;
-        moments[(M + 1) * P + o0] = o.uy;
-        moments[(M + 2) * P + o0] = o.pr;
+    for (int i = 0; i < 9; ++i) h[i] += sh[i].shift;
+#pragma unroll
+    for (int i = 1; i < 5; ++i) {
+        if (side_[i] >= 0) {
+#pragma unroll
+            for (int a = 0; a < M; ++a)
+                if ((p.dirichlet[side_[i]] >> a) & 1u) f[a][i] = p.abb[side_[i]][a] - f[a][i];
+        }
     }
+
+    NodeOut<M> o;
+    collide<M>(p, f, h, pref_at(p, x, y), sp1, false, o);
+    store_node<M, T>(out, P, o0, f, h);
+    if (consume) sprev[o0] = o.s1;
+    if (moments) write_moments<M>(moments, P, o0, o);
 }
 
 // ---- initialisation from moments (collide-only pass at t = 0) ------------------
@@ -326,11 +384,15 @@ __global__ void init_kernel(const LbParams p, const float *__restrict__ fields, 
     if (x >= p.nx || y >= p.ny) return;
     const long long P = p.plane, FP = (long long)fpitch * p.ny;
     const long long o0 = (long long)y * p.pitch + x, i0 = (long long)y * fpitch + x;
-    float phi[M];
+    float phi[M], phid[M];
 #pragma unroll
-    for (int a = 0; a < M; ++a) phi[a] = fields[a * FP + i0];
+    for (int a = 0; a < M; ++a) {
+        phi[a] = fields[a * FP + i0];
+        phid[a] = phi[a] - p.phi_ref[a];
+    }
     const float ux = fields[M * FP + i0], uy = fields[(M + 1) * FP + i0];
-    const float pr = fields[(M + 2) * FP + i0];
+    const float prx = pref_at(p, x, y);
+    const float prd = fields[(M + 2) * FP + i0] - prx;
     float fm = p.Fbase;
 #pragma unroll
     for (int a = 0; a < M; ++a) fm = fmaf(p.beta[a], phi[a], fm);
@@ -338,29 +400,18 @@ __global__ void init_kernel(const LbParams p, const float *__restrict__ fields, 
     // f = f^eq(phi, u); h = h^eq(u, p) - F_i / 2 (moments then return the inputs)
     float f[M][5], h[9];
     const float usq = ux * ux + uy * uy;
-    scalar_equilibrium<M>(phi, ux, uy, f);
+    scalar_equilibrium<M>(phid, phi, ux, uy, f);
 #pragma unroll
     for (int i = 0; i < 9; ++i)
-        h[i] = fluid_equilibrium(i, p.rho0, pr, ux, uy, usq) -
-               0.5f * kA9(i) * (kC9x(i) * Fx + kC9y(i) * Fy);
+        h[i] = fluid_equilibrium(i, prd, ux, uy, usq) - 0.5f * kA9(i) * (kC9x(i) * Fx + kC9y(i) * Fy);
     NodeOut<M> o;
-    collide<M>(p, f, h, 0.f, true, o);
-#pragma unroll
-    for (int i = 0; i < 9; ++i) Store<T>::store(out + i * P + o0, h[i] - fluid_ref<T>(p, i));
-#pragma unroll
-    for (int a = 0; a < M; ++a)
-#pragma unroll
-        for (int i = 0; i < 5; ++i)
-            Store<T>::store(out + (9 + 5 * a + i) * P + o0, f[a][i] - scalar_ref<T>(p, a, i));
+    collide<M>(p, f, h, prx, 0.f, true, o);
+    store_node<M, T>(out, P, o0, f, h);
     if (M >= 2 && p.skind == 2) sprev[o0] = o.s1;
-#pragma unroll
-    for (int a = 0; a < M; ++a) moments[a * P + o0] = o.phi[a];
-    moments[M * P + o0] = o.ux;
-    moments[(M + 1) * P + o0] = o.uy;
-    moments[(M + 2) * P + o0] = o.pr;
+    write_moments<M>(moments, P, o0, o);
 }
 
-// Post-collision populations as dense FP32 planes [9 + 5m][ny][nx].
+// Post-collision populations (full values) as dense FP32 planes [9 + 5m][ny][nx].
 template <int M, typename T>
 __global__ void export_kernel(const LbParams p, const T *__restrict__ in, float *__restrict__ dense) {
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
@@ -368,14 +419,17 @@ __global__ void export_kernel(const LbParams p, const T *__restrict__ in, float 
     if (x >= p.nx || y >= p.ny) return;
     const long long P = p.plane, N = (long long)p.nx * p.ny;
     const long long o0 = (long long)y * p.pitch + x, d0 = (long long)y * p.nx + x;
+    const float prx = pref_at(p, x, y);
 #pragma unroll
-    for (int i = 0; i < 9; ++i) dense[i * N + d0] = Store<T>::load(in + i * P + o0) + fluid_ref<T>(p, i);
+    for (int i = 0; i < 9; ++i) {
+        const float ref = (i == 0) ? p.rho0 - kC * prx : kA9(i) * prx;
+        dense[i * N + d0] = Store<T>::load(in + i * P + o0) + ref;
+    }
 #pragma unroll
     for (int a = 0; a < M; ++a)
 #pragma unroll
         for (int i = 0; i < 5; ++i)
-            dense[(9 + 5 * a + i) * N + d0] =
-                Store<T>::load(in + (9 + 5 * a + i) * P + o0) + scalar_ref<T>(p, a, i);
+            dense[(9 + 5 * a + i) * N + d0] = Store<T>::load(in + (9 + 5 * a + i) * P + o0) + kWs(i) * p.phi_ref[a];
 }
 
 __global__ void pack_kernel(const LbParams p, int nf, const float *__restrict__ mom,

@@ -61,7 +61,7 @@ class cdf_boundaries(ctypes.Structure):
 
 class cdf_options(ctypes.Structure):
     _fields_ = [("storage", ctypes.c_int), ("rho0", ctypes.c_double), ("cuda_stream", ctypes.c_void_p),
-                ("phi_ref16", ctypes.c_double * MAX_M), ("block_x", ctypes.c_int), ("block_y", ctypes.c_int)]
+                ("phi_ref", ctypes.c_double * MAX_M), ("block_x", ctypes.c_int), ("block_y", ctypes.c_int)]
 
 
 class cdf_info(ctypes.Structure):
@@ -197,7 +197,7 @@ def cdf_lb_last_error() -> str:
 
 
 # ---- problem description -> C structs ------------------------------------------------
-def structs_from_problem(pb: Problem, storage: str = "fp32", stream: int = 0, block=None, phi_ref16=None):
+def structs_from_problem(pb: Problem, storage: str = "fp32", stream: int = 0, block=None, phi_ref=None):
     m = pb.m
     if m > MAX_M:
         raise ValueError(f"m = {m} > {MAX_M}")
@@ -230,16 +230,16 @@ def structs_from_problem(pb: Problem, storage: str = "fp32", stream: int = 0, bl
     opt.storage = STORAGE[storage]
     opt.rho0 = pb.rho0
     opt.cuda_stream = stream or None
-    ref = phi_ref16 if phi_ref16 is not None else default_ref16(pb)
+    ref = phi_ref if phi_ref is not None else default_phi_ref(pb)
     for a in range(m):
-        opt.phi_ref16[a] = float(ref[a])
+        opt.phi_ref[a] = float(ref[a])
     if block is not None:
         opt.block_x, opt.block_y = block
     return grid, dif, src, frc, bc, opt
 
 
-def default_ref16(pb: Problem):
-    """Reference scalar values of the 16-bit deviation storage: the midpoint of the
+def default_phi_ref(pb: Problem):
+    """Reference scalar values of the deviation storage: the midpoint of the
     initial range of each scalar, widened to include its Dirichlet values."""
     ref = []
     for a in range(pb.m):
@@ -256,11 +256,11 @@ class Solver:
     """One lattice on the GPU behind the C ABI."""
 
     def __init__(self, pb: Problem, storage: str = "fp32", stream: int = 0, block=None, init: bool = True,
-                 phi_ref16=None):
+                 phi_ref=None):
         self.pb = pb
         self.m, self.nx, self.ny = pb.m, pb.nx, pb.ny
         self.storage = storage
-        self._structs = structs_from_problem(pb, storage, stream, block, phi_ref16)
+        self._structs = structs_from_problem(pb, storage, stream, block, phi_ref)
         grid, dif, src, frc, bc, opt = self._structs
         self.h = cdf_lb_create(grid, pb.m, dif, pb.nu, src, frc, bc, opt)
         if init:
