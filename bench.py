@@ -227,6 +227,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="chemotaxis_plume_512x256")
     ap.add_argument("--lb-steps", type=int, default=2000, help="lattice time steps per benchmark step")
+    ap.add_argument("--storage", default="fp32", choices=["fp32", "fp16", "bf16"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=3)
     args = ap.parse_args()
@@ -247,7 +248,7 @@ def main():
     from paper_2101_03055_gb300 import build, lib
     build.build()
     pb = workload(args.workload, rank)
-    solver = lib.Solver(pb)
+    solver = lib.Solver(pb, storage=args.storage)
     info = solver.info()
     nodes = pb.nodes
     K, W, S = args.steps, args.warmup, args.lb_steps
@@ -325,7 +326,8 @@ def main():
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": traffic,
                      "peak_source": f"{peak_kind} copy bandwidth (MEASURED_PEAKS.json hbm_gbs)",
-                     "bytes_per_lup": info.bytes_per_lup, "kernel": "step_kernel<2,float>",
+                     "bytes_per_lup": info.bytes_per_lup,
+                     "kernel": f"step_kernel<{pb.m},{ {0: 'float', 1: '__half', 2: '__nv_bfloat16'}[info.storage]}>",
                      "launch_us": launch_s * 1e6},
         "gpu_launches": S * K,
         "clocks": clk.summary(),

@@ -56,9 +56,12 @@ typedef enum {
 
 /* Population storage.  Every mode stores each population as its deviation from
  * a reference state -- W_i phi_ref_a for scalar a; h^eq_i(p_ref(x), u = 0) for
- * the fluid, with p_ref the hydrostatic pressure of the force at phi_ref along
- * walled axes -- as FP32, FP16 or BF16; every collision is computed in FP32 on
- * these deviations (paper: silent on precision). */
+ * the fluid, with the linear reference pressure p_ref(x) = p_ref_grad . (x -
+ * centre) -- as FP32, FP16 or BF16; every collision is computed in FP32 on
+ * these deviations (paper: silent on precision).  The references change no
+ * result in exact arithmetic; chosen near the solution (phi_ref inside the
+ * scalar range, p_ref_grad the hydrostatic gradient of the mean force) they
+ * keep the stored numbers small and the rounding error with them. */
 typedef enum { CDF_FP32 = 0, CDF_FP16_DEV = 1, CDF_BF16_DEV = 2 } cdf_storage;
 
 typedef enum { CDF_BC_PERIODIC = 0, CDF_BC_WALL = 1 } cdf_bckind;
@@ -116,6 +119,7 @@ typedef struct {
     double rho0;                       /* the constant of sigma_0 in Eq. heq (> 0) */
     void *cuda_stream;                 /* cudaStream_t of the caller, NULL = default */
     double phi_ref[CDF_MAX_M];         /* reference scalar values of the stored deviations */
+    double p_ref_grad[2];              /* reference pressure gradient (used along walled axes only) */
     int block_x, block_y;              /* step kernel CTA shape; 0 = autotuned */
 } cdf_options;
 

@@ -305,6 +305,10 @@ cdf_status cdf_lb_create(const cdf_grid *grid, int m, const cdf_diffusion *dif, 
         return fail(CDF_EINVAL, "chemotaxis / consumption closures need m >= 2");
     if (opt->storage < CDF_FP32 || opt->storage > CDF_BF16_DEV) return fail(CDF_EINVAL, "bad storage");
     if (!(opt->rho0 > 0.0)) return fail(CDF_EINVAL, "rho0 must be positive");
+    for (int a = 0; a < m; ++a)
+        if (!std::isfinite(opt->phi_ref[a])) return fail(CDF_EINVAL, "phi_ref must be finite");
+    if (!std::isfinite(opt->p_ref_grad[0]) || !std::isfinite(opt->p_ref_grad[1]))
+        return fail(CDF_EINVAL, "p_ref_grad must be finite");
     cdf_status st;
     if ((st = check_side_pair(bc->west, bc->east, "x")) != CDF_OK) return st;
     if ((st = check_side_pair(bc->south, bc->north, "y")) != CDF_OK) return st;
@@ -377,12 +381,10 @@ cdf_status cdf_lb_create(const cdf_grid *grid, int m, const cdf_diffusion *dif, 
         P.phi_ref[a] = (float)opt->phi_ref[a];
     }
     P.Fbase = (float)Fbase;
-    // Pressure reference of the fluid deviations: hydrostatic balance grad p = F
-    // of the force at the reference scalar values, along walled axes only.
-    double Fref = Fbase;
-    for (int a = 0; a < m; ++a) Fref += frc->beta[a] * opt->phi_ref[a];
-    P.gref[0] = bc->west.kind == CDF_BC_WALL ? (float)(frc->g[0] * Fref) : 0.f;
-    P.gref[1] = bc->south.kind == CDF_BC_WALL ? (float)(frc->g[1] * Fref) : 0.f;
+    // Reference pressure gradient of the fluid deviations; a linear reference
+    // cannot wrap around a periodic axis, so it is used along walled axes only.
+    P.gref[0] = bc->west.kind == CDF_BC_WALL ? (float)opt->p_ref_grad[0] : 0.f;
+    P.gref[1] = bc->south.kind == CDF_BC_WALL ? (float)opt->p_ref_grad[1] : 0.f;
     P.xc = 0.5f * (float)(grid->nx - 1);
     P.yc = 0.5f * (float)(grid->ny - 1);
     P.rho0 = (float)opt->rho0;

@@ -61,7 +61,8 @@ class cdf_boundaries(ctypes.Structure):
 
 class cdf_options(ctypes.Structure):
     _fields_ = [("storage", ctypes.c_int), ("rho0", ctypes.c_double), ("cuda_stream", ctypes.c_void_p),
-                ("phi_ref", ctypes.c_double * MAX_M), ("block_x", ctypes.c_int), ("block_y", ctypes.c_int)]
+                ("phi_ref", ctypes.c_double * MAX_M), ("p_ref_grad", ctypes.c_double * 2),
+                ("block_x", ctypes.c_int), ("block_y", ctypes.c_int)]
 
 
 class cdf_info(ctypes.Structure):
@@ -197,7 +198,8 @@ def cdf_lb_last_error() -> str:
 
 
 # ---- problem description -> C structs ------------------------------------------------
-def structs_from_problem(pb: Problem, storage: str = "fp32", stream: int = 0, block=None, phi_ref=None):
+def structs_from_problem(pb: Problem, storage: str = "fp32", stream: int = 0, block=None, phi_ref=None,
+                         p_ref_grad=None):
     m = pb.m
     if m > MAX_M:
         raise ValueError(f"m = {m} > {MAX_M}")
@@ -233,6 +235,8 @@ def structs_from_problem(pb: Problem, storage: str = "fp32", stream: int = 0, bl
     ref = phi_ref if phi_ref is not None else default_phi_ref(pb)
     for a in range(m):
         opt.phi_ref[a] = float(ref[a])
+    grad = p_ref_grad if p_ref_grad is not None else default_p_ref_grad(pb)
+    opt.p_ref_grad[0], opt.p_ref_grad[1] = float(grad[0]), float(grad[1])
     if block is not None:
         opt.block_x, opt.block_y = block
     return grid, dif, src, frc, bc, opt
@@ -252,15 +256,22 @@ def default_phi_ref(pb: Problem):
     return ref
 
 
+def default_p_ref_grad(pb: Problem):
+    """Reference pressure gradient of the fluid deviation storage: the hydrostatic
+    gradient grad p = F of the force at the mean initial scalar values."""
+    mag = pb.F0 + sum(float(pb.beta[a]) * (float(pb.phi0[a].mean()) - float(pb.phi_ref[a])) for a in range(pb.m))
+    return (float(pb.g[0]) * mag, float(pb.g[1]) * mag)
+
+
 class Solver:
     """One lattice on the GPU behind the C ABI."""
 
     def __init__(self, pb: Problem, storage: str = "fp32", stream: int = 0, block=None, init: bool = True,
-                 phi_ref=None):
+                 phi_ref=None, p_ref_grad=None):
         self.pb = pb
         self.m, self.nx, self.ny = pb.m, pb.nx, pb.ny
         self.storage = storage
-        self._structs = structs_from_problem(pb, storage, stream, block, phi_ref)
+        self._structs = structs_from_problem(pb, storage, stream, block, phi_ref, p_ref_grad)
         grid, dif, src, frc, bc, opt = self._structs
         self.h = cdf_lb_create(grid, pb.m, dif, pb.nu, src, frc, bc, opt)
         if init:
