@@ -2,7 +2,11 @@
 
 Tolerance: relative L2 <= 1e-5 per field for FP32 population storage, the
 bound the solver is specified to; every comparison is element by element on
-the same seeded inputs.  Sizes span several CTA tiles and ragged tails; the
+the same seeded inputs.  The pressure is the one field whose error has a floor
+set by the storage rather than by its own size: p is recovered from fluid
+populations whose magnitude is set by the velocity term (3 W_i c_i.u ~ |u|/3),
+so FP32 storage resolves p only to about 2^-24 |u| / 3 per node; its relative
+L2 is therefore taken against max(||p||, ||u|| / 3).  Sizes span several CTA tiles and ragged tails; the
 full-size workloads run in the launch configuration the benchmark uses
 (autotuned CTA shape, CUDA-graph batches) for a shorter window.
 """
@@ -27,7 +31,8 @@ def rel_l2(a, b):
 def field_errors(Mg, Mo, m):
     errs = {f"phi{a}": rel_l2(Mg[a], Mo[a]) for a in range(m)}
     errs["u"] = rel_l2(Mg[m:m + 2], Mo[m:m + 2])
-    errs["p"] = rel_l2(Mg[m + 2], Mo[m + 2])
+    p_scale = max(np.linalg.norm(Mo[m + 2]), np.linalg.norm(Mo[m:m + 2]) / 3.0)
+    errs["p"] = np.linalg.norm(Mg[m + 2] - Mo[m + 2]) / (p_scale if p_scale > 0 else 1.0)
     return errs
 
 
@@ -101,7 +106,9 @@ def developed_cavity(n, seed=0):
     U = 0.02
     ux = -U * np.sin(np.pi * X) * np.cos(np.pi * Y)
     uy = U * np.cos(np.pi * X) * np.sin(np.pi * Y)
-    return pb.replace(phi0=np.stack([T, C]), u0=np.stack([ux, uy]))
+    # pressure near hydrostatic balance with the buoyancy g (T + Nc C) along y
+    p0 = (pb.beta[0] * T + pb.beta[1] * C) * (np.arange(n)[:, None] - 0.5 * (n - 1))
+    return pb.replace(phi0=np.stack([T, C]), u0=np.stack([ux, uy]), p0=p0)
 
 
 def test_ddc_cavity_full_size(cdf, oracle_mod):
