@@ -199,6 +199,30 @@ cdf_status cdf_lb_get_info(const cdf_lb *h, cdf_info *out);
  * step kernels run; for timing with events.  Borrowed, do not destroy. */
 void *cdf_lb_stream(const cdf_lb *h);
 
+/* Allocation-free FP64 sums over a device moment stack -- the reduction behind
+ * cdf_lb_mass and the stop test of cdf_lb_run_to_steady, for callers that
+ * cannot allocate device memory once running (real-time loops that forbid
+ * allocation after start-up, plug-ins inside a host application that owns all
+ * device memory through its own pool, processes under a fixed device-memory
+ * quota).  The paper has no counterpart: it is a systems addition.
+ *   dev_fields      device FP32 stack [m+3][ny][nx] (phi..., u_x, u_y, p), contiguous,
+ *                   e.g. filled by cdf_lb_moments_device
+ *   dev_fields_old  same layout, or NULL
+ *   dev_out         device FP64 array of 3m + 5 entries, written on `stream`:
+ *                   [0, m) sum phi_a; [m, 2m+2) sum |q - q_old| (0 without old);
+ *                   [2m+2, 3m+4) sum |q| for q in {phi_0..phi_{m-1}, u_x, u_y};
+ *                   [3m+4] number of non-finite values
+ *   stream          cudaStream_t, NULL = legacy default stream
+ * Allocates nothing: the block partials live in a file-scope device array of
+ * 41,344 bytes (304 blocks x 17 sums) that every GPU loading the library holds
+ * until exit.  Limits: 1 <= m <= 4, nx * ny < 2^31 (CDF_EINVAL beyond).  The
+ * first call on each device looks up the array's device address
+ * (cudaGetSymbolAddress) with that device current; make that first call before
+ * any stream capture.  All calls share the array: calls that overlap on the
+ * GPU race.  Returns after launching; dev_out is ready when `stream` is. */
+cdf_status cdf_moment_sums_static(const float *dev_fields, const float *dev_fields_old, int nx, int ny, int m,
+                                  double *dev_out, void *stream);
+
 /* Release the handle and its device memory (NULL is a no-op). */
 void cdf_lb_destroy(cdf_lb *h);
 

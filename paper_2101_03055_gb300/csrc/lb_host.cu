@@ -282,6 +282,11 @@ cdf_status check_side_pair(const cdf_side &a, const cdf_side &b, const char *axi
 
 }  // namespace
 
+cdf_status cdflb::report_error(cdf_status status, const char *msg) {
+    std::snprintf(g_err, sizeof g_err, "%s", msg);
+    return status;
+}
+
 extern "C" {
 
 const char *cdf_lb_last_error(void) { return g_err; }

@@ -4,6 +4,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "../../include/cdf_lb.h"
+
 namespace cdflb {
 
 constexpr int kMaxM = 4;
@@ -63,5 +65,8 @@ constexpr int kReduceBlocks = 304;  // 2 x 152 SMs
 int reduce_quantities(int m);
 cudaError_t launch_reduce(const float *mom_new, const float *mom_old, int nx, int ny, int pitch,
                           long long plane, int m, double *partials, double *out, cudaStream_t s);
+
+// Sets the calling thread's cdf_lb_last_error() message and returns `status`.
+cdf_status report_error(cdf_status status, const char *msg);
 
 }  // namespace cdflb

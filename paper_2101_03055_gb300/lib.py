@@ -98,6 +98,8 @@ SIGNATURES = {
     "cdf_lb_stream": (ctypes.c_void_p, [_H]),
     "cdf_lb_destroy": (None, [_H]),
     "cdf_lb_last_error": (ctypes.c_char_p, []),
+    "cdf_moment_sums_static": (ctypes.c_int, [_FP, _FP, ctypes.c_int, ctypes.c_int, ctypes.c_int, _FP,
+                                              ctypes.c_void_p]),
 }
 
 
@@ -195,6 +197,14 @@ def cdf_lb_destroy(h):
 
 def cdf_lb_last_error() -> str:
     return load().cdf_lb_last_error().decode()
+
+
+def cdf_moment_sums_static(dev_fields: int, dev_fields_old: int, nx: int, ny: int, m: int, dev_out: int,
+                           stream: int = 0) -> int:
+    """Allocation-free FP64 sums over a device moment stack (see include/cdf_lb.h);
+    returns the status code without raising."""
+    return load().cdf_moment_sums_static(ctypes.c_void_p(dev_fields or None), ctypes.c_void_p(dev_fields_old or None),
+                                         nx, ny, m, ctypes.c_void_p(dev_out or None), ctypes.c_void_p(stream or None))
 
 
 # ---- problem description -> C structs ------------------------------------------------
