@@ -116,6 +116,8 @@ struct cdf_lb {
     int cur = 0;  // buffer that holds the current post-collision populations
     float *sprev = nullptr;
     float *mom = nullptr, *mom_prev = nullptr;
+    bool mr = false;                       // 16-bit storage: node-equilibrium deviations
+    float *mom_pp[2] = {nullptr, nullptr};  // 16-bit storage: moments beside buf[0], buf[1]
     float *dense = nullptr;       // dense FP32 staging (export, host init)
     float *host_stage = nullptr;  // pinned host staging of one moment stack
     double *partials = nullptr, *red = nullptr, *red_host = nullptr;
@@ -141,6 +143,8 @@ void release(cdf_lb *h) {
     cudaFree(h->sprev);
     cudaFree(h->mom);
     cudaFree(h->mom_prev);
+    cudaFree(h->mom_pp[0]);
+    cudaFree(h->mom_pp[1]);
     cudaFree(h->dense);
     cudaFree(h->partials);
     cudaFree(h->red);
@@ -164,9 +168,20 @@ cdf_status leave(cdf_lb *h) {
     return CDF_OK;
 }
 
+// Moments of the current time: FP32 storage writes them to `mom` on the last
+// step of a call; 16-bit storage keeps them beside the current populations.
+float *current_moments(cdf_lb *h) { return h->mr ? h->mom_pp[h->cur] : h->mom; }
+
+cudaError_t launch_any(cdf_lb *h, int src, bool with_moments) {
+    if (h->mr)
+        return launch_step_mr(h->P, h->storage, h->buf[src], h->mom_pp[src], h->buf[src ^ 1], h->mom_pp[src ^ 1],
+                              h->sprev, h->block, h->s);
+    return launch_step(h->P, h->storage, h->buf[src], h->buf[src ^ 1], h->sprev, with_moments ? h->mom : nullptr,
+                       h->block, h->s);
+}
+
 cdf_status launch_one(cdf_lb *h, int src, bool with_moments) {
-    CK(launch_step(h->P, h->storage, h->buf[src], h->buf[src ^ 1], h->sprev,
-                   with_moments ? h->mom : nullptr, h->block, h->s));
+    CK(launch_any(h, src, with_moments));
     return CDF_OK;
 }
 
@@ -176,9 +191,7 @@ cdf_status get_graph(cdf_lb *h, int parity, int with_moments, cudaGraphExec_t *o
         CK(cudaStreamBeginCapture(h->s, cudaStreamCaptureModeThreadLocal));
         int src = parity;
         for (int k = 0; k < kGraphSteps; ++k) {
-            cudaError_t e = launch_step(h->P, h->storage, h->buf[src], h->buf[src ^ 1], h->sprev,
-                                        (with_moments && k == kGraphSteps - 1) ? h->mom : nullptr,
-                                        h->block, h->s);
+            cudaError_t e = launch_any(h, src, with_moments && k == kGraphSteps - 1);
             if (e != cudaSuccess) {
                 cudaStreamEndCapture(h->s, &graph);
                 if (graph) cudaGraphDestroy(graph);
@@ -359,6 +372,7 @@ cdf_status cdf_lb_create(const cdf_grid *grid, int m, const cdf_diffusion *dif, 
     h->plane = (long long)h->pitch * h->ny;
     h->planes = 9 + 5 * m;
     h->sprev_planes = src->kind == CDF_S_CONSUMPTION ? 1 : 0;
+    h->mr = opt->storage != CDF_FP32;
     h->user = static_cast<cudaStream_t>(opt->cuda_stream);
 
     LbParams &P = h->P;
@@ -390,6 +404,10 @@ cdf_status cdf_lb_create(const cdf_grid *grid, int m, const cdf_diffusion *dif, 
     // cannot wrap around a periodic axis, so it is used along walled axes only.
     P.gref[0] = bc->west.kind == CDF_BC_WALL ? (float)opt->p_ref_grad[0] : 0.f;
     P.gref[1] = bc->south.kind == CDF_BC_WALL ? (float)opt->p_ref_grad[1] : 0.f;
+    if (h->mr) {  // 16-bit storage references each node's own equilibrium instead
+        for (int a = 0; a < m; ++a) P.phi_ref[a] = 0.f;
+        P.gref[0] = P.gref[1] = 0.f;
+    }
     P.xc = 0.5f * (float)(grid->nx - 1);
     P.yc = 0.5f * (float)(grid->ny - 1);
     P.rho0 = (float)opt->rho0;
@@ -401,7 +419,7 @@ cdf_status cdf_lb_create(const cdf_grid *grid, int m, const cdf_diffusion *dif, 
         for (int a = 0; a < m; ++a) {
             if (sides[s]->kind == CDF_BC_WALL && sides[s]->scalar[a] == CDF_SC_DIRICHLET) {
                 P.dirichlet[s] |= 1u << a;
-                P.abb[s][a] = (float)((sides[s]->value[a] - opt->phi_ref[a]) / 3.0);  // 2 W_i (phi_w - phi_ref)
+                P.abb[s][a] = (float)((sides[s]->value[a] - P.phi_ref[a]) / 3.0);  // 2 W_i (phi_w - phi_ref)
             }
         }
     }
@@ -415,6 +433,8 @@ cdf_status cdf_lb_create(const cdf_grid *grid, int m, const cdf_diffusion *dif, 
               alloc((void **)&h->sprev, (size_t)h->plane * 4) &&
               alloc((void **)&h->mom, (size_t)(m + 3) * h->plane * 4) &&
               alloc((void **)&h->mom_prev, (size_t)(m + 3) * h->plane * 4) &&
+              (!h->mr || (alloc((void **)&h->mom_pp[0], (size_t)(m + 3) * h->plane * 4) &&
+                          alloc((void **)&h->mom_pp[1], (size_t)(m + 3) * h->plane * 4))) &&
               alloc((void **)&h->dense, (size_t)h->planes * n * 4) &&
               alloc((void **)&h->partials, (size_t)reduce_quantities(m) * kReduceBlocks * sizeof(double)) &&
               alloc((void **)&h->red, (size_t)reduce_quantities(m) * sizeof(double)) &&
@@ -434,7 +454,9 @@ cdf_status cdf_lb_create(const cdf_grid *grid, int m, const cdf_diffusion *dif, 
     if (cudaMemsetAsync(h->buf[0], 0, pop_bytes, h->s) != cudaSuccess ||
         cudaMemsetAsync(h->buf[1], 0, pop_bytes, h->s) != cudaSuccess ||
         cudaMemsetAsync(h->sprev, 0, (size_t)h->plane * 4, h->s) != cudaSuccess ||
-        cudaMemsetAsync(h->mom, 0, (size_t)(m + 3) * h->plane * 4, h->s) != cudaSuccess) {
+        cudaMemsetAsync(h->mom, 0, (size_t)(m + 3) * h->plane * 4, h->s) != cudaSuccess ||
+        (h->mr && (cudaMemsetAsync(h->mom_pp[0], 0, (size_t)(m + 3) * h->plane * 4, h->s) != cudaSuccess ||
+                   cudaMemsetAsync(h->mom_pp[1], 0, (size_t)(m + 3) * h->plane * 4, h->s) != cudaSuccess))) {
         release(h);
         return fail(CDF_ECUDA, "memset failed");
     }
@@ -462,7 +484,10 @@ void cdf_lb_destroy(cdf_lb *h) {
 }
 
 static cdf_status init_from_device_fields(cdf_lb *h, const float *fields) {
-    CK(launch_init(h->P, h->storage, fields, h->nx, h->buf[0], h->sprev, h->mom, h->s));
+    if (h->mr)
+        CK(launch_init_mr(h->P, h->storage, fields, h->nx, h->buf[0], h->mom_pp[0], h->sprev, h->s));
+    else
+        CK(launch_init(h->P, h->storage, fields, h->nx, h->buf[0], h->sprev, h->mom, h->s));
     h->cur = 0;
     h->t = 0;
     h->initialised = true;
@@ -527,11 +552,11 @@ cdf_status cdf_lb_run_to_steady(cdf_lb *h, double tol, long long check_every, lo
     double R = INFINITY;
     cdf_status result = CDF_ENOTCONVERGED;
     while (taken < max_steps) {
-        CK(cudaMemcpyAsync(h->mom_prev, h->mom, mom_bytes, cudaMemcpyDeviceToDevice, h->s));
+        CK(cudaMemcpyAsync(h->mom_prev, current_moments(h), mom_bytes, cudaMemcpyDeviceToDevice, h->s));
         const long long k = std::min(check_every, max_steps - taken);
         if ((st = run_steps(h, k)) != CDF_OK) return st;
         taken += k;
-        if ((st = reduce(h, h->mom, h->mom_prev, q)) != CDF_OK) return st;
+        if ((st = reduce(h, current_moments(h), h->mom_prev, q)) != CDF_OK) return st;
         if (q[3 * m + 4] > 0) { result = CDF_EUNSTABLE; break; }
         R = 0.0;
         for (int f = 0; f < m + 2; ++f) {
@@ -556,7 +581,7 @@ cdf_status cdf_lb_moments_device(cdf_lb *h, float *dev_out) {
     DeviceGuard g(h->device);
     cdf_status st = enter(h);
     if (st != CDF_OK) return st;
-    CK(launch_pack_moments(h->P, h->mom, dev_out, h->s));
+    CK(launch_pack_moments(h->P, current_moments(h), dev_out, h->s));
     return leave(h);
 }
 
@@ -568,7 +593,7 @@ cdf_status cdf_lb_moments(cdf_lb *h, double *host_out) {
     cdf_status st = enter(h);
     if (st != CDF_OK) return st;
     const size_t n = (size_t)h->nx * h->ny * (h->m + 3);
-    CK(launch_pack_moments(h->P, h->mom, h->dense, h->s));
+    CK(launch_pack_moments(h->P, current_moments(h), h->dense, h->s));
     CK(cudaMemcpyAsync(h->host_stage, h->dense, n * 4, cudaMemcpyDeviceToHost, h->s));
     CK(cudaStreamSynchronize(h->s));
     for (size_t i = 0; i < n; ++i) host_out[i] = h->host_stage[i];
@@ -583,7 +608,7 @@ cdf_status cdf_lb_mass(cdf_lb *h, double *sums) {
     cdf_status st = enter(h);
     if (st != CDF_OK) return st;
     double q[3 * kMaxM + 5];
-    if ((st = reduce(h, h->mom, nullptr, q)) != CDF_OK) return st;
+    if ((st = reduce(h, current_moments(h), nullptr, q)) != CDF_OK) return st;
     for (int a = 0; a < h->m; ++a) sums[a] = q[a];
     return leave(h);
 }
@@ -597,7 +622,10 @@ cdf_status cdf_lb_populations(cdf_lb *h, double *f, double *hf, double *s_now) {
     if (st != CDF_OK) return st;
     const size_t n = (size_t)h->nx * h->ny;
     std::vector<float> tmp((size_t)h->planes * n), sp;
-    CK(launch_export(h->P, h->storage, h->buf[h->cur], h->dense, h->s));
+    if (h->mr)
+        CK(launch_export_mr(h->P, h->storage, h->buf[h->cur], h->mom_pp[h->cur], h->dense, h->s));
+    else
+        CK(launch_export(h->P, h->storage, h->buf[h->cur], h->dense, h->s));
     CK(cudaMemcpyAsync(tmp.data(), h->dense, tmp.size() * 4, cudaMemcpyDeviceToHost, h->s));
     if (s_now && h->sprev_planes) {
         sp.resize((size_t)h->plane);
@@ -641,7 +669,7 @@ cdf_status cdf_lb_save(cdf_lb *h, const char *path) {
     std::vector<char> data(pop + spb + momb);
     CK(cudaMemcpyAsync(data.data(), h->buf[h->cur], pop, cudaMemcpyDeviceToHost, h->s));
     CK(cudaMemcpyAsync(data.data() + pop, h->sprev, spb, cudaMemcpyDeviceToHost, h->s));
-    CK(cudaMemcpyAsync(data.data() + pop + spb, h->mom, momb, cudaMemcpyDeviceToHost, h->s));
+    CK(cudaMemcpyAsync(data.data() + pop + spb, current_moments(h), momb, cudaMemcpyDeviceToHost, h->s));
     CK(cudaStreamSynchronize(h->s));
     FileHeader hd{};
     std::memcpy(hd.magic, kMagic, 8);
@@ -685,11 +713,11 @@ cdf_status cdf_lb_load(cdf_lb *h, const char *path) {
     DeviceGuard g(h->device);
     cdf_status st = enter(h);
     if (st != CDF_OK) return st;
+    h->cur = 0;
     CK(cudaMemcpyAsync(h->buf[0], data.data(), pop, cudaMemcpyHostToDevice, h->s));
     CK(cudaMemcpyAsync(h->sprev, data.data() + pop, spb, cudaMemcpyHostToDevice, h->s));
-    CK(cudaMemcpyAsync(h->mom, data.data() + pop + spb, momb, cudaMemcpyHostToDevice, h->s));
+    CK(cudaMemcpyAsync(current_moments(h), data.data() + pop + spb, momb, cudaMemcpyHostToDevice, h->s));
     CK(cudaStreamSynchronize(h->s));
-    h->cur = 0;
     h->t = hd.t;
     h->initialised = true;
     return leave(h);
@@ -700,7 +728,8 @@ cdf_status cdf_lb_get_info(const cdf_lb *h, cdf_info *out) {
     out->nx = h->nx; out->ny = h->ny; out->m = h->m; out->pitch = h->pitch;
     out->storage = h->storage; out->planes = h->planes; out->sprev_planes = h->sprev_planes;
     out->block_x = (int)h->block.x; out->block_y = (int)h->block.y;
-    out->bytes_per_lup = 2.0 * h->planes * (double)elem_size(h->storage) + 8.0 * h->sprev_planes;
+    out->bytes_per_lup = 2.0 * h->planes * (double)elem_size(h->storage) + 8.0 * h->sprev_planes +
+                         (h->mr ? 2.0 * 4.0 * (h->m + 3) : 0.0);
     out->t = h->t;
     return CDF_OK;
 }

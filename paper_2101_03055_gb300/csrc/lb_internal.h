@@ -54,6 +54,15 @@ cudaError_t launch_init(const LbParams &p, int storage, const float *fields, int
                         void *out, float *sprev, float *moments, cudaStream_t s);
 cudaError_t launch_export(const LbParams &p, int storage, const void *in, float *dense,
                           cudaStream_t s);
+// 16-bit storage (FP16/BF16): populations stored as deviations from each node's
+// own equilibrium, with the node's moments (phi, u, p) in FP32 (m + 3 planes);
+// moments are ping-ponged with the populations.
+cudaError_t launch_step_mr(const LbParams &p, int storage, const void *in, const float *moments_in, void *out,
+                           float *moments_out, float *sprev, dim3 block, cudaStream_t s);
+cudaError_t launch_init_mr(const LbParams &p, int storage, const float *fields, int fields_pitch, void *out,
+                           float *moments_out, float *sprev, cudaStream_t s);
+cudaError_t launch_export_mr(const LbParams &p, int storage, const void *in, const float *moments, float *dense,
+                             cudaStream_t s);
 cudaError_t launch_pack_moments(const LbParams &p, const float *moments, float *dense,
                                 cudaStream_t s);
 

@@ -45,32 +45,6 @@ __host__ __device__ constexpr int kC5y(int i) { return i == 2 ? 1 : (i == 4 ? -1
 __host__ __device__ constexpr int kC9x(int i) { return (i == 1 || i == 5 || i == 8) ? 1 : ((i == 3 || i == 6 || i == 7) ? -1 : 0); }
 __host__ __device__ constexpr int kC9y(int i) { return (i == 2 || i == 5 || i == 6) ? 1 : ((i == 4 || i == 7 || i == 8) ? -1 : 0); }
 
-// Scalar equilibrium, Eq. feq-phi with lambda = I, vartheta = 0:
-// f^eq_i = W_i phi (1 + 3 c_i.u); the rest population is phi minus the moving
-// ones, so sum_i f^eq_i = phi up to one rounding.
-template <int M>
-__device__ __forceinline__ void scalar_equilibrium(const float (&phi)[M], float ux, float uy,
-                                                   float (&feq)[M][5]) {
-#pragma unroll
-    for (int b = 0; b < M; ++b) {
-        const float wp = kW5 * phi[b];
-        feq[b][1] = wp * fmaf(3.f, ux, 1.f);
-        feq[b][2] = wp * fmaf(3.f, uy, 1.f);
-        feq[b][3] = wp * fmaf(-3.f, ux, 1.f);
-        feq[b][4] = wp * fmaf(-3.f, uy, 1.f);
-        feq[b][0] = phi[b] - ((feq[b][1] + feq[b][3]) + (feq[b][2] + feq[b][4]));
-    }
-}
-
-// Fluid equilibrium, Eq. heq: h^eq_i = sigma_i + W_i [3 c_i.u + 4.5 (c_i.u)^2 - 1.5 u.u],
-// sigma_i = 3 W_i p (i != 0), sigma_0 = rho0 - (1 - W_0) p / cs^2; written with
-// kA_i = 3 W_i as kA_i (p + c_i.u + 1.5 (c_i.u)^2 - 0.5 u.u).
-__device__ __forceinline__ float fluid_equilibrium(int i, float rho0, float pr, float ux, float uy, float usq) {
-    if (i == 0) return rho0 - kC * pr - kQ * usq;
-    const float cu = kC9x(i) * ux + kC9y(i) * uy;
-    return kA9(i) * ((pr + cu) + fmaf(1.5f * cu, cu, -0.5f * usq));
-}
-
 // ---- storage types ---------------------------------------------------------------
 // Populations are stored as deviations from a reference state (below) in FP32,
 // FP16 or BF16; every collision is computed in FP32.
@@ -79,16 +53,20 @@ template <> struct Store<float> {
     __device__ static float load(const float *p) { return __ldg(p); }
     __device__ static void store(float *p, float v) { *p = v; }
 };
+// FP16 holds the small deviations scaled by 2^12 (exactly invertible), which
+// moves them out of FP16's subnormal range: normal numbers then cover
+// |d| in [1.5e-8, 16].
+constexpr float kHalfScale = 4096.f, kHalfUnscale = 1.f / 4096.f;
 template <> struct Store<__half> {
-    __device__ static float load(const __half *p) { return __half2float(__ldg(p)); }
-    __device__ static void store(__half *p, float v) { *p = __float2half_rn(v); }
+    __device__ static float load(const __half *p) { return __half2float(__ldg(p)) * kHalfUnscale; }
+    __device__ static void store(__half *p, float v) { *p = __float2half_rn(v * kHalfScale); }
 };
 template <> struct Store<__nv_bfloat16> {
     __device__ static float load(const __nv_bfloat16 *p) { return __bfloat162float(__ldg(p)); }
     __device__ static void store(__nv_bfloat16 *p, float v) { *p = __float2bfloat16_rn(v); }
 };
 
-// Reference state of the deviation variables at node x:
+// Reference state of the deviation variables at node x (FP32 storage):
 //   scalars  f_ref_i,a = W_i phi_ref_a                      (constant)
 //   fluid    h_ref_i   = h^eq_i(p_ref(x), u = 0)            (Eq. heq)
 //            p_ref(x)  = G . (x - x_c), G the hydrostatic gradient of the mean force
@@ -113,19 +91,25 @@ struct NodeOut {
     float phi[M], ux, uy, pr, s1;
 };
 
-// Scalar equilibrium deviation: f^eq_i - W_i phi_ref = W_i (phi' + 3 phi c_i.u) for the
-// moving directions (Eq. feq-phi, lambda = I, vartheta = 0); the rest direction is phi'
-// minus the moving ones, so the populations' sum is phi' up to one rounding.
+// Scalar equilibrium deviation, Eq. feq-phi with lambda = I, vartheta = 0:
+// f^eq_i - W_i phi_ref = W_i (phi' + 3 phi c_i.u) for the moving directions; the
+// rest direction is phi' minus the moving ones, so the sum is phi' up to one rounding.
+// One moving direction j = 1..4 of the scalar equilibrium deviation
+// W_j (phi' + 3 phi c_j.u); shared by the collision and by the pull of the
+// 16-bit storage so both evaluate it bit for bit the same way.
+__device__ __forceinline__ float feq_dir(int j, float phid, float t3phi, float ux, float uy) {
+    const float cu = (j == 1) ? ux : (j == 2) ? uy : (j == 3) ? -ux : -uy;
+    return kW5 * fmaf(t3phi, cu, phid);
+}
+
 template <int M>
 __device__ __forceinline__ void scalar_equilibrium(const float (&phid)[M], const float (&phi)[M], float ux,
                                                    float uy, float (&feq)[M][5]) {
 #pragma unroll
     for (int b = 0; b < M; ++b) {
         const float t = 3.f * phi[b];
-        feq[b][1] = kW5 * fmaf(t, ux, phid[b]);
-        feq[b][2] = kW5 * fmaf(t, uy, phid[b]);
-        feq[b][3] = kW5 * fmaf(-t, ux, phid[b]);
-        feq[b][4] = kW5 * fmaf(-t, uy, phid[b]);
+#pragma unroll
+        for (int j = 1; j < 5; ++j) feq[b][j] = feq_dir(j, phid[b], t, ux, uy);
         feq[b][0] = phid[b] - ((feq[b][1] + feq[b][3]) + (feq[b][2] + feq[b][4]));
     }
 }
@@ -441,6 +425,254 @@ __global__ void pack_kernel(const LbParams p, int nf, const float *__restrict__ 
     for (int k = 0; k < nf; ++k) dense[k * N + (long long)y * p.nx + x] = mom[k * P + (long long)y * p.pitch + x];
 }
 
+// ---- 16-bit storage: deviations from each node's own equilibrium ----------------
+// For FP16/BF16 the stored value of a post-collision population at node x is
+// d_i(x) = f*_i(x) - f^eq_i(phi(x), u(x)) (h*_i - h^eq_i(p(x), u(x)) for the fluid):
+// the non-equilibrium part plus the source terms, a small number that 16 bits
+// resolve well.  The node's moments (phi, u, p) of the same step are stored in
+// FP32 next to it, and the receiving node rebuilds the population as
+// d_j(src) + f^eq_j(moments(src)).  Both ends evaluate the equilibrium with the
+// same functions on the same stored moments.  The collision itself is the FP32
+// one above with phi_ref = 0 and p_ref = 0 (the host sets them so).
+__device__ __forceinline__ float heq_dir(int j, float pr, float ux, float uy) {
+    return fluid_equilibrium(j, pr, ux, uy, ux * ux + uy * uy);
+}
+
+// Body force at a node from its scalars, F = g (Fbase + sum_a beta_a phi_a); the
+// same float arithmetic as in collide().
+template <int M>
+__device__ __forceinline__ float force_mag(const LbParams &p, const float (&phi)[M]) {
+    float fm = p.Fbase;
+#pragma unroll
+    for (int a = 0; a < M; ++a) fm = fmaf(p.beta[a], phi[a], fm);
+    return fm;
+}
+
+// Reference of a stored post-collision fluid population: h^eq_j(p, u) + F_j / 2.
+// Its first moment u + F/2 is that of h* itself, so the stored deviation holds
+// only the viscous non-equilibrium part.
+__device__ __forceinline__ float href_dir(const LbParams &p, int j, float pr, float ux, float uy, float fm) {
+    return fmaf(0.5f * kA9(j), kC9x(j) * (p.g[0] * fm) + kC9y(j) * (p.g[1] * fm), heq_dir(j, pr, ux, uy));
+}
+
+template <int M, typename T>
+__global__ void __launch_bounds__(256) step_kernel_mr(const LbParams p, const T *__restrict__ in,
+                                                      const float *__restrict__ min, T *__restrict__ out,
+                                                      float *__restrict__ mout, float *__restrict__ sprev) {
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int y = blockIdx.y * blockDim.y + threadIdx.y;
+    if (x >= p.nx || y >= p.ny) return;
+    const long long P = p.plane;
+    int xw = x - 1, xe = x + 1, ys = y - 1, yn = y + 1;
+    const bool cw = xw < 0 && !p.periodic_x, ce = xe >= p.nx && !p.periodic_x;
+    const bool cs = ys < 0 && !p.periodic_y, cn = yn >= p.ny && !p.periodic_y;
+    xw = xw < 0 ? p.nx - 1 : xw;
+    xe = xe >= p.nx ? 0 : xe;
+    ys = ys < 0 ? p.ny - 1 : ys;
+    yn = yn >= p.ny ? 0 : yn;
+    const int r0 = y * p.pitch, rs = ys * p.pitch, rn = yn * p.pitch;
+    const int o0 = r0 + x;
+    const bool fw = p.freeslip[0], fe = p.freeslip[1], fs = p.freeslip[2], fn = p.freeslip[3];
+
+    // Pull sources exactly as in step_kernel (plane j at node offset off).
+    Src sh[9];
+    sh[0] = {0, o0, 0.f};
+    sh[1] = cw ? Src{3, o0, 0.f} : Src{1, r0 + xw, 0.f};
+    sh[2] = cs ? Src{4, o0, 0.f} : Src{2, rs + x, 0.f};
+    sh[3] = ce ? Src{1, o0, 0.f} : Src{3, r0 + xe, 0.f};
+    sh[4] = cn ? Src{2, o0, 0.f} : Src{4, rn + x, 0.f};
+    {
+        Src v{5, rs + xw, 0.f};
+        v = (cw || cs) ? Src{7, o0, 0.f} : v;
+        v = (cw && !cs && fw) ? Src{6, rs + x, 0.f} : v;
+        v = (cs && !cw && fs) ? Src{8, r0 + xw, 0.f} : v;
+        sh[5] = v;
+    }
+    {
+        Src v{6, rs + xe, 0.f};
+        v = (ce || cs) ? Src{8, o0, 0.f} : v;
+        v = (ce && !cs && fe) ? Src{5, rs + x, 0.f} : v;
+        v = (cs && !ce && fs) ? Src{7, r0 + xe, 0.f} : v;
+        sh[6] = v;
+    }
+    {
+        Src v{7, rn + xe, 0.f};
+        v = (ce || cn) ? Src{5, o0, 0.f} : v;
+        v = (ce && !cn && fe) ? Src{8, rn + x, 0.f} : v;
+        v = (cn && !ce && fn) ? Src{6, r0 + xe, 0.f} : v;
+        sh[7] = v;
+    }
+    {
+        Src v{8, rn + xw, 0.f};
+        v = (cw || cn) ? Src{6, o0, 0.f} : v;
+        v = (cw && !cn && fw) ? Src{7, rn + x, 0.f} : v;
+        v = (cn && !cw && fn) ? Src{5, r0 + xw, 0.f} : v;
+        sh[8] = v;
+    }
+    const int sp_[5] = {0, cw ? 3 : 1, cs ? 4 : 2, ce ? 1 : 3, cn ? 2 : 4};
+    const int so_[5] = {o0, cw ? o0 : r0 + xw, cs ? o0 : rs + x, ce ? o0 : r0 + xe, cn ? o0 : rn + x};
+    const int side_[5] = {-1, cw ? 0 : -1, cs ? 2 : -1, ce ? 1 : -1, cn ? 3 : -1};
+
+    // ---- loads: stored deviations and the source nodes' moments (the axis
+    // sources of the fluid and of the scalars are the same nodes)
+    const float *mux = min + M * P, *muy = min + (M + 1) * P, *mpr = min + (M + 2) * P;
+    float h[9], hu[9], hv[9], hp[9], hphi[9][M];
+#pragma unroll
+    for (int i = 0; i < 9; ++i) {
+        h[i] = Store<T>::load(in + sh[i].plane * P + sh[i].off);
+        hu[i] = __ldg(mux + sh[i].off);
+        hv[i] = __ldg(muy + sh[i].off);
+        hp[i] = __ldg(mpr + sh[i].off);
+#pragma unroll
+        for (int a = 0; a < M; ++a) hphi[i][a] = __ldg(min + a * P + sh[i].off);
+    }
+    float f[M][5];
+#pragma unroll
+    for (int i = 0; i < 5; ++i)
+#pragma unroll
+        for (int a = 0; a < M; ++a) f[a][i] = Store<T>::load(in + (9 + 5 * a + sp_[i]) * P + so_[i]);
+    const bool consume = (M >= 2 && p.skind == 2);
+    const float sp1 = consume ? sprev[o0] : 0.f;
+
+    // ---- rebuild the pre-collision populations (deviation variables of collide)
+#pragma unroll
+    for (int i = 0; i < 9; ++i) h[i] += href_dir(p, sh[i].plane, hp[i], hu[i], hv[i], force_mag<M>(p, hphi[i]));
+#pragma unroll
+    for (int a = 0; a < M; ++a) {
+        // rest direction: from this node's own moments, rest by difference
+        const float ph = hphi[0][a], t = 3.f * ph;
+        const float e1 = feq_dir(1, ph, t, hu[0], hv[0]), e2 = feq_dir(2, ph, t, hu[0], hv[0]);
+        const float e3 = feq_dir(3, ph, t, hu[0], hv[0]), e4 = feq_dir(4, ph, t, hu[0], hv[0]);
+        f[a][0] += ph - ((e1 + e3) + (e2 + e4));
+#pragma unroll
+        for (int i = 1; i < 5; ++i) {
+            f[a][i] += feq_dir(sp_[i], hphi[i][a], 3.f * hphi[i][a], hu[i], hv[i]);
+            if (side_[i] >= 0 && ((p.dirichlet[side_[i]] >> a) & 1u)) f[a][i] = p.abb[side_[i]][a] - f[a][i];
+        }
+    }
+
+    NodeOut<M> o;
+    collide<M>(p, f, h, 0.f, sp1, false, o);
+
+    // ---- store deviations from this node's new equilibrium, and its moments
+    float feq[M][5];
+    scalar_equilibrium<M>(o.phi, o.phi, o.ux, o.uy, feq);
+    const float fmo = force_mag<M>(p, o.phi);
+#pragma unroll
+    for (int i = 0; i < 9; ++i) Store<T>::store(out + i * P + o0, h[i] - href_dir(p, i, o.pr, o.ux, o.uy, fmo));
+#pragma unroll
+    for (int a = 0; a < M; ++a)
+#pragma unroll
+        for (int i = 0; i < 5; ++i) Store<T>::store(out + (9 + 5 * a + i) * P + o0, f[a][i] - feq[a][i]);
+    if (consume) sprev[o0] = o.s1;
+    write_moments<M>(mout, P, o0, o);
+}
+
+template <int M, typename T>
+__global__ void init_kernel_mr(const LbParams p, const float *__restrict__ fields, int fpitch, T *__restrict__ out,
+                               float *__restrict__ mout, float *__restrict__ sprev) {
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int y = blockIdx.y * blockDim.y + threadIdx.y;
+    if (x >= p.nx || y >= p.ny) return;
+    const long long P = p.plane, FP = (long long)fpitch * p.ny;
+    const long long o0 = (long long)y * p.pitch + x, i0 = (long long)y * fpitch + x;
+    float phi[M];
+#pragma unroll
+    for (int a = 0; a < M; ++a) phi[a] = fields[a * FP + i0];
+    const float ux = fields[M * FP + i0], uy = fields[(M + 1) * FP + i0], pr = fields[(M + 2) * FP + i0];
+    float fm = p.Fbase;
+#pragma unroll
+    for (int a = 0; a < M; ++a) fm = fmaf(p.beta[a], phi[a], fm);
+    const float Fx = p.g[0] * fm, Fy = p.g[1] * fm;
+    float f[M][5], h[9];
+    scalar_equilibrium<M>(phi, phi, ux, uy, f);
+#pragma unroll
+    for (int i = 0; i < 9; ++i) h[i] = heq_dir(i, pr, ux, uy) - 0.5f * kA9(i) * (kC9x(i) * Fx + kC9y(i) * Fy);
+    NodeOut<M> o;
+    collide<M>(p, f, h, 0.f, 0.f, true, o);
+    float feq[M][5];
+    scalar_equilibrium<M>(o.phi, o.phi, o.ux, o.uy, feq);
+    const float fmo = force_mag<M>(p, o.phi);
+#pragma unroll
+    for (int i = 0; i < 9; ++i) Store<T>::store(out + i * P + o0, h[i] - href_dir(p, i, o.pr, o.ux, o.uy, fmo));
+#pragma unroll
+    for (int a = 0; a < M; ++a)
+#pragma unroll
+        for (int i = 0; i < 5; ++i) Store<T>::store(out + (9 + 5 * a + i) * P + o0, f[a][i] - feq[a][i]);
+    if (M >= 2 && p.skind == 2) sprev[o0] = o.s1;
+    write_moments<M>(mout, P, o0, o);
+}
+
+template <int M, typename T>
+__global__ void export_kernel_mr(const LbParams p, const T *__restrict__ in, const float *__restrict__ min,
+                                 float *__restrict__ dense) {
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int y = blockIdx.y * blockDim.y + threadIdx.y;
+    if (x >= p.nx || y >= p.ny) return;
+    const long long P = p.plane, N = (long long)p.nx * p.ny;
+    const long long o0 = (long long)y * p.pitch + x, d0 = (long long)y * p.nx + x;
+    const float ux = min[M * P + o0], uy = min[(M + 1) * P + o0], pr = min[(M + 2) * P + o0];
+    float phi[M];
+#pragma unroll
+    for (int a = 0; a < M; ++a) phi[a] = min[a * P + o0];
+    const float fm = force_mag<M>(p, phi);
+#pragma unroll
+    for (int i = 0; i < 9; ++i)
+        dense[i * N + d0] = Store<T>::load(in + i * P + o0) + href_dir(p, i, pr, ux, uy, fm) + (i == 0 ? p.rho0 : 0.f);
+    float feq[M][5];
+    scalar_equilibrium<M>(phi, phi, ux, uy, feq);
+#pragma unroll
+    for (int a = 0; a < M; ++a)
+#pragma unroll
+        for (int i = 0; i < 5; ++i)
+            dense[(9 + 5 * a + i) * N + d0] = Store<T>::load(in + (9 + 5 * a + i) * P + o0) + feq[a][i];
+}
+
+template <typename T>
+cudaError_t step_mr_dispatch(const LbParams &p, const void *in, const float *min, void *out, float *mout,
+                             float *sprev, dim3 block, cudaStream_t s) {
+    dim3 grid((p.nx + block.x - 1) / block.x, (p.ny + block.y - 1) / block.y);
+    const T *i = static_cast<const T *>(in);
+    T *o = static_cast<T *>(out);
+    switch (p.m) {
+        case 1: step_kernel_mr<1, T><<<grid, block, 0, s>>>(p, i, min, o, mout, sprev); break;
+        case 2: step_kernel_mr<2, T><<<grid, block, 0, s>>>(p, i, min, o, mout, sprev); break;
+        case 3: step_kernel_mr<3, T><<<grid, block, 0, s>>>(p, i, min, o, mout, sprev); break;
+        case 4: step_kernel_mr<4, T><<<grid, block, 0, s>>>(p, i, min, o, mout, sprev); break;
+        default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t init_mr_dispatch(const LbParams &p, const float *fields, int fpitch, void *out, float *mout,
+                             float *sprev, cudaStream_t s) {
+    dim3 block(128, 2), grid((p.nx + 127) / 128, (p.ny + 1) / 2);
+    T *o = static_cast<T *>(out);
+    switch (p.m) {
+        case 1: init_kernel_mr<1, T><<<grid, block, 0, s>>>(p, fields, fpitch, o, mout, sprev); break;
+        case 2: init_kernel_mr<2, T><<<grid, block, 0, s>>>(p, fields, fpitch, o, mout, sprev); break;
+        case 3: init_kernel_mr<3, T><<<grid, block, 0, s>>>(p, fields, fpitch, o, mout, sprev); break;
+        case 4: init_kernel_mr<4, T><<<grid, block, 0, s>>>(p, fields, fpitch, o, mout, sprev); break;
+        default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t export_mr_dispatch(const LbParams &p, const void *in, const float *min, float *dense, cudaStream_t s) {
+    dim3 block(128, 2), grid((p.nx + 127) / 128, (p.ny + 1) / 2);
+    const T *i = static_cast<const T *>(in);
+    switch (p.m) {
+        case 1: export_kernel_mr<1, T><<<grid, block, 0, s>>>(p, i, min, dense); break;
+        case 2: export_kernel_mr<2, T><<<grid, block, 0, s>>>(p, i, min, dense); break;
+        case 3: export_kernel_mr<3, T><<<grid, block, 0, s>>>(p, i, min, dense); break;
+        case 4: export_kernel_mr<4, T><<<grid, block, 0, s>>>(p, i, min, dense); break;
+        default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
 template <typename T>
 cudaError_t step_dispatch(const LbParams &p, const void *in, void *out, float *sprev, float *mom,
                           dim3 block, cudaStream_t s) {
@@ -513,6 +745,33 @@ cudaError_t launch_export(const LbParams &p, int storage, const void *in, float 
         case kFP32: return export_dispatch<float>(p, in, dense, s);
         case kFP16: return export_dispatch<__half>(p, in, dense, s);
         case kBF16: return export_dispatch<__nv_bfloat16>(p, in, dense, s);
+    }
+    return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_step_mr(const LbParams &p, int storage, const void *in, const float *moments_in, void *out,
+                           float *moments_out, float *sprev, dim3 block, cudaStream_t s) {
+    switch (storage) {
+        case kFP16: return step_mr_dispatch<__half>(p, in, moments_in, out, moments_out, sprev, block, s);
+        case kBF16: return step_mr_dispatch<__nv_bfloat16>(p, in, moments_in, out, moments_out, sprev, block, s);
+    }
+    return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_init_mr(const LbParams &p, int storage, const float *fields, int fields_pitch, void *out,
+                           float *moments_out, float *sprev, cudaStream_t s) {
+    switch (storage) {
+        case kFP16: return init_mr_dispatch<__half>(p, fields, fields_pitch, out, moments_out, sprev, s);
+        case kBF16: return init_mr_dispatch<__nv_bfloat16>(p, fields, fields_pitch, out, moments_out, sprev, s);
+    }
+    return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_export_mr(const LbParams &p, int storage, const void *in, const float *moments, float *dense,
+                             cudaStream_t s) {
+    switch (storage) {
+        case kFP16: return export_mr_dispatch<__half>(p, in, moments, dense, s);
+        case kBF16: return export_mr_dispatch<__nv_bfloat16>(p, in, moments, dense, s);
     }
     return cudaErrorInvalidValue;
 }

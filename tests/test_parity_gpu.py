@@ -119,7 +119,8 @@ def test_ddc_cavity_full_size(cdf, oracle_mod):
 
 
 # ---------------------------------------------------------------------------
-# 16-bit deviation storage (FP16 / BF16 storage, FP32 collision): relative L2 <= 1e-3
+# 16-bit storage (FP16 / BF16 deviations from each node's own equilibrium, FP32
+# moments and collision): relative L2 <= 1e-3
 # ---------------------------------------------------------------------------
 TOL16 = 1e-3
 
@@ -133,14 +134,29 @@ def test_16bit_storage_taylor_green(cdf, oracle_mod, storage):
 
 
 @pytest.mark.parametrize("storage", ["fp16", "bf16"])
+def test_16bit_storage_boundaries_and_restart(cdf, oracle_mod, storage, tmp_path):
+    pb = _rand_problem(37, 21, 3, 21, "mixed", "freeslip_dirichlet")
+    s, o = run_pair(cdf, oracle_mod, pb, 200, storage=storage)
+    assert_parity(s, o, 3, tol=TOL16)
+    a = cdf.Solver(pb, storage=storage)
+    a.step(33)
+    a.save(str(tmp_path / "c.bin"))
+    a.step(40)
+    b = cdf.Solver(pb, storage=storage, init=False)
+    b.load(str(tmp_path / "c.bin"))
+    b.step(40)
+    assert np.array_equal(a.moments(), b.moments())
+
+
+@pytest.mark.parametrize("storage", ["fp16", "bf16"])
 def test_16bit_storage_plume_and_cavity(cdf, oracle_mod, storage):
     pb = I.chemotaxis_plume(128, 64, seed=3)
     s, o = run_pair(cdf, oracle_mod, pb, 2000, storage=storage)
-    errs = assert_parity(s, o, 2, tol=TOL16 if storage == "fp16" else 4e-3, populations=False)
+    errs = assert_parity(s, o, 2, tol=TOL16, populations=False)
     print(storage, "plume 128x64 x 2000:", errs)
     pb = developed_cavity(128)
     s, o = run_pair(cdf, oracle_mod, pb, 2000, storage=storage)
-    errs = assert_parity(s, o, 2, tol=TOL16 if storage == "fp16" else 4e-3, populations=False)
+    errs = assert_parity(s, o, 2, tol=TOL16, populations=False)
     print(storage, "cavity 128^2 x 2000:", errs)
 
 
