@@ -55,6 +55,8 @@ def workload(name: str, rank: int):
         return I.periodic_box(4096, 4096, seed=rank)
     if name == "periodic_2048":
         return I.periodic_box(2048, 2048, seed=rank)
+    if name == "batched_plume_sweep_256":
+        return I.chemotaxis_plume_sweep(256, seed=rank)
     raise SystemExit(f"unknown workload {name}")
 
 
@@ -65,6 +67,8 @@ def describe(name: str) -> str:
         "ddc_cavity_1024": "double-diffusive cavity 1024x1024 with Soret/Dufour (Df=Sr=0.5), Ra=1e5, Pr=0.7, Le=2, N=1",
         "periodic_4096": "periodic 4096x4096 cross-diffusion box (roofline grid)",
         "periodic_2048": "periodic 2048x2048 cross-diffusion box (profiling grid above L2)",
+        "batched_plume_sweep_256": "256 chemotaxis-plume instances, W~U{128..512} x H~U{64..256} (13.2 M nodes), "
+                                   "per-instance chi, D_c, gravity; one persistent launch per 32 steps",
     }[name]
 
 
@@ -79,7 +83,7 @@ def measured_peaks():
 
 def kernel_source_hash() -> str:
     h = hashlib.sha256()
-    for f in ("lb_kernels.cu", "lb_internal.h"):
+    for f in ("lb_kernels.cu", "lb_device.cuh", "lb_internal.h"):
         with open(os.path.join(ROOT, "paper_2101_03055_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -144,6 +148,61 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(self.samples)}
 
 
+class _Single:
+    """Uniform view of the single-lattice solver for the timing loops."""
+
+    def __init__(self, lib, pb, storage):
+        self.lib, self.pb = lib, pb
+        self.s = lib.Solver(pb, storage=storage)
+        info = self.s.info()
+        self.nodes, self.bytes_per_lup, self.storage = pb.nodes, info.bytes_per_lup, info.storage
+        self.block = [info.block_x, info.block_y]
+        self.m = pb.m
+        self.kernel = f"step_kernel<{pb.m},{ {0: 'float', 1: '__half', 2: '__nv_bfloat16'}[info.storage]}>"
+
+    stream = property(lambda self: self.s.stream)
+
+    def step(self, n):
+        self.s.step(n)
+
+    def e2e_step(self, n):
+        pb = self.pb
+        self.s.init_moments(pb.phi0, pb.u0, pb.p0)
+        self.s.step(n)
+        out = np.empty((pb.m + 3, pb.ny, pb.nx))
+        self.lib.cdf_lb_moments(self.s.h, out)
+        return 2 * (pb.m + 3) * pb.nodes * 4
+
+
+class _Batch:
+    def __init__(self, lib, pbs, storage):
+        if storage != "fp32":
+            raise SystemExit("the batched solver stores FP32 populations")
+        self.lib, self.pbs = lib, pbs
+        self.s = lib.BatchSolver(pbs)
+        info = self.s.info()
+        self.nodes, self.bytes_per_lup, self.storage = info.nodes, info.bytes_per_lup, 0
+        self.block = [info.tile_x, info.tile_y]
+        self.m = pbs[0].m
+        self.kernel = f"batch_kernel<{self.m}> (persistent, {info.grid_blocks} CTAs, {info.steps_per_launch} steps/launch)"
+
+    stream = property(lambda self: self.s.stream)
+
+    def step(self, n):
+        self.s.step(n)
+
+    def e2e_step(self, n):
+        for k, pb in enumerate(self.pbs):
+            self.lib.cdf_batch_init_moments(self.s.h, k, pb.phi0, pb.u0, pb.p0)
+        self.s.step(n)
+        nbytes = 0
+        for k, pb in enumerate(self.pbs):
+            out = np.empty((pb.m + 3, pb.ny, pb.nx))
+            self.lib.cdf_batch_moments(self.s.h, k, out)
+            nbytes += 2 * (pb.m + 3) * pb.nodes * 4
+        return nbytes
+
+
 def dist_setup():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -191,7 +250,8 @@ def run_reference(args, world, rank):
         return
     import oracle
     oracle.build()
-    pb = workload(args.workload, 0)
+    wl = workload(args.workload, 0)
+    pb = wl[0] if isinstance(wl, list) else wl  # a batched sweep: its first instance as the sample
     o = oracle.OracleSim(pb)
     per_step_budget = 4.0
     t0 = time.perf_counter()
@@ -247,16 +307,15 @@ def main():
 
     from paper_2101_03055_gb300 import build, lib
     build.build()
-    pb = workload(args.workload, rank)
-    solver = lib.Solver(pb, storage=args.storage)
-    info = solver.info()
-    nodes = pb.nodes
+    wl = workload(args.workload, rank)
+    runner = _Batch(lib, wl, args.storage) if isinstance(wl, list) else _Single(lib, wl, args.storage)
+    nodes = runner.nodes
     K, W, S = args.steps, args.warmup, args.lb_steps
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=device)
-    lib_stream = torch.cuda.ExternalStream(solver.stream, device=device)
+    lib_stream = torch.cuda.ExternalStream(runner.stream, device=device)
 
     for _ in range(W):
-        solver.step(S)
+        runner.step(S)
     torch.cuda.synchronize()
 
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
@@ -268,7 +327,7 @@ def main():
             flush.zero_()  # evict L2 between benchmark steps
             torch.cuda.synchronize()
             ev[k][0].record(lib_stream)
-            solver.step(S)
+            runner.step(S)
             ev[k][1].record(lib_stream)
         torch.cuda.synchronize()
         wall = time.perf_counter() - wall0
@@ -277,29 +336,22 @@ def main():
     t_ms = all_max(kernel_ms, world, device)
     value = world * nodes * S * K / (t_ms * 1e-3) / 1e6
 
-    # e2e: host moments in, K' steps through the C ABI, host moments out
-    phi = np.ascontiguousarray(pb.phi0)
-    u0 = np.ascontiguousarray(pb.u0)
-    p0 = np.ascontiguousarray(pb.p0)
-    out = np.empty((pb.m + 3, pb.ny, pb.nx))
+    # e2e: host moments in, S steps through the C ABI, host moments out
     E = max(1, args.e2e_steps)
-    solver.init_moments(phi, u0, p0)
-    solver.step(S)
-    solver.moments()
+    runner.e2e_step(S)
     barrier(world)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
+    moved = 0
     for _ in range(E):
-        solver.init_moments(phi, u0, p0)
-        solver.step(S)
-        lib.cdf_lb_moments(solver.h, out)
+        moved = runner.e2e_step(S)
     torch.cuda.synchronize()
     e2e_s = all_max(time.perf_counter() - t0, world, device)
     e2e_value = world * nodes * S * E / e2e_s / 1e6
-    stage_bytes = (pb.m + 3) * nodes * 4
+    stage_bytes = moved // 2
 
     peak, peak_kind = measured_peaks()
-    bytes_per_launch = info.bytes_per_lup * nodes
+    bytes_per_launch = runner.bytes_per_lup * nodes
     launch_s = t_ms * 1e-3 / (S * K)
     achieved = bytes_per_launch / launch_s / 1e9
     traffic = recorded_traffic(args.workload)
@@ -313,12 +365,12 @@ def main():
         "metric": "MLUPS (lattice updates per second, millions)",
         "value": value, "unit": "MLUPS", "n_gpus": world, "steps": K, "warmup": W,
         "ms_per_step": t_ms / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": {0: "f32", 1: "f16", 2: "bf16"}[info.storage] + " storage, f32 math",
+        "dtype": {0: "f32", 1: "f16", 2: "bf16"}[runner.storage] + " storage, f32 math",
         "data": "synthetic",
-        "config": {"workload": args.workload, "description": describe(args.workload), "nx": pb.nx, "ny": pb.ny,
-                   "m": pb.m, "lb_steps_per_step": S, "block": [info.block_x, info.block_y],
-                   "l2": "flushed between benchmark steps (256 MiB write); the 21 MB state is L2-resident "
-                         "within a step" if nodes * info.bytes_per_lup < 120e6 else
+        "config": {"workload": args.workload, "description": describe(args.workload), "nodes": nodes,
+                   "m": runner.m, "lb_steps_per_step": S, "block": runner.block,
+                   "l2": "flushed between benchmark steps (256 MiB write); the state is L2-resident "
+                         "within a step" if nodes * runner.bytes_per_lup < 120e6 else
                          "flushed between benchmark steps; working set larger than L2",
                    "parallelism": f"replicas x{world} (independent instances, seed = rank)"},
         "e2e": {"value": e2e_value, "unit": "MLUPS", "h2d_bytes_per_step": stage_bytes,
@@ -326,15 +378,15 @@ def main():
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": traffic,
                      "peak_source": f"{peak_kind} copy bandwidth (MEASURED_PEAKS.json hbm_gbs)",
-                     "bytes_per_lup": info.bytes_per_lup,
-                     "kernel": f"step_kernel<{pb.m},{ {0: 'float', 1: '__half', 2: '__nv_bfloat16'}[info.storage]}>",
+                     "bytes_per_lup": runner.bytes_per_lup, "kernel": runner.kernel,
                      "launch_us": launch_s * 1e6},
         "gpu_launches": S * K,
         "clocks": clk.summary(),
         "wall_s": wall,
     }
     if world == 1 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(workload(args.workload, 0))
+        wl0 = workload(args.workload, 0)
+        line["cpu_baseline"] = cpu_baseline(wl0[0] if isinstance(wl0, list) else wl0)
     print(json.dumps(line), flush=True)
     if world > 1:
         import torch.distributed as dist

@@ -199,6 +199,50 @@ cdf_status cdf_lb_get_info(const cdf_lb *h, cdf_info *out);
  * step kernels run; for timing with events.  Borrowed, do not destroy. */
 void *cdf_lb_stream(const cdf_lb *h);
 
+/* ---- batched solver --------------------------------------------------------
+ * Many independent lattices of uneven size (a parameter sweep) advanced together
+ * by one persistent kernel: work is scheduled as (instance, tile) units and a
+ * bounded grid barrier separates the time steps inside a launch.  Each instance
+ * is the model of cdf_lb_create (same equations, same boundary rules) with its
+ * own grid, D, nu, S, F and boundaries; all share m, the source kind and FP32
+ * population storage. */
+typedef struct cdf_batch cdf_batch;
+typedef struct {
+    int storage;                 /* CDF_FP32 (the only mode of the batched solver) */
+    double rho0;
+    void *cuda_stream;           /* caller's stream, NULL = legacy default */
+    int tile_x, tile_y;          /* tile shape (nodes); 0 = autotuned */
+    int steps_per_launch;        /* time steps per persistent launch; 0 = 32 */
+    double barrier_timeout_s;    /* bound of every grid-barrier wait; 0 = 1 s */
+    int test_unreachable_barrier;/* test hook: the barrier expects one block more than runs,
+                                    so every wait runs out and cdf_batch_step returns CDF_ETIMEOUT */
+} cdf_batch_options;
+typedef struct {
+    int count, m;
+    long long nodes, tiles;
+    int tile_x, tile_y, grid_blocks, steps_per_launch;
+    double bytes_per_lup;
+    long long t;
+} cdf_batch_info;
+
+/* Create `count` lattices; every array argument has `count` entries (phi_ref:
+ * count x m, p_ref_grad: count x 2, the references of cdf_options per instance).
+ * Checks each instance like cdf_lb_create. */
+cdf_status cdf_batch_create(int count, const cdf_grid *grids, int m, const cdf_diffusion *diffusion, const double *nu,
+                            const cdf_source *source, const cdf_force *force, const cdf_boundaries *boundaries,
+                            const double *phi_ref, const double *p_ref_grad, const cdf_batch_options *options,
+                            cdf_batch **out);
+/* Initial state of instance k from host FP64 moments (as cdf_lb_init_moments). */
+cdf_status cdf_batch_init_moments(cdf_batch *b, int k, const double *phi, const double *u, const double *p);
+/* Advance every instance by n steps (Eqs. evolution12, evolution3).  Returns
+ * CDF_ETIMEOUT if a grid-barrier wait ran out (state then undefined). */
+cdf_status cdf_batch_step(cdf_batch *b, long long n);
+/* Moments of instance k at the current time into a host FP64 stack [m+3][ny][nx]. */
+cdf_status cdf_batch_moments(cdf_batch *b, int k, double *host_out);
+cdf_status cdf_batch_get_info(const cdf_batch *b, cdf_batch_info *out);
+void *cdf_batch_stream(const cdf_batch *b);
+void cdf_batch_destroy(cdf_batch *b);
+
 /* Allocation-free FP64 sums over a device moment stack -- the reduction behind
  * cdf_lb_mass and the stop test of cdf_lb_run_to_steady, for callers that
  * cannot allocate device memory once running (real-time loops that forbid

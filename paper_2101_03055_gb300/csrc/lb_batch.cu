@@ -1,0 +1,460 @@
+// Batched solver: many lattices of uneven size advanced by one persistent
+// kernel.  Work is scheduled as (instance, tile) units; a bounded grid barrier
+// separates time steps inside a launch, so one launch advances every instance
+// by `steps_per_launch` steps.  Each node runs the same step_node() as the
+// single-lattice kernel, with its instance's parameters staged in shared memory.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <new>
+#include <tuple>
+#include <vector>
+
+#include "lb_device.cuh"
+
+namespace cdflb {
+namespace {
+
+struct BatchInst {
+    LbParams p;
+    long long pop_off;  // element offset of the instance's planes in a population buffer
+    long long sp_off;   // offset in the S(t-1) buffer
+    long long mom_off;  // offset in the moment buffer
+    int tile_base;      // first tile of the instance
+    int tiles_x;
+};
+
+__device__ __forceinline__ unsigned long long global_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Grid-wide barrier for a co-resident (cooperative) grid.  bar[0] counts
+// arrivals, bar[1] is the generation.  Every wait is bounded: after timeout_ns
+// (or an iteration cap) the block sets *err and the whole grid gives up.
+// Returns false when the barrier failed.
+__device__ bool grid_barrier(unsigned *bar, unsigned expected, unsigned long long timeout_ns, int *err) {
+    __shared__ int ok;
+    __syncthreads();
+    if (threadIdx.x == 0 && threadIdx.y == 0) {
+        ok = 1;
+        volatile unsigned *vgen = bar + 1;
+        volatile int *verr = err;
+        const unsigned gen = *vgen;
+        __threadfence();  // this block's stores of the step before the arrival
+        const unsigned arrived = atomicAdd(bar, 1u) + 1u;
+        if (arrived == expected) {
+            atomicExch(bar, 0u);
+            __threadfence();
+            atomicAdd(bar + 1, 1u);
+        } else {
+            const unsigned long long t0 = global_ns();
+            const unsigned long long cap = timeout_ns / 32ull + (1ull << 20);
+            unsigned long long it = 0;
+            while (*vgen == gen) {
+                if (*verr) { ok = 0; break; }
+                if (++it > cap || ((it & 63ull) == 0 && global_ns() - t0 > timeout_ns)) {
+                    atomicExch(err, 1);
+                    ok = 0;
+                    break;
+                }
+                __nanosleep(32);
+            }
+            __threadfence();
+        }
+    }
+    __syncthreads();
+    return ok != 0;
+}
+
+template <int M>
+__global__ void __launch_bounds__(256) batch_kernel(const BatchInst *__restrict__ inst, const int *__restrict__ tile_inst,
+                                                    int total_tiles, float *buf0, float *buf1, float *sprev,
+                                                    float *moments, int nsteps, int parity0, int moments_last,
+                                                    unsigned *bar, unsigned expected, unsigned long long timeout_ns,
+                                                    int *err) {
+    __shared__ LbParams sp;
+    __shared__ long long s_off[3];
+    __shared__ int s_tile[2];
+    const int tid = threadIdx.y * blockDim.x + threadIdx.x;
+    const int nthreads = blockDim.x * blockDim.y;
+    for (int s = 0; s < nsteps; ++s) {
+        const float *in = ((parity0 + s) & 1) ? buf1 : buf0;
+        float *out = ((parity0 + s) & 1) ? buf0 : buf1;
+        float *mom = (moments_last && s == nsteps - 1) ? moments : nullptr;
+        int cur_inst = -1;
+        for (int t = blockIdx.x; t < total_tiles; t += gridDim.x) {
+            const int k = tile_inst[t];
+            if (k != cur_inst) {  // stage the instance's parameters in shared memory
+                __syncthreads();
+                const int *src = reinterpret_cast<const int *>(&inst[k].p);
+                int *dst = reinterpret_cast<int *>(&sp);
+                for (int w = tid; w < (int)(sizeof(LbParams) / sizeof(int)); w += nthreads) dst[w] = src[w];
+                if (tid == 0) {
+                    s_off[0] = inst[k].pop_off;
+                    s_off[1] = inst[k].sp_off;
+                    s_off[2] = inst[k].mom_off;
+                    s_tile[0] = inst[k].tile_base;
+                    s_tile[1] = inst[k].tiles_x;
+                }
+                __syncthreads();
+                cur_inst = k;
+            }
+            const int lt = t - s_tile[0];
+            const int ty = lt / s_tile[1], tx = lt - ty * s_tile[1];
+            const int x = tx * blockDim.x + threadIdx.x, y = ty * blockDim.y + threadIdx.y;
+            if (x < sp.nx && y < sp.ny)
+                dev::step_node<M, float, true>(sp, x, y, in + s_off[0], out + s_off[0], sprev + s_off[1],
+                                         mom ? mom + s_off[2] : nullptr);
+        }
+        if (s + 1 < nsteps && !grid_barrier(bar, expected, timeout_ns, err)) return;
+    }
+}
+
+thread_local char g_berr[512] = "";
+cdf_status bfail(cdf_status st, const char *msg) {
+    std::snprintf(g_berr, sizeof g_berr, "%s", msg);
+    return report_error(st, msg);
+}
+
+#define BCK(call)                                                                     \
+    do {                                                                              \
+        cudaError_t e_ = (call);                                                      \
+        if (e_ != cudaSuccess) {                                                      \
+            char m_[400];                                                             \
+            std::snprintf(m_, sizeof m_, "%s failed: %s", #call, cudaGetErrorString(e_)); \
+            return bfail(CDF_ECUDA, m_);                                              \
+        }                                                                             \
+    } while (0)
+
+using TuneKey = std::tuple<long long, long long, int, int>;
+std::mutex g_btune_mu;
+std::map<TuneKey, dim3> g_btune;
+
+}  // namespace
+}  // namespace cdflb
+
+using namespace cdflb;
+
+struct cdf_batch {
+    int device = 0;
+    int count = 0, m = 0;
+    std::vector<LbParams> params;
+    std::vector<long long> pop_off, sp_off, mom_off;
+    long long pop_total = 0, sp_total = 0, mom_total = 0, nodes = 0;
+    int sprev_planes = 0;
+    float *buf[2] = {nullptr, nullptr};
+    float *sprev = nullptr, *mom = nullptr, *dense = nullptr, *host_stage = nullptr;
+    size_t stage_floats = 0;
+    BatchInst *d_inst = nullptr;
+    int *d_tile_inst = nullptr;
+    unsigned *d_bar = nullptr;
+    int *d_err = nullptr, *h_err = nullptr;
+    int total_tiles = 0, grid_blocks = 0;
+    dim3 tile{64, 4, 1};
+    int steps_per_launch = 32;
+    unsigned long long timeout_ns = 1000000000ull;
+    int extra_arrivals = 0;
+    cudaStream_t s = nullptr, user = nullptr;
+    cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+    int cur = 0;
+    long long t = 0;
+};
+
+namespace {
+
+void brelease(cdf_batch *b) {
+    if (!b) return;
+    cudaFree(b->buf[0]);
+    cudaFree(b->buf[1]);
+    cudaFree(b->sprev);
+    cudaFree(b->mom);
+    cudaFree(b->dense);
+    cudaFree(b->d_inst);
+    cudaFree(b->d_tile_inst);
+    cudaFree(b->d_bar);
+    cudaFree(b->d_err);
+    if (b->h_err) cudaFreeHost(b->h_err);
+    if (b->host_stage) cudaFreeHost(b->host_stage);
+    if (b->ev_in) cudaEventDestroy(b->ev_in);
+    if (b->ev_out) cudaEventDestroy(b->ev_out);
+    if (b->s) cudaStreamDestroy(b->s);
+    delete b;
+}
+
+// Tile table and instance descriptors for a tile shape; sets the grid size.
+cdf_status setup_tiles(cdf_batch *b, dim3 tile) {
+    std::vector<BatchInst> inst(b->count);
+    std::vector<int> tiles;
+    for (int k = 0; k < b->count; ++k) {
+        const LbParams &p = b->params[k];
+        const int tx = (p.nx + tile.x - 1) / tile.x, ty = (p.ny + tile.y - 1) / tile.y;
+        inst[k].p = p;
+        inst[k].pop_off = b->pop_off[k];
+        inst[k].sp_off = b->sp_off[k];
+        inst[k].mom_off = b->mom_off[k];
+        inst[k].tile_base = (int)tiles.size();
+        inst[k].tiles_x = tx;
+        for (int i = 0; i < tx * ty; ++i) tiles.push_back(k);
+    }
+    cudaFree(b->d_tile_inst);
+    b->d_tile_inst = nullptr;
+    BCK(cudaMalloc(&b->d_tile_inst, tiles.size() * sizeof(int)));
+    BCK(cudaMemcpy(b->d_inst, inst.data(), inst.size() * sizeof(BatchInst), cudaMemcpyHostToDevice));
+    BCK(cudaMemcpy(b->d_tile_inst, tiles.data(), tiles.size() * sizeof(int), cudaMemcpyHostToDevice));
+    b->total_tiles = (int)tiles.size();
+    b->tile = tile;
+    int per_sm = 0, sms = 0;
+    void (*kern)(const BatchInst *, const int *, int, float *, float *, float *, float *, int, int, int, unsigned *,
+                 unsigned, unsigned long long, int *) = nullptr;
+    switch (b->m) {
+        case 1: kern = batch_kernel<1>; break;
+        case 2: kern = batch_kernel<2>; break;
+        case 3: kern = batch_kernel<3>; break;
+        default: kern = batch_kernel<4>; break;
+    }
+    BCK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, tile.x * tile.y, 0));
+    BCK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, b->device));
+    b->grid_blocks = std::max(1, std::min(per_sm * sms, b->total_tiles));
+    return CDF_OK;
+}
+
+cdf_status launch_batch(cdf_batch *b, int nsteps, bool moments_last) {
+    BCK(cudaMemsetAsync(b->d_err, 0, sizeof(int), b->s));
+    BCK(cudaMemsetAsync(b->d_bar, 0, 2 * sizeof(unsigned), b->s));
+    unsigned expected = (unsigned)b->grid_blocks + (unsigned)b->extra_arrivals;
+    int parity = b->cur, ml = moments_last ? 1 : 0;
+    void *args[] = {&b->d_inst, &b->d_tile_inst, &b->total_tiles, &b->buf[0], &b->buf[1], &b->sprev, &b->mom,
+                    &nsteps, &parity, &ml, &b->d_bar, &expected, &b->timeout_ns, &b->d_err};
+    const void *kern = nullptr;
+    switch (b->m) {
+        case 1: kern = (const void *)batch_kernel<1>; break;
+        case 2: kern = (const void *)batch_kernel<2>; break;
+        case 3: kern = (const void *)batch_kernel<3>; break;
+        default: kern = (const void *)batch_kernel<4>; break;
+    }
+    BCK(cudaLaunchCooperativeKernel(kern, dim3(b->grid_blocks), b->tile, args, 0, b->s));
+    BCK(cudaMemcpyAsync(b->h_err, b->d_err, sizeof(int), cudaMemcpyDeviceToHost, b->s));
+    if (nsteps & 1) b->cur ^= 1;
+    b->t += nsteps;
+    return CDF_OK;
+}
+
+cdf_status check_err(cdf_batch *b) {
+    if (*b->h_err) return bfail(CDF_ETIMEOUT, "grid barrier wait timed out; the batch state is undefined");
+    return CDF_OK;
+}
+
+cdf_status bautotune(cdf_batch *b) {
+    TuneKey key{b->nodes, (long long)b->count, b->m, b->params[0].chemotaxis};
+    {
+        std::lock_guard<std::mutex> lk(g_btune_mu);
+        auto it = g_btune.find(key);
+        if (it != g_btune.end()) return setup_tiles(b, it->second);
+    }
+    const dim3 cands[] = {dim3(32, 4), dim3(32, 8), dim3(64, 2), dim3(64, 4), dim3(128, 1), dim3(128, 2)};
+    cudaEvent_t e0, e1;
+    BCK(cudaEventCreate(&e0));
+    BCK(cudaEventCreate(&e1));
+    float best = 1e30f;
+    dim3 best_t = cands[0];
+    const int steps = b->nodes > (1 << 22) ? 4 : 16;
+    for (const dim3 &c : cands) {
+        cdf_status st = setup_tiles(b, c);
+        if (st != CDF_OK) return st;
+        if ((st = launch_batch(b, 2, false)) != CDF_OK) return st;
+        BCK(cudaEventRecord(e0, b->s));
+        if ((st = launch_batch(b, steps, false)) != CDF_OK) return st;
+        BCK(cudaEventRecord(e1, b->s));
+        BCK(cudaEventSynchronize(e1));
+        if ((st = check_err(b)) != CDF_OK) return st;
+        float ms = 0;
+        BCK(cudaEventElapsedTime(&ms, e0, e1));
+        if (ms < best) { best = ms; best_t = c; }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    b->t = 0;
+    b->cur = 0;
+    {
+        std::lock_guard<std::mutex> lk(g_btune_mu);
+        g_btune[key] = best_t;
+    }
+    return setup_tiles(b, best_t);
+}
+
+}  // namespace
+
+extern "C" {
+
+cdf_status cdf_batch_create(int count, const cdf_grid *grids, int m, const cdf_diffusion *diffusion, const double *nu,
+                            const cdf_source *source, const cdf_force *force, const cdf_boundaries *boundaries,
+                            const double *phi_ref, const double *p_ref_grad, const cdf_batch_options *opt,
+                            cdf_batch **out) {
+    if (!out) return bfail(CDF_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (count < 1 || !grids || !diffusion || !nu || !source || !force || !boundaries || !phi_ref || !p_ref_grad || !opt)
+        return bfail(CDF_EINVAL, "NULL argument or count < 1");
+    if (opt->storage != CDF_FP32) return bfail(CDF_EINVAL, "the batched solver stores FP32 populations only");
+    if (!(opt->rho0 > 0.0)) return bfail(CDF_EINVAL, "rho0 must be positive");
+    if (opt->tile_x != 0 || opt->tile_y != 0) {
+        if (opt->tile_x <= 0 || opt->tile_y <= 0 || opt->tile_x * opt->tile_y > 256 || opt->tile_x % 32 != 0)
+            return bfail(CDF_EINVAL, "tile must be a multiple of 32 wide and at most 256 nodes");
+    }
+    if (opt->steps_per_launch < 0 || opt->barrier_timeout_s < 0) return bfail(CDF_EINVAL, "bad launch options");
+    cdf_batch *b = new (std::nothrow) cdf_batch;
+    if (!b) return bfail(CDF_ENOMEM, "host allocation failed");
+    b->count = count;
+    b->m = m;
+    b->params.resize(count);
+    int sprev_planes = -1;
+    for (int k = 0; k < count; ++k) {
+        const int pitch = grids[k].nx >= 1 ? (grids[k].nx + 31) / 32 * 32 : 0;
+        cdf_status st = build_params(&grids[k], m, &diffusion[k], nu[k], &source[k], &force[k], &boundaries[k], false,
+                                     opt->rho0, phi_ref + (size_t)k * m, p_ref_grad + 2 * (size_t)k, pitch,
+                                     &b->params[k]);
+        if (st != CDF_OK) {
+            delete b;
+            return st;
+        }
+        const int spp = source[k].kind == CDF_S_CONSUMPTION ? 1 : 0;
+        if (sprev_planes >= 0 && spp != sprev_planes) {
+            delete b;
+            return bfail(CDF_EINVAL, "all instances must use the same source kind");
+        }
+        sprev_planes = spp;
+        b->pop_off.push_back(b->pop_total);
+        b->sp_off.push_back(b->sp_total);
+        b->mom_off.push_back(b->mom_total);
+        const long long plane = b->params[k].plane;
+        b->pop_total += (long long)(9 + 5 * m) * plane;
+        b->sp_total += plane;
+        b->mom_total += (long long)(m + 3) * plane;
+        b->nodes += (long long)grids[k].nx * grids[k].ny;
+        b->stage_floats = std::max(b->stage_floats, (size_t)(m + 3) * grids[k].nx * grids[k].ny);
+    }
+    b->sprev_planes = sprev_planes;
+    b->steps_per_launch = opt->steps_per_launch > 0 ? opt->steps_per_launch : 32;
+    b->timeout_ns = opt->barrier_timeout_s > 0 ? (unsigned long long)(opt->barrier_timeout_s * 1e9) : 1000000000ull;
+    b->extra_arrivals = opt->test_unreachable_barrier ? 1 : 0;
+    b->user = static_cast<cudaStream_t>(opt->cuda_stream);
+    if (cudaGetDevice(&b->device) != cudaSuccess) { delete b; return bfail(CDF_ECUDA, "no CUDA device"); }
+    bool ok = cudaMalloc(&b->buf[0], b->pop_total * 4) == cudaSuccess &&
+              cudaMalloc(&b->buf[1], b->pop_total * 4) == cudaSuccess &&
+              cudaMalloc(&b->sprev, b->sp_total * 4) == cudaSuccess &&
+              cudaMalloc(&b->mom, b->mom_total * 4) == cudaSuccess &&
+              cudaMalloc(&b->dense, b->stage_floats * 4) == cudaSuccess &&
+              cudaMalloc(&b->d_inst, count * sizeof(BatchInst)) == cudaSuccess &&
+              cudaMalloc(&b->d_bar, 2 * sizeof(unsigned)) == cudaSuccess &&
+              cudaMalloc(&b->d_err, sizeof(int)) == cudaSuccess &&
+              cudaMallocHost(&b->h_err, sizeof(int)) == cudaSuccess &&
+              cudaMallocHost(&b->host_stage, b->stage_floats * 4) == cudaSuccess;
+    if (!ok) {
+        cudaGetLastError();
+        brelease(b);
+        return bfail(CDF_ENOMEM, "device allocation failed");
+    }
+    if (cudaStreamCreateWithFlags(&b->s, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&b->ev_in, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&b->ev_out, cudaEventDisableTiming) != cudaSuccess ||
+        cudaMemset(b->buf[0], 0, b->pop_total * 4) != cudaSuccess || cudaMemset(b->buf[1], 0, b->pop_total * 4) != cudaSuccess ||
+        cudaMemset(b->sprev, 0, b->sp_total * 4) != cudaSuccess || cudaMemset(b->mom, 0, b->mom_total * 4) != cudaSuccess ||
+        cudaMemset(b->d_bar, 0, 2 * sizeof(unsigned)) != cudaSuccess) {
+        brelease(b);
+        return bfail(CDF_ECUDA, "stream / memory set-up failed");
+    }
+    cdf_status st;
+    if (opt->tile_x > 0) st = setup_tiles(b, dim3(opt->tile_x, opt->tile_y));
+    else if (b->extra_arrivals) st = setup_tiles(b, dim3(64, 4));
+    else st = bautotune(b);
+    if (st == CDF_OK && cudaStreamSynchronize(b->s) != cudaSuccess) st = bfail(CDF_ECUDA, "set-up failed");
+    if (st != CDF_OK) {
+        brelease(b);
+        return st;
+    }
+    *out = b;
+    return CDF_OK;
+}
+
+void cdf_batch_destroy(cdf_batch *b) {
+    if (!b) return;
+    cudaStreamSynchronize(b->s);
+    brelease(b);
+}
+
+cdf_status cdf_batch_init_moments(cdf_batch *b, int k, const double *phi, const double *u, const double *p) {
+    if (!b || !phi || !u || k < 0 || k >= b->count) return bfail(CDF_EINVAL, "bad argument");
+    const LbParams &P = b->params[k];
+    const size_t n = (size_t)P.nx * P.ny;
+    BCK(cudaStreamSynchronize(b->s));  // the staging buffer may still feed a copy
+    float *h = b->host_stage;
+    for (int a = 0; a < b->m; ++a)
+        for (size_t i = 0; i < n; ++i) h[a * n + i] = (float)phi[a * n + i];
+    for (size_t i = 0; i < 2 * n; ++i) h[b->m * n + i] = (float)u[i];
+    for (size_t i = 0; i < n; ++i) h[(b->m + 2) * n + i] = p ? (float)p[i] : 0.f;
+    BCK(cudaEventRecord(b->ev_in, b->user));
+    BCK(cudaStreamWaitEvent(b->s, b->ev_in, 0));
+    BCK(cudaMemcpyAsync(b->dense, h, (size_t)(b->m + 3) * n * 4, cudaMemcpyHostToDevice, b->s));
+    BCK(launch_init(P, kFP32, b->dense, P.nx, b->buf[b->cur] + b->pop_off[k], b->sprev + b->sp_off[k],
+                    b->mom + b->mom_off[k], b->s));
+    BCK(cudaEventRecord(b->ev_out, b->s));
+    BCK(cudaStreamWaitEvent(b->user, b->ev_out, 0));
+    return CDF_OK;
+}
+
+cdf_status cdf_batch_step(cdf_batch *b, long long n) {
+    if (!b || n < 0) return bfail(CDF_EINVAL, "bad argument");
+    if (n == 0) return CDF_OK;
+    BCK(cudaEventRecord(b->ev_in, b->user));
+    BCK(cudaStreamWaitEvent(b->s, b->ev_in, 0));
+    while (n > 0) {
+        const int k = (int)std::min<long long>(n, b->steps_per_launch);
+        cdf_status st = launch_batch(b, k, n == k);
+        if (st != CDF_OK) return st;
+        n -= k;
+    }
+    BCK(cudaStreamSynchronize(b->s));  // the barrier's error flag is read on the host
+    cdf_status st = check_err(b);
+    if (st != CDF_OK) return st;
+    BCK(cudaEventRecord(b->ev_out, b->s));
+    BCK(cudaStreamWaitEvent(b->user, b->ev_out, 0));
+    return CDF_OK;
+}
+
+cdf_status cdf_batch_moments(cdf_batch *b, int k, double *host_out) {
+    if (!b || !host_out || k < 0 || k >= b->count) return bfail(CDF_EINVAL, "bad argument");
+    const LbParams &P = b->params[k];
+    const size_t n = (size_t)P.nx * P.ny * (b->m + 3);
+    BCK(cudaEventRecord(b->ev_in, b->user));
+    BCK(cudaStreamWaitEvent(b->s, b->ev_in, 0));
+    BCK(launch_pack_moments(P, b->mom + b->mom_off[k], b->dense, b->s));
+    BCK(cudaMemcpyAsync(b->host_stage, b->dense, n * 4, cudaMemcpyDeviceToHost, b->s));
+    BCK(cudaStreamSynchronize(b->s));
+    for (size_t i = 0; i < n; ++i) host_out[i] = b->host_stage[i];
+    return CDF_OK;
+}
+
+cdf_status cdf_batch_get_info(const cdf_batch *b, cdf_batch_info *out) {
+    if (!b || !out) return bfail(CDF_EINVAL, "NULL argument");
+    out->count = b->count;
+    out->m = b->m;
+    out->nodes = b->nodes;
+    out->tiles = b->total_tiles;
+    out->tile_x = (int)b->tile.x;
+    out->tile_y = (int)b->tile.y;
+    out->grid_blocks = b->grid_blocks;
+    out->steps_per_launch = b->steps_per_launch;
+    out->bytes_per_lup = 2.0 * (9 + 5 * b->m) * 4.0 + 8.0 * b->sprev_planes;
+    out->t = b->t;
+    return CDF_OK;
+}
+
+void *cdf_batch_stream(const cdf_batch *b) { return b ? static_cast<void *>(b->s) : nullptr; }
+
+}  // extern "C"

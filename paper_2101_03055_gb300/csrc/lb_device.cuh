@@ -1,0 +1,360 @@
+// Device-side building blocks of the fused lattice Boltzmann step (Zhan, Chai &
+// Shi, arXiv:2101.03055): FP32 lattice constants, storage types, equilibria, the
+// node collision and the node update of the pull scheme.  Included by the
+// single-lattice kernels (lb_kernels.cu) and the batched kernel (lb_batch.cu).
+#pragma once
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
+#include "lb_internal.h"
+
+namespace cdflb {
+namespace dev {
+
+// Lattice constants of Eq. D2Q5 and Eq. D2Q9 in FP32.  Rounding 1/3, 1/6,
+// 1/9, 1/36 independently would break the discrete conservation identities by
+// a few 1e-8 per collision, and because scalar mass, fluid momentum and the
+// mean pressure are neutral (conserved) modes the error would pile up linearly
+// over the run.  The constants below are chosen so that, for the rounded
+// values themselves, sum W = 1 (scalars), 3 sum W c_x^2 = 1 and
+// 3 sum_{i!=0} W = kC (fluid) hold exactly; they differ from the exact
+// weights by at most 1.2e-7 relative.
+//   kW5  = fl(1/6)                W_1..4 of D2Q5;   kW50 = 1 - 4 kW5
+//   kA1  = 3 W_1..4 of D2Q9 ~ 1/3; kA5 = 3 W_5..8 ~ 1/12;  2 kA1 + 4 kA5 = 1
+//   kC   = 4 kA1 + 4 kA5 ~ 5/3 (= (1 - W_0)/cs^2);  kQ = 3/2 - kC/2 ~ 2/3
+constexpr float kW5 = 0x1.555556p-3f;
+constexpr float kW50 = 0x1.555554p-2f;
+constexpr float kA1 = 0x1.555554p-2f;
+constexpr float kA5 = 0x1.555558p-4f;
+constexpr float kC = 0x1.aaaaaap+0f;
+constexpr float kQ = 0x1.555556p-1f;
+__host__ __device__ constexpr float kWs(int i) { return i == 0 ? kW50 : kW5; }
+__host__ __device__ constexpr float kA9(int i) { return i == 0 ? 0.f : (i < 5 ? kA1 : kA5); }
+__host__ __device__ constexpr int kC5x(int i) { return i == 1 ? 1 : (i == 3 ? -1 : 0); }
+__host__ __device__ constexpr int kC5y(int i) { return i == 2 ? 1 : (i == 4 ? -1 : 0); }
+__host__ __device__ constexpr int kC9x(int i) { return (i == 1 || i == 5 || i == 8) ? 1 : ((i == 3 || i == 6 || i == 7) ? -1 : 0); }
+__host__ __device__ constexpr int kC9y(int i) { return (i == 2 || i == 5 || i == 6) ? 1 : ((i == 4 || i == 7 || i == 8) ? -1 : 0); }
+
+// ---- storage types ---------------------------------------------------------------
+// Populations are stored as deviations from a reference state (below) in FP32,
+// FP16 or BF16; every collision is computed in FP32.
+template <typename T> struct Store;
+template <> struct Store<float> {
+    __device__ static float load(const float *p) { return __ldg(p); }
+    __device__ static void store(float *p, float v) { *p = v; }
+};
+// FP16 holds the small deviations scaled by 2^12 (exactly invertible), which
+// moves them out of FP16's subnormal range: normal numbers then cover
+// |d| in [1.5e-8, 16].
+constexpr float kHalfScale = 4096.f, kHalfUnscale = 1.f / 4096.f;
+template <> struct Store<__half> {
+    __device__ static float load(const __half *p) { return __half2float(__ldg(p)) * kHalfUnscale; }
+    __device__ static void store(__half *p, float v) { *p = __float2half_rn(v * kHalfScale); }
+};
+template <> struct Store<__nv_bfloat16> {
+    __device__ static float load(const __nv_bfloat16 *p) { return __bfloat162float(__ldg(p)); }
+    __device__ static void store(__nv_bfloat16 *p, float v) { *p = __float2bfloat16_rn(v); }
+};
+
+// Population load of the step.  A kernel that runs one step per launch reads
+// data that is read-only for the launch (non-coherent path); the persistent
+// batched kernel reads buffers that other blocks wrote earlier in the same
+// launch, so it loads through L2 (.cg), which is coherent across SMs.
+template <typename T, bool kL2>
+__device__ __forceinline__ float load_pop(const T *p) {
+    if constexpr (kL2) return __ldcg(p);
+    else return Store<T>::load(p);
+}
+
+// Reference state of the deviation variables at node x (FP32 storage):
+//   scalars  f_ref_i,a = W_i phi_ref_a                      (constant)
+//   fluid    h_ref_i   = h^eq_i(p_ref(x), u = 0)            (Eq. heq)
+//            p_ref(x)  = G . (x - x_c), G the hydrostatic gradient of the mean force
+// The collision below is written in these variables; it is the same update as
+// Eqs. evolution12/evolution3 term by term, with phi = phi_ref + sum_i f'_i,
+// u = sum_i c_i h'_i + F/2 (sum_i c_i h_ref_i = 0) and p = p_ref(x) + p'.
+__device__ __forceinline__ float pref_at(const LbParams &p, int x, int y) {
+    return p.gref[0] * ((float)x - p.xc) + p.gref[1] * ((float)y - p.yc);
+}
+
+__device__ __forceinline__ float cutoff(const LbParams &p, float c) {
+    // r(c): step (Sec. 3.1.3) or regularised (Sec. 3.1.2)
+    if (p.r_regularised) {
+        float d = c - p.c_star;
+        return 0.5f * (1.f + d * rsqrtf(d * d + p.eps2));
+    }
+    return c >= p.c_star ? 1.f : 0.f;
+}
+
+template <int M>
+struct NodeOut {
+    float phi[M], ux, uy, pr, s1;
+};
+
+// Scalar equilibrium deviation, Eq. feq-phi with lambda = I, vartheta = 0:
+// f^eq_i - W_i phi_ref = W_i (phi' + 3 phi c_i.u) for the moving directions; the
+// rest direction is phi' minus the moving ones, so the sum is phi' up to one rounding.
+// One moving direction j = 1..4 of the scalar equilibrium deviation
+// W_j (phi' + 3 phi c_j.u); shared by the collision and by the pull of the
+// 16-bit storage so both evaluate it bit for bit the same way.
+__device__ __forceinline__ float feq_dir(int j, float phid, float t3phi, float ux, float uy) {
+    const float cu = (j == 1) ? ux : (j == 2) ? uy : (j == 3) ? -ux : -uy;
+    return kW5 * fmaf(t3phi, cu, phid);
+}
+
+template <int M>
+__device__ __forceinline__ void scalar_equilibrium(const float (&phid)[M], const float (&phi)[M], float ux,
+                                                   float uy, float (&feq)[M][5]) {
+#pragma unroll
+    for (int b = 0; b < M; ++b) {
+        const float t = 3.f * phi[b];
+#pragma unroll
+        for (int j = 1; j < 5; ++j) feq[b][j] = feq_dir(j, phid[b], t, ux, uy);
+        feq[b][0] = phid[b] - ((feq[b][1] + feq[b][3]) + (feq[b][2] + feq[b][4]));
+    }
+}
+
+// Fluid equilibrium deviation (Eq. heq): h^eq_i(p, u) - h^eq_i(p_ref, 0)
+//   = kA_i (p' + c_i.u + 1.5 (c_i.u)^2 - 0.5 u.u)  (i != 0),  -kC p' - kQ u.u  (i = 0).
+__device__ __forceinline__ float fluid_equilibrium(int i, float prd, float ux, float uy, float usq) {
+    if (i == 0) return -kC * prd - kQ * usq;
+    const float cu = kC9x(i) * ux + kC9y(i) * uy;
+    return kA9(i) * ((prd + cu) + fmaf(1.5f * cu, cu, -0.5f * usq));
+}
+
+// Collision of one node (Eqs. evolution12, evolution3) in deviation variables.
+// f, h: pre-collision deviations, overwritten by the post-collision ones.  prx:
+// p_ref at the node.  sp1: S_1(t-1) of the consumption closure; `first` uses
+// S(t-1) = S(t) (initialisation).
+template <int M>
+__device__ __forceinline__ void collide(const LbParams &p, float (&f)[M][5], float (&h)[9], float prx,
+                                        float sp1, bool first, NodeOut<M> &o) {
+    // Eq. sum-phi and the closures of Sec. 3
+    float phid[M], phi[M];
+#pragma unroll
+    for (int a = 0; a < M; ++a) {
+        phid[a] = ((f[a][0] + f[a][1]) + (f[a][2] + f[a][3])) + f[a][4];
+        phi[a] = p.phi_ref[a] + phid[a];
+    }
+    float r = 0.f;
+    if (M >= 2 && (p.chemotaxis || p.skind == 2)) r = cutoff(p, phi[M >= 2 ? 1 : 0]);
+    float S[M], Sp[M];
+#pragma unroll
+    for (int a = 0; a < M; ++a) {
+        S[a] = (p.skind == 1) ? p.S[a] : 0.f;
+        Sp[a] = S[a];
+    }
+    if (M >= 2 && p.skind == 2) {
+        S[1] = -p.k * phi[0] * r;
+        Sp[1] = first ? S[1] : sp1;
+    }
+    float fm = p.Fbase;
+#pragma unroll
+    for (int a = 0; a < M; ++a) fm = fmaf(p.beta[a], phi[a], fm);
+    const float Fx = p.g[0] * fm, Fy = p.g[1] * fm;
+
+    // Eq. sum-u and Eq. sum-p (varphi = 0):
+    // p = cs^2/(1 - W0) [sum_{i!=0} h_i - W0 u.u / (2 cs^2)] = (sum_{i!=0} h_i - kQ u.u) / kC
+    const float jx = (h[1] - h[3]) + (h[5] - h[6]) + (h[8] - h[7]);
+    const float jy = (h[2] - h[4]) + (h[5] - h[8]) + (h[6] - h[7]);
+    const float ux = fmaf(0.5f, Fx, jx), uy = fmaf(0.5f, Fy, jy);
+    const float usq = ux * ux + uy * uy;
+    const float snr = ((h[1] + h[2]) + (h[3] + h[4])) + ((h[5] + h[6]) + (h[7] + h[8]));
+    const float prd = (snr - kQ * usq) / kC;
+
+    // Eq. omega-D.  Constant D: omega from the host.  Chemotaxis: omega^-1 =
+    // B + delta e_0 e_1^T with delta = -3 chi phi_0 r, inverted by Sherman-Morrison.
+    float om[M][M];
+#pragma unroll
+    for (int a = 0; a < M; ++a)
+#pragma unroll
+        for (int b = 0; b < M; ++b) om[a][b] = p.omega[a * M + b];
+    if (M >= 2 && p.chemotaxis) {
+        const float delta = -p.chi3 * phi[0] * r;
+        const float den = 1.f / fmaf(delta, om[M >= 2 ? 1 : 0][0], 1.f);
+        float col0[M], row1[M];
+#pragma unroll
+        for (int a = 0; a < M; ++a) { col0[a] = om[a][0]; row1[a] = om[M >= 2 ? 1 : 0][a]; }
+#pragma unroll
+        for (int a = 0; a < M; ++a)
+#pragma unroll
+            for (int b = 0; b < M; ++b) om[a][b] -= delta * den * col0[a] * row1[b];
+    }
+
+    // Eq. Gi: G_{i,a} = 3 W_i c_i . J_a,  J_a = sum_b (delta_ab - omega_ab / 2)(u S_b + phi_b F)
+    float Jx[M], Jy[M];
+#pragma unroll
+    for (int a = 0; a < M; ++a) {
+        float jxa = 0.f, jya = 0.f;
+#pragma unroll
+        for (int b = 0; b < M; ++b) {
+            const float c = (a == b ? 1.f : 0.f) - 0.5f * om[a][b];
+            jxa = fmaf(c, fmaf(ux, S[b], phi[b] * Fx), jxa);
+            jya = fmaf(c, fmaf(uy, S[b], phi[b] * Fy), jya);
+        }
+        Jx[a] = jxa;
+        Jy[a] = jya;
+    }
+
+    // Eq. evolution12: f*_i,a = f_i,a - sum_b omega_ab (f_i,b - f^eq_i,b) + W_i S_a
+    // + (W_i S_a - W_i S_a(t-1)) / 2 + G_i,a
+    float feq[M][5];
+    scalar_equilibrium<M>(phid, phi, ux, uy, feq);
+#pragma unroll
+    for (int i = 0; i < 5; ++i) {
+        float neq[M];
+#pragma unroll
+        for (int b = 0; b < M; ++b) neq[b] = f[b][i] - feq[b][i];
+#pragma unroll
+        for (int a = 0; a < M; ++a) {
+            float coll = 0.f;
+#pragma unroll
+            for (int b = 0; b < M; ++b) coll = fmaf(om[a][b], neq[b], coll);
+            const float src = kWs(i) * fmaf(1.5f, S[a], -0.5f * Sp[a]);
+            const float G = (i == 0) ? 0.f : 3.f * kW5 * (kC5x(i) * Jx[a] + kC5y(i) * Jy[a]);
+            f[a][i] = (f[a][i] - coll) + (src + G);
+        }
+    }
+
+    // Eq. evolution3 with Eq. force (varphi = 0): F_i = 3 W_i c_i.F, weighted by (1 - omega_f / 2).
+    const float wf = p.omega_f, fw = 1.f - 0.5f * wf;
+#pragma unroll
+    for (int i = 0; i < 9; ++i) {
+        const float heq = fluid_equilibrium(i, prd, ux, uy, usq);
+        const float Fi = kA9(i) * (kC9x(i) * Fx + kC9y(i) * Fy);
+        h[i] = fmaf(-wf, h[i] - heq, h[i]) + fw * Fi;
+    }
+#pragma unroll
+    for (int a = 0; a < M; ++a) o.phi[a] = phi[a];
+    o.ux = ux;
+    o.uy = uy;
+    o.pr = prx + prd;
+    o.s1 = (M >= 2) ? S[M >= 2 ? 1 : 0] : 0.f;
+}
+
+template <int M>
+__device__ __forceinline__ void write_moments(float *moments, long long P, long long o0, const NodeOut<M> &o) {
+#pragma unroll
+    for (int a = 0; a < M; ++a) moments[a * P + o0] = o.phi[a];
+    moments[M * P + o0] = o.ux;
+    moments[(M + 1) * P + o0] = o.uy;
+    moments[(M + 2) * P + o0] = o.pr;
+}
+
+template <int M, typename T>
+__device__ __forceinline__ void store_node(T *out, long long P, long long o0, const float (&f)[M][5],
+                                           const float (&h)[9]) {
+#pragma unroll
+    for (int i = 0; i < 9; ++i) Store<T>::store(out + i * P + o0, h[i]);
+#pragma unroll
+    for (int a = 0; a < M; ++a)
+#pragma unroll
+        for (int i = 0; i < 5; ++i) Store<T>::store(out + (9 + 5 * a + i) * P + o0, f[a][i]);
+}
+
+// Pull source of one fluid direction: plane j at in-plane offset `off`, with the
+// change of the pressure reference between source and node, kA_j G.(src - x).
+struct Src {
+    int plane, off;
+    float shift;
+};
+
+// ---- the fused step ------------------------------------------------------------
+// One node of the fused step (x < nx, y < ny): pull, moments, collision, store.
+template <int M, typename T, bool kL2 = false>
+__device__ __forceinline__ void step_node(const LbParams &p, int x, int y, const T *__restrict__ in,
+                                          T *__restrict__ out, float *__restrict__ sprev,
+                                          float *__restrict__ moments) {
+    const long long P = p.plane;
+
+    // Neighbour coordinates (periodic wrap) and wall crossings of the pull links.
+    int xw = x - 1, xe = x + 1, ys = y - 1, yn = y + 1;
+    const bool cw = xw < 0 && !p.periodic_x, ce = xe >= p.nx && !p.periodic_x;
+    const bool cs = ys < 0 && !p.periodic_y, cn = yn >= p.ny && !p.periodic_y;
+    xw = xw < 0 ? p.nx - 1 : xw;
+    xe = xe >= p.nx ? 0 : xe;
+    ys = ys < 0 ? p.ny - 1 : ys;
+    yn = yn >= p.ny ? 0 : yn;
+    const int r0 = y * p.pitch, rs = ys * p.pitch, rn = yn * p.pitch;
+    const int o0 = r0 + x;
+    const float ax = kA1 * p.gref[0], ay = kA1 * p.gref[1];  // axis-link shifts
+    const float dx5 = kA5 * p.gref[0], dy5 = kA5 * p.gref[1];  // diagonal-link shifts
+    const bool fw = p.freeslip[0], fe = p.freeslip[1], fs = p.freeslip[2], fn = p.freeslip[3];
+
+    // Fluid, D2Q9: h_i(x) = h*_j(src).  Regular link: j = i, src = x - c_i.  No-slip
+    // wall: bounce-back j = opp(i), src = x.  Free-slip wall: the specular image j
+    // from the neighbour along the wall.  Corner links: bounce-back.  Every
+    // source is chosen by selects, so all loads issue before any arithmetic.
+    Src sh[9];
+    sh[0] = {0, o0, 0.f};
+    sh[1] = cw ? Src{3, o0, 0.f} : Src{1, r0 + xw, -ax};
+    sh[2] = cs ? Src{4, o0, 0.f} : Src{2, rs + x, -ay};
+    sh[3] = ce ? Src{1, o0, 0.f} : Src{3, r0 + xe, ax};
+    sh[4] = cn ? Src{2, o0, 0.f} : Src{4, rn + x, ay};
+    {   // (1,1) from (x-1, y-1)
+        Src v{5, rs + xw, -dx5 - dy5};
+        v = (cw || cs) ? Src{7, o0, 0.f} : v;
+        v = (cw && !cs && fw) ? Src{6, rs + x, -dy5} : v;
+        v = (cs && !cw && fs) ? Src{8, r0 + xw, -dx5} : v;
+        sh[5] = v;
+    }
+    {   // (-1,1) from (x+1, y-1)
+        Src v{6, rs + xe, dx5 - dy5};
+        v = (ce || cs) ? Src{8, o0, 0.f} : v;
+        v = (ce && !cs && fe) ? Src{5, rs + x, -dy5} : v;
+        v = (cs && !ce && fs) ? Src{7, r0 + xe, dx5} : v;
+        sh[6] = v;
+    }
+    {   // (-1,-1) from (x+1, y+1)
+        Src v{7, rn + xe, dx5 + dy5};
+        v = (ce || cn) ? Src{5, o0, 0.f} : v;
+        v = (ce && !cn && fe) ? Src{8, rn + x, dy5} : v;
+        v = (cn && !ce && fn) ? Src{6, r0 + xe, dx5} : v;
+        sh[7] = v;
+    }
+    {   // (1,-1) from (x-1, y+1)
+        Src v{8, rn + xw, -dx5 + dy5};
+        v = (cw || cn) ? Src{6, o0, 0.f} : v;
+        v = (cw && !cn && fw) ? Src{7, rn + x, dy5} : v;
+        v = (cn && !cw && fn) ? Src{5, r0 + xw, -dx5} : v;
+        sh[8] = v;
+    }
+    // Scalars, D2Q5: bounce-back f*_opp(i)(x) (no flux) or anti-bounce-back
+    // -f*_opp(i)(x) + 2 W_i phi_w (Dirichlet); in deviations the latter is
+    // -f'*_opp(i)(x) + 2 W_i (phi_w - phi_ref).
+    const int sp_[5] = {0, cw ? 3 : 1, cs ? 4 : 2, ce ? 1 : 3, cn ? 2 : 4};
+    const int so_[5] = {o0, cw ? o0 : r0 + xw, cs ? o0 : rs + x, ce ? o0 : r0 + xe, cn ? o0 : rn + x};
+    const int side_[5] = {-1, cw ? 0 : -1, cs ? 2 : -1, ce ? 1 : -1, cn ? 3 : -1};
+
+    // ---- loads
+    float h[9], f[M][5];
+#pragma unroll
+    for (int i = 0; i < 9; ++i) h[i] = load_pop<T, kL2>(in + sh[i].plane * P + sh[i].off);
+#pragma unroll
+    for (int a = 0; a < M; ++a)
+#pragma unroll
+        for (int i = 0; i < 5; ++i) f[a][i] = load_pop<T, kL2>(in + (9 + 5 * a + sp_[i]) * P + so_[i]);
+    const bool consume = (M >= 2 && p.skind == 2);
+    const float sp1 = consume ? (kL2 ? __ldcg(sprev + o0) : sprev[o0]) : 0.f;
+
+    // ---- boundary values
+#pragma unroll
+    for (int i = 0; i < 9; ++i) h[i] += sh[i].shift;
+#pragma unroll
+    for (int i = 1; i < 5; ++i) {
+        if (side_[i] >= 0) {
+#pragma unroll
+            for (int a = 0; a < M; ++a)
+                if ((p.dirichlet[side_[i]] >> a) & 1u) f[a][i] = p.abb[side_[i]][a] - f[a][i];
+        }
+    }
+
+    NodeOut<M> o;
+    collide<M>(p, f, h, pref_at(p, x, y), sp1, false, o);
+    store_node<M, T>(out, P, o0, f, h);
+    if (consume) sprev[o0] = o.s1;
+    if (moments) write_moments<M>(moments, P, o0, o);
+}
+
+}  // namespace dev
+}  // namespace cdflb

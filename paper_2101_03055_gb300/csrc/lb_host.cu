@@ -300,17 +300,14 @@ cdf_status cdflb::report_error(cdf_status status, const char *msg) {
     return status;
 }
 
-extern "C" {
-
-const char *cdf_lb_last_error(void) { return g_err; }
-
-cdf_status cdf_lb_create(const cdf_grid *grid, int m, const cdf_diffusion *dif, double nu,
-                         const cdf_source *src, const cdf_force *frc, const cdf_boundaries *bc,
-                         const cdf_options *opt, cdf_lb **out) {
-    g_err[0] = 0;
-    if (!out) return fail(CDF_EINVAL, "out is NULL");
-    *out = nullptr;
-    if (!grid || !dif || !src || !frc || !bc || !opt) return fail(CDF_EINVAL, "NULL argument");
+// Checks one lattice's parameter set and scales it for the kernels (shared by
+// the single-lattice and the batched solver).  node_reference: 16-bit storage,
+// whose deviations are taken from each node's own equilibrium.
+cdf_status cdflb::build_params(const cdf_grid *grid, int m, const cdf_diffusion *dif, double nu,
+                               const cdf_source *src, const cdf_force *frc, const cdf_boundaries *bc,
+                               bool node_reference, double rho0, const double *phi_ref, const double *p_ref_grad,
+                               int pitch, LbParams *out) {
+    if (!grid || !dif || !src || !frc || !bc || !phi_ref || !p_ref_grad || !out) return fail(CDF_EINVAL, "NULL argument");
     if (grid->nx < 1 || grid->ny < 1) return fail(CDF_EINVAL, "grid must be at least 1 x 1");
     if ((long long)(grid->nx + 63) * grid->ny >= (1LL << 31) - 1)
         return fail(CDF_EINVAL, "grid too large: one padded plane must hold fewer than 2^31 elements");
@@ -321,11 +318,9 @@ cdf_status cdf_lb_create(const cdf_grid *grid, int m, const cdf_diffusion *dif, 
         return fail(CDF_EINVAL, "bad source kind");
     if ((dif->kind == CDF_D_CHEMOTAXIS || src->kind == CDF_S_CONSUMPTION) && m < 2)
         return fail(CDF_EINVAL, "chemotaxis / consumption closures need m >= 2");
-    if (opt->storage < CDF_FP32 || opt->storage > CDF_BF16_DEV) return fail(CDF_EINVAL, "bad storage");
-    if (!(opt->rho0 > 0.0)) return fail(CDF_EINVAL, "rho0 must be positive");
     for (int a = 0; a < m; ++a)
-        if (!std::isfinite(opt->phi_ref[a])) return fail(CDF_EINVAL, "phi_ref must be finite");
-    if (!std::isfinite(opt->p_ref_grad[0]) || !std::isfinite(opt->p_ref_grad[1]))
+        if (!std::isfinite(phi_ref[a])) return fail(CDF_EINVAL, "phi_ref must be finite");
+    if (!std::isfinite(p_ref_grad[0]) || !std::isfinite(p_ref_grad[1]))
         return fail(CDF_EINVAL, "p_ref_grad must be finite");
     cdf_status st;
     if ((st = check_side_pair(bc->west, bc->east, "x")) != CDF_OK) return st;
@@ -355,31 +350,12 @@ cdf_status cdf_lb_create(const cdf_grid *grid, int m, const cdf_diffusion *dif, 
                 return fail(CDF_EINVAL, "Dirichlet value on a periodic side");
         }
     }
-    if (opt->block_x != 0 || opt->block_y != 0) {
-        if (opt->block_x <= 0 || opt->block_y <= 0 || opt->block_x * opt->block_y > 256 || opt->block_x % 32 != 0)
-            return fail(CDF_EINVAL, "block must be a multiple of 32 wide and at most 256 threads");
-    }
-
-    cdf_lb *h = new (std::nothrow) cdf_lb;
-    if (!h) return fail(CDF_ENOMEM, "host allocation failed");
-    if (cudaGetDevice(&h->device) != cudaSuccess) { delete h; return fail(CDF_ECUDA, "no CUDA device"); }
-    h->nx = grid->nx;
-    h->ny = grid->ny;
-    h->m = m;
-    h->storage = opt->storage;
-    const int align = opt->storage == CDF_FP32 ? 32 : 64;  // 128-byte rows
-    h->pitch = (grid->nx + align - 1) / align * align;
-    h->plane = (long long)h->pitch * h->ny;
-    h->planes = 9 + 5 * m;
-    h->sprev_planes = src->kind == CDF_S_CONSUMPTION ? 1 : 0;
-    h->mr = opt->storage != CDF_FP32;
-    h->user = static_cast<cudaStream_t>(opt->cuda_stream);
-
-    LbParams &P = h->P;
-    P.nx = h->nx;
-    P.ny = h->ny;
-    P.pitch = h->pitch;
-    P.plane = h->plane;
+    if (!(rho0 > 0.0)) return fail(CDF_EINVAL, "rho0 must be positive");
+    LbParams &P = *out;
+    P.nx = grid->nx;
+    P.ny = grid->ny;
+    P.pitch = pitch;
+    P.plane = (long long)pitch * grid->ny;
     P.m = m;
     for (int i = 0; i < m * m; ++i) P.omega[i] = (float)Binv[i];
     P.omega_f = (float)(1.0 / (3.0 * nu + 0.5));
@@ -397,20 +373,20 @@ cdf_status cdf_lb_create(const cdf_grid *grid, int m, const cdf_diffusion *dif, 
     for (int a = 0; a < m; ++a) {
         P.beta[a] = (float)frc->beta[a];
         Fbase -= frc->beta[a] * frc->phi_ref[a];
-        P.phi_ref[a] = (float)opt->phi_ref[a];
+        P.phi_ref[a] = (float)phi_ref[a];
     }
     P.Fbase = (float)Fbase;
     // Reference pressure gradient of the fluid deviations; a linear reference
     // cannot wrap around a periodic axis, so it is used along walled axes only.
-    P.gref[0] = bc->west.kind == CDF_BC_WALL ? (float)opt->p_ref_grad[0] : 0.f;
-    P.gref[1] = bc->south.kind == CDF_BC_WALL ? (float)opt->p_ref_grad[1] : 0.f;
-    if (h->mr) {  // 16-bit storage references each node's own equilibrium instead
+    P.gref[0] = bc->west.kind == CDF_BC_WALL ? (float)p_ref_grad[0] : 0.f;
+    P.gref[1] = bc->south.kind == CDF_BC_WALL ? (float)p_ref_grad[1] : 0.f;
+    if (node_reference) {  // 16-bit storage references each node's own equilibrium instead
         for (int a = 0; a < m; ++a) P.phi_ref[a] = 0.f;
         P.gref[0] = P.gref[1] = 0.f;
     }
     P.xc = 0.5f * (float)(grid->nx - 1);
     P.yc = 0.5f * (float)(grid->ny - 1);
-    P.rho0 = (float)opt->rho0;
+    P.rho0 = (float)rho0;
     P.periodic_x = bc->west.kind == CDF_BC_PERIODIC;
     P.periodic_y = bc->south.kind == CDF_BC_PERIODIC;
     for (int s = 0; s < 4; ++s) {
@@ -423,6 +399,49 @@ cdf_status cdf_lb_create(const cdf_grid *grid, int m, const cdf_diffusion *dif, 
             }
         }
     }
+
+    return CDF_OK;
+}
+
+extern "C" {
+
+const char *cdf_lb_last_error(void) { return g_err; }
+
+cdf_status cdf_lb_create(const cdf_grid *grid, int m, const cdf_diffusion *dif, double nu,
+                         const cdf_source *src, const cdf_force *frc, const cdf_boundaries *bc,
+                         const cdf_options *opt, cdf_lb **out) {
+    g_err[0] = 0;
+    if (!out) return fail(CDF_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (!grid || !dif || !src || !frc || !bc || !opt) return fail(CDF_EINVAL, "NULL argument");
+    if (opt->storage < CDF_FP32 || opt->storage > CDF_BF16_DEV) return fail(CDF_EINVAL, "bad storage");
+    if (!(opt->rho0 > 0.0)) return fail(CDF_EINVAL, "rho0 must be positive");
+    LbParams P0{};
+    const int align = opt->storage == CDF_FP32 ? 32 : 64;  // 128-byte rows
+    const int pitch = grid->nx >= 1 ? (grid->nx + align - 1) / align * align : 0;
+    cdf_status st = cdflb::build_params(grid, m, dif, nu, src, frc, bc, opt->storage != CDF_FP32, opt->rho0,
+                                        opt->phi_ref, opt->p_ref_grad, pitch, &P0);
+    if (st != CDF_OK) return st;
+    if (opt->block_x != 0 || opt->block_y != 0) {
+        if (opt->block_x <= 0 || opt->block_y <= 0 || opt->block_x * opt->block_y > 256 || opt->block_x % 32 != 0)
+            return fail(CDF_EINVAL, "block must be a multiple of 32 wide and at most 256 threads");
+    }
+
+    cdf_lb *h = new (std::nothrow) cdf_lb;
+    if (!h) return fail(CDF_ENOMEM, "host allocation failed");
+    if (cudaGetDevice(&h->device) != cudaSuccess) { delete h; return fail(CDF_ECUDA, "no CUDA device"); }
+    h->nx = grid->nx;
+    h->ny = grid->ny;
+    h->m = m;
+    h->storage = opt->storage;
+    h->pitch = pitch;
+    h->plane = (long long)h->pitch * h->ny;
+    h->planes = 9 + 5 * m;
+    h->sprev_planes = src->kind == CDF_S_CONSUMPTION ? 1 : 0;
+    h->mr = opt->storage != CDF_FP32;
+    h->user = static_cast<cudaStream_t>(opt->cuda_stream);
+
+    h->P = P0;
 
     DeviceGuard g(h->device);
     const size_t esz = elem_size(h->storage);

@@ -75,6 +75,11 @@ int reduce_quantities(int m);
 cudaError_t launch_reduce(const float *mom_new, const float *mom_old, int nx, int ny, int pitch,
                           long long plane, int m, double *partials, double *out, cudaStream_t s);
 
+// Checks one lattice's parameter set and fills the kernel parameters.
+cdf_status build_params(const cdf_grid *grid, int m, const cdf_diffusion *dif, double nu, const cdf_source *src,
+                        const cdf_force *frc, const cdf_boundaries *bc, bool node_reference, double rho0,
+                        const double *phi_ref, const double *p_ref_grad, int pitch, LbParams *out);
+
 // Sets the calling thread's cdf_lb_last_error() message and returns `status`.
 cdf_status report_error(cdf_status status, const char *msg);
 

@@ -201,6 +201,25 @@ def chemotaxis_plume(nx: int = 512, ny: int = 256, seed: int = 0, chi: float = 0
                    north=top, phi0=phi0, steps=steps)
 
 
+def chemotaxis_plume_sweep(count: int = 256, seed: int = 0, wmin: int = 128, wmax: int = 512,
+                           hmin: int = 64, hmax: int = 256, steps: int = 50_000):
+    """Parameter sweep of plume instances of uneven size: W ~ U{wmin..wmax},
+    H ~ U{hmin..hmax}, chi ~ U[0.1, 0.5], D_c ~ U[0.1, 0.3], gravity scale ~
+    U[0.5, 2]; instance k draws its parameters from counters 8k..8k+4 of `seed`
+    and its initial noise from seed 1000 seed + k + 1."""
+    out = []
+    for k in range(count):
+        u = uniform(seed, np.arange(8 * k, 8 * k + 5))
+        nx = wmin + int(u[0] * (wmax - wmin + 1))
+        ny = hmin + int(u[1] * (hmax - hmin + 1))
+        chi = 0.1 + 0.4 * u[2]
+        Dc = 0.1 + 0.2 * u[3]
+        gs = 0.5 + 1.5 * u[4]
+        out.append(chemotaxis_plume(nx, ny, seed=1000 * seed + k + 1, chi=chi, Dc=Dc, gravity_scale=gs,
+                                    steps=steps).replace(name=f"chemotaxis_plume_sweep[{k}]"))
+    return out
+
+
 def ddc_lattice_parameters(L: int, Ra: float, Pr: float, Ma: float = 0.1):
     """Lattice mapping of the dimensionless DDC system (Sec. 3.2): buoyancy velocity
     U = Ma cs, alpha = U L / sqrt(Ra Pr), nu = Pr alpha, buoyancy g = U^2 / L."""

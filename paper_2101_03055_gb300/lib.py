@@ -72,6 +72,19 @@ class cdf_info(ctypes.Structure):
                 ("t", ctypes.c_longlong)]
 
 
+class cdf_batch_options(ctypes.Structure):
+    _fields_ = [("storage", ctypes.c_int), ("rho0", ctypes.c_double), ("cuda_stream", ctypes.c_void_p),
+                ("tile_x", ctypes.c_int), ("tile_y", ctypes.c_int), ("steps_per_launch", ctypes.c_int),
+                ("barrier_timeout_s", ctypes.c_double), ("test_unreachable_barrier", ctypes.c_int)]
+
+
+class cdf_batch_info(ctypes.Structure):
+    _fields_ = [("count", ctypes.c_int), ("m", ctypes.c_int), ("nodes", ctypes.c_longlong),
+                ("tiles", ctypes.c_longlong), ("tile_x", ctypes.c_int), ("tile_y", ctypes.c_int),
+                ("grid_blocks", ctypes.c_int), ("steps_per_launch", ctypes.c_int),
+                ("bytes_per_lup", ctypes.c_double), ("t", ctypes.c_longlong)]
+
+
 _DP = ctypes.POINTER(ctypes.c_double)
 _FP = ctypes.c_void_p
 _H = ctypes.c_void_p
@@ -100,6 +113,16 @@ SIGNATURES = {
     "cdf_lb_last_error": (ctypes.c_char_p, []),
     "cdf_moment_sums_static": (ctypes.c_int, [_FP, _FP, ctypes.c_int, ctypes.c_int, ctypes.c_int, _FP,
                                               ctypes.c_void_p]),
+    "cdf_batch_create": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(cdf_grid), ctypes.c_int,
+                                        ctypes.POINTER(cdf_diffusion), _DP, ctypes.POINTER(cdf_source),
+                                        ctypes.POINTER(cdf_force), ctypes.POINTER(cdf_boundaries), _DP, _DP,
+                                        ctypes.POINTER(cdf_batch_options), ctypes.POINTER(ctypes.c_void_p)]),
+    "cdf_batch_init_moments": (ctypes.c_int, [_H, ctypes.c_int, _DP, _DP, _DP]),
+    "cdf_batch_step": (ctypes.c_int, [_H, ctypes.c_longlong]),
+    "cdf_batch_moments": (ctypes.c_int, [_H, ctypes.c_int, _DP]),
+    "cdf_batch_get_info": (ctypes.c_int, [_H, ctypes.POINTER(cdf_batch_info)]),
+    "cdf_batch_stream": (ctypes.c_void_p, [_H]),
+    "cdf_batch_destroy": (None, [_H]),
 }
 
 
@@ -356,3 +379,104 @@ class Solver:
     @property
     def t(self) -> int:
         return self.info().t
+
+
+# ---- batched solver -------------------------------------------------------------------
+def cdf_batch_create(count, grids, m, diffusion, nu, source, force, boundaries, phi_ref, p_ref_grad, options):
+    h = ctypes.c_void_p()
+    _check(load().cdf_batch_create(count, grids, m, diffusion, nu.ctypes.data_as(_DP), source, force, boundaries,
+                                   phi_ref.ctypes.data_as(_DP), p_ref_grad.ctypes.data_as(_DP),
+                                   ctypes.byref(options), ctypes.byref(h)))
+    return h
+
+
+def cdf_batch_init_moments(h, k, phi, u, p=None):
+    _check(load().cdf_batch_init_moments(h, k, _dptr(phi), _dptr(u), None if p is None else _dptr(p)))
+
+
+def cdf_batch_step(h, n):
+    _check(load().cdf_batch_step(h, int(n)))
+
+
+def cdf_batch_moments(h, k, out):
+    _check(load().cdf_batch_moments(h, k, _dptr(out)))
+
+
+def cdf_batch_get_info(h) -> cdf_batch_info:
+    info = cdf_batch_info()
+    _check(load().cdf_batch_get_info(h, ctypes.byref(info)))
+    return info
+
+
+def cdf_batch_stream(h) -> int:
+    return load().cdf_batch_stream(h) or 0
+
+
+def cdf_batch_destroy(h):
+    load().cdf_batch_destroy(h)
+
+
+class BatchSolver:
+    """Many lattices (same m and source kind, FP32) advanced by the persistent batched kernel."""
+
+    def __init__(self, problems, stream: int = 0, tile=None, steps_per_launch: int = 0, barrier_timeout_s: float = 0.0,
+                 test_unreachable_barrier: bool = False, init: bool = True):
+        self.problems = list(problems)
+        n = len(self.problems)
+        m = self.problems[0].m
+        grids = (cdf_grid * n)()
+        dif = (cdf_diffusion * n)()
+        src = (cdf_source * n)()
+        frc = (cdf_force * n)()
+        bcs = (cdf_boundaries * n)()
+        nu = np.empty(n)
+        phi_ref = np.empty((n, m))
+        grad = np.empty((n, 2))
+        for k, pb in enumerate(self.problems):
+            if pb.m != m:
+                raise ValueError("all instances need the same m")
+            g, d, s_, f, b, o = structs_from_problem(pb)
+            grids[k], dif[k], src[k], frc[k], bcs[k] = g, d, s_, f, b
+            nu[k] = pb.nu
+            phi_ref[k] = default_phi_ref(pb)
+            grad[k] = default_p_ref_grad(pb)
+        opt = cdf_batch_options()
+        opt.storage, opt.rho0, opt.cuda_stream = 0, self.problems[0].rho0, stream or None
+        if tile is not None:
+            opt.tile_x, opt.tile_y = tile
+        opt.steps_per_launch = steps_per_launch
+        opt.barrier_timeout_s = barrier_timeout_s
+        opt.test_unreachable_barrier = int(test_unreachable_barrier)
+        self.h = cdf_batch_create(n, grids, m, dif, nu, src, frc, bcs, phi_ref, grad, opt)
+        self.m = m
+        if init:
+            for k, pb in enumerate(self.problems):
+                cdf_batch_init_moments(self.h, k, np.ascontiguousarray(pb.phi0, np.float64),
+                                       np.ascontiguousarray(pb.u0, np.float64), np.ascontiguousarray(pb.p0, np.float64))
+
+    def close(self):
+        if getattr(self, "h", None):
+            cdf_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def step(self, n: int = 1):
+        cdf_batch_step(self.h, n)
+
+    def moments(self, k: int) -> np.ndarray:
+        pb = self.problems[k]
+        out = np.empty((self.m + 3, pb.ny, pb.nx))
+        cdf_batch_moments(self.h, k, out)
+        return out
+
+    def info(self) -> cdf_batch_info:
+        return cdf_batch_get_info(self.h)
+
+    @property
+    def stream(self) -> int:
+        return cdf_batch_stream(self.h)
