@@ -57,6 +57,8 @@ def workload(name: str, rank: int):
         return I.periodic_box(2048, 2048, seed=rank)
     if name == "batched_plume_sweep_256":
         return I.chemotaxis_plume_sweep(256, seed=rank)
+    if name == "batched_plume_sweep_64":
+        return I.chemotaxis_plume_sweep(64, seed=rank)
     raise SystemExit(f"unknown workload {name}")
 
 
@@ -67,6 +69,7 @@ def describe(name: str) -> str:
         "ddc_cavity_1024": "double-diffusive cavity 1024x1024 with Soret/Dufour (Df=Sr=0.5), Ra=1e5, Pr=0.7, Le=2, N=1",
         "periodic_4096": "periodic 4096x4096 cross-diffusion box (roofline grid)",
         "periodic_2048": "periodic 2048x2048 cross-diffusion box (profiling grid above L2)",
+        "batched_plume_sweep_64": "64 chemotaxis-plume instances of the 256-instance sweep (profiling size)",
         "batched_plume_sweep_256": "256 chemotaxis-plume instances, W~U{128..512} x H~U{64..256} (13.2 M nodes), "
                                    "per-instance chi, D_c, gravity; one persistent launch per 32 steps",
     }[name]

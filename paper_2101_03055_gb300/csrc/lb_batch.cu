@@ -74,7 +74,7 @@ __device__ bool grid_barrier(unsigned *bar, unsigned expected, unsigned long lon
 }
 
 template <int M>
-__global__ void __launch_bounds__(256) batch_kernel(const BatchInst *__restrict__ inst, const int *__restrict__ tile_inst,
+__global__ void __launch_bounds__(256, 4) batch_kernel(const BatchInst *__restrict__ inst, const int *__restrict__ tile_inst,
                                                     int total_tiles, float *buf0, float *buf1, float *sprev,
                                                     float *moments, int nsteps, int parity0, int moments_last,
                                                     unsigned *bar, unsigned expected, unsigned long long timeout_ns,
@@ -258,7 +258,8 @@ cdf_status bautotune(cdf_batch *b) {
         auto it = g_btune.find(key);
         if (it != g_btune.end()) return setup_tiles(b, it->second);
     }
-    const dim3 cands[] = {dim3(32, 4), dim3(32, 8), dim3(64, 2), dim3(64, 4), dim3(128, 1), dim3(128, 2)};
+    const dim3 cands[] = {dim3(32, 4), dim3(32, 8), dim3(64, 2), dim3(64, 4), dim3(128, 1), dim3(128, 2),
+                          dim3(256, 1)};
     cudaEvent_t e0, e1;
     BCK(cudaEventCreate(&e0));
     BCK(cudaEventCreate(&e1));

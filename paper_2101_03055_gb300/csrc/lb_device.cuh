@@ -57,12 +57,13 @@ template <> struct Store<__nv_bfloat16> {
 };
 
 // Population load of the step.  A kernel that runs one step per launch reads
-// data that is read-only for the launch (non-coherent path); the persistent
+// data that is read-only for the launch (non-coherent path).  The persistent
 // batched kernel reads buffers that other blocks wrote earlier in the same
-// launch, so it loads through L2 (.cg), which is coherent across SMs.
-template <typename T, bool kL2>
+// launch, which the non-coherent path may not do: it uses ordinary cached
+// loads (ld.global.ca), made current by the acquire fence of its grid barrier.
+template <typename T, bool kCoherent>
 __device__ __forceinline__ float load_pop(const T *p) {
-    if constexpr (kL2) return __ldcg(p);
+    if constexpr (kCoherent) return __ldca(p);
     else return Store<T>::load(p);
 }
 
@@ -335,7 +336,7 @@ __device__ __forceinline__ void step_node(const LbParams &p, int x, int y, const
 #pragma unroll
         for (int i = 0; i < 5; ++i) f[a][i] = load_pop<T, kL2>(in + (9 + 5 * a + sp_[i]) * P + so_[i]);
     const bool consume = (M >= 2 && p.skind == 2);
-    const float sp1 = consume ? (kL2 ? __ldcg(sprev + o0) : sprev[o0]) : 0.f;
+    const float sp1 = consume ? (kL2 ? __ldca(sprev + o0) : sprev[o0]) : 0.f;
 
     // ---- boundary values
 #pragma unroll
