@@ -214,6 +214,7 @@ def dist_setup():
 
 
 def all_max(x: float, world: int, device) -> float:
+    """Max of x over ranks (the whole job is as slow as its slowest rank)."""
     if world == 1:
         return x
     import torch
@@ -221,6 +222,12 @@ def all_max(x: float, world: int, device) -> float:
     t = torch.tensor([x], dtype=torch.float64, device=device)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
+
+
+def job_mlups(nodes_per_rank: int, lb_steps: int, bench_steps: int, world: int, max_ms: float) -> float:
+    """Whole-job throughput: every rank advances its own instance (weak scaling),
+    so the job processed world x nodes x steps lattice updates in the slowest rank's time."""
+    return world * nodes_per_rank * lb_steps * bench_steps / (max_ms * 1e-3) / 1e6
 
 
 def barrier(world: int):
@@ -337,7 +344,7 @@ def main():
     barrier(world)
     kernel_ms = sum(a.elapsed_time(b) for a, b in ev)
     t_ms = all_max(kernel_ms, world, device)
-    value = world * nodes * S * K / (t_ms * 1e-3) / 1e6
+    value = job_mlups(nodes, S, K, world, t_ms)
 
     # e2e: host moments in, S steps through the C ABI, host moments out
     E = max(1, args.e2e_steps)

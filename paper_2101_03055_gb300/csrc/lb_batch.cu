@@ -89,7 +89,11 @@ __global__ void __launch_bounds__(256, 4) batch_kernel(const BatchInst *__restri
         float *out = ((parity0 + s) & 1) ? buf0 : buf1;
         float *mom = (moments_last && s == nsteps - 1) ? moments : nullptr;
         int cur_inst = -1;
-        for (int t = blockIdx.x; t < total_tiles; t += gridDim.x) {
+        // Each block takes a contiguous range of tiles: long runs of one instance
+        // (parameters staged once) and neighbouring tiles whose halos are still in L1.
+        const int t_begin = (int)((long long)total_tiles * blockIdx.x / gridDim.x);
+        const int t_end = (int)((long long)total_tiles * (blockIdx.x + 1) / gridDim.x);
+        for (int t = t_begin; t < t_end; ++t) {
             const int k = tile_inst[t];
             if (k != cur_inst) {  // stage the instance's parameters in shared memory
                 __syncthreads();
