@@ -187,7 +187,13 @@ class _Batch:
         self.nodes, self.bytes_per_lup, self.storage = info.nodes, info.bytes_per_lup, 0
         self.block = [info.tile_x, info.tile_y]
         self.m = pbs[0].m
-        self.kernel = f"batch_kernel<{self.m}> (persistent, {info.grid_blocks} CTAs, {info.steps_per_launch} steps/launch)"
+        if info.mode == 1:
+            self.block = [info.chain_block_x, info.chain_block_y]
+            self.kernel = (f"step_kernel<{self.m},float> x {info.count} instance chains "
+                           f"(graph of 32 steps over a 32-stream pool)")
+        else:
+            self.kernel = (f"batch_kernel<{self.m}> (persistent, {info.grid_blocks} CTAs, "
+                           f"{info.steps_per_launch} steps/launch)")
 
     stream = property(lambda self: self.s.stream)
 

@@ -200,9 +200,12 @@ cdf_status cdf_lb_get_info(const cdf_lb *h, cdf_info *out);
 void *cdf_lb_stream(const cdf_lb *h);
 
 /* ---- batched solver --------------------------------------------------------
- * Many independent lattices of uneven size (a parameter sweep) advanced together
- * by one persistent kernel: work is scheduled as (instance, tile) units and a
- * bounded grid barrier separates the time steps inside a launch.  Each instance
+ * Many independent lattices of uneven size (a parameter sweep) advanced together,
+ * in one of two modes chosen by measurement: a persistent kernel that schedules
+ * (instance, tile) units with a bounded grid barrier between the time steps of
+ * a launch, or one CUDA graph of per-instance chains of step kernels fanned out
+ * over a stream pool (the instances are independent, so the chains need no
+ * barrier).  Each instance
  * is the model of cdf_lb_create (same equations, same boundary rules) with its
  * own grid, D, nu, S, F and boundaries; all share m, the source kind and FP32
  * population storage. */
@@ -216,6 +219,9 @@ typedef struct {
     double barrier_timeout_s;    /* bound of every grid-barrier wait; 0 = 1 s */
     int test_unreachable_barrier;/* test hook: the barrier expects one block more than runs,
                                     so every wait runs out and cdf_batch_step returns CDF_ETIMEOUT */
+    int mode;                    /* with tile_x > 0: 0 = persistent kernel (tile = tile shape),
+                                    1 = graph of per-instance kernel chains (tile = CTA shape);
+                                    with tile_x = 0 the autotuner measures both and picks */
 } cdf_batch_options;
 typedef struct {
     int count, m;
@@ -223,6 +229,8 @@ typedef struct {
     int tile_x, tile_y, grid_blocks, steps_per_launch;
     double bytes_per_lup;
     long long t;
+    int mode;                    /* 0 persistent kernel, 1 graph of per-instance chains */
+    int chain_block_x, chain_block_y;
 } cdf_batch_info;
 
 /* Create `count` lattices; every array argument has `count` entries (phi_ref:

@@ -169,12 +169,28 @@ struct cdf_batch {
     cudaEvent_t ev_in = nullptr, ev_out = nullptr;
     int cur = 0;
     long long t = 0;
+    // Second execution mode: one chain of single-lattice step kernels per
+    // instance (each launch reads its parameters as kernel operands), fanned out
+    // over a pool of streams and captured as one CUDA graph; instances are
+    // independent, so the chains need no barrier between them.
+    int mode = 0;  // 0: persistent kernel, 1: graph of per-instance chains
+    dim3 chain_block{128, 1, 1};
+    std::vector<cudaStream_t> pool;
+    cudaEvent_t ev_fork = nullptr;
+    std::vector<cudaEvent_t> ev_join;
+    cudaGraphExec_t chain_graph[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};  // [parity][moments]
 };
 
 namespace {
 
 void brelease(cdf_batch *b) {
     if (!b) return;
+    for (auto &row : b->chain_graph)
+        for (auto &g : row)
+            if (g) cudaGraphExecDestroy(g);
+    for (cudaStream_t ps : b->pool) cudaStreamDestroy(ps);
+    for (cudaEvent_t e : b->ev_join) cudaEventDestroy(e);
+    if (b->ev_fork) cudaEventDestroy(b->ev_fork);
     cudaFree(b->buf[0]);
     cudaFree(b->buf[1]);
     cudaFree(b->sprev);
@@ -250,38 +266,109 @@ cdf_status launch_batch(cdf_batch *b, int nsteps, bool moments_last) {
     return CDF_OK;
 }
 
+constexpr int kPoolStreams = 32;
+constexpr int kChainGraphSteps = 32;  // even: the buffer parity returns
+
+// Enqueue n steps of every instance as chains of single-lattice step kernels on
+// the stream pool (fork from and join back to the batch stream).
+cdf_status enqueue_chains(cdf_batch *b, int nsteps, bool moments_last, int parity0) {
+    BCK(cudaEventRecord(b->ev_fork, b->s));
+    for (cudaStream_t ps : b->pool) BCK(cudaStreamWaitEvent(ps, b->ev_fork, 0));
+    for (int st = 0; st < nsteps; ++st) {
+        const int par = (parity0 + st) & 1;
+        for (int k = 0; k < b->count; ++k) {
+            float *mom = (moments_last && st == nsteps - 1) ? b->mom + b->mom_off[k] : nullptr;
+            BCK(launch_step(b->params[k], kFP32, b->buf[par] + b->pop_off[k], b->buf[par ^ 1] + b->pop_off[k],
+                            b->sprev + b->sp_off[k], mom, b->chain_block, b->pool[k % b->pool.size()]));
+        }
+    }
+    for (size_t j = 0; j < b->pool.size(); ++j) {
+        BCK(cudaEventRecord(b->ev_join[j], b->pool[j]));
+        BCK(cudaStreamWaitEvent(b->s, b->ev_join[j], 0));
+    }
+    return CDF_OK;
+}
+
+cdf_status run_chains(cdf_batch *b, int nsteps, bool moments_last) {
+    if (nsteps == kChainGraphSteps) {
+        cudaGraphExec_t &ge = b->chain_graph[b->cur][moments_last ? 1 : 0];
+        if (!ge) {
+            cudaGraph_t g = nullptr;
+            BCK(cudaStreamBeginCapture(b->s, cudaStreamCaptureModeThreadLocal));
+            cdf_status st = enqueue_chains(b, nsteps, moments_last, b->cur);
+            cudaError_t e = cudaStreamEndCapture(b->s, &g);
+            if (st != CDF_OK) {
+                if (g) cudaGraphDestroy(g);
+                return st;
+            }
+            BCK(e);
+            e = cudaGraphInstantiate(&ge, g, 0);
+            cudaGraphDestroy(g);
+            BCK(e);
+        }
+        BCK(cudaGraphLaunch(ge, b->s));
+    } else {
+        cdf_status st = enqueue_chains(b, nsteps, moments_last, b->cur);
+        if (st != CDF_OK) return st;
+    }
+    if (nsteps & 1) b->cur ^= 1;
+    b->t += nsteps;
+    return CDF_OK;
+}
+
 cdf_status check_err(cdf_batch *b) {
     if (*b->h_err) return bfail(CDF_ETIMEOUT, "grid barrier wait timed out; the batch state is undefined");
     return CDF_OK;
 }
 
+using ModeChoice = std::pair<int, dim3>;  // (mode, tile or chain block)
+std::map<TuneKey, ModeChoice> g_bmode;
+
 cdf_status bautotune(cdf_batch *b) {
     TuneKey key{b->nodes, (long long)b->count, b->m, b->params[0].chemotaxis};
     {
         std::lock_guard<std::mutex> lk(g_btune_mu);
-        auto it = g_btune.find(key);
-        if (it != g_btune.end()) return setup_tiles(b, it->second);
+        auto it = g_bmode.find(key);
+        if (it != g_bmode.end()) {
+            b->mode = it->second.first;
+            if (b->mode == 1) {
+                b->chain_block = it->second.second;
+                return setup_tiles(b, dim3(64, 4));
+            }
+            return setup_tiles(b, it->second.second);
+        }
     }
-    const dim3 cands[] = {dim3(32, 4), dim3(32, 8), dim3(64, 2), dim3(64, 4), dim3(128, 1), dim3(128, 2),
-                          dim3(256, 1)};
     cudaEvent_t e0, e1;
     BCK(cudaEventCreate(&e0));
     BCK(cudaEventCreate(&e1));
     float best = 1e30f;
-    dim3 best_t = cands[0];
+    ModeChoice choice{0, dim3(64, 4)};
     const int steps = b->nodes > (1 << 22) ? 4 : 16;
-    for (const dim3 &c : cands) {
+    auto time_it = [&](auto &&run) -> float {
+        if (run(2) != CDF_OK) return -1.f;
+        if (cudaEventRecord(e0, b->s) != cudaSuccess) return -1.f;
+        if (run(steps) != CDF_OK) return -1.f;
+        if (cudaEventRecord(e1, b->s) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess) return -1.f;
+        if (check_err(b) != CDF_OK) return -1.f;
+        float ms = 0;
+        cudaEventElapsedTime(&ms, e0, e1);
+        return ms;
+    };
+    const dim3 tiles[] = {dim3(32, 4), dim3(32, 8), dim3(64, 2), dim3(64, 4), dim3(128, 1), dim3(128, 2),
+                          dim3(256, 1)};
+    for (const dim3 &c : tiles) {
         cdf_status st = setup_tiles(b, c);
         if (st != CDF_OK) return st;
-        if ((st = launch_batch(b, 2, false)) != CDF_OK) return st;
-        BCK(cudaEventRecord(e0, b->s));
-        if ((st = launch_batch(b, steps, false)) != CDF_OK) return st;
-        BCK(cudaEventRecord(e1, b->s));
-        BCK(cudaEventSynchronize(e1));
-        if ((st = check_err(b)) != CDF_OK) return st;
-        float ms = 0;
-        BCK(cudaEventElapsedTime(&ms, e0, e1));
-        if (ms < best) { best = ms; best_t = c; }
+        float ms = time_it([&](int n) { return launch_batch(b, n, false); });
+        if (ms < 0) return bfail(CDF_ECUDA, "autotuning the persistent kernel failed");
+        if (ms < best) { best = ms; choice = {0, c}; }
+    }
+    const dim3 blocks[] = {dim3(128, 1), dim3(128, 2), dim3(256, 1), dim3(64, 4), dim3(32, 8)};
+    for (const dim3 &c : blocks) {
+        b->chain_block = c;
+        float ms = time_it([&](int n) { return run_chains(b, n, false); });
+        if (ms < 0) return bfail(CDF_ECUDA, "autotuning the kernel chains failed");
+        if (ms < best) { best = ms; choice = {1, c}; }
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
@@ -289,9 +376,14 @@ cdf_status bautotune(cdf_batch *b) {
     b->cur = 0;
     {
         std::lock_guard<std::mutex> lk(g_btune_mu);
-        g_btune[key] = best_t;
+        g_bmode[key] = choice;
     }
-    return setup_tiles(b, best_t);
+    b->mode = choice.first;
+    if (b->mode == 1) {
+        b->chain_block = choice.second;
+        return setup_tiles(b, dim3(64, 4));
+    }
+    return setup_tiles(b, choice.second);
 }
 
 }  // namespace
@@ -374,8 +466,21 @@ cdf_status cdf_batch_create(int count, const cdf_grid *grids, int m, const cdf_d
         brelease(b);
         return bfail(CDF_ECUDA, "stream / memory set-up failed");
     }
+    b->pool.resize(std::min(count, kPoolStreams));
+    b->ev_join.resize(b->pool.size());
+    bool pok = cudaEventCreateWithFlags(&b->ev_fork, cudaEventDisableTiming) == cudaSuccess;
+    for (size_t j = 0; j < b->pool.size() && pok; ++j)
+        pok = cudaStreamCreateWithFlags(&b->pool[j], cudaStreamNonBlocking) == cudaSuccess &&
+              cudaEventCreateWithFlags(&b->ev_join[j], cudaEventDisableTiming) == cudaSuccess;
+    if (!pok) {
+        brelease(b);
+        return bfail(CDF_ECUDA, "stream pool set-up failed");
+    }
+    b->mode = opt->mode;
+    if (opt->mode == 1 && opt->tile_x > 0) b->chain_block = dim3(opt->tile_x, opt->tile_y);
     cdf_status st;
-    if (opt->tile_x > 0) st = setup_tiles(b, dim3(opt->tile_x, opt->tile_y));
+    if (opt->mode == 1 && opt->tile_x > 0) st = setup_tiles(b, dim3(64, 4));
+    else if (opt->tile_x > 0) st = setup_tiles(b, dim3(opt->tile_x, opt->tile_y));
     else if (b->extra_arrivals) st = setup_tiles(b, dim3(64, 4));
     else st = bautotune(b);
     if (st == CDF_OK && cudaStreamSynchronize(b->s) != cudaSuccess) st = bfail(CDF_ECUDA, "set-up failed");
@@ -419,8 +524,8 @@ cdf_status cdf_batch_step(cdf_batch *b, long long n) {
     BCK(cudaEventRecord(b->ev_in, b->user));
     BCK(cudaStreamWaitEvent(b->s, b->ev_in, 0));
     while (n > 0) {
-        const int k = (int)std::min<long long>(n, b->steps_per_launch);
-        cdf_status st = launch_batch(b, k, n == k);
+        const int k = (int)std::min<long long>(n, b->mode == 1 ? kChainGraphSteps : b->steps_per_launch);
+        cdf_status st = b->mode == 1 ? run_chains(b, k, n == k) : launch_batch(b, k, n == k);
         if (st != CDF_OK) return st;
         n -= k;
     }
@@ -456,6 +561,9 @@ cdf_status cdf_batch_get_info(const cdf_batch *b, cdf_batch_info *out) {
     out->grid_blocks = b->grid_blocks;
     out->steps_per_launch = b->steps_per_launch;
     out->bytes_per_lup = 2.0 * (9 + 5 * b->m) * 4.0 + 8.0 * b->sprev_planes;
+    out->mode = b->mode;
+    out->chain_block_x = (int)b->chain_block.x;
+    out->chain_block_y = (int)b->chain_block.y;
     out->t = b->t;
     return CDF_OK;
 }

@@ -13,12 +13,15 @@ def small_sweep(count=5, seed=3):
     return I.chemotaxis_plume_sweep(count, seed=seed, wmin=16, wmax=140, hmin=9, hmax=70)
 
 
-@pytest.mark.parametrize("tile,spl", [((64, 4), 32), ((32, 8), 7), ((128, 1), 1)])
-def test_batch_equals_single_lattice_solver(cdf, tile, spl):
+@pytest.mark.parametrize("tile,spl,mode", [((64, 4), 32, 0), ((32, 8), 7, 0), ((128, 1), 1, 0),
+                                           ((128, 1), 0, 1), ((64, 4), 0, 1)])
+def test_batch_equals_single_lattice_solver(cdf, tile, spl, mode):
     """Each instance of the batch follows exactly the single-lattice solver: the
-    same per-node update, bit for bit, across launches and grid barriers."""
+    same per-node update, bit for bit, across launches, grid barriers (persistent
+    mode) and graph-captured kernel chains (chain mode)."""
     pbs = small_sweep()
-    b = cdf.BatchSolver(pbs, tile=tile, steps_per_launch=spl)
+    b = cdf.BatchSolver(pbs, tile=tile, steps_per_launch=spl, mode=mode)
+    assert b.info().mode == mode
     b.step(70)
     assert b.info().t == 70
     for k, pb in enumerate(pbs):
