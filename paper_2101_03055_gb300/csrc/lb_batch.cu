@@ -289,6 +289,17 @@ cdf_status enqueue_chains(cdf_batch *b, int nsteps, bool moments_last, int parit
     return CDF_OK;
 }
 
+// Changing the CTA shape of the chains invalidates their captured graphs.
+void set_chain_block(cdf_batch *b, dim3 blk) {
+    for (auto &row : b->chain_graph)
+        for (auto &g : row)
+            if (g) {
+                cudaGraphExecDestroy(g);
+                g = nullptr;
+            }
+    b->chain_block = blk;
+}
+
 cdf_status run_chains(cdf_batch *b, int nsteps, bool moments_last) {
     if (nsteps == kChainGraphSteps) {
         cudaGraphExec_t &ge = b->chain_graph[b->cur][moments_last ? 1 : 0];
@@ -332,7 +343,7 @@ cdf_status bautotune(cdf_batch *b) {
         if (it != g_bmode.end()) {
             b->mode = it->second.first;
             if (b->mode == 1) {
-                b->chain_block = it->second.second;
+                set_chain_block(b, it->second.second);
                 return setup_tiles(b, dim3(64, 4));
             }
             return setup_tiles(b, it->second.second);
@@ -344,10 +355,10 @@ cdf_status bautotune(cdf_batch *b) {
     float best = 1e30f;
     ModeChoice choice{0, dim3(64, 4)};
     const int steps = b->nodes > (1 << 22) ? 4 : 16;
-    auto time_it = [&](auto &&run) -> float {
-        if (run(2) != CDF_OK) return -1.f;
+    auto time_it = [&](auto &&run, int nsteps) -> float {
+        if (run(nsteps) != CDF_OK) return -1.f;  // warm-up (and graph capture)
         if (cudaEventRecord(e0, b->s) != cudaSuccess) return -1.f;
-        if (run(steps) != CDF_OK) return -1.f;
+        if (run(nsteps) != CDF_OK) return -1.f;
         if (cudaEventRecord(e1, b->s) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess) return -1.f;
         if (check_err(b) != CDF_OK) return -1.f;
         float ms = 0;
@@ -359,14 +370,15 @@ cdf_status bautotune(cdf_batch *b) {
     for (const dim3 &c : tiles) {
         cdf_status st = setup_tiles(b, c);
         if (st != CDF_OK) return st;
-        float ms = time_it([&](int n) { return launch_batch(b, n, false); });
+        float ms = time_it([&](int n) { return launch_batch(b, n, false); }, steps);
         if (ms < 0) return bfail(CDF_ECUDA, "autotuning the persistent kernel failed");
+        ms *= (float)kChainGraphSteps / steps;  // per 32 steps, comparable with the chains
         if (ms < best) { best = ms; choice = {0, c}; }
     }
     const dim3 blocks[] = {dim3(128, 1), dim3(128, 2), dim3(256, 1), dim3(64, 4), dim3(32, 8)};
     for (const dim3 &c : blocks) {
-        b->chain_block = c;
-        float ms = time_it([&](int n) { return run_chains(b, n, false); });
+        set_chain_block(b, c);
+        float ms = time_it([&](int n) { return run_chains(b, n, false); }, kChainGraphSteps);
         if (ms < 0) return bfail(CDF_ECUDA, "autotuning the kernel chains failed");
         if (ms < best) { best = ms; choice = {1, c}; }
     }
@@ -380,7 +392,7 @@ cdf_status bautotune(cdf_batch *b) {
     }
     b->mode = choice.first;
     if (b->mode == 1) {
-        b->chain_block = choice.second;
+        set_chain_block(b, choice.second);
         return setup_tiles(b, dim3(64, 4));
     }
     return setup_tiles(b, choice.second);
@@ -477,7 +489,7 @@ cdf_status cdf_batch_create(int count, const cdf_grid *grids, int m, const cdf_d
         return bfail(CDF_ECUDA, "stream pool set-up failed");
     }
     b->mode = opt->mode;
-    if (opt->mode == 1 && opt->tile_x > 0) b->chain_block = dim3(opt->tile_x, opt->tile_y);
+    if (opt->mode == 1 && opt->tile_x > 0) set_chain_block(b, dim3(opt->tile_x, opt->tile_y));
     cdf_status st;
     if (opt->mode == 1 && opt->tile_x > 0) st = setup_tiles(b, dim3(64, 4));
     else if (opt->tile_x > 0) st = setup_tiles(b, dim3(opt->tile_x, opt->tile_y));
