@@ -120,7 +120,8 @@ typedef struct {
     void *cuda_stream;                 /* cudaStream_t of the caller, NULL = default */
     double phi_ref[CDF_MAX_M];         /* reference scalar values of the stored deviations */
     double p_ref_grad[2];              /* reference pressure gradient (used along walled axes only) */
-    int block_x, block_y;              /* step kernel CTA shape; 0 = autotuned */
+    int block_x, block_y;              /* step kernel CTA shape; block_x = 0: autotuned;
+                                          block_y = 0: flat launch of block_x threads (FP32) */
 } cdf_options;
 
 /* Facts about a handle (for benchmarks and tests). */

@@ -375,7 +375,8 @@ cdf_status bautotune(cdf_batch *b) {
         ms *= (float)kChainGraphSteps / steps;  // per 32 steps, comparable with the chains
         if (ms < best) { best = ms; choice = {0, c}; }
     }
-    const dim3 blocks[] = {dim3(128, 1), dim3(128, 2), dim3(256, 1), dim3(64, 4), dim3(32, 8)};
+    const dim3 blocks[] = {dim3(128, 1), dim3(128, 2), dim3(256, 1), dim3(64, 4), dim3(32, 8), dim3(128, 0),
+                           dim3(256, 0)};  // y == 0: flat launch
     for (const dim3 &c : blocks) {
         set_chain_block(b, c);
         float ms = time_it([&](int n) { return run_chains(b, n, false); }, kChainGraphSteps);

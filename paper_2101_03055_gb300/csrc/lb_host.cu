@@ -249,8 +249,13 @@ cdf_status autotune(cdf_lb *h) {
         auto it = g_tune_cache.find(key);
         if (it != g_tune_cache.end()) { h->block = it->second; return CDF_OK; }
     }
-    const dim3 cands[] = {dim3(32, 4), dim3(32, 8), dim3(64, 2), dim3(64, 4),
-                          dim3(128, 1), dim3(128, 2), dim3(256, 1)};
+    // block.y == 0 marks a flat launch (one thread per node in row order)
+    std::vector<dim3> cands = {dim3(32, 4), dim3(32, 8), dim3(64, 2), dim3(64, 4),
+                               dim3(128, 1), dim3(128, 2), dim3(256, 1)};
+    if (!h->mr) {
+        cands.push_back(dim3(128, 0));
+        cands.push_back(dim3(256, 0));
+    }
     cudaEvent_t a, b;
     CK(cudaEventCreate(&a));
     CK(cudaEventCreate(&b));
@@ -423,8 +428,11 @@ cdf_status cdf_lb_create(const cdf_grid *grid, int m, const cdf_diffusion *dif, 
                                         opt->phi_ref, opt->p_ref_grad, pitch, &P0);
     if (st != CDF_OK) return st;
     if (opt->block_x != 0 || opt->block_y != 0) {
-        if (opt->block_x <= 0 || opt->block_y <= 0 || opt->block_x * opt->block_y > 256 || opt->block_x % 32 != 0)
+        const int threads = opt->block_x * (opt->block_y > 0 ? opt->block_y : 1);
+        if (opt->block_x <= 0 || opt->block_y < 0 || threads > 256 || opt->block_x % 32 != 0)
             return fail(CDF_EINVAL, "block must be a multiple of 32 wide and at most 256 threads");
+        if (opt->block_y == 0 && opt->storage != CDF_FP32)
+            return fail(CDF_EINVAL, "the flat launch (block_y = 0) exists for FP32 storage only");
     }
 
     cdf_lb *h = new (std::nothrow) cdf_lb;
@@ -479,8 +487,8 @@ cdf_status cdf_lb_create(const cdf_grid *grid, int m, const cdf_diffusion *dif, 
         release(h);
         return fail(CDF_ECUDA, "memset failed");
     }
-    if (opt->block_x > 0 && opt->block_y > 0) {
-        h->block = dim3(opt->block_x, opt->block_y);
+    if (opt->block_x > 0) {
+        h->block = dim3(opt->block_x, opt->block_y, 1);
     } else if ((st = autotune(h)) != CDF_OK) {
         release(h);
         return st;
@@ -746,7 +754,7 @@ cdf_status cdf_lb_get_info(const cdf_lb *h, cdf_info *out) {
     if (!h || !out) return fail(CDF_EINVAL, "NULL argument");
     out->nx = h->nx; out->ny = h->ny; out->m = h->m; out->pitch = h->pitch;
     out->storage = h->storage; out->planes = h->planes; out->sprev_planes = h->sprev_planes;
-    out->block_x = (int)h->block.x; out->block_y = (int)h->block.y;
+    out->block_x = (int)h->block.x; out->block_y = (int)h->block.y;  // block_y 0: flat launch
     out->bytes_per_lup = 2.0 * h->planes * (double)elem_size(h->storage) + 8.0 * h->sprev_planes +
                          (h->mr ? 2.0 * 4.0 * (h->m + 3) : 0.0);
     out->t = h->t;

@@ -45,7 +45,8 @@ struct LbParams {
 
 enum Storage { kFP32 = 0, kFP16 = 1, kBF16 = 2 };
 
-// Launchers (lb_kernels.cu).  `in`/`out` point at the first of `planes`
+// Launchers (lb_kernels.cu).  A step launch with block.y == 0 is flat: block.x
+// threads per CTA over the nx * ny nodes in row order (FP32 storage path).  `in`/`out` point at the first of `planes`
 // population planes; plane k starts at base + k * plane.  Planes are ordered
 // h_0..h_8, then f_{a,0..4} for a = 0..m-1.
 cudaError_t launch_step(const LbParams &p, int storage, const void *in, void *out, float *sprev,

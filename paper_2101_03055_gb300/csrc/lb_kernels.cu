@@ -30,6 +30,17 @@ __global__ void __launch_bounds__(256) step_kernel(const LbParams p, const T *__
     step_node<M, T>(p, x, y, in, out, sprev, moments);
 }
 
+// Flat launch: one thread per node over nx * ny (no idle threads in ragged rows).
+template <int M, typename T>
+__global__ void __launch_bounds__(256) step_kernel_flat(const LbParams p, const T *__restrict__ in,
+                                                        T *__restrict__ out, float *__restrict__ sprev,
+                                                        float *__restrict__ moments) {
+    const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= p.nx * p.ny) return;
+    const int y = idx / p.nx, x = idx - y * p.nx;
+    step_node<M, T>(p, x, y, in, out, sprev, moments);
+}
+
 // ---- initialisation from moments (collide-only pass at t = 0) ------------------
 template <int M, typename T>
 __global__ void init_kernel(const LbParams p, const float *__restrict__ fields, int fpitch,
@@ -348,9 +359,21 @@ cudaError_t export_mr_dispatch(const LbParams &p, const void *in, const float *m
 template <typename T>
 cudaError_t step_dispatch(const LbParams &p, const void *in, void *out, float *sprev, float *mom,
                           dim3 block, cudaStream_t s) {
-    dim3 grid((p.nx + block.x - 1) / block.x, (p.ny + block.y - 1) / block.y);
     const T *i = static_cast<const T *>(in);
     T *o = static_cast<T *>(out);
+    if (block.y == 0) {  // flat launch
+        const long long n = (long long)p.nx * p.ny;
+        dim3 fb(block.x), grid((unsigned)((n + block.x - 1) / block.x));
+        switch (p.m) {
+            case 1: step_kernel_flat<1, T><<<grid, fb, 0, s>>>(p, i, o, sprev, mom); break;
+            case 2: step_kernel_flat<2, T><<<grid, fb, 0, s>>>(p, i, o, sprev, mom); break;
+            case 3: step_kernel_flat<3, T><<<grid, fb, 0, s>>>(p, i, o, sprev, mom); break;
+            case 4: step_kernel_flat<4, T><<<grid, fb, 0, s>>>(p, i, o, sprev, mom); break;
+            default: return cudaErrorInvalidValue;
+        }
+        return cudaGetLastError();
+    }
+    dim3 grid((p.nx + block.x - 1) / block.x, (p.ny + block.y - 1) / block.y);
     switch (p.m) {
         case 1: step_kernel<1, T><<<grid, block, 0, s>>>(p, i, o, sprev, mom); break;
         case 2: step_kernel<2, T><<<grid, block, 0, s>>>(p, i, o, sprev, mom); break;

@@ -234,7 +234,7 @@ def test_regularised_cutoff_and_const_source(cdf, oracle_mod):
 def test_block_shapes_agree_bitwise(cdf):
     pb = I.chemotaxis_plume(100, 60, seed=4)
     ref = None
-    for blk in [(32, 4), (64, 2), (128, 1), (256, 1), (32, 8)]:
+    for blk in [(32, 4), (64, 2), (128, 1), (256, 1), (32, 8), (128, 0), (256, 0)]:
         s = cdf.Solver(pb, block=blk)
         s.step(77)
         M = s.moments()
