@@ -248,6 +248,12 @@ cdf_status cdf_batch_init_moments(cdf_batch *b, int k, const double *phi, const 
 cdf_status cdf_batch_step(cdf_batch *b, long long n);
 /* Moments of instance k at the current time into a host FP64 stack [m+3][ny][nx]. */
 cdf_status cdf_batch_moments(cdf_batch *b, int k, double *host_out);
+/* Keep a copy of every instance's current moments; cdf_batch_residuals then gives,
+ * per instance, the stop-test residual R of cdf_lb_run_to_steady between that copy
+ * and the current moments (FP64 sums; +Inf where a field is not finite).
+ * residual has `count` entries (host). */
+cdf_status cdf_batch_snapshot(cdf_batch *b);
+cdf_status cdf_batch_residuals(cdf_batch *b, double *residual);
 cdf_status cdf_batch_get_info(const cdf_batch *b, cdf_batch_info *out);
 void *cdf_batch_stream(const cdf_batch *b);
 void cdf_batch_destroy(cdf_batch *b);

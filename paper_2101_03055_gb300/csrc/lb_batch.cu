@@ -155,6 +155,8 @@ struct cdf_batch {
     int sprev_planes = 0;
     float *buf[2] = {nullptr, nullptr};
     float *sprev = nullptr, *mom = nullptr, *dense = nullptr, *host_stage = nullptr;
+    float *mom_prev = nullptr;                        // snapshot for per-instance residuals
+    double *partials = nullptr, *red = nullptr, *red_host = nullptr;  // per-instance reductions
     size_t stage_floats = 0;
     BatchInst *d_inst = nullptr;
     int *d_tile_inst = nullptr;
@@ -195,6 +197,10 @@ void brelease(cdf_batch *b) {
     cudaFree(b->buf[1]);
     cudaFree(b->sprev);
     cudaFree(b->mom);
+    cudaFree(b->mom_prev);
+    cudaFree(b->partials);
+    cudaFree(b->red);
+    if (b->red_host) cudaFreeHost(b->red_host);
     cudaFree(b->dense);
     cudaFree(b->d_inst);
     cudaFree(b->d_tile_inst);
@@ -459,6 +465,10 @@ cdf_status cdf_batch_create(int count, const cdf_grid *grids, int m, const cdf_d
               cudaMalloc(&b->buf[1], b->pop_total * 4) == cudaSuccess &&
               cudaMalloc(&b->sprev, b->sp_total * 4) == cudaSuccess &&
               cudaMalloc(&b->mom, b->mom_total * 4) == cudaSuccess &&
+              cudaMalloc(&b->mom_prev, b->mom_total * 4) == cudaSuccess &&
+              cudaMalloc(&b->partials, (size_t)reduce_quantities(m) * kReduceBlocks * sizeof(double)) == cudaSuccess &&
+              cudaMalloc(&b->red, (size_t)count * reduce_quantities(m) * sizeof(double)) == cudaSuccess &&
+              cudaMallocHost(&b->red_host, (size_t)count * reduce_quantities(m) * sizeof(double)) == cudaSuccess &&
               cudaMalloc(&b->dense, b->stage_floats * 4) == cudaSuccess &&
               cudaMalloc(&b->d_inst, count * sizeof(BatchInst)) == cudaSuccess &&
               cudaMalloc(&b->d_bar, 2 * sizeof(unsigned)) == cudaSuccess &&
@@ -578,6 +588,37 @@ cdf_status cdf_batch_get_info(const cdf_batch *b, cdf_batch_info *out) {
     out->chain_block_x = (int)b->chain_block.x;
     out->chain_block_y = (int)b->chain_block.y;
     out->t = b->t;
+    return CDF_OK;
+}
+
+cdf_status cdf_batch_snapshot(cdf_batch *b) {
+    if (!b) return bfail(CDF_EINVAL, "NULL handle");
+    BCK(cudaEventRecord(b->ev_in, b->user));
+    BCK(cudaStreamWaitEvent(b->s, b->ev_in, 0));
+    BCK(cudaMemcpyAsync(b->mom_prev, b->mom, b->mom_total * 4, cudaMemcpyDeviceToDevice, b->s));
+    BCK(cudaEventRecord(b->ev_out, b->s));
+    BCK(cudaStreamWaitEvent(b->user, b->ev_out, 0));
+    return CDF_OK;
+}
+
+cdf_status cdf_batch_residuals(cdf_batch *b, double *residual) {
+    if (!b || !residual) return bfail(CDF_EINVAL, "NULL argument");
+    const int nq = reduce_quantities(b->m), m = b->m;
+    BCK(cudaEventRecord(b->ev_in, b->user));
+    BCK(cudaStreamWaitEvent(b->s, b->ev_in, 0));
+    for (int k = 0; k < b->count; ++k) {
+        const LbParams &P = b->params[k];
+        BCK(launch_reduce(b->mom + b->mom_off[k], b->mom_prev + b->mom_off[k], P.nx, P.ny, P.pitch, P.plane, m,
+                          b->partials, b->red + (size_t)k * nq, b->s));
+    }
+    BCK(cudaMemcpyAsync(b->red_host, b->red, (size_t)b->count * nq * sizeof(double), cudaMemcpyDeviceToHost, b->s));
+    BCK(cudaStreamSynchronize(b->s));
+    for (int k = 0; k < b->count; ++k) {
+        const double *q = b->red_host + (size_t)k * nq;
+        double R = 0.0;
+        for (int f = 0; f < m + 2; ++f) R = std::max(R, q[m + f] / std::max(q[2 * m + 2 + f], 1e-300));
+        residual[k] = q[3 * m + 4] > 0 ? INFINITY : R;
+    }
     return CDF_OK;
 }
 

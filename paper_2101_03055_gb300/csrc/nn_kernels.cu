@@ -1,0 +1,544 @@
+// BF16 kernels of the convolutional surrogate that warm-starts the steady
+// solve: 3x3 convolutions as implicit GEMMs on the tensor cores (BF16 operands,
+// FP32 accumulation), their two backward passes, and the small layers around
+// them (bias + ReLU epilogue, 2x2 average pooling, nearest 2x upsampling,
+// channel copies for skip connections, 1x1 output head, MSE loss, Adam).
+// Activations are NHWC with the channel count a multiple of 16; 3x3 weights
+// are [Cout][3][3][Cin].
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <mma.h>
+
+#include <cstdint>
+
+#include "../../include/cdf_nn.h"
+
+using namespace nvcuda;
+
+namespace {
+
+constexpr int kBM = 64;      // pixels per CTA tile (forward / backward-data)
+constexpr int kThreads = 128;
+constexpr int kLdA = 24;     // padded leading dimensions of the shared tiles (bf16 elements)
+
+// ---------------------------------------------------------------------------
+// 3x3 convolution as an implicit GEMM.
+//   forward:       Y[p][co] = act(sum_{t, ci} X[p + d(t)][ci] W[co][t][ci] + b[co])
+//   backward data: dX[p][ci] = sum_{t, co} dY[p + d(t)][co] W[co][8 - t][ci]
+// with d(t) = (ky - 1, kx - 1) for tap t = 3 ky + kx and zero outside the image.
+// GEMM: M = pixels (tile kBM), N = output channels (tile BN), K = 9 x input channels.
+// ---------------------------------------------------------------------------
+template <bool kBwdData, int BN>
+__global__ void __launch_bounds__(kThreads) conv3x3_kernel(const __nv_bfloat16 *__restrict__ in,
+                                                           const __nv_bfloat16 *__restrict__ w,
+                                                           const float *__restrict__ bias,
+                                                           __nv_bfloat16 *__restrict__ out, int N, int H, int Wd,
+                                                           int Cin_g, int Cout_g, int relu) {
+    // Cin_g / Cout_g: channels of the GEMM input / output (fwd: Cin / Cout; bwd: Cout / Cin).
+    constexpr int kLdB = BN + 8;
+    __shared__ __align__(32) __nv_bfloat16 As[kBM * kLdA];
+    __shared__ __align__(32) __nv_bfloat16 Bs[16 * kLdB > BN * kLdA ? 16 * kLdB : BN * kLdA];
+    __shared__ __align__(32) float Cs[kBM * (BN + 4)];
+    const int tid = threadIdx.x, warp = tid >> 5;
+    const long long P = (long long)N * H * Wd;
+    const long long p0 = (long long)blockIdx.x * kBM;
+    const int n0 = blockIdx.y * BN;
+    // The original weight tensor's channel counts: Cout_w x 9 x Cin_w.
+    const int Cin_w = kBwdData ? Cout_g : Cin_g;
+
+    // A-tile row handled by this thread: pixel p0 + tid / 2, 8 channels at (tid & 1) * 8.
+    const int arow = tid >> 1, acol = (tid & 1) * 8;
+    const long long pa = p0 + arow;
+    int an = 0, ay = 0, ax = 0;
+    if (pa < P) {
+        an = (int)(pa / ((long long)H * Wd));
+        const int rem = (int)(pa - (long long)an * H * Wd);
+        ay = rem / Wd;
+        ax = rem - ay * Wd;
+    }
+
+    wmma::fragment<wmma::accumulator, 16, 16, 16, float> acc[BN / 16];
+#pragma unroll
+    for (int j = 0; j < BN / 16; ++j) wmma::fill_fragment(acc[j], 0.f);
+
+    const int K = 9 * Cin_g;
+    for (int k0 = 0; k0 < K; k0 += 16) {
+        const int tap = k0 / Cin_g, c0 = k0 - tap * Cin_g;
+        const int dy = tap / 3 - 1, dx = tap % 3 - 1;
+        // A tile: 16 input channels of the shifted pixels (zero outside the image).
+        {
+            uint4 v = make_uint4(0, 0, 0, 0);
+            const int sy = ay + dy, sx = ax + dx;
+            if (pa < P && sy >= 0 && sy < H && sx >= 0 && sx < Wd)
+                v = *reinterpret_cast<const uint4 *>(in + (((long long)an * H + sy) * Wd + sx) * Cin_g + c0 + acol);
+            *reinterpret_cast<uint4 *>(As + arow * kLdA + acol) = v;
+        }
+        // B tile: 16 (k) x BN (n) weights.
+        if (!kBwdData) {
+            // B(k = ci, n = co) = W[co][tap][ci]: per output channel 16 contiguous ci (col-major).
+            for (int e = tid; e < BN * 2; e += kThreads) {
+                const int nn = e >> 1, half = (e & 1) * 8;
+                const uint4 v = *reinterpret_cast<const uint4 *>(w + ((long long)(n0 + nn) * 9 + tap) * Cin_w + c0 + half);
+                *reinterpret_cast<uint4 *>(Bs + nn * kLdA + half) = v;
+            }
+        } else {
+            // B(k = co, n = ci) = W[co][8 - tap][ci]: per k a row of BN contiguous ci (row-major).
+            for (int e = tid; e < 16 * (BN / 8); e += kThreads) {
+                const int kk = e / (BN / 8), seg = (e % (BN / 8)) * 8;
+                const uint4 v = *reinterpret_cast<const uint4 *>(
+                    w + ((long long)(c0 + kk) * 9 + (8 - tap)) * Cin_w + n0 + seg);
+                *reinterpret_cast<uint4 *>(Bs + kk * kLdB + seg) = v;
+            }
+        }
+        __syncthreads();
+        wmma::fragment<wmma::matrix_a, 16, 16, 16, __nv_bfloat16, wmma::row_major> a;
+        wmma::load_matrix_sync(a, As + warp * 16 * kLdA, kLdA);
+#pragma unroll
+        for (int j = 0; j < BN / 16; ++j) {
+            if (!kBwdData) {
+                wmma::fragment<wmma::matrix_b, 16, 16, 16, __nv_bfloat16, wmma::col_major> b;
+                wmma::load_matrix_sync(b, Bs + j * 16 * kLdA, kLdA);
+                wmma::mma_sync(acc[j], a, b, acc[j]);
+            } else {
+                wmma::fragment<wmma::matrix_b, 16, 16, 16, __nv_bfloat16, wmma::row_major> b;
+                wmma::load_matrix_sync(b, Bs + j * 16, kLdB);
+                wmma::mma_sync(acc[j], a, b, acc[j]);
+            }
+        }
+        __syncthreads();
+    }
+    // Epilogue: bias, ReLU, BF16, one 16-byte store per 8 channels.
+#pragma unroll
+    for (int j = 0; j < BN / 16; ++j)
+        wmma::store_matrix_sync(Cs + warp * 16 * (BN + 4) + j * 16, acc[j], BN + 4, wmma::mem_row_major);
+    __syncthreads();
+    for (int e = tid; e < kBM * (BN / 8); e += kThreads) {
+        const int r = e / (BN / 8), seg = (e % (BN / 8)) * 8;
+        const long long p = p0 + r;
+        if (p >= P) continue;
+        __align__(16) __nv_bfloat16 o[8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            float v = Cs[r * (BN + 4) + seg + q];
+            if (bias) v += bias[n0 + seg + q];
+            if (relu) v = fmaxf(v, 0.f);
+            o[q] = __float2bfloat16_rn(v);
+        }
+        *reinterpret_cast<uint4 *>(out + p * Cout_g + n0 + seg) = *reinterpret_cast<const uint4 *>(o);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// 3x3 convolution, weight gradient: dW[co][t][ci] += sum_p dY[p][co] X[p + d(t)][ci]
+// GEMM per tap: M = Cout (tile 64), N = Cin (tile 16), K = pixels (chunk of 64 per
+// stage, split over the grid's z dimension); FP32 partial sums are added atomically.
+// ---------------------------------------------------------------------------
+constexpr int kWBM = 64, kWBK = 64;
+__global__ void __launch_bounds__(kThreads) conv3x3_wgrad_kernel(const __nv_bfloat16 *__restrict__ x,
+                                                                 const __nv_bfloat16 *__restrict__ dy,
+                                                                 float *__restrict__ dw, int N, int H, int Wd,
+                                                                 int Cin, int Cout, long long pix_per_split) {
+    __shared__ __align__(32) __nv_bfloat16 As[kWBK * (kWBM + 8)];  // [k = pixel][m = co]
+    __shared__ __align__(32) __nv_bfloat16 Bs[kWBK * kLdA];       // [k = pixel][n = ci]
+    __shared__ __align__(32) float Cs[kWBM * 20];
+    const int tid = threadIdx.x, warp = tid >> 5;
+    const int co0 = blockIdx.x * kWBM;
+    const int tap = blockIdx.y / (Cin / 16), ci0 = (blockIdx.y % (Cin / 16)) * 16;
+    const int dyy = tap / 3 - 1, dxx = tap % 3 - 1;
+    const long long P = (long long)N * H * Wd;
+    const long long pbeg = (long long)blockIdx.z * pix_per_split;
+    const long long pend = pbeg + pix_per_split < P ? pbeg + pix_per_split : P;
+    const int mrows = Cout - co0 < kWBM ? Cout - co0 : kWBM;  // 32 or 64 output channels
+
+    wmma::fragment<wmma::accumulator, 16, 16, 16, float> acc;
+    wmma::fill_fragment(acc, 0.f);
+    for (long long pk = pbeg; pk < pend; pk += kWBK) {
+        // A: dY rows (pixel k, output channels co0..co0+63), 8 channels per 16-byte load.
+        for (int e = tid; e < kWBK * (kWBM / 8); e += kThreads) {
+            const int kk = e / (kWBM / 8), seg = (e % (kWBM / 8)) * 8;
+            uint4 v = make_uint4(0, 0, 0, 0);
+            const long long p = pk + kk;
+            if (p < pend && seg < mrows) v = *reinterpret_cast<const uint4 *>(dy + p * Cout + co0 + seg);
+            *reinterpret_cast<uint4 *>(As + kk * (kWBM + 8) + seg) = v;
+        }
+        // B: X at the shifted pixel, 16 input channels.
+        {
+            const int kk = tid >> 1, half = (tid & 1) * 8;
+            uint4 v = make_uint4(0, 0, 0, 0);
+            const long long p = pk + kk;
+            if (p < pend) {
+                const int n = (int)(p / ((long long)H * Wd));
+                const int rem = (int)(p - (long long)n * H * Wd);
+                const int yy = rem / Wd + dyy, xx = rem % Wd + dxx;
+                if (yy >= 0 && yy < H && xx >= 0 && xx < Wd)
+                    v = *reinterpret_cast<const uint4 *>(x + (((long long)n * H + yy) * Wd + xx) * Cin + ci0 + half);
+            }
+            *reinterpret_cast<uint4 *>(Bs + kk * kLdA + half) = v;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int ks = 0; ks < kWBK; ks += 16) {
+            wmma::fragment<wmma::matrix_a, 16, 16, 16, __nv_bfloat16, wmma::col_major> a;
+            wmma::fragment<wmma::matrix_b, 16, 16, 16, __nv_bfloat16, wmma::row_major> b;
+            wmma::load_matrix_sync(a, As + ks * (kWBM + 8) + warp * 16, kWBM + 8);
+            wmma::load_matrix_sync(b, Bs + ks * kLdA, kLdA);
+            wmma::mma_sync(acc, a, b, acc);
+        }
+        __syncthreads();
+    }
+    wmma::store_matrix_sync(Cs + warp * 16 * 20, acc, 20, wmma::mem_row_major);
+    __syncthreads();
+    for (int e = tid; e < kWBM * 16; e += kThreads) {
+        const int r = e >> 4, c = e & 15;
+        if (r < mrows) atomicAdd(dw + ((long long)(co0 + r) * 9 + tap) * Cin + ci0 + c, Cs[r * 20 + c]);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Small layers (one thread per element unless stated).
+// ---------------------------------------------------------------------------
+__global__ void bias_grad_kernel(const __nv_bfloat16 *__restrict__ dy, float *__restrict__ db, long long P, int C) {
+    // block: 256 threads over pixels for one channel group of 8; grid.x = C / 8, grid.y = splits
+    const int c0 = blockIdx.x * 8;
+    float s[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    for (long long p = (long long)blockIdx.y * blockDim.x + threadIdx.x; p < P; p += (long long)gridDim.y * blockDim.x) {
+        const uint4 v = *reinterpret_cast<const uint4 *>(dy + p * C + c0);
+        const __nv_bfloat16 *e = reinterpret_cast<const __nv_bfloat16 *>(&v);
+#pragma unroll
+        for (int q = 0; q < 8; ++q) s[q] += __bfloat162float(e[q]);
+    }
+    __shared__ float red[8][256];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) red[q][threadIdx.x] = s[q];
+    __syncthreads();
+    for (int st = blockDim.x / 2; st > 0; st >>= 1) {
+        if ((int)threadIdx.x < st)
+#pragma unroll
+            for (int q = 0; q < 8; ++q) red[q][threadIdx.x] += red[q][threadIdx.x + st];
+        __syncthreads();
+    }
+    if (threadIdx.x < 8) atomicAdd(db + c0 + threadIdx.x, red[threadIdx.x][0]);
+}
+
+__global__ void relu_bwd_kernel(__nv_bfloat16 *__restrict__ d, const __nv_bfloat16 *__restrict__ y, long long n) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n && !(__bfloat162float(y[i]) > 0.f)) d[i] = __float2bfloat16_rn(0.f);
+}
+
+__global__ void avgpool2_fwd_kernel(const __nv_bfloat16 *__restrict__ x, __nv_bfloat16 *__restrict__ y, int N, int H,
+                                    int W, int C) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const int Ho = H / 2, Wo = W / 2;
+    const long long n_out = (long long)N * Ho * Wo * C;
+    if (i >= n_out) return;
+    const int c = (int)(i % C);
+    long long q = i / C;
+    const int xo = (int)(q % Wo);
+    q /= Wo;
+    const int yo = (int)(q % Ho);
+    const int n = (int)(q / Ho);
+    float s = 0.f;
+#pragma unroll
+    for (int a = 0; a < 2; ++a)
+#pragma unroll
+        for (int b = 0; b < 2; ++b)
+            s += __bfloat162float(x[(((long long)n * H + 2 * yo + a) * W + 2 * xo + b) * C + c]);
+    y[i] = __float2bfloat16_rn(0.25f * s);
+}
+
+__global__ void avgpool2_bwd_kernel(const __nv_bfloat16 *__restrict__ dy, __nv_bfloat16 *__restrict__ dx, int N, int H,
+                                    int W, int C) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;  // over dx
+    const long long n_in = (long long)N * H * W * C;
+    if (i >= n_in) return;
+    const int c = (int)(i % C);
+    long long q = i / C;
+    const int xx = (int)(q % W);
+    q /= W;
+    const int yy = (int)(q % H);
+    const int n = (int)(q / H);
+    const float g = __bfloat162float(dy[(((long long)n * (H / 2) + yy / 2) * (W / 2) + xx / 2) * C + c]);
+    dx[i] = __float2bfloat16_rn(0.25f * g);
+}
+
+// Nearest 2x upsampling of x [N, H, W, C] into channels [coff, coff + C) of y [N, 2H, 2W, Cy].
+__global__ void upsample2_fwd_kernel(const __nv_bfloat16 *__restrict__ x, __nv_bfloat16 *__restrict__ y, int N, int H,
+                                     int W, int C, int Cy, int coff) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;  // over y's selected channels
+    const long long n_out = (long long)N * 2 * H * 2 * W * C;
+    if (i >= n_out) return;
+    const int c = (int)(i % C);
+    long long q = i / C;
+    const int xo = (int)(q % (2 * W));
+    q /= 2 * W;
+    const int yo = (int)(q % (2 * H));
+    const int n = (int)(q / (2 * H));
+    y[(((long long)n * 2 * H + yo) * 2 * W + xo) * Cy + coff + c] = x[(((long long)n * H + yo / 2) * W + xo / 2) * C + c];
+}
+
+// Backward of the above: dx[n][y][x][c] = sum of the 4 covering dy values (channels coff..coff+C of dy).
+__global__ void upsample2_bwd_kernel(const __nv_bfloat16 *__restrict__ dy, __nv_bfloat16 *__restrict__ dx, int N, int H,
+                                     int W, int C, int Cy, int coff) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long long n_in = (long long)N * H * W * C;
+    if (i >= n_in) return;
+    const int c = (int)(i % C);
+    long long q = i / C;
+    const int xx = (int)(q % W);
+    q /= W;
+    const int yy = (int)(q % H);
+    const int n = (int)(q / H);
+    float s = 0.f;
+#pragma unroll
+    for (int a = 0; a < 2; ++a)
+#pragma unroll
+        for (int b = 0; b < 2; ++b)
+            s += __bfloat162float(dy[(((long long)n * 2 * H + 2 * yy + a) * 2 * W + 2 * xx + b) * Cy + coff + c]);
+    dx[i] = __float2bfloat16_rn(s);
+}
+
+// y[:, :, :, dst_off + c] = x[:, :, :, src_off + c] for c < count (skip concat / split).
+__global__ void copy_channels_kernel(const __nv_bfloat16 *__restrict__ x, __nv_bfloat16 *__restrict__ y, long long P,
+                                     int Cx, int Cy, int src_off, int dst_off, int count, int accumulate) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= P * count) return;
+    const long long p = i / count;
+    const int c = (int)(i - p * count);
+    const float v = __bfloat162float(x[p * Cx + src_off + c]);
+    __nv_bfloat16 *d = y + p * Cy + dst_off + c;
+    *d = __float2bfloat16_rn(accumulate ? v + __bfloat162float(*d) : v);
+}
+
+// 1x1 output head in FP32 arithmetic: out[p][o] = sum_c x[p][c] w[o][c] + b[o].
+__global__ void head_fwd_kernel(const __nv_bfloat16 *__restrict__ x, const float *__restrict__ w,
+                                const float *__restrict__ b, float *__restrict__ out, long long P, int C, int O) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= P * O) return;
+    const long long p = i / O;
+    const int o = (int)(i - p * O);
+    float s = b[o];
+    for (int c = 0; c < C; ++c) s = fmaf(__bfloat162float(x[p * C + c]), w[o * C + c], s);
+    out[i] = s;
+}
+
+// dx[p][c] = sum_o dout[p][o] w[o][c]
+__global__ void head_bwd_data_kernel(const float *__restrict__ dout, const float *__restrict__ w,
+                                     __nv_bfloat16 *__restrict__ dx, long long P, int C, int O) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= P * C) return;
+    const long long p = i / C;
+    const int c = (int)(i - p * C);
+    float s = 0.f;
+    for (int o = 0; o < O; ++o) s = fmaf(dout[p * O + o], w[o * C + c], s);
+    dx[i] = __float2bfloat16_rn(s);
+}
+
+// dw[o][c] += sum_p dout[p][o] x[p][c]; db[o] += sum_p dout[p][o]  (one block per (o, c-chunk) pair, grid-stride)
+__global__ void head_bwd_weight_kernel(const __nv_bfloat16 *__restrict__ x, const float *__restrict__ dout,
+                                       float *__restrict__ dw, float *__restrict__ db, long long P, int C, int O) {
+    const int o = blockIdx.x / (C + 1), c = blockIdx.x % (C + 1);  // c == C: bias
+    float s = 0.f;
+    for (long long p = (long long)blockIdx.y * blockDim.x + threadIdx.x; p < P; p += (long long)gridDim.y * blockDim.x)
+        s += dout[p * O + o] * (c < C ? __bfloat162float(x[p * C + c]) : 1.f);
+    __shared__ float red[256];
+    red[threadIdx.x] = s;
+    __syncthreads();
+    for (int st = blockDim.x / 2; st > 0; st >>= 1) {
+        if ((int)threadIdx.x < st) red[threadIdx.x] += red[threadIdx.x + st];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) atomicAdd(c < C ? dw + o * C + c : db + o, red[0]);
+}
+
+// Mean squared error over n values; loss (FP32 sum, atomically added) and its gradient 2 (pred - target) / n.
+__global__ void mse_kernel(const float *__restrict__ pred, const float *__restrict__ target, float *__restrict__ grad,
+                           float *__restrict__ loss, long long n) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    float e = 0.f;
+    if (i < n) {
+        const float d = pred[i] - target[i];
+        grad[i] = 2.f * d / (float)n;
+        e = d * d / (float)n;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) e += __shfl_down_sync(0xffffffffu, e, o);
+    if ((threadIdx.x & 31) == 0) atomicAdd(loss, e);
+}
+
+// Adam on FP32 master weights; refreshes the BF16 copy when one is given.
+__global__ void adam_kernel(float *__restrict__ w, const float *__restrict__ g, float *__restrict__ m,
+                            float *__restrict__ v, __nv_bfloat16 *__restrict__ wb, long long n, float lr, float b1,
+                            float b2, float eps, float c1, float c2) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const float gi = g[i];
+    const float mi = b1 * m[i] + (1.f - b1) * gi;
+    const float vi = b2 * v[i] + (1.f - b2) * gi * gi;
+    m[i] = mi;
+    v[i] = vi;
+    const float wi = w[i] - lr * (mi / c1) / (sqrtf(vi / c2) + eps);
+    w[i] = wi;
+    if (wb) wb[i] = __float2bfloat16_rn(wi);
+}
+
+inline unsigned blocks_for(long long n, int t = 256) { return (unsigned)((n + t - 1) / t); }
+
+thread_local char g_nn_err[256] = "";
+cdf_nn_status nn_fail(const char *m) {
+    int i = 0;
+    for (; m[i] && i < 255; ++i) g_nn_err[i] = m[i];
+    g_nn_err[i] = 0;
+    return CDF_NN_EINVAL;
+}
+cdf_nn_status launched() {
+    const cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) return CDF_NN_OK;
+    int i = 0;
+    const char *m = cudaGetErrorString(e);
+    for (; m[i] && i < 255; ++i) g_nn_err[i] = m[i];
+    g_nn_err[i] = 0;
+    return CDF_NN_ECUDA;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *cdf_nn_last_error(void) { return g_nn_err; }
+
+cdf_nn_status cdf_nn_conv3x3_fwd(const void *x, const void *w, const float *bias, void *y, int N, int H, int W,
+                                 int Cin, int Cout, int relu, void *stream) {
+    if (!x || !w || !y || N < 1 || H < 1 || W < 1 || Cin % 16 || Cout % 32 || Cin < 16)
+        return nn_fail("conv3x3_fwd: bad arguments (Cin % 16, Cout % 32)");
+    const long long P = (long long)N * H * W;
+    const int BN = Cout % 64 == 0 ? 64 : 32;
+    dim3 grid((unsigned)((P + kBM - 1) / kBM), Cout / BN);
+    auto s = static_cast<cudaStream_t>(stream);
+    const auto *xi = static_cast<const __nv_bfloat16 *>(x);
+    const auto *wi = static_cast<const __nv_bfloat16 *>(w);
+    auto *yo = static_cast<__nv_bfloat16 *>(y);
+    if (BN == 64) conv3x3_kernel<false, 64><<<grid, kThreads, 0, s>>>(xi, wi, bias, yo, N, H, W, Cin, Cout, relu);
+    else conv3x3_kernel<false, 32><<<grid, kThreads, 0, s>>>(xi, wi, bias, yo, N, H, W, Cin, Cout, relu);
+    return launched();
+}
+
+cdf_nn_status cdf_nn_conv3x3_bwd_data(const void *dy, const void *w, void *dx, int N, int H, int W, int Cin, int Cout,
+                                      void *stream) {
+    if (!dy || !w || !dx || N < 1 || H < 1 || W < 1 || Cin % 16 || Cout % 32)
+        return nn_fail("conv3x3_bwd_data: bad arguments (Cin % 16, Cout % 32)");
+    const long long P = (long long)N * H * W;
+    const int BN = Cin % 64 == 0 ? 64 : (Cin % 32 == 0 ? 32 : 16);
+    dim3 grid((unsigned)((P + kBM - 1) / kBM), Cin / BN);
+    auto s = static_cast<cudaStream_t>(stream);
+    const auto *di = static_cast<const __nv_bfloat16 *>(dy);
+    const auto *wi = static_cast<const __nv_bfloat16 *>(w);
+    auto *xo = static_cast<__nv_bfloat16 *>(dx);
+    if (BN == 64) conv3x3_kernel<true, 64><<<grid, kThreads, 0, s>>>(di, wi, nullptr, xo, N, H, W, Cout, Cin, 0);
+    else if (BN == 32) conv3x3_kernel<true, 32><<<grid, kThreads, 0, s>>>(di, wi, nullptr, xo, N, H, W, Cout, Cin, 0);
+    else conv3x3_kernel<true, 16><<<grid, kThreads, 0, s>>>(di, wi, nullptr, xo, N, H, W, Cout, Cin, 0);
+    return launched();
+}
+
+cdf_nn_status cdf_nn_conv3x3_bwd_weight(const void *x, const void *dy, float *dw, float *db, int N, int H, int W,
+                                        int Cin, int Cout, void *stream) {
+    if (!x || !dy || !dw || N < 1 || H < 1 || W < 1 || Cin % 16 || Cout % 32)
+        return nn_fail("conv3x3_bwd_weight: bad arguments (Cin % 16, Cout % 32)");
+    const long long P = (long long)N * H * W;
+    const long long per = 4096;
+    dim3 grid((unsigned)((Cout + kWBM - 1) / kWBM), 9 * (Cin / 16), (unsigned)((P + per - 1) / per));
+    auto s = static_cast<cudaStream_t>(stream);
+    conv3x3_wgrad_kernel<<<grid, kThreads, 0, s>>>(static_cast<const __nv_bfloat16 *>(x),
+                                                   static_cast<const __nv_bfloat16 *>(dy), dw, N, H, W, Cin, Cout, per);
+    if (db) {
+        dim3 g2(Cout / 8, (unsigned)((P + 256 * 64 - 1) / (256 * 64)));
+        bias_grad_kernel<<<g2, 256, 0, s>>>(static_cast<const __nv_bfloat16 *>(dy), db, P, Cout);
+    }
+    return launched();
+}
+
+cdf_nn_status cdf_nn_relu_bwd(void *d, const void *y, long long n, void *stream) {
+    if (!d || !y || n < 0) return nn_fail("relu_bwd: bad arguments");
+    if (n) relu_bwd_kernel<<<blocks_for(n), 256, 0, static_cast<cudaStream_t>(stream)>>>(
+        static_cast<__nv_bfloat16 *>(d), static_cast<const __nv_bfloat16 *>(y), n);
+    return launched();
+}
+
+cdf_nn_status cdf_nn_avgpool2_fwd(const void *x, void *y, int N, int H, int W, int C, void *stream) {
+    if (!x || !y || H % 2 || W % 2) return nn_fail("avgpool2: H and W must be even");
+    const long long n = (long long)N * (H / 2) * (W / 2) * C;
+    avgpool2_fwd_kernel<<<blocks_for(n), 256, 0, static_cast<cudaStream_t>(stream)>>>(
+        static_cast<const __nv_bfloat16 *>(x), static_cast<__nv_bfloat16 *>(y), N, H, W, C);
+    return launched();
+}
+
+cdf_nn_status cdf_nn_avgpool2_bwd(const void *dy, void *dx, int N, int H, int W, int C, void *stream) {
+    if (!dy || !dx || H % 2 || W % 2) return nn_fail("avgpool2: H and W must be even");
+    const long long n = (long long)N * H * W * C;
+    avgpool2_bwd_kernel<<<blocks_for(n), 256, 0, static_cast<cudaStream_t>(stream)>>>(
+        static_cast<const __nv_bfloat16 *>(dy), static_cast<__nv_bfloat16 *>(dx), N, H, W, C);
+    return launched();
+}
+
+cdf_nn_status cdf_nn_upsample2_fwd(const void *x, void *y, int N, int H, int W, int C, int Cy, int coff, void *stream) {
+    if (!x || !y || coff < 0 || coff + C > Cy) return nn_fail("upsample2: bad channel slice");
+    const long long n = (long long)N * 4 * H * W * C;
+    upsample2_fwd_kernel<<<blocks_for(n), 256, 0, static_cast<cudaStream_t>(stream)>>>(
+        static_cast<const __nv_bfloat16 *>(x), static_cast<__nv_bfloat16 *>(y), N, H, W, C, Cy, coff);
+    return launched();
+}
+
+cdf_nn_status cdf_nn_upsample2_bwd(const void *dy, void *dx, int N, int H, int W, int C, int Cy, int coff, void *stream) {
+    if (!dy || !dx || coff < 0 || coff + C > Cy) return nn_fail("upsample2: bad channel slice");
+    const long long n = (long long)N * H * W * C;
+    upsample2_bwd_kernel<<<blocks_for(n), 256, 0, static_cast<cudaStream_t>(stream)>>>(
+        static_cast<const __nv_bfloat16 *>(dy), static_cast<__nv_bfloat16 *>(dx), N, H, W, C, Cy, coff);
+    return launched();
+}
+
+cdf_nn_status cdf_nn_copy_channels(const void *x, void *y, long long P, int Cx, int Cy, int src_off, int dst_off,
+                                   int count, int accumulate, void *stream) {
+    if (!x || !y || src_off + count > Cx || dst_off + count > Cy || count < 0) return nn_fail("copy_channels: bad slice");
+    const long long n = P * count;
+    if (n) copy_channels_kernel<<<blocks_for(n), 256, 0, static_cast<cudaStream_t>(stream)>>>(
+        static_cast<const __nv_bfloat16 *>(x), static_cast<__nv_bfloat16 *>(y), P, Cx, Cy, src_off, dst_off, count,
+        accumulate);
+    return launched();
+}
+
+cdf_nn_status cdf_nn_head_fwd(const void *x, const float *w, const float *b, float *out, long long P, int C, int O,
+                              void *stream) {
+    if (!x || !w || !b || !out) return nn_fail("head_fwd: NULL argument");
+    head_fwd_kernel<<<blocks_for(P * O), 256, 0, static_cast<cudaStream_t>(stream)>>>(
+        static_cast<const __nv_bfloat16 *>(x), w, b, out, P, C, O);
+    return launched();
+}
+
+cdf_nn_status cdf_nn_head_bwd(const void *x, const float *w, const float *dout, void *dx, float *dw, float *db,
+                              long long P, int C, int O, void *stream) {
+    if (!x || !w || !dout || !dx || !dw || !db) return nn_fail("head_bwd: NULL argument");
+    auto s = static_cast<cudaStream_t>(stream);
+    head_bwd_data_kernel<<<blocks_for(P * C), 256, 0, s>>>(dout, w, static_cast<__nv_bfloat16 *>(dx), P, C, O);
+    dim3 g((unsigned)(O * (C + 1)), (unsigned)((P + 256 * 32 - 1) / (256 * 32)));
+    head_bwd_weight_kernel<<<g, 256, 0, s>>>(static_cast<const __nv_bfloat16 *>(x), dout, dw, db, P, C, O);
+    return launched();
+}
+
+cdf_nn_status cdf_nn_mse(const float *pred, const float *target, float *grad, float *loss, long long n, void *stream) {
+    if (!pred || !target || !grad || !loss) return nn_fail("mse: NULL argument");
+    mse_kernel<<<blocks_for(n), 256, 0, static_cast<cudaStream_t>(stream)>>>(pred, target, grad, loss, n);
+    return launched();
+}
+
+cdf_nn_status cdf_nn_adam(float *w, const float *g, float *m, float *v, void *w_bf16, long long n, float lr, float b1,
+                          float b2, float eps, long long step, void *stream) {
+    if (!w || !g || !m || !v || step < 1) return nn_fail("adam: bad arguments");
+    float c1 = 1.f, c2 = 1.f, p1 = 1.f, p2 = 1.f;
+    for (long long i = 0; i < step && i < 100000; ++i) { p1 *= b1; p2 *= b2; }
+    c1 -= p1;
+    c2 -= p2;
+    adam_kernel<<<blocks_for(n), 256, 0, static_cast<cudaStream_t>(stream)>>>(
+        w, g, m, v, static_cast<__nv_bfloat16 *>(w_bf16), n, lr, b1, b2, eps, c1, c2);
+    return launched();
+}
+
+}  // extern "C"

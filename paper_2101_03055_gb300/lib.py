@@ -123,6 +123,8 @@ SIGNATURES = {
     "cdf_batch_step": (ctypes.c_int, [_H, ctypes.c_longlong]),
     "cdf_batch_moments": (ctypes.c_int, [_H, ctypes.c_int, _DP]),
     "cdf_batch_get_info": (ctypes.c_int, [_H, ctypes.POINTER(cdf_batch_info)]),
+    "cdf_batch_snapshot": (ctypes.c_int, [_H]),
+    "cdf_batch_residuals": (ctypes.c_int, [_H, _DP]),
     "cdf_batch_stream": (ctypes.c_void_p, [_H]),
     "cdf_batch_destroy": (None, [_H]),
 }
@@ -404,6 +406,14 @@ def cdf_batch_moments(h, k, out):
     _check(load().cdf_batch_moments(h, k, _dptr(out)))
 
 
+def cdf_batch_snapshot(h):
+    _check(load().cdf_batch_snapshot(h))
+
+
+def cdf_batch_residuals(h, out: np.ndarray):
+    _check(load().cdf_batch_residuals(h, _dptr(out)))
+
+
 def cdf_batch_get_info(h) -> cdf_batch_info:
     info = cdf_batch_info()
     _check(load().cdf_batch_get_info(h, ctypes.byref(info)))
@@ -479,6 +489,31 @@ class BatchSolver:
 
     def info(self) -> cdf_batch_info:
         return cdf_batch_get_info(self.h)
+
+    def residuals_after(self, n: int) -> np.ndarray:
+        """Advance n steps and return each instance's residual over those steps."""
+        cdf_batch_snapshot(self.h)
+        self.step(n)
+        out = np.empty(len(self.problems))
+        cdf_batch_residuals(self.h, out)
+        return out
+
+    def run_to_steady(self, tol: float, check_every: int = 1000, max_steps: int = 10 ** 6):
+        """Step all instances until every residual is below tol (or max_steps);
+        returns (steps taken, residuals, step at which each instance first met tol)."""
+        n = len(self.problems)
+        first = np.full(n, -1, dtype=np.int64)
+        taken = 0
+        R = np.full(n, np.inf)
+        while taken < max_steps:
+            k = min(check_every, max_steps - taken)
+            R = self.residuals_after(k)
+            taken += k
+            newly = (R < tol) & (first < 0)
+            first[newly] = taken
+            if (first >= 0).all():
+                break
+        return taken, R, first
 
     @property
     def stream(self) -> int:

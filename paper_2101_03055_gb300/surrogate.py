@@ -1,0 +1,408 @@
+"""Convolutional surrogate that warm-starts steady solves of the double-diffusive
+cavity (Sec. 3.2 setup), trained on steady states the solver generates itself.
+
+A 4-level U-Net (base 32 channels: 32-64-128-256, two 3x3 convolutions with
+ReLU per level, 2x2 average pooling, nearest upsampling with skip
+concatenation, 1x1 head) maps seven input planes -- log10 Ra, Nc, Le, Sr, Df
+and the node coordinates -- to (u_x, u_y, T, C).  Every layer runs in this
+package's BF16 kernels (include/cdf_nn.h; tensor cores, FP32 accumulation);
+PyTorch only allocates device memory.  The prediction initialises
+cdf_lb_init_moments_device, and the lattice Boltzmann residual decides
+convergence as for a start from rest.
+"""
+from __future__ import annotations
+
+import ctypes
+import math
+import os
+
+import numpy as np
+
+from . import inputs as I
+from . import lib
+
+NN_SIGNATURES = {
+    "cdf_nn_conv3x3_fwd": [ctypes.c_void_p] * 4 + [ctypes.c_int] * 6 + [ctypes.c_void_p],
+    "cdf_nn_conv3x3_bwd_data": [ctypes.c_void_p] * 3 + [ctypes.c_int] * 5 + [ctypes.c_void_p],
+    "cdf_nn_conv3x3_bwd_weight": [ctypes.c_void_p] * 4 + [ctypes.c_int] * 5 + [ctypes.c_void_p],
+    "cdf_nn_relu_bwd": [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_longlong, ctypes.c_void_p],
+    "cdf_nn_avgpool2_fwd": [ctypes.c_void_p] * 2 + [ctypes.c_int] * 4 + [ctypes.c_void_p],
+    "cdf_nn_avgpool2_bwd": [ctypes.c_void_p] * 2 + [ctypes.c_int] * 4 + [ctypes.c_void_p],
+    "cdf_nn_upsample2_fwd": [ctypes.c_void_p] * 2 + [ctypes.c_int] * 6 + [ctypes.c_void_p],
+    "cdf_nn_upsample2_bwd": [ctypes.c_void_p] * 2 + [ctypes.c_int] * 6 + [ctypes.c_void_p],
+    "cdf_nn_copy_channels": [ctypes.c_void_p] * 2 + [ctypes.c_longlong] + [ctypes.c_int] * 6 + [ctypes.c_void_p],
+    "cdf_nn_head_fwd": [ctypes.c_void_p] * 4 + [ctypes.c_longlong, ctypes.c_int, ctypes.c_int, ctypes.c_void_p],
+    "cdf_nn_head_bwd": [ctypes.c_void_p] * 6 + [ctypes.c_longlong, ctypes.c_int, ctypes.c_int, ctypes.c_void_p],
+    "cdf_nn_mse": [ctypes.c_void_p] * 4 + [ctypes.c_longlong, ctypes.c_void_p],
+    "cdf_nn_adam": [ctypes.c_void_p] * 5 + [ctypes.c_longlong] + [ctypes.c_float] * 4 + [ctypes.c_longlong,
+                                                                                         ctypes.c_void_p],
+}
+_nn = None
+
+
+def nn_lib():
+    global _nn
+    if _nn is None:
+        L = lib.load()
+        for name, args in NN_SIGNATURES.items():
+            fn = getattr(L, name)
+            fn.argtypes = args
+            fn.restype = ctypes.c_int
+        L.cdf_nn_last_error.restype = ctypes.c_char_p
+        _nn = L
+    return _nn
+
+
+def _call(name, *args):
+    st = getattr(nn_lib(), name)(*args)
+    if st != 0:
+        raise RuntimeError(f"{name}: {nn_lib().cdf_nn_last_error().decode()}")
+
+
+def _p(t):
+    return ctypes.c_void_p(t.data_ptr()) if t is not None else None
+
+
+def _stream():
+    import torch
+    return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream or None)
+
+
+# ---- thin same-name wrappers of include/cdf_nn.h ----------------------------------------
+def conv3x3_fwd(x, w, b, relu):
+    import torch
+    N, H, W, Cin = x.shape
+    Cout = w.shape[0]
+    y = torch.empty((N, H, W, Cout), dtype=torch.bfloat16, device=x.device)
+    _call("cdf_nn_conv3x3_fwd", _p(x), _p(w), _p(b), _p(y), N, H, W, Cin, Cout, int(relu), _stream())
+    return y
+
+
+def conv3x3_bwd_data(dy, w, Cin):
+    import torch
+    N, H, W, Cout = dy.shape
+    dx = torch.empty((N, H, W, Cin), dtype=torch.bfloat16, device=dy.device)
+    _call("cdf_nn_conv3x3_bwd_data", _p(dy), _p(w), _p(dx), N, H, W, Cin, Cout, _stream())
+    return dx
+
+
+def conv3x3_bwd_weight(x, dy, dw, db):
+    N, H, W, Cin = x.shape
+    Cout = dy.shape[3]
+    _call("cdf_nn_conv3x3_bwd_weight", _p(x), _p(dy), _p(dw), _p(db), N, H, W, Cin, Cout, _stream())
+
+
+def relu_bwd(d, y):
+    _call("cdf_nn_relu_bwd", _p(d), _p(y), d.numel(), _stream())
+
+
+def avgpool2_fwd(x):
+    import torch
+    N, H, W, C = x.shape
+    y = torch.empty((N, H // 2, W // 2, C), dtype=torch.bfloat16, device=x.device)
+    _call("cdf_nn_avgpool2_fwd", _p(x), _p(y), N, H, W, C, _stream())
+    return y
+
+
+def avgpool2_bwd(dy, H, W):
+    import torch
+    N, _, _, C = dy.shape
+    dx = torch.empty((N, H, W, C), dtype=torch.bfloat16, device=dy.device)
+    _call("cdf_nn_avgpool2_bwd", _p(dy), _p(dx), N, H, W, C, _stream())
+    return dx
+
+
+def upsample2_into(x, y, coff):
+    N, H, W, C = x.shape
+    _call("cdf_nn_upsample2_fwd", _p(x), _p(y), N, H, W, C, y.shape[3], coff, _stream())
+
+
+def upsample2_bwd_from(dy, C, coff):
+    import torch
+    N, H2, W2, Cy = dy.shape
+    dx = torch.empty((N, H2 // 2, W2 // 2, C), dtype=torch.bfloat16, device=dy.device)
+    _call("cdf_nn_upsample2_bwd", _p(dy), _p(dx), N, H2 // 2, W2 // 2, C, Cy, coff, _stream())
+    return dx
+
+
+def copy_channels(x, y, src_off, dst_off, count, accumulate=False):
+    P = x.numel() // x.shape[-1]
+    _call("cdf_nn_copy_channels", _p(x), _p(y), P, x.shape[-1], y.shape[-1], src_off, dst_off, count,
+          int(accumulate), _stream())
+
+
+def head_fwd(x, w, b):
+    import torch
+    N, H, W, C = x.shape
+    O = w.shape[0]
+    out = torch.empty((N, H, W, O), dtype=torch.float32, device=x.device)
+    _call("cdf_nn_head_fwd", _p(x), _p(w), _p(b), _p(out), N * H * W, C, O, _stream())
+    return out
+
+
+def head_bwd(x, w, dout, dw, db):
+    import torch
+    N, H, W, C = x.shape
+    O = w.shape[0]
+    dx = torch.empty((N, H, W, C), dtype=torch.bfloat16, device=x.device)
+    _call("cdf_nn_head_bwd", _p(x), _p(w), _p(dout), _p(dx), _p(dw), _p(db), N * H * W, C, O, _stream())
+    return dx
+
+
+def mse(pred, target):
+    import torch
+    grad = torch.empty_like(pred)
+    loss = torch.zeros(1, dtype=torch.float32, device=pred.device)
+    _call("cdf_nn_mse", _p(pred), _p(target), _p(grad), _p(loss), pred.numel(), _stream())
+    return loss, grad
+
+
+def adam(w, g, m, v, w_bf16, lr, step, b1=0.9, b2=0.999, eps=1e-8):
+    _call("cdf_nn_adam", _p(w), _p(g), _p(m), _p(v), _p(w_bf16), w.numel(), lr, b1, b2, eps, step, _stream())
+
+
+# ---- the network ----------------------------------------------------------------------------
+IN_PLANES = 7
+IN_PAD = 16
+OUT_PLANES = 4
+
+
+class UNet:
+    """4-level U-Net; parameter names follow the FP64 oracle (e{L}a/b, d{L}a/b, head)."""
+
+    def __init__(self, base: int = 32, levels: int = 4, cin: int = IN_PAD, cout: int = OUT_PLANES, seed: int = 0):
+        import torch
+        self.levels, self.cin, self.cout = levels, cin, cout
+        self.ch = [base * 2 ** L for L in range(levels)]
+        g = torch.Generator().manual_seed(seed)
+        shapes = {}
+        prev = cin
+        for L, c in enumerate(self.ch):
+            shapes[f"e{L}a"] = (c, prev)
+            shapes[f"e{L}b"] = (c, c)
+            prev = c
+        for L in range(levels - 2, -1, -1):
+            shapes[f"d{L}a"] = (self.ch[L], self.ch[L + 1] + self.ch[L])
+            shapes[f"d{L}b"] = (self.ch[L], self.ch[L])
+        self.conv_names = list(shapes)
+        self.shapes = shapes
+        self.master, self.bf16, self.m, self.v = {}, {}, {}, {}
+        for name, (co, ci) in shapes.items():
+            fan_in = 9 * ci
+            w = torch.randn((co, 3, 3, ci), generator=g) * math.sqrt(2.0 / fan_in)
+            self.master[name + ".w"] = w.cuda()
+            self.master[name + ".b"] = torch.zeros(co).cuda()
+        self.master["head.w"] = (torch.randn((cout, self.ch[0]), generator=g) * math.sqrt(1.0 / self.ch[0])).cuda()
+        self.master["head.b"] = torch.zeros(cout).cuda()
+        for k, t in self.master.items():
+            self.m[k] = torch.zeros_like(t)
+            self.v[k] = torch.zeros_like(t)
+            if k.endswith(".w") and not k.startswith("head"):
+                self.bf16[k] = t.to(torch.bfloat16)
+        self.step_count = 0
+
+    # forward: returns FP32 output [N, H, W, cout] and the activations the backward needs
+    def forward(self, x):
+        acts = {}
+        h = x
+        skips = []
+        for L in range(self.levels):
+            if L > 0:
+                h = avgpool2_fwd(h)
+            acts[f"e{L}.in"] = h
+            h1 = conv3x3_fwd(h, self.bf16[f"e{L}a.w"], self.master[f"e{L}a.b"], True)
+            h2 = conv3x3_fwd(h1, self.bf16[f"e{L}b.w"], self.master[f"e{L}b.b"], True)
+            acts[f"e{L}a"], acts[f"e{L}b"] = h1, h2
+            skips.append(h2)
+            h = h2
+        import torch
+        for L in range(self.levels - 2, -1, -1):
+            N, Hh, Ww, C = h.shape
+            cat = torch.empty((N, 2 * Hh, 2 * Ww, C + self.ch[L]), dtype=torch.bfloat16, device=h.device)
+            upsample2_into(h, cat, 0)
+            copy_channels(skips[L], cat, 0, C, self.ch[L])
+            acts[f"d{L}.cat"] = cat
+            h1 = conv3x3_fwd(cat, self.bf16[f"d{L}a.w"], self.master[f"d{L}a.b"], True)
+            h2 = conv3x3_fwd(h1, self.bf16[f"d{L}b.w"], self.master[f"d{L}b.b"], True)
+            acts[f"d{L}a"], acts[f"d{L}b"] = h1, h2
+            h = h2
+        acts["head.in"] = h
+        return head_fwd(h, self.master["head.w"], self.master["head.b"]), acts
+
+    def backward(self, acts, dout):
+        import torch
+        grads = {k: torch.zeros_like(t) for k, t in self.master.items()}
+        dh = head_bwd(acts["head.in"], self.master["head.w"], dout, grads["head.w"], grads["head.b"])
+        dskip = [None] * self.levels
+        for L in range(0, self.levels - 1):
+            dh, dskip[L] = self._block_bwd(f"d{L}", acts[f"d{L}.cat"], acts, dh, grads, split=self.ch[L])
+        for L in range(self.levels - 1, -1, -1):
+            if dskip[L] is not None:
+                copy_channels(dskip[L], dh, 0, 0, self.ch[L], accumulate=True)
+            dx, _ = self._block_bwd(f"e{L}", acts[f"e{L}.in"], acts, dh, grads, split=None)
+            if L > 0:
+                N, H, W, C = acts[f"e{L - 1}b"].shape
+                dh = avgpool2_bwd(dx, H, W)
+        return grads
+
+    def _block_bwd(self, name, x_in, acts, dh, grads, split):
+        # second conv
+        relu_bwd(dh, acts[f"{name}b"])
+        conv3x3_bwd_weight(acts[f"{name}a"], dh, grads[f"{name}b.w"], grads[f"{name}b.b"])
+        d1 = conv3x3_bwd_data(dh, self.bf16[f"{name}b.w"], acts[f"{name}a"].shape[3])
+        relu_bwd(d1, acts[f"{name}a"])
+        conv3x3_bwd_weight(x_in, d1, grads[f"{name}a.w"], grads[f"{name}a.b"])
+        dx = conv3x3_bwd_data(d1, self.bf16[f"{name}a.w"], x_in.shape[3])
+        if split is None:
+            return dx, None
+        cup = x_in.shape[3] - split
+        import torch
+        dskip = torch.empty((*dx.shape[:3], split), dtype=torch.bfloat16, device=dx.device)
+        copy_channels(dx, dskip, cup, 0, split)
+        return upsample2_bwd_from(dx, cup, 0), dskip
+
+    def adam_step(self, grads, lr):
+        self.step_count += 1
+        for k, w in self.master.items():
+            adam(w, grads[k], self.m[k], self.v[k], self.bf16.get(k), lr, self.step_count)
+
+    def state(self):
+        return {k: t.detach().cpu().numpy() for k, t in self.master.items()}
+
+    def load_state(self, st):
+        import torch
+        for k, v in st.items():
+            self.master[k].copy_(torch.as_tensor(v))
+            if k in self.bf16:
+                self.bf16[k].copy_(self.master[k].to(torch.bfloat16))
+
+
+# ---- data: steady cavity states from the solver ---------------------------------------------
+U_SCALE = 0.1 * math.sqrt(1.0 / 3.0)  # the buoyancy velocity of the lattice mapping (Ma = 0.1)
+
+
+def draw_parameters(count: int, seed: int):
+    """Ra ~ logU[1e4, 1e6], Nc ~ U[-2, 2], Le ~ U[1, 10], Sr, Df ~ U[0, 0.5] (counters 8k..8k+4)."""
+    out = []
+    for k in range(count):
+        u = I.uniform(seed, np.arange(8 * k, 8 * k + 5))
+        out.append(dict(Ra=10 ** (4 + 2 * u[0]), Nc=-2 + 4 * u[1], Le=1 + 9 * u[2], Sr=0.5 * u[3], Df=0.5 * u[4]))
+    return out
+
+
+def cavity(n: int, prm) -> I.Problem:
+    return I.ddc_cavity(n, Ra=prm["Ra"], Pr=0.7, Le=prm["Le"], Nc=prm["Nc"], Df=prm["Df"], Sr=prm["Sr"])
+
+
+def input_planes(n: int, prms) -> np.ndarray:
+    """[N, n, n, IN_PAD] float32 inputs: log10 Ra - 5, Nc / 2, (Le - 5.5) / 4.5, 4 Sr - 1, 4 Df - 1, x, y."""
+    N = len(prms)
+    x = np.zeros((N, n, n, IN_PAD), np.float32)
+    c = (np.arange(n) + 0.5) / n
+    for k, prm in enumerate(prms):
+        x[k, :, :, 0] = math.log10(prm["Ra"]) - 5
+        x[k, :, :, 1] = prm["Nc"] / 2
+        x[k, :, :, 2] = (prm["Le"] - 5.5) / 4.5
+        x[k, :, :, 3] = 4 * prm["Sr"] - 1
+        x[k, :, :, 4] = 4 * prm["Df"] - 1
+        x[k, :, :, 5] = c[None, :]
+        x[k, :, :, 6] = c[:, None]
+    return x
+
+
+def targets_from_moments(M) -> np.ndarray:
+    """(u_x / U, u_y / U, T - 1/2, C - 1/2) from a moment stack [m+3][ny][nx]."""
+    return np.stack([M[2] / U_SCALE, M[3] / U_SCALE, M[0] - 0.5, M[1] - 0.5], axis=-1).astype(np.float32)
+
+
+def moments_from_prediction(y) -> np.ndarray:
+    """Inverse of targets_from_moments for one sample [n, n, 4] -> [5][n][n] (p = 0)."""
+    n = y.shape[0]
+    M = np.zeros((5, n, n))
+    M[0], M[1] = y[..., 2] + 0.5, y[..., 3] + 0.5
+    M[2], M[3] = y[..., 0] * U_SCALE, y[..., 1] * U_SCALE
+    return M
+
+
+def generate_steady_states(prms, n: int, tol: float, check_every: int = 2000, max_steps: int = 600_000):
+    """Run every cavity from rest with the batched solver until its residual is below
+    tol; returns (moment stacks, steps to tol per case (-1: not converged))."""
+    pbs = [cavity(n, prm) for prm in prms]
+    b = lib.BatchSolver(pbs)
+    steps, R, first = b.run_to_steady(tol, check_every, max_steps)
+    Ms = [b.moments(k) for k in range(len(pbs))]
+    b.close()
+    return Ms, first, R
+
+
+def train(net: UNet, x, y, epochs: int, batch: int, lr: float, seed: int = 0, log=None):
+    """x: torch bf16 [S, n, n, 16], y: torch fp32 [S, n, n, 4]; plain Adam with a cosine decay."""
+    import torch
+    S = x.shape[0]
+    r = np.random.default_rng(seed)
+    steps_per_epoch = max(1, S // batch)
+    total = epochs * steps_per_epoch
+    it = 0
+    hist = []
+    for ep in range(epochs):
+        perm = torch.as_tensor(r.permutation(S), device=x.device)
+        ep_loss = 0.0
+        for s in range(steps_per_epoch):
+            idx = perm[s * batch:(s + 1) * batch]
+            xb, yb = x.index_select(0, idx).contiguous(), y.index_select(0, idx).contiguous()
+            out, acts = net.forward(xb)
+            loss, dout = mse(out, yb)
+            grads = net.backward(acts, dout)
+            cur = lr * 0.5 * (1 + math.cos(math.pi * it / total))
+            net.adam_step(grads, cur)
+            ep_loss += float(loss.item())
+            it += 1
+        hist.append(ep_loss / steps_per_epoch)
+        if log:
+            log(f"epoch {ep}: loss {hist[-1]:.4e}")
+    return hist
+
+
+def predict(net: UNet, x, batch: int = 64):
+    import torch
+    outs = []
+    for s in range(0, x.shape[0], batch):
+        out, _ = net.forward(x[s:s + batch].contiguous())
+        outs.append(out)
+    return torch.cat(outs)
+
+
+def warm_start_comparison(net: UNet, prms, n: int, tol: float, check_every: int = 2000, max_steps: int = 600_000):
+    """Steps to tol for each case from rest and from the network's prediction, both
+    with the batched solver; also the relative L2 between the two final states."""
+    import torch
+    x = torch.as_tensor(input_planes(n, prms)).cuda().to(torch.bfloat16)
+    pred = predict(net, x).float().cpu().numpy()
+    pbs_cold = [cavity(n, prm) for prm in prms]
+    pbs_warm = []
+    for k, prm in enumerate(prms):
+        M = moments_from_prediction(pred[k])
+        pb = cavity(n, prm)
+        pbs_warm.append(pb.replace(phi0=M[:2].copy(), u0=M[2:4].copy(), p0=M[4].copy()))
+    out = {}
+    for name, pbs in (("cold", pbs_cold), ("warm", pbs_warm)):
+        b = lib.BatchSolver(pbs)
+        torch.cuda.synchronize()
+        import time
+        t0 = time.perf_counter()
+        steps, R, first = b.run_to_steady(tol, check_every, max_steps)
+        torch.cuda.synchronize()
+        out[name] = dict(first=first, R=R, seconds=time.perf_counter() - t0, total_steps=steps,
+                         moments=[b.moments(k) for k in range(len(pbs))])
+        b.close()
+    diffs = []
+    for k in range(len(prms)):
+        a, c = out["warm"]["moments"][k], out["cold"]["moments"][k]
+        diffs.append(max(np.linalg.norm(a[q] - c[q]) / max(np.linalg.norm(c[q]), 1e-30) for q in range(4)))
+    out["final_rel_l2"] = np.array(diffs)
+    out["prediction"] = pred
+    return out
+
+
+def default_model_path():
+    return os.path.join(os.path.dirname(os.path.abspath(__file__)), "surrogate_cavity64.npz")
