@@ -326,9 +326,10 @@ def moments_from_prediction(y) -> np.ndarray:
 
 def generate_steady_states(prms, n: int, tol: float, check_every: int = 2000, max_steps: int = 600_000):
     """Run every cavity from rest with the batched solver until its residual is below
-    tol; returns (moment stacks, steps to tol per case (-1: not converged))."""
+    tol; returns (moment stacks, steps to tol per case (-1: not converged), residuals).
+    Many small lattices: the persistent kernel (one launch for all of them)."""
     pbs = [cavity(n, prm) for prm in prms]
-    b = lib.BatchSolver(pbs)
+    b = lib.BatchSolver(pbs, tile=(64, 4), mode=0)
     steps, R, first = b.run_to_steady(tol, check_every, max_steps)
     Ms = [b.moments(k) for k in range(len(pbs))]
     b.close()
@@ -386,7 +387,7 @@ def warm_start_comparison(net: UNet, prms, n: int, tol: float, check_every: int 
         pbs_warm.append(pb.replace(phi0=M[:2].copy(), u0=M[2:4].copy(), p0=M[4].copy()))
     out = {}
     for name, pbs in (("cold", pbs_cold), ("warm", pbs_warm)):
-        b = lib.BatchSolver(pbs)
+        b = lib.BatchSolver(pbs, tile=(64, 4), mode=0)
         torch.cuda.synchronize()
         import time
         t0 = time.perf_counter()
@@ -406,3 +407,68 @@ def warm_start_comparison(net: UNet, prms, n: int, tol: float, check_every: int 
 
 def default_model_path():
     return os.path.join(os.path.dirname(os.path.abspath(__file__)), "surrogate_cavity64.npz")
+
+
+def run_experiment(n=64, train_count=1000, eval_count=100, tol=1e-6, epochs=60, batch=32, lr=2e-3,
+                   max_steps=600_000, check_every=2000, seed=0, log=print):
+    """Generate steady states, train the U-Net, and compare warm with cold starts on
+    held-out parameters.  Returns a JSON-ready summary."""
+    import time
+    import torch
+    t0 = time.perf_counter()
+    prms = draw_parameters(train_count, seed)
+    Ms, first, R = generate_steady_states(prms, n, tol, check_every, max_steps)
+    keep = [k for k in range(train_count) if first[k] >= 0]
+    t_data = time.perf_counter() - t0
+    log(f"data: {len(keep)}/{train_count} converged to {tol:g} in {t_data:.1f} s; "
+        f"median steps {int(np.median(first[keep])) if keep else -1}")
+    x = torch.as_tensor(input_planes(n, [prms[k] for k in keep])).cuda().to(torch.bfloat16)
+    y = torch.as_tensor(np.stack([targets_from_moments(Ms[k]) for k in keep])).cuda()
+    net = UNet(seed=seed)
+    torch.cuda.synchronize()
+    t1 = time.perf_counter()
+    hist = train(net, x, y, epochs, batch, lr, seed, log=None)
+    torch.cuda.synchronize()
+    t_train = time.perf_counter() - t1
+    log(f"train: {epochs} epochs on {len(keep)} states in {t_train:.1f} s, loss {hist[0]:.3e} -> {hist[-1]:.3e}")
+    eprm = draw_parameters(eval_count, seed + 1)
+    res = warm_start_comparison(net, eprm, n, tol, check_every, max_steps)
+    cold, warm = res["cold"]["first"], res["warm"]["first"]
+    both = (cold >= 0) & (warm >= 0)
+    ratio = warm[both] / np.maximum(cold[both], 1)
+    summary = {
+        "n": n, "train_requested": train_count, "train_converged": len(keep), "eval": eval_count, "tol": tol,
+        "data_seconds": t_data, "train_seconds": t_train, "epochs": epochs, "loss_first": hist[0],
+        "loss_last": hist[-1],
+        "eval_converged_cold": int((cold >= 0).sum()), "eval_converged_warm": int((warm >= 0).sum()),
+        "median_steps_cold": float(np.median(cold[both])) if both.any() else None,
+        "median_steps_warm": float(np.median(warm[both])) if both.any() else None,
+        "median_step_ratio_warm_over_cold": float(np.median(ratio)) if both.any() else None,
+        "fraction_warm_faster": float((ratio < 1).mean()) if both.any() else None,
+        "seconds_cold_batch": res["cold"]["seconds"], "seconds_warm_batch": res["warm"]["seconds"],
+        "max_final_rel_l2_warm_vs_cold": float(res["final_rel_l2"][both].max()) if both.any() else None,
+        "median_final_rel_l2_warm_vs_cold": float(np.median(res["final_rel_l2"][both])) if both.any() else None,
+    }
+    log(str(summary))
+    return summary, net
+
+
+if __name__ == "__main__":
+    import argparse
+    import json
+    ap = argparse.ArgumentParser(description="surrogate warm-start experiment on the double-diffusive cavity")
+    ap.add_argument("--n", type=int, default=64)
+    ap.add_argument("--train", type=int, default=1000)
+    ap.add_argument("--eval", type=int, default=100)
+    ap.add_argument("--tol", type=float, default=1e-6)
+    ap.add_argument("--epochs", type=int, default=60)
+    ap.add_argument("--max-steps", type=int, default=600_000)
+    ap.add_argument("--out", default="")
+    a = ap.parse_args()
+    from . import build
+    build.build()
+    summ, net = run_experiment(a.n, a.train, a.eval, a.tol, a.epochs, max_steps=a.max_steps)
+    if a.out:
+        with open(a.out, "w") as fh:
+            json.dump(summ, fh, indent=1)
+        np.savez(a.out.replace(".json", "_model.npz"), **net.state())
