@@ -315,12 +315,17 @@ def targets_from_moments(M) -> np.ndarray:
     return np.stack([M[2] / U_SCALE, M[3] / U_SCALE, M[0] - 0.5, M[1] - 0.5], axis=-1).astype(np.float32)
 
 
-def moments_from_prediction(y) -> np.ndarray:
-    """Inverse of targets_from_moments for one sample [n, n, 4] -> [5][n][n] (p = 0)."""
+def moments_from_prediction(y, pb=None) -> np.ndarray:
+    """Inverse of targets_from_moments for one sample [n, n, 4] -> [5][n][n]; with the
+    problem given, p is the hydrostatic pressure of the predicted buoyancy (dp/dy = F_y)."""
     n = y.shape[0]
     M = np.zeros((5, n, n))
     M[0], M[1] = y[..., 2] + 0.5, y[..., 3] + 0.5
     M[2], M[3] = y[..., 0] * U_SCALE, y[..., 1] * U_SCALE
+    if pb is not None:
+        Fy = pb.g[1] * (pb.F0 + sum(pb.beta[a] * (M[a] - pb.phi_ref[a]) for a in range(2)))
+        p = np.cumsum(Fy, axis=0) - 0.5 * Fy
+        M[4] = p - p.mean()
     return M
 
 
@@ -382,8 +387,8 @@ def warm_start_comparison(net: UNet, prms, n: int, tol: float, check_every: int 
     pbs_cold = [cavity(n, prm) for prm in prms]
     pbs_warm = []
     for k, prm in enumerate(prms):
-        M = moments_from_prediction(pred[k])
         pb = cavity(n, prm)
+        M = moments_from_prediction(pred[k], pb)
         pbs_warm.append(pb.replace(phi0=M[:2].copy(), u0=M[2:4].copy(), p0=M[4].copy()))
     out = {}
     for name, pbs in (("cold", pbs_cold), ("warm", pbs_warm)):
@@ -409,8 +414,8 @@ def default_model_path():
     return os.path.join(os.path.dirname(os.path.abspath(__file__)), "surrogate_cavity64.npz")
 
 
-def run_experiment(n=64, train_count=1000, eval_count=100, tol=1e-6, epochs=60, batch=32, lr=2e-3,
-                   max_steps=600_000, check_every=2000, seed=0, log=print):
+def run_experiment(n=64, train_count=2000, eval_count=200, tol=1e-6, epochs=100, batch=32, lr=2e-3,
+                   max_steps=2_000_000, check_every=10_000, seed=0, log=print):
     """Generate steady states, train the U-Net, and compare warm with cold starts on
     held-out parameters.  Returns a JSON-ready summary."""
     import time
@@ -448,8 +453,13 @@ def run_experiment(n=64, train_count=1000, eval_count=100, tol=1e-6, epochs=60, 
         "seconds_cold_batch": res["cold"]["seconds"], "seconds_warm_batch": res["warm"]["seconds"],
         "max_final_rel_l2_warm_vs_cold": float(res["final_rel_l2"][both].max()) if both.any() else None,
         "median_final_rel_l2_warm_vs_cold": float(np.median(res["final_rel_l2"][both])) if both.any() else None,
+        "check_every": check_every, "max_steps": max_steps,
+        "train_cases": [dict(prms[k], steps=int(first[k]), R=float(R[k])) for k in range(train_count)],
+        "eval_cases": [dict(eprm[k], steps_cold=int(cold[k]), steps_warm=int(warm[k]),
+                            R_cold=float(res["cold"]["R"][k]), R_warm=float(res["warm"]["R"][k]),
+                            final_rel_l2=float(res["final_rel_l2"][k])) for k in range(eval_count)],
     }
-    log(str(summary))
+    log(str({k: v for k, v in summary.items() if not k.endswith("_cases")}))
     return summary, net
 
 
@@ -458,16 +468,18 @@ if __name__ == "__main__":
     import json
     ap = argparse.ArgumentParser(description="surrogate warm-start experiment on the double-diffusive cavity")
     ap.add_argument("--n", type=int, default=64)
-    ap.add_argument("--train", type=int, default=1000)
-    ap.add_argument("--eval", type=int, default=100)
+    ap.add_argument("--train", type=int, default=2000)
+    ap.add_argument("--eval", type=int, default=200)
     ap.add_argument("--tol", type=float, default=1e-6)
-    ap.add_argument("--epochs", type=int, default=60)
-    ap.add_argument("--max-steps", type=int, default=600_000)
+    ap.add_argument("--epochs", type=int, default=100)
+    ap.add_argument("--max-steps", type=int, default=2_000_000)
+    ap.add_argument("--check-every", type=int, default=10_000)
     ap.add_argument("--out", default="")
     a = ap.parse_args()
     from . import build
     build.build()
-    summ, net = run_experiment(a.n, a.train, a.eval, a.tol, a.epochs, max_steps=a.max_steps)
+    summ, net = run_experiment(a.n, a.train, a.eval, a.tol, a.epochs, max_steps=a.max_steps,
+                               check_every=a.check_every)
     if a.out:
         with open(a.out, "w") as fh:
             json.dump(summ, fh, indent=1)
