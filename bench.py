@@ -86,7 +86,7 @@ def measured_peaks():
 
 def kernel_source_hash() -> str:
     h = hashlib.sha256()
-    for f in ("lb_kernels.cu", "lb_device.cuh", "lb_internal.h"):
+    for f in ("lb_kernels.cu", "lb_device.cuh", "lb_internal.h", "lb_resident.cu"):
         with open(os.path.join(ROOT, "paper_2101_03055_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -161,7 +161,21 @@ class _Single:
         self.nodes, self.bytes_per_lup, self.storage = pb.nodes, info.bytes_per_lup, info.storage
         self.block = [info.block_x, info.block_y]
         self.m = pb.m
-        self.kernel = f"step_kernel<{pb.m},{ {0: 'float', 1: '__half', 2: '__nv_bfloat16'}[info.storage]}>"
+        self.resident = bool(info.resident)
+        if self.resident:
+            self.block = [info.tile_x, info.tile_y]
+            self.kernel = (f"resident_kernel<{pb.m}> (tile-resident persistent step, {info.tiles} CTAs of "
+                           f"{info.tile_x}x{info.tile_y} nodes)")
+        else:
+            self.kernel = f"step_kernel<{pb.m},{ {0: 'float', 1: '__half', 2: '__nv_bfloat16'}[info.storage]}>"
+
+    def steps_per_launch(self, n):
+        """Lattice steps per kernel launch inside step(n)."""
+        return min(n, RESIDENT_MAX_STEPS) if self.resident else 1
+
+    def launches(self, n):
+        """Kernels of this package launched by step(n)."""
+        return -(-n // RESIDENT_MAX_STEPS) if self.resident else n
 
     stream = property(lambda self: self.s.stream)
 
@@ -175,6 +189,9 @@ class _Single:
         out = np.empty((pb.m + 3, pb.ny, pb.nx))
         self.lib.cdf_lb_moments(self.s.h, out)
         return 2 * (pb.m + 3) * pb.nodes * 4
+
+
+RESIDENT_MAX_STEPS = 4096  # steps per launch of the tile-resident step
 
 
 class _Batch:
@@ -194,6 +211,17 @@ class _Batch:
         else:
             self.kernel = (f"batch_kernel<{self.m}> (persistent, {info.grid_blocks} CTAs, "
                            f"{info.steps_per_launch} steps/launch)")
+        self.mode = info.mode
+        self.count = info.count
+        self.spl = info.steps_per_launch
+
+    def steps_per_launch(self, n):
+        """Lattice steps per launch of the dominant kernel inside step(n) (chains:
+        one lattice step of one instance, counted here per whole sweep step)."""
+        return 1 if self.mode == 1 else min(n, self.spl)
+
+    def launches(self, n):
+        return n * self.count if self.mode == 1 else -(-n // self.spl)
 
     stream = property(lambda self: self.s.stream)
 
@@ -367,8 +395,9 @@ def main():
     stage_bytes = moved // 2
 
     peak, peak_kind = measured_peaks()
-    bytes_per_launch = runner.bytes_per_lup * nodes
-    launch_s = t_ms * 1e-3 / (S * K)
+    spl = runner.steps_per_launch(S)
+    bytes_per_launch = runner.bytes_per_lup * nodes * spl
+    launch_s = t_ms * 1e-3 / (S * K) * spl
     achieved = bytes_per_launch / launch_s / 1e9
     traffic = recorded_traffic(args.workload)
 
@@ -395,8 +424,8 @@ def main():
                      "frac": achieved / peak, "traffic": traffic,
                      "peak_source": f"{peak_kind} copy bandwidth (MEASURED_PEAKS.json hbm_gbs)",
                      "bytes_per_lup": runner.bytes_per_lup, "kernel": runner.kernel,
-                     "launch_us": launch_s * 1e6},
-        "gpu_launches": S * K,
+                     "launch_us": launch_s * 1e6, "lattice_steps_per_launch": spl},
+        "gpu_launches": runner.launches(S) * K,
         "clocks": clk.summary(),
         "wall_s": wall,
     }

@@ -122,6 +122,15 @@ typedef struct {
     double p_ref_grad[2];              /* reference pressure gradient (used along walled axes only) */
     int block_x, block_y;              /* step kernel CTA shape; block_x = 0: autotuned;
                                           block_y = 0: flat launch of block_x threads (FP32) */
+    int resident;                      /* tile-resident persistent step (FP32, lattices that fit
+                                          in shared memory, about 150 k nodes for m = 2):
+                                          0 = used when the autotuner measures it faster,
+                                          1 = always (CDF_EINVAL if the lattice does not fit),
+                                          -1 = never */
+    double wait_timeout_s;             /* bound of every wait of the resident step; 0 = 1 s */
+    int test_stall_tile;               /* test hook: k > 0 makes tile k - 1 of the resident step
+                                          never publish its step, so the waits of its neighbours
+                                          run out (CDF_ETIMEOUT); 0 in normal use */
 } cdf_options;
 
 /* Facts about a handle (for benchmarks and tests). */
@@ -131,6 +140,8 @@ typedef struct {
     int planes;                        /* population planes per buffer */
     int sprev_planes;                  /* S(t-1) planes (CONSUMPTION: 1) */
     int block_x, block_y;              /* step kernel CTA shape in use */
+    int resident;                      /* 1 if the tile-resident persistent step is in use */
+    int tile_x, tile_y, tiles;         /* its tile shape (nodes) and number of tiles */
     double bytes_per_lup;              /* minimal HBM bytes moved per node update */
     long long t;                       /* time steps taken since initialisation */
 } cdf_info;

@@ -29,12 +29,6 @@ struct BatchInst {
     int tiles_x;
 };
 
-__device__ __forceinline__ unsigned long long global_ns() {
-    unsigned long long t;
-    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-    return t;
-}
-
 // Grid-wide barrier for a co-resident (cooperative) grid.  bar[0] counts
 // arrivals, bar[1] is the generation.  Every wait is bounded: after timeout_ns
 // (or an iteration cap) the block sets *err and the whole grid gives up.
@@ -54,12 +48,12 @@ __device__ bool grid_barrier(unsigned *bar, unsigned expected, unsigned long lon
             __threadfence();
             atomicAdd(bar + 1, 1u);
         } else {
-            const unsigned long long t0 = global_ns();
+            const unsigned long long t0 = dev::global_ns();
             const unsigned long long cap = timeout_ns / 32ull + (1ull << 20);
             unsigned long long it = 0;
             while (*vgen == gen) {
                 if (*verr) { ok = 0; break; }
-                if (++it > cap || ((it & 63ull) == 0 && global_ns() - t0 > timeout_ns)) {
+                if (++it > cap || ((it & 63ull) == 0 && dev::global_ns() - t0 > timeout_ns)) {
                     atomicExch(err, 1);
                     ok = 0;
                     break;

@@ -6,6 +6,8 @@
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
+#include <utility>
+
 #include "lb_internal.h"
 
 namespace cdflb {
@@ -34,6 +36,13 @@ __host__ __device__ constexpr int kC5x(int i) { return i == 1 ? 1 : (i == 3 ? -1
 __host__ __device__ constexpr int kC5y(int i) { return i == 2 ? 1 : (i == 4 ? -1 : 0); }
 __host__ __device__ constexpr int kC9x(int i) { return (i == 1 || i == 5 || i == 8) ? 1 : ((i == 3 || i == 6 || i == 7) ? -1 : 0); }
 __host__ __device__ constexpr int kC9y(int i) { return (i == 2 || i == 5 || i == 6) ? 1 : ((i == 4 || i == 7 || i == 8) ? -1 : 0); }
+
+// Nanoseconds of the GPU's global timer: the clock of every bounded wait.
+__device__ __forceinline__ unsigned long long global_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
 
 // ---- storage types ---------------------------------------------------------------
 // Populations are stored as deviations from a reference state (below) in FP32,
@@ -75,14 +84,14 @@ __device__ __forceinline__ float load_pop(const T *p) {
 // Eqs. evolution12/evolution3 term by term, with phi = phi_ref + sum_i f'_i,
 // u = sum_i c_i h'_i + F/2 (sum_i c_i h_ref_i = 0) and p = p_ref(x) + p'.
 __device__ __forceinline__ float pref_at(const LbParams &p, int x, int y) {
-    return p.gref[0] * ((float)x - p.xc) + p.gref[1] * ((float)y - p.yc);
+    return fmaf(p.gref[0], (float)x - p.xc, __fmul_rn(p.gref[1], (float)y - p.yc));
 }
 
 __device__ __forceinline__ float cutoff(const LbParams &p, float c) {
     // r(c): step (Sec. 3.1.3) or regularised (Sec. 3.1.2)
     if (p.r_regularised) {
         float d = c - p.c_star;
-        return 0.5f * (1.f + d * rsqrtf(d * d + p.eps2));
+        return 0.5f * fmaf(d, rsqrtf(fmaf(d, d, p.eps2)), 1.f);
     }
     return c >= p.c_star ? 1.f : 0.f;
 }
@@ -100,7 +109,7 @@ struct NodeOut {
 // 16-bit storage so both evaluate it bit for bit the same way.
 __device__ __forceinline__ float feq_dir(int j, float phid, float t3phi, float ux, float uy) {
     const float cu = (j == 1) ? ux : (j == 2) ? uy : (j == 3) ? -ux : -uy;
-    return kW5 * fmaf(t3phi, cu, phid);
+    return __fmul_rn(kW5, fmaf(t3phi, cu, phid));
 }
 
 template <int M>
@@ -115,12 +124,18 @@ __device__ __forceinline__ void scalar_equilibrium(const float (&phid)[M], const
     }
 }
 
+// u.u with a fixed rounding.  The kernels share these device functions but are
+// compiled in different contexts; every multiply-add whose FMA contraction the
+// compiler could decide differently in each context is written out (fmaf,
+// __fmul_rn), so all kernels round identically and agree bit for bit.
+__device__ __forceinline__ float usq_of(float ux, float uy) { return fmaf(ux, ux, __fmul_rn(uy, uy)); }
+
 // Fluid equilibrium deviation (Eq. heq): h^eq_i(p, u) - h^eq_i(p_ref, 0)
 //   = kA_i (p' + c_i.u + 1.5 (c_i.u)^2 - 0.5 u.u)  (i != 0),  -kC p' - kQ u.u  (i = 0).
 __device__ __forceinline__ float fluid_equilibrium(int i, float prd, float ux, float uy, float usq) {
-    if (i == 0) return -kC * prd - kQ * usq;
+    if (i == 0) return fmaf(-kC, prd, __fmul_rn(-kQ, usq));
     const float cu = kC9x(i) * ux + kC9y(i) * uy;
-    return kA9(i) * ((prd + cu) + fmaf(1.5f * cu, cu, -0.5f * usq));
+    return __fmul_rn(kA9(i), (prd + cu) + fmaf(__fmul_rn(1.5f, cu), cu, __fmul_rn(-0.5f, usq)));
 }
 
 // Collision of one node (Eqs. evolution12, evolution3) in deviation variables.
@@ -159,9 +174,9 @@ __device__ __forceinline__ void collide(const LbParams &p, float (&f)[M][5], flo
     const float jx = (h[1] - h[3]) + (h[5] - h[6]) + (h[8] - h[7]);
     const float jy = (h[2] - h[4]) + (h[5] - h[8]) + (h[6] - h[7]);
     const float ux = fmaf(0.5f, Fx, jx), uy = fmaf(0.5f, Fy, jy);
-    const float usq = ux * ux + uy * uy;
+    const float usq = usq_of(ux, uy);
     const float snr = ((h[1] + h[2]) + (h[3] + h[4])) + ((h[5] + h[6]) + (h[7] + h[8]));
-    const float prd = (snr - kQ * usq) / kC;
+    const float prd = fmaf(-kQ, usq, snr) / kC;
 
     // Eq. omega-D.  Constant D: omega from the host.  Chemotaxis: omega^-1 =
     // B + delta e_0 e_1^T with delta = -3 chi phi_0 r, inverted by Sherman-Morrison.
@@ -179,7 +194,7 @@ __device__ __forceinline__ void collide(const LbParams &p, float (&f)[M][5], flo
 #pragma unroll
         for (int a = 0; a < M; ++a)
 #pragma unroll
-            for (int b = 0; b < M; ++b) om[a][b] -= delta * den * col0[a] * row1[b];
+            for (int b = 0; b < M; ++b) om[a][b] = fmaf(-__fmul_rn(__fmul_rn(delta, den), col0[a]), row1[b], om[a][b]);
     }
 
     // Eq. Gi: G_{i,a} = 3 W_i c_i . J_a,  J_a = sum_b (delta_ab - omega_ab / 2)(u S_b + phi_b F)
@@ -189,7 +204,7 @@ __device__ __forceinline__ void collide(const LbParams &p, float (&f)[M][5], flo
         float jxa = 0.f, jya = 0.f;
 #pragma unroll
         for (int b = 0; b < M; ++b) {
-            const float c = (a == b ? 1.f : 0.f) - 0.5f * om[a][b];
+            const float c = fmaf(-0.5f, om[a][b], a == b ? 1.f : 0.f);
             jxa = fmaf(c, fmaf(ux, S[b], phi[b] * Fx), jxa);
             jya = fmaf(c, fmaf(uy, S[b], phi[b] * Fy), jya);
         }
@@ -211,9 +226,8 @@ __device__ __forceinline__ void collide(const LbParams &p, float (&f)[M][5], flo
             float coll = 0.f;
 #pragma unroll
             for (int b = 0; b < M; ++b) coll = fmaf(om[a][b], neq[b], coll);
-            const float src = kWs(i) * fmaf(1.5f, S[a], -0.5f * Sp[a]);
-            const float G = (i == 0) ? 0.f : 3.f * kW5 * (kC5x(i) * Jx[a] + kC5y(i) * Jy[a]);
-            f[a][i] = (f[a][i] - coll) + (src + G);
+            const float G = (i == 0) ? 0.f : __fmul_rn(3.f * kW5, kC5x(i) * Jx[a] + kC5y(i) * Jy[a]);
+            f[a][i] = (f[a][i] - coll) + fmaf(kWs(i), fmaf(1.5f, S[a], __fmul_rn(-0.5f, Sp[a])), G);
         }
     }
 
@@ -223,7 +237,7 @@ __device__ __forceinline__ void collide(const LbParams &p, float (&f)[M][5], flo
     for (int i = 0; i < 9; ++i) {
         const float heq = fluid_equilibrium(i, prd, ux, uy, usq);
         const float Fi = kA9(i) * (kC9x(i) * Fx + kC9y(i) * Fy);
-        h[i] = fmaf(-wf, h[i] - heq, h[i]) + fw * Fi;
+        h[i] = fmaf(fw, Fi, fmaf(-wf, h[i] - heq, h[i]));
     }
 #pragma unroll
     for (int a = 0; a < M; ++a) o.phi[a] = phi[a];
@@ -253,102 +267,162 @@ __device__ __forceinline__ void store_node(T *out, long long P, long long o0, co
         for (int i = 0; i < 5; ++i) Store<T>::store(out + (9 + 5 * a + i) * P + o0, f[a][i]);
 }
 
-// Pull source of one fluid direction: plane j at in-plane offset `off`, with the
-// change of the pressure reference between source and node, kA_j G.(src - x).
-struct Src {
-    int plane, off;
-    float shift;
+// ---- the pull of one node -------------------------------------------------------
+// Where the pre-collision populations of node (x, y) come from: for each fluid
+// direction i the source plane, node and pressure-reference shift; for each
+// scalar direction the source plane and node and the wall side whose rule
+// applies (-1 for a regular link).  mk(sx, sy) names a source node (an element
+// offset, a pair of coordinates, ...), so the same rules serve the
+// global-memory kernels, the tile-resident kernel and the 16-bit storage.
+// kInterior: the caller guarantees that no link of the node crosses a wall or
+// wraps; every source is then x - c_i and the selects fold away.
+template <class Pos>
+struct PullTable {
+    int hplane[9];
+    Pos hpos[9];
+    float hshift[9];
+    int splane[5];
+    Pos spos[5];
+    int side[5];
 };
 
-// ---- the fused step ------------------------------------------------------------
-// One node of the fused step (x < nx, y < ny): pull, moments, collision, store.
-template <int M, typename T, bool kL2 = false>
-__device__ __forceinline__ void step_node(const LbParams &p, int x, int y, const T *__restrict__ in,
-                                          T *__restrict__ out, float *__restrict__ sprev,
-                                          float *__restrict__ moments) {
-    const long long P = p.plane;
-
+template <bool kInterior, class MakePos>
+__device__ __forceinline__ PullTable<decltype(std::declval<MakePos>()(0, 0))> pull_table(const LbParams &p, int x,
+                                                                                           int y, const MakePos &mk) {
+    using Pos = decltype(mk(0, 0));
+    struct Src {
+        int plane;
+        Pos pos;
+        float shift;
+    };
     // Neighbour coordinates (periodic wrap) and wall crossings of the pull links.
     int xw = x - 1, xe = x + 1, ys = y - 1, yn = y + 1;
-    const bool cw = xw < 0 && !p.periodic_x, ce = xe >= p.nx && !p.periodic_x;
-    const bool cs = ys < 0 && !p.periodic_y, cn = yn >= p.ny && !p.periodic_y;
-    xw = xw < 0 ? p.nx - 1 : xw;
-    xe = xe >= p.nx ? 0 : xe;
-    ys = ys < 0 ? p.ny - 1 : ys;
-    yn = yn >= p.ny ? 0 : yn;
-    const int r0 = y * p.pitch, rs = ys * p.pitch, rn = yn * p.pitch;
-    const int o0 = r0 + x;
-    const float ax = kA1 * p.gref[0], ay = kA1 * p.gref[1];  // axis-link shifts
-    const float dx5 = kA5 * p.gref[0], dy5 = kA5 * p.gref[1];  // diagonal-link shifts
+    bool cw = false, ce = false, cs = false, cn = false;
+    if (!kInterior) {
+        cw = xw < 0 && !p.periodic_x;
+        ce = xe >= p.nx && !p.periodic_x;
+        cs = ys < 0 && !p.periodic_y;
+        cn = yn >= p.ny && !p.periodic_y;
+        xw = xw < 0 ? p.nx - 1 : xw;
+        xe = xe >= p.nx ? 0 : xe;
+        ys = ys < 0 ? p.ny - 1 : ys;
+        yn = yn >= p.ny ? 0 : yn;
+    }
+    const Pos o0 = mk(x, y), pw = mk(xw, y), pe = mk(xe, y), ps = mk(x, ys), pn = mk(x, yn);
+    const Pos psw = mk(xw, ys), pse = mk(xe, ys), pne = mk(xe, yn), pnw = mk(xw, yn);
+    // axis- and diagonal-link shifts (products kept out of FMA contraction so that
+    // every kernel adds them with the same rounding)
+    const float ax = __fmul_rn(kA1, p.gref[0]), ay = __fmul_rn(kA1, p.gref[1]);
+    const float dx5 = __fmul_rn(kA5, p.gref[0]), dy5 = __fmul_rn(kA5, p.gref[1]);
     const bool fw = p.freeslip[0], fe = p.freeslip[1], fs = p.freeslip[2], fn = p.freeslip[3];
 
     // Fluid, D2Q9: h_i(x) = h*_j(src).  Regular link: j = i, src = x - c_i.  No-slip
     // wall: bounce-back j = opp(i), src = x.  Free-slip wall: the specular image j
     // from the neighbour along the wall.  Corner links: bounce-back.  Every
-    // source is chosen by selects, so all loads issue before any arithmetic.
+    // source is chosen by selects, so all loads can issue before any arithmetic.
+    // The shift is the change of the pressure reference, kA_j G.(src - x).
     Src sh[9];
-    sh[0] = {0, o0, 0.f};
-    sh[1] = cw ? Src{3, o0, 0.f} : Src{1, r0 + xw, -ax};
-    sh[2] = cs ? Src{4, o0, 0.f} : Src{2, rs + x, -ay};
-    sh[3] = ce ? Src{1, o0, 0.f} : Src{3, r0 + xe, ax};
-    sh[4] = cn ? Src{2, o0, 0.f} : Src{4, rn + x, ay};
+    sh[0] = Src{0, o0, 0.f};
+    sh[1] = cw ? Src{3, o0, 0.f} : Src{1, pw, -ax};
+    sh[2] = cs ? Src{4, o0, 0.f} : Src{2, ps, -ay};
+    sh[3] = ce ? Src{1, o0, 0.f} : Src{3, pe, ax};
+    sh[4] = cn ? Src{2, o0, 0.f} : Src{4, pn, ay};
     {   // (1,1) from (x-1, y-1)
-        Src v{5, rs + xw, -dx5 - dy5};
+        Src v{5, psw, -dx5 - dy5};
         v = (cw || cs) ? Src{7, o0, 0.f} : v;
-        v = (cw && !cs && fw) ? Src{6, rs + x, -dy5} : v;
-        v = (cs && !cw && fs) ? Src{8, r0 + xw, -dx5} : v;
+        v = (cw && !cs && fw) ? Src{6, ps, -dy5} : v;
+        v = (cs && !cw && fs) ? Src{8, pw, -dx5} : v;
         sh[5] = v;
     }
     {   // (-1,1) from (x+1, y-1)
-        Src v{6, rs + xe, dx5 - dy5};
+        Src v{6, pse, dx5 - dy5};
         v = (ce || cs) ? Src{8, o0, 0.f} : v;
-        v = (ce && !cs && fe) ? Src{5, rs + x, -dy5} : v;
-        v = (cs && !ce && fs) ? Src{7, r0 + xe, dx5} : v;
+        v = (ce && !cs && fe) ? Src{5, ps, -dy5} : v;
+        v = (cs && !ce && fs) ? Src{7, pe, dx5} : v;
         sh[6] = v;
     }
     {   // (-1,-1) from (x+1, y+1)
-        Src v{7, rn + xe, dx5 + dy5};
+        Src v{7, pne, dx5 + dy5};
         v = (ce || cn) ? Src{5, o0, 0.f} : v;
-        v = (ce && !cn && fe) ? Src{8, rn + x, dy5} : v;
-        v = (cn && !ce && fn) ? Src{6, r0 + xe, dx5} : v;
+        v = (ce && !cn && fe) ? Src{8, pn, dy5} : v;
+        v = (cn && !ce && fn) ? Src{6, pe, dx5} : v;
         sh[7] = v;
     }
     {   // (1,-1) from (x-1, y+1)
-        Src v{8, rn + xw, -dx5 + dy5};
+        Src v{8, pnw, -dx5 + dy5};
         v = (cw || cn) ? Src{6, o0, 0.f} : v;
-        v = (cw && !cn && fw) ? Src{7, rn + x, dy5} : v;
-        v = (cn && !cw && fn) ? Src{5, r0 + xw, -dx5} : v;
+        v = (cw && !cn && fw) ? Src{7, pn, dy5} : v;
+        v = (cn && !cw && fn) ? Src{5, pw, -dx5} : v;
         sh[8] = v;
     }
-    // Scalars, D2Q5: bounce-back f*_opp(i)(x) (no flux) or anti-bounce-back
-    // -f*_opp(i)(x) + 2 W_i phi_w (Dirichlet); in deviations the latter is
-    // -f'*_opp(i)(x) + 2 W_i (phi_w - phi_ref).
-    const int sp_[5] = {0, cw ? 3 : 1, cs ? 4 : 2, ce ? 1 : 3, cn ? 2 : 4};
-    const int so_[5] = {o0, cw ? o0 : r0 + xw, cs ? o0 : rs + x, ce ? o0 : r0 + xe, cn ? o0 : rn + x};
-    const int side_[5] = {-1, cw ? 0 : -1, cs ? 2 : -1, ce ? 1 : -1, cn ? 3 : -1};
-
-    // ---- loads
-    float h[9], f[M][5];
+    PullTable<Pos> t;
 #pragma unroll
-    for (int i = 0; i < 9; ++i) h[i] = load_pop<T, kL2>(in + sh[i].plane * P + sh[i].off);
+    for (int i = 0; i < 9; ++i) {
+        t.hplane[i] = sh[i].plane;
+        t.hpos[i] = sh[i].pos;
+        t.hshift[i] = sh[i].shift;
+    }
+    // Scalars, D2Q5: bounce-back f*_opp(i)(x) (no flux) or anti-bounce-back
+    // -f*_opp(i)(x) + 2 W_i phi_w (Dirichlet) at the wall `side`.  The axis
+    // sources are the nodes of the fluid's axis sources.
+    t.splane[0] = 0;
+    t.splane[1] = cw ? 3 : 1;
+    t.splane[2] = cs ? 4 : 2;
+    t.splane[3] = ce ? 1 : 3;
+    t.splane[4] = cn ? 2 : 4;
+#pragma unroll
+    for (int i = 0; i < 5; ++i) t.spos[i] = sh[i].pos;
+    t.side[0] = -1;
+    t.side[1] = cw ? 0 : -1;
+    t.side[2] = cs ? 2 : -1;
+    t.side[3] = ce ? 1 : -1;
+    t.side[4] = cn ? 3 : -1;
+    return t;
+}
+
+// Pre-collision populations of node (x, y) in deviation variables: the loads of
+// the pull table through ld(plane, pos), then the pressure-reference shifts and,
+// in deviations, the anti-bounce-back value -f'*_opp(i)(x) + 2 W_i (phi_w - phi_ref).
+template <int M, bool kInterior, class MakePos, class Load>
+__device__ __forceinline__ void pull_node(const LbParams &p, int x, int y, const MakePos &mk, const Load &ld,
+                                          float (&f)[M][5], float (&h)[9]) {
+    const auto t = pull_table<kInterior>(p, x, y, mk);
+#pragma unroll
+    for (int i = 0; i < 9; ++i) h[i] = ld(t.hplane[i], t.hpos[i]);
 #pragma unroll
     for (int a = 0; a < M; ++a)
 #pragma unroll
-        for (int i = 0; i < 5; ++i) f[a][i] = load_pop<T, kL2>(in + (9 + 5 * a + sp_[i]) * P + so_[i]);
-    const bool consume = (M >= 2 && p.skind == 2);
-    const float sp1 = consume ? (kL2 ? __ldca(sprev + o0) : sprev[o0]) : 0.f;
-
-    // ---- boundary values
+        for (int i = 0; i < 5; ++i) f[a][i] = ld(9 + 5 * a + t.splane[i], t.spos[i]);
 #pragma unroll
-    for (int i = 0; i < 9; ++i) h[i] += sh[i].shift;
+    for (int i = 0; i < 9; ++i) h[i] += t.hshift[i];
+    if (!kInterior) {
 #pragma unroll
-    for (int i = 1; i < 5; ++i) {
-        if (side_[i] >= 0) {
+        for (int i = 1; i < 5; ++i) {
+            if (t.side[i] >= 0) {
 #pragma unroll
-            for (int a = 0; a < M; ++a)
-                if ((p.dirichlet[side_[i]] >> a) & 1u) f[a][i] = p.abb[side_[i]][a] - f[a][i];
+                for (int a = 0; a < M; ++a)
+                    if ((p.dirichlet[t.side[i]] >> a) & 1u) f[a][i] = p.abb[t.side[i]][a] - f[a][i];
+            }
         }
     }
+}
+
+// ---- the fused step ------------------------------------------------------------
+// One node of the fused step (x < nx, y < ny) on global-memory buffers: pull,
+// moments, collision, store.
+template <int M, typename T, bool kL2 = false>
+__device__ __forceinline__ void step_node(const LbParams &p, int x, int y, const T *__restrict__ in,
+                                          T *__restrict__ out, float *__restrict__ sprev,
+                                          float *__restrict__ moments) {
+    const long long P = p.plane;
+    const int pitch = p.pitch;
+    const auto mk = [pitch](int sx, int sy) { return sy * pitch + sx; };
+    const auto ld = [in, P](int plane, int off) { return load_pop<T, kL2>(in + plane * P + off); };
+    const int o0 = y * pitch + x;
+    const bool consume = (M >= 2 && p.skind == 2);
+    const float sp1 = consume ? (kL2 ? __ldca(sprev + o0) : sprev[o0]) : 0.f;
+    float h[9], f[M][5];
+    pull_node<M, false>(p, x, y, mk, ld, f, h);
 
     NodeOut<M> o;
     collide<M>(p, f, h, pref_at(p, x, y), sp1, false, o);

@@ -126,6 +126,12 @@ struct cdf_lb {
     cudaEvent_t ev_in = nullptr, ev_out = nullptr;
     cudaGraphExec_t graph[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};  // [parity][moments]
     dim3 block{64, 4, 1};
+    // Tile-resident persistent step (FP32 lattices that fit in shared memory).
+    bool resident = false;
+    ResidentGeom rg{};
+    unsigned *counters = nullptr;  // one step counter per tile
+    int *d_err = nullptr, *h_err = nullptr;  // wait time-out flag (device, pinned copy)
+    unsigned long long wait_ns = 1000000000ull;
     long long t = 0;
     bool initialised = false;
 };
@@ -146,6 +152,9 @@ void release(cdf_lb *h) {
     cudaFree(h->mom_pp[0]);
     cudaFree(h->mom_pp[1]);
     cudaFree(h->dense);
+    cudaFree(h->counters);
+    cudaFree(h->d_err);
+    if (h->h_err) cudaFreeHost(h->h_err);
     cudaFree(h->partials);
     cudaFree(h->red);
     if (h->red_host) cudaFreeHost(h->red_host);
@@ -208,8 +217,44 @@ cdf_status get_graph(cdf_lb *h, int parity, int with_moments, cudaGraphExec_t *o
     return CDF_OK;
 }
 
+constexpr long long kResidentMaxSteps = 4096;  // steps per resident launch
+
+// Zero the resident step counters and the time-out flag (after a new state).
+cdf_status reset_resident(cdf_lb *h) {
+    if (!h->resident) return CDF_OK;
+    CK(cudaMemsetAsync(h->counters, 0, sizeof(unsigned) * h->rg.tiles_x * h->rg.tiles_y, h->s));
+    CK(cudaMemsetAsync(h->d_err, 0, sizeof(int), h->s));
+    CK(cudaMemcpyAsync(h->h_err, h->d_err, sizeof(int), cudaMemcpyDeviceToHost, h->s));
+    return CDF_OK;
+}
+
+// After a stream synchronisation: did a wait of the resident step run out?
+// The state is then undefined; the handle needs a new initial state.
+cdf_status check_wait(cdf_lb *h) {
+    if (!h->resident || !*h->h_err) return CDF_OK;
+    *h->h_err = 0;
+    h->initialised = false;
+    reset_resident(h);
+    cudaStreamSynchronize(h->s);
+    return fail(CDF_ETIMEOUT, "a wait of the resident step timed out; the state is undefined (initialise again)");
+}
+
+cdf_status sync(cdf_lb *h) {
+    CK(cudaStreamSynchronize(h->s));
+    return check_wait(h);
+}
+
 // n steps on the library stream; the last one writes the moments.
 cdf_status run_steps(cdf_lb *h, long long n) {
+    while (h->resident && n > 0) {
+        const int k = (int)std::min(n, kResidentMaxSteps);
+        CK(launch_resident(h->P, h->rg, static_cast<float *>(h->buf[0]), static_cast<float *>(h->buf[1]), h->sprev,
+                           h->mom, k, h->cur, k == n, h->counters, h->wait_ns, h->d_err, h->s));
+        CK(cudaMemcpyAsync(h->h_err, h->d_err, sizeof(int), cudaMemcpyDeviceToHost, h->s));
+        if (k & 1) h->cur ^= 1;
+        h->t += k;
+        n -= k;
+    }
     while (n > 0) {
         if (n >= kGraphSteps) {
             cudaGraphExec_t ge;
@@ -235,7 +280,8 @@ cdf_status reduce(cdf_lb *h, const float *nw, const float *od, double *host_out)
     CK(launch_reduce(nw, od, h->nx, h->ny, h->pitch, h->plane, h->m, h->partials, h->red, h->s));
     const int nq = reduce_quantities(h->m);
     CK(cudaMemcpyAsync(h->red_host, h->red, nq * sizeof(double), cudaMemcpyDeviceToHost, h->s));
-    CK(cudaStreamSynchronize(h->s));
+    cdf_status st = sync(h);
+    if (st != CDF_OK) return st;
     std::memcpy(host_out, h->red_host, nq * sizeof(double));
     return CDF_OK;
 }
@@ -287,6 +333,77 @@ cdf_status autotune(cdf_lb *h) {
     std::lock_guard<std::mutex> lk(g_tune_mu);
     g_tune_cache[key] = best_b;
     return CDF_OK;
+}
+
+std::map<TuneKey, bool> g_resident_cache;
+
+// Time `steps` steps of the current mode on the library stream (ms).
+cdf_status time_steps(cdf_lb *h, long long steps, float *ms) {
+    cudaEvent_t a, b;
+    CK(cudaEventCreate(&a));
+    CK(cudaEventCreate(&b));
+    cdf_status st = run_steps(h, steps);  // warm-up (captures graphs)
+    if (st == CDF_OK) {
+        cudaEventRecord(a, h->s);
+        st = run_steps(h, steps);
+        cudaEventRecord(b, h->s);
+    }
+    cudaError_t e = cudaEventSynchronize(b);
+    if (st == CDF_OK && e == cudaSuccess) e = cudaEventElapsedTime(ms, a, b);
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    if (st != CDF_OK) return st;
+    if (e != cudaSuccess) return fail(CDF_ECUDA, "timing failed: %s", cudaGetErrorString(e));
+    return check_wait(h);
+}
+
+// Decide whether the tile-resident step runs this lattice: always when asked
+// for, never when refused or when the lattice does not fit, otherwise when it
+// measures faster than the graph-launched kernel with the autotuned block.
+cdf_status setup_resident(cdf_lb *h, const cdf_options *opt) {
+    if (h->storage != CDF_FP32 || opt->resident == -1) return CDF_OK;
+    if (!plan_resident(h->nx, h->ny, h->m, h->P.periodic_x, h->P.periodic_y, &h->rg)) {
+        cudaGetLastError();
+        if (opt->resident == 1) return fail(CDF_EINVAL, "the lattice does not fit the resident step");
+        return CDF_OK;
+    }
+    h->rg.stall_tile = opt->test_stall_tile - 1;
+    h->wait_ns = opt->wait_timeout_s > 0 ? (unsigned long long)(opt->wait_timeout_s * 1e9) : 1000000000ull;
+    const size_t tiles = (size_t)h->rg.tiles_x * h->rg.tiles_y;
+    if (cudaMalloc((void **)&h->counters, tiles * sizeof(unsigned)) != cudaSuccess ||
+        cudaMalloc((void **)&h->d_err, sizeof(int)) != cudaSuccess ||
+        cudaMallocHost((void **)&h->h_err, sizeof(int)) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(CDF_ENOMEM, "allocation of the resident step's counters failed");
+    }
+    *h->h_err = 0;
+    h->resident = true;
+    cdf_status st = reset_resident(h);
+    if (st != CDF_OK || opt->resident == 1) return st;
+    // opt->resident == 0: keep the faster mode (the tuner runs on the zeroed
+    // buffers; the state is set by the init calls afterwards)
+    TuneKey key{h->nx, h->ny, h->m, h->storage, h->P.chemotaxis};
+    bool use = false;
+    bool cached = false;
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        auto it = g_resident_cache.find(key);
+        if (it != g_resident_cache.end()) { use = it->second; cached = true; }
+    }
+    if (!cached) {
+        float t_res = 0.f, t_graph = 0.f;
+        const long long steps = 128;
+        if ((st = time_steps(h, steps, &t_res)) != CDF_OK) return st;
+        h->resident = false;
+        if ((st = time_steps(h, steps, &t_graph)) != CDF_OK) return st;
+        use = t_res < t_graph;
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        g_resident_cache[key] = use;
+    }
+    h->resident = use;
+    h->cur = 0;
+    h->t = 0;
+    return reset_resident(h);
 }
 
 cdf_status check_side_pair(const cdf_side &a, const cdf_side &b, const char *axis) {
@@ -420,6 +537,10 @@ cdf_status cdf_lb_create(const cdf_grid *grid, int m, const cdf_diffusion *dif, 
     *out = nullptr;
     if (!grid || !dif || !src || !frc || !bc || !opt) return fail(CDF_EINVAL, "NULL argument");
     if (opt->storage < CDF_FP32 || opt->storage > CDF_BF16_DEV) return fail(CDF_EINVAL, "bad storage");
+    if (opt->resident < -1 || opt->resident > 1 || !(opt->wait_timeout_s >= 0.0) || opt->test_stall_tile < 0)
+        return fail(CDF_EINVAL, "bad resident-step options");
+    if (opt->resident == 1 && opt->storage != CDF_FP32)
+        return fail(CDF_EINVAL, "the resident step exists for FP32 storage only");
     if (!(opt->rho0 > 0.0)) return fail(CDF_EINVAL, "rho0 must be positive");
     LbParams P0{};
     const int align = opt->storage == CDF_FP32 ? 32 : 64;  // 128-byte rows
@@ -493,6 +614,10 @@ cdf_status cdf_lb_create(const cdf_grid *grid, int m, const cdf_diffusion *dif, 
         release(h);
         return st;
     }
+    if ((st = setup_resident(h, opt)) != CDF_OK) {
+        release(h);
+        return st;
+    }
     if (cudaStreamSynchronize(h->s) != cudaSuccess) {
         release(h);
         return fail(CDF_ECUDA, "set-up failed");
@@ -518,7 +643,7 @@ static cdf_status init_from_device_fields(cdf_lb *h, const float *fields) {
     h->cur = 0;
     h->t = 0;
     h->initialised = true;
-    return CDF_OK;
+    return reset_resident(h);
 }
 
 cdf_status cdf_lb_init_moments(cdf_lb *h, const double *phi, const double *u, const double *p) {
@@ -622,7 +747,7 @@ cdf_status cdf_lb_moments(cdf_lb *h, double *host_out) {
     const size_t n = (size_t)h->nx * h->ny * (h->m + 3);
     CK(launch_pack_moments(h->P, current_moments(h), h->dense, h->s));
     CK(cudaMemcpyAsync(h->host_stage, h->dense, n * 4, cudaMemcpyDeviceToHost, h->s));
-    CK(cudaStreamSynchronize(h->s));
+    if ((st = sync(h)) != CDF_OK) return st;
     for (size_t i = 0; i < n; ++i) host_out[i] = h->host_stage[i];
     return leave(h);
 }
@@ -658,7 +783,7 @@ cdf_status cdf_lb_populations(cdf_lb *h, double *f, double *hf, double *s_now) {
         sp.resize((size_t)h->plane);
         CK(cudaMemcpyAsync(sp.data(), h->sprev, sp.size() * 4, cudaMemcpyDeviceToHost, h->s));
     }
-    CK(cudaStreamSynchronize(h->s));
+    if ((st = sync(h)) != CDF_OK) return st;
     if (hf)
         for (size_t i = 0; i < 9 * n; ++i) hf[i] = tmp[i];
     if (f)
@@ -697,7 +822,7 @@ cdf_status cdf_lb_save(cdf_lb *h, const char *path) {
     CK(cudaMemcpyAsync(data.data(), h->buf[h->cur], pop, cudaMemcpyDeviceToHost, h->s));
     CK(cudaMemcpyAsync(data.data() + pop, h->sprev, spb, cudaMemcpyDeviceToHost, h->s));
     CK(cudaMemcpyAsync(data.data() + pop + spb, current_moments(h), momb, cudaMemcpyDeviceToHost, h->s));
-    CK(cudaStreamSynchronize(h->s));
+    if ((st = sync(h)) != CDF_OK) return st;
     FileHeader hd{};
     std::memcpy(hd.magic, kMagic, 8);
     hd.version = 1;
@@ -744,6 +869,7 @@ cdf_status cdf_lb_load(cdf_lb *h, const char *path) {
     CK(cudaMemcpyAsync(h->buf[0], data.data(), pop, cudaMemcpyHostToDevice, h->s));
     CK(cudaMemcpyAsync(h->sprev, data.data() + pop, spb, cudaMemcpyHostToDevice, h->s));
     CK(cudaMemcpyAsync(current_moments(h), data.data() + pop + spb, momb, cudaMemcpyHostToDevice, h->s));
+    if ((st = reset_resident(h)) != CDF_OK) return st;
     CK(cudaStreamSynchronize(h->s));
     h->t = hd.t;
     h->initialised = true;
@@ -755,6 +881,10 @@ cdf_status cdf_lb_get_info(const cdf_lb *h, cdf_info *out) {
     out->nx = h->nx; out->ny = h->ny; out->m = h->m; out->pitch = h->pitch;
     out->storage = h->storage; out->planes = h->planes; out->sprev_planes = h->sprev_planes;
     out->block_x = (int)h->block.x; out->block_y = (int)h->block.y;  // block_y 0: flat launch
+    out->resident = h->resident ? 1 : 0;
+    out->tile_x = h->resident ? h->rg.tw : 0;
+    out->tile_y = h->resident ? h->rg.th : 0;
+    out->tiles = h->resident ? h->rg.tiles_x * h->rg.tiles_y : 0;
     out->bytes_per_lup = 2.0 * h->planes * (double)elem_size(h->storage) + 8.0 * h->sprev_planes +
                          (h->mr ? 2.0 * 4.0 * (h->m + 3) : 0.0);
     out->t = h->t;

@@ -67,6 +67,29 @@ cudaError_t launch_export_mr(const LbParams &p, int storage, const void *in, con
 cudaError_t launch_pack_moments(const LbParams &p, const float *moments, float *dense,
                                 cudaStream_t s);
 
+// Tile-resident persistent step (lb_resident.cu), FP32 storage.  The lattice
+// is cut into tiles_x x tiles_y tiles of tw x th nodes (the last row and column
+// of tiles may be smaller), one co-resident CTA of `threads` threads and
+// `smem_bytes` of dynamic shared memory per tile.  stall_tile >= 0 is a test
+// hook: that tile never publishes its step counter, so its neighbours' bounded
+// waits run out.
+struct ResidentGeom {
+    int tiles_x, tiles_y, tw, th;
+    int threads;
+    size_t smem_bytes;
+    int stall_tile;
+};
+// Finds a tiling of the nx x ny lattice with m scalars that fits one CTA per
+// SM of the current device; false if the lattice is too large (or the device
+// lacks the shared memory).
+bool plan_resident(int nx, int ny, int m, int periodic_x, int periodic_y, ResidentGeom *out);
+// nsteps steps from buffer parity0 (buf0 or buf1) in one cooperative launch;
+// `counters` holds one step counter per tile (all equal between launches;
+// zero them together), *err is set when a wait ran out.
+cudaError_t launch_resident(const LbParams &p, const ResidentGeom &g, float *buf0, float *buf1, float *sprev,
+                            float *moments, int nsteps, int parity0, bool moments_last, unsigned *counters,
+                            unsigned long long timeout_ns, int *err, cudaStream_t s);
+
 // FP64 reductions (lb_reduce.cu).  Over `fields` stacks of (m+3) planes with the
 // given pitch: out[0..m) = sum phi_a; out[m + q] = sum |q_new - q_old| and
 // out[2m + 2 + q] = sum |q_new| for q in {phi_0..phi_{m-1}, u_x, u_y};

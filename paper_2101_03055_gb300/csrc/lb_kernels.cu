@@ -66,7 +66,7 @@ __global__ void init_kernel(const LbParams p, const float *__restrict__ fields, 
     const float Fx = p.g[0] * fm, Fy = p.g[1] * fm;
     // f = f^eq(phi, u); h = h^eq(u, p) - F_i / 2 (moments then return the inputs)
     float f[M][5], h[9];
-    const float usq = ux * ux + uy * uy;
+    const float usq = usq_of(ux, uy);
     scalar_equilibrium<M>(phid, phi, ux, uy, f);
 #pragma unroll
     for (int i = 0; i < 9; ++i)
@@ -118,7 +118,7 @@ __global__ void pack_kernel(const LbParams p, int nf, const float *__restrict__ 
 // same functions on the same stored moments.  The collision itself is the FP32
 // one above with phi_ref = 0 and p_ref = 0 (the host sets them so).
 __device__ __forceinline__ float heq_dir(int j, float pr, float ux, float uy) {
-    return fluid_equilibrium(j, pr, ux, uy, ux * ux + uy * uy);
+    return fluid_equilibrium(j, pr, ux, uy, usq_of(ux, uy));
 }
 
 // Body force at a node from its scalars, F = g (Fbase + sum_a beta_a phi_a); the
@@ -135,66 +135,22 @@ __device__ __forceinline__ float force_mag(const LbParams &p, const float (&phi)
 // Its first moment u + F/2 is that of h* itself, so the stored deviation holds
 // only the viscous non-equilibrium part.
 __device__ __forceinline__ float href_dir(const LbParams &p, int j, float pr, float ux, float uy, float fm) {
-    return fmaf(0.5f * kA9(j), kC9x(j) * (p.g[0] * fm) + kC9y(j) * (p.g[1] * fm), heq_dir(j, pr, ux, uy));
+    return fmaf(0.5f * kA9(j), kC9x(j) * __fmul_rn(p.g[0], fm) + kC9y(j) * __fmul_rn(p.g[1], fm), heq_dir(j, pr, ux, uy));
 }
 
 template <int M, typename T>
-__global__ void __launch_bounds__(256) step_kernel_mr(const LbParams p, const T *__restrict__ in,
+__global__ void __launch_bounds__(256, (M <= 2 ? 3 : 1)) step_kernel_mr(const LbParams p, const T *__restrict__ in,
                                                       const float *__restrict__ min, T *__restrict__ out,
                                                       float *__restrict__ mout, float *__restrict__ sprev) {
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     const int y = blockIdx.y * blockDim.y + threadIdx.y;
     if (x >= p.nx || y >= p.ny) return;
     const long long P = p.plane;
-    int xw = x - 1, xe = x + 1, ys = y - 1, yn = y + 1;
-    const bool cw = xw < 0 && !p.periodic_x, ce = xe >= p.nx && !p.periodic_x;
-    const bool cs = ys < 0 && !p.periodic_y, cn = yn >= p.ny && !p.periodic_y;
-    xw = xw < 0 ? p.nx - 1 : xw;
-    xe = xe >= p.nx ? 0 : xe;
-    ys = ys < 0 ? p.ny - 1 : ys;
-    yn = yn >= p.ny ? 0 : yn;
-    const int r0 = y * p.pitch, rs = ys * p.pitch, rn = yn * p.pitch;
-    const int o0 = r0 + x;
-    const bool fw = p.freeslip[0], fe = p.freeslip[1], fs = p.freeslip[2], fn = p.freeslip[3];
-
-    // Pull sources exactly as in step_kernel (plane j at node offset off).
-    Src sh[9];
-    sh[0] = {0, o0, 0.f};
-    sh[1] = cw ? Src{3, o0, 0.f} : Src{1, r0 + xw, 0.f};
-    sh[2] = cs ? Src{4, o0, 0.f} : Src{2, rs + x, 0.f};
-    sh[3] = ce ? Src{1, o0, 0.f} : Src{3, r0 + xe, 0.f};
-    sh[4] = cn ? Src{2, o0, 0.f} : Src{4, rn + x, 0.f};
-    {
-        Src v{5, rs + xw, 0.f};
-        v = (cw || cs) ? Src{7, o0, 0.f} : v;
-        v = (cw && !cs && fw) ? Src{6, rs + x, 0.f} : v;
-        v = (cs && !cw && fs) ? Src{8, r0 + xw, 0.f} : v;
-        sh[5] = v;
-    }
-    {
-        Src v{6, rs + xe, 0.f};
-        v = (ce || cs) ? Src{8, o0, 0.f} : v;
-        v = (ce && !cs && fe) ? Src{5, rs + x, 0.f} : v;
-        v = (cs && !ce && fs) ? Src{7, r0 + xe, 0.f} : v;
-        sh[6] = v;
-    }
-    {
-        Src v{7, rn + xe, 0.f};
-        v = (ce || cn) ? Src{5, o0, 0.f} : v;
-        v = (ce && !cn && fe) ? Src{8, rn + x, 0.f} : v;
-        v = (cn && !ce && fn) ? Src{6, r0 + xe, 0.f} : v;
-        sh[7] = v;
-    }
-    {
-        Src v{8, rn + xw, 0.f};
-        v = (cw || cn) ? Src{6, o0, 0.f} : v;
-        v = (cw && !cn && fw) ? Src{7, rn + x, 0.f} : v;
-        v = (cn && !cw && fn) ? Src{5, r0 + xw, 0.f} : v;
-        sh[8] = v;
-    }
-    const int sp_[5] = {0, cw ? 3 : 1, cs ? 4 : 2, ce ? 1 : 3, cn ? 2 : 4};
-    const int so_[5] = {o0, cw ? o0 : r0 + xw, cs ? o0 : rs + x, ce ? o0 : r0 + xe, cn ? o0 : rn + x};
-    const int side_[5] = {-1, cw ? 0 : -1, cs ? 2 : -1, ce ? 1 : -1, cn ? 3 : -1};
+    const int pitch = p.pitch;
+    const int o0 = y * pitch + x;
+    // Pull sources exactly as in step_kernel (the pressure-reference shifts are
+    // zero here: the host sets p_ref = 0 for this storage).
+    const auto t = pull_table<false>(p, x, y, [pitch](int sx, int sy) { return sy * pitch + sx; });
 
     // ---- loads: stored deviations and the source nodes' moments (the axis
     // sources of the fluid and of the scalars are the same nodes)
@@ -202,35 +158,35 @@ __global__ void __launch_bounds__(256) step_kernel_mr(const LbParams p, const T 
     float h[9], hu[9], hv[9], hp[9], hphi[9][M];
 #pragma unroll
     for (int i = 0; i < 9; ++i) {
-        h[i] = Store<T>::load(in + sh[i].plane * P + sh[i].off);
-        hu[i] = __ldg(mux + sh[i].off);
-        hv[i] = __ldg(muy + sh[i].off);
-        hp[i] = __ldg(mpr + sh[i].off);
+        h[i] = Store<T>::load(in + t.hplane[i] * P + t.hpos[i]);
+        hu[i] = __ldg(mux + t.hpos[i]);
+        hv[i] = __ldg(muy + t.hpos[i]);
+        hp[i] = __ldg(mpr + t.hpos[i]);
 #pragma unroll
-        for (int a = 0; a < M; ++a) hphi[i][a] = __ldg(min + a * P + sh[i].off);
+        for (int a = 0; a < M; ++a) hphi[i][a] = __ldg(min + a * P + t.hpos[i]);
     }
     float f[M][5];
 #pragma unroll
     for (int i = 0; i < 5; ++i)
 #pragma unroll
-        for (int a = 0; a < M; ++a) f[a][i] = Store<T>::load(in + (9 + 5 * a + sp_[i]) * P + so_[i]);
+        for (int a = 0; a < M; ++a) f[a][i] = Store<T>::load(in + (9 + 5 * a + t.splane[i]) * P + t.spos[i]);
     const bool consume = (M >= 2 && p.skind == 2);
     const float sp1 = consume ? sprev[o0] : 0.f;
 
     // ---- rebuild the pre-collision populations (deviation variables of collide)
 #pragma unroll
-    for (int i = 0; i < 9; ++i) h[i] += href_dir(p, sh[i].plane, hp[i], hu[i], hv[i], force_mag<M>(p, hphi[i]));
+    for (int i = 0; i < 9; ++i) h[i] += href_dir(p, t.hplane[i], hp[i], hu[i], hv[i], force_mag<M>(p, hphi[i]));
 #pragma unroll
     for (int a = 0; a < M; ++a) {
         // rest direction: from this node's own moments, rest by difference
-        const float ph = hphi[0][a], t = 3.f * ph;
-        const float e1 = feq_dir(1, ph, t, hu[0], hv[0]), e2 = feq_dir(2, ph, t, hu[0], hv[0]);
-        const float e3 = feq_dir(3, ph, t, hu[0], hv[0]), e4 = feq_dir(4, ph, t, hu[0], hv[0]);
+        const float ph = hphi[0][a], t3 = 3.f * ph;
+        const float e1 = feq_dir(1, ph, t3, hu[0], hv[0]), e2 = feq_dir(2, ph, t3, hu[0], hv[0]);
+        const float e3 = feq_dir(3, ph, t3, hu[0], hv[0]), e4 = feq_dir(4, ph, t3, hu[0], hv[0]);
         f[a][0] += ph - ((e1 + e3) + (e2 + e4));
 #pragma unroll
         for (int i = 1; i < 5; ++i) {
-            f[a][i] += feq_dir(sp_[i], hphi[i][a], 3.f * hphi[i][a], hu[i], hv[i]);
-            if (side_[i] >= 0 && ((p.dirichlet[side_[i]] >> a) & 1u)) f[a][i] = p.abb[side_[i]][a] - f[a][i];
+            f[a][i] += feq_dir(t.splane[i], hphi[i][a], 3.f * hphi[i][a], hu[i], hv[i]);
+            if (t.side[i] >= 0 && ((p.dirichlet[t.side[i]] >> a) & 1u)) f[a][i] = p.abb[t.side[i]][a] - f[a][i];
         }
     }
 

@@ -62,14 +62,16 @@ class cdf_boundaries(ctypes.Structure):
 class cdf_options(ctypes.Structure):
     _fields_ = [("storage", ctypes.c_int), ("rho0", ctypes.c_double), ("cuda_stream", ctypes.c_void_p),
                 ("phi_ref", ctypes.c_double * MAX_M), ("p_ref_grad", ctypes.c_double * 2),
-                ("block_x", ctypes.c_int), ("block_y", ctypes.c_int)]
+                ("block_x", ctypes.c_int), ("block_y", ctypes.c_int), ("resident", ctypes.c_int),
+                ("wait_timeout_s", ctypes.c_double), ("test_stall_tile", ctypes.c_int)]
 
 
 class cdf_info(ctypes.Structure):
     _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int), ("m", ctypes.c_int), ("pitch", ctypes.c_int),
                 ("storage", ctypes.c_int), ("planes", ctypes.c_int), ("sprev_planes", ctypes.c_int),
-                ("block_x", ctypes.c_int), ("block_y", ctypes.c_int), ("bytes_per_lup", ctypes.c_double),
-                ("t", ctypes.c_longlong)]
+                ("block_x", ctypes.c_int), ("block_y", ctypes.c_int), ("resident", ctypes.c_int),
+                ("tile_x", ctypes.c_int), ("tile_y", ctypes.c_int), ("tiles", ctypes.c_int),
+                ("bytes_per_lup", ctypes.c_double), ("t", ctypes.c_longlong)]
 
 
 class cdf_batch_options(ctypes.Structure):
@@ -236,7 +238,7 @@ def cdf_moment_sums_static(dev_fields: int, dev_fields_old: int, nx: int, ny: in
 
 # ---- problem description -> C structs ------------------------------------------------
 def structs_from_problem(pb: Problem, storage: str = "fp32", stream: int = 0, block=None, phi_ref=None,
-                         p_ref_grad=None):
+                         p_ref_grad=None, resident: int = 0, wait_timeout_s: float = 0.0, test_stall_tile: int = 0):
     m = pb.m
     if m > MAX_M:
         raise ValueError(f"m = {m} > {MAX_M}")
@@ -276,6 +278,7 @@ def structs_from_problem(pb: Problem, storage: str = "fp32", stream: int = 0, bl
     opt.p_ref_grad[0], opt.p_ref_grad[1] = float(grad[0]), float(grad[1])
     if block is not None:
         opt.block_x, opt.block_y = block
+    opt.resident, opt.wait_timeout_s, opt.test_stall_tile = int(resident), float(wait_timeout_s), int(test_stall_tile)
     return grid, dif, src, frc, bc, opt
 
 
@@ -304,11 +307,15 @@ class Solver:
     """One lattice on the GPU behind the C ABI."""
 
     def __init__(self, pb: Problem, storage: str = "fp32", stream: int = 0, block=None, init: bool = True,
-                 phi_ref=None, p_ref_grad=None):
+                 phi_ref=None, p_ref_grad=None, resident: int = 0, wait_timeout_s: float = 0.0,
+                 test_stall_tile: int = 0):
+        """resident: 0 = the autotuner decides whether the tile-resident step is
+        used, 1 = always, -1 = never (cdf_options.resident)."""
         self.pb = pb
         self.m, self.nx, self.ny = pb.m, pb.nx, pb.ny
         self.storage = storage
-        self._structs = structs_from_problem(pb, storage, stream, block, phi_ref, p_ref_grad)
+        self._structs = structs_from_problem(pb, storage, stream, block, phi_ref, p_ref_grad, resident,
+                                             wait_timeout_s, test_stall_tile)
         grid, dif, src, frc, bc, opt = self._structs
         self.h = cdf_lb_create(grid, pb.m, dif, pb.nu, src, frc, bc, opt)
         if init:
