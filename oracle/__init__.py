@@ -55,6 +55,7 @@ class _Params(ctypes.Structure):
         ("nu", ctypes.c_double), ("rho0", ctypes.c_double), ("theta", ctypes.c_double),
         ("side_kind", ctypes.c_int * 4), ("fluid_bc", ctypes.c_int * 4),
         ("scalar_bc", (ctypes.c_int * MAX_M) * 4), ("value", (ctypes.c_double * MAX_M) * 4),
+        ("case1", ctypes.c_int),
     ]
 
 
@@ -82,6 +83,7 @@ def _bind(path):
     lib.orc_fluid_relaxation.argtypes = [ctypes.c_double]
     lib.orc_aux_source.argtypes = [ctypes.c_int, _DP, _DP, ctypes.c_double, ctypes.c_double,
                                    _DP, ctypes.c_double, ctypes.c_double, _DP]
+    lib.orc_aux_source_case1.argtypes = [ctypes.c_int, _DP, _DP, _DP, ctypes.c_double, ctypes.c_double, _DP]
     lib.orc_cutoff.restype = ctypes.c_double
     lib.orc_cutoff.argtypes = [ctypes.c_double] * 3 + [ctypes.c_int]
     lib.orc_closures.argtypes = [ctypes.POINTER(_Params), _DP, _DP, _DP, _DP]
@@ -119,6 +121,7 @@ def params_from_problem(pb, theta: float = 0.0) -> _Params:
     P.k = pb.k
     P.g[0], P.g[1] = float(pb.g[0]), float(pb.g[1])
     P.F0, P.nu, P.rho0, P.theta = pb.F0, pb.nu, pb.rho0, theta
+    P.case1 = int(getattr(pb, "case1", False))
     for s, name in enumerate(_SIDES):
         side = getattr(pb, name)
         P.side_kind[s] = {"periodic": 0, "wall": 1}[side.kind]

@@ -40,6 +40,13 @@
  *     consumption S_1 = -k phi_0 r(phi_1); r is the step cut-off
  *     (r = 1 for c >= c*) or its regularised form with width eps.
  *   - Force F = g (F0 + sum_a beta_a (phi_a - phi_ref_a)).
+ *   - Case 1 of Sec. 2.1 (case1 = 1): the convection cross-diffusion equations
+ *     alone, no fluid populations.  The velocity passed to orc_init is a steady
+ *     prescribed field (p = 0, F = 0), and the auxiliary source is
+ *       G_{i,a} = sum_b (delta_ab - omega_ab / 2) W_i c_i.d_t(phi_b u) / cs^2
+ *     with the first-order explicit difference
+ *       d_t(phi_b u) = u (phi_b(t) - phi_b(t - 1));
+ *     phi(t - 1) at t = 0 is phi0, so the first step has G = 0.
  */
 #include <math.h>
 #include <stdlib.h>
@@ -72,6 +79,7 @@ typedef struct {
     int fluid_bc[4];
     int scalar_bc[4][ORC_MAX_M];
     double value[4][ORC_MAX_M];
+    int case1;              /* Case 1 of Sec. 2.1: prescribed steady velocity, no fluid */
 } orc_params;
 
 /* ---- lattices (Eq. D2Q5 and Eq. D2Q9), c_hat = 1 ---------------------------- */
@@ -185,6 +193,23 @@ void orc_aux_source(int m, const double *omega, const double *phi, double ux, do
         }
 }
 
+/* Case 1 of Sec. 2.1: G_{i,a} = sum_b (delta_ab - omega_ab / 2) W_i c_i.d_t(phi_b u) / cs^2,
+ * d_t(phi_b u) = u (phi_b - phi_prev_b) (steady u, first-order explicit difference).
+ * out[a*5 + i]. */
+void orc_aux_source_case1(int m, const double *omega, const double *phi_prev, const double *phi, double ux,
+                          double uy, double *out) {
+    for (int a = 0; a < m; ++a)
+        for (int i = 0; i < 5; ++i) {
+            double acc = 0.0;
+            for (int b = 0; b < m; ++b) {
+                double coef = a == b ? 1.0 - 0.5 * omega[a * m + b] : -0.5 * omega[a * m + b];
+                double dphi = phi[b] - phi_prev[b];
+                acc += coef * Q5_W[i] * (Q5_CX[i] * ux + Q5_CY[i] * uy) * dphi / CS2;
+            }
+            out[a * 5 + i] = acc;
+        }
+}
+
 /* Chemotactic cut-off r(c): step form (Sec. 3.1.3) or regularised form (Sec. 3.1.2). */
 double orc_cutoff(double c, double c_star, double eps, int regularised) {
     if (regularised) {
@@ -221,6 +246,8 @@ typedef struct {
     double *h;     /* [node][9]    pre-collision fluid populations at time t */
     double *sprev; /* [node][a]    S_a(t-1) */
     double *fpost, *hpost, *fnew, *hnew;
+    double *uf;      /* [node][2] prescribed velocity (Case 1) */
+    double *phiprev; /* [node][a] phi_a(t-1) (Case 1) */
 } orc_sim;
 
 #define NODE(P, x, y) ((long)(y) * (P)->nx + (x))
@@ -247,9 +274,11 @@ orc_sim *orc_create(const orc_params *P) {
     s->hpost = (double *)calloc((size_t)n * 9, sizeof(double));
     s->hnew = (double *)calloc((size_t)n * 9, sizeof(double));
     s->sprev = (double *)calloc((size_t)n * P->m, sizeof(double));
-    if (!s->f || !s->fpost || !s->fnew || !s->h || !s->hpost || !s->hnew || !s->sprev) {
+    s->uf = (double *)calloc((size_t)n * 2, sizeof(double));
+    s->phiprev = (double *)calloc((size_t)n * P->m, sizeof(double));
+    if (!s->f || !s->fpost || !s->fnew || !s->h || !s->hpost || !s->hnew || !s->sprev || !s->uf || !s->phiprev) {
         free(s->f); free(s->fpost); free(s->fnew); free(s->h); free(s->hpost); free(s->hnew);
-        free(s->sprev); free(s);
+        free(s->sprev); free(s->uf); free(s->phiprev); free(s);
         return NULL;
     }
     return s;
@@ -259,6 +288,7 @@ void orc_destroy(orc_sim *s) {
     if (!s) return;
     free(s->f); free(s->fpost); free(s->fnew);
     free(s->h); free(s->hpost); free(s->hnew); free(s->sprev);
+    free(s->uf); free(s->phiprev);
     free(s);
 }
 
@@ -277,6 +307,13 @@ static void node_moments(const orc_sim *s, long node, double *phi, double *u, do
         for (int i = 0; i < 5; ++i) phi[a] += f[a * 5 + i];
     }
     orc_closures(P, phi, D, S, F);
+    if (P->case1) { /* Case 1: the velocity is prescribed; no fluid, no force */
+        u[0] = s->uf[node * 2];
+        u[1] = s->uf[node * 2 + 1];
+        *p = 0.0;
+        F[0] = F[1] = 0.0;
+        return;
+    }
     double jx = 0.0, jy = 0.0, sum_nonrest = 0.0;
     for (int i = 0; i < 9; ++i) {
         jx += Q9_CX[i] * h[i];
@@ -302,7 +339,10 @@ static int node_collide(orc_sim *s, long node, double *fpost, double *hpost, int
 
     double feq[ORC_MAX_M][5], G[ORC_MAX_M * 5];
     for (int a = 0; a < m; ++a) orc_feq_scalar(phi[a], u[0], u[1], P->theta, feq[a]);
-    orc_aux_source(m, omega, phi, u[0], u[1], S, F[0], F[1], G);
+    if (P->case1)
+        orc_aux_source_case1(m, omega, s->phiprev + node * m, phi, u[0], u[1], G);
+    else
+        orc_aux_source(m, omega, phi, u[0], u[1], S, F[0], F[1], G);
 
     const double *f = s->f + node * m * 5;
     double *sp = s->sprev + node * m;
@@ -316,6 +356,12 @@ static int node_collide(orc_sim *s, long node, double *fpost, double *hpost, int
         }
     if (update_sprev)
         for (int a = 0; a < m; ++a) sp[a] = S[a];
+    if (update_sprev && P->case1)
+        for (int a = 0; a < m; ++a) s->phiprev[node * m + a] = phi[a];
+    if (P->case1) {
+        for (int i = 0; i < 9; ++i) hpost[i] = 0.0;
+        return 0;
+    }
 
     const double *h = s->h + node * 9;
     double heq[9], Fi[9];
@@ -402,6 +448,13 @@ int orc_init(orc_sim *s, const double *phi0, const double *u0, const double *p0)
         for (int a = 0; a < m; ++a) {
             orc_feq_scalar(phi[a], ux, uy, P->theta, s->f + (node * m + a) * 5);
             s->sprev[node * m + a] = S[a];
+            s->phiprev[node * m + a] = phi[a];
+        }
+        s->uf[node * 2] = ux;
+        s->uf[node * 2 + 1] = uy;
+        if (P->case1) {
+            for (int i = 0; i < 9; ++i) s->h[node * 9 + i] = 0.0;
+            continue;
         }
         double heq[9], Fi[9];
         orc_heq(p, ux, uy, P->rho0, heq);

@@ -124,6 +124,7 @@ class Problem:
     u0: np.ndarray = None              # (2, ny, nx)
     p0: np.ndarray = None              # (ny, nx)
     steps: int = 0                     # nominal step count of the workload
+    case1: bool = False                # Case 1 of Sec. 2.1: no fluid; u0 is a steady prescribed velocity
 
     def __post_init__(self):
         m = self.m
@@ -271,6 +272,33 @@ def fourier_box(nx: int, ny: int, m: int, D, mode=(1, 0), amp=(0.01, 0.02), u=(0
     u0 = np.stack([np.full((ny, nx), u[0]), np.full((ny, nx), u[1])])
     return Problem("fourier_box", nx, ny, m, np.asarray(D, np.float64), nu, skind=skind, S=S,
                    k=k, g=tuple(g), F0=F0, phi0=phi0, u0=u0)
+
+
+def cde_cellular(nx: int, ny: int, m: int = 2, U0: float = 0.05, D=((0.05, 0.01), (0.005, 0.03)),
+                 seed: int = 0, walls: bool = True, steps: int = 0) -> Problem:
+    """Case 1 of Sec. 2.1 (convection cross-diffusion without the fluid solver) in a
+    prescribed steady cellular flow.  Walls: stream function psi = A sin(pi x / W)
+    sin(pi y / H) (no normal velocity at the four walls), scalars Dirichlet on
+    the west (phi = 1.2) and east (phi = 0.8) walls, no flux on the others.
+    Periodic: u = U0 (sin(2 pi x / W) cos(2 pi y / H), -(H/W) cos(2 pi x / W) sin(2 pi y / H)).
+    phi_a = 1 + 0.1 U(-1, 1) (seed; counters a * nx * ny + y * nx + x)."""
+    x = node_coords(nx, walls)[None, :]
+    y = node_coords(ny, walls)[:, None]
+    W, H = float(nx), float(ny)
+    if walls:
+        ux = U0 * np.sin(math.pi * x / W) * np.cos(math.pi * y / H)
+        uy = -U0 * (H / W) * np.cos(math.pi * x / W) * np.sin(math.pi * y / H)
+        hot = wall_side(m, NOSLIP, [DIRICHLET] * m, [1.2] * m)
+        cold = wall_side(m, NOSLIP, [DIRICHLET] * m, [0.8] * m)
+        sides = dict(west=hot, east=cold, south=wall_side(m), north=wall_side(m))
+    else:
+        ux = U0 * np.sin(2 * math.pi * x / W) * np.cos(2 * math.pi * y / H)
+        uy = -U0 * (H / W) * np.cos(2 * math.pi * x / W) * np.sin(2 * math.pi * y / H)
+        sides = {}
+    u0 = np.stack([np.broadcast_to(ux, (ny, nx)), np.broadcast_to(uy, (ny, nx))]).astype(np.float64)
+    phi0 = 1.0 + 0.1 * (2.0 * uniform(seed, np.arange(m * nx * ny)) - 1.0).reshape(m, ny, nx)
+    return Problem("cde_cellular", nx, ny, m, np.asarray(D, np.float64)[:m, :m], 0.1, phi0=phi0, u0=u0,
+                   steps=steps, case1=True, **sides)
 
 
 def periodic_box(nx: int, ny: int, seed: int = 0, m: int = 2, u0: float = 0.02) -> Problem:
