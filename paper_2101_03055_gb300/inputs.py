@@ -304,3 +304,92 @@ def cde_cellular(nx: int, ny: int, m: int = 2, U0: float = 0.05, D=((0.05, 0.01)
 def periodic_box(nx: int, ny: int, seed: int = 0, m: int = 2, u0: float = 0.02) -> Problem:
     """Large periodic cross-diffusion box (roofline grid): the Taylor-Green setup at any size."""
     return cross_diffusion_taylor_green(nx, ny, seed=seed, u0=u0).replace(name="periodic_box")
+
+
+# ----------------------------------------------------------------------------
+# three-dimensional problems (D3Q7 scalars, D3Q19 fluid)
+# ----------------------------------------------------------------------------
+@dataclass
+class Problem3D:
+    """A 3-D CDF problem in lattice units plus its initial moments.  Sides in the
+    order x-, x+, y-, y+, z-, z+; walls are no slip for the fluid."""
+    name: str
+    nx: int
+    ny: int
+    nz: int
+    m: int
+    D: np.ndarray
+    nu: float
+    dkind: str = "const"
+    chi: float = 0.0
+    c_star: float = 0.3
+    eps: float = 0.0
+    r_regularised: bool = False
+    skind: str = "none"
+    S: np.ndarray = None
+    k: float = 0.0
+    g: tuple = (0.0, 0.0, 0.0)
+    beta: np.ndarray = None
+    phi_ref: np.ndarray = None
+    F0: float = 0.0
+    rho0: float = 1.0
+    sides: List[Side] = None
+    phi0: np.ndarray = None            # (m, nz, ny, nx)
+    u0: np.ndarray = None              # (3, nz, ny, nx)
+    p0: np.ndarray = None              # (nz, ny, nx)
+    steps: int = 0
+
+    def __post_init__(self):
+        m = self.m
+        self.D = np.asarray(self.D, dtype=np.float64).reshape(m, m)
+        self.S = np.zeros(m) if self.S is None else np.asarray(self.S, np.float64)
+        self.beta = np.zeros(m) if self.beta is None else np.asarray(self.beta, np.float64)
+        self.phi_ref = np.zeros(m) if self.phi_ref is None else np.asarray(self.phi_ref, np.float64)
+        if self.sides is None:
+            self.sides = [periodic_side(m) for _ in range(6)]
+        shape = (self.nz, self.ny, self.nx)
+        if self.phi0 is None:
+            self.phi0 = np.ones((m,) + shape)
+        if self.u0 is None:
+            self.u0 = np.zeros((3,) + shape)
+        if self.p0 is None:
+            self.p0 = np.zeros(shape)
+
+    @property
+    def nodes(self) -> int:
+        return self.nx * self.ny * self.nz
+
+    def replace(self, **kw) -> "Problem3D":
+        return dataclasses.replace(self, **kw)
+
+
+def periodic_box3d(nx: int, ny: int = None, nz: int = None, seed: int = 0, m: int = 2, u0: float = 0.02,
+                   D=((0.05, 0.01), (0.005, 0.03)), nu: float = 0.1) -> Problem3D:
+    """Periodic box, constant cross-diffusion D, the 3-D Taylor-Green initial velocity
+    u = u0 (sin kx cos ky cos kz, -cos kx sin ky cos kz, 0) (k = 2 pi / n per axis),
+    scalars 1 + 0.1 U(-1, 1) from seed (counters a * N + node)."""
+    ny = nx if ny is None else ny
+    nz = nx if nz is None else nz
+    z, y, x = np.meshgrid(np.arange(nz), np.arange(ny), np.arange(nx), indexing="ij")
+    kx, ky, kz = 2 * math.pi * x / nx, 2 * math.pi * y / ny, 2 * math.pi * z / nz
+    u = np.stack([u0 * np.sin(kx) * np.cos(ky) * np.cos(kz), -u0 * np.cos(kx) * np.sin(ky) * np.cos(kz),
+                  np.zeros_like(kx)])
+    n = nx * ny * nz
+    phi0 = 1.0 + 0.1 * (2.0 * uniform(seed, np.arange(m * n)) - 1.0).reshape(m, nz, ny, nx)
+    return Problem3D("periodic_box3d", nx, ny, nz, m, np.asarray(D, np.float64)[:m, :m], nu, phi0=phi0, u0=u)
+
+
+def ddc_cavity3d(n: int, Ra: float = 1e4, Pr: float = 0.7, Le: float = 2.0, Nc: float = 1.0, Df: float = 0.1,
+                 Sr: float = 0.1, seed: int = 0) -> Problem3D:
+    """Cubic double-diffusive cavity (the Sec. 3.2 setup in 3-D): T = C = 1 on the
+    x- wall, 0 on the x+ wall, the other walls adiabatic, gravity along +z in the
+    dimensionless form F = g (T + Nc C) z_hat; the lattice mapping of the 2-D
+    cavity; from rest with T = C = 0."""
+    m = 2
+    alpha, nu, g = ddc_lattice_parameters(n, Ra, Pr)
+    D = alpha * np.array([[1.0, Df], [Sr / Le, 1.0 / Le]])
+    hot = wall_side(m, NOSLIP, [DIRICHLET, DIRICHLET], [1.0, 1.0])
+    cold = wall_side(m, NOSLIP, [DIRICHLET, DIRICHLET], [0.0, 0.0])
+    sides = [hot, cold] + [wall_side(m) for _ in range(4)]
+    return Problem3D("ddc_cavity3d", n, n, n, m, D, nu, g=(0.0, 0.0, 1.0), beta=np.array([g, g * Nc]),
+                     sides=sides, phi0=np.zeros((m, n, n, n)))
