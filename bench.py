@@ -55,6 +55,12 @@ def workload(name: str, rank: int):
         return I.periodic_box(4096, 4096, seed=rank)
     if name == "periodic_2048":
         return I.periodic_box(2048, 2048, seed=rank)
+    if name == "periodic3d_256":
+        return I.periodic_box3d(256, seed=rank)
+    if name == "ddc_cavity3d_128":
+        return I.ddc_cavity3d(128)
+    if name == "cde_cellular_4096":
+        return I.cde_cellular(4096, 4096, seed=rank)
     if name == "batched_plume_sweep_256":
         return I.chemotaxis_plume_sweep(256, seed=rank)
     if name == "batched_plume_sweep_64":
@@ -69,6 +75,12 @@ def describe(name: str) -> str:
         "ddc_cavity_1024": "double-diffusive cavity 1024x1024 with Soret/Dufour (Df=Sr=0.5), Ra=1e5, Pr=0.7, Le=2, N=1",
         "periodic_4096": "periodic 4096x4096 cross-diffusion box (roofline grid)",
         "periodic_2048": "periodic 2048x2048 cross-diffusion box (profiling grid above L2)",
+        "periodic3d_256": "3-D periodic 256^3 cross-diffusion box, m=2, D3Q7 scalars + D3Q19 fluid "
+                          "(Taylor-Green initial velocity)",
+        "ddc_cavity3d_128": "3-D double-diffusive cube 128^3 (hot/cold x walls, Ra=1e4, Pr=0.7, Le=2, N=1), "
+                            "D3Q7 + D3Q19",
+        "cde_cellular_4096": "Case 1 of Sec. 2.1: convection cross-diffusion (m=2) in a prescribed steady cellular "
+                             "flow, 4096x4096, Dirichlet west/east walls, no fluid populations",
         "batched_plume_sweep_64": "64 chemotaxis-plume instances of the 256-instance sweep (profiling size)",
         "batched_plume_sweep_256": "256 chemotaxis-plume instances, W~U{128..512} x H~U{64..256} (13.2 M nodes), "
                                    "per-instance chi, D_c, gravity; one persistent launch per 32 steps",
@@ -168,6 +180,8 @@ class _Single:
                            f"{info.tile_x}x{info.tile_y} nodes)")
         else:
             self.kernel = f"step_kernel<{pb.m},{ {0: 'float', 1: '__half', 2: '__nv_bfloat16'}[info.storage]}>"
+        if getattr(pb, "case1", False):
+            self.kernel = f"step_kernel_case1<{pb.m}> (prescribed velocity, no fluid)"
 
     def steps_per_launch(self, n):
         """Lattice steps per kernel launch inside step(n)."""
@@ -192,6 +206,39 @@ class _Single:
 
 
 RESIDENT_MAX_STEPS = 4096  # steps per launch of the tile-resident step
+
+
+class _Single3D:
+    """The 3-D solver (D3Q7 scalars, D3Q19 fluid) for the timing loops."""
+
+    def __init__(self, lib, pb, storage):
+        if storage != "fp32":
+            raise SystemExit("the 3-D solver stores FP32 populations")
+        self.lib, self.pb = lib, pb
+        self.s = lib.Solver3D(pb)
+        info = self.s.info()
+        self.nodes, self.bytes_per_lup, self.storage = pb.nodes, info.bytes_per_lup, 0
+        self.block = [info.block_x, info.block_y]
+        self.m = pb.m
+        self.kernel = f"step3d_kernel<{pb.m}>"
+
+    stream = property(lambda self: self.s.stream)
+
+    def step(self, n):
+        self.s.step(n)
+
+    def steps_per_launch(self, n):
+        return 1
+
+    def launches(self, n):
+        return n
+
+    def e2e_step(self, n):
+        pb = self.pb
+        self.s.init_moments(pb.phi0, pb.u0, pb.p0)
+        self.s.step(n)
+        self.s.moments()
+        return 2 * (pb.m + 4) * pb.nodes * 4
 
 
 class _Batch:
@@ -270,12 +317,25 @@ def barrier(world: int):
         dist.barrier()
 
 
+def _oracle_sim(pb):
+    """The FP64 oracle (2-D or 3-D) of a problem, as it stands."""
+    if isinstance(pb, I.Problem3D):
+        from oracle import oracle3d
+        oracle3d.build()
+        return oracle3d.Sim(pb)
+    import oracle
+    oracle.build()
+    return oracle.OracleSim(pb)
+
+
+def _dims(pb) -> str:
+    return f"{pb.nx}x{pb.ny}x{pb.nz}" if isinstance(pb, I.Problem3D) else f"{pb.nx}x{pb.ny}"
+
+
 def cpu_baseline(pb, budget_s: float = 15.0):
     """The FP64 oracle as it stands, single-threaded, on a bounded sample: the
     same lattice advanced for as many steps as fit in about `budget_s`."""
-    import oracle
-    oracle.build()
-    o = oracle.OracleSim(pb)
+    o = _oracle_sim(pb)
     t0 = time.perf_counter()
     o.step(2)
     per = (time.perf_counter() - t0) / 2
@@ -284,7 +344,7 @@ def cpu_baseline(pb, budget_s: float = 15.0):
     o.step(n)
     dt = time.perf_counter() - t0
     return {"value": pb.nodes * n / dt / 1e6, "unit": "MLUPS", "cores": 1, "kind": "oracle",
-            "sample": f"{n} time steps of the {pb.nx}x{pb.ny} lattice (FP64, one thread, "
+            "sample": f"{n} time steps of the {_dims(pb)} lattice (FP64, one thread, "
                       f"{pb.nodes * n / 1e6:.1f} M lattice updates, {dt:.1f} s)"}
 
 
@@ -292,11 +352,9 @@ def run_reference(args, world, rank):
     """Reference arm: the FP64 CPU oracle on the host cores, same metric and workload."""
     if rank != 0:
         return
-    import oracle
-    oracle.build()
     wl = workload(args.workload, 0)
     pb = wl[0] if isinstance(wl, list) else wl  # a batched sweep: its first instance as the sample
-    o = oracle.OracleSim(pb)
+    o = _oracle_sim(pb)
     per_step_budget = 4.0
     t0 = time.perf_counter()
     o.step(1)
@@ -317,7 +375,7 @@ def run_reference(args, world, rank):
         "config": {"workload": args.workload, "description": describe(args.workload),
                    "nx": pb.nx, "ny": pb.ny, "m": pb.m, "lb_steps_per_step": n},
         "cpu_baseline": {"value": value, "unit": "MLUPS", "cores": 1, "kind": "oracle",
-                         "sample": f"{n} time steps of the {pb.nx}x{pb.ny} lattice per benchmark step"},
+                         "sample": f"{n} time steps of the {_dims(pb)} lattice per benchmark step"},
         "e2e": {"value": value, "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -352,7 +410,12 @@ def main():
     from paper_2101_03055_gb300 import build, lib
     build.build()
     wl = workload(args.workload, rank)
-    runner = _Batch(lib, wl, args.storage) if isinstance(wl, list) else _Single(lib, wl, args.storage)
+    if isinstance(wl, list):
+        runner = _Batch(lib, wl, args.storage)
+    elif isinstance(wl, I.Problem3D):
+        runner = _Single3D(lib, wl, args.storage)
+    else:
+        runner = _Single(lib, wl, args.storage)
     nodes = runner.nodes
     K, W, S = args.steps, args.warmup, args.lb_steps
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=device)

@@ -63,7 +63,8 @@ class cdf_options(ctypes.Structure):
     _fields_ = [("storage", ctypes.c_int), ("rho0", ctypes.c_double), ("cuda_stream", ctypes.c_void_p),
                 ("phi_ref", ctypes.c_double * MAX_M), ("p_ref_grad", ctypes.c_double * 2),
                 ("block_x", ctypes.c_int), ("block_y", ctypes.c_int), ("resident", ctypes.c_int),
-                ("wait_timeout_s", ctypes.c_double), ("test_stall_tile", ctypes.c_int)]
+                ("wait_timeout_s", ctypes.c_double), ("test_stall_tile", ctypes.c_int),
+                ("prescribed_velocity", ctypes.c_int)]
 
 
 class cdf_info(ctypes.Structure):
@@ -95,6 +96,30 @@ _H = ctypes.c_void_p
 _lib = None
 
 # name -> (restype, argtypes); the C ABI of include/cdf_lb.h
+class cdf_grid3(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int)]
+
+
+class cdf_force3(ctypes.Structure):
+    _fields_ = [("g", ctypes.c_double * 3), ("beta", ctypes.c_double * MAX_M), ("phi_ref", ctypes.c_double * MAX_M),
+                ("F0", ctypes.c_double)]
+
+
+class cdf_boundaries3(ctypes.Structure):
+    _fields_ = [("side", cdf_side * 6)]
+
+
+class cdf_options3(ctypes.Structure):
+    _fields_ = [("rho0", ctypes.c_double), ("cuda_stream", ctypes.c_void_p), ("phi_ref", ctypes.c_double * MAX_M),
+                ("p_ref_grad", ctypes.c_double * 3), ("block_x", ctypes.c_int), ("block_y", ctypes.c_int)]
+
+
+class cdf_info3(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int), ("m", ctypes.c_int),
+                ("pitch", ctypes.c_int), ("block_x", ctypes.c_int), ("block_y", ctypes.c_int),
+                ("bytes_per_lup", ctypes.c_double), ("t", ctypes.c_longlong)]
+
+
 SIGNATURES = {
     "cdf_lb_create": (ctypes.c_int, [ctypes.POINTER(cdf_grid), ctypes.c_int, ctypes.POINTER(cdf_diffusion),
                                      ctypes.c_double, ctypes.POINTER(cdf_source), ctypes.POINTER(cdf_force),
@@ -129,6 +154,20 @@ SIGNATURES = {
     "cdf_batch_residuals": (ctypes.c_int, [_H, _DP]),
     "cdf_batch_stream": (ctypes.c_void_p, [_H]),
     "cdf_batch_destroy": (None, [_H]),
+    "cdf_lb3d_create": (ctypes.c_int, [ctypes.POINTER(cdf_grid3), ctypes.c_int, ctypes.POINTER(cdf_diffusion),
+                                       ctypes.c_double, ctypes.POINTER(cdf_source), ctypes.POINTER(cdf_force3),
+                                       ctypes.POINTER(cdf_boundaries3), ctypes.POINTER(cdf_options3),
+                                       ctypes.POINTER(ctypes.c_void_p)]),
+    "cdf_lb3d_init_moments": (ctypes.c_int, [_H, _DP, _DP, _DP]),
+    "cdf_lb3d_step": (ctypes.c_int, [_H, ctypes.c_longlong]),
+    "cdf_lb3d_run_to_steady": (ctypes.c_int, [_H, ctypes.c_double, ctypes.c_longlong, ctypes.c_longlong,
+                                              ctypes.POINTER(ctypes.c_longlong), _DP]),
+    "cdf_lb3d_moments": (ctypes.c_int, [_H, _DP]),
+    "cdf_lb3d_mass": (ctypes.c_int, [_H, _DP]),
+    "cdf_lb3d_populations": (ctypes.c_int, [_H, _DP, _DP]),
+    "cdf_lb3d_get_info": (ctypes.c_int, [_H, ctypes.POINTER(cdf_info3)]),
+    "cdf_lb3d_stream": (ctypes.c_void_p, [_H]),
+    "cdf_lb3d_destroy": (None, [_H]),
 }
 
 
@@ -279,6 +318,7 @@ def structs_from_problem(pb: Problem, storage: str = "fp32", stream: int = 0, bl
     if block is not None:
         opt.block_x, opt.block_y = block
     opt.resident, opt.wait_timeout_s, opt.test_stall_tile = int(resident), float(wait_timeout_s), int(test_stall_tile)
+    opt.prescribed_velocity = int(getattr(pb, "case1", False))
     return grid, dif, src, frc, bc, opt
 
 
@@ -525,3 +565,123 @@ class BatchSolver:
     @property
     def stream(self) -> int:
         return cdf_batch_stream(self.h)
+
+
+# ---- three-dimensional solver (include/cdf_lb3d.h) --------------------------------------------
+def structs3_from_problem(pb, stream: int = 0, block=None, phi_ref=None, p_ref_grad=None):
+    m = pb.m
+    grid = cdf_grid3(pb.nx, pb.ny, pb.nz)
+    dif = cdf_diffusion()
+    dif.kind = {"const": 0, "chemotaxis": 1}[pb.dkind]
+    for a in range(m):
+        for b in range(m):
+            dif.D[a * m + b] = float(pb.D[a, b])
+    dif.chi, dif.c_star, dif.eps, dif.r_regularised = pb.chi, pb.c_star, pb.eps, int(pb.r_regularised)
+    src = cdf_source()
+    src.kind = {"none": 0, "const": 1, "consumption": 2}[pb.skind]
+    src.k = pb.k
+    frc = cdf_force3()
+    for d in range(3):
+        frc.g[d] = float(pb.g[d])
+    frc.F0 = pb.F0
+    for a in range(m):
+        src.S[a] = float(pb.S[a])
+        frc.beta[a] = float(pb.beta[a])
+        frc.phi_ref[a] = float(pb.phi_ref[a])
+    bc = cdf_boundaries3()
+    for k, side in enumerate(pb.sides):
+        cs = bc.side[k]
+        cs.kind = {"periodic": 0, "wall": 1}[side.kind]
+        cs.fluid = 0
+        for a in range(m):
+            cs.scalar[a] = {"noflux": 0, "dirichlet": 1}[side.scalar[a]]
+            cs.value[a] = float(side.value[a])
+    opt = cdf_options3()
+    opt.rho0 = pb.rho0
+    opt.cuda_stream = stream or None
+    if phi_ref is None:
+        phi_ref = []
+        for a in range(m):
+            lo, hi = float(pb.phi0[a].min()), float(pb.phi0[a].max())
+            for side in pb.sides:
+                if side.kind == "wall" and side.scalar[a] == "dirichlet":
+                    lo, hi = min(lo, side.value[a]), max(hi, side.value[a])
+            phi_ref.append(0.5 * (lo + hi))
+    for a in range(m):
+        opt.phi_ref[a] = float(phi_ref[a])
+    if p_ref_grad is None:
+        mag = pb.F0 + sum(float(pb.beta[a]) * (float(pb.phi0[a].mean()) - float(pb.phi_ref[a])) for a in range(m))
+        p_ref_grad = [float(pb.g[d]) * mag for d in range(3)]
+    for d in range(3):
+        opt.p_ref_grad[d] = float(p_ref_grad[d])
+    if block is not None:
+        opt.block_x, opt.block_y = block
+    return grid, dif, src, frc, bc, opt
+
+
+class Solver3D:
+    """One 3-D lattice (D3Q7 scalars, D3Q19 fluid) on the GPU behind include/cdf_lb3d.h."""
+
+    def __init__(self, pb, stream: int = 0, block=None, init: bool = True):
+        self.pb = pb
+        self.m, self.nx, self.ny, self.nz = pb.m, pb.nx, pb.ny, pb.nz
+        self._structs = structs3_from_problem(pb, stream, block)
+        grid, dif, src, frc, bc, opt = self._structs
+        h = ctypes.c_void_p()
+        _check(load().cdf_lb3d_create(ctypes.byref(grid), pb.m, ctypes.byref(dif), pb.nu, ctypes.byref(src),
+                                      ctypes.byref(frc), ctypes.byref(bc), ctypes.byref(opt), ctypes.byref(h)))
+        self.h = h
+        if init:
+            self.init_moments(pb.phi0, pb.u0, pb.p0)
+
+    def close(self):
+        if getattr(self, "h", None):
+            load().cdf_lb3d_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def init_moments(self, phi, u, p=None):
+        f64 = lambda a: np.ascontiguousarray(a, np.float64)  # noqa: E731
+        _check(load().cdf_lb3d_init_moments(self.h, _dptr(f64(phi)), _dptr(f64(u)),
+                                            None if p is None else _dptr(f64(p))))
+
+    def step(self, n: int = 1):
+        _check(load().cdf_lb3d_step(self.h, int(n)))
+
+    def run_to_steady(self, tol: float, check_every: int = 1000, max_steps: int = 10 ** 7):
+        steps, res = ctypes.c_longlong(), ctypes.c_double()
+        st = load().cdf_lb3d_run_to_steady(self.h, tol, check_every, max_steps, ctypes.byref(steps),
+                                           ctypes.byref(res))
+        if st not in (CDF_OK, CDF_ENOTCONVERGED):
+            _check(st)
+        return st == CDF_OK, steps.value, res.value
+
+    def moments(self) -> np.ndarray:
+        out = np.empty((self.m + 4, self.nz, self.ny, self.nx))
+        _check(load().cdf_lb3d_moments(self.h, _dptr(out)))
+        return out
+
+    def mass(self) -> np.ndarray:
+        out = np.empty(self.m)
+        _check(load().cdf_lb3d_mass(self.h, _dptr(out)))
+        return out
+
+    def populations(self):
+        f = np.empty((self.m, 7, self.nz, self.ny, self.nx))
+        hf = np.empty((19, self.nz, self.ny, self.nx))
+        _check(load().cdf_lb3d_populations(self.h, _dptr(f), _dptr(hf)))
+        return f, hf
+
+    def info(self) -> cdf_info3:
+        out = cdf_info3()
+        _check(load().cdf_lb3d_get_info(self.h, ctypes.byref(out)))
+        return out
+
+    @property
+    def stream(self) -> int:
+        return load().cdf_lb3d_stream(self.h)

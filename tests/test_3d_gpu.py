@@ -1,0 +1,139 @@
+"""The 3-D solver (include/cdf_lb3d.h: D3Q7 scalars, D3Q19 fluid) against the
+3-D FP64 oracle (oracle/cdf_oracle3d.c), element by element on the same seeded
+inputs.  Tolerance: relative L2 <= 1e-5 per field (FP32 populations); the
+pressure against max(||p||, ||u||/3), its FP32 storage floor (the fluid
+populations carry the velocity term ~|u|/3)."""
+
+import numpy as np
+import pytest
+
+from oracle import oracle3d as O3
+from paper_2101_03055_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+TOL32 = 1e-5
+
+
+@pytest.fixture(scope="module")
+def o3():
+    O3.build()
+    return O3
+
+
+def rel(a, b):
+    nb = np.linalg.norm(b)
+    return float(np.linalg.norm(a - b) / (nb if nb > 0 else 1.0))
+
+
+def compare(cdf, o3, pb, steps, block=None, tol=TOL32):
+    s = cdf.Solver3D(pb, block=block)
+    o = o3.Sim(pb)
+    s.step(steps)
+    o.step(steps)
+    Mg, Mo = s.moments(), o.moments()
+    m = pb.m
+    errs = {f"phi{a}": rel(Mg[a], Mo[a]) for a in range(m)}
+    errs["u"] = rel(Mg[m:m + 3], Mo[m:m + 3])
+    pscale = max(np.linalg.norm(Mo[m + 3]), np.linalg.norm(Mo[m:m + 3]) / 3.0)
+    errs["p"] = float(np.linalg.norm(Mg[m + 3] - Mo[m + 3]) / (pscale if pscale > 0 else 1.0))
+    bad = {k: v for k, v in errs.items() if not v <= tol}
+    assert not bad, errs
+    fg, hg = s.populations()
+    fo, ho = o.post_collision()
+    assert rel(fg, fo) <= tol and rel(hg, ho) <= tol
+    return s, errs
+
+
+def chemotaxis3d(n=(24, 16, 20), seed=1):
+    """Bacteria (n) and oxygen (c) in a box: chemotactic cross term D_01 =
+    -chi n r(c) with the regularised cut-off, consumption, gravity along -z on n,
+    oxygen Dirichlet (c = 1) at the top z wall, walls elsewhere."""
+    nx, ny, nz = n
+    m = 2
+    top = I.wall_side(m, I.NOSLIP, [I.NOFLUX, I.DIRICHLET], [0.0, 1.0])
+    sides = [I.wall_side(m) for _ in range(5)] + [top]
+    N = nx * ny * nz
+    phi0 = np.stack([1.0 + 0.05 * (2 * I.uniform(seed, np.arange(N)) - 1).reshape(nz, ny, nx),
+                     np.ones((nz, ny, nx))])
+    return I.Problem3D("chemotaxis3d", nx, ny, nz, m, np.diag([0.05, 0.25]), 0.25, dkind="chemotaxis", chi=0.5,
+                       c_star=0.3, eps=0.05, r_regularised=True, skind="consumption", k=2e-4,
+                       g=(0.0, 0.0, -5e-4), beta=np.array([1.0, 0.0]), phi_ref=np.array([1.0, 0.0]), sides=sides,
+                       phi0=phi0)
+
+
+def test_periodic_taylor_green_box(cdf, o3):
+    _, errs = compare(cdf, o3, I.periodic_box3d(24, 20, 16, u0=0.03), 150)
+    print("periodic 24x20x16 x 150:", errs)
+
+
+def test_double_diffusive_cube(cdf, o3):
+    pb = I.ddc_cavity3d(20, Ra=1e5, Pr=0.7, Le=2.0, Nc=1.0, Df=0.2, Sr=0.2)
+    r = np.random.default_rng(3)
+    phi0 = np.clip(0.5 + 0.2 * r.standard_normal((2, 20, 20, 20)), 0, 1)
+    u0 = 0.01 * r.standard_normal((3, 20, 20, 20))
+    _, errs = compare(cdf, o3, pb.replace(phi0=phi0, u0=u0), 400)
+    print("DDC cube 20^3 x 400:", errs)
+
+
+def test_chemotaxis_box(cdf, o3):
+    _, errs = compare(cdf, o3, chemotaxis3d(), 300)
+    print("chemotaxis 24x16x20 x 300:", errs)
+
+
+@pytest.mark.parametrize("dims", [(1, 1, 1), (9, 1, 1), (1, 9, 1), (1, 1, 9), (7, 5, 3), (33, 9, 4)])
+def test_degenerate_and_ragged_sizes(cdf, o3, dims):
+    nx, ny, nz = dims
+    pb = I.periodic_box3d(nx, ny, nz, u0=0.02, seed=4)
+    sides = []
+    for n in dims:
+        if n < 3:
+            sides += [I.periodic_side(2), I.periodic_side(2)]
+        else:
+            sides += [I.wall_side(2, I.NOSLIP, [I.DIRICHLET, I.NOFLUX], [1.1, 0.0]), I.wall_side(2)]
+    compare(cdf, o3, pb.replace(sides=sides, g=(1e-5, -2e-5, 3e-5), beta=np.array([1.0, -0.5]),
+                                phi_ref=np.array([1.0, 1.0])), 40)
+
+
+@pytest.mark.parametrize("m", [1, 3])
+def test_other_scalar_counts(cdf, o3, m):
+    r = np.random.default_rng(m)
+    A = 0.03 * r.standard_normal((m, m))
+    D = A @ A.T + np.diag(r.uniform(0.02, 0.1, m))
+    pb = I.periodic_box3d(12, 10, 8, m=m, D=D, u0=0.02, seed=m)
+    compare(cdf, o3, pb.replace(sides=[I.wall_side(m) for _ in range(6)]), 60)
+
+
+def test_block_shapes_graphs_and_mass(cdf):
+    pb = I.periodic_box3d(40, 24, 12, u0=0.03)
+    ref = None
+    for blk in [(32, 4), (64, 2), (128, 1)]:
+        s = cdf.Solver3D(pb, block=blk)
+        m0 = s.mass()
+        s.step(70)
+        M = s.moments()
+        if ref is None:
+            ref = M
+            assert np.abs(s.mass() / m0 - 1).max() < 1e-6
+        else:
+            assert np.array_equal(M, ref), blk
+    a, b = cdf.Solver3D(pb), cdf.Solver3D(pb)
+    a.step(64)
+    for _ in range(64):
+        b.step(1)
+    assert np.array_equal(a.moments(), b.moments())
+
+
+def test_run_to_steady_linear_profile(cdf):
+    n = 12
+    hot = I.wall_side(2, I.NOSLIP, [I.DIRICHLET] * 2, [1.0, 1.0])
+    cold = I.wall_side(2, I.NOSLIP, [I.DIRICHLET] * 2, [0.0, 0.0])
+    pb = I.periodic_box3d(n, 6, 5, u0=0.0).replace(sides=[hot, cold] + [I.wall_side(2) for _ in range(4)],
+                                                    phi0=np.full((2, 5, 6, n), 0.5))
+    s = cdf.Solver3D(pb)
+    ok, steps, R = s.run_to_steady(1e-7, 500, 200_000)
+    assert ok, (steps, R)
+    M = s.moments()
+    want = 1.0 - (np.arange(n) + 0.5) / n
+    np.testing.assert_allclose(M[0], np.broadcast_to(want, M[0].shape), atol=2e-5)
+    with pytest.raises(RuntimeError):
+        cdf.Solver3D(I.periodic_box3d(8, m=4, D=np.eye(4) * 0.05))

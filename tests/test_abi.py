@@ -50,13 +50,17 @@ def test_binding_covers_the_header():
 
 def test_struct_layout_matches_c(tmp_path):
     structs = ["cdf_grid", "cdf_diffusion", "cdf_source", "cdf_force", "cdf_side", "cdf_boundaries",
-               "cdf_options", "cdf_info"]
+               "cdf_options", "cdf_info", "cdf_grid3", "cdf_force3", "cdf_boundaries3", "cdf_options3", "cdf_info3",
+               "cdf_batch_options", "cdf_batch_info"]
     src = tmp_path / "probe.c"
-    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "cdf_lb.h"', "int main(void){"]
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "cdf_lb.h"', '#include "cdf_lb3d.h"',
+             "int main(void){"]
     for s in structs:
         lines.append(f'printf("{s} %zu\\n", sizeof({s}));')
     lines.append('printf("opt.cuda_stream %zu\\n", offsetof(cdf_options, cuda_stream));')
     lines.append('printf("info.bytes_per_lup %zu\\n", offsetof(cdf_info, bytes_per_lup));')
+    lines.append('printf("opt.prescribed_velocity %zu\\n", offsetof(cdf_options, prescribed_velocity));')
+    lines.append('printf("opt3.block_y %zu\\n", offsetof(cdf_options3, block_y));')
     lines.append("return 0;}")
     src.write_text("\n".join(lines))
     exe = tmp_path / "probe"
@@ -66,6 +70,8 @@ def test_struct_layout_matches_c(tmp_path):
         assert int(got[s]) == ctypes.sizeof(getattr(lib, s)), s
     assert int(got["opt.cuda_stream"]) == lib.cdf_options.cuda_stream.offset
     assert int(got["info.bytes_per_lup"]) == lib.cdf_info.bytes_per_lup.offset
+    assert int(got["opt.prescribed_velocity"]) == lib.cdf_options.prescribed_velocity.offset
+    assert int(got["opt3.block_y"]) == lib.cdf_options3.block_y.offset
 
 
 def _create_status(pb, **kw):
