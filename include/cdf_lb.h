@@ -131,6 +131,13 @@ typedef struct {
     int test_stall_tile;               /* test hook: k > 0 makes tile k - 1 of the resident step
                                           never publish its step, so the waits of its neighbours
                                           run out (CDF_ETIMEOUT); 0 in normal use */
+    int prescribed_velocity;           /* 1: Case 1 of Sec. 2.1 -- the convection cross-diffusion
+                                          equations alone in a steady prescribed velocity, no fluid
+                                          populations.  The u passed to the init calls is that
+                                          velocity (p is ignored and reported as 0); nu (still
+                                          > 0) is not used and the force must be zero; G comes
+                                          from the first-order difference u (phi(t) - phi(t - 1)).
+                                          FP32 storage only. */
 } cdf_options;
 
 /* Facts about a handle (for benchmarks and tests). */

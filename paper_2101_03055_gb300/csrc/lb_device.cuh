@@ -138,55 +138,44 @@ __device__ __forceinline__ float fluid_equilibrium(int i, float prd, float ux, f
     return __fmul_rn(kA9(i), (prd + cu) + fmaf(__fmul_rn(1.5f, cu), cu, __fmul_rn(-0.5f, usq)));
 }
 
-// Collision of one node (Eqs. evolution12, evolution3) in deviation variables.
-// f, h: pre-collision deviations, overwritten by the post-collision ones.  prx:
-// p_ref at the node.  sp1: S_1(t-1) of the consumption closure; `first` uses
-// S(t-1) = S(t) (initialisation).
+// Scalar moments of one node (Eq. sum-phi) and the closures of Sec. 3 that
+// depend on them: the cut-off r(phi_1), the source S(phi) and S(t - 1).
+// sp1: S_1(t-1) of the consumption closure; `first` uses S(t-1) = S(t).
 template <int M>
-__device__ __forceinline__ void collide(const LbParams &p, float (&f)[M][5], float (&h)[9], float prx,
-                                        float sp1, bool first, NodeOut<M> &o) {
-    // Eq. sum-phi and the closures of Sec. 3
-    float phid[M], phi[M];
+struct ScalarState {
+    float phid[M], phi[M], S[M], Sp[M], r;
+};
+template <int M>
+__device__ __forceinline__ void scalar_closures(const LbParams &p, const float (&f)[M][5], float sp1, bool first,
+                                                ScalarState<M> &s) {
 #pragma unroll
     for (int a = 0; a < M; ++a) {
-        phid[a] = ((f[a][0] + f[a][1]) + (f[a][2] + f[a][3])) + f[a][4];
-        phi[a] = p.phi_ref[a] + phid[a];
+        s.phid[a] = ((f[a][0] + f[a][1]) + (f[a][2] + f[a][3])) + f[a][4];
+        s.phi[a] = p.phi_ref[a] + s.phid[a];
     }
-    float r = 0.f;
-    if (M >= 2 && (p.chemotaxis || p.skind == 2)) r = cutoff(p, phi[M >= 2 ? 1 : 0]);
-    float S[M], Sp[M];
+    s.r = 0.f;
+    if (M >= 2 && (p.chemotaxis || p.skind == 2)) s.r = cutoff(p, s.phi[M >= 2 ? 1 : 0]);
 #pragma unroll
     for (int a = 0; a < M; ++a) {
-        S[a] = (p.skind == 1) ? p.S[a] : 0.f;
-        Sp[a] = S[a];
+        s.S[a] = (p.skind == 1) ? p.S[a] : 0.f;
+        s.Sp[a] = s.S[a];
     }
     if (M >= 2 && p.skind == 2) {
-        S[1] = -p.k * phi[0] * r;
-        Sp[1] = first ? S[1] : sp1;
+        s.S[1] = -p.k * s.phi[0] * s.r;
+        s.Sp[1] = first ? s.S[1] : sp1;
     }
-    float fm = p.Fbase;
-#pragma unroll
-    for (int a = 0; a < M; ++a) fm = fmaf(p.beta[a], phi[a], fm);
-    const float Fx = p.g[0] * fm, Fy = p.g[1] * fm;
+}
 
-    // Eq. sum-u and Eq. sum-p (varphi = 0):
-    // p = cs^2/(1 - W0) [sum_{i!=0} h_i - W0 u.u / (2 cs^2)] = (sum_{i!=0} h_i - kQ u.u) / kC
-    const float jx = (h[1] - h[3]) + (h[5] - h[6]) + (h[8] - h[7]);
-    const float jy = (h[2] - h[4]) + (h[5] - h[8]) + (h[6] - h[7]);
-    const float ux = fmaf(0.5f, Fx, jx), uy = fmaf(0.5f, Fy, jy);
-    const float usq = usq_of(ux, uy);
-    const float snr = ((h[1] + h[2]) + (h[3] + h[4])) + ((h[5] + h[6]) + (h[7] + h[8]));
-    const float prd = fmaf(-kQ, usq, snr) / kC;
-
-    // Eq. omega-D.  Constant D: omega from the host.  Chemotaxis: omega^-1 =
-    // B + delta e_0 e_1^T with delta = -3 chi phi_0 r, inverted by Sherman-Morrison.
-    float om[M][M];
+// Eq. omega-D.  Constant D: omega from the host.  Chemotaxis: omega^-1 =
+// B + delta e_0 e_1^T with delta = -3 chi phi_0 r, inverted by Sherman-Morrison.
+template <int M>
+__device__ __forceinline__ void relaxation_matrix(const LbParams &p, const ScalarState<M> &s, float (&om)[M][M]) {
 #pragma unroll
     for (int a = 0; a < M; ++a)
 #pragma unroll
         for (int b = 0; b < M; ++b) om[a][b] = p.omega[a * M + b];
     if (M >= 2 && p.chemotaxis) {
-        const float delta = -p.chi3 * phi[0] * r;
+        const float delta = -p.chi3 * s.phi[0] * s.r;
         const float den = 1.f / fmaf(delta, om[M >= 2 ? 1 : 0][0], 1.f);
         float col0[M], row1[M];
 #pragma unroll
@@ -196,26 +185,17 @@ __device__ __forceinline__ void collide(const LbParams &p, float (&f)[M][5], flo
 #pragma unroll
             for (int b = 0; b < M; ++b) om[a][b] = fmaf(-__fmul_rn(__fmul_rn(delta, den), col0[a]), row1[b], om[a][b]);
     }
+}
 
-    // Eq. Gi: G_{i,a} = 3 W_i c_i . J_a,  J_a = sum_b (delta_ab - omega_ab / 2)(u S_b + phi_b F)
-    float Jx[M], Jy[M];
-#pragma unroll
-    for (int a = 0; a < M; ++a) {
-        float jxa = 0.f, jya = 0.f;
-#pragma unroll
-        for (int b = 0; b < M; ++b) {
-            const float c = fmaf(-0.5f, om[a][b], a == b ? 1.f : 0.f);
-            jxa = fmaf(c, fmaf(ux, S[b], phi[b] * Fx), jxa);
-            jya = fmaf(c, fmaf(uy, S[b], phi[b] * Fy), jya);
-        }
-        Jx[a] = jxa;
-        Jy[a] = jya;
-    }
-
-    // Eq. evolution12: f*_i,a = f_i,a - sum_b omega_ab (f_i,b - f^eq_i,b) + W_i S_a
-    // + (W_i S_a - W_i S_a(t-1)) / 2 + G_i,a
+// Eq. evolution12 for the scalars of one node: f*_i,a = f_i,a - sum_b omega_ab
+// (f_i,b - f^eq_i,b) + W_i S_a + (W_i S_a - W_i S_a(t-1)) / 2 + G_i,a with the
+// auxiliary source G_i,a = 3 W_i c_i . J_a (J from Eq. Gi, or from the time
+// difference of phi u in Case 1 of Sec. 2.1).
+template <int M>
+__device__ __forceinline__ void scalar_collide(float (&f)[M][5], const ScalarState<M> &s, float ux, float uy,
+                                               const float (&om)[M][M], const float (&Jx)[M], const float (&Jy)[M]) {
     float feq[M][5];
-    scalar_equilibrium<M>(phid, phi, ux, uy, feq);
+    scalar_equilibrium<M>(s.phid, s.phi, ux, uy, feq);
 #pragma unroll
     for (int i = 0; i < 5; ++i) {
         float neq[M];
@@ -227,9 +207,52 @@ __device__ __forceinline__ void collide(const LbParams &p, float (&f)[M][5], flo
 #pragma unroll
             for (int b = 0; b < M; ++b) coll = fmaf(om[a][b], neq[b], coll);
             const float G = (i == 0) ? 0.f : __fmul_rn(3.f * kW5, kC5x(i) * Jx[a] + kC5y(i) * Jy[a]);
-            f[a][i] = (f[a][i] - coll) + fmaf(kWs(i), fmaf(1.5f, S[a], __fmul_rn(-0.5f, Sp[a])), G);
+            f[a][i] = (f[a][i] - coll) + fmaf(kWs(i), fmaf(1.5f, s.S[a], __fmul_rn(-0.5f, s.Sp[a])), G);
         }
     }
+}
+
+// Collision of one node (Eqs. evolution12, evolution3) in deviation variables.
+// f, h: pre-collision deviations, overwritten by the post-collision ones.  prx:
+// p_ref at the node.  sp1: S_1(t-1) of the consumption closure; `first` uses
+// S(t-1) = S(t) (initialisation).
+template <int M>
+__device__ __forceinline__ void collide(const LbParams &p, float (&f)[M][5], float (&h)[9], float prx,
+                                        float sp1, bool first, NodeOut<M> &o) {
+    ScalarState<M> s;
+    scalar_closures<M>(p, f, sp1, first, s);
+    float fm = p.Fbase;
+#pragma unroll
+    for (int a = 0; a < M; ++a) fm = fmaf(p.beta[a], s.phi[a], fm);
+    const float Fx = p.g[0] * fm, Fy = p.g[1] * fm;
+
+    // Eq. sum-u and Eq. sum-p (varphi = 0):
+    // p = cs^2/(1 - W0) [sum_{i!=0} h_i - W0 u.u / (2 cs^2)] = (sum_{i!=0} h_i - kQ u.u) / kC
+    const float jx = (h[1] - h[3]) + (h[5] - h[6]) + (h[8] - h[7]);
+    const float jy = (h[2] - h[4]) + (h[5] - h[8]) + (h[6] - h[7]);
+    const float ux = fmaf(0.5f, Fx, jx), uy = fmaf(0.5f, Fy, jy);
+    const float usq = usq_of(ux, uy);
+    const float snr = ((h[1] + h[2]) + (h[3] + h[4])) + ((h[5] + h[6]) + (h[7] + h[8]));
+    const float prd = fmaf(-kQ, usq, snr) / kC;
+
+    float om[M][M];
+    relaxation_matrix<M>(p, s, om);
+
+    // Eq. Gi: G_{i,a} = 3 W_i c_i . J_a,  J_a = sum_b (delta_ab - omega_ab / 2)(u S_b + phi_b F)
+    float Jx[M], Jy[M];
+#pragma unroll
+    for (int a = 0; a < M; ++a) {
+        float jxa = 0.f, jya = 0.f;
+#pragma unroll
+        for (int b = 0; b < M; ++b) {
+            const float c = fmaf(-0.5f, om[a][b], a == b ? 1.f : 0.f);
+            jxa = fmaf(c, fmaf(ux, s.S[b], s.phi[b] * Fx), jxa);
+            jya = fmaf(c, fmaf(uy, s.S[b], s.phi[b] * Fy), jya);
+        }
+        Jx[a] = jxa;
+        Jy[a] = jya;
+    }
+    scalar_collide<M>(f, s, ux, uy, om, Jx, Jy);
 
     // Eq. evolution3 with Eq. force (varphi = 0): F_i = 3 W_i c_i.F, weighted by (1 - omega_f / 2).
     const float wf = p.omega_f, fw = 1.f - 0.5f * wf;
@@ -240,11 +263,44 @@ __device__ __forceinline__ void collide(const LbParams &p, float (&f)[M][5], flo
         h[i] = fmaf(fw, Fi, fmaf(-wf, h[i] - heq, h[i]));
     }
 #pragma unroll
-    for (int a = 0; a < M; ++a) o.phi[a] = phi[a];
+    for (int a = 0; a < M; ++a) o.phi[a] = s.phi[a];
     o.ux = ux;
     o.uy = uy;
     o.pr = prx + prd;
-    o.s1 = (M >= 2) ? S[M >= 2 ? 1 : 0] : 0.f;
+    o.s1 = (M >= 2) ? s.S[M >= 2 ? 1 : 0] : 0.f;
+}
+
+// Case 1 of Sec. 2.1: the convection cross-diffusion equations in a prescribed
+// steady velocity (ux, uy), no fluid.  The auxiliary source is
+// G_i,a = sum_b (delta_ab - omega_ab / 2) W_i c_i . d_t(phi_b u) / cs^2 with the
+// first-order explicit difference d_t(phi_b u) = u (phi_b - phi_prev_b).
+// phi_prev: phi(t - 1), overwritten with phi(t).
+template <int M>
+__device__ __forceinline__ void collide_case1(const LbParams &p, float (&f)[M][5], float ux, float uy,
+                                              float (&phi_prev)[M], float sp1, bool first, NodeOut<M> &o) {
+    ScalarState<M> s;
+    scalar_closures<M>(p, f, sp1, first, s);
+    float om[M][M];
+    relaxation_matrix<M>(p, s, om);
+    float Jx[M], Jy[M];
+#pragma unroll
+    for (int a = 0; a < M; ++a) {
+        float ja = 0.f;
+#pragma unroll
+        for (int b = 0; b < M; ++b) ja = fmaf(fmaf(-0.5f, om[a][b], a == b ? 1.f : 0.f), s.phi[b] - phi_prev[b], ja);
+        Jx[a] = __fmul_rn(ux, ja);
+        Jy[a] = __fmul_rn(uy, ja);
+    }
+    scalar_collide<M>(f, s, ux, uy, om, Jx, Jy);
+#pragma unroll
+    for (int a = 0; a < M; ++a) {
+        o.phi[a] = s.phi[a];
+        phi_prev[a] = s.phi[a];
+    }
+    o.ux = ux;
+    o.uy = uy;
+    o.pr = 0.f;
+    o.s1 = (M >= 2) ? s.S[M >= 2 ? 1 : 0] : 0.f;
 }
 
 template <int M>
@@ -395,6 +451,27 @@ __device__ __forceinline__ void pull_node(const LbParams &p, int x, int y, const
         for (int i = 0; i < 5; ++i) f[a][i] = ld(9 + 5 * a + t.splane[i], t.spos[i]);
 #pragma unroll
     for (int i = 0; i < 9; ++i) h[i] += t.hshift[i];
+    if (!kInterior) {
+#pragma unroll
+        for (int i = 1; i < 5; ++i) {
+            if (t.side[i] >= 0) {
+#pragma unroll
+                for (int a = 0; a < M; ++a)
+                    if ((p.dirichlet[t.side[i]] >> a) & 1u) f[a][i] = p.abb[t.side[i]][a] - f[a][i];
+            }
+        }
+    }
+}
+
+// The scalar part of pull_node (Case 1 of Sec. 2.1 has no fluid populations).
+template <int M, bool kInterior, class MakePos, class Load>
+__device__ __forceinline__ void pull_scalars(const LbParams &p, int x, int y, const MakePos &mk, const Load &ld,
+                                             float (&f)[M][5]) {
+    const auto t = pull_table<kInterior>(p, x, y, mk);
+#pragma unroll
+    for (int a = 0; a < M; ++a)
+#pragma unroll
+        for (int i = 0; i < 5; ++i) f[a][i] = ld(9 + 5 * a + t.splane[i], t.spos[i]);
     if (!kInterior) {
 #pragma unroll
         for (int i = 1; i < 5; ++i) {

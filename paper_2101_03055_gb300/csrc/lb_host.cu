@@ -115,6 +115,7 @@ struct cdf_lb {
     void *buf[2] = {nullptr, nullptr};
     int cur = 0;  // buffer that holds the current post-collision populations
     float *sprev = nullptr;
+    float *vel = nullptr;  // Case 1: prescribed velocity and phi(t - 1), 2 + m planes
     float *mom = nullptr, *mom_prev = nullptr;
     bool mr = false;                       // 16-bit storage: node-equilibrium deviations
     float *mom_pp[2] = {nullptr, nullptr};  // 16-bit storage: moments beside buf[0], buf[1]
@@ -147,6 +148,7 @@ void release(cdf_lb *h) {
     cudaFree(h->buf[0]);
     cudaFree(h->buf[1]);
     cudaFree(h->sprev);
+    cudaFree(h->vel);
     cudaFree(h->mom);
     cudaFree(h->mom_prev);
     cudaFree(h->mom_pp[0]);
@@ -298,7 +300,7 @@ cdf_status autotune(cdf_lb *h) {
     // block.y == 0 marks a flat launch (one thread per node in row order)
     std::vector<dim3> cands = {dim3(32, 4), dim3(32, 8), dim3(64, 2), dim3(64, 4),
                                dim3(128, 1), dim3(128, 2), dim3(256, 1)};
-    if (!h->mr) {
+    if (!h->mr && !h->P.case1) {
         cands.push_back(dim3(128, 0));
         cands.push_back(dim3(256, 0));
     }
@@ -361,7 +363,7 @@ cdf_status time_steps(cdf_lb *h, long long steps, float *ms) {
 // for, never when refused or when the lattice does not fit, otherwise when it
 // measures faster than the graph-launched kernel with the autotuned block.
 cdf_status setup_resident(cdf_lb *h, const cdf_options *opt) {
-    if (h->storage != CDF_FP32 || opt->resident == -1) return CDF_OK;
+    if (h->storage != CDF_FP32 || opt->resident == -1 || h->P.case1) return CDF_OK;
     if (!plan_resident(h->nx, h->ny, h->m, h->P.periodic_x, h->P.periodic_y, &h->rg)) {
         cudaGetLastError();
         if (opt->resident == 1) return fail(CDF_EINVAL, "the lattice does not fit the resident step");
@@ -541,6 +543,14 @@ cdf_status cdf_lb_create(const cdf_grid *grid, int m, const cdf_diffusion *dif, 
         return fail(CDF_EINVAL, "bad resident-step options");
     if (opt->resident == 1 && opt->storage != CDF_FP32)
         return fail(CDF_EINVAL, "the resident step exists for FP32 storage only");
+    if (opt->prescribed_velocity != 0 && opt->prescribed_velocity != 1)
+        return fail(CDF_EINVAL, "prescribed_velocity must be 0 or 1");
+    if (opt->prescribed_velocity && opt->storage != CDF_FP32)
+        return fail(CDF_EINVAL, "the prescribed-velocity mode (Case 1) stores FP32 populations");
+    if (opt->prescribed_velocity && opt->resident == 1)
+        return fail(CDF_EINVAL, "the resident step does not run the prescribed-velocity mode");
+    if (opt->prescribed_velocity && (frc->g[0] != 0.0 || frc->g[1] != 0.0))
+        return fail(CDF_EINVAL, "the prescribed-velocity mode has no force: set g = 0");
     if (!(opt->rho0 > 0.0)) return fail(CDF_EINVAL, "rho0 must be positive");
     LbParams P0{};
     const int align = opt->storage == CDF_FP32 ? 32 : 64;  // 128-byte rows
@@ -571,6 +581,7 @@ cdf_status cdf_lb_create(const cdf_grid *grid, int m, const cdf_diffusion *dif, 
     h->user = static_cast<cudaStream_t>(opt->cuda_stream);
 
     h->P = P0;
+    h->P.case1 = opt->prescribed_velocity;
 
     DeviceGuard g(h->device);
     const size_t esz = elem_size(h->storage);
@@ -579,6 +590,7 @@ cdf_status cdf_lb_create(const cdf_grid *grid, int m, const cdf_diffusion *dif, 
     auto alloc = [&](void **p, size_t bytes) -> bool { return cudaMalloc(p, bytes) == cudaSuccess; };
     bool ok = alloc(&h->buf[0], pop_bytes) && alloc(&h->buf[1], pop_bytes) &&
               alloc((void **)&h->sprev, (size_t)h->plane * 4) &&
+              (!h->P.case1 || alloc((void **)&h->vel, (size_t)(2 + m) * h->plane * 4)) &&
               alloc((void **)&h->mom, (size_t)(m + 3) * h->plane * 4) &&
               alloc((void **)&h->mom_prev, (size_t)(m + 3) * h->plane * 4) &&
               (!h->mr || (alloc((void **)&h->mom_pp[0], (size_t)(m + 3) * h->plane * 4) &&
@@ -593,6 +605,7 @@ cdf_status cdf_lb_create(const cdf_grid *grid, int m, const cdf_diffusion *dif, 
         release(h);
         return fail(CDF_ENOMEM, "device allocation of %.1f MB failed", 2.0 * pop_bytes / 1e6);
     }
+    h->P.vel = h->vel;
     if (cudaStreamCreateWithFlags(&h->s, cudaStreamNonBlocking) != cudaSuccess ||
         cudaEventCreateWithFlags(&h->ev_in, cudaEventDisableTiming) != cudaSuccess ||
         cudaEventCreateWithFlags(&h->ev_out, cudaEventDisableTiming) != cudaSuccess) {
@@ -818,16 +831,19 @@ cdf_status cdf_lb_save(cdf_lb *h, const char *path) {
     if (st != CDF_OK) return st;
     const size_t pop = (size_t)h->planes * h->plane * elem_size(h->storage);
     const size_t spb = (size_t)h->plane * 4, momb = (size_t)(h->m + 3) * h->plane * 4;
-    std::vector<char> data(pop + spb + momb);
+    const size_t velb = h->P.case1 ? (size_t)(2 + h->m) * h->plane * 4 : 0;
+    std::vector<char> data(pop + spb + momb + velb);
     CK(cudaMemcpyAsync(data.data(), h->buf[h->cur], pop, cudaMemcpyDeviceToHost, h->s));
     CK(cudaMemcpyAsync(data.data() + pop, h->sprev, spb, cudaMemcpyDeviceToHost, h->s));
     CK(cudaMemcpyAsync(data.data() + pop + spb, current_moments(h), momb, cudaMemcpyDeviceToHost, h->s));
+    if (velb) CK(cudaMemcpyAsync(data.data() + pop + spb + momb, h->vel, velb, cudaMemcpyDeviceToHost, h->s));
     if ((st = sync(h)) != CDF_OK) return st;
     FileHeader hd{};
     std::memcpy(hd.magic, kMagic, 8);
     hd.version = 1;
     hd.nx = h->nx; hd.ny = h->ny; hd.m = h->m; hd.storage = h->storage;
     hd.planes = h->planes; hd.sprev_planes = h->sprev_planes; hd.pitch = h->pitch; hd.t = h->t;
+    hd.reserved[0] = h->P.case1;
     for (int a = 0; a < kMaxM; ++a) hd.phi_ref[a] = h->P.phi_ref[a];
     hd.gref[0] = h->P.gref[0];
     hd.gref[1] = h->P.gref[1];
@@ -851,6 +867,7 @@ cdf_status cdf_lb_load(cdf_lb *h, const char *path) {
     }
     if (hd.nx != h->nx || hd.ny != h->ny || hd.m != h->m || hd.storage != h->storage ||
         hd.planes != h->planes || hd.sprev_planes != h->sprev_planes || hd.pitch != h->pitch ||
+        hd.reserved[0] != h->P.case1 ||
         std::memcmp(hd.phi_ref, h->P.phi_ref, sizeof hd.phi_ref) != 0 || hd.gref[0] != h->P.gref[0] ||
         hd.gref[1] != h->P.gref[1]) {
         std::fclose(fp);
@@ -858,7 +875,8 @@ cdf_status cdf_lb_load(cdf_lb *h, const char *path) {
     }
     const size_t pop = (size_t)h->planes * h->plane * elem_size(h->storage);
     const size_t spb = (size_t)h->plane * 4, momb = (size_t)(h->m + 3) * h->plane * 4;
-    std::vector<char> data(pop + spb + momb);
+    const size_t velb = h->P.case1 ? (size_t)(2 + h->m) * h->plane * 4 : 0;
+    std::vector<char> data(pop + spb + momb + velb);
     const bool ok = std::fread(data.data(), 1, data.size(), fp) == data.size();
     std::fclose(fp);
     if (!ok) return fail(CDF_EIO, "%s is truncated", path);
@@ -869,6 +887,7 @@ cdf_status cdf_lb_load(cdf_lb *h, const char *path) {
     CK(cudaMemcpyAsync(h->buf[0], data.data(), pop, cudaMemcpyHostToDevice, h->s));
     CK(cudaMemcpyAsync(h->sprev, data.data() + pop, spb, cudaMemcpyHostToDevice, h->s));
     CK(cudaMemcpyAsync(current_moments(h), data.data() + pop + spb, momb, cudaMemcpyHostToDevice, h->s));
+    if (velb) CK(cudaMemcpyAsync(h->vel, data.data() + pop + spb + momb, velb, cudaMemcpyHostToDevice, h->s));
     if ((st = reset_resident(h)) != CDF_OK) return st;
     CK(cudaStreamSynchronize(h->s));
     h->t = hd.t;
@@ -887,6 +906,8 @@ cdf_status cdf_lb_get_info(const cdf_lb *h, cdf_info *out) {
     out->tiles = h->resident ? h->rg.tiles_x * h->rg.tiles_y : 0;
     out->bytes_per_lup = 2.0 * h->planes * (double)elem_size(h->storage) + 8.0 * h->sprev_planes +
                          (h->mr ? 2.0 * 4.0 * (h->m + 3) : 0.0);
+    if (h->P.case1)  // scalars read and written, u read, phi(t - 1) read and written
+        out->bytes_per_lup = 2.0 * 5 * h->m * 4.0 + 8.0 + 8.0 * h->m + 8.0 * h->sprev_planes;
     out->t = h->t;
     return CDF_OK;
 }

@@ -41,6 +41,10 @@ struct LbParams {
     float phi_ref[kMaxM];
     float gref[2];
     float xc, yc;
+    // Case 1 of Sec. 2.1 (no fluid populations): planes of the prescribed
+    // velocity u_x, u_y and of phi_a(t - 1), `plane` floats each (device memory).
+    int case1;
+    float *vel;
 };
 
 enum Storage { kFP32 = 0, kFP16 = 1, kBF16 = 2 };

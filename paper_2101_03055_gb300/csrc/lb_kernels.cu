@@ -15,6 +15,8 @@
 // addresses, and the overlap between neighbouring warps is served from L1/L2.
 #include "lb_device.cuh"
 
+#include <type_traits>
+
 namespace cdflb {
 namespace {
 using namespace dev;
@@ -39,6 +41,85 @@ __global__ void __launch_bounds__(256) step_kernel_flat(const LbParams p, const 
     if (idx >= p.nx * p.ny) return;
     const int y = idx / p.nx, x = idx - y * p.nx;
     step_node<M, T>(p, x, y, in, out, sprev, moments);
+}
+
+// ---- Case 1 of Sec. 2.1: convection cross-diffusion in a prescribed velocity -----
+// Scalars only: pull the 5m scalar populations, read the node's prescribed
+// velocity and phi(t - 1) (p.vel), collide with the Case-1 auxiliary source,
+// store the scalars and phi(t) in place of phi(t - 1) (each node reads and
+// writes only its own entry).  Algorithmic bytes: 2 x 5m x 4 + 8 + 2 x 4m.
+template <int M>
+__global__ void __launch_bounds__(256) step_kernel_case1(const LbParams p, const float *__restrict__ in,
+                                                         float *__restrict__ out, float *__restrict__ sprev,
+                                                         float *__restrict__ moments) {
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int y = blockIdx.y * blockDim.y + threadIdx.y;
+    if (x >= p.nx || y >= p.ny) return;
+    const long long P = p.plane;
+    const int pitch = p.pitch;
+    const auto mk = [pitch](int sx, int sy) { return sy * pitch + sx; };
+    const auto ld = [in, P](int plane, int off) { return __ldg(in + plane * P + off); };
+    const int o0 = y * pitch + x;
+    float f[M][5];
+    pull_scalars<M, false>(p, x, y, mk, ld, f);
+    float *vel = p.vel;
+    const float ux = __ldg(vel + o0), uy = __ldg(vel + P + o0);
+    float php[M];
+#pragma unroll
+    for (int a = 0; a < M; ++a) php[a] = vel[(2 + a) * P + o0];
+    const bool consume = (M >= 2 && p.skind == 2);
+    const float sp1 = consume ? sprev[o0] : 0.f;
+    NodeOut<M> o;
+    collide_case1<M>(p, f, ux, uy, php, sp1, false, o);
+#pragma unroll
+    for (int a = 0; a < M; ++a)
+#pragma unroll
+        for (int i = 0; i < 5; ++i) out[(9 + 5 * a + i) * P + o0] = f[a][i];
+#pragma unroll
+    for (int a = 0; a < M; ++a) vel[(2 + a) * P + o0] = php[a];
+    if (consume) sprev[o0] = o.s1;
+    if (moments) write_moments<M>(moments, P, o0, o);
+}
+
+// Case 1 initialisation: f = f^eq(phi0, u) collided once with phi(t - 1) = phi0
+// (so G = 0) and S(t - 1) = S(phi0); u becomes the prescribed velocity.
+template <int M>
+__global__ void init_kernel_case1(const LbParams p, const float *__restrict__ fields, int fpitch,
+                                  float *__restrict__ out, float *__restrict__ sprev, float *__restrict__ moments) {
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int y = blockIdx.y * blockDim.y + threadIdx.y;
+    if (x >= p.nx || y >= p.ny) return;
+    const long long P = p.plane, FP = (long long)fpitch * p.ny;
+    const long long o0 = (long long)y * p.pitch + x, i0 = (long long)y * fpitch + x;
+    float phi[M], phid[M];
+#pragma unroll
+    for (int a = 0; a < M; ++a) {
+        phi[a] = fields[a * FP + i0];
+        phid[a] = phi[a] - p.phi_ref[a];
+    }
+    const float ux = fields[M * FP + i0], uy = fields[(M + 1) * FP + i0];
+    float f[M][5];
+    scalar_equilibrium<M>(phid, phi, ux, uy, f);
+    float php[M];
+    NodeOut<M> o;
+    {
+        // phi(t - 1) = phi0 as the scalar moments see it (sum of the populations)
+        ScalarState<M> s;
+        scalar_closures<M>(p, f, 0.f, true, s);
+#pragma unroll
+        for (int a = 0; a < M; ++a) php[a] = s.phi[a];
+    }
+    collide_case1<M>(p, f, ux, uy, php, 0.f, true, o);
+#pragma unroll
+    for (int a = 0; a < M; ++a)
+#pragma unroll
+        for (int i = 0; i < 5; ++i) out[(9 + 5 * a + i) * P + o0] = f[a][i];
+    p.vel[o0] = ux;
+    p.vel[P + o0] = uy;
+#pragma unroll
+    for (int a = 0; a < M; ++a) p.vel[(2 + a) * P + o0] = php[a];
+    if (M >= 2 && p.skind == 2) sprev[o0] = o.s1;
+    write_moments<M>(moments, P, o0, o);
 }
 
 // ---- initialisation from moments (collide-only pass at t = 0) ------------------
@@ -317,6 +398,21 @@ cudaError_t step_dispatch(const LbParams &p, const void *in, void *out, float *s
                           dim3 block, cudaStream_t s) {
     const T *i = static_cast<const T *>(in);
     T *o = static_cast<T *>(out);
+    if (p.case1) {  // FP32 only (the host refuses other storage), 2-D blocks
+        if constexpr (std::is_same<T, float>::value) {
+            const dim3 b2(block.x, block.y ? block.y : 1);
+            dim3 grid((p.nx + b2.x - 1) / b2.x, (p.ny + b2.y - 1) / b2.y);
+            switch (p.m) {
+                case 1: step_kernel_case1<1><<<grid, b2, 0, s>>>(p, i, o, sprev, mom); break;
+                case 2: step_kernel_case1<2><<<grid, b2, 0, s>>>(p, i, o, sprev, mom); break;
+                case 3: step_kernel_case1<3><<<grid, b2, 0, s>>>(p, i, o, sprev, mom); break;
+                case 4: step_kernel_case1<4><<<grid, b2, 0, s>>>(p, i, o, sprev, mom); break;
+                default: return cudaErrorInvalidValue;
+            }
+            return cudaGetLastError();
+        }
+        return cudaErrorInvalidValue;
+    }
     if (block.y == 0) {  // flat launch
         const long long n = (long long)p.nx * p.ny;
         dim3 fb(block.x), grid((unsigned)((n + block.x - 1) / block.x));
@@ -345,6 +441,19 @@ cudaError_t init_dispatch(const LbParams &p, const float *fields, int fpitch, vo
                           float *mom, cudaStream_t s) {
     dim3 block(128, 2), grid((p.nx + 127) / 128, (p.ny + 1) / 2);
     T *o = static_cast<T *>(out);
+    if (p.case1) {
+        if constexpr (std::is_same<T, float>::value) {
+            switch (p.m) {
+                case 1: init_kernel_case1<1><<<grid, block, 0, s>>>(p, fields, fpitch, o, sprev, mom); break;
+                case 2: init_kernel_case1<2><<<grid, block, 0, s>>>(p, fields, fpitch, o, sprev, mom); break;
+                case 3: init_kernel_case1<3><<<grid, block, 0, s>>>(p, fields, fpitch, o, sprev, mom); break;
+                case 4: init_kernel_case1<4><<<grid, block, 0, s>>>(p, fields, fpitch, o, sprev, mom); break;
+                default: return cudaErrorInvalidValue;
+            }
+            return cudaGetLastError();
+        }
+        return cudaErrorInvalidValue;
+    }
     switch (p.m) {
         case 1: init_kernel<1, T><<<grid, block, 0, s>>>(p, fields, fpitch, o, sprev, mom); break;
         case 2: init_kernel<2, T><<<grid, block, 0, s>>>(p, fields, fpitch, o, sprev, mom); break;
