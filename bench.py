@@ -57,6 +57,8 @@ def workload(name: str, rank: int):
         return I.periodic_box(2048, 2048, seed=rank)
     if name == "periodic3d_256":
         return I.periodic_box3d(256, seed=rank)
+    if name == "periodic3d_128":
+        return I.periodic_box3d(128, seed=rank)
     if name == "ddc_cavity3d_128":
         return I.ddc_cavity3d(128)
     if name == "cde_cellular_4096":
@@ -77,6 +79,7 @@ def describe(name: str) -> str:
         "periodic_2048": "periodic 2048x2048 cross-diffusion box (profiling grid above L2)",
         "periodic3d_256": "3-D periodic 256^3 cross-diffusion box, m=2, D3Q7 scalars + D3Q19 fluid "
                           "(Taylor-Green initial velocity)",
+        "periodic3d_128": "3-D periodic 128^3 cross-diffusion box (profiling size, 0.55 GB state > L2)",
         "ddc_cavity3d_128": "3-D double-diffusive cube 128^3 (hot/cold x walls, Ra=1e4, Pr=0.7, Le=2, N=1), "
                             "D3Q7 + D3Q19",
         "cde_cellular_4096": "Case 1 of Sec. 2.1: convection cross-diffusion (m=2) in a prescribed steady cellular "

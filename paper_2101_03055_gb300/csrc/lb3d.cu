@@ -248,6 +248,10 @@ template <int M>
 __global__ void __launch_bounds__(256) step3d_kernel(const Lb3Params p, const float *__restrict__ in,
                                                      float *__restrict__ out, float *__restrict__ sprev,
                                                      float *__restrict__ moments) {
+    // programmatic dependent launch: wait for the previous step's results, then
+    // let the next step's CTAs be scheduled (hides the launch gap)
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     const int y = blockIdx.y * blockDim.y + threadIdx.y;
     const int z = blockIdx.z;
@@ -422,10 +426,29 @@ __global__ void pack3d_kernel(const Lb3Params p, int nf, const float *__restrict
 
 dim3 grid_of(const Lb3Params &p, dim3 b) { return dim3((p.nx + b.x - 1) / b.x, (p.ny + b.y - 1) / b.y, p.nz); }
 
+template <int M>
+cudaError_t launch_step3_m(const Lb3Params &p, const float *in, float *out, float *sprev, float *mom, dim3 b,
+                           cudaStream_t s) {
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = grid_of(p, b);
+    cfg.blockDim = b;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, step3d_kernel<M>, p, in, out, sprev, mom);
+}
+
 cudaError_t launch_step3(const Lb3Params &p, const float *in, float *out, float *sprev, float *mom, dim3 b,
                          cudaStream_t s) {
-    DISPATCH_M(step3d_kernel, grid_of(p, b), b, s, p, in, out, sprev, mom)
-    return cudaGetLastError();
+    switch (p.m) {
+        case 1: return launch_step3_m<1>(p, in, out, sprev, mom, b, s);
+        case 2: return launch_step3_m<2>(p, in, out, sprev, mom, b, s);
+        case 3: return launch_step3_m<3>(p, in, out, sprev, mom, b, s);
+        default: return cudaErrorInvalidValue;
+    }
 }
 cudaError_t launch_init3(const Lb3Params &p, const float *fields, float *out, float *sprev, float *mom,
                          cudaStream_t s) {

@@ -44,6 +44,17 @@ __device__ __forceinline__ unsigned long long global_ns() {
     return t;
 }
 
+// Programmatic dependent launch: a step kernel launched with the programmatic
+// stream-serialisation attribute may start while the previous step is still
+// running; griddepcontrol.wait holds it until that grid has completed and its
+// memory is visible (a no-op without the attribute), and
+// griddepcontrol.launch_dependents lets the next step's CTAs be scheduled
+// early, which hides the launch gap between the short steps of a small lattice.
+__device__ __forceinline__ void pdl_wait_and_release() {
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
 // ---- storage types ---------------------------------------------------------------
 // Populations are stored as deviations from a reference state (below) in FP32,
 // FP16 or BF16; every collision is computed in FP32.

@@ -21,11 +21,30 @@ namespace cdflb {
 namespace {
 using namespace dev;
 
+// Launch a step kernel with programmatic stream serialisation (see
+// pdl_wait_and_release): it may begin while the previous kernel of the stream
+// finishes, and waits inside for that kernel's results.
+template <typename... KArgs, typename... Args>
+cudaError_t launch_pdl(void (*kern)(KArgs...), dim3 grid, dim3 block, cudaStream_t s, Args... args) {
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kern, args...);
+}
+
 // ---- the fused step ------------------------------------------------------------
 template <int M, typename T>
 __global__ void __launch_bounds__(256) step_kernel(const LbParams p, const T *__restrict__ in,
                                                    T *__restrict__ out, float *__restrict__ sprev,
                                                    float *__restrict__ moments) {
+    pdl_wait_and_release();
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     const int y = blockIdx.y * blockDim.y + threadIdx.y;
     if (x >= p.nx || y >= p.ny) return;
@@ -37,6 +56,7 @@ template <int M, typename T>
 __global__ void __launch_bounds__(256) step_kernel_flat(const LbParams p, const T *__restrict__ in,
                                                         T *__restrict__ out, float *__restrict__ sprev,
                                                         float *__restrict__ moments) {
+    pdl_wait_and_release();
     const int idx = blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= p.nx * p.ny) return;
     const int y = idx / p.nx, x = idx - y * p.nx;
@@ -52,6 +72,7 @@ template <int M>
 __global__ void __launch_bounds__(256) step_kernel_case1(const LbParams p, const float *__restrict__ in,
                                                          float *__restrict__ out, float *__restrict__ sprev,
                                                          float *__restrict__ moments) {
+    pdl_wait_and_release();
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     const int y = blockIdx.y * blockDim.y + threadIdx.y;
     if (x >= p.nx || y >= p.ny) return;
@@ -223,6 +244,7 @@ template <int M, typename T>
 __global__ void __launch_bounds__(256, (M <= 2 ? 3 : 1)) step_kernel_mr(const LbParams p, const T *__restrict__ in,
                                                       const float *__restrict__ min, T *__restrict__ out,
                                                       float *__restrict__ mout, float *__restrict__ sprev) {
+    pdl_wait_and_release();
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     const int y = blockIdx.y * blockDim.y + threadIdx.y;
     if (x >= p.nx || y >= p.ny) return;
@@ -354,14 +376,15 @@ cudaError_t step_mr_dispatch(const LbParams &p, const void *in, const float *min
     dim3 grid((p.nx + block.x - 1) / block.x, (p.ny + block.y - 1) / block.y);
     const T *i = static_cast<const T *>(in);
     T *o = static_cast<T *>(out);
+    cudaError_t e = cudaSuccess;
     switch (p.m) {
-        case 1: step_kernel_mr<1, T><<<grid, block, 0, s>>>(p, i, min, o, mout, sprev); break;
-        case 2: step_kernel_mr<2, T><<<grid, block, 0, s>>>(p, i, min, o, mout, sprev); break;
-        case 3: step_kernel_mr<3, T><<<grid, block, 0, s>>>(p, i, min, o, mout, sprev); break;
-        case 4: step_kernel_mr<4, T><<<grid, block, 0, s>>>(p, i, min, o, mout, sprev); break;
+        case 1: e = launch_pdl(step_kernel_mr<1, T>, grid, block, s, p, i, min, o, mout, sprev); break;
+        case 2: e = launch_pdl(step_kernel_mr<2, T>, grid, block, s, p, i, min, o, mout, sprev); break;
+        case 3: e = launch_pdl(step_kernel_mr<3, T>, grid, block, s, p, i, min, o, mout, sprev); break;
+        case 4: e = launch_pdl(step_kernel_mr<4, T>, grid, block, s, p, i, min, o, mout, sprev); break;
         default: return cudaErrorInvalidValue;
     }
-    return cudaGetLastError();
+    return e != cudaSuccess ? e : cudaGetLastError();
 }
 
 template <typename T>
@@ -402,38 +425,41 @@ cudaError_t step_dispatch(const LbParams &p, const void *in, void *out, float *s
         if constexpr (std::is_same<T, float>::value) {
             const dim3 b2(block.x, block.y ? block.y : 1);
             dim3 grid((p.nx + b2.x - 1) / b2.x, (p.ny + b2.y - 1) / b2.y);
+            cudaError_t e = cudaSuccess;
             switch (p.m) {
-                case 1: step_kernel_case1<1><<<grid, b2, 0, s>>>(p, i, o, sprev, mom); break;
-                case 2: step_kernel_case1<2><<<grid, b2, 0, s>>>(p, i, o, sprev, mom); break;
-                case 3: step_kernel_case1<3><<<grid, b2, 0, s>>>(p, i, o, sprev, mom); break;
-                case 4: step_kernel_case1<4><<<grid, b2, 0, s>>>(p, i, o, sprev, mom); break;
+                case 1: e = launch_pdl(step_kernel_case1<1>, grid, b2, s, p, i, o, sprev, mom); break;
+                case 2: e = launch_pdl(step_kernel_case1<2>, grid, b2, s, p, i, o, sprev, mom); break;
+                case 3: e = launch_pdl(step_kernel_case1<3>, grid, b2, s, p, i, o, sprev, mom); break;
+                case 4: e = launch_pdl(step_kernel_case1<4>, grid, b2, s, p, i, o, sprev, mom); break;
                 default: return cudaErrorInvalidValue;
             }
-            return cudaGetLastError();
+            return e != cudaSuccess ? e : cudaGetLastError();
         }
         return cudaErrorInvalidValue;
     }
     if (block.y == 0) {  // flat launch
         const long long n = (long long)p.nx * p.ny;
         dim3 fb(block.x), grid((unsigned)((n + block.x - 1) / block.x));
+        cudaError_t e = cudaSuccess;
         switch (p.m) {
-            case 1: step_kernel_flat<1, T><<<grid, fb, 0, s>>>(p, i, o, sprev, mom); break;
-            case 2: step_kernel_flat<2, T><<<grid, fb, 0, s>>>(p, i, o, sprev, mom); break;
-            case 3: step_kernel_flat<3, T><<<grid, fb, 0, s>>>(p, i, o, sprev, mom); break;
-            case 4: step_kernel_flat<4, T><<<grid, fb, 0, s>>>(p, i, o, sprev, mom); break;
+            case 1: e = launch_pdl(step_kernel_flat<1, T>, grid, fb, s, p, i, o, sprev, mom); break;
+            case 2: e = launch_pdl(step_kernel_flat<2, T>, grid, fb, s, p, i, o, sprev, mom); break;
+            case 3: e = launch_pdl(step_kernel_flat<3, T>, grid, fb, s, p, i, o, sprev, mom); break;
+            case 4: e = launch_pdl(step_kernel_flat<4, T>, grid, fb, s, p, i, o, sprev, mom); break;
             default: return cudaErrorInvalidValue;
         }
-        return cudaGetLastError();
+        return e != cudaSuccess ? e : cudaGetLastError();
     }
     dim3 grid((p.nx + block.x - 1) / block.x, (p.ny + block.y - 1) / block.y);
+    cudaError_t e = cudaSuccess;
     switch (p.m) {
-        case 1: step_kernel<1, T><<<grid, block, 0, s>>>(p, i, o, sprev, mom); break;
-        case 2: step_kernel<2, T><<<grid, block, 0, s>>>(p, i, o, sprev, mom); break;
-        case 3: step_kernel<3, T><<<grid, block, 0, s>>>(p, i, o, sprev, mom); break;
-        case 4: step_kernel<4, T><<<grid, block, 0, s>>>(p, i, o, sprev, mom); break;
+        case 1: e = launch_pdl(step_kernel<1, T>, grid, block, s, p, i, o, sprev, mom); break;
+        case 2: e = launch_pdl(step_kernel<2, T>, grid, block, s, p, i, o, sprev, mom); break;
+        case 3: e = launch_pdl(step_kernel<3, T>, grid, block, s, p, i, o, sprev, mom); break;
+        case 4: e = launch_pdl(step_kernel<4, T>, grid, block, s, p, i, o, sprev, mom); break;
         default: return cudaErrorInvalidValue;
     }
-    return cudaGetLastError();
+    return e != cudaSuccess ? e : cudaGetLastError();
 }
 
 template <typename T>

@@ -1,0 +1,72 @@
+"""What the surrogate gains, and how close the FP32 steady state it is judged
+against sits to the FP64 one.
+
+1. The double-diffusive cavity (Sec. 3.2 setup, 32^2) run to its steady state on
+   the GPU (FP32 populations) and in the FP64 oracle, both from rest: the two
+   steady states agree to relative L2 <= 1e-4 in T, C, u_x and u_y, so "within
+   1e-4 of the long-run FP32 state" is within ~1e-4 of the FP64 steady state.
+2. A U-Net trained by this package's BF16 kernels on solver-generated steady
+   states of 32^2 cavities starts held-out cases closer to their steady states
+   and reaches relative L2 1e-4 in fewer lattice steps than a start from rest.
+"""
+import numpy as np
+import pytest
+
+from paper_2101_03055_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+
+def rel_fields(M, Mref):
+    return [float(np.linalg.norm(M[q] - Mref[q]) / np.linalg.norm(Mref[q])) for q in range(4)]
+
+
+def test_fp32_steady_state_matches_fp64_oracle(cdf, oracle_mod):
+    pb = I.ddc_cavity(32, Ra=2e4, Pr=0.7, Le=2.0, Nc=0.5, Df=0.1, Sr=0.1)
+    s = cdf.Solver(pb)
+    ok, steps, R = s.run_to_steady(2e-7, 2000, 1_000_000)
+    assert ok or R < 2e-6, R
+    M32 = s.moments()
+    o = oracle_mod.OracleSim(pb)
+    prev = o.moments()
+    K = 5000
+    for _ in range(200):
+        o.step(K)
+        cur = o.moments()
+        Ro = max(np.abs(cur[q] - prev[q]).sum() / np.abs(cur[q]).sum() for q in range(4))
+        prev = cur
+        if Ro < 1e-7:  # contraction ~0.53 per 5000 steps: the state is within ~2e-7 of steady
+            break
+    assert Ro < 1e-7, Ro
+    err = rel_fields(M32, cur)
+    print(f"FP32 steady (R={R:.1e}, {steps} steps) vs FP64 steady ({o.t} steps): rel L2 T, C, ux, uy = {err}")
+    assert max(err) < 1e-4
+
+
+def test_warm_start_reaches_steady_state_in_fewer_steps(cdf):
+    import torch
+    from paper_2101_03055_gb300 import surrogate as S
+    n = 32
+    rng = dict(log10_Ra=(4.0, 5.0), Nc=(0.5, 2.0), Le=(1.0, 4.0), SrDf=(0.0, 0.2))
+    prms = S.draw_parameters(96, 10, **rng)
+    Ms, R, steady = S.generate_steady_states(prms, n, steps=400_000, check_every=5000, steady_tol=1e-5)
+    keep = np.flatnonzero(steady)
+    assert len(keep) >= 80, int(len(keep))
+    x = torch.as_tensor(S.input_planes(n, [prms[k] for k in keep])).cuda().to(torch.bfloat16)
+    y = torch.as_tensor(np.stack([S.targets_from_moments(Ms[k]) for k in keep])).cuda()
+    net = S.UNet(seed=0)
+    hist = S.train(net, x, y, epochs=60, batch=16, lr=2e-3)
+    assert hist[-1] < 0.05 * hist[0]
+    eprm = S.draw_parameters(16, 11, **rng)
+    res = S.warm_start_comparison(net, eprm, n, eps_list=(1e-3, 1e-4), ref_steps=1_600_000, check_every=4000,
+                                  steady_tol=2e-6)
+    st = res["steady"]
+    c, w = res["cold"]["first"][1e-4], res["warm"]["first"][1e-4]
+    both = st & (c > 0) & (w > 0)
+    assert both.sum() >= 12, (st, c, w)
+    ratio = w[both] / c[both]
+    print(f"warm/cold steps to rel L2 1e-4: median {np.median(ratio):.3f}, warm faster in "
+          f"{(ratio < 1).mean():.0%} of {both.sum()}; prediction rel L2 median "
+          f"{np.median(res['prediction_error'][st]):.3e}")
+    assert np.median(ratio) < 0.8
+    assert (ratio < 1).mean() >= 0.75
