@@ -25,7 +25,10 @@ def rel(a, b):
     return float(np.linalg.norm(a - b) / (nb if nb > 0 else 1.0))
 
 
-def compare(cdf, o3, pb, steps, block=None, tol=TOL32):
+def compare(cdf, o3, pb, steps, block=None, tol=TOL32, u_floor=0.0):
+    """u_floor: a velocity scale below which the relative error of u is not
+    meaningful (a flow that has decayed by orders of magnitude keeps the
+    rounding of its initial size); its error is taken against max(||u||, u_floor)."""
     s = cdf.Solver3D(pb, block=block)
     o = o3.Sim(pb)
     s.step(steps)
@@ -33,7 +36,8 @@ def compare(cdf, o3, pb, steps, block=None, tol=TOL32):
     Mg, Mo = s.moments(), o.moments()
     m = pb.m
     errs = {f"phi{a}": rel(Mg[a], Mo[a]) for a in range(m)}
-    errs["u"] = rel(Mg[m:m + 3], Mo[m:m + 3])
+    uscale = max(np.linalg.norm(Mo[m:m + 3]), u_floor)
+    errs["u"] = float(np.linalg.norm(Mg[m:m + 3] - Mo[m:m + 3]) / (uscale if uscale > 0 else 1.0))
     pscale = max(np.linalg.norm(Mo[m + 3]), np.linalg.norm(Mo[m:m + 3]) / 3.0)
     errs["p"] = float(np.linalg.norm(Mg[m + 3] - Mo[m + 3]) / (pscale if pscale > 0 else 1.0))
     bad = {k: v for k, v in errs.items() if not v <= tol}
@@ -90,8 +94,10 @@ def test_degenerate_and_ragged_sizes(cdf, o3, dims):
             sides += [I.periodic_side(2), I.periodic_side(2)]
         else:
             sides += [I.wall_side(2, I.NOSLIP, [I.DIRICHLET, I.NOFLUX], [1.1, 0.0]), I.wall_side(2)]
+    # in a box a few nodes wide the wall friction damps the initial flow by ~100x
+    # within the window: u is compared against 5 % of its initial size
     compare(cdf, o3, pb.replace(sides=sides, g=(1e-5, -2e-5, 3e-5), beta=np.array([1.0, -0.5]),
-                                phi_ref=np.array([1.0, 1.0])), 40)
+                                phi_ref=np.array([1.0, 1.0])), 40, u_floor=0.05 * np.linalg.norm(pb.u0))
 
 
 @pytest.mark.parametrize("m", [1, 3])
