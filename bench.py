@@ -63,6 +63,8 @@ def workload(name: str, rank: int):
         return I.ddc_cavity3d(128)
     if name == "cde_cellular_4096":
         return I.cde_cellular(4096, 4096, seed=rank)
+    if name == "cde_cellular_2048":
+        return I.cde_cellular(2048, 2048, seed=rank)
     if name == "batched_plume_sweep_256":
         return I.chemotaxis_plume_sweep(256, seed=rank)
     if name == "batched_plume_sweep_64":
@@ -84,6 +86,7 @@ def describe(name: str) -> str:
                             "D3Q7 + D3Q19",
         "cde_cellular_4096": "Case 1 of Sec. 2.1: convection cross-diffusion (m=2) in a prescribed steady cellular "
                              "flow, 4096x4096, Dirichlet west/east walls, no fluid populations",
+        "cde_cellular_2048": "Case 1 cellular flow at 2048x2048 (profiling size above L2)",
         "batched_plume_sweep_64": "64 chemotaxis-plume instances of the 256-instance sweep (profiling size)",
         "batched_plume_sweep_256": "256 chemotaxis-plume instances, W~U{128..512} x H~U{64..256} (13.2 M nodes), "
                                    "per-instance chi, D_c, gravity; one persistent launch per 32 steps",
@@ -99,24 +102,30 @@ def measured_peaks():
     return 6800.0, "fallback"
 
 
-def kernel_source_hash() -> str:
+KERNEL_SOURCES_2D = ("lb_kernels.cu", "lb_device.cuh", "lb_internal.h", "lb_resident.cu")
+KERNEL_SOURCES_3D = ("lb3d.cu",)
+
+
+def kernel_source_hash(files=KERNEL_SOURCES_2D) -> str:
     h = hashlib.sha256()
-    for f in ("lb_kernels.cu", "lb_device.cuh", "lb_internal.h", "lb_resident.cu"):
+    for f in files:
         with open(os.path.join(ROOT, "paper_2101_03055_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
 
 
-def recorded_traffic(workload_name: str):
-    """DRAM bytes per step-kernel launch from the committed ncu summary, if it was
-    taken on the current kernel source for this workload."""
+def recorded_traffic(workload_name: str, kernel: str):
+    """DRAM bytes per launch of the dominant kernel from the committed ncu summary
+    (profiles/step_kernel_traffic.json), if it was taken on the current kernel
+    source for this workload and kernel; else None."""
     path = os.path.join(ROOT, "profiles", "step_kernel_traffic.json")
     if not os.path.exists(path):
         return None
     with open(path) as fh:
         d = json.load(fh)
     e = d.get(workload_name)
-    if not e or e.get("kernel_hash") != kernel_source_hash():
+    files = KERNEL_SOURCES_3D if "3d" in workload_name else KERNEL_SOURCES_2D
+    if not e or e.get("kernel_hash") != kernel_source_hash(files) or not kernel.startswith(e.get("kernel", "?")):
         return None
     return float(e["dram_bytes_per_launch"])
 
@@ -169,9 +178,9 @@ class ClockSampler:
 class _Single:
     """Uniform view of the single-lattice solver for the timing loops."""
 
-    def __init__(self, lib, pb, storage):
+    def __init__(self, lib, pb, storage, resident=0):
         self.lib, self.pb = lib, pb
-        self.s = lib.Solver(pb, storage=storage)
+        self.s = lib.Solver(pb, storage=storage, resident=resident)
         info = self.s.info()
         self.nodes, self.bytes_per_lup, self.storage = pb.nodes, info.bytes_per_lup, info.storage
         self.block = [info.block_x, info.block_y]
@@ -393,6 +402,8 @@ def main():
     ap.add_argument("--workload", default="chemotaxis_plume_512x256")
     ap.add_argument("--lb-steps", type=int, default=2000, help="lattice time steps per benchmark step")
     ap.add_argument("--storage", default="fp32", choices=["fp32", "fp16", "bf16"])
+    ap.add_argument("--resident", type=int, default=0, choices=[-1, 0, 1],
+                    help="tile-resident step: 0 = the autotuner decides, 1 = always, -1 = never")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=3)
     args = ap.parse_args()
@@ -418,7 +429,7 @@ def main():
     elif isinstance(wl, I.Problem3D):
         runner = _Single3D(lib, wl, args.storage)
     else:
-        runner = _Single(lib, wl, args.storage)
+        runner = _Single(lib, wl, args.storage, args.resident)
     nodes = runner.nodes
     K, W, S = args.steps, args.warmup, args.lb_steps
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=device)
@@ -465,7 +476,7 @@ def main():
     bytes_per_launch = runner.bytes_per_lup * nodes * spl
     launch_s = t_ms * 1e-3 / (S * K) * spl
     achieved = bytes_per_launch / launch_s / 1e9
-    traffic = recorded_traffic(args.workload)
+    traffic = recorded_traffic(args.workload, runner.kernel)
 
     if rank != 0:
         if world > 1:
