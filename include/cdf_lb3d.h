@@ -66,7 +66,8 @@ cdf_status cdf_lb3d_create(const cdf_grid3 *grid, int m, const cdf_diffusion *di
 cdf_status cdf_lb3d_init_moments(cdf_lb3d *h, const double *phi, const double *u, const double *p);
 /* Advance n >= 0 steps (one fused kernel per step, CUDA-graph launched). */
 cdf_status cdf_lb3d_step(cdf_lb3d *h, long long n);
-/* Stop test of cdf_lb_run_to_steady over phi_0..phi_{m-1}, u_x, u_y, u_z. */
+/* Stop test of cdf_lb_run_to_steady over phi_0..phi_{m-1} and the velocity taken
+ * as one field: R_u = sum(|du_x| + |du_y| + |du_z|) / sum(|u_x| + |u_y| + |u_z|). */
 cdf_status cdf_lb3d_run_to_steady(cdf_lb3d *h, double tol, long long check_every, long long max_steps,
                                   long long *steps_taken, double *residual);
 /* Moments at the current time into a host FP64 stack [m+4][nz][ny][nx]:

@@ -861,8 +861,17 @@ cdf_status cdf_lb3d_run_to_steady(cdf_lb3d *h, double tol, long long check_every
         taken += k;
         if ((st = reduce3(h, h->mom, h->mom_prev, q)) != CDF_OK) return st;
         if (q[3 * m1 + 4] > 0) { result = CDF_EUNSTABLE; break; }
+        // scalars one by one, the velocity as one vector field (a component that
+        // stays at round-off level, e.g. u_z of a z-independent flow, has no
+        // meaningful relative change of its own)
         R = 0.0;
-        for (int f = 0; f < m1 + 2; ++f) R = std::max(R, q[m1 + f] / std::max(q[2 * m1 + 2 + f], 1e-300));
+        for (int f = 0; f < h->m; ++f) R = std::max(R, q[m1 + f] / std::max(q[2 * m1 + 2 + f], 1e-300));
+        double du = 0.0, su = 0.0;
+        for (int f = h->m; f < m1 + 2; ++f) {
+            du += q[m1 + f];
+            su += q[2 * m1 + 2 + f];
+        }
+        R = std::max(R, du / std::max(su, 1e-300));
         if (k == check_every && R < tol) { result = CDF_OK; break; }
     }
     if (steps_taken) *steps_taken = taken;

@@ -380,16 +380,23 @@ def periodic_box3d(nx: int, ny: int = None, nz: int = None, seed: int = 0, m: in
 
 
 def ddc_cavity3d(n: int, Ra: float = 1e4, Pr: float = 0.7, Le: float = 2.0, Nc: float = 1.0, Df: float = 0.1,
-                 Sr: float = 0.1, seed: int = 0) -> Problem3D:
-    """Cubic double-diffusive cavity (the Sec. 3.2 setup in 3-D): T = C = 1 on the
-    x- wall, 0 on the x+ wall, the other walls adiabatic, gravity along +z in the
-    dimensionless form F = g (T + Nc C) z_hat; the lattice mapping of the 2-D
-    cavity; from rest with T = C = 0."""
+                 Sr: float = 0.1, seed: int = 0, ny: Optional[int] = None, nz: Optional[int] = None,
+                 gravity_axis: int = 2, periodic_z: bool = False) -> Problem3D:
+    """Double-diffusive cavity (the Sec. 3.2 setup in 3-D): T = C = 1 on the x- wall,
+    0 on the x+ wall, the other walls adiabatic, gravity along +z (gravity_axis = 2)
+    or +y (1) in the dimensionless form F = g (T + Nc C) e_g; the lattice mapping of
+    the 2-D cavity with n nodes across; from rest with T = C = 0.  periodic_z makes a
+    slab whose z-independent solution is the 2-D cavity's."""
     m = 2
+    ny = n if ny is None else ny
+    nz = n if nz is None else nz
     alpha, nu, g = ddc_lattice_parameters(n, Ra, Pr)
     D = alpha * np.array([[1.0, Df], [Sr / Le, 1.0 / Le]])
     hot = wall_side(m, NOSLIP, [DIRICHLET, DIRICHLET], [1.0, 1.0])
     cold = wall_side(m, NOSLIP, [DIRICHLET, DIRICHLET], [0.0, 0.0])
-    sides = [hot, cold] + [wall_side(m) for _ in range(4)]
-    return Problem3D("ddc_cavity3d", n, n, n, m, D, nu, g=(0.0, 0.0, 1.0), beta=np.array([g, g * Nc]),
-                     sides=sides, phi0=np.zeros((m, n, n, n)))
+    zs = [periodic_side(m), periodic_side(m)] if periodic_z else [wall_side(m), wall_side(m)]
+    sides = [hot, cold, wall_side(m), wall_side(m)] + zs
+    gv = [0.0, 0.0, 0.0]
+    gv[gravity_axis] = 1.0
+    return Problem3D("ddc_cavity3d", n, ny, nz, m, D, nu, g=tuple(gv), beta=np.array([g, g * Nc]),
+                     sides=sides, phi0=np.zeros((m, nz, ny, n)))
