@@ -364,7 +364,7 @@ cdf_status time_steps(cdf_lb *h, long long steps, float *ms) {
 // measures faster than the graph-launched kernel with the autotuned block.
 cdf_status setup_resident(cdf_lb *h, const cdf_options *opt) {
     if (h->storage != CDF_FP32 || opt->resident == -1 || h->P.case1) return CDF_OK;
-    if (!plan_resident(h->nx, h->ny, h->m, h->P.periodic_x, h->P.periodic_y, &h->rg)) {
+    if (!plan_resident(h->nx, h->ny, h->m, &h->rg)) {
         cudaGetLastError();
         if (opt->resident == 1) return fail(CDF_EINVAL, "the lattice does not fit the resident step");
         return CDF_OK;

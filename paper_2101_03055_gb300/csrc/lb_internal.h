@@ -86,7 +86,7 @@ struct ResidentGeom {
 // Finds a tiling of the nx x ny lattice with m scalars that fits one CTA per
 // SM of the current device; false if the lattice is too large (or the device
 // lacks the shared memory).
-bool plan_resident(int nx, int ny, int m, int periodic_x, int periodic_y, ResidentGeom *out);
+bool plan_resident(int nx, int ny, int m, ResidentGeom *out);
 // nsteps steps from buffer parity0 (buf0 or buf1) in one cooperative launch;
 // `counters` holds one step counter per tile (all equal between launches;
 // zero them together), *err is set when a wait ran out.

@@ -232,9 +232,7 @@ const void *resident_kernel_for(int m) {
 
 }  // namespace
 
-bool plan_resident(int nx, int ny, int m, int periodic_x, int periodic_y, ResidentGeom *out) {
-    (void)periodic_x;
-    (void)periodic_y;
+bool plan_resident(int nx, int ny, int m, ResidentGeom *out) {
     const void *kern = resident_kernel_for(m);
     if (!kern || nx < 1 || ny < 1) return false;
     int dev = 0, sms = 0, smem_optin = 0;
