@@ -63,6 +63,14 @@ cdf_nn_status cdf_nn_mse(const float *pred, const float *target, float *grad, fl
 cdf_nn_status cdf_nn_adam(float *w, const float *g, float *m, float *v, void *w_bf16, long long n, float lr, float b1,
                           float b2, float eps, long long step, void *stream);
 const char *cdf_nn_last_error(void);
+/* Tensor-core path of the two convolutions above: nonzero (the default) uses the
+ * 5th-generation tensor cores (tcgen05.mma, accumulators in tensor memory), zero
+ * the warp-level MMA kernels.  Process-wide; both give the same results up to the
+ * order of the FP32 accumulation. */
+cdf_nn_status cdf_nn_set_tensor_path(int tcgen05);
+/* *out = 1 if a bounded wait of a tcgen05 convolution ever ran out (its output is
+ * then undefined), else 0.  Synchronises with the device. */
+cdf_nn_status cdf_nn_error_flag(int *out);
 
 #ifdef __cplusplus
 }

@@ -129,6 +129,241 @@ __global__ void __launch_bounds__(kThreads) conv3x3_kernel(const __nv_bfloat16 *
 }
 
 // ---------------------------------------------------------------------------
+// The same two convolutions on the 5th-generation tensor cores (tcgen05): one CTA
+// of 128 threads owns 128 output pixels (one TMEM lane each) and BN output
+// channels (BN TMEM columns of FP32 accumulators).  K = 9 x channels runs in
+// stages of 64: all threads stage the im2col rows of A (128 x 64) and the
+// weights B (BN x 64) in shared memory in the K-major core-matrix layout (8 rows
+// x 16 bytes per 128-byte core matrix), one thread issues four
+// tcgen05.mma.kind::f16 (M = 128, N = BN, K = 16) and commits them to an
+// mbarrier; two stage buffers let the next stage load while the tensor core
+// works.  The epilogue reads the accumulators with tcgen05.ld (warp w owns
+// lanes 32w..32w+31), adds the bias, applies the ReLU and stores BF16.  Every
+// mbarrier wait is bounded; on time-out the kernel sets g_tc_error and still
+// frees its tensor memory.
+// ---------------------------------------------------------------------------
+constexpr int kTM = 128, kTK = 64, kTcThreads = 128;
+__device__ int g_tc_error = 0;
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+// Shared-memory matrix descriptor, K-major without swizzle: start address,
+// leading byte offset (between the two core matrices along K of one MMA) and
+// stride byte offset (between core matrices along M or N), all in 16-byte units;
+// bit 46 is the descriptor version of this architecture.
+__device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
+    return (uint64_t)((addr & 0x3FFFFu) >> 4) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
+           ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46);
+}
+
+// Instruction descriptor of tcgen05.mma.kind::f16: FP32 accumulator, BF16 A and B,
+// both K-major, N >> 3 at bit 17, M >> 4 at bit 24.
+__host__ __device__ constexpr uint32_t mma_idesc(int M, int N) {
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+// Byte offset of element (r, k) of a rows x 64 stage tile in the core-matrix layout.
+__device__ __forceinline__ uint32_t cm_offset(int r, int k, int rows) {
+    return (uint32_t)((((k >> 3) * (rows >> 3) + (r >> 3)) << 7) + ((r & 7) << 4) + ((k & 7) << 1));
+}
+
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
+    for (long long it = 0; it < (1ll << 26); ++it) {
+        uint32_t done;
+        asm volatile(
+            "{\n .reg .pred P;\n mbarrier.try_wait.parity.shared::cta.b64 P, [%1], %2;\n selp.u32 %0, 1, 0, P;\n}"
+            : "=r"(done)
+            : "r"(bar), "r"(parity)
+            : "memory");
+        if (done) return true;
+    }
+    atomicExch(&g_tc_error, 1);
+    return false;
+}
+
+template <bool kBwdData, int BN>
+__global__ void __launch_bounds__(kTcThreads) conv3x3_tc_kernel(const __nv_bfloat16 *__restrict__ in,
+                                                                const __nv_bfloat16 *__restrict__ w,
+                                                                const float *__restrict__ bias,
+                                                                __nv_bfloat16 *__restrict__ out, int N, int H, int Wd,
+                                                                int Cin_g, int Cout_g, int relu) {
+    constexpr int kCols = BN < 32 ? 32 : BN;               // TMEM columns (power of two >= 32)
+    constexpr uint32_t kABytes = kTM * kTK * 2, kBBytes = BN * kTK * 2;
+    extern __shared__ __align__(128) unsigned char tc_smem[];
+    unsigned char *A = tc_smem;                              // 2 x kABytes
+    unsigned char *B = tc_smem + 2 * kABytes;                // 2 x kBBytes
+    __shared__ __align__(8) uint64_t mbar[2];
+    __shared__ uint32_t tmem_slot;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const long long P = (long long)N * H * Wd;
+    const long long p0 = (long long)blockIdx.x * kTM;
+    const int n0 = blockIdx.y * BN;
+    const int Cin_w = kBwdData ? Cout_g : Cin_g;  // the weight tensor is Cout_w x 9 x Cin_w
+    const int K = 9 * Cin_g, nst = (K + kTK - 1) / kTK;
+
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_slot)),
+                     "r"(kCols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    if (tid == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&mbar[0])) : "memory");
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&mbar[1])) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = tmem_slot;
+
+    // the pixel of this thread's A row
+    const long long pa = p0 + tid;
+    int an = 0, ay = 0, ax = 0;
+    if (pa < P) {
+        an = (int)(pa / ((long long)H * Wd));
+        const int rem = (int)(pa - (long long)an * H * Wd);
+        ay = rem / Wd;
+        ax = rem - ay * Wd;
+    }
+    constexpr uint32_t idesc = mma_idesc(kTM, BN);
+    bool ok = true;
+    int last = -1;  // last stage whose MMAs were committed
+    for (int s = 0; s < nst && ok; ++s) {
+        const int buf = s & 1;
+        if (s >= 2) ok = mbar_wait(smem_u32(&mbar[buf]), (uint32_t)(((s - 2) >> 1) & 1));
+        if (!ok) break;
+        unsigned char *As = A + buf * kABytes, *Bs = B + buf * kBBytes;
+        const int k0 = s * kTK;
+        // A: row tid, eight 16-byte groups of 8 consecutive k (one tap, 8 channels each)
+#pragma unroll
+        for (int g = 0; g < kTK / 8; ++g) {
+            const int k = k0 + 8 * g;
+            uint4 v = make_uint4(0, 0, 0, 0);
+            if (pa < P && k < K) {
+                const int tap = k / Cin_g, c = k - tap * Cin_g;
+                const int sy = ay + tap / 3 - 1, sx = ax + tap % 3 - 1;
+                if (sy >= 0 && sy < H && sx >= 0 && sx < Wd)
+                    v = *reinterpret_cast<const uint4 *>(in + (((long long)an * H + sy) * Wd + sx) * Cin_g + c);
+            }
+            *reinterpret_cast<uint4 *>(As + cm_offset(tid, 8 * g, kTM)) = v;
+        }
+        // B: BN rows (output channels of the GEMM) x 64 k
+        for (int e = tid; e < BN * (kTK / 8); e += kTcThreads) {
+            const int nn = e / (kTK / 8), g = e % (kTK / 8);
+            const int k = k0 + 8 * g;
+            uint4 v = make_uint4(0, 0, 0, 0);
+            if (k < K) {
+                const int tap = k / Cin_g, c = k - tap * Cin_g;
+                if (!kBwdData) {
+                    // B(k = (tap, ci), n = co) = W[co][tap][ci]: 8 contiguous ci
+                    v = *reinterpret_cast<const uint4 *>(w + ((long long)(n0 + nn) * 9 + tap) * Cin_w + c);
+                } else {
+                    // B(k = (tap, co), n = ci) = W[co][8 - tap][ci]: 8 co with stride 9 Cin_w
+                    __align__(16) __nv_bfloat16 t[8];
+#pragma unroll
+                    for (int q = 0; q < 8; ++q) t[q] = w[((long long)(c + q) * 9 + (8 - tap)) * Cin_w + n0 + nn];
+                    v = *reinterpret_cast<const uint4 *>(t);
+                }
+            }
+            *reinterpret_cast<uint4 *>(Bs + cm_offset(nn, 8 * g, BN)) = v;
+        }
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        __syncthreads();
+        if (tid == 0) {
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const uint32_t a0 = smem_u32(As), b0 = smem_u32(Bs);
+#pragma unroll
+            for (int j = 0; j < kTK / 16; ++j) {
+                // K slice j: core-matrix columns 2j and 2j + 1
+                const uint64_t ad = smem_desc(a0 + 2 * j * (kTM / 8) * 128, (kTM / 8) * 128, 128);
+                const uint64_t bd = smem_desc(b0 + 2 * j * (BN / 8) * 128, (BN / 8) * 128, 128);
+                const uint32_t acc = (s > 0 || j > 0) ? 1u : 0u;
+                asm volatile(
+                    "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+                    " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(tmem),
+                    "l"(ad), "l"(bd), "r"(idesc), "r"(acc)
+                    : "memory");
+            }
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                             smem_u32(&mbar[buf]))
+                         : "memory");
+        }
+        last = s;
+    }
+    // all MMAs done: the last commit tracks every earlier MMA of the issuing
+    // thread (waited for also after a time-out, before the tensor memory is freed)
+    if (last >= 0) ok = mbar_wait(smem_u32(&mbar[last & 1]), (uint32_t)((last >> 1) & 1)) && ok;
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    if (ok) {
+        const long long p = p0 + warp * 32 + lane;  // TMEM lane = tile row = pixel
+#pragma unroll
+        for (int c = 0; c < BN; c += 8) {
+            uint32_t r[8];
+            asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+                         : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+                           "=r"(r[7])
+                         : "r"(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c));
+            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+            if (p < P) {
+                __align__(16) __nv_bfloat16 o[8];
+#pragma unroll
+                for (int q = 0; q < 8; ++q) {
+                    float v = __uint_as_float(r[q]);
+                    if (bias) v += bias[n0 + c + q];
+                    if (relu) v = fmaxf(v, 0.f);
+                    o[q] = __float2bfloat16_rn(v);
+                }
+                *reinterpret_cast<uint4 *>(out + p * Cout_g + n0 + c) = *reinterpret_cast<const uint4 *>(o);
+            }
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kCols) : "memory");
+}
+
+template <bool kBwdData, int BN>
+cudaError_t launch_conv_tc(const __nv_bfloat16 *in, const __nv_bfloat16 *w, const float *bias, __nv_bfloat16 *out,
+                           int N, int H, int W, int Cin_g, int Cout_g, int relu, cudaStream_t s) {
+    const size_t smem = 2 * (size_t)(kTM * kTK * 2) + 2 * (size_t)(BN * kTK * 2);
+    cudaError_t e = cudaFuncSetAttribute(conv3x3_tc_kernel<kBwdData, BN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess) return e;
+    const long long P = (long long)N * H * W;
+    dim3 grid((unsigned)((P + kTM - 1) / kTM), Cout_g / BN);
+    conv3x3_tc_kernel<kBwdData, BN><<<grid, kTcThreads, smem, s>>>(in, w, bias, out, N, H, W, Cin_g, Cout_g, relu);
+    return cudaGetLastError();
+}
+
+// Convolution on the tcgen05 path (default) or the warp-level MMA path.
+bool g_use_tc = true;
+
+template <bool kBwdData>
+cudaError_t conv_dispatch(const __nv_bfloat16 *in, const __nv_bfloat16 *w, const float *bias, __nv_bfloat16 *out,
+                          int N, int H, int W, int Cin_g, int Cout_g, int relu, cudaStream_t s) {
+    const int BN = Cout_g % 128 == 0 ? 128 : (Cout_g % 64 == 0 ? 64 : (Cout_g % 32 == 0 ? 32 : 16));
+    if (g_use_tc) {
+        switch (BN) {
+            case 128: return launch_conv_tc<kBwdData, 128>(in, w, bias, out, N, H, W, Cin_g, Cout_g, relu, s);
+            case 64: return launch_conv_tc<kBwdData, 64>(in, w, bias, out, N, H, W, Cin_g, Cout_g, relu, s);
+            case 32: return launch_conv_tc<kBwdData, 32>(in, w, bias, out, N, H, W, Cin_g, Cout_g, relu, s);
+            default: return launch_conv_tc<kBwdData, 16>(in, w, bias, out, N, H, W, Cin_g, Cout_g, relu, s);
+        }
+    }
+    const long long P = (long long)N * H * W;
+    const int bn = BN >= 64 ? 64 : BN;
+    dim3 grid((unsigned)((P + kBM - 1) / kBM), Cout_g / bn);
+    if (bn == 64) conv3x3_kernel<kBwdData, 64><<<grid, kThreads, 0, s>>>(in, w, bias, out, N, H, W, Cin_g, Cout_g, relu);
+    else if (bn == 32) conv3x3_kernel<kBwdData, 32><<<grid, kThreads, 0, s>>>(in, w, bias, out, N, H, W, Cin_g, Cout_g, relu);
+    else conv3x3_kernel<kBwdData, 16><<<grid, kThreads, 0, s>>>(in, w, bias, out, N, H, W, Cin_g, Cout_g, relu);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
 // 3x3 convolution, weight gradient: dW[co][t][ci] += sum_p dY[p][co] X[p + d(t)][ci]
 // GEMM per tap: M = Cout (tile 64), N = Cin (tile 16), K = pixels (chunk of 64 per
 // stage, split over the grid's z dimension); FP32 partial sums are added atomically.
@@ -406,19 +641,26 @@ extern "C" {
 
 const char *cdf_nn_last_error(void) { return g_nn_err; }
 
+cdf_nn_status cdf_nn_set_tensor_path(int tcgen05) {
+    g_use_tc = tcgen05 != 0;
+    return CDF_NN_OK;
+}
+
+cdf_nn_status cdf_nn_error_flag(int *out) {
+    if (!out) return nn_fail("error_flag: NULL argument");
+    const cudaError_t e = cudaMemcpyFromSymbol(out, g_tc_error, sizeof(int));
+    if (e != cudaSuccess) return nn_fail(cudaGetErrorString(e));
+    return CDF_NN_OK;
+}
+
 cdf_nn_status cdf_nn_conv3x3_fwd(const void *x, const void *w, const float *bias, void *y, int N, int H, int W,
                                  int Cin, int Cout, int relu, void *stream) {
     if (!x || !w || !y || N < 1 || H < 1 || W < 1 || Cin % 16 || Cout % 32 || Cin < 16)
         return nn_fail("conv3x3_fwd: bad arguments (Cin % 16, Cout % 32)");
-    const long long P = (long long)N * H * W;
-    const int BN = Cout % 64 == 0 ? 64 : 32;
-    dim3 grid((unsigned)((P + kBM - 1) / kBM), Cout / BN);
-    auto s = static_cast<cudaStream_t>(stream);
-    const auto *xi = static_cast<const __nv_bfloat16 *>(x);
-    const auto *wi = static_cast<const __nv_bfloat16 *>(w);
-    auto *yo = static_cast<__nv_bfloat16 *>(y);
-    if (BN == 64) conv3x3_kernel<false, 64><<<grid, kThreads, 0, s>>>(xi, wi, bias, yo, N, H, W, Cin, Cout, relu);
-    else conv3x3_kernel<false, 32><<<grid, kThreads, 0, s>>>(xi, wi, bias, yo, N, H, W, Cin, Cout, relu);
+    cudaError_t e = conv_dispatch<false>(static_cast<const __nv_bfloat16 *>(x), static_cast<const __nv_bfloat16 *>(w),
+                                         bias, static_cast<__nv_bfloat16 *>(y), N, H, W, Cin, Cout, relu,
+                                         static_cast<cudaStream_t>(stream));
+    if (e != cudaSuccess) { cudaGetLastError(); return nn_fail(cudaGetErrorString(e)); }
     return launched();
 }
 
@@ -426,16 +668,10 @@ cdf_nn_status cdf_nn_conv3x3_bwd_data(const void *dy, const void *w, void *dx, i
                                       void *stream) {
     if (!dy || !w || !dx || N < 1 || H < 1 || W < 1 || Cin % 16 || Cout % 32)
         return nn_fail("conv3x3_bwd_data: bad arguments (Cin % 16, Cout % 32)");
-    const long long P = (long long)N * H * W;
-    const int BN = Cin % 64 == 0 ? 64 : (Cin % 32 == 0 ? 32 : 16);
-    dim3 grid((unsigned)((P + kBM - 1) / kBM), Cin / BN);
-    auto s = static_cast<cudaStream_t>(stream);
-    const auto *di = static_cast<const __nv_bfloat16 *>(dy);
-    const auto *wi = static_cast<const __nv_bfloat16 *>(w);
-    auto *xo = static_cast<__nv_bfloat16 *>(dx);
-    if (BN == 64) conv3x3_kernel<true, 64><<<grid, kThreads, 0, s>>>(di, wi, nullptr, xo, N, H, W, Cout, Cin, 0);
-    else if (BN == 32) conv3x3_kernel<true, 32><<<grid, kThreads, 0, s>>>(di, wi, nullptr, xo, N, H, W, Cout, Cin, 0);
-    else conv3x3_kernel<true, 16><<<grid, kThreads, 0, s>>>(di, wi, nullptr, xo, N, H, W, Cout, Cin, 0);
+    cudaError_t e = conv_dispatch<true>(static_cast<const __nv_bfloat16 *>(dy), static_cast<const __nv_bfloat16 *>(w),
+                                        nullptr, static_cast<__nv_bfloat16 *>(dx), N, H, W, Cout, Cin, 0,
+                                        static_cast<cudaStream_t>(stream));
+    if (e != cudaSuccess) { cudaGetLastError(); return nn_fail(cudaGetErrorString(e)); }
     return launched();
 }
 

@@ -36,6 +36,8 @@ NN_SIGNATURES = {
     "cdf_nn_mse": [ctypes.c_void_p] * 4 + [ctypes.c_longlong, ctypes.c_void_p],
     "cdf_nn_adam": [ctypes.c_void_p] * 5 + [ctypes.c_longlong] + [ctypes.c_float] * 4 + [ctypes.c_longlong,
                                                                                          ctypes.c_void_p],
+    "cdf_nn_set_tensor_path": [ctypes.c_int],
+    "cdf_nn_error_flag": [ctypes.POINTER(ctypes.c_int)],
 }
 _nn = None
 
@@ -51,6 +53,19 @@ def nn_lib():
         L.cdf_nn_last_error.restype = ctypes.c_char_p
         _nn = L
     return _nn
+
+
+def set_tensor_path(tcgen05: bool):
+    """Convolutions on the 5th-generation tensor cores (True, the default) or on the
+    warp-level MMA kernels (False)."""
+    _call("cdf_nn_set_tensor_path", int(bool(tcgen05)))
+
+
+def tensor_error_flag() -> int:
+    """1 if a bounded wait of a tcgen05 convolution ever ran out."""
+    v = ctypes.c_int(0)
+    _call("cdf_nn_error_flag", ctypes.byref(v))
+    return v.value
 
 
 def _call(name, *args):

@@ -29,14 +29,26 @@ def S(cdf):
     return surrogate, torch
 
 
+@pytest.fixture(params=["tcgen05", "mma"])
+def path(S, request):
+    """Run a convolution test on each tensor-core path, and check afterwards that no
+    bounded wait of the tcgen05 kernels ran out."""
+    sur, torch = S
+    sur.set_tensor_path(request.param == "tcgen05")
+    yield request.param
+    torch.cuda.synchronize()
+    sur.set_tensor_path(True)
+    assert sur.tensor_error_flag() == 0
+
+
 def bf(torch, a):
     t = torch.as_tensor(np.asarray(a, np.float32)).cuda().to(torch.bfloat16)
     return t, t.float().cpu().numpy().astype(np.float64)
 
 
 @pytest.mark.parametrize("N,H,W,Cin,Cout", [(2, 9, 13, 16, 32), (1, 8, 8, 32, 64), (2, 5, 7, 96, 32),
-                                            (1, 4, 4, 384, 128)])
-def test_conv_forward(S, N, H, W, Cin, Cout):
+                                            (1, 4, 4, 384, 128), (2, 24, 20, 64, 128)])
+def test_conv_forward(S, path, N, H, W, Cin, Cout):
     sur, torch = S
     r = np.random.default_rng(N * 1000 + Cin)
     x, xr = bf(torch, r.normal(size=(N, H, W, Cin)))
@@ -48,8 +60,8 @@ def test_conv_forward(S, N, H, W, Cin, Cout):
 
 
 @pytest.mark.parametrize("N,H,W,Cin,Cout", [(2, 9, 13, 16, 32), (1, 8, 8, 64, 64), (2, 5, 7, 96, 32),
-                                            (1, 4, 4, 384, 128)])
-def test_conv_backward(S, N, H, W, Cin, Cout):
+                                            (1, 4, 4, 384, 128), (2, 24, 20, 128, 64)])
+def test_conv_backward(S, path, N, H, W, Cin, Cout):
     sur, torch = S
     r = np.random.default_rng(N * 7 + Cin)
     x, xr = bf(torch, r.normal(size=(N, H, W, Cin)))
