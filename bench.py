@@ -191,7 +191,8 @@ class _Single:
             self.kernel = (f"resident_kernel<{pb.m}> (tile-resident persistent step, {info.tiles} CTAs of "
                            f"{info.tile_x}x{info.tile_y} nodes)")
         else:
-            self.kernel = f"step_kernel<{pb.m},{ {0: 'float', 1: '__half', 2: '__nv_bfloat16'}[info.storage]}>"
+            self.kernel = (f"step_kernel<{pb.m},float>" if info.storage == 0 else
+                           f"step_kernel_mr<{pb.m},{ {1: '__half', 2: '__nv_bfloat16'}[info.storage]}>")
         if getattr(pb, "case1", False):
             self.kernel = f"step_kernel_case1<{pb.m}> (prescribed velocity, no fluid)"
 

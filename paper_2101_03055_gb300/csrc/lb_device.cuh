@@ -343,6 +343,11 @@ __device__ __forceinline__ void store_node(T *out, long long P, long long o0, co
 // global-memory kernels, the tile-resident kernel and the 16-bit storage.
 // kInterior: the caller guarantees that no link of the node crosses a wall or
 // wraps; every source is then x - c_i and the selects fold away.
+// Is node (x, y) at least one node away from every edge of the lattice?
+__device__ __forceinline__ bool inner_node(const LbParams &p, int x, int y) {
+    return x >= 1 && x + 1 < p.nx && y >= 1 && y + 1 < p.ny;
+}
+
 template <class Pos>
 struct PullTable {
     int hplane[9];
@@ -497,8 +502,11 @@ __device__ __forceinline__ void pull_scalars(const LbParams &p, int x, int y, co
 
 // ---- the fused step ------------------------------------------------------------
 // One node of the fused step (x < nx, y < ny) on global-memory buffers: pull,
-// moments, collision, store.
-template <int M, typename T, bool kL2 = false>
+// moments, collision, store.  kInterior: the caller guarantees that the node is
+// at least one node away from every edge of the lattice (no link crosses a wall
+// or wraps); the pull then reads x - c_i directly.  Both forms give the same
+// bits for such a node.
+template <int M, typename T, bool kL2 = false, bool kInterior = false>
 __device__ __forceinline__ void step_node(const LbParams &p, int x, int y, const T *__restrict__ in,
                                           T *__restrict__ out, float *__restrict__ sprev,
                                           float *__restrict__ moments) {
@@ -510,7 +518,7 @@ __device__ __forceinline__ void step_node(const LbParams &p, int x, int y, const
     const bool consume = (M >= 2 && p.skind == 2);
     const float sp1 = consume ? (kL2 ? __ldca(sprev + o0) : sprev[o0]) : 0.f;
     float h[9], f[M][5];
-    pull_node<M, false>(p, x, y, mk, ld, f, h);
+    pull_node<M, kInterior>(p, x, y, mk, ld, f, h);
 
     NodeOut<M> o;
     collide<M>(p, f, h, pref_at(p, x, y), sp1, false, o);

@@ -301,8 +301,10 @@ cdf_status autotune(cdf_lb *h) {
     std::vector<dim3> cands = {dim3(32, 4), dim3(32, 8), dim3(64, 2), dim3(64, 4),
                                dim3(128, 1), dim3(128, 2), dim3(256, 1)};
     if (!h->mr && !h->P.case1) {
-        cands.push_back(dim3(128, 0));
-        cands.push_back(dim3(256, 0));
+        // flat launches of several widths: a lattice that fills about one wave
+        // is fastest when its nodes split evenly over the 152 SMs (e.g. 131,072
+        // nodes in 1366 CTAs of 96 threads: nine CTAs on every SM)
+        for (unsigned w : {64u, 96u, 128u, 160u, 192u, 224u, 256u}) cands.push_back(dim3(w, 0));
     }
     cudaEvent_t a, b;
     CK(cudaEventCreate(&a));

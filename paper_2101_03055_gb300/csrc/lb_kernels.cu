@@ -47,8 +47,12 @@ __global__ void __launch_bounds__(256) step_kernel(const LbParams p, const T *__
     pdl_wait_and_release();
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     const int y = blockIdx.y * blockDim.y + threadIdx.y;
-    if (x >= p.nx || y >= p.ny) return;
-    step_node<M, T>(p, x, y, in, out, sprev, moments);
+    // Warp-uniform choice (every CTA holds whole warps): a warp whose 32 nodes
+    // all lie inside the boundary ring runs the pull without boundary selects.
+    if (__all_sync(0xffffffffu, inner_node(p, x, y)))
+        step_node<M, T, false, true>(p, x, y, in, out, sprev, moments);
+    else if (x < p.nx && y < p.ny)
+        step_node<M, T>(p, x, y, in, out, sprev, moments);
 }
 
 // Flat launch: one thread per node over nx * ny (no idle threads in ragged rows).
@@ -58,9 +62,12 @@ __global__ void __launch_bounds__(256) step_kernel_flat(const LbParams p, const 
                                                         float *__restrict__ moments) {
     pdl_wait_and_release();
     const int idx = blockIdx.x * blockDim.x + threadIdx.x;
-    if (idx >= p.nx * p.ny) return;
+    const bool valid = idx < p.nx * p.ny;
     const int y = idx / p.nx, x = idx - y * p.nx;
-    step_node<M, T>(p, x, y, in, out, sprev, moments);
+    if (__all_sync(0xffffffffu, valid && inner_node(p, x, y)))
+        step_node<M, T, false, true>(p, x, y, in, out, sprev, moments);
+    else if (valid)
+        step_node<M, T>(p, x, y, in, out, sprev, moments);
 }
 
 // ---- Case 1 of Sec. 2.1: convection cross-diffusion in a prescribed velocity -----
@@ -240,20 +247,19 @@ __device__ __forceinline__ float href_dir(const LbParams &p, int j, float pr, fl
     return fmaf(0.5f * kA9(j), kC9x(j) * __fmul_rn(p.g[0], fm) + kC9y(j) * __fmul_rn(p.g[1], fm), heq_dir(j, pr, ux, uy));
 }
 
-template <int M, typename T>
-__global__ void __launch_bounds__(256, (M <= 2 ? 3 : 1)) step_kernel_mr(const LbParams p, const T *__restrict__ in,
-                                                      const float *__restrict__ min, T *__restrict__ out,
-                                                      float *__restrict__ mout, float *__restrict__ sprev) {
-    pdl_wait_and_release();
-    const int x = blockIdx.x * blockDim.x + threadIdx.x;
-    const int y = blockIdx.y * blockDim.y + threadIdx.y;
-    if (x >= p.nx || y >= p.ny) return;
+// One node of the 16-bit step.  kInterior as in step_node: with no link
+// crossing a wall the source directions are compile-time constants, so the
+// rebuilt equilibria need no run-time direction selects.
+template <int M, typename T, bool kInterior>
+__device__ __forceinline__ void step_node_mr(const LbParams &p, int x, int y, const T *__restrict__ in,
+                                             const float *__restrict__ min, T *__restrict__ out,
+                                             float *__restrict__ mout, float *__restrict__ sprev) {
     const long long P = p.plane;
     const int pitch = p.pitch;
     const int o0 = y * pitch + x;
     // Pull sources exactly as in step_kernel (the pressure-reference shifts are
     // zero here: the host sets p_ref = 0 for this storage).
-    const auto t = pull_table<false>(p, x, y, [pitch](int sx, int sy) { return sy * pitch + sx; });
+    const auto t = pull_table<kInterior>(p, x, y, [pitch](int sx, int sy) { return sy * pitch + sx; });
 
     // ---- loads: stored deviations and the source nodes' moments (the axis
     // sources of the fluid and of the scalars are the same nodes)
@@ -308,6 +314,20 @@ __global__ void __launch_bounds__(256, (M <= 2 ? 3 : 1)) step_kernel_mr(const Lb
         for (int i = 0; i < 5; ++i) Store<T>::store(out + (9 + 5 * a + i) * P + o0, f[a][i] - feq[a][i]);
     if (consume) sprev[o0] = o.s1;
     write_moments<M>(mout, P, o0, o);
+}
+
+template <int M, typename T>
+__global__ void __launch_bounds__(256, (M <= 2 ? 3 : 1)) step_kernel_mr(const LbParams p, const T *__restrict__ in,
+                                                      const float *__restrict__ min, T *__restrict__ out,
+                                                      float *__restrict__ mout, float *__restrict__ sprev) {
+    pdl_wait_and_release();
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int y = blockIdx.y * blockDim.y + threadIdx.y;
+    // warp-uniform interior path, as in step_kernel
+    if (__all_sync(0xffffffffu, inner_node(p, x, y)))
+        step_node_mr<M, T, true>(p, x, y, in, min, out, mout, sprev);
+    else if (x < p.nx && y < p.ny)
+        step_node_mr<M, T, false>(p, x, y, in, min, out, mout, sprev);
 }
 
 template <int M, typename T>
