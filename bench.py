@@ -178,15 +178,19 @@ class ClockSampler:
 class _Single:
     """Uniform view of the single-lattice solver for the timing loops."""
 
-    def __init__(self, lib, pb, storage, resident=0):
+    def __init__(self, lib, pb, storage, resident=0, block=None, temporal=0):
         self.lib, self.pb = lib, pb
-        self.s = lib.Solver(pb, storage=storage, resident=resident)
+        self.s = lib.Solver(pb, storage=storage, resident=resident, block=block, temporal=temporal)
         info = self.s.info()
         self.nodes, self.bytes_per_lup, self.storage = pb.nodes, info.bytes_per_lup, info.storage
         self.block = [info.block_x, info.block_y]
         self.m = pb.m
         self.resident = bool(info.resident)
-        if self.resident:
+        self.pair = bool(info.temporal) and not self.resident
+        if self.pair:
+            self.kernel = (f"step2_kernel<{pb.m}> (two time steps per launch, CTAs of {info.block_x}x{info.block_y} "
+                           f"threads, output tiles {info.tile_x}x{info.tile_y})")
+        elif self.resident:
             self.block = [info.tile_x, info.tile_y]
             self.kernel = (f"resident_kernel<{pb.m}> (tile-resident persistent step, {info.tiles} CTAs of "
                            f"{info.tile_x}x{info.tile_y} nodes)")
@@ -198,11 +202,13 @@ class _Single:
 
     def steps_per_launch(self, n):
         """Lattice steps per kernel launch inside step(n)."""
-        return min(n, RESIDENT_MAX_STEPS) if self.resident else 1
+        return min(n, RESIDENT_MAX_STEPS) if self.resident else (2 if self.pair and n >= 2 else 1)
 
     def launches(self, n):
         """Kernels of this package launched by step(n)."""
-        return -(-n // RESIDENT_MAX_STEPS) if self.resident else n
+        if self.resident:
+            return -(-n // RESIDENT_MAX_STEPS)
+        return n // 2 + n % 2 if self.pair else n
 
     stream = property(lambda self: self.s.stream)
 
@@ -405,6 +411,10 @@ def main():
     ap.add_argument("--storage", default="fp32", choices=["fp32", "fp16", "bf16"])
     ap.add_argument("--resident", type=int, default=0, choices=[-1, 0, 1],
                     help="tile-resident step: 0 = the autotuner decides, 1 = always, -1 = never")
+    ap.add_argument("--temporal", type=int, default=0, choices=[-1, 0, 1],
+                    help="two time steps per launch: 0 = the autotuner decides, 1 = always, -1 = never")
+    ap.add_argument("--block", default=None,
+                    help="CTA shape 'X,Y' of the single-lattice step (Y = 0: flat launch); default: autotuned")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=3)
     args = ap.parse_args()
@@ -430,7 +440,8 @@ def main():
     elif isinstance(wl, I.Problem3D):
         runner = _Single3D(lib, wl, args.storage)
     else:
-        runner = _Single(lib, wl, args.storage, args.resident)
+        block = tuple(int(v) for v in args.block.split(",")) if args.block else None
+        runner = _Single(lib, wl, args.storage, args.resident, block, args.temporal)
     nodes = runner.nodes
     K, W, S = args.steps, args.warmup, args.lb_steps
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=device)

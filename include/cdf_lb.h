@@ -138,6 +138,19 @@ typedef struct {
                                           > 0) is not used and the force must be zero; G comes
                                           from the first-order difference u (phi(t) - phi(t - 1)).
                                           FP32 storage only. */
+    int temporal;                      /* two time steps per launch (temporal blocking: each CTA
+                                          updates its tile and a one-node halo into shared memory,
+                                          then the tile again from there; one pass over global
+                                          memory serves two steps), FP32 storage, full model:
+                                          0 = used when the autotuner measures it faster,
+                                          1 = always, -1 = never; a fixed block_x with
+                                          temporal = 0 keeps one step per launch */
+    int temporal_block_x, temporal_block_y, temporal_tile_y;
+                                       /* with temporal = 1: the two-step kernel's CTA shape
+                                          (block_x 32 or 64: the halo region is block_x nodes wide,
+                                          the output tile block_x - 2) and its output tile height;
+                                          0 = autotuned.  CDF_EINVAL if it cannot run the lattice
+                                          (periodic axes need nx >= block_x, ny >= tile_y + 2) */
 } cdf_options;
 
 /* Facts about a handle (for benchmarks and tests). */
@@ -151,6 +164,8 @@ typedef struct {
     int tile_x, tile_y, tiles;         /* its tile shape (nodes) and number of tiles */
     double bytes_per_lup;              /* minimal HBM bytes moved per node update */
     long long t;                       /* time steps taken since initialisation */
+    int temporal;                      /* 1 if two steps run per launch; block_x/y is then that
+                                          kernel's CTA shape and tile_x/y its output tile */
 } cdf_info;
 
 typedef struct cdf_lb cdf_lb;

@@ -109,7 +109,7 @@ __global__ void __launch_bounds__(256, 4) batch_kernel(const BatchInst *__restri
             const int x = tx * blockDim.x + threadIdx.x, y = ty * blockDim.y + threadIdx.y;
             if (x < sp.nx && y < sp.ny)
                 dev::step_node<M, float, true>(sp, x, y, in + s_off[0], out + s_off[0], sprev + s_off[1],
-                                         mom ? mom + s_off[2] : nullptr);
+                                               sprev + s_off[1], mom ? mom + s_off[2] : nullptr);
         }
         if (s + 1 < nsteps && !grid_barrier(bar, expected, timeout_ns, err)) return;
     }
@@ -279,7 +279,8 @@ cdf_status enqueue_chains(cdf_batch *b, int nsteps, bool moments_last, int parit
         for (int k = 0; k < b->count; ++k) {
             float *mom = (moments_last && st == nsteps - 1) ? b->mom + b->mom_off[k] : nullptr;
             BCK(launch_step(b->params[k], kFP32, b->buf[par] + b->pop_off[k], b->buf[par ^ 1] + b->pop_off[k],
-                            b->sprev + b->sp_off[k], mom, b->chain_block, b->pool[k % b->pool.size()]));
+                            b->sprev + b->sp_off[k], b->sprev + b->sp_off[k], mom, b->chain_block,
+                            b->pool[k % b->pool.size()]));
         }
     }
     for (size_t j = 0; j < b->pool.size(); ++j) {

@@ -506,9 +506,11 @@ __device__ __forceinline__ void pull_scalars(const LbParams &p, int x, int y, co
 // at least one node away from every edge of the lattice (no link crosses a wall
 // or wraps); the pull then reads x - c_i directly.  Both forms give the same
 // bits for such a node.
+// sp_in / sp_out: S_1(t - 1) of the consumption closure in, S_1(t) out (the
+// same plane, or two planes that alternate with the population buffers).
 template <int M, typename T, bool kL2 = false, bool kInterior = false>
 __device__ __forceinline__ void step_node(const LbParams &p, int x, int y, const T *__restrict__ in,
-                                          T *__restrict__ out, float *__restrict__ sprev,
+                                          T *__restrict__ out, const float *sp_in, float *sp_out,
                                           float *__restrict__ moments) {
     const long long P = p.plane;
     const int pitch = p.pitch;
@@ -516,14 +518,14 @@ __device__ __forceinline__ void step_node(const LbParams &p, int x, int y, const
     const auto ld = [in, P](int plane, int off) { return load_pop<T, kL2>(in + plane * P + off); };
     const int o0 = y * pitch + x;
     const bool consume = (M >= 2 && p.skind == 2);
-    const float sp1 = consume ? (kL2 ? __ldca(sprev + o0) : sprev[o0]) : 0.f;
+    const float sp1 = consume ? (kL2 ? __ldca(sp_in + o0) : sp_in[o0]) : 0.f;
     float h[9], f[M][5];
     pull_node<M, kInterior>(p, x, y, mk, ld, f, h);
 
     NodeOut<M> o;
     collide<M>(p, f, h, pref_at(p, x, y), sp1, false, o);
     store_node<M, T>(out, P, o0, f, h);
-    if (consume) sprev[o0] = o.s1;
+    if (consume) sp_out[o0] = o.s1;
     if (moments) write_moments<M>(moments, P, o0, o);
 }
 

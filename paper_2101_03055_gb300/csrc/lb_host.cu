@@ -114,7 +114,11 @@ struct cdf_lb {
     LbParams P{};
     void *buf[2] = {nullptr, nullptr};
     int cur = 0;  // buffer that holds the current post-collision populations
-    float *sprev = nullptr;
+    // S_1(t - 1) of the consumption closure: two planes that alternate with the
+    // population buffers (sprev_pp[cur] belongs to buf[cur]); a launch that
+    // advances two steps reads halo nodes that other CTAs rewrite, so the
+    // planes cannot be updated in place.
+    float *sprev_pp[2] = {nullptr, nullptr};
     float *vel = nullptr;  // Case 1: prescribed velocity and phi(t - 1), 2 + m planes
     float *mom = nullptr, *mom_prev = nullptr;
     bool mr = false;                       // 16-bit storage: node-equilibrium deviations
@@ -127,6 +131,10 @@ struct cdf_lb {
     cudaEvent_t ev_in = nullptr, ev_out = nullptr;
     cudaGraphExec_t graph[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};  // [parity][moments]
     dim3 block{64, 4, 1};
+    // Two time steps per launch (step2_kernel), FP32 storage: CTA shape and tile height.
+    bool pair = false;
+    dim3 pair_block{32, 16, 1};
+    int pair_th = 30;
     // Tile-resident persistent step (FP32 lattices that fit in shared memory).
     bool resident = false;
     ResidentGeom rg{};
@@ -147,7 +155,8 @@ void release(cdf_lb *h) {
             if (ge) cudaGraphExecDestroy(ge);
     cudaFree(h->buf[0]);
     cudaFree(h->buf[1]);
-    cudaFree(h->sprev);
+    cudaFree(h->sprev_pp[0]);
+    cudaFree(h->sprev_pp[1]);
     cudaFree(h->vel);
     cudaFree(h->mom);
     cudaFree(h->mom_prev);
@@ -186,9 +195,16 @@ float *current_moments(cdf_lb *h) { return h->mr ? h->mom_pp[h->cur] : h->mom; }
 cudaError_t launch_any(cdf_lb *h, int src, bool with_moments) {
     if (h->mr)
         return launch_step_mr(h->P, h->storage, h->buf[src], h->mom_pp[src], h->buf[src ^ 1], h->mom_pp[src ^ 1],
-                              h->sprev, h->block, h->s);
-    return launch_step(h->P, h->storage, h->buf[src], h->buf[src ^ 1], h->sprev, with_moments ? h->mom : nullptr,
-                       h->block, h->s);
+                              h->sprev_pp[src], h->sprev_pp[src ^ 1], h->block, h->s);
+    return launch_step(h->P, h->storage, h->buf[src], h->buf[src ^ 1], h->sprev_pp[src], h->sprev_pp[src ^ 1],
+                       with_moments ? h->mom : nullptr, h->block, h->s);
+}
+
+// Two steps from buf[src] to buf[src ^ 1] in one launch (FP32 storage).
+cudaError_t launch_two(cdf_lb *h, int src, bool with_moments) {
+    return launch_step2(h->P, static_cast<const float *>(h->buf[src]), static_cast<float *>(h->buf[src ^ 1]),
+                        h->sprev_pp[src], h->sprev_pp[src ^ 1], with_moments ? h->mom : nullptr, h->pair_block,
+                        h->pair_th, h->s);
 }
 
 cdf_status launch_one(cdf_lb *h, int src, bool with_moments) {
@@ -201,8 +217,10 @@ cdf_status get_graph(cdf_lb *h, int parity, int with_moments, cudaGraphExec_t *o
         cudaGraph_t graph = nullptr;
         CK(cudaStreamBeginCapture(h->s, cudaStreamCaptureModeThreadLocal));
         int src = parity;
-        for (int k = 0; k < kGraphSteps; ++k) {
-            cudaError_t e = launch_any(h, src, with_moments && k == kGraphSteps - 1);
+        const int launches = h->pair ? kGraphSteps / 2 : kGraphSteps;  // even: the graph keeps the parity
+        for (int k = 0; k < launches; ++k) {
+            const bool wm = with_moments && k == launches - 1;
+            cudaError_t e = h->pair ? launch_two(h, src, wm) : launch_any(h, src, wm);
             if (e != cudaSuccess) {
                 cudaStreamEndCapture(h->s, &graph);
                 if (graph) cudaGraphDestroy(graph);
@@ -250,8 +268,9 @@ cdf_status sync(cdf_lb *h) {
 cdf_status run_steps(cdf_lb *h, long long n) {
     while (h->resident && n > 0) {
         const int k = (int)std::min(n, kResidentMaxSteps);
-        CK(launch_resident(h->P, h->rg, static_cast<float *>(h->buf[0]), static_cast<float *>(h->buf[1]), h->sprev,
-                           h->mom, k, h->cur, k == n, h->counters, h->wait_ns, h->d_err, h->s));
+        CK(launch_resident(h->P, h->rg, static_cast<float *>(h->buf[0]), static_cast<float *>(h->buf[1]),
+                           h->sprev_pp[h->cur], h->sprev_pp[h->cur ^ (k & 1)], h->mom, k, h->cur, k == n,
+                           h->counters, h->wait_ns, h->d_err, h->s));
         CK(cudaMemcpyAsync(h->h_err, h->d_err, sizeof(int), cudaMemcpyDeviceToHost, h->s));
         if (k & 1) h->cur ^= 1;
         h->t += k;
@@ -266,7 +285,12 @@ cdf_status run_steps(cdf_lb *h, long long n) {
             n -= kGraphSteps;
             h->t += kGraphSteps;
         } else {
-            for (long long j = 0; j < n; ++j) {
+            long long j = 0;
+            for (; h->pair && j + 2 <= n; j += 2) {
+                CK(launch_two(h, h->cur, j + 2 == n));
+                h->cur ^= 1;
+            }
+            for (; j < n; ++j) {
                 cdf_status st = launch_one(h, h->cur, j == n - 1);
                 if (st != CDF_OK) return st;
                 h->cur ^= 1;
@@ -359,6 +383,129 @@ cdf_status time_steps(cdf_lb *h, long long steps, float *ms) {
     if (st != CDF_OK) return st;
     if (e != cudaSuccess) return fail(CDF_ECUDA, "timing failed: %s", cudaGetErrorString(e));
     return check_wait(h);
+}
+
+// Drop the captured step graphs (after a change of launch mode or shape).
+void drop_graphs(cdf_lb *h) {
+    for (auto &row : h->graph)
+        for (auto &ge : row)
+            if (ge) {
+                cudaGraphExecDestroy(ge);
+                ge = nullptr;
+            }
+}
+
+// Can step2_kernel run this lattice with CTA shape b and tile height th?
+bool pair_fits(const cdf_lb *h, dim3 b, int th) {
+    if (b.x % 32 != 0 || b.x < 32 || (int)(b.x * b.y) > step2_max_threads(h->m) || th < 1) return false;
+    if (step2_smem_bytes(h->m, b, th) > (size_t)kStep2MaxSmem) return false;
+    if (h->P.periodic_x && h->nx < (int)b.x) return false;
+    if (h->P.periodic_y && h->ny < th + 2) return false;
+    return true;
+}
+
+// Decide whether two steps per launch (step2_kernel) run this lattice: always
+// when asked for (with the best measured tile), never when refused, otherwise
+// when a pair of steps measures faster than two launches of the step kernel.
+// Results are cached per (nx, ny, m, storage, closure).
+struct PairChoice {
+    bool use;
+    dim3 block;
+    int th;
+};
+using PairKey = std::tuple<int, int, int, int, int, int>;  // + periodic axes
+std::map<PairKey, PairChoice> g_pair_cache;
+
+cdf_status setup_pair(cdf_lb *h, const cdf_options *opt) {
+    // a fixed CTA shape of the step kernel fixes the one-step launch unless two
+    // steps per launch are asked for explicitly
+    if (h->mr || h->P.case1 || opt->temporal == -1 || opt->resident == 1 || (opt->block_x > 0 && opt->temporal == 0))
+        return CDF_OK;
+    if (opt->temporal_block_x > 0) {  // a given shape
+        const dim3 b(opt->temporal_block_x, opt->temporal_block_y, 1);
+        if (!pair_fits(h, b, opt->temporal_tile_y))
+            return fail(CDF_EINVAL, "the two-step kernel shape %d x %d, tile height %d, cannot run this lattice",
+                        opt->temporal_block_x, opt->temporal_block_y, opt->temporal_tile_y);
+        h->pair = true;
+        h->pair_block = b;
+        h->pair_th = opt->temporal_tile_y;
+        return CDF_OK;
+    }
+    PairKey key{h->nx, h->ny, h->m, h->P.chemotaxis, h->P.periodic_x, h->P.periodic_y};
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        auto it = g_pair_cache.find(key);
+        if (it != g_pair_cache.end()) {
+            h->pair = opt->temporal == 1 || it->second.use;
+            h->pair_block = it->second.block;
+            h->pair_th = it->second.th;
+            return CDF_OK;
+        }
+    }
+    // candidates: R1 rows of 32 or 64 nodes, tile heights that give one or two
+    // passes of the CTA's thread rows
+    std::vector<std::pair<dim3, int>> cands;
+    for (unsigned w : {32u, 64u})
+        for (int th : {6, 14, 30, 32, 46, 62})
+            for (unsigned by : {(unsigned)(th + 2), (unsigned)((th + 3) / 2), 8u, 16u}) {
+                const dim3 b(w, by, 1);
+                if (!pair_fits(h, b, th)) continue;
+                bool dup = false;
+                for (auto &c : cands) dup = dup || (c.first.x == b.x && c.first.y == b.y && c.second == th);
+                if (!dup) cands.push_back({b, th});
+            }
+    if (cands.empty()) {
+        if (opt->temporal == 1) return fail(CDF_EINVAL, "the lattice is too small for two steps per launch");
+        return CDF_OK;
+    }
+    cudaEvent_t a, b;
+    CK(cudaEventCreate(&a));
+    CK(cudaEventCreate(&b));
+    const long long nodes = (long long)h->nx * h->ny;
+    const int reps = nodes >= (1 << 22) ? 4 : 16;
+    auto timed = [&](auto &&launch, float *ms) -> cdf_status {
+        for (int w = 0; w < 2; ++w) CK(launch(w & 1));
+        CK(cudaEventRecord(a, h->s));
+        for (int r = 0; r < reps; ++r) CK(launch(r & 1));
+        CK(cudaEventRecord(b, h->s));
+        CK(cudaEventSynchronize(b));
+        CK(cudaEventElapsedTime(ms, a, b));
+        return CDF_OK;
+    };
+    float t_single = 0.f;
+    cdf_status st = timed([&](int src) -> cudaError_t {
+        cudaError_t e = launch_any(h, src, false);
+        return e != cudaSuccess ? e : launch_any(h, src ^ 1, false);
+    }, &t_single);
+    float best = 1e30f;
+    PairChoice choice{false, h->pair_block, h->pair_th};
+    for (size_t k = 0; st == CDF_OK && k < cands.size(); ++k) {
+        h->pair_block = cands[k].first;
+        h->pair_th = cands[k].second;
+        float ms = 0.f;
+        st = timed([&](int src) { return launch_two(h, src, false); }, &ms);
+        if (st == CDF_OK && ms < best) {
+            best = ms;
+            choice.block = cands[k].first;
+            choice.th = cands[k].second;
+        }
+    }
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    if (st != CDF_OK) return st;
+    choice.use = opt->temporal == 1 || best < t_single;
+    h->pair = choice.use;
+    h->pair_block = choice.block;
+    h->pair_th = choice.th;
+    drop_graphs(h);
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        g_pair_cache[key] = PairChoice{best < t_single, choice.block, choice.th};
+    }
+    // the timing ran on the zeroed buffers; the init calls set the state
+    CK(cudaMemsetAsync(h->sprev_pp[0], 0, (size_t)h->plane * 4, h->s));
+    CK(cudaMemsetAsync(h->sprev_pp[1], 0, (size_t)h->plane * 4, h->s));
+    return CDF_OK;
 }
 
 // Decide whether the tile-resident step runs this lattice: always when asked
@@ -554,6 +701,16 @@ cdf_status cdf_lb_create(const cdf_grid *grid, int m, const cdf_diffusion *dif, 
     if (opt->prescribed_velocity && (frc->g[0] != 0.0 || frc->g[1] != 0.0))
         return fail(CDF_EINVAL, "the prescribed-velocity mode has no force: set g = 0");
     if (!(opt->rho0 > 0.0)) return fail(CDF_EINVAL, "rho0 must be positive");
+    if (opt->temporal < -1 || opt->temporal > 1) return fail(CDF_EINVAL, "temporal must be -1, 0 or 1");
+    if (opt->temporal_block_x != 0 || opt->temporal_block_y != 0 || opt->temporal_tile_y != 0) {
+        if (opt->temporal != 1) return fail(CDF_EINVAL, "a two-step kernel shape needs temporal = 1");
+        if ((opt->temporal_block_x != 32 && opt->temporal_block_x != 64) || opt->temporal_block_y < 1 ||
+            opt->temporal_tile_y < 1)
+            return fail(CDF_EINVAL, "two-step kernel shape: block_x 32 or 64, block_y >= 1, tile_y >= 1");
+    }
+    if (opt->temporal == 1 && (opt->storage != CDF_FP32 || opt->prescribed_velocity || opt->resident == 1))
+        return fail(CDF_EINVAL, "two steps per launch exist for FP32 storage of the full model, without the "
+                                "resident step");
     LbParams P0{};
     const int align = opt->storage == CDF_FP32 ? 32 : 64;  // 128-byte rows
     const int pitch = grid->nx >= 1 ? (grid->nx + align - 1) / align * align : 0;
@@ -591,7 +748,8 @@ cdf_status cdf_lb_create(const cdf_grid *grid, int m, const cdf_diffusion *dif, 
     const size_t n = (size_t)h->nx * h->ny;
     auto alloc = [&](void **p, size_t bytes) -> bool { return cudaMalloc(p, bytes) == cudaSuccess; };
     bool ok = alloc(&h->buf[0], pop_bytes) && alloc(&h->buf[1], pop_bytes) &&
-              alloc((void **)&h->sprev, (size_t)h->plane * 4) &&
+              alloc((void **)&h->sprev_pp[0], (size_t)h->plane * 4) &&
+              alloc((void **)&h->sprev_pp[1], (size_t)h->plane * 4) &&
               (!h->P.case1 || alloc((void **)&h->vel, (size_t)(2 + m) * h->plane * 4)) &&
               alloc((void **)&h->mom, (size_t)(m + 3) * h->plane * 4) &&
               alloc((void **)&h->mom_prev, (size_t)(m + 3) * h->plane * 4) &&
@@ -616,7 +774,8 @@ cdf_status cdf_lb_create(const cdf_grid *grid, int m, const cdf_diffusion *dif, 
     }
     if (cudaMemsetAsync(h->buf[0], 0, pop_bytes, h->s) != cudaSuccess ||
         cudaMemsetAsync(h->buf[1], 0, pop_bytes, h->s) != cudaSuccess ||
-        cudaMemsetAsync(h->sprev, 0, (size_t)h->plane * 4, h->s) != cudaSuccess ||
+        cudaMemsetAsync(h->sprev_pp[0], 0, (size_t)h->plane * 4, h->s) != cudaSuccess ||
+        cudaMemsetAsync(h->sprev_pp[1], 0, (size_t)h->plane * 4, h->s) != cudaSuccess ||
         cudaMemsetAsync(h->mom, 0, (size_t)(m + 3) * h->plane * 4, h->s) != cudaSuccess ||
         (h->mr && (cudaMemsetAsync(h->mom_pp[0], 0, (size_t)(m + 3) * h->plane * 4, h->s) != cudaSuccess ||
                    cudaMemsetAsync(h->mom_pp[1], 0, (size_t)(m + 3) * h->plane * 4, h->s) != cudaSuccess))) {
@@ -629,7 +788,7 @@ cdf_status cdf_lb_create(const cdf_grid *grid, int m, const cdf_diffusion *dif, 
         release(h);
         return st;
     }
-    if ((st = setup_resident(h, opt)) != CDF_OK) {
+    if ((st = setup_pair(h, opt)) != CDF_OK || (st = setup_resident(h, opt)) != CDF_OK) {
         release(h);
         return st;
     }
@@ -652,9 +811,9 @@ void cdf_lb_destroy(cdf_lb *h) {
 
 static cdf_status init_from_device_fields(cdf_lb *h, const float *fields) {
     if (h->mr)
-        CK(launch_init_mr(h->P, h->storage, fields, h->nx, h->buf[0], h->mom_pp[0], h->sprev, h->s));
+        CK(launch_init_mr(h->P, h->storage, fields, h->nx, h->buf[0], h->mom_pp[0], h->sprev_pp[0], h->s));
     else
-        CK(launch_init(h->P, h->storage, fields, h->nx, h->buf[0], h->sprev, h->mom, h->s));
+        CK(launch_init(h->P, h->storage, fields, h->nx, h->buf[0], h->sprev_pp[0], h->mom, h->s));
     h->cur = 0;
     h->t = 0;
     h->initialised = true;
@@ -796,7 +955,7 @@ cdf_status cdf_lb_populations(cdf_lb *h, double *f, double *hf, double *s_now) {
     CK(cudaMemcpyAsync(tmp.data(), h->dense, tmp.size() * 4, cudaMemcpyDeviceToHost, h->s));
     if (s_now && h->sprev_planes) {
         sp.resize((size_t)h->plane);
-        CK(cudaMemcpyAsync(sp.data(), h->sprev, sp.size() * 4, cudaMemcpyDeviceToHost, h->s));
+        CK(cudaMemcpyAsync(sp.data(), h->sprev_pp[h->cur], sp.size() * 4, cudaMemcpyDeviceToHost, h->s));
     }
     if ((st = sync(h)) != CDF_OK) return st;
     if (hf)
@@ -836,7 +995,7 @@ cdf_status cdf_lb_save(cdf_lb *h, const char *path) {
     const size_t velb = h->P.case1 ? (size_t)(2 + h->m) * h->plane * 4 : 0;
     std::vector<char> data(pop + spb + momb + velb);
     CK(cudaMemcpyAsync(data.data(), h->buf[h->cur], pop, cudaMemcpyDeviceToHost, h->s));
-    CK(cudaMemcpyAsync(data.data() + pop, h->sprev, spb, cudaMemcpyDeviceToHost, h->s));
+    CK(cudaMemcpyAsync(data.data() + pop, h->sprev_pp[h->cur], spb, cudaMemcpyDeviceToHost, h->s));
     CK(cudaMemcpyAsync(data.data() + pop + spb, current_moments(h), momb, cudaMemcpyDeviceToHost, h->s));
     if (velb) CK(cudaMemcpyAsync(data.data() + pop + spb + momb, h->vel, velb, cudaMemcpyDeviceToHost, h->s));
     if ((st = sync(h)) != CDF_OK) return st;
@@ -887,7 +1046,7 @@ cdf_status cdf_lb_load(cdf_lb *h, const char *path) {
     if (st != CDF_OK) return st;
     h->cur = 0;
     CK(cudaMemcpyAsync(h->buf[0], data.data(), pop, cudaMemcpyHostToDevice, h->s));
-    CK(cudaMemcpyAsync(h->sprev, data.data() + pop, spb, cudaMemcpyHostToDevice, h->s));
+    CK(cudaMemcpyAsync(h->sprev_pp[0], data.data() + pop, spb, cudaMemcpyHostToDevice, h->s));
     CK(cudaMemcpyAsync(current_moments(h), data.data() + pop + spb, momb, cudaMemcpyHostToDevice, h->s));
     if (velb) CK(cudaMemcpyAsync(h->vel, data.data() + pop + spb + momb, velb, cudaMemcpyHostToDevice, h->s));
     if ((st = reset_resident(h)) != CDF_OK) return st;
@@ -911,6 +1070,14 @@ cdf_status cdf_lb_get_info(const cdf_lb *h, cdf_info *out) {
     if (h->P.case1)  // scalars read and written, u read, phi(t - 1) read and written
         out->bytes_per_lup = 2.0 * 5 * h->m * 4.0 + 8.0 + 8.0 * h->m + 8.0 * h->sprev_planes;
     out->t = h->t;
+    out->temporal = h->pair ? 1 : 0;
+    if (h->pair) {
+        out->block_x = (int)h->pair_block.x;
+        out->block_y = (int)h->pair_block.y;
+        out->tile_x = (int)h->pair_block.x - 2;
+        out->tile_y = h->pair_th;
+        out->tiles = ((h->nx + out->tile_x - 1) / out->tile_x) * ((h->ny + h->pair_th - 1) / h->pair_th);
+    }
     return CDF_OK;
 }
 

@@ -53,8 +53,18 @@ enum Storage { kFP32 = 0, kFP16 = 1, kBF16 = 2 };
 // threads per CTA over the nx * ny nodes in row order (FP32 storage path).  `in`/`out` point at the first of `planes`
 // population planes; plane k starts at base + k * plane.  Planes are ordered
 // h_0..h_8, then f_{a,0..4} for a = 0..m-1.
-cudaError_t launch_step(const LbParams &p, int storage, const void *in, void *out, float *sprev,
-                        float *moments, dim3 block, cudaStream_t s);
+cudaError_t launch_step(const LbParams &p, int storage, const void *in, void *out, const float *sp_in,
+                        float *sp_out, float *moments, dim3 block, cudaStream_t s);
+// Two time steps in one launch (FP32 storage): block.x (32 or 64) x block.y
+// threads per CTA, output tiles of (block.x - 2) x th nodes; sp_in and sp_out
+// must be different planes.  step2_smem_bytes: its dynamic shared memory.
+constexpr int kStep2MaxSmem = 227 * 1024;
+// CTA size bound of step2_kernel: 64 registers a thread (1024 threads) hold the
+// node update for m <= 2 without spills; m = 3, 4 need 128 (512 threads).
+constexpr int step2_max_threads(int m) { return m <= 2 ? 1024 : 512; }
+size_t step2_smem_bytes(int m, dim3 block, int th);
+cudaError_t launch_step2(const LbParams &p, const float *in, float *out, const float *sp_in, float *sp_out,
+                         float *moments, dim3 block, int th, cudaStream_t s);
 cudaError_t launch_init(const LbParams &p, int storage, const float *fields, int fields_pitch,
                         void *out, float *sprev, float *moments, cudaStream_t s);
 cudaError_t launch_export(const LbParams &p, int storage, const void *in, float *dense,
@@ -63,7 +73,7 @@ cudaError_t launch_export(const LbParams &p, int storage, const void *in, float 
 // own equilibrium, with the node's moments (phi, u, p) in FP32 (m + 3 planes);
 // moments are ping-ponged with the populations.
 cudaError_t launch_step_mr(const LbParams &p, int storage, const void *in, const float *moments_in, void *out,
-                           float *moments_out, float *sprev, dim3 block, cudaStream_t s);
+                           float *moments_out, const float *sp_in, float *sp_out, dim3 block, cudaStream_t s);
 cudaError_t launch_init_mr(const LbParams &p, int storage, const float *fields, int fields_pitch, void *out,
                            float *moments_out, float *sprev, cudaStream_t s);
 cudaError_t launch_export_mr(const LbParams &p, int storage, const void *in, const float *moments, float *dense,
@@ -90,7 +100,8 @@ bool plan_resident(int nx, int ny, int m, ResidentGeom *out);
 // nsteps steps from buffer parity0 (buf0 or buf1) in one cooperative launch;
 // `counters` holds one step counter per tile (all equal between launches;
 // zero them together), *err is set when a wait ran out.
-cudaError_t launch_resident(const LbParams &p, const ResidentGeom &g, float *buf0, float *buf1, float *sprev,
+cudaError_t launch_resident(const LbParams &p, const ResidentGeom &g, float *buf0, float *buf1, const float *sp_in,
+                            float *sprev,
                             float *moments, int nsteps, int parity0, bool moments_last, unsigned *counters,
                             unsigned long long timeout_ns, int *err, cudaStream_t s);
 

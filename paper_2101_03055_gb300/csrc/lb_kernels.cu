@@ -15,6 +15,7 @@
 // addresses, and the overlap between neighbouring warps is served from L1/L2.
 #include "lb_device.cuh"
 
+#include <atomic>
 #include <type_traits>
 
 namespace cdflb {
@@ -25,11 +26,12 @@ using namespace dev;
 // pdl_wait_and_release): it may begin while the previous kernel of the stream
 // finishes, and waits inside for that kernel's results.
 template <typename... KArgs, typename... Args>
-cudaError_t launch_pdl(void (*kern)(KArgs...), dim3 grid, dim3 block, cudaStream_t s, Args... args) {
+cudaError_t launch_pdl_smem(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+                            Args... args) {
     cudaLaunchConfig_t cfg{};
     cfg.gridDim = grid;
     cfg.blockDim = block;
-    cfg.dynamicSmemBytes = 0;
+    cfg.dynamicSmemBytes = smem;
     cfg.stream = s;
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
@@ -38,11 +40,15 @@ cudaError_t launch_pdl(void (*kern)(KArgs...), dim3 grid, dim3 block, cudaStream
     cfg.numAttrs = 1;
     return cudaLaunchKernelEx(&cfg, kern, args...);
 }
+template <typename... KArgs, typename... Args>
+cudaError_t launch_pdl(void (*kern)(KArgs...), dim3 grid, dim3 block, cudaStream_t s, Args... args) {
+    return launch_pdl_smem(kern, grid, block, 0, s, args...);
+}
 
 // ---- the fused step ------------------------------------------------------------
 template <int M, typename T>
 __global__ void __launch_bounds__(256) step_kernel(const LbParams p, const T *__restrict__ in,
-                                                   T *__restrict__ out, float *__restrict__ sprev,
+                                                   T *__restrict__ out, const float *sp_in, float *sp_out,
                                                    float *__restrict__ moments) {
     pdl_wait_and_release();
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
@@ -50,24 +56,124 @@ __global__ void __launch_bounds__(256) step_kernel(const LbParams p, const T *__
     // Warp-uniform choice (every CTA holds whole warps): a warp whose 32 nodes
     // all lie inside the boundary ring runs the pull without boundary selects.
     if (__all_sync(0xffffffffu, inner_node(p, x, y)))
-        step_node<M, T, false, true>(p, x, y, in, out, sprev, moments);
+        step_node<M, T, false, true>(p, x, y, in, out, sp_in, sp_out, moments);
     else if (x < p.nx && y < p.ny)
-        step_node<M, T>(p, x, y, in, out, sprev, moments);
+        step_node<M, T>(p, x, y, in, out, sp_in, sp_out, moments);
 }
 
 // Flat launch: one thread per node over nx * ny (no idle threads in ragged rows).
 template <int M, typename T>
 __global__ void __launch_bounds__(256) step_kernel_flat(const LbParams p, const T *__restrict__ in,
-                                                        T *__restrict__ out, float *__restrict__ sprev,
+                                                        T *__restrict__ out, const float *sp_in, float *sp_out,
                                                         float *__restrict__ moments) {
     pdl_wait_and_release();
     const int idx = blockIdx.x * blockDim.x + threadIdx.x;
     const bool valid = idx < p.nx * p.ny;
     const int y = idx / p.nx, x = idx - y * p.nx;
     if (__all_sync(0xffffffffu, valid && inner_node(p, x, y)))
-        step_node<M, T, false, true>(p, x, y, in, out, sprev, moments);
+        step_node<M, T, false, true>(p, x, y, in, out, sp_in, sp_out, moments);
     else if (valid)
-        step_node<M, T>(p, x, y, in, out, sprev, moments);
+        step_node<M, T>(p, x, y, in, out, sp_in, sp_out, moments);
+}
+
+// ---- two time steps per launch (temporal blocking), FP32 storage ----------------
+// A small lattice lives in L2 between steps, and a one-step launch is then
+// bound by one full pass over the state plus the launch gap.  Here a CTA of
+// W1 x BY threads owns an output tile of (W1 - 2) x TH nodes and the region R1
+// around it, W1 x (TH + 2) nodes with origin (X0 - 1, Y0 - 1) (wrapped on
+// periodic axes).  Step t -> t+1: every R1 node that some tile node pulls from
+// is updated from the global buffer `in` into shared memory (plane stride
+// W1 (TH + 2), planes h_0..h_8, f_{a,0..4}, then S_1(t)); step t+1 -> t+2:
+// every tile node pulls from shared memory and stores to `out`.  The halo ring
+// is computed by both neighbouring CTAs, one pass over global memory serves
+// two steps, and each node runs the same pull table and collision as
+// step_kernel, so two launches of step_kernel and one of this kernel give the
+// same bits.  Needs nx >= W1 on a periodic x axis and ny >= TH + 2 on a
+// periodic y axis (a wrapped source must not land twice in R1).  S_1 is read
+// from sp_in and written to sp_out, which must be different planes: the halo
+// of one CTA is the tile of another.
+template <int M>
+__global__ void __launch_bounds__(step2_max_threads(M)) step2_kernel(const LbParams p, int TH, const float *__restrict__ in,
+                                                     float *__restrict__ out, const float *sp_in, float *sp_out,
+                                                     float *__restrict__ moments) {
+    constexpr int NP = 9 + 5 * M;
+    extern __shared__ float sm[];
+    pdl_wait_and_release();
+    const int W1 = blockDim.x, H1 = TH + 2, SP = W1 * H1, TW = W1 - 2;
+    const int X0 = blockIdx.x * TW, Y0 = blockIdx.y * TH;
+    const long long P = p.plane;
+    const int pitch = p.pitch, nx = p.nx, ny = p.ny;
+    const bool consume = M >= 2 && p.skind == 2;
+    const int lx = threadIdx.x;
+
+    // Column lx of R1: unwrapped x = X0 - 1 + lx.  It is needed when some tile
+    // node (x < min(X0 + TW, nx)) pulls from it, and it exists when it lies in
+    // the lattice or wraps on a periodic axis.
+    const int xu = X0 - 1 + lx;
+    const bool colv = xu <= min(X0 + TW, nx) && (p.periodic_x || (xu >= 0 && xu < nx));
+    const int gx = xu < 0 ? xu + nx : (xu >= nx ? xu - nx : xu);
+
+    // ---- step 1: R1 from global memory into shared memory
+    {
+        const auto mk = [pitch](int sx, int sy) { return sy * pitch + sx; };
+        const auto ld = [in, P](int plane, int off) { return __ldg(in + plane * P + off); };
+        for (int ly = threadIdx.y; ly < H1; ly += blockDim.y) {
+            const int yu = Y0 - 1 + ly;
+            const bool ok = colv && yu <= min(Y0 + TH, ny) && (p.periodic_y || (yu >= 0 && yu < ny));
+            const int gy = yu < 0 ? yu + ny : (yu >= ny ? yu - ny : yu);
+            const bool general = ok && !inner_node(p, gx, gy);
+            float h[9], f[M][5];
+            if (!__any_sync(0xffffffffu, general)) {
+                if (!ok) continue;
+                pull_node<M, true>(p, gx, gy, mk, ld, f, h);
+            } else {
+                if (!ok) continue;
+                pull_node<M, false>(p, gx, gy, mk, ld, f, h);
+            }
+            const int o0 = gy * pitch + gx, l0 = ly * W1 + lx;
+            NodeOut<M> o;
+            collide<M>(p, f, h, pref_at(p, gx, gy), consume ? sp_in[o0] : 0.f, false, o);
+#pragma unroll
+            for (int i = 0; i < 9; ++i) sm[i * SP + l0] = h[i];
+#pragma unroll
+            for (int a = 0; a < M; ++a)
+#pragma unroll
+                for (int i = 0; i < 5; ++i) sm[(9 + 5 * a + i) * SP + l0] = f[a][i];
+            if (consume) sm[NP * SP + l0] = o.s1;
+        }
+    }
+    __syncthreads();
+
+    // ---- step 2: the tile from shared memory into global memory
+    const auto lds = [SP](int plane, int off) { return sm[plane * SP + off]; };
+    // interior nodes pull from x - c_i without wrapping
+    const auto mk_in = [W1, X0, Y0](int sx, int sy) { return (sy - Y0 + 1) * W1 + (sx - X0 + 1); };
+    // general nodes: wrapped source coordinates back into R1
+    const auto mk_gen = [W1, H1, X0, Y0, nx, ny](int sx, int sy) {
+        int a = sx - X0 + 1, b = sy - Y0 + 1;
+        a = a < 0 ? a + nx : (a >= W1 ? a - nx : a);
+        b = b < 0 ? b + ny : (b >= H1 ? b - ny : b);
+        return b * W1 + a;
+    };
+    for (int ly = 1 + threadIdx.y; ly <= TH; ly += blockDim.y) {
+        const int x = xu, y = Y0 - 1 + ly;
+        const bool ok = lx >= 1 && lx <= TW && x < nx && y < ny;
+        const bool general = ok && !inner_node(p, x, y);
+        float h[9], f[M][5];
+        if (!__any_sync(0xffffffffu, general)) {
+            if (!ok) continue;
+            pull_node<M, true>(p, x, y, mk_in, lds, f, h);
+        } else {
+            if (!ok) continue;
+            pull_node<M, false>(p, x, y, mk_gen, lds, f, h);
+        }
+        const int o0 = y * pitch + x;
+        NodeOut<M> o;
+        collide<M>(p, f, h, pref_at(p, x, y), consume ? sm[NP * SP + ly * W1 + lx] : 0.f, false, o);
+        store_node<M, float>(out, P, o0, f, h);
+        if (consume) sp_out[o0] = o.s1;
+        if (moments) write_moments<M>(moments, P, o0, o);
+    }
 }
 
 // ---- Case 1 of Sec. 2.1: convection cross-diffusion in a prescribed velocity -----
@@ -77,7 +183,7 @@ __global__ void __launch_bounds__(256) step_kernel_flat(const LbParams p, const 
 // writes only its own entry).  Algorithmic bytes: 2 x 5m x 4 + 8 + 2 x 4m.
 template <int M>
 __global__ void __launch_bounds__(256) step_kernel_case1(const LbParams p, const float *__restrict__ in,
-                                                         float *__restrict__ out, float *__restrict__ sprev,
+                                                         float *__restrict__ out, const float *sp_in, float *sp_out,
                                                          float *__restrict__ moments) {
     pdl_wait_and_release();
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
@@ -96,7 +202,7 @@ __global__ void __launch_bounds__(256) step_kernel_case1(const LbParams p, const
 #pragma unroll
     for (int a = 0; a < M; ++a) php[a] = vel[(2 + a) * P + o0];
     const bool consume = (M >= 2 && p.skind == 2);
-    const float sp1 = consume ? sprev[o0] : 0.f;
+    const float sp1 = consume ? sp_in[o0] : 0.f;
     NodeOut<M> o;
     collide_case1<M>(p, f, ux, uy, php, sp1, false, o);
 #pragma unroll
@@ -105,7 +211,7 @@ __global__ void __launch_bounds__(256) step_kernel_case1(const LbParams p, const
         for (int i = 0; i < 5; ++i) out[(9 + 5 * a + i) * P + o0] = f[a][i];
 #pragma unroll
     for (int a = 0; a < M; ++a) vel[(2 + a) * P + o0] = php[a];
-    if (consume) sprev[o0] = o.s1;
+    if (consume) sp_out[o0] = o.s1;
     if (moments) write_moments<M>(moments, P, o0, o);
 }
 
@@ -253,7 +359,7 @@ __device__ __forceinline__ float href_dir(const LbParams &p, int j, float pr, fl
 template <int M, typename T, bool kInterior>
 __device__ __forceinline__ void step_node_mr(const LbParams &p, int x, int y, const T *__restrict__ in,
                                              const float *__restrict__ min, T *__restrict__ out,
-                                             float *__restrict__ mout, float *__restrict__ sprev) {
+                                             float *__restrict__ mout, const float *sp_in, float *sp_out) {
     const long long P = p.plane;
     const int pitch = p.pitch;
     const int o0 = y * pitch + x;
@@ -280,7 +386,7 @@ __device__ __forceinline__ void step_node_mr(const LbParams &p, int x, int y, co
 #pragma unroll
         for (int a = 0; a < M; ++a) f[a][i] = Store<T>::load(in + (9 + 5 * a + t.splane[i]) * P + t.spos[i]);
     const bool consume = (M >= 2 && p.skind == 2);
-    const float sp1 = consume ? sprev[o0] : 0.f;
+    const float sp1 = consume ? sp_in[o0] : 0.f;
 
     // ---- rebuild the pre-collision populations (deviation variables of collide)
 #pragma unroll
@@ -312,22 +418,22 @@ __device__ __forceinline__ void step_node_mr(const LbParams &p, int x, int y, co
     for (int a = 0; a < M; ++a)
 #pragma unroll
         for (int i = 0; i < 5; ++i) Store<T>::store(out + (9 + 5 * a + i) * P + o0, f[a][i] - feq[a][i]);
-    if (consume) sprev[o0] = o.s1;
+    if (consume) sp_out[o0] = o.s1;
     write_moments<M>(mout, P, o0, o);
 }
 
 template <int M, typename T>
 __global__ void __launch_bounds__(256, (M <= 2 ? 3 : 1)) step_kernel_mr(const LbParams p, const T *__restrict__ in,
                                                       const float *__restrict__ min, T *__restrict__ out,
-                                                      float *__restrict__ mout, float *__restrict__ sprev) {
+                                                      float *__restrict__ mout, const float *sp_in, float *sp_out) {
     pdl_wait_and_release();
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     const int y = blockIdx.y * blockDim.y + threadIdx.y;
     // warp-uniform interior path, as in step_kernel
     if (__all_sync(0xffffffffu, inner_node(p, x, y)))
-        step_node_mr<M, T, true>(p, x, y, in, min, out, mout, sprev);
+        step_node_mr<M, T, true>(p, x, y, in, min, out, mout, sp_in, sp_out);
     else if (x < p.nx && y < p.ny)
-        step_node_mr<M, T, false>(p, x, y, in, min, out, mout, sprev);
+        step_node_mr<M, T, false>(p, x, y, in, min, out, mout, sp_in, sp_out);
 }
 
 template <int M, typename T>
@@ -392,16 +498,16 @@ __global__ void export_kernel_mr(const LbParams p, const T *__restrict__ in, con
 
 template <typename T>
 cudaError_t step_mr_dispatch(const LbParams &p, const void *in, const float *min, void *out, float *mout,
-                             float *sprev, dim3 block, cudaStream_t s) {
+                             const float *sp_in, float *sp_out, dim3 block, cudaStream_t s) {
     dim3 grid((p.nx + block.x - 1) / block.x, (p.ny + block.y - 1) / block.y);
     const T *i = static_cast<const T *>(in);
     T *o = static_cast<T *>(out);
     cudaError_t e = cudaSuccess;
     switch (p.m) {
-        case 1: e = launch_pdl(step_kernel_mr<1, T>, grid, block, s, p, i, min, o, mout, sprev); break;
-        case 2: e = launch_pdl(step_kernel_mr<2, T>, grid, block, s, p, i, min, o, mout, sprev); break;
-        case 3: e = launch_pdl(step_kernel_mr<3, T>, grid, block, s, p, i, min, o, mout, sprev); break;
-        case 4: e = launch_pdl(step_kernel_mr<4, T>, grid, block, s, p, i, min, o, mout, sprev); break;
+        case 1: e = launch_pdl(step_kernel_mr<1, T>, grid, block, s, p, i, min, o, mout, sp_in, sp_out); break;
+        case 2: e = launch_pdl(step_kernel_mr<2, T>, grid, block, s, p, i, min, o, mout, sp_in, sp_out); break;
+        case 3: e = launch_pdl(step_kernel_mr<3, T>, grid, block, s, p, i, min, o, mout, sp_in, sp_out); break;
+        case 4: e = launch_pdl(step_kernel_mr<4, T>, grid, block, s, p, i, min, o, mout, sp_in, sp_out); break;
         default: return cudaErrorInvalidValue;
     }
     return e != cudaSuccess ? e : cudaGetLastError();
@@ -437,7 +543,7 @@ cudaError_t export_mr_dispatch(const LbParams &p, const void *in, const float *m
 }
 
 template <typename T>
-cudaError_t step_dispatch(const LbParams &p, const void *in, void *out, float *sprev, float *mom,
+cudaError_t step_dispatch(const LbParams &p, const void *in, void *out, const float *sp_in, float *sp_out, float *mom,
                           dim3 block, cudaStream_t s) {
     const T *i = static_cast<const T *>(in);
     T *o = static_cast<T *>(out);
@@ -447,10 +553,10 @@ cudaError_t step_dispatch(const LbParams &p, const void *in, void *out, float *s
             dim3 grid((p.nx + b2.x - 1) / b2.x, (p.ny + b2.y - 1) / b2.y);
             cudaError_t e = cudaSuccess;
             switch (p.m) {
-                case 1: e = launch_pdl(step_kernel_case1<1>, grid, b2, s, p, i, o, sprev, mom); break;
-                case 2: e = launch_pdl(step_kernel_case1<2>, grid, b2, s, p, i, o, sprev, mom); break;
-                case 3: e = launch_pdl(step_kernel_case1<3>, grid, b2, s, p, i, o, sprev, mom); break;
-                case 4: e = launch_pdl(step_kernel_case1<4>, grid, b2, s, p, i, o, sprev, mom); break;
+                case 1: e = launch_pdl(step_kernel_case1<1>, grid, b2, s, p, i, o, sp_in, sp_out, mom); break;
+                case 2: e = launch_pdl(step_kernel_case1<2>, grid, b2, s, p, i, o, sp_in, sp_out, mom); break;
+                case 3: e = launch_pdl(step_kernel_case1<3>, grid, b2, s, p, i, o, sp_in, sp_out, mom); break;
+                case 4: e = launch_pdl(step_kernel_case1<4>, grid, b2, s, p, i, o, sp_in, sp_out, mom); break;
                 default: return cudaErrorInvalidValue;
             }
             return e != cudaSuccess ? e : cudaGetLastError();
@@ -462,10 +568,10 @@ cudaError_t step_dispatch(const LbParams &p, const void *in, void *out, float *s
         dim3 fb(block.x), grid((unsigned)((n + block.x - 1) / block.x));
         cudaError_t e = cudaSuccess;
         switch (p.m) {
-            case 1: e = launch_pdl(step_kernel_flat<1, T>, grid, fb, s, p, i, o, sprev, mom); break;
-            case 2: e = launch_pdl(step_kernel_flat<2, T>, grid, fb, s, p, i, o, sprev, mom); break;
-            case 3: e = launch_pdl(step_kernel_flat<3, T>, grid, fb, s, p, i, o, sprev, mom); break;
-            case 4: e = launch_pdl(step_kernel_flat<4, T>, grid, fb, s, p, i, o, sprev, mom); break;
+            case 1: e = launch_pdl(step_kernel_flat<1, T>, grid, fb, s, p, i, o, sp_in, sp_out, mom); break;
+            case 2: e = launch_pdl(step_kernel_flat<2, T>, grid, fb, s, p, i, o, sp_in, sp_out, mom); break;
+            case 3: e = launch_pdl(step_kernel_flat<3, T>, grid, fb, s, p, i, o, sp_in, sp_out, mom); break;
+            case 4: e = launch_pdl(step_kernel_flat<4, T>, grid, fb, s, p, i, o, sp_in, sp_out, mom); break;
             default: return cudaErrorInvalidValue;
         }
         return e != cudaSuccess ? e : cudaGetLastError();
@@ -473,10 +579,10 @@ cudaError_t step_dispatch(const LbParams &p, const void *in, void *out, float *s
     dim3 grid((p.nx + block.x - 1) / block.x, (p.ny + block.y - 1) / block.y);
     cudaError_t e = cudaSuccess;
     switch (p.m) {
-        case 1: e = launch_pdl(step_kernel<1, T>, grid, block, s, p, i, o, sprev, mom); break;
-        case 2: e = launch_pdl(step_kernel<2, T>, grid, block, s, p, i, o, sprev, mom); break;
-        case 3: e = launch_pdl(step_kernel<3, T>, grid, block, s, p, i, o, sprev, mom); break;
-        case 4: e = launch_pdl(step_kernel<4, T>, grid, block, s, p, i, o, sprev, mom); break;
+        case 1: e = launch_pdl(step_kernel<1, T>, grid, block, s, p, i, o, sp_in, sp_out, mom); break;
+        case 2: e = launch_pdl(step_kernel<2, T>, grid, block, s, p, i, o, sp_in, sp_out, mom); break;
+        case 3: e = launch_pdl(step_kernel<3, T>, grid, block, s, p, i, o, sp_in, sp_out, mom); break;
+        case 4: e = launch_pdl(step_kernel<4, T>, grid, block, s, p, i, o, sp_in, sp_out, mom); break;
         default: return cudaErrorInvalidValue;
     }
     return e != cudaSuccess ? e : cudaGetLastError();
@@ -526,14 +632,49 @@ cudaError_t export_dispatch(const LbParams &p, const void *in, float *dense, cud
 
 }  // namespace
 
-cudaError_t launch_step(const LbParams &p, int storage, const void *in, void *out, float *sprev,
+cudaError_t launch_step(const LbParams &p, int storage, const void *in, void *out, const float *sp_in, float *sp_out,
                         float *moments, dim3 block, cudaStream_t s) {
     switch (storage) {
-        case kFP32: return step_dispatch<float>(p, in, out, sprev, moments, block, s);
-        case kFP16: return step_dispatch<__half>(p, in, out, sprev, moments, block, s);
-        case kBF16: return step_dispatch<__nv_bfloat16>(p, in, out, sprev, moments, block, s);
+        case kFP32: return step_dispatch<float>(p, in, out, sp_in, sp_out, moments, block, s);
+        case kFP16: return step_dispatch<__half>(p, in, out, sp_in, sp_out, moments, block, s);
+        case kBF16: return step_dispatch<__nv_bfloat16>(p, in, out, sp_in, sp_out, moments, block, s);
     }
     return cudaErrorInvalidValue;
+}
+
+size_t step2_smem_bytes(int m, dim3 block, int th) {
+    return (size_t)(9 + 5 * m + 1) * block.x * (th + 2) * sizeof(float);
+}
+
+cudaError_t launch_step2(const LbParams &p, const float *in, float *out, const float *sp_in, float *sp_out,
+                         float *moments, dim3 block, int th, cudaStream_t s) {
+    const size_t smem = step2_smem_bytes(p.m, block, th);
+    dim3 grid((p.nx + block.x - 3) / (block.x - 2), (p.ny + th - 1) / th);
+    // the opt-in to more than 48 KB of dynamic shared memory, once per device and m
+    static std::atomic<bool> attr_set[64][kMaxM + 1];
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+    switch (p.m) {
+#define CDF_STEP2_CASE(MM)                                                                               \
+    case MM:                                                                                             \
+        if (!attr_set[dev][MM].load()) {                                                                 \
+            e = cudaFuncSetAttribute(step2_kernel<MM>, cudaFuncAttributeMaxDynamicSharedMemorySize,      \
+                                     kStep2MaxSmem);                                                     \
+            if (e != cudaSuccess) return e;                                                              \
+            attr_set[dev][MM].store(true);                                                               \
+        }                                                                                                \
+        e = launch_pdl_smem(step2_kernel<MM>, grid, block, smem, s, p, th, in, out, sp_in, sp_out, moments); \
+        break;
+        CDF_STEP2_CASE(1)
+        CDF_STEP2_CASE(2)
+        CDF_STEP2_CASE(3)
+        CDF_STEP2_CASE(4)
+#undef CDF_STEP2_CASE
+        default: return cudaErrorInvalidValue;
+    }
+    return e != cudaSuccess ? e : cudaGetLastError();
 }
 
 cudaError_t launch_init(const LbParams &p, int storage, const float *fields, int fields_pitch,
@@ -556,10 +697,10 @@ cudaError_t launch_export(const LbParams &p, int storage, const void *in, float 
 }
 
 cudaError_t launch_step_mr(const LbParams &p, int storage, const void *in, const float *moments_in, void *out,
-                           float *moments_out, float *sprev, dim3 block, cudaStream_t s) {
+                           float *moments_out, const float *sp_in, float *sp_out, dim3 block, cudaStream_t s) {
     switch (storage) {
-        case kFP16: return step_mr_dispatch<__half>(p, in, moments_in, out, moments_out, sprev, block, s);
-        case kBF16: return step_mr_dispatch<__nv_bfloat16>(p, in, moments_in, out, moments_out, sprev, block, s);
+        case kFP16: return step_mr_dispatch<__half>(p, in, moments_in, out, moments_out, sp_in, sp_out, block, s);
+        case kBF16: return step_mr_dispatch<__nv_bfloat16>(p, in, moments_in, out, moments_out, sp_in, sp_out, block, s);
     }
     return cudaErrorInvalidValue;
 }

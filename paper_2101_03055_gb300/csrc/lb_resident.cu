@@ -120,7 +120,8 @@ __device__ __forceinline__ void ring_barrier(int threads) {
 
 template <int M>
 __global__ void __launch_bounds__(kResidentThreads, 1)
-    resident_kernel(const LbParams p, const ResidentGeom g, float *buf0, float *buf1, float *sprev, float *moments,
+    resident_kernel(const LbParams p, const ResidentGeom g, float *buf0, float *buf1, const float *sp_in,
+                    float *sprev, float *moments,
                     int nsteps, int parity0, int moments_last, unsigned *counters, unsigned long long timeout_ns,
                     int *err) {
     constexpr int NP = 9 + 5 * M;
@@ -172,7 +173,7 @@ __global__ void __launch_bounds__(kResidentThreads, 1)
             const int o0 = y * p.pitch + x, l0 = ly * g.tw + lx;
 #pragma unroll
             for (int k = 0; k < NP; ++k) sm[k * TS + l0] = in[k * P + o0];
-            if (consume) sp1 = sprev[o0];
+            if (consume) sp1 = sp_in[o0];
         }
     }
     __syncthreads();
@@ -289,7 +290,8 @@ bool plan_resident(int nx, int ny, int m, ResidentGeom *out) {
     return true;
 }
 
-cudaError_t launch_resident(const LbParams &p, const ResidentGeom &g, float *buf0, float *buf1, float *sprev,
+cudaError_t launch_resident(const LbParams &p, const ResidentGeom &g, float *buf0, float *buf1, const float *sp_in,
+                            float *sprev,
                             float *moments, int nsteps, int parity0, bool moments_last, unsigned *counters,
                             unsigned long long timeout_ns, int *err, cudaStream_t s) {
     const void *kern = resident_kernel_for(p.m);
@@ -297,7 +299,7 @@ cudaError_t launch_resident(const LbParams &p, const ResidentGeom &g, float *buf
     LbParams pp = p;
     ResidentGeom gg = g;
     int ml = moments_last ? 1 : 0;
-    void *args[] = {&pp, &gg, &buf0, &buf1, &sprev, &moments, &nsteps, &parity0, &ml, &counters, &timeout_ns, &err};
+    void *args[] = {&pp, &gg, &buf0, &buf1, &sp_in, &sprev, &moments, &nsteps, &parity0, &ml, &counters, &timeout_ns, &err};
     return cudaLaunchCooperativeKernel(kern, dim3(g.tiles_x * g.tiles_y), dim3(g.threads), args, g.smem_bytes, s);
 }
 

@@ -64,7 +64,9 @@ class cdf_options(ctypes.Structure):
                 ("phi_ref", ctypes.c_double * MAX_M), ("p_ref_grad", ctypes.c_double * 2),
                 ("block_x", ctypes.c_int), ("block_y", ctypes.c_int), ("resident", ctypes.c_int),
                 ("wait_timeout_s", ctypes.c_double), ("test_stall_tile", ctypes.c_int),
-                ("prescribed_velocity", ctypes.c_int)]
+                ("prescribed_velocity", ctypes.c_int), ("temporal", ctypes.c_int),
+                ("temporal_block_x", ctypes.c_int), ("temporal_block_y", ctypes.c_int),
+                ("temporal_tile_y", ctypes.c_int)]
 
 
 class cdf_info(ctypes.Structure):
@@ -72,7 +74,7 @@ class cdf_info(ctypes.Structure):
                 ("storage", ctypes.c_int), ("planes", ctypes.c_int), ("sprev_planes", ctypes.c_int),
                 ("block_x", ctypes.c_int), ("block_y", ctypes.c_int), ("resident", ctypes.c_int),
                 ("tile_x", ctypes.c_int), ("tile_y", ctypes.c_int), ("tiles", ctypes.c_int),
-                ("bytes_per_lup", ctypes.c_double), ("t", ctypes.c_longlong)]
+                ("bytes_per_lup", ctypes.c_double), ("t", ctypes.c_longlong), ("temporal", ctypes.c_int)]
 
 
 class cdf_batch_options(ctypes.Structure):
@@ -277,7 +279,8 @@ def cdf_moment_sums_static(dev_fields: int, dev_fields_old: int, nx: int, ny: in
 
 # ---- problem description -> C structs ------------------------------------------------
 def structs_from_problem(pb: Problem, storage: str = "fp32", stream: int = 0, block=None, phi_ref=None,
-                         p_ref_grad=None, resident: int = 0, wait_timeout_s: float = 0.0, test_stall_tile: int = 0):
+                         p_ref_grad=None, resident: int = 0, wait_timeout_s: float = 0.0, test_stall_tile: int = 0,
+                         temporal: int = 0, temporal_shape=None):
     m = pb.m
     if m > MAX_M:
         raise ValueError(f"m = {m} > {MAX_M}")
@@ -319,6 +322,9 @@ def structs_from_problem(pb: Problem, storage: str = "fp32", stream: int = 0, bl
         opt.block_x, opt.block_y = block
     opt.resident, opt.wait_timeout_s, opt.test_stall_tile = int(resident), float(wait_timeout_s), int(test_stall_tile)
     opt.prescribed_velocity = int(getattr(pb, "case1", False))
+    opt.temporal = int(temporal)
+    if temporal_shape is not None:
+        opt.temporal_block_x, opt.temporal_block_y, opt.temporal_tile_y = (int(v) for v in temporal_shape)
     return grid, dif, src, frc, bc, opt
 
 
@@ -348,14 +354,16 @@ class Solver:
 
     def __init__(self, pb: Problem, storage: str = "fp32", stream: int = 0, block=None, init: bool = True,
                  phi_ref=None, p_ref_grad=None, resident: int = 0, wait_timeout_s: float = 0.0,
-                 test_stall_tile: int = 0):
+                 test_stall_tile: int = 0, temporal: int = 0, temporal_shape=None):
         """resident: 0 = the autotuner decides whether the tile-resident step is
-        used, 1 = always, -1 = never (cdf_options.resident)."""
+        used, 1 = always, -1 = never (cdf_options.resident).  temporal: the
+        same choice for two steps per launch (cdf_options.temporal);
+        temporal_shape: (block_x, block_y, tile_y) of that kernel, or None."""
         self.pb = pb
         self.m, self.nx, self.ny = pb.m, pb.nx, pb.ny
         self.storage = storage
         self._structs = structs_from_problem(pb, storage, stream, block, phi_ref, p_ref_grad, resident,
-                                             wait_timeout_s, test_stall_tile)
+                                             wait_timeout_s, test_stall_tile, temporal, temporal_shape)
         grid, dif, src, frc, bc, opt = self._structs
         self.h = cdf_lb_create(grid, pb.m, dif, pb.nu, src, frc, bc, opt)
         if init:

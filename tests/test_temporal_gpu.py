@@ -1,0 +1,127 @@
+"""Two time steps per launch (cdf_options.temporal, step2_kernel).
+
+Each CTA updates its tile plus a one-node halo from global memory into shared
+memory, then the tile again from shared memory; every node runs the same pull
+table and collision as the one-step kernel.  So every result (moments,
+populations, S(t - 1)) must be bitwise equal to the one-step kernel's
+(temporal = -1) for every boundary combination, tile shape, scalar count and
+step count (odd counts end with one single step), and within the FP32 bound
+of the FP64 oracle.
+"""
+import os
+
+import numpy as np
+import pytest
+
+from paper_2101_03055_gb300 import inputs as I
+
+from test_parity_gpu import SIDE_CASES, _rand_problem, assert_parity
+
+pytestmark = pytest.mark.gpu
+
+
+def pair(cdf, pb, shape=None):
+    a = cdf.Solver(pb, temporal=1, resident=-1, temporal_shape=shape)
+    b = cdf.Solver(pb, temporal=-1, resident=-1, block=(128, 1))
+    ia, ib = a.info(), b.info()
+    assert ia.temporal == 1 and ib.temporal == 0
+    if shape is not None:
+        assert (ia.block_x, ia.block_y, ia.tile_x, ia.tile_y) == (shape[0], shape[1], shape[0] - 2, shape[2])
+    return a, b
+
+
+def assert_same(a, b):
+    assert np.array_equal(a.moments(), b.moments())
+    fa, ha, sa = a.populations()
+    fb, hb, sb = b.populations()
+    assert np.array_equal(fa, fb) and np.array_equal(ha, hb) and np.array_equal(sa, sb)
+    assert a.t == b.t
+
+
+@pytest.mark.parametrize("pb", [
+    I.chemotaxis_plume(512, 256, seed=3),
+    I.chemotaxis_plume(128, 64, seed=1),
+    I.cross_diffusion_taylor_green(),
+    I.ddc_cavity(128, Ra=1e5, Pr=0.7, Le=2.0, Nc=1.0, Df=0.1, Sr=0.1),
+], ids=["plume512x256", "plume128x64", "taylor_green64", "cavity128"])
+def test_two_step_launch_equals_one_step_kernel_bitwise(cdf, pb):
+    a, b = pair(cdf, pb)
+    for n in (1, 2, 37, 64, 100):  # odd counts, graph batches and their remainders
+        a.step(n)
+        b.step(n)
+    assert_same(a, b)
+
+
+@pytest.mark.parametrize("shape", [(32, 8, 6), (32, 16, 30), (32, 17, 32), (64, 8, 14), (32, 32, 30), (64, 5, 9)])
+def test_tile_shapes_bitwise(cdf, shape):
+    """CTA shapes with one, two and uneven passes of thread rows, halo regions of
+    32 and 64 nodes, tiles that do not divide the lattice."""
+    pb = I.chemotaxis_plume(200, 90, seed=6)
+    a, b = pair(cdf, pb, shape)
+    a.step(33)
+    b.step(33)
+    assert_same(a, b)
+
+
+@pytest.mark.parametrize("xcase", list(SIDE_CASES))
+@pytest.mark.parametrize("ycase", list(SIDE_CASES))
+def test_boundaries_bitwise_and_oracle(cdf, oracle_mod, xcase, ycase):
+    """Every pair of side types on a ragged 37 x 21 lattice: corners, free-slip
+    images and anti-bounce-back links computed in the halo and in the tile."""
+    pb = _rand_problem(37, 21, 2, 11, xcase, ycase)
+    a, b = pair(cdf, pb, (32, 8, 6))
+    a.step(60)
+    b.step(60)
+    assert_same(a, b)
+    o = oracle_mod.OracleSim(pb)
+    o.step(60)
+    assert_parity(a, o, 2)
+
+
+@pytest.mark.parametrize("nx,ny,m", [(1, 1, 2), (9, 1, 2), (2, 30, 2), (130, 3, 2), (29, 19, 1), (29, 19, 3),
+                                     (29, 19, 4), (70, 40, 4)])
+def test_sizes_and_scalar_counts(cdf, nx, ny, m):
+    """Walled lattices narrower than one tile, one-row lattices and m = 1 .. 4."""
+    pb = _rand_problem(nx, ny, m, 5, "mixed", "noslip_noflux")
+    a, b = pair(cdf, pb, (32, 4, 6) if m > 2 else (32, 8, 6))
+    a.step(25)
+    b.step(25)
+    assert_same(a, b)
+
+
+def test_periodic_wrap_and_consumption(cdf):
+    """Periodic axes exactly as wide as the halo region (the wrapped halo node is
+    the tile's own first column) with the consumption closure, whose S(t - 1)
+    planes alternate between the launches."""
+    pb = I.chemotaxis_plume(32, 40, seed=2)
+    w = I.periodic_side(pb.m)
+    pb = pb.replace(west=w, east=w)
+    a, b = pair(cdf, pb, (32, 8, 38))
+    a.step(41)
+    b.step(41)
+    assert_same(a, b)
+
+
+def test_too_small_periodic_lattice_is_refused(cdf):
+    pb = I.cross_diffusion_taylor_green(16, 16)
+    with pytest.raises(cdf.CdfError) as e:
+        cdf.Solver(pb, temporal=1, resident=-1, temporal_shape=(32, 8, 6))
+    assert e.value.status == cdf.CDF_EINVAL
+
+
+def test_checkpoint_and_run_to_steady(cdf, tmp_path):
+    pb = I.ddc_cavity(64, Ra=1e4, Pr=0.7, Le=2.0, Nc=1.0, Df=0.1, Sr=0.1)
+    a, b = pair(cdf, pb)
+    a.step(51)
+    path = os.path.join(tmp_path, "ck.bin")
+    a.save(path)
+    c = cdf.Solver(pb, temporal=1, resident=-1, init=False)
+    c.load(path)
+    b.step(51)
+    c.step(77)
+    b.step(77)
+    assert_same(c, b)
+    rc = c.run_to_steady(1e-30, check_every=41, max_steps=123)
+    rb = b.run_to_steady(1e-30, check_every=41, max_steps=123)
+    assert rc == rb and rc[1] == 123
+    assert_same(c, b)
