@@ -23,6 +23,11 @@ roofline -- the step kernel: algorithmic bytes per launch (bytes per lattice
            copy bandwidth.
 cpu_baseline -- the FP64 oracle on a bounded sample of the same workload on
            the host cores (rank 0, N = 1 only).
+copy_pass -- context for the roofline: one pass of a plain device copy (torch's
+           copy kernel, 32 copies per CUDA graph, two buffers used in turn) of
+           as many bytes as one lattice step reads and writes; the time floor of
+           any one-pass-per-step kernel at this size, also when the state is
+           L2-resident.
 """
 from __future__ import annotations
 
@@ -274,6 +279,11 @@ class _Batch:
             self.block = [info.chain_block_x, info.chain_block_y]
             self.kernel = (f"step_kernel<{self.m},float> x {info.count} instance chains "
                            f"(graph of 32 steps over a 32-stream pool)")
+        elif info.mode == 2:
+            self.block = [info.chain_block_x, info.chain_block_y]
+            self.kernel = (f"step2_kernel<{self.m}> x {info.count} instance chains (two time steps per launch, "
+                           f"CTAs of {info.chain_block_x}x{info.chain_block_y}, output tiles "
+                           f"{info.chain_block_x - 2}x{info.chain_tile_y}; graph of 32 steps over a 32-stream pool)")
         else:
             self.kernel = (f"batch_kernel<{self.m}> (persistent, {info.grid_blocks} CTAs, "
                            f"{info.steps_per_launch} steps/launch)")
@@ -283,11 +293,15 @@ class _Batch:
 
     def steps_per_launch(self, n):
         """Lattice steps per launch of the dominant kernel inside step(n) (chains:
-        one lattice step of one instance, counted here per whole sweep step)."""
-        return 1 if self.mode == 1 else min(n, self.spl)
+        one or two lattice steps of one instance, counted here per whole sweep step)."""
+        return {1: 1, 2: 2 if n >= 2 else 1}.get(self.mode, min(n, self.spl))
 
     def launches(self, n):
-        return n * self.count if self.mode == 1 else -(-n // self.spl)
+        if self.mode == 1:
+            return n * self.count
+        if self.mode == 2:
+            return (n // 2 + n % 2) * self.count
+        return -(-n // self.spl)
 
     stream = property(lambda self: self.s.stream)
 
@@ -304,6 +318,39 @@ class _Batch:
             self.lib.cdf_batch_moments(self.s.h, k, out)
             nbytes += 2 * (pb.m + 3) * pb.nodes * 4
         return nbytes
+
+
+def copy_pass(nbytes: int, device) -> dict:
+    """Time of one device copy of nbytes / 2 bytes (read + write = nbytes)."""
+    import torch
+    full = max(16, nbytes // 2 // 4)
+    n = min(full, 1 << 27)  # at most 512 MiB a buffer; the time is scaled to the full size
+    a = torch.zeros(n, dtype=torch.float32, device=device)
+    b = torch.zeros_like(a)
+    s = torch.cuda.Stream(device=device)
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.stream(s):
+        for _ in range(3):
+            b.copy_(a)
+            a.copy_(b)
+        torch.cuda.synchronize()
+        with torch.cuda.graph(g, stream=s):
+            for _ in range(16):
+                b.copy_(a)
+                a.copy_(b)
+        g.replay()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        reps = 10
+        e0.record(s)
+        for _ in range(reps):
+            g.replay()
+        e1.record(s)
+    torch.cuda.synchronize()
+    us = e0.elapsed_time(e1) * 1e3 / (32 * reps) * full / n
+    del a, b, g
+    return {"us": us, "bytes": 8 * full, "gbs": 8 * full / us / 1e3,
+            "what": "one torch copy of a state-sized buffer (bytes read + written = one lattice step's)"}
 
 
 def dist_setup():
@@ -483,6 +530,7 @@ def main():
     e2e_value = world * nodes * S * E / e2e_s / 1e6
     stage_bytes = moved // 2
 
+    cp = copy_pass(int(runner.bytes_per_lup * nodes), device)
     peak, peak_kind = measured_peaks()
     spl = runner.steps_per_launch(S)
     bytes_per_launch = runner.bytes_per_lup * nodes * spl
@@ -514,6 +562,7 @@ def main():
                      "peak_source": f"{peak_kind} copy bandwidth (MEASURED_PEAKS.json hbm_gbs)",
                      "bytes_per_lup": runner.bytes_per_lup, "kernel": runner.kernel,
                      "launch_us": launch_s * 1e6, "lattice_steps_per_launch": spl},
+        "copy_pass": cp,
         "gpu_launches": runner.launches(S) * K,
         "clocks": clk.summary(),
         "wall_s": wall,

@@ -254,8 +254,12 @@ typedef struct {
     int test_unreachable_barrier;/* test hook: the barrier expects one block more than runs,
                                     so every wait runs out and cdf_batch_step returns CDF_ETIMEOUT */
     int mode;                    /* with tile_x > 0: 0 = persistent kernel (tile = tile shape),
-                                    1 = graph of per-instance kernel chains (tile = CTA shape);
-                                    with tile_x = 0 the autotuner measures both and picks */
+                                    1 = graph of per-instance kernel chains (tile = CTA shape),
+                                    2 = the same chains of two-step launches (step2_kernel of
+                                    cdf_options.temporal; tile = its CTA shape, tile_x 32 or 64);
+                                    with tile_x = 0 the autotuner measures all three and picks */
+    int chain_tile_y;            /* mode 2 with tile_x > 0: output tile height of the two-step
+                                    kernel (0 = 14) */
 } cdf_batch_options;
 typedef struct {
     int count, m;
@@ -263,8 +267,10 @@ typedef struct {
     int tile_x, tile_y, grid_blocks, steps_per_launch;
     double bytes_per_lup;
     long long t;
-    int mode;                    /* 0 persistent kernel, 1 graph of per-instance chains */
+    int mode;                    /* 0 persistent kernel, 1 graph of per-instance chains,
+                                    2 chains of two-step launches */
     int chain_block_x, chain_block_y;
+    int chain_tile_y;            /* mode 2: output tile height of the two-step kernel */
 } cdf_batch_info;
 
 /* Create `count` lattices; every array argument has `count` entries (phi_ref:

@@ -148,7 +148,10 @@ struct cdf_batch {
     long long pop_total = 0, sp_total = 0, mom_total = 0, nodes = 0;
     int sprev_planes = 0;
     float *buf[2] = {nullptr, nullptr};
-    float *sprev = nullptr, *mom = nullptr, *dense = nullptr, *host_stage = nullptr;
+    // S_1(t - 1): the persistent kernel updates `sprev` in place; the kernel
+    // chains alternate `sprev` and `sprev2` with the population buffers (a
+    // two-step launch reads halo nodes that other CTAs rewrite).
+    float *sprev = nullptr, *sprev2 = nullptr, *mom = nullptr, *dense = nullptr, *host_stage = nullptr;
     float *mom_prev = nullptr;                        // snapshot for per-instance residuals
     double *partials = nullptr, *red = nullptr, *red_host = nullptr;  // per-instance reductions
     size_t stage_floats = 0;
@@ -169,8 +172,9 @@ struct cdf_batch {
     // instance (each launch reads its parameters as kernel operands), fanned out
     // over a pool of streams and captured as one CUDA graph; instances are
     // independent, so the chains need no barrier between them.
-    int mode = 0;  // 0: persistent kernel, 1: graph of per-instance chains
+    int mode = 0;  // 0: persistent kernel, 1: graph of per-instance chains, 2: chains of two-step launches
     dim3 chain_block{128, 1, 1};
+    int chain_th = 14;  // mode 2: output tile height of step2_kernel (chain_block is its CTA)
     std::vector<cudaStream_t> pool;
     cudaEvent_t ev_fork = nullptr;
     std::vector<cudaEvent_t> ev_join;
@@ -190,6 +194,7 @@ void brelease(cdf_batch *b) {
     cudaFree(b->buf[0]);
     cudaFree(b->buf[1]);
     cudaFree(b->sprev);
+    cudaFree(b->sprev2);
     cudaFree(b->mom);
     cudaFree(b->mom_prev);
     cudaFree(b->partials);
@@ -269,18 +274,32 @@ cdf_status launch_batch(cdf_batch *b, int nsteps, bool moments_last) {
 constexpr int kPoolStreams = 32;
 constexpr int kChainGraphSteps = 32;  // even: the buffer parity returns
 
+// S_1(t - 1) plane set that belongs to population buffer `par`.
+float *sprev_of(cdf_batch *b, int par) { return (b->mode == 0 || par == 0) ? b->sprev : b->sprev2; }
+
+// Kernel launches of the chains for n steps: one per step, or in mode 2 one per
+// two steps plus one single step for an odd n.  Each launch flips the parity.
+int chain_launches(const cdf_batch *b, int nsteps) { return b->mode == 2 ? nsteps / 2 + nsteps % 2 : nsteps; }
+
 // Enqueue n steps of every instance as chains of single-lattice step kernels on
 // the stream pool (fork from and join back to the batch stream).
 cdf_status enqueue_chains(cdf_batch *b, int nsteps, bool moments_last, int parity0) {
     BCK(cudaEventRecord(b->ev_fork, b->s));
     for (cudaStream_t ps : b->pool) BCK(cudaStreamWaitEvent(ps, b->ev_fork, 0));
-    for (int st = 0; st < nsteps; ++st) {
-        const int par = (parity0 + st) & 1;
+    const int launches = chain_launches(b, nsteps);
+    for (int j = 0; j < launches; ++j) {
+        const int par = (parity0 + j) & 1;
+        const bool two = b->mode == 2 && 2 * (j + 1) <= nsteps;
         for (int k = 0; k < b->count; ++k) {
-            float *mom = (moments_last && st == nsteps - 1) ? b->mom + b->mom_off[k] : nullptr;
-            BCK(launch_step(b->params[k], kFP32, b->buf[par] + b->pop_off[k], b->buf[par ^ 1] + b->pop_off[k],
-                            b->sprev + b->sp_off[k], b->sprev + b->sp_off[k], mom, b->chain_block,
-                            b->pool[k % b->pool.size()]));
+            float *mom = (moments_last && j == launches - 1) ? b->mom + b->mom_off[k] : nullptr;
+            float *in = b->buf[par] + b->pop_off[k], *out = b->buf[par ^ 1] + b->pop_off[k];
+            float *sin = sprev_of(b, par) + b->sp_off[k], *sout = sprev_of(b, par ^ 1) + b->sp_off[k];
+            cudaStream_t ps = b->pool[k % b->pool.size()];
+            if (two)
+                BCK(launch_step2(b->params[k], in, out, sin, sout, mom, b->chain_block, b->chain_th, ps));
+            else
+                BCK(launch_step(b->params[k], kFP32, in, out, sin, sout, mom,
+                                b->mode == 2 ? dim3(128, 1) : b->chain_block, ps));
         }
     }
     for (size_t j = 0; j < b->pool.size(); ++j) {
@@ -323,9 +342,18 @@ cdf_status run_chains(cdf_batch *b, int nsteps, bool moments_last) {
         cdf_status st = enqueue_chains(b, nsteps, moments_last, b->cur);
         if (st != CDF_OK) return st;
     }
-    if (nsteps & 1) b->cur ^= 1;
+    if (chain_launches(b, nsteps) & 1) b->cur ^= 1;
     b->t += nsteps;
     return CDF_OK;
+}
+
+// Can step2_kernel with CTA blk and tile height th run every instance?
+bool chain_pair_fits(const cdf_batch *b, dim3 blk, int th) {
+    if (blk.x % 32 != 0 || (int)(blk.x * blk.y) > step2_max_threads(b->m) || th < 1) return false;
+    if (step2_smem_bytes(b->m, blk, th) > (size_t)kStep2MaxSmem) return false;
+    for (const LbParams &p : b->params)
+        if ((p.periodic_x && p.nx < (int)blk.x) || (p.periodic_y && p.ny < th + 2)) return false;
+    return true;
 }
 
 cdf_status check_err(cdf_batch *b) {
@@ -341,10 +369,13 @@ cdf_status bautotune(cdf_batch *b) {
     {
         std::lock_guard<std::mutex> lk(g_btune_mu);
         auto it = g_bmode.find(key);
-        if (it != g_bmode.end()) {
+        if (it != g_bmode.end() && (it->second.first != 2 || chain_pair_fits(b, dim3(it->second.second.x,
+                                                                                         it->second.second.y),
+                                                                              (int)it->second.second.z))) {
             b->mode = it->second.first;
-            if (b->mode == 1) {
-                set_chain_block(b, it->second.second);
+            if (b->mode >= 1) {
+                set_chain_block(b, dim3(it->second.second.x, it->second.second.y));
+                b->chain_th = (int)it->second.second.z;
                 return setup_tiles(b, dim3(64, 4));
             }
             return setup_tiles(b, it->second.second);
@@ -378,11 +409,23 @@ cdf_status bautotune(cdf_batch *b) {
     }
     const dim3 blocks[] = {dim3(128, 1), dim3(128, 2), dim3(256, 1), dim3(64, 4), dim3(32, 8), dim3(128, 0),
                            dim3(256, 0)};  // y == 0: flat launch
+    b->mode = 1;
     for (const dim3 &c : blocks) {
         set_chain_block(b, c);
         float ms = time_it([&](int n) { return run_chains(b, n, false); }, kChainGraphSteps);
         if (ms < 0) return bfail(CDF_ECUDA, "autotuning the kernel chains failed");
         if (ms < best) { best = ms; choice = {1, c}; }
+    }
+    // chains of two-step launches: CTA shape (x, y) and tile height z
+    const dim3 pairs[] = {dim3(32, 8, 14), dim3(32, 8, 6), dim3(32, 16, 14), dim3(64, 8, 14), dim3(32, 16, 30)};
+    b->mode = 2;
+    for (const dim3 &c : pairs) {
+        if (!chain_pair_fits(b, dim3(c.x, c.y), (int)c.z)) continue;
+        set_chain_block(b, dim3(c.x, c.y));
+        b->chain_th = (int)c.z;
+        float ms = time_it([&](int n) { return run_chains(b, n, false); }, kChainGraphSteps);
+        if (ms < 0) return bfail(CDF_ECUDA, "autotuning the two-step kernel chains failed");
+        if (ms < best) { best = ms; choice = {2, c}; }
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
@@ -393,8 +436,9 @@ cdf_status bautotune(cdf_batch *b) {
         g_bmode[key] = choice;
     }
     b->mode = choice.first;
-    if (b->mode == 1) {
-        set_chain_block(b, choice.second);
+    if (b->mode >= 1) {
+        set_chain_block(b, dim3(choice.second.x, choice.second.y));
+        b->chain_th = (int)choice.second.z;
         return setup_tiles(b, dim3(64, 4));
     }
     return setup_tiles(b, choice.second);
@@ -414,7 +458,8 @@ cdf_status cdf_batch_create(int count, const cdf_grid *grids, int m, const cdf_d
         return bfail(CDF_EINVAL, "NULL argument or count < 1");
     if (opt->storage != CDF_FP32) return bfail(CDF_EINVAL, "the batched solver stores FP32 populations only");
     if (!(opt->rho0 > 0.0)) return bfail(CDF_EINVAL, "rho0 must be positive");
-    if (opt->tile_x != 0 || opt->tile_y != 0) {
+    if (opt->mode < 0 || opt->mode > 2) return bfail(CDF_EINVAL, "mode must be 0, 1 or 2");
+    if ((opt->tile_x != 0 || opt->tile_y != 0) && opt->mode != 2) {
         if (opt->tile_x <= 0 || opt->tile_y <= 0 || opt->tile_x * opt->tile_y > 256 || opt->tile_x % 32 != 0)
             return bfail(CDF_EINVAL, "tile must be a multiple of 32 wide and at most 256 nodes");
     }
@@ -459,6 +504,7 @@ cdf_status cdf_batch_create(int count, const cdf_grid *grids, int m, const cdf_d
     bool ok = cudaMalloc(&b->buf[0], b->pop_total * 4) == cudaSuccess &&
               cudaMalloc(&b->buf[1], b->pop_total * 4) == cudaSuccess &&
               cudaMalloc(&b->sprev, b->sp_total * 4) == cudaSuccess &&
+              cudaMalloc(&b->sprev2, b->sp_total * 4) == cudaSuccess &&
               cudaMalloc(&b->mom, b->mom_total * 4) == cudaSuccess &&
               cudaMalloc(&b->mom_prev, b->mom_total * 4) == cudaSuccess &&
               cudaMalloc(&b->partials, (size_t)reduce_quantities(m) * kReduceBlocks * sizeof(double)) == cudaSuccess &&
@@ -479,7 +525,8 @@ cdf_status cdf_batch_create(int count, const cdf_grid *grids, int m, const cdf_d
         cudaEventCreateWithFlags(&b->ev_in, cudaEventDisableTiming) != cudaSuccess ||
         cudaEventCreateWithFlags(&b->ev_out, cudaEventDisableTiming) != cudaSuccess ||
         cudaMemset(b->buf[0], 0, b->pop_total * 4) != cudaSuccess || cudaMemset(b->buf[1], 0, b->pop_total * 4) != cudaSuccess ||
-        cudaMemset(b->sprev, 0, b->sp_total * 4) != cudaSuccess || cudaMemset(b->mom, 0, b->mom_total * 4) != cudaSuccess ||
+        cudaMemset(b->sprev, 0, b->sp_total * 4) != cudaSuccess || cudaMemset(b->sprev2, 0, b->sp_total * 4) != cudaSuccess ||
+        cudaMemset(b->mom, 0, b->mom_total * 4) != cudaSuccess ||
         cudaMemset(b->d_bar, 0, 2 * sizeof(unsigned)) != cudaSuccess) {
         brelease(b);
         return bfail(CDF_ECUDA, "stream / memory set-up failed");
@@ -495,9 +542,16 @@ cdf_status cdf_batch_create(int count, const cdf_grid *grids, int m, const cdf_d
         return bfail(CDF_ECUDA, "stream pool set-up failed");
     }
     b->mode = opt->mode;
-    if (opt->mode == 1 && opt->tile_x > 0) set_chain_block(b, dim3(opt->tile_x, opt->tile_y));
+    if (opt->mode >= 1 && opt->tile_x > 0) set_chain_block(b, dim3(opt->tile_x, opt->tile_y));
+    if (opt->mode == 2 && opt->tile_x > 0) {
+        b->chain_th = opt->chain_tile_y > 0 ? opt->chain_tile_y : 14;
+        if (!chain_pair_fits(b, b->chain_block, b->chain_th)) {
+            brelease(b);
+            return bfail(CDF_EINVAL, "the two-step kernel shape cannot run every instance");
+        }
+    }
     cdf_status st;
-    if (opt->mode == 1 && opt->tile_x > 0) st = setup_tiles(b, dim3(64, 4));
+    if (opt->mode >= 1 && opt->tile_x > 0) st = setup_tiles(b, dim3(64, 4));
     else if (opt->tile_x > 0) st = setup_tiles(b, dim3(opt->tile_x, opt->tile_y));
     else if (b->extra_arrivals) st = setup_tiles(b, dim3(64, 4));
     else st = bautotune(b);
@@ -529,7 +583,7 @@ cdf_status cdf_batch_init_moments(cdf_batch *b, int k, const double *phi, const 
     BCK(cudaEventRecord(b->ev_in, b->user));
     BCK(cudaStreamWaitEvent(b->s, b->ev_in, 0));
     BCK(cudaMemcpyAsync(b->dense, h, (size_t)(b->m + 3) * n * 4, cudaMemcpyHostToDevice, b->s));
-    BCK(launch_init(P, kFP32, b->dense, P.nx, b->buf[b->cur] + b->pop_off[k], b->sprev + b->sp_off[k],
+    BCK(launch_init(P, kFP32, b->dense, P.nx, b->buf[b->cur] + b->pop_off[k], sprev_of(b, b->cur) + b->sp_off[k],
                     b->mom + b->mom_off[k], b->s));
     BCK(cudaEventRecord(b->ev_out, b->s));
     BCK(cudaStreamWaitEvent(b->user, b->ev_out, 0));
@@ -542,8 +596,8 @@ cdf_status cdf_batch_step(cdf_batch *b, long long n) {
     BCK(cudaEventRecord(b->ev_in, b->user));
     BCK(cudaStreamWaitEvent(b->s, b->ev_in, 0));
     while (n > 0) {
-        const int k = (int)std::min<long long>(n, b->mode == 1 ? kChainGraphSteps : b->steps_per_launch);
-        cdf_status st = b->mode == 1 ? run_chains(b, k, n == k) : launch_batch(b, k, n == k);
+        const int k = (int)std::min<long long>(n, b->mode >= 1 ? kChainGraphSteps : b->steps_per_launch);
+        cdf_status st = b->mode >= 1 ? run_chains(b, k, n == k) : launch_batch(b, k, n == k);
         if (st != CDF_OK) return st;
         n -= k;
     }
@@ -582,6 +636,7 @@ cdf_status cdf_batch_get_info(const cdf_batch *b, cdf_batch_info *out) {
     out->mode = b->mode;
     out->chain_block_x = (int)b->chain_block.x;
     out->chain_block_y = (int)b->chain_block.y;
+    out->chain_tile_y = b->mode == 2 ? b->chain_th : 0;
     out->t = b->t;
     return CDF_OK;
 }

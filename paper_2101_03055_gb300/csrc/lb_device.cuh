@@ -30,6 +30,7 @@ constexpr float kA1 = 0x1.555554p-2f;
 constexpr float kA5 = 0x1.555558p-4f;
 constexpr float kC = 0x1.aaaaaap+0f;
 constexpr float kQ = 0x1.555556p-1f;
+constexpr float kInvC = 0x1.333334p-1f;  // fl(1 / kC): Eq. sum-p by one multiply
 __host__ __device__ constexpr float kWs(int i) { return i == 0 ? kW50 : kW5; }
 __host__ __device__ constexpr float kA9(int i) { return i == 0 ? 0.f : (i < 5 ? kA1 : kA5); }
 __host__ __device__ constexpr int kC5x(int i) { return i == 1 ? 1 : (i == 3 ? -1 : 0); }
@@ -187,7 +188,12 @@ __device__ __forceinline__ void relaxation_matrix(const LbParams &p, const Scala
         for (int b = 0; b < M; ++b) om[a][b] = p.omega[a * M + b];
     if (M >= 2 && p.chemotaxis) {
         const float delta = -p.chi3 * s.phi[0] * s.r;
-        const float den = 1.f / fmaf(delta, om[M >= 2 ? 1 : 0][0], 1.f);
+        // 1 / (1 + delta omega_10); omega_10 = 0 (a diagonal constant part, as in
+        // the benchmark closures) makes it exactly 1, so the quotient is skipped
+        // by a branch that is uniform over the launch
+        const float o10 = om[M >= 2 ? 1 : 0][0];
+        float den = 1.f;
+        if (o10 != 0.f) den = 1.f / fmaf(delta, o10, 1.f);
         float col0[M], row1[M];
 #pragma unroll
         for (int a = 0; a < M; ++a) { col0[a] = om[a][0]; row1[a] = om[M >= 2 ? 1 : 0][a]; }
@@ -238,13 +244,14 @@ __device__ __forceinline__ void collide(const LbParams &p, float (&f)[M][5], flo
     const float Fx = p.g[0] * fm, Fy = p.g[1] * fm;
 
     // Eq. sum-u and Eq. sum-p (varphi = 0):
-    // p = cs^2/(1 - W0) [sum_{i!=0} h_i - W0 u.u / (2 cs^2)] = (sum_{i!=0} h_i - kQ u.u) / kC
+    // p = cs^2/(1 - W0) [sum_{i!=0} h_i - W0 u.u / (2 cs^2)] = (sum_{i!=0} h_i - kQ u.u) / kC,
+    // taken as a product with fl(1 / kC) (one rounding more than the quotient)
     const float jx = (h[1] - h[3]) + (h[5] - h[6]) + (h[8] - h[7]);
     const float jy = (h[2] - h[4]) + (h[5] - h[8]) + (h[6] - h[7]);
     const float ux = fmaf(0.5f, Fx, jx), uy = fmaf(0.5f, Fy, jy);
     const float usq = usq_of(ux, uy);
     const float snr = ((h[1] + h[2]) + (h[3] + h[4])) + ((h[5] + h[6]) + (h[7] + h[8]));
-    const float prd = fmaf(-kQ, usq, snr) / kC;
+    const float prd = __fmul_rn(fmaf(-kQ, usq, snr), kInvC);
 
     float om[M][M];
     relaxation_matrix<M>(p, s, om);

@@ -81,7 +81,7 @@ class cdf_batch_options(ctypes.Structure):
     _fields_ = [("storage", ctypes.c_int), ("rho0", ctypes.c_double), ("cuda_stream", ctypes.c_void_p),
                 ("tile_x", ctypes.c_int), ("tile_y", ctypes.c_int), ("steps_per_launch", ctypes.c_int),
                 ("barrier_timeout_s", ctypes.c_double), ("test_unreachable_barrier", ctypes.c_int),
-                ("mode", ctypes.c_int)]
+                ("mode", ctypes.c_int), ("chain_tile_y", ctypes.c_int)]
 
 
 class cdf_batch_info(ctypes.Structure):
@@ -89,7 +89,7 @@ class cdf_batch_info(ctypes.Structure):
                 ("tiles", ctypes.c_longlong), ("tile_x", ctypes.c_int), ("tile_y", ctypes.c_int),
                 ("grid_blocks", ctypes.c_int), ("steps_per_launch", ctypes.c_int),
                 ("bytes_per_lup", ctypes.c_double), ("t", ctypes.c_longlong), ("mode", ctypes.c_int),
-                ("chain_block_x", ctypes.c_int), ("chain_block_y", ctypes.c_int)]
+                ("chain_block_x", ctypes.c_int), ("chain_block_y", ctypes.c_int), ("chain_tile_y", ctypes.c_int)]
 
 
 _DP = ctypes.POINTER(ctypes.c_double)
@@ -487,7 +487,7 @@ class BatchSolver:
     """Many lattices (same m and source kind, FP32) advanced by the persistent batched kernel."""
 
     def __init__(self, problems, stream: int = 0, tile=None, steps_per_launch: int = 0, barrier_timeout_s: float = 0.0,
-                 test_unreachable_barrier: bool = False, init: bool = True, mode: int = 0):
+                 test_unreachable_barrier: bool = False, init: bool = True, mode: int = 0, chain_tile_y: int = 0):
         self.problems = list(problems)
         n = len(self.problems)
         m = self.problems[0].m
@@ -515,6 +515,7 @@ class BatchSolver:
         opt.barrier_timeout_s = barrier_timeout_s
         opt.test_unreachable_barrier = int(test_unreachable_barrier)
         opt.mode = mode
+        opt.chain_tile_y = chain_tile_y
         self.h = cdf_batch_create(n, grids, m, dif, nu, src, frc, bcs, phi_ref, grad, opt)
         self.m = m
         if init:

@@ -13,16 +13,23 @@ def small_sweep(count=5, seed=3):
     return I.chemotaxis_plume_sweep(count, seed=seed, wmin=16, wmax=140, hmin=9, hmax=70)
 
 
-@pytest.mark.parametrize("tile,spl,mode", [((64, 4), 32, 0), ((32, 8), 7, 0), ((128, 1), 1, 0),
-                                           ((128, 1), 0, 1), ((64, 4), 0, 1)])
-def test_batch_equals_single_lattice_solver(cdf, tile, spl, mode):
+@pytest.mark.parametrize("tile,spl,mode,th", [((64, 4), 32, 0, 0), ((32, 8), 7, 0, 0), ((128, 1), 1, 0, 0),
+                                              ((128, 1), 0, 1, 0), ((64, 4), 0, 1, 0), ((32, 8), 0, 2, 14),
+                                              ((32, 4), 0, 2, 6), ((64, 8), 0, 2, 30)])
+def test_batch_equals_single_lattice_solver(cdf, tile, spl, mode, th):
     """Each instance of the batch follows exactly the single-lattice solver: the
     same per-node update, bit for bit, across launches, grid barriers (persistent
-    mode) and graph-captured kernel chains (chain mode)."""
+    mode), graph-captured kernel chains (chain mode) and chains of two-step
+    launches with an odd remainder (mode 2; 70 = two graphs of 32 steps + 6,
+    then 3 more steps)."""
     pbs = small_sweep()
-    b = cdf.BatchSolver(pbs, tile=tile, steps_per_launch=spl, mode=mode)
-    assert b.info().mode == mode
-    b.step(70)
+    b = cdf.BatchSolver(pbs, tile=tile, steps_per_launch=spl, mode=mode, chain_tile_y=th)
+    info = b.info()
+    assert info.mode == mode
+    if mode == 2:
+        assert (info.chain_block_x, info.chain_block_y, info.chain_tile_y) == (tile[0], tile[1], th)
+    b.step(67)
+    b.step(3)
     assert b.info().t == 70
     for k, pb in enumerate(pbs):
         s = cdf.Solver(pb)
