@@ -244,14 +244,18 @@ __device__ __forceinline__ void store3(const Lb3Params &p, float *out, float *sp
     }
 }
 
-// One node of the 3-D step.  kInterior: the caller guarantees that the node is
-// at least one node away from every face (no link crosses a wall or wraps);
-// every source is then x - c_i and the wall selects fold away.  Both forms give
-// the same bits for such a node.
-template <int M, bool kInterior>
-__device__ __forceinline__ void step3d_node(const Lb3Params &p, int x, int y, int z, const float *__restrict__ in,
-                                            float *__restrict__ out, float *__restrict__ sprev,
-                                            float *__restrict__ moments) {
+template <int M>
+__global__ void __launch_bounds__(256) step3d_kernel(const Lb3Params p, const float *__restrict__ in,
+                                                     float *__restrict__ out, float *__restrict__ sprev,
+                                                     float *__restrict__ moments) {
+    // programmatic dependent launch: wait for the previous step's results, then
+    // let the next step's CTAs be scheduled (hides the launch gap)
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int y = blockIdx.y * blockDim.y + threadIdx.y;
+    const int z = blockIdx.z;
+    if (x >= p.nx || y >= p.ny) return;
     const long long P = p.plane;
     // neighbour coordinates (periodic wrap) and wall crossings of the pull links
     const int X[3] = {x, y, z}, N[3] = {p.nx, p.ny, p.nz};
@@ -261,12 +265,10 @@ __device__ __forceinline__ void step3d_node(const Lb3Params &p, int x, int y, in
     for (int d = 0; d < 3; ++d) {
         lo[d] = X[d] - 1;
         hi[d] = X[d] + 1;
-        clo[d] = !kInterior && lo[d] < 0 && !p.periodic[d];
-        chi[d] = !kInterior && hi[d] >= N[d] && !p.periodic[d];
-        if (!kInterior) {
-            lo[d] = lo[d] < 0 ? N[d] - 1 : lo[d];
-            hi[d] = hi[d] >= N[d] ? 0 : hi[d];
-        }
+        clo[d] = lo[d] < 0 && !p.periodic[d];
+        chi[d] = hi[d] >= N[d] && !p.periodic[d];
+        lo[d] = lo[d] < 0 ? N[d] - 1 : lo[d];
+        hi[d] = hi[d] >= N[d] ? 0 : hi[d];
     }
     // in-plane offsets fit in int: the host keeps pitch * ny * nz < 2^31
     const auto off = [&](int sx, int sy, int sz) { return (sz * p.ny + sy) * p.pitch + sx; };
@@ -332,26 +334,6 @@ __device__ __forceinline__ void step3d_node(const Lb3Params &p, int x, int y, in
     Out3<M> o;
     collide3<M>(p, f, h, pref_at(p, x, y, z), sp1, false, o);
     store3<M>(p, out, sprev, moments, o0, f, h, o);
-}
-
-template <int M>
-__global__ void __launch_bounds__(256) step3d_kernel(const Lb3Params p, const float *__restrict__ in,
-                                                     float *__restrict__ out, float *__restrict__ sprev,
-                                                     float *__restrict__ moments) {
-    // programmatic dependent launch: wait for the previous step's results, then
-    // let the next step's CTAs be scheduled (hides the launch gap)
-    asm volatile("griddepcontrol.wait;" ::: "memory");
-    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
-    const int x = blockIdx.x * blockDim.x + threadIdx.x;
-    const int y = blockIdx.y * blockDim.y + threadIdx.y;
-    const int z = blockIdx.z;
-    // warp-uniform choice (CTAs hold whole warps): a warp whose nodes all lie
-    // inside the boundary shell pulls without the wall selects
-    const bool inner = x >= 1 && x + 1 < p.nx && y >= 1 && y + 1 < p.ny && z >= 1 && z + 1 < p.nz;
-    if (__all_sync(0xffffffffu, inner))
-        step3d_node<M, true>(p, x, y, z, in, out, sprev, moments);
-    else if (x < p.nx && y < p.ny)
-        step3d_node<M, false>(p, x, y, z, in, out, sprev, moments);
 }
 
 // t = 0: f = f^eq(phi0, u0), h = h^eq(u0, p0) - F_i/2, collided once (S(t-1) = S).

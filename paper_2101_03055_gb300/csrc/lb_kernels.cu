@@ -194,13 +194,8 @@ __global__ void __launch_bounds__(256) step_kernel_case1(const LbParams p, const
     const auto ld = [in, P](int plane, int off) { return __ldg(in + plane * P + off); };
     const int o0 = y * pitch + x;
     float f[M][5];
-    // warp-uniform interior path, as in step_kernel
-    if (__all_sync(0xffffffffu, inner_node(p, x, y))) {
-        pull_scalars<M, true>(p, x, y, mk, ld, f);
-    } else {
-        if (x >= p.nx || y >= p.ny) return;
-        pull_scalars<M, false>(p, x, y, mk, ld, f);
-    }
+    if (x >= p.nx || y >= p.ny) return;
+    pull_scalars<M, false>(p, x, y, mk, ld, f);
     float *vel = p.vel;
     const float ux = __ldg(vel + o0), uy = __ldg(vel + P + o0);
     float php[M];

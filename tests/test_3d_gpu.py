@@ -166,11 +166,10 @@ def test_ddc_slab_reproduces_the_paper_table(cdf):
     assert abs(Nu - Nu_e) / Nu < 1e-2 and abs(Sh - Sh_e) / Sh < 1e-2
 
 
-def test_interior_and_edge_paths_agree_bitwise(cdf):
-    """Warps whose nodes all lie inside the boundary shell pull without the wall
-    selects, the others take the general pull.  A periodic update commutes with
-    translations, so a state rolled by (16, 3, 2) nodes, stepped and rolled back
-    equals the unrolled run bit for bit only if both pulls give the same bits."""
+def test_translation_invariance_bitwise(cdf):
+    """A periodic update commutes with translations: a state rolled by (16, 3, 2)
+    nodes, stepped and rolled back equals the unrolled run bit for bit, so no
+    node's arithmetic depends on where it sits in its CTA or warp."""
     pb = I.periodic_box3d(64, 20, 12, u0=0.03, seed=5)
     a = cdf.Solver3D(pb, block=(32, 4))
     a.step(40)

@@ -109,10 +109,10 @@ def test_case1_refusals(cdf):
         cdf.Solver(pb, resident=1)
 
 
-def test_interior_and_edge_paths_agree_bitwise(cdf):
-    """The warp-uniform interior pull gives the same bits as the general pull:
-    a periodic Case-1 state (scalars and the prescribed velocity) rolled by
-    (16, 3) nodes, stepped and rolled back equals the unrolled run."""
+def test_translation_invariance_bitwise(cdf):
+    """A periodic Case-1 state (scalars and the prescribed velocity) rolled by
+    (16, 3) nodes, stepped and rolled back equals the unrolled run bit for bit:
+    no node's arithmetic depends on where it sits in its CTA or warp."""
     pb = I.cde_cellular(96, 40, walls=False, U0=0.08)
     a = cdf.Solver(pb, block=(32, 4))
     a.step(60)
