@@ -4,8 +4,9 @@ Workload (default): the chemotaxis-plume configuration, 512 x 256 lattice,
 m = 2 (bacteria n, oxygen c), FP32 populations, no-slip side and bottom walls,
 free-slip top with c = 1, chemotactic cross term D_01 = -chi n r(c) with the
 step cut-off, consumption S_c = -k n r(c), buoyancy -g n, n0 = 1 + 0.01 N(0, 1).
-One benchmark step = `--lb-steps` lattice time steps (2000 by default) of the
-whole hot path; L2 is flushed (a 256 MiB write) between benchmark steps.
+One benchmark step = `--lb-steps` lattice time steps (by default about 0.1 s
+of work: 20000 for this lattice) of the whole hot path; L2 is flushed (a
+256 MiB write) between benchmark steps.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--workload NAME]
 
@@ -200,8 +201,12 @@ class _Single:
             self.kernel = (f"resident_kernel<{pb.m}> (tile-resident persistent step, {info.tiles} CTAs of "
                            f"{info.tile_x}x{info.tile_y} nodes)")
         else:
-            self.kernel = (f"step_kernel<{pb.m},float>" if info.storage == 0 else
-                           f"step_kernel_mr<{pb.m},{ {1: '__half', 2: '__nv_bfloat16'}[info.storage]}>")
+            if info.storage != 0:
+                self.kernel = f"step_kernel_mr<{pb.m},{ {1: '__half', 2: '__nv_bfloat16'}[info.storage]}>"
+            elif info.block_y == 0:
+                self.kernel = f"step_kernel_flat<{pb.m},float> (flat launch, {info.block_x} threads per CTA)"
+            else:
+                self.kernel = f"step_kernel<{pb.m},float>"
         if getattr(pb, "case1", False):
             self.kernel = f"step_kernel_case1<{pb.m}> (prescribed velocity, no fluid)"
 
@@ -454,7 +459,9 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="chemotaxis_plume_512x256")
-    ap.add_argument("--lb-steps", type=int, default=2000, help="lattice time steps per benchmark step")
+    ap.add_argument("--lb-steps", type=int, default=None,
+                    help="lattice time steps per benchmark step (default: about 0.1 s of work, a multiple "
+                         "of 32, at most 20000)")
     ap.add_argument("--storage", default="fp32", choices=["fp32", "fp16", "bf16"])
     ap.add_argument("--resident", type=int, default=0, choices=[-1, 0, 1],
                     help="tile-resident step: 0 = the autotuner decides, 1 = always, -1 = never")
@@ -490,7 +497,10 @@ def main():
         block = tuple(int(v) for v in args.block.split(",")) if args.block else None
         runner = _Single(lib, wl, args.storage, args.resident, block, args.temporal)
     nodes = runner.nodes
-    K, W, S = args.steps, args.warmup, args.lb_steps
+    S = args.lb_steps
+    if S is None:  # about 0.1 s of lattice updates at ~30 GLUPS per benchmark step
+        S = int(min(20000, max(32, 3e9 / nodes)) // 32 * 32)
+    K, W = args.steps, args.warmup
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=device)
     lib_stream = torch.cuda.ExternalStream(runner.stream, device=device)
 

@@ -445,15 +445,24 @@ cdf_status setup_pair(cdf_lb *h, const cdf_options *opt) {
     // candidates: R1 rows of 32 or 64 nodes, tile heights that give one or two
     // passes of the CTA's thread rows
     std::vector<std::pair<dim3, int>> cands;
-    for (unsigned w : {32u, 64u})
-        for (int th : {6, 14, 30, 32, 46, 62})
-            for (unsigned by : {(unsigned)(th + 2), (unsigned)((th + 3) / 2), 8u, 16u}) {
-                const dim3 b(w, by, 1);
-                if (!pair_fits(h, b, th)) continue;
-                bool dup = false;
-                for (auto &c : cands) dup = dup || (c.first.x == b.x && c.first.y == b.y && c.second == th);
-                if (!dup) cands.push_back({b, th});
-            }
+    const long long nodes = (long long)h->nx * h->ny;
+    if (nodes >= (1ll << 24)) {
+        // a large lattice: a launch takes milliseconds, so time only the shapes that
+        // measured best on large boxes (many small CTAs, or 512-thread CTAs)
+        for (auto c : {std::make_pair(dim3(32, 8, 1), 14), std::make_pair(dim3(32, 16, 1), 30),
+                       std::make_pair(dim3(64, 8, 1), 14)})
+            if (pair_fits(h, c.first, c.second)) cands.push_back(c);
+    } else {
+        for (unsigned w : {32u, 64u})
+            for (int th : {6, 14, 30, 32, 46, 62})
+                for (unsigned by : {(unsigned)(th + 2), (unsigned)((th + 3) / 2), 8u, 16u}) {
+                    const dim3 b(w, by, 1);
+                    if (!pair_fits(h, b, th)) continue;
+                    bool dup = false;
+                    for (auto &c : cands) dup = dup || (c.first.x == b.x && c.first.y == b.y && c.second == th);
+                    if (!dup) cands.push_back({b, th});
+                }
+    }
     if (cands.empty()) {
         if (opt->temporal == 1) return fail(CDF_EINVAL, "the lattice is too small for two steps per launch");
         return CDF_OK;
@@ -461,7 +470,6 @@ cdf_status setup_pair(cdf_lb *h, const cdf_options *opt) {
     cudaEvent_t a, b;
     CK(cudaEventCreate(&a));
     CK(cudaEventCreate(&b));
-    const long long nodes = (long long)h->nx * h->ny;
     const int reps = nodes >= (1 << 22) ? 4 : 16;
     auto timed = [&](auto &&launch, float *ms) -> cdf_status {
         for (int w = 0; w < 2; ++w) CK(launch(w & 1));
