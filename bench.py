@@ -194,7 +194,9 @@ class _Single:
         self.resident = bool(info.resident)
         self.pair = bool(info.temporal) and not self.resident
         if self.pair:
-            self.kernel = (f"step2_kernel<{pb.m}> (two time steps per launch, CTAs of {info.block_x}x{info.block_y} "
+            kname = (f"step2_kernel<{pb.m}>" if info.storage == 0 else
+                     f"step2_kernel_mr<{pb.m},{ {1: '__half', 2: '__nv_bfloat16'}[info.storage]}>")
+            self.kernel = (f"{kname} (two time steps per launch, CTAs of {info.block_x}x{info.block_y} "
                            f"threads, output tiles {info.tile_x}x{info.tile_y})")
         elif self.resident:
             self.block = [info.tile_x, info.tile_y]

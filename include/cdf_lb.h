@@ -141,10 +141,15 @@ typedef struct {
     int temporal;                      /* two time steps per launch (temporal blocking: each CTA
                                           updates its tile and a one-node halo into shared memory,
                                           then the tile again from there; one pass over global
-                                          memory serves two steps), FP32 storage, full model:
+                                          memory serves two steps), full model (not Case 1):
                                           0 = used when the autotuner measures it faster,
                                           1 = always, -1 = never; a fixed block_x with
-                                          temporal = 0 keeps one step per launch */
+                                          temporal = 0 keeps one step per launch.  FP32: bitwise
+                                          the same as one step per launch.  16-bit storage: the
+                                          intermediate step stays in FP32 in shared memory, so
+                                          the populations are rounded to 16 bits once per two
+                                          steps (results differ from one step per launch by that
+                                          saved rounding) */
     int temporal_block_x, temporal_block_y, temporal_tile_y;
                                        /* with temporal = 1: the two-step kernel's CTA shape
                                           (block_x 32 or 64: the halo region is block_x nodes wide,

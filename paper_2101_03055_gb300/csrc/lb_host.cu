@@ -200,8 +200,12 @@ cudaError_t launch_any(cdf_lb *h, int src, bool with_moments) {
                        with_moments ? h->mom : nullptr, h->block, h->s);
 }
 
-// Two steps from buf[src] to buf[src ^ 1] in one launch (FP32 storage).
+// Two steps from buf[src] to buf[src ^ 1] in one launch (16-bit storage keeps
+// its moments beside the populations, so they are written every launch).
 cudaError_t launch_two(cdf_lb *h, int src, bool with_moments) {
+    if (h->mr)
+        return launch_step2_mr(h->P, h->storage, h->buf[src], h->mom_pp[src], h->buf[src ^ 1], h->mom_pp[src ^ 1],
+                               h->sprev_pp[src], h->sprev_pp[src ^ 1], h->pair_block, h->pair_th, h->s);
     return launch_step2(h->P, static_cast<const float *>(h->buf[src]), static_cast<float *>(h->buf[src ^ 1]),
                         h->sprev_pp[src], h->sprev_pp[src ^ 1], with_moments ? h->mom : nullptr, h->pair_block,
                         h->pair_th, h->s);
@@ -397,7 +401,8 @@ void drop_graphs(cdf_lb *h) {
 
 // Can step2_kernel run this lattice with CTA shape b and tile height th?
 bool pair_fits(const cdf_lb *h, dim3 b, int th) {
-    if (b.x % 32 != 0 || b.x < 32 || (int)(b.x * b.y) > step2_max_threads(h->m) || th < 1) return false;
+    const int max_threads = h->mr ? step2_mr_max_threads(h->m) : step2_max_threads(h->m);
+    if (b.x % 32 != 0 || b.x < 32 || (int)(b.x * b.y) > max_threads || th < 1) return false;
     if (step2_smem_bytes(h->m, b, th) > (size_t)kStep2MaxSmem) return false;
     if (h->P.periodic_x && h->nx < (int)b.x) return false;
     if (h->P.periodic_y && h->ny < th + 2) return false;
@@ -419,7 +424,7 @@ std::map<PairKey, PairChoice> g_pair_cache;
 cdf_status setup_pair(cdf_lb *h, const cdf_options *opt) {
     // a fixed CTA shape of the step kernel fixes the one-step launch unless two
     // steps per launch are asked for explicitly
-    if (h->mr || h->P.case1 || opt->temporal == -1 || opt->resident == 1 || (opt->block_x > 0 && opt->temporal == 0))
+    if (h->P.case1 || opt->temporal == -1 || opt->resident == 1 || (opt->block_x > 0 && opt->temporal == 0))
         return CDF_OK;
     if (opt->temporal_block_x > 0) {  // a given shape
         const dim3 b(opt->temporal_block_x, opt->temporal_block_y, 1);
@@ -431,7 +436,7 @@ cdf_status setup_pair(cdf_lb *h, const cdf_options *opt) {
         h->pair_th = opt->temporal_tile_y;
         return CDF_OK;
     }
-    PairKey key{h->nx, h->ny, h->m, h->P.chemotaxis, h->P.periodic_x, h->P.periodic_y};
+    PairKey key{h->nx, h->ny, h->m * 4 + h->storage, h->P.chemotaxis, h->P.periodic_x, h->P.periodic_y};
     {
         std::lock_guard<std::mutex> lk(g_tune_mu);
         auto it = g_pair_cache.find(key);
@@ -716,9 +721,8 @@ cdf_status cdf_lb_create(const cdf_grid *grid, int m, const cdf_diffusion *dif, 
             opt->temporal_tile_y < 1)
             return fail(CDF_EINVAL, "two-step kernel shape: block_x 32 or 64, block_y >= 1, tile_y >= 1");
     }
-    if (opt->temporal == 1 && (opt->storage != CDF_FP32 || opt->prescribed_velocity || opt->resident == 1))
-        return fail(CDF_EINVAL, "two steps per launch exist for FP32 storage of the full model, without the "
-                                "resident step");
+    if (opt->temporal == 1 && (opt->prescribed_velocity || opt->resident == 1))
+        return fail(CDF_EINVAL, "two steps per launch exist for the full model, without the resident step");
     LbParams P0{};
     const int align = opt->storage == CDF_FP32 ? 32 : 64;  // 128-byte rows
     const int pitch = grid->nx >= 1 ? (grid->nx + align - 1) / align * align : 0;

@@ -350,24 +350,25 @@ __device__ __forceinline__ float heq_dir(int j, float pr, float ux, float uy) {
 // out of the reference costs no precision and saves its evaluation at both ends.
 __device__ __forceinline__ float href_dir(int j, float pr, float ux, float uy) { return heq_dir(j, pr, ux, uy); }
 
-// One node of the 16-bit step.  kInterior as in step_node: with no link
-// crossing a wall the source directions are compile-time constants, so the
-// rebuilt equilibria need no run-time direction selects.
+// Pre-collision populations of node (x, y) for 16-bit storage: the stored
+// deviations of the pull sources plus the equilibria of those sources' stored
+// moments (full values: the host sets phi_ref = 0 and p_ref = 0 for this
+// storage).  kInterior as in step_node: with no link crossing a wall the source
+// directions are compile-time constants, so the rebuilt equilibria need no
+// run-time direction selects.
 template <int M, typename T, bool kInterior>
-__device__ __forceinline__ void step_node_mr(const LbParams &p, int x, int y, const T *__restrict__ in,
-                                             const float *__restrict__ min, T *__restrict__ out,
-                                             float *__restrict__ mout, const float *sp_in, float *sp_out) {
+__device__ __forceinline__ void pull_node_mr(const LbParams &p, int x, int y, const T *__restrict__ in,
+                                             const float *__restrict__ min, float (&f)[M][5], float (&h)[9]) {
     const long long P = p.plane;
     const int pitch = p.pitch;
-    const int o0 = y * pitch + x;
     // Pull sources exactly as in step_kernel (the pressure-reference shifts are
-    // zero here: the host sets p_ref = 0 for this storage).
+    // zero here).
     const auto t = pull_table<kInterior>(p, x, y, [pitch](int sx, int sy) { return sy * pitch + sx; });
 
     // ---- loads: stored deviations and the source nodes' moments (the axis
     // sources of the fluid and of the scalars are the same nodes)
     const float *mux = min + M * P, *muy = min + (M + 1) * P, *mpr = min + (M + 2) * P;
-    float h[9], hu[9], hv[9], hp[9], hphi[9][M];
+    float hu[9], hv[9], hp[9], hphi[9][M];
 #pragma unroll
     for (int i = 0; i < 9; ++i) {
         h[i] = Store<T>::load(in + t.hplane[i] * P + t.hpos[i]);
@@ -377,15 +378,12 @@ __device__ __forceinline__ void step_node_mr(const LbParams &p, int x, int y, co
 #pragma unroll
         for (int a = 0; a < M; ++a) hphi[i][a] = __ldg(min + a * P + t.hpos[i]);
     }
-    float f[M][5];
 #pragma unroll
     for (int i = 0; i < 5; ++i)
 #pragma unroll
         for (int a = 0; a < M; ++a) f[a][i] = Store<T>::load(in + (9 + 5 * a + t.splane[i]) * P + t.spos[i]);
-    const bool consume = (M >= 2 && p.skind == 2);
-    const float sp1 = consume ? sp_in[o0] : 0.f;
 
-    // ---- rebuild the pre-collision populations (deviation variables of collide)
+    // ---- rebuild the pre-collision populations
 #pragma unroll
     for (int i = 0; i < 9; ++i) h[i] += href_dir(t.hplane[i], hp[i], hu[i], hv[i]);
 #pragma unroll
@@ -401,11 +399,15 @@ __device__ __forceinline__ void step_node_mr(const LbParams &p, int x, int y, co
             if (t.side[i] >= 0 && ((p.dirichlet[t.side[i]] >> a) & 1u)) f[a][i] = p.abb[t.side[i]][a] - f[a][i];
         }
     }
+}
 
-    NodeOut<M> o;
-    collide<M>(p, f, h, 0.f, sp1, false, o);
-
-    // ---- store deviations from this node's new equilibrium, and its moments
+// Store of one node for 16-bit storage: deviations of the post-collision
+// populations from this node's new equilibrium, and its moments in FP32.
+template <int M, typename T>
+__device__ __forceinline__ void store_node_mr(const LbParams &p, int o0, T *__restrict__ out,
+                                              float *__restrict__ mout, const float (&f)[M][5],
+                                              const float (&h)[9], const NodeOut<M> &o) {
+    const long long P = p.plane;
     float feq[M][5];
     scalar_equilibrium<M>(o.phi, o.phi, o.ux, o.uy, feq);
 #pragma unroll
@@ -414,8 +416,102 @@ __device__ __forceinline__ void step_node_mr(const LbParams &p, int x, int y, co
     for (int a = 0; a < M; ++a)
 #pragma unroll
         for (int i = 0; i < 5; ++i) Store<T>::store(out + (9 + 5 * a + i) * P + o0, f[a][i] - feq[a][i]);
-    if (consume) sp_out[o0] = o.s1;
     write_moments<M>(mout, P, o0, o);
+}
+
+// One node of the 16-bit step.
+template <int M, typename T, bool kInterior>
+__device__ __forceinline__ void step_node_mr(const LbParams &p, int x, int y, const T *__restrict__ in,
+                                             const float *__restrict__ min, T *__restrict__ out,
+                                             float *__restrict__ mout, const float *sp_in, float *sp_out) {
+    const int o0 = y * p.pitch + x;
+    float f[M][5], h[9];
+    pull_node_mr<M, T, kInterior>(p, x, y, in, min, f, h);
+    const bool consume = (M >= 2 && p.skind == 2);
+    const float sp1 = consume ? sp_in[o0] : 0.f;
+    NodeOut<M> o;
+    collide<M>(p, f, h, 0.f, sp1, false, o);
+    store_node_mr<M, T>(p, o0, out, mout, f, h, o);
+    if (consume) sp_out[o0] = o.s1;
+}
+
+// Two time steps per launch with 16-bit storage: the tiling of step2_kernel.
+// Step 1 rebuilds the populations of the R1 nodes from the stored deviations
+// and moments, collides, and keeps the post-collision populations in FP32 in
+// shared memory (no 16-bit rounding in between); step 2 pulls them from there,
+// collides and stores deviations and moments.  Per two steps the populations
+// are rounded to 16 bits once, so the results differ from two one-step
+// launches by that saved rounding (both are held to the FP64 oracle).
+template <int M, typename T>
+__global__ void __launch_bounds__(step2_mr_max_threads(M), (M <= 2 ? 3 : 1)) step2_kernel_mr(
+    const LbParams p, int TH, const T *__restrict__ in, const float *__restrict__ mom_in, T *__restrict__ out,
+    float *__restrict__ mout, const float *sp_in, float *sp_out) {
+    constexpr int NP = 9 + 5 * M;
+    extern __shared__ float sm[];
+    pdl_wait_and_release();
+    const int W1 = blockDim.x, H1 = TH + 2, SP = W1 * H1, TW = W1 - 2;
+    const int X0 = blockIdx.x * TW, Y0 = blockIdx.y * TH;
+    const int pitch = p.pitch, nx = p.nx, ny = p.ny;
+    const bool consume = M >= 2 && p.skind == 2;
+    const int lx = threadIdx.x;
+    const int xu = X0 - 1 + lx;
+    const bool colv = xu <= min(X0 + TW, nx) && (p.periodic_x || (xu >= 0 && xu < nx));
+    const int gx = xu < 0 ? xu + nx : (xu >= nx ? xu - nx : xu);
+
+    // ---- step 1: R1 from the stored deviations into shared memory (FP32)
+    for (int ly = threadIdx.y; ly < H1; ly += blockDim.y) {
+        const int yu = Y0 - 1 + ly;
+        const bool ok = colv && yu <= min(Y0 + TH, ny) && (p.periodic_y || (yu >= 0 && yu < ny));
+        const int gy = yu < 0 ? yu + ny : (yu >= ny ? yu - ny : yu);
+        const bool general = ok && !inner_node(p, gx, gy);
+        float h[9], f[M][5];
+        if (!__any_sync(0xffffffffu, general)) {
+            if (!ok) continue;
+            pull_node_mr<M, T, true>(p, gx, gy, in, mom_in, f, h);
+        } else {
+            if (!ok) continue;
+            pull_node_mr<M, T, false>(p, gx, gy, in, mom_in, f, h);
+        }
+        const int o0 = gy * pitch + gx, l0 = ly * W1 + lx;
+        NodeOut<M> o;
+        collide<M>(p, f, h, 0.f, consume ? sp_in[o0] : 0.f, false, o);
+#pragma unroll
+        for (int i = 0; i < 9; ++i) sm[i * SP + l0] = h[i];
+#pragma unroll
+        for (int a = 0; a < M; ++a)
+#pragma unroll
+            for (int i = 0; i < 5; ++i) sm[(9 + 5 * a + i) * SP + l0] = f[a][i];
+        if (consume) sm[NP * SP + l0] = o.s1;
+    }
+    __syncthreads();
+
+    // ---- step 2: the tile from shared memory into 16-bit deviations and moments
+    const auto lds = [SP](int plane, int off) { return sm[plane * SP + off]; };
+    const auto mk_in = [W1, X0, Y0](int sx, int sy) { return (sy - Y0 + 1) * W1 + (sx - X0 + 1); };
+    const auto mk_gen = [W1, H1, X0, Y0, nx, ny](int sx, int sy) {
+        int a = sx - X0 + 1, b = sy - Y0 + 1;
+        a = a < 0 ? a + nx : (a >= W1 ? a - nx : a);
+        b = b < 0 ? b + ny : (b >= H1 ? b - ny : b);
+        return b * W1 + a;
+    };
+    for (int ly = 1 + threadIdx.y; ly <= TH; ly += blockDim.y) {
+        const int x = xu, y = Y0 - 1 + ly;
+        const bool ok = lx >= 1 && lx <= TW && x < nx && y < ny;
+        const bool general = ok && !inner_node(p, x, y);
+        float h[9], f[M][5];
+        if (!__any_sync(0xffffffffu, general)) {
+            if (!ok) continue;
+            pull_node<M, true>(p, x, y, mk_in, lds, f, h);
+        } else {
+            if (!ok) continue;
+            pull_node<M, false>(p, x, y, mk_gen, lds, f, h);
+        }
+        const int o0 = y * pitch + x;
+        NodeOut<M> o;
+        collide<M>(p, f, h, 0.f, consume ? sm[NP * SP + ly * W1 + lx] : 0.f, false, o);
+        store_node_mr<M, T>(p, o0, out, mout, f, h, o);
+        if (consume) sp_out[o0] = o.s1;
+    }
 }
 
 template <int M, typename T>
@@ -669,6 +765,52 @@ cudaError_t launch_step2(const LbParams &p, const float *in, float *out, const f
         default: return cudaErrorInvalidValue;
     }
     return e != cudaSuccess ? e : cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t step2_mr_dispatch(const LbParams &p, const void *in, const float *min, void *out, float *mout,
+                              const float *sp_in, float *sp_out, dim3 block, int th, cudaStream_t s) {
+    const size_t smem = step2_smem_bytes(p.m, block, th);
+    dim3 grid((p.nx + block.x - 3) / (block.x - 2), (p.ny + th - 1) / th);
+    const T *i = static_cast<const T *>(in);
+    T *o = static_cast<T *>(out);
+    static std::atomic<bool> attr_set[64][kMaxM + 1];
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+    switch (p.m) {
+#define CDF_STEP2MR_CASE(MM)                                                                             \
+    case MM:                                                                                             \
+        if (!attr_set[dev][MM].load()) {                                                                 \
+            e = cudaFuncSetAttribute(step2_kernel_mr<MM, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
+                                     kStep2MaxSmem);                                                     \
+            if (e != cudaSuccess) return e;                                                              \
+            attr_set[dev][MM].store(true);                                                               \
+        }                                                                                                \
+        e = launch_pdl_smem(step2_kernel_mr<MM, T>, grid, block, smem, s, p, th, i, min, o, mout, sp_in, sp_out); \
+        break;
+        CDF_STEP2MR_CASE(1)
+        CDF_STEP2MR_CASE(2)
+        CDF_STEP2MR_CASE(3)
+        CDF_STEP2MR_CASE(4)
+#undef CDF_STEP2MR_CASE
+        default: return cudaErrorInvalidValue;
+    }
+    return e != cudaSuccess ? e : cudaGetLastError();
+}
+
+cudaError_t launch_step2_mr(const LbParams &p, int storage, const void *in, const float *moments_in, void *out,
+                            float *moments_out, const float *sp_in, float *sp_out, dim3 block, int th,
+                            cudaStream_t s) {
+    switch (storage) {
+        case kFP16:
+            return step2_mr_dispatch<__half>(p, in, moments_in, out, moments_out, sp_in, sp_out, block, th, s);
+        case kBF16:
+            return step2_mr_dispatch<__nv_bfloat16>(p, in, moments_in, out, moments_out, sp_in, sp_out, block, th,
+                                                    s);
+    }
+    return cudaErrorInvalidValue;
 }
 
 cudaError_t launch_init(const LbParams &p, int storage, const float *fields, int fields_pitch,
