@@ -67,16 +67,9 @@ __global__ void __launch_bounds__(256) step_kernel_flat(const LbParams p, const 
                                                         T *__restrict__ out, const float *sp_in, float *sp_out,
                                                         float *__restrict__ moments) {
     pdl_wait_and_release();
-    // node idx = y nx + x: one division for the CTA's first node (a value uniform
-    // over the CTA), then at most blockDim.x / nx + 1 row steps per thread
-    const int base = blockIdx.x * blockDim.x;
-    int y = base / p.nx;
-    int x = base - y * p.nx + (int)threadIdx.x;
-    while (x >= p.nx) {
-        x -= p.nx;
-        ++y;
-    }
-    const bool valid = y < p.ny;
+    const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+    const bool valid = idx < p.nx * p.ny;
+    const int y = idx / p.nx, x = idx - y * p.nx;
     if (__all_sync(0xffffffffu, valid && inner_node(p, x, y)))
         step_node<M, T, false, true>(p, x, y, in, out, sp_in, sp_out, moments);
     else if (valid)
