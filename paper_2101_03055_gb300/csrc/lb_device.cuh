@@ -536,5 +536,31 @@ __device__ __forceinline__ void step_node(const LbParams &p, int x, int y, const
     if (moments) write_moments<M>(moments, P, o0, o);
 }
 
+// step_node with the planes given one pointer each (Planes): the form of the
+// single-lattice step kernels.  Same node update, same bits.
+template <int M, typename T, bool kInterior = false>
+__device__ __forceinline__ void step_node_planes(const LbParams &p, int x, int y, const Planes<T> &pl,
+                                                 const float *sp_in, float *sp_out, float *__restrict__ moments) {
+    const int pitch = p.pitch;
+    const auto mk = [pitch](int sx, int sy) { return sy * pitch + sx; };
+    const auto ld = [&pl](int plane, int off) { return Store<T>::load(pl.in[plane] + off); };
+    const int o0 = y * pitch + x;
+    const bool consume = (M >= 2 && p.skind == 2);
+    const float sp1 = consume ? sp_in[o0] : 0.f;
+    float h[9], f[M][5];
+    pull_node<M, kInterior>(p, x, y, mk, ld, f, h);
+
+    NodeOut<M> o;
+    collide<M>(p, f, h, pref_at(p, x, y), sp1, false, o);
+#pragma unroll
+    for (int i = 0; i < 9; ++i) Store<T>::store(pl.out[i] + o0, h[i]);
+#pragma unroll
+    for (int a = 0; a < M; ++a)
+#pragma unroll
+        for (int i = 0; i < 5; ++i) Store<T>::store(pl.out[9 + 5 * a + i] + o0, f[a][i]);
+    if (consume) sp_out[o0] = o.s1;
+    if (moments) write_moments<M>(moments, p.plane, o0, o);
+}
+
 }  // namespace dev
 }  // namespace cdflb

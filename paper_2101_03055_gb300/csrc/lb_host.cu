@@ -316,57 +316,6 @@ cdf_status reduce(cdf_lb *h, const float *nw, const float *od, double *host_out)
     return CDF_OK;
 }
 
-// Time the step kernel for a few CTA shapes on the (zeroed) buffers and keep the
-// fastest; results are cached per (nx, ny, m, storage).
-cdf_status autotune(cdf_lb *h) {
-    TuneKey key{h->nx, h->ny, h->m, h->storage, h->P.chemotaxis};
-    {
-        std::lock_guard<std::mutex> lk(g_tune_mu);
-        auto it = g_tune_cache.find(key);
-        if (it != g_tune_cache.end()) { h->block = it->second; return CDF_OK; }
-    }
-    // block.y == 0 marks a flat launch (one thread per node in row order)
-    std::vector<dim3> cands = {dim3(32, 4), dim3(32, 8), dim3(64, 2), dim3(64, 4),
-                               dim3(128, 1), dim3(128, 2), dim3(256, 1)};
-    if (!h->mr && !h->P.case1) {
-        // flat launches of several widths: a lattice that fills about one wave
-        // is fastest when its nodes split evenly over the 152 SMs (e.g. 131,072
-        // nodes in 1366 CTAs of 96 threads: nine CTAs on every SM)
-        for (unsigned w : {64u, 96u, 128u, 160u, 192u, 224u, 256u}) cands.push_back(dim3(w, 0));
-    }
-    cudaEvent_t a, b;
-    CK(cudaEventCreate(&a));
-    CK(cudaEventCreate(&b));
-    float best = 1e30f;
-    dim3 best_b = h->block;
-    const long long nodes = (long long)h->nx * h->ny;
-    const int reps = nodes >= (1 << 22) ? 4 : 16;
-    for (const dim3 &c : cands) {
-        if ((int)c.x > 2 * h->nx && c.x > 32) continue;
-        h->block = c;
-        for (int w = 0; w < 2; ++w) {
-            cdf_status st = launch_one(h, 0, false);
-            if (st != CDF_OK) return st;
-        }
-        CK(cudaEventRecord(a, h->s));
-        for (int r = 0; r < reps; ++r) {
-            cdf_status st = launch_one(h, r & 1, false);
-            if (st != CDF_OK) return st;
-        }
-        CK(cudaEventRecord(b, h->s));
-        CK(cudaEventSynchronize(b));
-        float ms = 0;
-        CK(cudaEventElapsedTime(&ms, a, b));
-        if (ms < best) { best = ms; best_b = c; }
-    }
-    cudaEventDestroy(a);
-    cudaEventDestroy(b);
-    h->block = best_b;
-    std::lock_guard<std::mutex> lk(g_tune_mu);
-    g_tune_cache[key] = best_b;
-    return CDF_OK;
-}
-
 std::map<TuneKey, bool> g_resident_cache;
 
 // Time `steps` steps of the current mode on the library stream (ms).
@@ -397,6 +346,48 @@ void drop_graphs(cdf_lb *h) {
                 cudaGraphExecDestroy(ge);
                 ge = nullptr;
             }
+}
+
+// Time the step kernel for a few CTA shapes on the (zeroed) buffers and keep the
+// fastest; results are cached per (nx, ny, m, storage).  The shapes are timed
+// through the path the steps run in (CUDA graphs of 32 launches): a short step
+// launched one by one from the host would time the host's launch rate.
+cdf_status autotune(cdf_lb *h) {
+    TuneKey key{h->nx, h->ny, h->m, h->storage, h->P.chemotaxis};
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        auto it = g_tune_cache.find(key);
+        if (it != g_tune_cache.end()) { h->block = it->second; return CDF_OK; }
+    }
+    // block.y == 0 marks a flat launch (one thread per node in row order)
+    std::vector<dim3> cands = {dim3(32, 4), dim3(32, 8), dim3(64, 2), dim3(64, 4),
+                               dim3(128, 1), dim3(128, 2), dim3(256, 1)};
+    if (!h->mr && !h->P.case1) {
+        // flat launches of several widths: a lattice that fills about one wave
+        // is fastest when its nodes split evenly over the 152 SMs (e.g. 131,072
+        // nodes in 1366 CTAs of 96 threads: nine CTAs on every SM)
+        for (unsigned w : {64u, 96u, 128u, 160u, 192u, 224u, 256u}) cands.push_back(dim3(w, 0));
+    }
+    const long long nodes = (long long)h->nx * h->ny;
+    const long long steps = nodes >= (1 << 22) ? 4 : 2 * kGraphSteps;
+    float best = 1e30f;
+    dim3 best_b = h->block;
+    for (const dim3 &c : cands) {
+        if ((int)c.x > 2 * h->nx && c.x > 32) continue;
+        h->block = c;
+        drop_graphs(h);
+        float ms = 0.f;
+        cdf_status st = time_steps(h, steps, &ms);
+        if (st != CDF_OK) return st;
+        if (ms < best) { best = ms; best_b = c; }
+    }
+    drop_graphs(h);
+    h->block = best_b;
+    h->cur = 0;
+    h->t = 0;
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_tune_cache[key] = best_b;
+    return CDF_OK;
 }
 
 // Can step2_kernel run this lattice with CTA shape b and tile height th?
@@ -472,39 +463,29 @@ cdf_status setup_pair(cdf_lb *h, const cdf_options *opt) {
         if (opt->temporal == 1) return fail(CDF_EINVAL, "the lattice is too small for two steps per launch");
         return CDF_OK;
     }
-    cudaEvent_t a, b;
-    CK(cudaEventCreate(&a));
-    CK(cudaEventCreate(&b));
-    const int reps = nodes >= (1 << 22) ? 4 : 16;
-    auto timed = [&](auto &&launch, float *ms) -> cdf_status {
-        for (int w = 0; w < 2; ++w) CK(launch(w & 1));
-        CK(cudaEventRecord(a, h->s));
-        for (int r = 0; r < reps; ++r) CK(launch(r & 1));
-        CK(cudaEventRecord(b, h->s));
-        CK(cudaEventSynchronize(b));
-        CK(cudaEventElapsedTime(ms, a, b));
-        return CDF_OK;
-    };
+    // timed through the path the steps run in (CUDA graphs; see autotune)
+    const long long steps = nodes >= (1 << 22) ? 4 : 2 * kGraphSteps;
+    h->pair = false;
+    drop_graphs(h);
     float t_single = 0.f;
-    cdf_status st = timed([&](int src) -> cudaError_t {
-        cudaError_t e = launch_any(h, src, false);
-        return e != cudaSuccess ? e : launch_any(h, src ^ 1, false);
-    }, &t_single);
+    cdf_status st = time_steps(h, steps, &t_single);
     float best = 1e30f;
     PairChoice choice{false, h->pair_block, h->pair_th};
     for (size_t k = 0; st == CDF_OK && k < cands.size(); ++k) {
+        h->pair = true;
         h->pair_block = cands[k].first;
         h->pair_th = cands[k].second;
+        drop_graphs(h);
         float ms = 0.f;
-        st = timed([&](int src) { return launch_two(h, src, false); }, &ms);
+        st = time_steps(h, steps, &ms);
         if (st == CDF_OK && ms < best) {
             best = ms;
             choice.block = cands[k].first;
             choice.th = cands[k].second;
         }
     }
-    cudaEventDestroy(a);
-    cudaEventDestroy(b);
+    h->cur = 0;
+    h->t = 0;
     if (st != CDF_OK) return st;
     choice.use = opt->temporal == 1 || best < t_single;
     h->pair = choice.use;

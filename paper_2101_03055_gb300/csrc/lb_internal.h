@@ -49,6 +49,16 @@ struct LbParams {
 
 enum Storage { kFP32 = 0, kFP16 = 1, kBF16 = 2 };
 
+// The population planes of a step, one pointer per plane, passed to the step
+// kernels as a parameter: a plane's address is then an operand from the
+// constant bank instead of a 64-bit multiply-add per access.
+constexpr int kMaxPlanes = 9 + 5 * kMaxM;
+template <typename T>
+struct Planes {
+    const T *in[kMaxPlanes];
+    T *out[kMaxPlanes];
+};
+
 // Launchers (lb_kernels.cu).  A step launch with block.y == 0 is flat: block.x
 // threads per CTA over the nx * ny nodes in row order (FP32 storage path).  `in`/`out` point at the first of `planes`
 // population planes; plane k starts at base + k * plane.  Planes are ordered

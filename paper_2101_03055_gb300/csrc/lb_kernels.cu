@@ -45,35 +45,44 @@ cudaError_t launch_pdl(void (*kern)(KArgs...), dim3 grid, dim3 block, cudaStream
     return launch_pdl_smem(kern, grid, block, 0, s, args...);
 }
 
+// One pointer per population plane of the buffers `in` (read) and `out` (written).
+template <typename T>
+Planes<T> planes_of(const LbParams &p, const T *in, T *out) {
+    Planes<T> pl{};
+    for (int k = 0; k < 9 + 5 * p.m; ++k) {
+        pl.in[k] = in + k * p.plane;
+        pl.out[k] = out + k * p.plane;
+    }
+    return pl;
+}
+
 // ---- the fused step ------------------------------------------------------------
 template <int M, typename T>
-__global__ void __launch_bounds__(256) step_kernel(const LbParams p, const T *__restrict__ in,
-                                                   T *__restrict__ out, const float *sp_in, float *sp_out,
-                                                   float *__restrict__ moments) {
+__global__ void __launch_bounds__(256) step_kernel(const LbParams p, const Planes<T> pl, const float *sp_in,
+                                                   float *sp_out, float *__restrict__ moments) {
     pdl_wait_and_release();
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     const int y = blockIdx.y * blockDim.y + threadIdx.y;
     // Warp-uniform choice (every CTA holds whole warps): a warp whose 32 nodes
     // all lie inside the boundary ring runs the pull without boundary selects.
     if (__all_sync(0xffffffffu, inner_node(p, x, y)))
-        step_node<M, T, false, true>(p, x, y, in, out, sp_in, sp_out, moments);
+        step_node_planes<M, T, true>(p, x, y, pl, sp_in, sp_out, moments);
     else if (x < p.nx && y < p.ny)
-        step_node<M, T>(p, x, y, in, out, sp_in, sp_out, moments);
+        step_node_planes<M, T>(p, x, y, pl, sp_in, sp_out, moments);
 }
 
 // Flat launch: one thread per node over nx * ny (no idle threads in ragged rows).
 template <int M, typename T>
-__global__ void __launch_bounds__(256) step_kernel_flat(const LbParams p, const T *__restrict__ in,
-                                                        T *__restrict__ out, const float *sp_in, float *sp_out,
-                                                        float *__restrict__ moments) {
+__global__ void __launch_bounds__(256) step_kernel_flat(const LbParams p, const Planes<T> pl, const float *sp_in,
+                                                        float *sp_out, float *__restrict__ moments) {
     pdl_wait_and_release();
     const int idx = blockIdx.x * blockDim.x + threadIdx.x;
     const bool valid = idx < p.nx * p.ny;
     const int y = idx / p.nx, x = idx - y * p.nx;
     if (__all_sync(0xffffffffu, valid && inner_node(p, x, y)))
-        step_node<M, T, false, true>(p, x, y, in, out, sp_in, sp_out, moments);
+        step_node_planes<M, T, true>(p, x, y, pl, sp_in, sp_out, moments);
     else if (valid)
-        step_node<M, T>(p, x, y, in, out, sp_in, sp_out, moments);
+        step_node_planes<M, T>(p, x, y, pl, sp_in, sp_out, moments);
 }
 
 // ---- two time steps per launch (temporal blocking), FP32 storage ----------------
@@ -93,9 +102,9 @@ __global__ void __launch_bounds__(256) step_kernel_flat(const LbParams p, const 
 // from sp_in and written to sp_out, which must be different planes: the halo
 // of one CTA is the tile of another.
 template <int M>
-__global__ void __launch_bounds__(step2_max_threads(M)) step2_kernel(const LbParams p, int TH, const float *__restrict__ in,
-                                                     float *__restrict__ out, const float *sp_in, float *sp_out,
-                                                     float *__restrict__ moments) {
+__global__ void __launch_bounds__(step2_max_threads(M)) step2_kernel(const LbParams p, int TH, const Planes<float> pl,
+                                                                     const float *sp_in, float *sp_out,
+                                                                     float *__restrict__ moments) {
     constexpr int NP = 9 + 5 * M;
     extern __shared__ float sm[];
     pdl_wait_and_release();
@@ -116,7 +125,7 @@ __global__ void __launch_bounds__(step2_max_threads(M)) step2_kernel(const LbPar
     // ---- step 1: R1 from global memory into shared memory
     {
         const auto mk = [pitch](int sx, int sy) { return sy * pitch + sx; };
-        const auto ld = [in, P](int plane, int off) { return __ldg(in + plane * P + off); };
+        const auto ld = [&pl](int plane, int off) { return __ldg(pl.in[plane] + off); };
         for (int ly = threadIdx.y; ly < H1; ly += blockDim.y) {
             const int yu = Y0 - 1 + ly;
             const bool ok = colv && yu <= min(Y0 + TH, ny) && (p.periodic_y || (yu >= 0 && yu < ny));
@@ -170,7 +179,12 @@ __global__ void __launch_bounds__(step2_max_threads(M)) step2_kernel(const LbPar
         const int o0 = y * pitch + x;
         NodeOut<M> o;
         collide<M>(p, f, h, pref_at(p, x, y), consume ? sm[NP * SP + ly * W1 + lx] : 0.f, false, o);
-        store_node<M, float>(out, P, o0, f, h);
+#pragma unroll
+        for (int i = 0; i < 9; ++i) pl.out[i][o0] = h[i];
+#pragma unroll
+        for (int a = 0; a < M; ++a)
+#pragma unroll
+            for (int i = 0; i < 5; ++i) pl.out[9 + 5 * a + i][o0] = f[a][i];
         if (consume) sp_out[o0] = o.s1;
         if (moments) write_moments<M>(moments, P, o0, o);
     }
@@ -646,15 +660,16 @@ cudaError_t step_dispatch(const LbParams &p, const void *in, void *out, const fl
         }
         return cudaErrorInvalidValue;
     }
+    const Planes<T> pl = planes_of(p, i, o);
     if (block.y == 0) {  // flat launch
         const long long n = (long long)p.nx * p.ny;
         dim3 fb(block.x), grid((unsigned)((n + block.x - 1) / block.x));
         cudaError_t e = cudaSuccess;
         switch (p.m) {
-            case 1: e = launch_pdl(step_kernel_flat<1, T>, grid, fb, s, p, i, o, sp_in, sp_out, mom); break;
-            case 2: e = launch_pdl(step_kernel_flat<2, T>, grid, fb, s, p, i, o, sp_in, sp_out, mom); break;
-            case 3: e = launch_pdl(step_kernel_flat<3, T>, grid, fb, s, p, i, o, sp_in, sp_out, mom); break;
-            case 4: e = launch_pdl(step_kernel_flat<4, T>, grid, fb, s, p, i, o, sp_in, sp_out, mom); break;
+            case 1: e = launch_pdl(step_kernel_flat<1, T>, grid, fb, s, p, pl, sp_in, sp_out, mom); break;
+            case 2: e = launch_pdl(step_kernel_flat<2, T>, grid, fb, s, p, pl, sp_in, sp_out, mom); break;
+            case 3: e = launch_pdl(step_kernel_flat<3, T>, grid, fb, s, p, pl, sp_in, sp_out, mom); break;
+            case 4: e = launch_pdl(step_kernel_flat<4, T>, grid, fb, s, p, pl, sp_in, sp_out, mom); break;
             default: return cudaErrorInvalidValue;
         }
         return e != cudaSuccess ? e : cudaGetLastError();
@@ -662,10 +677,10 @@ cudaError_t step_dispatch(const LbParams &p, const void *in, void *out, const fl
     dim3 grid((p.nx + block.x - 1) / block.x, (p.ny + block.y - 1) / block.y);
     cudaError_t e = cudaSuccess;
     switch (p.m) {
-        case 1: e = launch_pdl(step_kernel<1, T>, grid, block, s, p, i, o, sp_in, sp_out, mom); break;
-        case 2: e = launch_pdl(step_kernel<2, T>, grid, block, s, p, i, o, sp_in, sp_out, mom); break;
-        case 3: e = launch_pdl(step_kernel<3, T>, grid, block, s, p, i, o, sp_in, sp_out, mom); break;
-        case 4: e = launch_pdl(step_kernel<4, T>, grid, block, s, p, i, o, sp_in, sp_out, mom); break;
+        case 1: e = launch_pdl(step_kernel<1, T>, grid, block, s, p, pl, sp_in, sp_out, mom); break;
+        case 2: e = launch_pdl(step_kernel<2, T>, grid, block, s, p, pl, sp_in, sp_out, mom); break;
+        case 3: e = launch_pdl(step_kernel<3, T>, grid, block, s, p, pl, sp_in, sp_out, mom); break;
+        case 4: e = launch_pdl(step_kernel<4, T>, grid, block, s, p, pl, sp_in, sp_out, mom); break;
         default: return cudaErrorInvalidValue;
     }
     return e != cudaSuccess ? e : cudaGetLastError();
@@ -733,6 +748,7 @@ cudaError_t launch_step2(const LbParams &p, const float *in, float *out, const f
                          float *moments, dim3 block, int th, cudaStream_t s) {
     const size_t smem = step2_smem_bytes(p.m, block, th);
     dim3 grid((p.nx + block.x - 3) / (block.x - 2), (p.ny + th - 1) / th);
+    const Planes<float> pl = planes_of(p, in, out);
     // the opt-in to more than 48 KB of dynamic shared memory, once per device and m
     static std::atomic<bool> attr_set[64][kMaxM + 1];
     int dev = 0;
@@ -748,7 +764,7 @@ cudaError_t launch_step2(const LbParams &p, const float *in, float *out, const f
             if (e != cudaSuccess) return e;                                                              \
             attr_set[dev][MM].store(true);                                                               \
         }                                                                                                \
-        e = launch_pdl_smem(step2_kernel<MM>, grid, block, smem, s, p, th, in, out, sp_in, sp_out, moments); \
+        e = launch_pdl_smem(step2_kernel<MM>, grid, block, smem, s, p, th, pl, sp_in, sp_out, moments);   \
         break;
         CDF_STEP2_CASE(1)
         CDF_STEP2_CASE(2)
