@@ -210,7 +210,9 @@ class _Single:
             else:
                 self.kernel = f"step_kernel<{pb.m},float>"
         if getattr(pb, "case1", False):
-            self.kernel = f"step_kernel_case1<{pb.m}> (prescribed velocity, no fluid)"
+            self.kernel = (f"step2_kernel_case1<{pb.m}> (prescribed velocity, no fluid; two time steps per launch, "
+                           f"CTAs of {info.block_x}x{info.block_y} threads, output tiles {info.tile_x}x{info.tile_y})"
+                           if self.pair else f"step_kernel_case1<{pb.m}> (prescribed velocity, no fluid)")
 
     def steps_per_launch(self, n):
         """Lattice steps per kernel launch inside step(n)."""

@@ -141,7 +141,7 @@ typedef struct {
     int temporal;                      /* two time steps per launch (temporal blocking: each CTA
                                           updates its tile and a one-node halo into shared memory,
                                           then the tile again from there; one pass over global
-                                          memory serves two steps), full model (not Case 1):
+                                          memory serves two steps), full model and Case 1:
                                           0 = used when the autotuner measures it faster,
                                           1 = always, -1 = never; a fixed block_x with
                                           temporal = 0 keeps one step per launch.  FP32: bitwise

@@ -119,7 +119,7 @@ struct cdf_lb {
     // advances two steps reads halo nodes that other CTAs rewrite, so the
     // planes cannot be updated in place.
     float *sprev_pp[2] = {nullptr, nullptr};
-    float *vel = nullptr;  // Case 1: prescribed velocity and phi(t - 1), 2 + m planes
+    float *vel = nullptr;  // Case 1: prescribed velocity (2 planes) and two sets of m phi planes
     float *mom = nullptr, *mom_prev = nullptr;
     bool mr = false;                       // 16-bit storage: node-equilibrium deviations
     float *mom_pp[2] = {nullptr, nullptr};  // 16-bit storage: moments beside buf[0], buf[1]
@@ -192,12 +192,25 @@ cdf_status leave(cdf_lb *h) {
 // step of a call; 16-bit storage keeps them beside the current populations.
 float *current_moments(cdf_lb *h) { return h->mr ? h->mom_pp[h->cur] : h->mom; }
 
+// Case 1: the phi set that belongs to population buffer `par`.
+float *phi_set(cdf_lb *h, int par) { return h->vel + (2 + (long long)par * h->m) * h->plane; }
+
+// The step parameters for a launch reading buffer `src` (Case 1: its phi sets).
+LbParams params_for(cdf_lb *h, int src) {
+    LbParams p = h->P;
+    if (p.case1) {
+        p.php_in = phi_set(h, src);
+        p.php_out = phi_set(h, src ^ 1);
+    }
+    return p;
+}
+
 cudaError_t launch_any(cdf_lb *h, int src, bool with_moments) {
     if (h->mr)
         return launch_step_mr(h->P, h->storage, h->buf[src], h->mom_pp[src], h->buf[src ^ 1], h->mom_pp[src ^ 1],
                               h->sprev_pp[src], h->sprev_pp[src ^ 1], h->block, h->s);
-    return launch_step(h->P, h->storage, h->buf[src], h->buf[src ^ 1], h->sprev_pp[src], h->sprev_pp[src ^ 1],
-                       with_moments ? h->mom : nullptr, h->block, h->s);
+    return launch_step(params_for(h, src), h->storage, h->buf[src], h->buf[src ^ 1], h->sprev_pp[src],
+                       h->sprev_pp[src ^ 1], with_moments ? h->mom : nullptr, h->block, h->s);
 }
 
 // Two steps from buf[src] to buf[src ^ 1] in one launch (16-bit storage keeps
@@ -206,7 +219,8 @@ cudaError_t launch_two(cdf_lb *h, int src, bool with_moments) {
     if (h->mr)
         return launch_step2_mr(h->P, h->storage, h->buf[src], h->mom_pp[src], h->buf[src ^ 1], h->mom_pp[src ^ 1],
                                h->sprev_pp[src], h->sprev_pp[src ^ 1], h->pair_block, h->pair_th, h->s);
-    return launch_step2(h->P, static_cast<const float *>(h->buf[src]), static_cast<float *>(h->buf[src ^ 1]),
+    return launch_step2(params_for(h, src), static_cast<const float *>(h->buf[src]),
+                        static_cast<float *>(h->buf[src ^ 1]),
                         h->sprev_pp[src], h->sprev_pp[src ^ 1], with_moments ? h->mom : nullptr, h->pair_block,
                         h->pair_th, h->s);
 }
@@ -415,8 +429,7 @@ std::map<PairKey, PairChoice> g_pair_cache;
 cdf_status setup_pair(cdf_lb *h, const cdf_options *opt) {
     // a fixed CTA shape of the step kernel fixes the one-step launch unless two
     // steps per launch are asked for explicitly
-    if (h->P.case1 || opt->temporal == -1 || opt->resident == 1 || (opt->block_x > 0 && opt->temporal == 0))
-        return CDF_OK;
+    if (opt->temporal == -1 || opt->resident == 1 || (opt->block_x > 0 && opt->temporal == 0)) return CDF_OK;
     if (opt->temporal_block_x > 0) {  // a given shape
         const dim3 b(opt->temporal_block_x, opt->temporal_block_y, 1);
         if (!pair_fits(h, b, opt->temporal_tile_y))
@@ -702,8 +715,8 @@ cdf_status cdf_lb_create(const cdf_grid *grid, int m, const cdf_diffusion *dif, 
             opt->temporal_tile_y < 1)
             return fail(CDF_EINVAL, "two-step kernel shape: block_x 32 or 64, block_y >= 1, tile_y >= 1");
     }
-    if (opt->temporal == 1 && (opt->prescribed_velocity || opt->resident == 1))
-        return fail(CDF_EINVAL, "two steps per launch exist for the full model, without the resident step");
+    if (opt->temporal == 1 && opt->resident == 1)
+        return fail(CDF_EINVAL, "two steps per launch and the resident step exclude each other");
     LbParams P0{};
     const int align = opt->storage == CDF_FP32 ? 32 : 64;  // 128-byte rows
     const int pitch = grid->nx >= 1 ? (grid->nx + align - 1) / align * align : 0;
@@ -743,7 +756,7 @@ cdf_status cdf_lb_create(const cdf_grid *grid, int m, const cdf_diffusion *dif, 
     bool ok = alloc(&h->buf[0], pop_bytes) && alloc(&h->buf[1], pop_bytes) &&
               alloc((void **)&h->sprev_pp[0], (size_t)h->plane * 4) &&
               alloc((void **)&h->sprev_pp[1], (size_t)h->plane * 4) &&
-              (!h->P.case1 || alloc((void **)&h->vel, (size_t)(2 + m) * h->plane * 4)) &&
+              (!h->P.case1 || alloc((void **)&h->vel, (size_t)(2 + 2 * m) * h->plane * 4)) &&
               alloc((void **)&h->mom, (size_t)(m + 3) * h->plane * 4) &&
               alloc((void **)&h->mom_prev, (size_t)(m + 3) * h->plane * 4) &&
               (!h->mr || (alloc((void **)&h->mom_pp[0], (size_t)(m + 3) * h->plane * 4) &&
@@ -803,10 +816,13 @@ void cdf_lb_destroy(cdf_lb *h) {
 }
 
 static cdf_status init_from_device_fields(cdf_lb *h, const float *fields) {
-    if (h->mr)
+    if (h->mr) {
         CK(launch_init_mr(h->P, h->storage, fields, h->nx, h->buf[0], h->mom_pp[0], h->sprev_pp[0], h->s));
-    else
-        CK(launch_init(h->P, h->storage, fields, h->nx, h->buf[0], h->sprev_pp[0], h->mom, h->s));
+    } else {
+        LbParams pi = h->P;  // Case 1: phi(t - 1) = phi0 goes to the set of buf[0]
+        if (pi.case1) pi.php_out = phi_set(h, 0);
+        CK(launch_init(pi, h->storage, fields, h->nx, h->buf[0], h->sprev_pp[0], h->mom, h->s));
+    }
     h->cur = 0;
     h->t = 0;
     h->initialised = true;
@@ -990,7 +1006,12 @@ cdf_status cdf_lb_save(cdf_lb *h, const char *path) {
     CK(cudaMemcpyAsync(data.data(), h->buf[h->cur], pop, cudaMemcpyDeviceToHost, h->s));
     CK(cudaMemcpyAsync(data.data() + pop, h->sprev_pp[h->cur], spb, cudaMemcpyDeviceToHost, h->s));
     CK(cudaMemcpyAsync(data.data() + pop + spb, current_moments(h), momb, cudaMemcpyDeviceToHost, h->s));
-    if (velb) CK(cudaMemcpyAsync(data.data() + pop + spb + momb, h->vel, velb, cudaMemcpyDeviceToHost, h->s));
+    if (velb) {  // Case 1: the prescribed velocity and the current phi set
+        const size_t ub = (size_t)2 * h->plane * 4;
+        CK(cudaMemcpyAsync(data.data() + pop + spb + momb, h->vel, ub, cudaMemcpyDeviceToHost, h->s));
+        CK(cudaMemcpyAsync(data.data() + pop + spb + momb + ub, phi_set(h, h->cur), velb - ub,
+                           cudaMemcpyDeviceToHost, h->s));
+    }
     if ((st = sync(h)) != CDF_OK) return st;
     FileHeader hd{};
     std::memcpy(hd.magic, kMagic, 8);
@@ -1041,7 +1062,12 @@ cdf_status cdf_lb_load(cdf_lb *h, const char *path) {
     CK(cudaMemcpyAsync(h->buf[0], data.data(), pop, cudaMemcpyHostToDevice, h->s));
     CK(cudaMemcpyAsync(h->sprev_pp[0], data.data() + pop, spb, cudaMemcpyHostToDevice, h->s));
     CK(cudaMemcpyAsync(current_moments(h), data.data() + pop + spb, momb, cudaMemcpyHostToDevice, h->s));
-    if (velb) CK(cudaMemcpyAsync(h->vel, data.data() + pop + spb + momb, velb, cudaMemcpyHostToDevice, h->s));
+    if (velb) {
+        const size_t ub = (size_t)2 * h->plane * 4;
+        CK(cudaMemcpyAsync(h->vel, data.data() + pop + spb + momb, ub, cudaMemcpyHostToDevice, h->s));
+        CK(cudaMemcpyAsync(phi_set(h, 0), data.data() + pop + spb + momb + ub, velb - ub, cudaMemcpyHostToDevice,
+                           h->s));
+    }
     if ((st = reset_resident(h)) != CDF_OK) return st;
     CK(cudaStreamSynchronize(h->s));
     h->t = hd.t;

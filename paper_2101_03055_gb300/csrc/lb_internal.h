@@ -42,9 +42,14 @@ struct LbParams {
     float gref[2];
     float xc, yc;
     // Case 1 of Sec. 2.1 (no fluid populations): planes of the prescribed
-    // velocity u_x, u_y and of phi_a(t - 1), `plane` floats each (device memory).
+    // velocity u_x, u_y (`vel`), and the m planes of phi_a(t - 1) a step reads
+    // (`php_in`) and the m planes of phi_a(t) it writes (`php_out`), `plane`
+    // floats each (device memory).  The two phi sets alternate with the
+    // population buffers.
     int case1;
     float *vel;
+    const float *php_in;
+    float *php_out;
 };
 
 enum Storage { kFP32 = 0, kFP16 = 1, kBF16 = 2 };

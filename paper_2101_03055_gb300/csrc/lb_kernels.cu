@@ -192,9 +192,9 @@ __global__ void __launch_bounds__(step2_max_threads(M)) step2_kernel(const LbPar
 
 // ---- Case 1 of Sec. 2.1: convection cross-diffusion in a prescribed velocity -----
 // Scalars only: pull the 5m scalar populations, read the node's prescribed
-// velocity and phi(t - 1) (p.vel), collide with the Case-1 auxiliary source,
-// store the scalars and phi(t) in place of phi(t - 1) (each node reads and
-// writes only its own entry).  Algorithmic bytes: 2 x 5m x 4 + 8 + 2 x 4m.
+// velocity (p.vel) and phi(t - 1) (p.php_in), collide with the Case-1
+// auxiliary source, store the scalars and phi(t) (p.php_out, the other phi
+// set).  Algorithmic bytes: 2 x 5m x 4 + 8 + 2 x 4m.
 template <int M>
 __global__ void __launch_bounds__(256) step_kernel_case1(const LbParams p, const float *__restrict__ in,
                                                          float *__restrict__ out, const float *sp_in, float *sp_out,
@@ -210,11 +210,11 @@ __global__ void __launch_bounds__(256) step_kernel_case1(const LbParams p, const
     float f[M][5];
     if (x >= p.nx || y >= p.ny) return;
     pull_scalars<M, false>(p, x, y, mk, ld, f);
-    float *vel = p.vel;
+    const float *vel = p.vel;
     const float ux = __ldg(vel + o0), uy = __ldg(vel + P + o0);
     float php[M];
 #pragma unroll
-    for (int a = 0; a < M; ++a) php[a] = vel[(2 + a) * P + o0];
+    for (int a = 0; a < M; ++a) php[a] = p.php_in[a * P + o0];
     const bool consume = (M >= 2 && p.skind == 2);
     const float sp1 = consume ? sp_in[o0] : 0.f;
     NodeOut<M> o;
@@ -224,9 +224,93 @@ __global__ void __launch_bounds__(256) step_kernel_case1(const LbParams p, const
 #pragma unroll
         for (int i = 0; i < 5; ++i) out[(9 + 5 * a + i) * P + o0] = f[a][i];
 #pragma unroll
-    for (int a = 0; a < M; ++a) vel[(2 + a) * P + o0] = php[a];
+    for (int a = 0; a < M; ++a) p.php_out[a * P + o0] = php[a];
     if (consume) sp_out[o0] = o.s1;
     if (moments) write_moments<M>(moments, P, o0, o);
+}
+
+// Two steps of Case 1 per launch: the tiling of step2_kernel for the scalar
+// populations.  Shared memory holds, per R1 node, the 5m post-collision scalar
+// populations, phi(t) (the next step's phi(t - 1)) and S_1(t).  The prescribed
+// velocity is read from global memory at every node; phi is read from
+// p.php_in and written to p.php_out (different sets: the halo of one CTA is the
+// tile of another).  Bitwise equal to two launches of step_kernel_case1.
+template <int M>
+__global__ void __launch_bounds__(step2_max_threads(M)) step2_kernel_case1(const LbParams p, int TH,
+                                                                           const Planes<float> pl,
+                                                                           const float *sp_in, float *sp_out,
+                                                                           float *__restrict__ moments) {
+    constexpr int NS = 5 * M;  // scalar planes; then M planes of phi(t), then S_1(t)
+    extern __shared__ float sm[];
+    pdl_wait_and_release();
+    const int W1 = blockDim.x, H1 = TH + 2, SP = W1 * H1, TW = W1 - 2;
+    const int X0 = blockIdx.x * TW, Y0 = blockIdx.y * TH;
+    const long long P = p.plane;
+    const int pitch = p.pitch, nx = p.nx, ny = p.ny;
+    const bool consume = M >= 2 && p.skind == 2;
+    const int lx = threadIdx.x;
+    const int xu = X0 - 1 + lx;
+    const bool colv = xu <= min(X0 + TW, nx) && (p.periodic_x || (xu >= 0 && xu < nx));
+    const int gx = xu < 0 ? xu + nx : (xu >= nx ? xu - nx : xu);
+
+    // ---- step 1: R1 from global memory into shared memory
+    {
+        const auto mk = [pitch](int sx, int sy) { return sy * pitch + sx; };
+        const auto ld = [&pl](int plane, int off) { return __ldg(pl.in[plane] + off); };
+        for (int ly = threadIdx.y; ly < H1; ly += blockDim.y) {
+            const int yu = Y0 - 1 + ly;
+            const bool ok = colv && yu <= min(Y0 + TH, ny) && (p.periodic_y || (yu >= 0 && yu < ny));
+            const int gy = yu < 0 ? yu + ny : (yu >= ny ? yu - ny : yu);
+            if (!ok) continue;
+            float f[M][5];
+            pull_scalars<M, false>(p, gx, gy, mk, ld, f);
+            const int o0 = gy * pitch + gx, l0 = ly * W1 + lx;
+            const float ux = __ldg(p.vel + o0), uy = __ldg(p.vel + P + o0);
+            float php[M];
+#pragma unroll
+            for (int a = 0; a < M; ++a) php[a] = p.php_in[a * P + o0];
+            NodeOut<M> o;
+            collide_case1<M>(p, f, ux, uy, php, consume ? sp_in[o0] : 0.f, false, o);
+#pragma unroll
+            for (int a = 0; a < M; ++a)
+#pragma unroll
+                for (int i = 0; i < 5; ++i) sm[(5 * a + i) * SP + l0] = f[a][i];
+#pragma unroll
+            for (int a = 0; a < M; ++a) sm[(NS + a) * SP + l0] = php[a];
+            if (consume) sm[(NS + M) * SP + l0] = o.s1;
+        }
+    }
+    __syncthreads();
+
+    // ---- step 2: the tile from shared memory into global memory
+    const auto lds = [SP](int plane, int off) { return sm[(plane - 9) * SP + off]; };
+    const auto mk_gen = [W1, H1, X0, Y0, nx, ny](int sx, int sy) {
+        int a = sx - X0 + 1, b = sy - Y0 + 1;
+        a = a < 0 ? a + nx : (a >= W1 ? a - nx : a);
+        b = b < 0 ? b + ny : (b >= H1 ? b - ny : b);
+        return b * W1 + a;
+    };
+    for (int ly = 1 + threadIdx.y; ly <= TH; ly += blockDim.y) {
+        const int x = xu, y = Y0 - 1 + ly;
+        if (!(lx >= 1 && lx <= TW && x < nx && y < ny)) continue;
+        float f[M][5];
+        pull_scalars<M, false>(p, x, y, mk_gen, lds, f);
+        const int o0 = y * pitch + x, l0 = ly * W1 + lx;
+        const float ux = __ldg(p.vel + o0), uy = __ldg(p.vel + P + o0);
+        float php[M];
+#pragma unroll
+        for (int a = 0; a < M; ++a) php[a] = sm[(NS + a) * SP + l0];
+        NodeOut<M> o;
+        collide_case1<M>(p, f, ux, uy, php, consume ? sm[(NS + M) * SP + l0] : 0.f, false, o);
+#pragma unroll
+        for (int a = 0; a < M; ++a)
+#pragma unroll
+            for (int i = 0; i < 5; ++i) pl.out[9 + 5 * a + i][o0] = f[a][i];
+#pragma unroll
+        for (int a = 0; a < M; ++a) p.php_out[a * P + o0] = php[a];
+        if (consume) sp_out[o0] = o.s1;
+        if (moments) write_moments<M>(moments, P, o0, o);
+    }
 }
 
 // Case 1 initialisation: f = f^eq(phi0, u) collided once with phi(t - 1) = phi0
@@ -265,7 +349,7 @@ __global__ void init_kernel_case1(const LbParams p, const float *__restrict__ fi
     p.vel[o0] = ux;
     p.vel[P + o0] = uy;
 #pragma unroll
-    for (int a = 0; a < M; ++a) p.vel[(2 + a) * P + o0] = php[a];
+    for (int a = 0; a < M; ++a) p.php_out[a * P + o0] = php[a];
     if (M >= 2 && p.skind == 2) sprev[o0] = o.s1;
     write_moments<M>(moments, P, o0, o);
 }
@@ -761,10 +845,15 @@ cudaError_t launch_step2(const LbParams &p, const float *in, float *out, const f
         if (!attr_set[dev][MM].load()) {                                                                 \
             e = cudaFuncSetAttribute(step2_kernel<MM>, cudaFuncAttributeMaxDynamicSharedMemorySize,      \
                                      kStep2MaxSmem);                                                     \
+            if (e == cudaSuccess)                                                                        \
+                e = cudaFuncSetAttribute(step2_kernel_case1<MM>,                                         \
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, kStep2MaxSmem);    \
             if (e != cudaSuccess) return e;                                                              \
             attr_set[dev][MM].store(true);                                                               \
         }                                                                                                \
-        e = launch_pdl_smem(step2_kernel<MM>, grid, block, smem, s, p, th, pl, sp_in, sp_out, moments);   \
+        e = p.case1 ? launch_pdl_smem(step2_kernel_case1<MM>, grid, block, smem, s, p, th, pl, sp_in, sp_out,   \
+                                      moments)                                                           \
+                    : launch_pdl_smem(step2_kernel<MM>, grid, block, smem, s, p, th, pl, sp_in, sp_out, moments); \
         break;
         CDF_STEP2_CASE(1)
         CDF_STEP2_CASE(2)

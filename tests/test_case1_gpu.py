@@ -122,3 +122,33 @@ def test_translation_invariance_bitwise(cdf):
     b.step(60)
     Ma, Mb = a.moments(), np.roll(b.moments(), (-3, -16), axis=ax)
     assert np.array_equal(Ma, Mb)
+
+
+@pytest.mark.parametrize("shape", [None, (32, 8, 6), (64, 4, 9)])
+def test_two_step_launch_equals_one_step_bitwise(cdf, tmp_path, shape):
+    """Two Case-1 steps per launch (the scalar tiling of the two-step kernel;
+    phi(t - 1) in two sets that alternate with the buffers) against one step per
+    launch: bitwise equal on walls with Dirichlet sides, on a periodic box and on
+    ragged side pairs, for odd step counts and across a checkpoint."""
+    import os
+    cases = [I.cde_cellular(64, 48), I.cde_cellular(96, 40, walls=False, U0=0.08)]
+    cases += [_rand_problem(37, 21, 2, 11, xc, yc, force=False).replace(case1=True)
+              for xc, yc in (("mixed", "freeslip_dirichlet"), ("noslip_noflux", "periodic"))]
+    for pb in cases:
+        a = cdf.Solver(pb, temporal=1, resident=-1, temporal_shape=shape)
+        b = cdf.Solver(pb, temporal=-1, resident=-1, block=(128, 1))
+        assert a.info().temporal == 1 and b.info().temporal == 0
+        for n in (1, 2, 37, 64):
+            a.step(n)
+            b.step(n)
+        assert np.array_equal(a.moments(), b.moments())
+        fa, _, sa = a.populations()
+        fb, _, sb = b.populations()
+        assert np.array_equal(fa, fb) and np.array_equal(sa, sb)
+        path = os.path.join(tmp_path, "c1.bin")
+        a.save(path)
+        c = cdf.Solver(pb, temporal=1, resident=-1, temporal_shape=shape, init=False)
+        c.load(path)
+        c.step(33)
+        b.step(33)
+        assert np.array_equal(c.moments(), b.moments())
