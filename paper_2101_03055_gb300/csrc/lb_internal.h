@@ -63,6 +63,12 @@ struct Planes {
     const T *in[kMaxPlanes];
     T *out[kMaxPlanes];
 };
+// The FP32 moment planes (phi_0 .. phi_{m-1}, u_x, u_y, p) that 16-bit storage
+// keeps beside its populations, read (`in`) and written (`out`), one pointer each.
+struct MomentPlanes {
+    const float *in[kMaxM + 3];
+    float *out[kMaxM + 3];
+};
 
 // Launchers (lb_kernels.cu).  A step launch with block.y == 0 is flat: block.x
 // threads per CTA over the nx * ny nodes in row order (FP32 storage path).  `in`/`out` point at the first of `planes`

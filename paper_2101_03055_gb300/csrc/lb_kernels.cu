@@ -45,6 +45,16 @@ cudaError_t launch_pdl(void (*kern)(KArgs...), dim3 grid, dim3 block, cudaStream
     return launch_pdl_smem(kern, grid, block, 0, s, args...);
 }
 
+// One pointer per moment plane of the stacks `in` (read) and `out` (written).
+MomentPlanes moments_of(const LbParams &p, const float *in, float *out) {
+    MomentPlanes mp{};
+    for (int k = 0; k < p.m + 3; ++k) {
+        mp.in[k] = in + k * p.plane;
+        mp.out[k] = out + k * p.plane;
+    }
+    return mp;
+}
+
 // One pointer per population plane of the buffers `in` (read) and `out` (written).
 template <typename T>
 Planes<T> planes_of(const LbParams &p, const T *in, T *out) {
@@ -448,9 +458,8 @@ __device__ __forceinline__ float href_dir(int j, float pr, float ux, float uy) {
 // directions are compile-time constants, so the rebuilt equilibria need no
 // run-time direction selects.
 template <int M, typename T, bool kInterior>
-__device__ __forceinline__ void pull_node_mr(const LbParams &p, int x, int y, const T *__restrict__ in,
-                                             const float *__restrict__ min, float (&f)[M][5], float (&h)[9]) {
-    const long long P = p.plane;
+__device__ __forceinline__ void pull_node_mr(const LbParams &p, int x, int y, const Planes<T> &pl,
+                                             const MomentPlanes &mp, float (&f)[M][5], float (&h)[9]) {
     const int pitch = p.pitch;
     // Pull sources exactly as in step_kernel (the pressure-reference shifts are
     // zero here).
@@ -458,21 +467,20 @@ __device__ __forceinline__ void pull_node_mr(const LbParams &p, int x, int y, co
 
     // ---- loads: stored deviations and the source nodes' moments (the axis
     // sources of the fluid and of the scalars are the same nodes)
-    const float *mux = min + M * P, *muy = min + (M + 1) * P, *mpr = min + (M + 2) * P;
     float hu[9], hv[9], hp[9], hphi[9][M];
 #pragma unroll
     for (int i = 0; i < 9; ++i) {
-        h[i] = Store<T>::load(in + t.hplane[i] * P + t.hpos[i]);
-        hu[i] = __ldg(mux + t.hpos[i]);
-        hv[i] = __ldg(muy + t.hpos[i]);
-        hp[i] = __ldg(mpr + t.hpos[i]);
+        h[i] = Store<T>::load(pl.in[t.hplane[i]] + t.hpos[i]);
+        hu[i] = __ldg(mp.in[M] + t.hpos[i]);
+        hv[i] = __ldg(mp.in[M + 1] + t.hpos[i]);
+        hp[i] = __ldg(mp.in[M + 2] + t.hpos[i]);
 #pragma unroll
-        for (int a = 0; a < M; ++a) hphi[i][a] = __ldg(min + a * P + t.hpos[i]);
+        for (int a = 0; a < M; ++a) hphi[i][a] = __ldg(mp.in[a] + t.hpos[i]);
     }
 #pragma unroll
     for (int i = 0; i < 5; ++i)
 #pragma unroll
-        for (int a = 0; a < M; ++a) f[a][i] = Store<T>::load(in + (9 + 5 * a + t.splane[i]) * P + t.spos[i]);
+        for (int a = 0; a < M; ++a) f[a][i] = Store<T>::load(pl.in[9 + 5 * a + t.splane[i]] + t.spos[i]);
 
     // ---- rebuild the pre-collision populations
 #pragma unroll
@@ -495,34 +503,35 @@ __device__ __forceinline__ void pull_node_mr(const LbParams &p, int x, int y, co
 // Store of one node for 16-bit storage: deviations of the post-collision
 // populations from this node's new equilibrium, and its moments in FP32.
 template <int M, typename T>
-__device__ __forceinline__ void store_node_mr(const LbParams &p, int o0, T *__restrict__ out,
-                                              float *__restrict__ mout, const float (&f)[M][5],
-                                              const float (&h)[9], const NodeOut<M> &o) {
-    const long long P = p.plane;
+__device__ __forceinline__ void store_node_mr(int o0, const Planes<T> &pl, const MomentPlanes &mp,
+                                              const float (&f)[M][5], const float (&h)[9], const NodeOut<M> &o) {
     float feq[M][5];
     scalar_equilibrium<M>(o.phi, o.phi, o.ux, o.uy, feq);
 #pragma unroll
-    for (int i = 0; i < 9; ++i) Store<T>::store(out + i * P + o0, h[i] - href_dir(i, o.pr, o.ux, o.uy));
+    for (int i = 0; i < 9; ++i) Store<T>::store(pl.out[i] + o0, h[i] - href_dir(i, o.pr, o.ux, o.uy));
 #pragma unroll
     for (int a = 0; a < M; ++a)
 #pragma unroll
-        for (int i = 0; i < 5; ++i) Store<T>::store(out + (9 + 5 * a + i) * P + o0, f[a][i] - feq[a][i]);
-    write_moments<M>(mout, P, o0, o);
+        for (int i = 0; i < 5; ++i) Store<T>::store(pl.out[9 + 5 * a + i] + o0, f[a][i] - feq[a][i]);
+#pragma unroll
+    for (int a = 0; a < M; ++a) mp.out[a][o0] = o.phi[a];
+    mp.out[M][o0] = o.ux;
+    mp.out[M + 1][o0] = o.uy;
+    mp.out[M + 2][o0] = o.pr;
 }
 
 // One node of the 16-bit step.
 template <int M, typename T, bool kInterior>
-__device__ __forceinline__ void step_node_mr(const LbParams &p, int x, int y, const T *__restrict__ in,
-                                             const float *__restrict__ min, T *__restrict__ out,
-                                             float *__restrict__ mout, const float *sp_in, float *sp_out) {
+__device__ __forceinline__ void step_node_mr(const LbParams &p, int x, int y, const Planes<T> &pl,
+                                             const MomentPlanes &mp, const float *sp_in, float *sp_out) {
     const int o0 = y * p.pitch + x;
     float f[M][5], h[9];
-    pull_node_mr<M, T, kInterior>(p, x, y, in, min, f, h);
+    pull_node_mr<M, T, kInterior>(p, x, y, pl, mp, f, h);
     const bool consume = (M >= 2 && p.skind == 2);
     const float sp1 = consume ? sp_in[o0] : 0.f;
     NodeOut<M> o;
     collide<M>(p, f, h, 0.f, sp1, false, o);
-    store_node_mr<M, T>(p, o0, out, mout, f, h, o);
+    store_node_mr<M, T>(o0, pl, mp, f, h, o);
     if (consume) sp_out[o0] = o.s1;
 }
 
@@ -535,8 +544,7 @@ __device__ __forceinline__ void step_node_mr(const LbParams &p, int x, int y, co
 // launches by that saved rounding (both are held to the FP64 oracle).
 template <int M, typename T>
 __global__ void __launch_bounds__(step2_mr_max_threads(M), (M <= 2 ? 3 : 1)) step2_kernel_mr(
-    const LbParams p, int TH, const T *__restrict__ in, const float *__restrict__ mom_in, T *__restrict__ out,
-    float *__restrict__ mout, const float *sp_in, float *sp_out) {
+    const LbParams p, int TH, const Planes<T> pl, const MomentPlanes mp, const float *sp_in, float *sp_out) {
     constexpr int NP = 9 + 5 * M;
     extern __shared__ float sm[];
     pdl_wait_and_release();
@@ -558,10 +566,10 @@ __global__ void __launch_bounds__(step2_mr_max_threads(M), (M <= 2 ? 3 : 1)) ste
         float h[9], f[M][5];
         if (!__any_sync(0xffffffffu, general)) {
             if (!ok) continue;
-            pull_node_mr<M, T, true>(p, gx, gy, in, mom_in, f, h);
+            pull_node_mr<M, T, true>(p, gx, gy, pl, mp, f, h);
         } else {
             if (!ok) continue;
-            pull_node_mr<M, T, false>(p, gx, gy, in, mom_in, f, h);
+            pull_node_mr<M, T, false>(p, gx, gy, pl, mp, f, h);
         }
         const int o0 = gy * pitch + gx, l0 = ly * W1 + lx;
         NodeOut<M> o;
@@ -600,23 +608,23 @@ __global__ void __launch_bounds__(step2_mr_max_threads(M), (M <= 2 ? 3 : 1)) ste
         const int o0 = y * pitch + x;
         NodeOut<M> o;
         collide<M>(p, f, h, 0.f, consume ? sm[NP * SP + ly * W1 + lx] : 0.f, false, o);
-        store_node_mr<M, T>(p, o0, out, mout, f, h, o);
+        store_node_mr<M, T>(o0, pl, mp, f, h, o);
         if (consume) sp_out[o0] = o.s1;
     }
 }
 
 template <int M, typename T>
-__global__ void __launch_bounds__(256, (M <= 2 ? 3 : 1)) step_kernel_mr(const LbParams p, const T *__restrict__ in,
-                                                      const float *__restrict__ min, T *__restrict__ out,
-                                                      float *__restrict__ mout, const float *sp_in, float *sp_out) {
+__global__ void __launch_bounds__(256, (M <= 2 ? 3 : 1)) step_kernel_mr(const LbParams p, const Planes<T> pl,
+                                                                       const MomentPlanes mp, const float *sp_in,
+                                                                       float *sp_out) {
     pdl_wait_and_release();
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     const int y = blockIdx.y * blockDim.y + threadIdx.y;
     // warp-uniform interior path, as in step_kernel
     if (__all_sync(0xffffffffu, inner_node(p, x, y)))
-        step_node_mr<M, T, true>(p, x, y, in, min, out, mout, sp_in, sp_out);
+        step_node_mr<M, T, true>(p, x, y, pl, mp, sp_in, sp_out);
     else if (x < p.nx && y < p.ny)
-        step_node_mr<M, T, false>(p, x, y, in, min, out, mout, sp_in, sp_out);
+        step_node_mr<M, T, false>(p, x, y, pl, mp, sp_in, sp_out);
 }
 
 template <int M, typename T>
@@ -683,12 +691,14 @@ cudaError_t step_mr_dispatch(const LbParams &p, const void *in, const float *min
     dim3 grid((p.nx + block.x - 1) / block.x, (p.ny + block.y - 1) / block.y);
     const T *i = static_cast<const T *>(in);
     T *o = static_cast<T *>(out);
+    const Planes<T> pl = planes_of(p, i, o);
+    const MomentPlanes mp = moments_of(p, min, mout);
     cudaError_t e = cudaSuccess;
     switch (p.m) {
-        case 1: e = launch_pdl(step_kernel_mr<1, T>, grid, block, s, p, i, min, o, mout, sp_in, sp_out); break;
-        case 2: e = launch_pdl(step_kernel_mr<2, T>, grid, block, s, p, i, min, o, mout, sp_in, sp_out); break;
-        case 3: e = launch_pdl(step_kernel_mr<3, T>, grid, block, s, p, i, min, o, mout, sp_in, sp_out); break;
-        case 4: e = launch_pdl(step_kernel_mr<4, T>, grid, block, s, p, i, min, o, mout, sp_in, sp_out); break;
+        case 1: e = launch_pdl(step_kernel_mr<1, T>, grid, block, s, p, pl, mp, sp_in, sp_out); break;
+        case 2: e = launch_pdl(step_kernel_mr<2, T>, grid, block, s, p, pl, mp, sp_in, sp_out); break;
+        case 3: e = launch_pdl(step_kernel_mr<3, T>, grid, block, s, p, pl, mp, sp_in, sp_out); break;
+        case 4: e = launch_pdl(step_kernel_mr<4, T>, grid, block, s, p, pl, mp, sp_in, sp_out); break;
         default: return cudaErrorInvalidValue;
     }
     return e != cudaSuccess ? e : cudaGetLastError();
@@ -872,6 +882,8 @@ cudaError_t step2_mr_dispatch(const LbParams &p, const void *in, const float *mi
     dim3 grid((p.nx + block.x - 3) / (block.x - 2), (p.ny + th - 1) / th);
     const T *i = static_cast<const T *>(in);
     T *o = static_cast<T *>(out);
+    const Planes<T> pl = planes_of(p, i, o);
+    const MomentPlanes mp = moments_of(p, min, mout);
     static std::atomic<bool> attr_set[64][kMaxM + 1];
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
@@ -886,7 +898,7 @@ cudaError_t step2_mr_dispatch(const LbParams &p, const void *in, const float *mi
             if (e != cudaSuccess) return e;                                                              \
             attr_set[dev][MM].store(true);                                                               \
         }                                                                                                \
-        e = launch_pdl_smem(step2_kernel_mr<MM, T>, grid, block, smem, s, p, th, i, min, o, mout, sp_in, sp_out); \
+        e = launch_pdl_smem(step2_kernel_mr<MM, T>, grid, block, smem, s, p, th, pl, mp, sp_in, sp_out);  \
         break;
         CDF_STEP2MR_CASE(1)
         CDF_STEP2MR_CASE(2)
