@@ -184,9 +184,10 @@ class ClockSampler:
 class _Single:
     """Uniform view of the single-lattice solver for the timing loops."""
 
-    def __init__(self, lib, pb, storage, resident=0, block=None, temporal=0):
+    def __init__(self, lib, pb, storage, resident=0, block=None, temporal=0, temporal_shape=None):
         self.lib, self.pb = lib, pb
-        self.s = lib.Solver(pb, storage=storage, resident=resident, block=block, temporal=temporal)
+        self.s = lib.Solver(pb, storage=storage, resident=resident, block=block, temporal=temporal,
+                            temporal_shape=temporal_shape)
         info = self.s.info()
         self.nodes, self.bytes_per_lup, self.storage = pb.nodes, info.bytes_per_lup, info.storage
         self.block = [info.block_x, info.block_y]
@@ -471,6 +472,9 @@ def main():
                     help="tile-resident step: 0 = the autotuner decides, 1 = always, -1 = never")
     ap.add_argument("--temporal", type=int, default=0, choices=[-1, 0, 1],
                     help="two time steps per launch: 0 = the autotuner decides, 1 = always, -1 = never")
+    ap.add_argument("--temporal-shape", default=None,
+                    help="'X,Y,TH': CTA shape and output tile height of the two-step kernel (with --temporal 1); "
+                         "default: autotuned")
     ap.add_argument("--block", default=None,
                     help="CTA shape 'X,Y' of the single-lattice step (Y = 0: flat launch); default: autotuned")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -499,7 +503,8 @@ def main():
         runner = _Single3D(lib, wl, args.storage)
     else:
         block = tuple(int(v) for v in args.block.split(",")) if args.block else None
-        runner = _Single(lib, wl, args.storage, args.resident, block, args.temporal)
+        tshape = tuple(int(v) for v in args.temporal_shape.split(",")) if args.temporal_shape else None
+        runner = _Single(lib, wl, args.storage, args.resident, block, args.temporal, tshape)
     nodes = runner.nodes
     S = args.lb_steps
     if S is None:  # about 0.1 s of lattice updates at ~30 GLUPS per benchmark step
