@@ -566,9 +566,10 @@ def main():
         "metric": "MLUPS (lattice updates per second, millions)",
         "value": value, "unit": "MLUPS", "n_gpus": world, "steps": K, "warmup": W,
         "ms_per_step": t_ms / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": {0: "f32", 1: "f16", 2: "bf16"}[runner.storage] + " storage, f32 math",
+        "dtype": "f32",
         "data": "synthetic",
         "config": {"workload": args.workload, "description": describe(args.workload), "nodes": nodes,
+                   "storage": {0: "f32", 1: "f16", 2: "bf16"}[runner.storage] + " populations (arithmetic in f32)",
                    "m": runner.m, "lb_steps_per_step": S, "block": runner.block,
                    "l2": "flushed between benchmark steps (256 MiB write); the state is L2-resident "
                          "within a step" if nodes * runner.bytes_per_lup < 120e6 else
