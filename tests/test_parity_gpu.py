@@ -265,16 +265,18 @@ def test_interior_and_edge_paths_agree_bitwise(cdf, storage):
 
 
 def test_graph_batches_equal_single_steps(cdf):
+    """One call of 300 steps (a 256-step graph, a 32-step graph, 12 single
+    launches) against 300 calls of one step."""
     pb = I.chemotaxis_plume(70, 50, seed=5)
-    a, b = cdf.Solver(pb), cdf.Solver(pb)
-    a.step(100)
-    for _ in range(100):
+    a, b = cdf.Solver(pb, temporal=-1), cdf.Solver(pb, temporal=-1)
+    a.step(300)
+    for _ in range(300):
         b.step(1)
     assert np.array_equal(a.moments(), b.moments())
     fa, ha, sa = a.populations()
     fb, hb, sb = b.populations()
     assert np.array_equal(fa, fb) and np.array_equal(ha, hb) and np.array_equal(sa, sb)
-    assert a.t == b.t == 100
+    assert a.t == b.t == 300
 
 
 # ---------------------------------------------------------------------------

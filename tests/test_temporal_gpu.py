@@ -46,7 +46,7 @@ def assert_same(a, b):
 ], ids=["plume512x256", "plume128x64", "taylor_green64", "cavity128"])
 def test_two_step_launch_equals_one_step_kernel_bitwise(cdf, pb):
     a, b = pair(cdf, pb)
-    for n in (1, 2, 37, 64, 100):  # odd counts, graph batches and their remainders
+    for n in (1, 2, 37, 64, 100, 301):  # odd counts, short and long graph batches, remainders
         a.step(n)
         b.step(n)
     assert_same(a, b)
