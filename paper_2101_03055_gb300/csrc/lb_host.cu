@@ -529,7 +529,9 @@ cdf_status setup_pair(cdf_lb *h, const cdf_options *opt) {
 // for, never when refused or when the lattice does not fit, otherwise when it
 // measures faster than the graph-launched kernel with the autotuned block.
 cdf_status setup_resident(cdf_lb *h, const cdf_options *opt) {
-    if (h->storage != CDF_FP32 || opt->resident == -1 || h->P.case1) return CDF_OK;
+    // two steps per launch asked for explicitly excludes the resident step
+    if (h->storage != CDF_FP32 || opt->resident == -1 || h->P.case1 || (opt->temporal == 1 && opt->resident == 0))
+        return CDF_OK;
     if (!plan_resident(h->nx, h->ny, h->m, &h->rg)) {
         cudaGetLastError();
         if (opt->resident == 1) return fail(CDF_EINVAL, "the lattice does not fit the resident step");
