@@ -124,7 +124,8 @@ typedef struct {
                                           block_y = 0: flat launch of block_x threads (FP32) */
     int resident;                      /* tile-resident persistent step (FP32, lattices that fit
                                           in shared memory, about 150 k nodes for m = 2):
-                                          0 = used when the autotuner measures it faster,
+                                          0 = used when the autotuner measures it faster
+                                          (not considered with temporal = 1),
                                           1 = always (CDF_EINVAL if the lattice does not fit),
                                           -1 = never */
     double wait_timeout_s;             /* bound of every wait of the resident step; 0 = 1 s */
