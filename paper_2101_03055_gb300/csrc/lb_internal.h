@@ -70,7 +70,8 @@ struct MomentPlanes {
     float *out[kMaxM + 3];
 };
 
-// Launchers (lb_kernels.cu).  A step launch with block.y == 0 is flat: block.x
+// Launchers (lb_kernels.cu), FP32 storage (16-bit storage has the _mr
+// launchers below).  A step launch with block.y == 0 is flat: block.x
 // threads per CTA over the nx * ny nodes in row order (FP32 storage path).  `in`/`out` point at the first of `planes`
 // population planes; plane k starts at base + k * plane.  Planes are ordered
 // h_0..h_8, then f_{a,0..4} for a = 0..m-1.

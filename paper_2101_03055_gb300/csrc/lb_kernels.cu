@@ -826,12 +826,9 @@ cudaError_t export_dispatch(const LbParams &p, const void *in, float *dense, cud
 
 cudaError_t launch_step(const LbParams &p, int storage, const void *in, void *out, const float *sp_in, float *sp_out,
                         float *moments, dim3 block, cudaStream_t s) {
-    switch (storage) {
-        case kFP32: return step_dispatch<float>(p, in, out, sp_in, sp_out, moments, block, s);
-        case kFP16: return step_dispatch<__half>(p, in, out, sp_in, sp_out, moments, block, s);
-        case kBF16: return step_dispatch<__nv_bfloat16>(p, in, out, sp_in, sp_out, moments, block, s);
-    }
-    return cudaErrorInvalidValue;
+    // 16-bit storage runs the node-equilibrium kernels (launch_step_mr)
+    if (storage != kFP32) return cudaErrorInvalidValue;
+    return step_dispatch<float>(p, in, out, sp_in, sp_out, moments, block, s);
 }
 
 size_t step2_smem_bytes(int m, dim3 block, int th) {
@@ -925,21 +922,13 @@ cudaError_t launch_step2_mr(const LbParams &p, int storage, const void *in, cons
 
 cudaError_t launch_init(const LbParams &p, int storage, const float *fields, int fields_pitch,
                         void *out, float *sprev, float *moments, cudaStream_t s) {
-    switch (storage) {
-        case kFP32: return init_dispatch<float>(p, fields, fields_pitch, out, sprev, moments, s);
-        case kFP16: return init_dispatch<__half>(p, fields, fields_pitch, out, sprev, moments, s);
-        case kBF16: return init_dispatch<__nv_bfloat16>(p, fields, fields_pitch, out, sprev, moments, s);
-    }
-    return cudaErrorInvalidValue;
+    if (storage != kFP32) return cudaErrorInvalidValue;  // 16-bit: launch_init_mr
+    return init_dispatch<float>(p, fields, fields_pitch, out, sprev, moments, s);
 }
 
 cudaError_t launch_export(const LbParams &p, int storage, const void *in, float *dense, cudaStream_t s) {
-    switch (storage) {
-        case kFP32: return export_dispatch<float>(p, in, dense, s);
-        case kFP16: return export_dispatch<__half>(p, in, dense, s);
-        case kBF16: return export_dispatch<__nv_bfloat16>(p, in, dense, s);
-    }
-    return cudaErrorInvalidValue;
+    if (storage != kFP32) return cudaErrorInvalidValue;  // 16-bit: launch_export_mr
+    return export_dispatch<float>(p, in, dense, s);
 }
 
 cudaError_t launch_step_mr(const LbParams &p, int storage, const void *in, const float *moments_in, void *out,
