@@ -377,7 +377,7 @@ void drop_graphs(cdf_lb *h) {
 // through the path the steps run in (CUDA graphs of 32 launches): a short step
 // launched one by one from the host would time the host's launch rate.
 cdf_status autotune(cdf_lb *h) {
-    TuneKey key{h->nx, h->ny, h->m, h->storage, h->P.chemotaxis};
+    TuneKey key{h->nx, h->ny, h->m, h->storage * 2 + h->P.case1, h->P.chemotaxis};
     {
         std::lock_guard<std::mutex> lk(g_tune_mu);
         auto it = g_tune_cache.find(key);
@@ -450,7 +450,8 @@ cdf_status setup_pair(cdf_lb *h, const cdf_options *opt) {
         h->pair_th = opt->temporal_tile_y;
         return CDF_OK;
     }
-    PairKey key{h->nx, h->ny, h->m * 4 + h->storage, h->P.chemotaxis, h->P.periodic_x, h->P.periodic_y};
+    PairKey key{h->nx, h->ny, (h->m * 4 + h->storage) * 2 + h->P.case1, h->P.chemotaxis, h->P.periodic_x,
+                h->P.periodic_y};
     {
         std::lock_guard<std::mutex> lk(g_tune_mu);
         auto it = g_pair_cache.find(key);
@@ -552,7 +553,7 @@ cdf_status setup_resident(cdf_lb *h, const cdf_options *opt) {
     if (st != CDF_OK || opt->resident == 1) return st;
     // opt->resident == 0: keep the faster mode (the tuner runs on the zeroed
     // buffers; the state is set by the init calls afterwards)
-    TuneKey key{h->nx, h->ny, h->m, h->storage, h->P.chemotaxis};
+    TuneKey key{h->nx, h->ny, h->m, h->storage * 2 + h->P.case1, h->P.chemotaxis};
     bool use = false;
     bool cached = false;
     {
