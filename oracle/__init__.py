@@ -33,14 +33,25 @@ _SIDES = ("west", "east", "south", "north")
 
 
 def build(force: bool = False) -> str:
-    """Compile the oracle with the host C compiler (plain C99, -O2, single thread)."""
+    """Compile the oracle with the host C compiler (plain C99, -O2).  OpenMP is
+    compiled in when the compiler has it, for the all-cores CPU baseline only: the
+    oracle runs one thread unless set_threads asks for more, and its results do
+    not depend on the thread count."""
     with _lock:
         if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
             tmp = _LIB + f".tmp{os.getpid()}"
-            subprocess.run(["gcc", "-std=c99", "-O2", "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"],
-                           check=True)
+            base = ["gcc", "-std=c99", "-O2", "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"]
+            r = subprocess.run(base[:1] + ["-fopenmp"] + base[1:], capture_output=True)
+            if r.returncode != 0:
+                subprocess.run(base, check=True)
             os.replace(tmp, _LIB)
     return _LIB
+
+
+def set_threads(n: int) -> int:
+    """Threads of the oracle's node and row loops (n < 1: all cores); returns the
+    count in use (1 if the oracle was built without OpenMP)."""
+    return int(_load().orc_set_threads(int(n)))
 
 
 class _Params(ctypes.Structure):
@@ -55,7 +66,7 @@ class _Params(ctypes.Structure):
         ("nu", ctypes.c_double), ("rho0", ctypes.c_double), ("theta", ctypes.c_double),
         ("side_kind", ctypes.c_int * 4), ("fluid_bc", ctypes.c_int * 4),
         ("scalar_bc", (ctypes.c_int * MAX_M) * 4), ("value", (ctypes.c_double * MAX_M) * 4),
-        ("case1", ctypes.c_int),
+        ("case1", ctypes.c_int), ("varphi", ctypes.c_double),
     ]
 
 
@@ -78,6 +89,7 @@ def _bind(path):
     lib.orc_feq_scalar.argtypes = [ctypes.c_double] * 4 + [_DP]
     lib.orc_heq.argtypes = [ctypes.c_double] * 4 + [_DP]
     lib.orc_force_pop.argtypes = [ctypes.c_double] * 2 + [_DP]
+    lib.orc_force_pop_phi.argtypes = [ctypes.c_double] * 5 + [_DP]
     lib.orc_relaxation_matrix.argtypes = [ctypes.c_int, _DP, _DP]
     lib.orc_fluid_relaxation.restype = ctypes.c_double
     lib.orc_fluid_relaxation.argtypes = [ctypes.c_double]
@@ -87,6 +99,8 @@ def _bind(path):
     lib.orc_cutoff.restype = ctypes.c_double
     lib.orc_cutoff.argtypes = [ctypes.c_double] * 3 + [ctypes.c_int]
     lib.orc_closures.argtypes = [ctypes.POINTER(_Params), _DP, _DP, _DP, _DP]
+    lib.orc_set_threads.restype = ctypes.c_int
+    lib.orc_set_threads.argtypes = [ctypes.c_int]
     return lib
 
 
@@ -122,6 +136,7 @@ def params_from_problem(pb, theta: float = 0.0) -> _Params:
     P.g[0], P.g[1] = float(pb.g[0]), float(pb.g[1])
     P.F0, P.nu, P.rho0, P.theta = pb.F0, pb.nu, pb.rho0, theta
     P.case1 = int(getattr(pb, "case1", False))
+    P.varphi = float(getattr(pb, "varphi", 0.0))
     for s, name in enumerate(_SIDES):
         side = getattr(pb, name)
         P.side_kind[s] = {"periodic": 0, "wall": 1}[side.kind]
@@ -211,6 +226,13 @@ def force_pop(Fx, Fy, lib=None):
     return out
 
 
+def force_pop_phi(F, u, varphi, lib=None):
+    """Eq. force with its second-order part: F_i = W_i [c_i.F/cs^2 + varphi (uF + Fu):(c_i c_i - cs^2 I)/(2 cs^4)]."""
+    out = np.empty(9)
+    (lib or _load()).orc_force_pop_phi(F[0], F[1], u[0], u[1], varphi, _ptr(out))
+    return out
+
+
 def relaxation_matrix(D, lib=None):
     D = np.ascontiguousarray(D, np.float64)
     m = D.shape[0]
@@ -266,7 +288,7 @@ class Binding:
         raise AttributeError(name)
 
 
-_NODE_FUNCS = {"feq_scalar", "heq", "force_pop", "relaxation_matrix", "fluid_relaxation",
+_NODE_FUNCS = {"feq_scalar", "heq", "force_pop", "force_pop_phi", "relaxation_matrix", "fluid_relaxation",
                "aux_source", "cutoff", "closures"}
 
 

@@ -48,6 +48,9 @@
  *       d_t(phi_b u) = u (phi_b(t) - phi_b(t - 1));
  *     phi(t - 1) at t = 0 is phi0, so the first step has G = 0.
  */
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 #include <math.h>
 #include <stdlib.h>
 #include <string.h>
@@ -80,6 +83,7 @@ typedef struct {
     int scalar_bc[4][ORC_MAX_M];
     double value[4][ORC_MAX_M];
     int case1;              /* Case 1 of Sec. 2.1: prescribed steady velocity, no fluid */
+    double varphi;          /* the parameter of the second-order part of Eq. force (0 or 1) */
 } orc_params;
 
 /* ---- lattices (Eq. D2Q5 and Eq. D2Q9), c_hat = 1 ---------------------------- */
@@ -126,10 +130,18 @@ void orc_heq(double p, double ux, double uy, double rho0, double out[9]) {
     }
 }
 
-/* Eq. force with varphi = 0: F_i = W_i c_i.F / cs^2 */
-void orc_force_pop(double Fx, double Fy, double out[9]) {
-    for (int i = 0; i < 9; ++i) out[i] = Q9_W[i] * (Q9_CX[i] * Fx + Q9_CY[i] * Fy) / CS2;
+/* Eq. force: F_i = W_i [ c_i.F / cs^2 + varphi (uF + Fu):(c_i c_i - cs^2 I) / (2 cs^4) ],
+ * with (uF + Fu):(c_i c_i - cs^2 I) = 2 (c_i.u)(c_i.F) - 2 cs^2 u.F. */
+void orc_force_pop_phi(double Fx, double Fy, double ux, double uy, double varphi, double out[9]) {
+    for (int i = 0; i < 9; ++i) {
+        double cF = Q9_CX[i] * Fx + Q9_CY[i] * Fy, cu = Q9_CX[i] * ux + Q9_CY[i] * uy;
+        double uFFu_cc = 2.0 * cu * cF - 2.0 * CS2 * (ux * Fx + uy * Fy);
+        out[i] = Q9_W[i] * (cF / CS2 + varphi * uFFu_cc / (2.0 * CS2 * CS2));
+    }
 }
+
+/* Eq. force with varphi = 0: F_i = W_i c_i.F / cs^2 */
+void orc_force_pop(double Fx, double Fy, double out[9]) { orc_force_pop_phi(Fx, Fy, 0.0, 0.0, 0.0, out); }
 
 /* Gauss-Jordan inverse with partial pivoting of an n x n row-major matrix.
  * Returns 0 on success, -1 if singular. */
@@ -295,7 +307,12 @@ void orc_destroy(orc_sim *s) {
 long orc_time(const orc_sim *s) { return s->t; }
 
 /* Step 1 of the update: moments of one node's pre-collision populations
- * (Eq. sum-phi, sum-u, sum-p with varphi = 0) and the closures. */
+ * (Eq. sum-phi, sum-u, and the pressure of the appendix's derivation) and the
+ * closures.  The appendix obtains p from h_0 = h_0^eq + h_0^ne with
+ * h_0^ne = (1/omega - 1/2) F_0 and F_0 = -W_0 varphi u.F / cs^2, i.e.
+ * p = cs^2/(1 - W_0) [sum_{i!=0} h_i - W_0 u.u/(2 cs^2) - W_0 varphi (1/omega - 1/2) u.F / cs^2];
+ * the printed Eq. sum-p has the opposite sign and no W_0 on the varphi term, the
+ * appendix's last line the sign of the derivation and no W_0 (moot at varphi = 0). */
 static void node_moments(const orc_sim *s, long node, double *phi, double *u, double *p,
                          double *D, double *S, double *F) {
     const orc_params *P = &s->P;
@@ -323,7 +340,10 @@ static void node_moments(const orc_sim *s, long node, double *phi, double *u, do
     u[0] = jx + 0.5 * F[0];
     u[1] = jy + 0.5 * F[1];
     double uu = u[0] * u[0] + u[1] * u[1];
-    *p = CS2 / (1.0 - Q9_W[0]) * (sum_nonrest - Q9_W[0] * uu / (2.0 * CS2));
+    double uF = u[0] * F[0] + u[1] * F[1];
+    double omega_f = orc_fluid_relaxation(P->nu);
+    *p = CS2 / (1.0 - Q9_W[0]) *
+         ((sum_nonrest - Q9_W[0] * uu / (2.0 * CS2)) - Q9_W[0] * P->varphi * (1.0 / omega_f - 0.5) * uF / CS2);
 }
 
 /* Steps 1-4 for one node: writes the post-collision populations and updates S(t-1). */
@@ -366,7 +386,7 @@ static int node_collide(orc_sim *s, long node, double *fpost, double *hpost, int
     const double *h = s->h + node * 9;
     double heq[9], Fi[9];
     orc_heq(p, u[0], u[1], P->rho0, heq);
-    orc_force_pop(F[0], F[1], Fi);
+    orc_force_pop_phi(F[0], F[1], u[0], u[1], P->varphi, Fi);
     for (int i = 0; i < 9; ++i)
         hpost[i] = h[i] - omega_f * (h[i] - heq[i]) + (1.0 - 0.5 * omega_f) * Fi[i];
     return 0;
@@ -385,10 +405,31 @@ static int crossed_side_y(const orc_params *P, int ty) {
 }
 static int wrap(int v, int n) { return ((v % n) + n) % n; }
 
+/* Threads of the node and row loops of orc_step (1 unless orc_set_threads asks
+ * for more; only the timed CPU baseline does).  Every node's arithmetic is the
+ * same whatever the thread count, and the push writes every target slot once,
+ * so the results do not depend on it. */
+static int g_threads = 1;
+
+/* Sets the thread count (n < 1: all cores); returns the count in use (1 when the
+ * oracle was built without OpenMP). */
+int orc_set_threads(int n) {
+#ifdef _OPENMP
+    g_threads = n < 1 ? omp_get_num_procs() : n;
+#else
+    (void)n;
+    g_threads = 1;
+#endif
+    return g_threads;
+}
+
 /* Step 5: push every post-collision population along its link. */
 static void stream(orc_sim *s) {
     const orc_params *P = &s->P;
     int m = P->m, nx = P->nx, ny = P->ny;
+#ifdef _OPENMP
+#pragma omp parallel for num_threads(g_threads) schedule(static)
+#endif
     for (int y = 0; y < ny; ++y)
         for (int x = 0; x < nx; ++x) {
             long node = NODE(P, x, y);
@@ -458,7 +499,7 @@ int orc_init(orc_sim *s, const double *phi0, const double *u0, const double *p0)
         }
         double heq[9], Fi[9];
         orc_heq(p, ux, uy, P->rho0, heq);
-        orc_force_pop(F[0], F[1], Fi);
+        orc_force_pop_phi(F[0], F[1], ux, uy, P->varphi, Fi);
         for (int i = 0; i < 9; ++i) s->h[node * 9 + i] = heq[i] - 0.5 * Fi[i];
     }
     s->t = 0;
@@ -471,9 +512,13 @@ int orc_step(orc_sim *s, long nsteps) {
     long n = (long)P->nx * P->ny;
     int m = P->m;
     for (long it = 0; it < nsteps; ++it) {
+        int bad = 0;
+#ifdef _OPENMP
+#pragma omp parallel for num_threads(g_threads) schedule(static) reduction(| : bad)
+#endif
         for (long node = 0; node < n; ++node)
-            if (node_collide(s, node, s->fpost + node * m * 5, s->hpost + node * 9, 1) != 0)
-                return -1;
+            bad |= node_collide(s, node, s->fpost + node * m * 5, s->hpost + node * 9, 1) != 0;
+        if (bad) return -1;
         stream(s);
         double *t;
         t = s->f; s->f = s->fnew; s->fnew = t;

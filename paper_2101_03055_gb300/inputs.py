@@ -125,6 +125,7 @@ class Problem:
     p0: np.ndarray = None              # (ny, nx)
     steps: int = 0                     # nominal step count of the workload
     case1: bool = False                # Case 1 of Sec. 2.1: no fluid; u0 is a steady prescribed velocity
+    varphi: float = 0.0                # second-order part of Eq. force (0: the paper's experiments, 1: Case 2)
 
     def __post_init__(self):
         m = self.m

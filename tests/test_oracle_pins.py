@@ -79,6 +79,94 @@ def test_force_population_moments(oracle_mod):
     assert np.abs(np.einsum("ia,ib,i->ab", Q9, Q9, Fi)).max() < 1e-18
 
 
+def test_force_population_moments_with_varphi(oracle_mod):
+    """Eq. force with its second-order part (varphi = 1, Case 2 of the appendix):
+    sum F_i = 0, sum c F_i = F, sum c c F_i = varphi (uF + Fu) (Eq. momentNS)."""
+    r = np.random.default_rng(11)
+    for varphi in (0.0, 1.0, 0.5):
+        F, u = r.normal(size=2) * 1e-3, r.normal(size=2) * 0.05
+        Fi = oracle_mod.force_pop_phi(F, u, varphi)
+        assert abs(Fi.sum()) < 1e-17
+        np.testing.assert_allclose(Q9.T @ Fi, F, rtol=1e-12)
+        want = varphi * (np.outer(u, F) + np.outer(F, u))
+        np.testing.assert_allclose(np.einsum("ia,ib,i->ab", Q9, Q9, Fi), want, atol=1e-18)
+
+
+def _accelerated_box(oracle_mod, varphi, steps, F=(2e-4, 1e-4), nu=0.1):
+    m, n = 1, 4
+    side = I.periodic_side(m)
+    pb = I.Problem("accelerated", n, n, m, np.array([[0.05]]), nu, g=F, beta=np.zeros(1), phi_ref=np.ones(1),
+                   F0=1.0, west=side, east=side, south=side, north=side, phi0=np.ones((m, n, n)),
+                   u0=np.zeros((2, n, n)), p0=np.zeros((n, n)), varphi=varphi)
+    o = oracle_mod.OracleSim(pb)
+    o.step(steps)
+    return o
+
+
+def test_uniform_acceleration_nonequilibrium_stress(oracle_mod):
+    """The non-equilibrium momentum flux of Eq. cicihine-1 in a periodic box under a
+    uniform force (grad u = 0, u grows by F every step): with varphi = 1 (Case 2)
+    sum c c h^ne + (uF + Fu)/2 vanishes, with varphi = 0 (Case 1) sum c c h^ne =
+    -(uF + Fu)/omega up to O(|F|^2), in the deviatoric components.  h^ne = h -
+    h^eq(p, u) with u and p the moments of the pre-collision populations."""
+    nu, F = 0.1, np.array([2e-4, 1e-4])
+    w = oracle_mod.fluid_relaxation(nu)
+    for steps in (50, 400):
+        for varphi in (0.0, 1.0):
+            o = _accelerated_box(oracle_mod, varphi, steps, tuple(F), nu)
+            M = o.moments()
+            _, h, _ = o.state()
+            u, p = M[1:3, 0, 0], M[3, 0, 0]
+            np.testing.assert_allclose(u, F * steps, rtol=1e-12)  # exact acceleration
+            hne = h[:, 0, 0] - oracle_mod.heq(p, u[0], u[1], 1.0)
+            Pi = np.einsum("ia,ib,i->ab", Q9, Q9, hne)
+            uF = np.outer(u, F) + np.outer(F, u)
+            R = Pi + 0.5 * varphi * uF - (varphi - 1.0) / w * uF
+            # the deviatoric part (the isotropic part carries the box's O(Ma^2) pressure drift)
+            resid = np.array([R[0, 1], R[0, 0] - R[1, 1]])
+            bound = 1e-15 if varphi == 1.0 else 10 * float(F @ F)
+            assert np.abs(resid).max() < bound, (varphi, steps, resid)
+            assert np.abs(uF[0, 1]) > 100 * np.abs(resid).max()
+
+
+def test_pressure_recovers_appendix_construction(oracle_mod):
+    """The pressure of the appendix's derivation: populations built from its premises
+    -- h = h^eq(p, u) + h^ne with sum_i h^ne_i = 0, h^ne_0 = (1/omega - 1/2) F_0 (the
+    rest direction does not stream), sum_i c_i h^ne_i = -F/2 (Eq. sum-u) -- must
+    return p and u exactly for varphi = 0 and 1.  The printed Eq. sum-p (opposite sign,
+    no W_0) and the appendix's last line (no W_0) miss by O(u.F) when varphi = 1."""
+    r = np.random.default_rng(5)
+    nu = 0.07
+    w = oracle_mod.fluid_relaxation(nu)
+    side = I.periodic_side(1)
+    for varphi in (0.0, 1.0):
+        for _ in range(3):
+            F = r.normal(size=2) * 1e-2
+            u, p = r.normal(size=2) * 0.1, float(r.normal()) * 1e-2
+            pb = I.Problem("node", 1, 1, 1, np.array([[0.05]]), nu, g=tuple(F), beta=np.zeros(1), phi_ref=np.ones(1),
+                           F0=1.0, west=side, east=side, south=side, north=side, phi0=np.ones((1, 1, 1)),
+                           u0=np.zeros((2, 1, 1)), p0=np.zeros((1, 1)), varphi=varphi)
+            Fi = oracle_mod.force_pop_phi(F, u, varphi)
+            ne = np.zeros(9)
+            ne[0] = (1.0 / w - 0.5) * Fi[0]
+            ne[1:] = r.normal(size=8) * 1e-3
+            # impose sum_i ne_i = 0 and sum_i c_i ne_i = -F/2 with the axis directions 1..4
+            ne[1:] += -(ne.sum()) / 8.0
+            dj = -0.5 * F - Q9.T @ ne
+            ne[1] += 0.5 * dj[0]
+            ne[3] -= 0.5 * dj[0]
+            ne[2] += 0.5 * dj[1]
+            ne[4] -= 0.5 * dj[1]
+            assert abs(ne.sum()) < 1e-15 and np.abs(Q9.T @ ne + 0.5 * F).max() < 1e-15
+            h = oracle_mod.heq(p, u[0], u[1], 1.0) + ne
+            f = oracle_mod.feq_scalar(1.0, u[0], u[1]).reshape(1, 5, 1, 1)
+            o = oracle_mod.OracleSim(pb)
+            o.set_state(f, h.reshape(9, 1, 1), np.zeros((1, 1, 1)))
+            M = o.moments()
+            np.testing.assert_allclose(M[1:3, 0, 0], u, rtol=0, atol=1e-15)
+            assert abs(M[3, 0, 0] - p) < 1e-15, (varphi, M[3, 0, 0] - p)
+
+
 def test_auxiliary_source_moments(oracle_mod):
     """Eq. moment + Case 2: sum_i G_i = 0 and sum_i c_i G_{i,a} = (I - omega/2)(u S + phi F)."""
     r = _rng(3)
@@ -551,6 +639,15 @@ PLANTED = [
     ("Case 1: phi(t-1) never updated", "for (int a = 0; a < m; ++a) s->phiprev[node * m + a] = phi[a];", ";"),
     ("Case 1: sign of omega/2 in G", "a == b ? 1.0 - 0.5 * omega[a * m + b] : -0.5 * omega[a * m + b]",
      "a == b ? 1.0 + 0.5 * omega[a * m + b] : 0.5 * omega[a * m + b]"),
+    ("varphi part of the force dropped", "varphi * uFFu_cc / (2.0 * CS2 * CS2)", "0.0 * uFFu_cc"),
+    ("varphi part of the force without its trace term", "2.0 * cu * cF - 2.0 * CS2 * (ux * Fx + uy * Fy)",
+     "2.0 * cu * cF"),
+    ("pressure varphi term with the sign of Eq. sum-p", "- Q9_W[0] * P->varphi * (1.0 / omega_f - 0.5)",
+     "+ P->varphi * (1.0 / omega_f - 0.5)"),
+    ("pressure varphi term without W_0", "- Q9_W[0] * P->varphi * (1.0 / omega_f - 0.5)",
+     "- P->varphi * (1.0 / omega_f - 0.5)"),
+    ("varphi force ignores the velocity", "orc_force_pop_phi(F[0], F[1], u[0], u[1], P->varphi, Fi);",
+     "orc_force_pop_phi(F[0], F[1], 0.0, 0.0, P->varphi, Fi);"),
 ]
 
 
