@@ -93,12 +93,19 @@ typedef struct {
 } cdf_source;
 
 /* Body force F = g * (F0 + sum_a beta[a] * (phi_a - phi_ref[a])) (Eq. NS2;
- * Sec. 3.1: F = -Sc gamma n z; Sec. 3.2: F = Ra Pr (T + Nc C) z). */
+ * Sec. 3.1: F = -Sc gamma n z; Sec. 3.2: F = Ra Pr (T + Nc C) z).
+ * varphi is the parameter of Eq. force: 0 (the paper's experiments, Sec. 3)
+ * leaves F_i = W_i c_i.F / cs^2; varphi != 0 adds its second-order part
+ * W_i varphi (uF + Fu):(c_i c_i - cs^2 I) / (2 cs^4) and gives the pressure the
+ * correction of the appendix's derivation, -W_0 varphi (1/omega - 1/2) u.F / cs^2
+ * inside the bracket of Eq. sum-p (with W_0 and this sign; the printed Eq. sum-p
+ * differs, see the appendix).  varphi = 1 is Case 2 of the appendix. */
 typedef struct {
     double g[2];
     double beta[CDF_MAX_M];
     double phi_ref[CDF_MAX_M];
     double F0;
+    double varphi;
 } cdf_force;
 
 /* One side of the box (Sec. 3: anti-bounce-back for scalar Dirichlet values,
@@ -157,6 +164,17 @@ typedef struct {
                                           the output tile block_x - 2) and its output tile height;
                                           0 = autotuned.  CDF_EINVAL if it cannot run the lattice
                                           (periodic axes need nx >= block_x, ny >= tile_y + 2) */
+    int halo_rows;                     /* a slab of a lattice split along y (see "split lattice"
+                                          below): bit 0 set = row 0 is a halo row, bit 1 set = row
+                                          ny - 1 is.  A halo row is not updated by the step; it holds
+                                          the neighbouring slab's post-collision populations, written by
+                                          cdf_lb_halo_unpack between steps, and the reductions leave it
+                                          out.  FP32 storage, full model, one step per launch (resident
+                                          and temporal 0 or -1).  0 = a whole lattice */
+    int origin_y;                      /* slab: the row of the whole lattice that local row 0 is (-1:
+                                          the halo row below row 0 of a periodic axis); 0 otherwise */
+    int ny_global;                     /* slab: rows of the whole lattice, whose pressure reference the
+                                          slab keeps; 0 = ny (and 0 for a whole lattice) */
 } cdf_options;
 
 /* Facts about a handle (for benchmarks and tests). */
@@ -239,6 +257,63 @@ cdf_status cdf_lb_get_info(const cdf_lb *h, cdf_info *out);
  * step kernels run; for timing with events.  Borrowed, do not destroy. */
 void *cdf_lb_stream(const cdf_lb *h);
 
+/* ---- split lattice (slabs along y) ---------------------------------------------
+ * The update of a node reads only the previous step's post-collision populations
+ * of its nearest neighbours (Eqs. evolution12 and evolution3 with streaming,
+ * Sec. 2), so a lattice cut into slabs of whole rows advances exactly like the
+ * whole lattice when, before every step, each slab's halo row holds the
+ * populations that cross the cut from its neighbour: per node of the cut, the
+ * three D2Q9 and the m D2Q5 populations whose velocity points across it.  Every
+ * node then computes the same bits as in the whole lattice.  One process per GPU
+ * runs one slab (a cdf_lb created with options.halo_rows) and moves those rows
+ * with its collective library; cdf_split runs all the slabs on one device.
+ *
+ * cdf_lb_halo_pack copies the crossing populations of the slab's boundary row on
+ * `side` (0 = south, the first updated row; 1 = north, the last) into dev_buf,
+ * a device FP32 array [3 + m][nx]: the rows of h_4, h_7, h_8, f_{a,4} (south) or
+ * h_2, h_5, h_6, f_{a,2} (north).  cdf_lb_halo_unpack writes such an array, packed
+ * by the neighbour on that side, into the slab's halo row.  Both act on the
+ * current populations (after the last step), on the handle's stream order, and
+ * return CDF_EINVAL when the slab has no halo row on `side`.
+ *
+ * cdf_lb_snapshot keeps a copy of the current moments; cdf_lb_change_sums then
+ * gives the FP64 sums of the stop test over the slab's updated rows (3m + 5
+ * values, laid out as in cdf_moment_sums_static): summed over the slabs, they
+ * give the stop test of the whole lattice. */
+cdf_status cdf_lb_halo_pack(cdf_lb *h, int side, float *dev_buf);
+cdf_status cdf_lb_halo_unpack(cdf_lb *h, int side, const float *dev_buf);
+cdf_status cdf_lb_snapshot(cdf_lb *h);
+cdf_status cdf_lb_change_sums(cdf_lb *h, double *sums);
+
+/* A lattice split into `nslabs` slabs of nearly equal row counts, all on the
+ * current device, advanced with a halo exchange (pack, device copy, unpack)
+ * after every step: the single-device form of the one-slab-per-GPU decomposition.
+ * Arguments as cdf_lb_create (the whole lattice's grid, parameters and
+ * boundaries); the options apply to every slab (FP32 storage; halo_rows,
+ * origin_y and ny_global must be 0: the split sets them).  2 <= nslabs <= ny
+ * (ny >= 2 nslabs on a periodic y axis).  The results equal the whole lattice's
+ * bit for bit. */
+typedef struct cdf_split cdf_split;
+cdf_status cdf_split_create(const cdf_grid *grid, int m, const cdf_diffusion *diffusion, double nu,
+                            const cdf_source *source, const cdf_force *force, const cdf_boundaries *boundaries,
+                            const cdf_options *options, int nslabs, cdf_split **out);
+/* Initial state of the whole lattice from host FP64 moments (as cdf_lb_init_moments). */
+cdf_status cdf_split_init_moments(cdf_split *s, const double *phi, const double *u, const double *p);
+/* n steps of every slab, with the halo exchange after each. */
+cdf_status cdf_split_step(cdf_split *s, long long n);
+/* Moments of the whole lattice, [m+3][ny][nx] host FP64. */
+cdf_status cdf_split_moments(cdf_split *s, double *host_out);
+/* Scalar totals: each slab's FP64 sums (cdf_lb_mass), added in slab order. */
+cdf_status cdf_split_mass(cdf_split *s, double *sums);
+/* The stop test of cdf_lb_run_to_steady on the whole lattice, from the slabs'
+ * change sums added together. */
+cdf_status cdf_split_run_to_steady(cdf_split *s, double tol, long long check_every, long long max_steps,
+                                   long long *steps_taken, double *residual);
+/* Slab k: its handle (borrowed), the first row of the whole lattice it updates
+ * and the number of rows it updates. */
+cdf_status cdf_split_slab(const cdf_split *s, int k, cdf_lb **slab, int *y0, int *rows);
+void cdf_split_destroy(cdf_split *s);
+
 /* ---- batched solver --------------------------------------------------------
  * Many independent lattices of uneven size (a parameter sweep) advanced together,
  * in one of two modes chosen by measurement: a persistent kernel that schedules
@@ -319,11 +394,15 @@ void cdf_batch_destroy(cdf_batch *b);
  *   stream          cudaStream_t, NULL = legacy default stream
  * Allocates nothing: the block partials live in a file-scope device array of
  * 41,344 bytes (304 blocks x 17 sums) that every GPU loading the library holds
- * until exit.  Limits: 1 <= m <= 4, nx * ny < 2^31 (CDF_EINVAL beyond).  The
- * first call on each device looks up the array's device address
- * (cudaGetSymbolAddress) with that device current; make that first call before
- * any stream capture.  All calls share the array: calls that overlap on the
- * GPU race.  Returns after launching; dev_out is ready when `stream` is. */
+ * until exit.  Limits: 1 <= m <= 4, nx * ny < 2^31, current device index < 64
+ * (CDF_EINVAL beyond).  The first call on each device -- and the first call after
+ * that device's context was torn down and recreated (cudaDeviceReset) -- does a
+ * set-up with that device current: it looks up the array's device address
+ * (cudaGetSymbolAddress) and loads the reduction kernels' code, which under lazy
+ * module loading may allocate.  Make that first call at start-up, before the
+ * phase that must not allocate and before any stream capture.  All calls share
+ * the array: calls that overlap on the GPU race.  Returns after launching;
+ * dev_out is ready when `stream` is. */
 cdf_status cdf_moment_sums_static(const float *dev_fields, const float *dev_fields_old, int nx, int ny, int m,
                                   double *dev_out, void *stream);
 

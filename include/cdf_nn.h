@@ -34,9 +34,16 @@ cdf_nn_status cdf_nn_conv3x3_fwd(const void *x, const void *w, const float *bias
 cdf_nn_status cdf_nn_conv3x3_bwd_data(const void *dy, const void *w, void *dx, int N, int H, int W, int Cin, int Cout,
                                       void *stream);
 /* dw[co][t][ci] += sum_p dy[p][co] x[p + d(t)][ci] and db[co] += sum_p dy[p][co]
- * (FP32, accumulated: zero them first).  db may be NULL. */
+ * (FP32, accumulated: zero them first).  db may be NULL.  On the tensor-core path
+ * the pixels are split over the GPU, each split's partial sums go to `workspace`
+ * (device memory of at least cdf_nn_conv3x3_bwd_weight_workspace() bytes, owned by
+ * the caller, contents overwritten) and are added in a fixed order: the result is
+ * the same bits on every run.  The warp-level MMA path adds its partial sums
+ * atomically (order-dependent) and ignores the workspace. */
 cdf_nn_status cdf_nn_conv3x3_bwd_weight(const void *x, const void *dy, float *dw, float *db, int N, int H, int W,
-                                        int Cin, int Cout, void *stream);
+                                        int Cin, int Cout, void *workspace, long long workspace_bytes, void *stream);
+/* Bytes of workspace cdf_nn_conv3x3_bwd_weight needs for this shape; -1 for a bad shape. */
+long long cdf_nn_conv3x3_bwd_weight_workspace(int N, int H, int W, int Cin, int Cout);
 /* d[i] = 0 where y[i] <= 0 (ReLU backward through the layer's output y), n elements. */
 cdf_nn_status cdf_nn_relu_bwd(void *d, const void *y, long long n, void *stream);
 /* 2x2 average pooling [N][H][W][C] -> [N][H/2][W/2][C] and its backward (H, W even). */

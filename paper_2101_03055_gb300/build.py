@@ -19,7 +19,7 @@ OBJ = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libcdflb.so")
 HEADERS = [os.path.join(ROOT, "include", "cdf_lb.h"), os.path.join(ROOT, "include", "cdf_lb3d.h"),
            os.path.join(ROOT, "include", "cdf_nn.h"), os.path.join(CSRC, "lb_internal.h"), os.path.join(CSRC, "lb_device.cuh")]
-SOURCES = ["lb_kernels.cu", "lb_reduce.cu", "lb_host.cu", "lb_static.cu", "lb_batch.cu", "lb_resident.cu",
+SOURCES = ["lb_kernels.cu", "lb_reduce.cu", "lb_host.cu", "lb_static.cu", "lb_batch.cu", "lb_resident.cu", "lb_split.cu",
            "lb3d.cu", "nn_kernels.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-Wall",

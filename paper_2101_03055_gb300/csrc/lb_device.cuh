@@ -69,12 +69,16 @@ template <> struct Store<float> {
 // |d| in [1.5e-8, 16].
 constexpr float kHalfScale = 4096.f, kHalfUnscale = 1.f / 4096.f;
 template <> struct Store<__half> {
-    __device__ static float load(const __half *p) { return __half2float(__ldg(p)) * kHalfUnscale; }
-    __device__ static void store(__half *p, float v) { *p = __float2half_rn(v * kHalfScale); }
+    __device__ static __half encode(float v) { return __float2half_rn(v * kHalfScale); }
+    __device__ static float decode(__half q) { return __half2float(q) * kHalfUnscale; }
+    __device__ static float load(const __half *p) { return decode(__ldg(p)); }
+    __device__ static void store(__half *p, float v) { *p = encode(v); }
 };
 template <> struct Store<__nv_bfloat16> {
-    __device__ static float load(const __nv_bfloat16 *p) { return __bfloat162float(__ldg(p)); }
-    __device__ static void store(__nv_bfloat16 *p, float v) { *p = __float2bfloat16_rn(v); }
+    __device__ static __nv_bfloat16 encode(float v) { return __float2bfloat16_rn(v); }
+    __device__ static float decode(__nv_bfloat16 q) { return __bfloat162float(q); }
+    __device__ static float load(const __nv_bfloat16 *p) { return decode(__ldg(p)); }
+    __device__ static void store(__nv_bfloat16 *p, float v) { *p = encode(v); }
 };
 
 // Population load of the step.  A kernel that runs one step per launch reads
@@ -148,6 +152,15 @@ __device__ __forceinline__ float fluid_equilibrium(int i, float prd, float ux, f
     if (i == 0) return fmaf(-kC, prd, __fmul_rn(-kQ, usq));
     const float cu = kC9x(i) * ux + kC9y(i) * uy;
     return __fmul_rn(kA9(i), (prd + cu) + fmaf(__fmul_rn(1.5f, cu), cu, __fmul_rn(-0.5f, usq)));
+}
+
+// The second-order part of Eq. force per unit varphi, W_i (uF + Fu):(c_i c_i -
+// cs^2 I) / (2 cs^4): 3 W_i (3 (c_i.u)(c_i.F) - u.F) for i != 0 and, so that the
+// nine sum to zero with the exact-identity weights, -(3 - kC) u.F for i = 0.
+__device__ __forceinline__ float force2_dir(int i, float ux, float uy, float Fx, float Fy, float uF) {
+    if (i == 0) return __fmul_rn(-(3.f - kC), uF);
+    const float cu = kC9x(i) * ux + kC9y(i) * uy, cF = kC9x(i) * Fx + kC9y(i) * Fy;
+    return __fmul_rn(kA9(i), fmaf(__fmul_rn(3.f, cu), cF, -uF));
 }
 
 // Scalar moments of one node (Eq. sum-phi) and the closures of Sec. 3 that
@@ -251,7 +264,11 @@ __device__ __forceinline__ void collide(const LbParams &p, float (&f)[M][5], flo
     const float ux = fmaf(0.5f, Fx, jx), uy = fmaf(0.5f, Fy, jy);
     const float usq = usq_of(ux, uy);
     const float snr = ((h[1] + h[2]) + (h[3] + h[4])) + ((h[5] + h[6]) + (h[7] + h[8]));
-    const float prd = __fmul_rn(fmaf(-kQ, usq, snr), kInvC);
+    float prd = __fmul_rn(fmaf(-kQ, usq, snr), kInvC);
+    // varphi != 0 (a branch uniform over the launch): the appendix's pressure,
+    // p = (sum_{i!=0} h_i - kQ u.u - varphi (1/omega - 1/2) (W_0/cs^2) u.F) / kC
+    const float uF = fmaf(ux, Fx, __fmul_rn(uy, Fy));
+    if (p.varphi != 0.f) prd = __fmul_rn(fmaf(-p.varphi_p, uF, fmaf(-kQ, usq, snr)), kInvC);
 
     float om[M][M];
     relaxation_matrix<M>(p, s, om);
@@ -272,12 +289,14 @@ __device__ __forceinline__ void collide(const LbParams &p, float (&f)[M][5], flo
     }
     scalar_collide<M>(f, s, ux, uy, om, Jx, Jy);
 
-    // Eq. evolution3 with Eq. force (varphi = 0): F_i = 3 W_i c_i.F, weighted by (1 - omega_f / 2).
+    // Eq. evolution3 with Eq. force, weighted by (1 - omega_f / 2):
+    // F_i = 3 W_i c_i.F  +  varphi [3 W_i (3 (c_i.u)(c_i.F) - u.F)  (i != 0),  -(3 - kC) u.F  (i = 0)]
     const float wf = p.omega_f, fw = 1.f - 0.5f * wf;
 #pragma unroll
     for (int i = 0; i < 9; ++i) {
         const float heq = fluid_equilibrium(i, prd, ux, uy, usq);
-        const float Fi = kA9(i) * (kC9x(i) * Fx + kC9y(i) * Fy);
+        float Fi = kA9(i) * (kC9x(i) * Fx + kC9y(i) * Fy);
+        if (p.varphi != 0.f) Fi = fmaf(p.varphi, force2_dir(i, ux, uy, Fx, Fy, uF), Fi);
         h[i] = fmaf(fw, Fi, fmaf(-wf, h[i] - heq, h[i]));
     }
 #pragma unroll

@@ -147,6 +147,7 @@ struct cdf_lb {
     unsigned long long wait_ns = 1000000000ull;
     long long t = 0;
     bool initialised = false;
+    int halo = 0;  // slab of a split lattice: bit 0 south halo row (y = 0), bit 1 north (y = ny - 1)
 };
 
 namespace {
@@ -329,8 +330,12 @@ cdf_status run_steps(cdf_lb *h, long long n) {
     return CDF_OK;
 }
 
+// FP64 sums over the rows the step updates (a slab's halo rows belong to its
+// neighbour and are left out).
 cdf_status reduce(cdf_lb *h, const float *nw, const float *od, double *host_out) {
-    CK(launch_reduce(nw, od, h->nx, h->ny, h->pitch, h->plane, h->m, h->partials, h->red, h->s));
+    const long long off = (long long)h->P.row_lo * h->pitch;
+    CK(launch_reduce(nw + off, od ? od + off : nullptr, h->nx, h->P.row_hi - h->P.row_lo, h->pitch, h->plane,
+                     h->m, h->partials, h->red, h->s));
     const int nq = reduce_quantities(h->m);
     CK(cudaMemcpyAsync(h->red_host, h->red, nq * sizeof(double), cudaMemcpyDeviceToHost, h->s));
     cdf_status st = sync(h);
@@ -511,14 +516,15 @@ cdf_status setup_pair(cdf_lb *h, const cdf_options *opt) {
     h->cur = 0;
     h->t = 0;
     if (st != CDF_OK) return st;
-    choice.use = opt->temporal == 1 || best < t_single;
+    const bool prefer = best < t_single;
+    choice.use = opt->temporal == 1 || prefer;
     h->pair = choice.use;
     h->pair_block = choice.block;
     h->pair_th = choice.th;
     drop_graphs(h);
     {
         std::lock_guard<std::mutex> lk(g_tune_mu);
-        g_pair_cache[key] = PairChoice{best < t_single, choice.block, choice.th};
+        g_pair_cache[key] = PairChoice{prefer, choice.block, choice.th};
     }
     // the timing ran on the zeroed buffers; the init calls set the state
     CK(cudaMemsetAsync(h->sprev_pp[0], 0, (size_t)h->plane * 4, h->s));
@@ -669,6 +675,9 @@ cdf_status cdflb::build_params(const cdf_grid *grid, int m, const cdf_diffusion 
         P.phi_ref[a] = (float)phi_ref[a];
     }
     P.Fbase = (float)Fbase;
+    if (!std::isfinite(frc->varphi)) return fail(CDF_EINVAL, "varphi must be finite");
+    P.varphi = (float)frc->varphi;
+    P.varphi_p = (float)(frc->varphi * 3.0 * nu * 4.0 / 3.0);  // (1/omega_f - 1/2) = 3 nu, W_0 / cs^2 = 4/3
     // Reference pressure gradient of the fluid deviations; a linear reference
     // cannot wrap around a periodic axis, so it is used along walled axes only.
     P.gref[0] = bc->west.kind == CDF_BC_WALL ? (float)p_ref_grad[0] : 0.f;
@@ -679,6 +688,8 @@ cdf_status cdflb::build_params(const cdf_grid *grid, int m, const cdf_diffusion 
     }
     P.xc = 0.5f * (float)(grid->nx - 1);
     P.yc = 0.5f * (float)(grid->ny - 1);
+    P.row_lo = 0;
+    P.row_hi = grid->ny;
     P.rho0 = (float)rho0;
     P.periodic_x = bc->west.kind == CDF_BC_PERIODIC;
     P.periodic_y = bc->south.kind == CDF_BC_PERIODIC;
@@ -730,6 +741,20 @@ cdf_status cdf_lb_create(const cdf_grid *grid, int m, const cdf_diffusion *dif, 
     }
     if (opt->temporal == 1 && opt->resident == 1)
         return fail(CDF_EINVAL, "two steps per launch and the resident step exclude each other");
+    if (opt->halo_rows < 0 || opt->halo_rows > 3) return fail(CDF_EINVAL, "halo_rows must be 0..3");
+    if (opt->halo_rows) {
+        if (opt->storage != CDF_FP32 || opt->prescribed_velocity)
+            return fail(CDF_EINVAL, "a slab with halo rows runs the full model with FP32 storage");
+        if (opt->resident == 1 || opt->temporal == 1)
+            return fail(CDF_EINVAL, "a slab with halo rows runs one step per launch (resident = temporal = 0 or -1)");
+        const int halos = (opt->halo_rows & 1) + (opt->halo_rows >> 1);
+        if (grid->ny < halos + 1) return fail(CDF_EINVAL, "a slab needs at least one row besides its halo rows");
+        const int nyg = opt->ny_global > 0 ? opt->ny_global : grid->ny;
+        if (opt->origin_y < -1 || opt->origin_y + grid->ny - halos > nyg + 1)
+            return fail(CDF_EINVAL, "origin_y / ny_global do not place the slab inside the lattice");
+    } else if (opt->origin_y != 0 || opt->ny_global != 0) {
+        return fail(CDF_EINVAL, "origin_y and ny_global belong to a slab (halo_rows != 0)");
+    }
     LbParams P0{};
     const int align = opt->storage == CDF_FP32 ? 32 : 64;  // 128-byte rows
     const int pitch = grid->nx >= 1 ? (grid->nx + align - 1) / align * align : 0;
@@ -760,6 +785,15 @@ cdf_status cdf_lb_create(const cdf_grid *grid, int m, const cdf_diffusion *dif, 
 
     h->P = P0;
     h->P.case1 = opt->prescribed_velocity;
+    if (opt->halo_rows) {
+        // a slab: its halo rows are not updated, and its pressure reference is the
+        // whole lattice's (centre of ny_global rows, local row 0 at global origin_y)
+        h->P.row_lo = opt->halo_rows & 1 ? 1 : 0;
+        h->P.row_hi = opt->halo_rows & 2 ? h->ny - 1 : h->ny;
+        const int nyg = opt->ny_global > 0 ? opt->ny_global : h->ny;
+        h->P.yc = (float)(0.5 * (nyg - 1) - opt->origin_y);
+        h->halo = opt->halo_rows;
+    }
 
     DeviceGuard g(h->device);
     const size_t esz = elem_size(h->storage);
@@ -807,7 +841,8 @@ cdf_status cdf_lb_create(const cdf_grid *grid, int m, const cdf_diffusion *dif, 
         release(h);
         return st;
     }
-    if ((st = setup_pair(h, opt)) != CDF_OK || (st = setup_resident(h, opt)) != CDF_OK) {
+    // a slab runs one step per launch: its halo rows are refreshed between steps
+    if (!h->halo && ((st = setup_pair(h, opt)) != CDF_OK || (st = setup_resident(h, opt)) != CDF_OK)) {
         release(h);
         return st;
     }
@@ -958,6 +993,73 @@ cdf_status cdf_lb_mass(cdf_lb *h, double *sums) {
     double q[3 * kMaxM + 5];
     if ((st = reduce(h, current_moments(h), nullptr, q)) != CDF_OK) return st;
     for (int a = 0; a < h->m; ++a) sums[a] = q[a];
+    return leave(h);
+}
+
+// The planes that cross a cut, in buffer order: moving down (c_y = -1: h_4, h_7,
+// h_8, then f_{a,4}) or up (c_y = +1: h_2, h_5, h_6, then f_{a,2}).
+static int crossing_planes(int m, bool up, int *planes) {
+    const int hp[2][3] = {{4, 7, 8}, {2, 5, 6}};
+    int k = 0;
+    for (int j = 0; j < 3; ++j) planes[k++] = hp[up][j];
+    for (int a = 0; a < m; ++a) planes[k++] = 9 + 5 * a + (up ? 2 : 4);
+    return k;
+}
+
+// One halo transfer of a slab: pack (row -> buffer) or unpack (buffer -> row).
+static cdf_status halo_copy(cdf_lb *h, int side, float *buf, bool pack) {
+    if (!h || !buf) return fail(CDF_EINVAL, "NULL argument");
+    if (side != 0 && side != 1) return fail(CDF_EINVAL, "side must be 0 (south) or 1 (north)");
+    if (!((h->halo >> side) & 1)) return fail(CDF_EINVAL, "the slab has no halo row on that side");
+    if (!h->initialised) return fail(CDF_EINVAL, "state not initialised");
+    // south: send the first updated row down, receive the halo row from below (moving up);
+    // north: send the last updated row up, receive the halo row from above (moving down)
+    const bool up = pack ? side == 1 : side == 0;
+    const int row = pack ? (side == 0 ? h->P.row_lo : h->P.row_hi - 1) : (side == 0 ? 0 : h->ny - 1);
+    int planes[3 + kMaxM];
+    const int np = crossing_planes(h->m, up, planes);
+    DeviceGuard g(h->device);
+    cdf_status st = enter(h);
+    if (st != CDF_OK) return st;
+    float *pop = static_cast<float *>(h->buf[h->cur]);
+    for (int k = 0; k < np; ++k) {
+        float *r = pop + planes[k] * h->plane + (long long)row * h->pitch;
+        float *b = buf + (long long)k * h->nx;
+        CK(cudaMemcpyAsync(pack ? b : r, pack ? r : b, (size_t)h->nx * 4, cudaMemcpyDeviceToDevice, h->s));
+    }
+    return leave(h);
+}
+
+cdf_status cdf_lb_halo_pack(cdf_lb *h, int side, float *dev_buf) {
+    g_err[0] = 0;
+    return halo_copy(h, side, dev_buf, true);
+}
+
+cdf_status cdf_lb_halo_unpack(cdf_lb *h, int side, const float *dev_buf) {
+    g_err[0] = 0;
+    return halo_copy(h, side, const_cast<float *>(dev_buf), false);
+}
+
+cdf_status cdf_lb_snapshot(cdf_lb *h) {
+    g_err[0] = 0;
+    if (!h) return fail(CDF_EINVAL, "NULL handle");
+    if (!h->initialised) return fail(CDF_EINVAL, "state not initialised");
+    DeviceGuard g(h->device);
+    cdf_status st = enter(h);
+    if (st != CDF_OK) return st;
+    CK(cudaMemcpyAsync(h->mom_prev, current_moments(h), (size_t)(h->m + 3) * h->plane * 4,
+                       cudaMemcpyDeviceToDevice, h->s));
+    return leave(h);
+}
+
+cdf_status cdf_lb_change_sums(cdf_lb *h, double *sums) {
+    g_err[0] = 0;
+    if (!h || !sums) return fail(CDF_EINVAL, "NULL argument");
+    if (!h->initialised) return fail(CDF_EINVAL, "state not initialised");
+    DeviceGuard g(h->device);
+    cdf_status st = enter(h);
+    if (st != CDF_OK) return st;
+    if ((st = reduce(h, current_moments(h), h->mom_prev, sums)) != CDF_OK) return st;
     return leave(h);
 }
 

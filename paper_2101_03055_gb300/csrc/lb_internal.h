@@ -31,6 +31,9 @@ struct LbParams {
     float g[2];                 // F = g (Fbase + sum_a beta_a phi_a)
     float beta[kMaxM];
     float Fbase;
+    // Eq. force's second-order part (varphi != 0): varphi itself and the pressure
+    // correction's coefficient varphi (1/omega_f - 1/2) W_0 / cs^2
+    float varphi, varphi_p;
     float rho0;
     int periodic_x, periodic_y;
     int freeslip[4];            // per side (west, east, south, north)
@@ -50,6 +53,11 @@ struct LbParams {
     float *vel;
     const float *php_in;
     float *php_out;
+    // Rows the step updates, row_lo <= y < row_hi: all of them, except on a slab
+    // of a split lattice, whose halo rows (y = 0 and/or y = ny - 1) hold the
+    // neighbouring slab's post-collision populations and are written by the halo
+    // exchange instead.
+    int row_lo, row_hi;
 };
 
 enum Storage { kFP32 = 0, kFP16 = 1, kBF16 = 2 };
@@ -145,6 +153,9 @@ constexpr int kReduceBlocks = 304;  // 2 x 152 SMs
 int reduce_quantities(int m);
 cudaError_t launch_reduce(const float *mom_new, const float *mom_old, int nx, int ny, int pitch,
                           long long plane, int m, double *partials, double *out, cudaStream_t s);
+// Loads the code of every reduction kernel on the current device now instead of
+// at its first launch.
+cudaError_t preload_reduce_kernels();
 
 // Checks one lattice's parameter set and fills the kernel parameters.
 cdf_status build_params(const cdf_grid *grid, int m, const cdf_diffusion *dif, double nu, const cdf_source *src,

@@ -75,9 +75,10 @@ __global__ void __launch_bounds__(256) step_kernel(const LbParams p, const Plane
     const int y = blockIdx.y * blockDim.y + threadIdx.y;
     // Warp-uniform choice (every CTA holds whole warps): a warp whose 32 nodes
     // all lie inside the boundary ring runs the pull without boundary selects.
+    // (halo rows of a slab, y = 0 or ny - 1, are never inner nodes)
     if (__all_sync(0xffffffffu, inner_node(p, x, y)))
         step_node_planes<M, T, true>(p, x, y, pl, sp_in, sp_out, moments);
-    else if (x < p.nx && y < p.ny)
+    else if (x < p.nx && y >= p.row_lo && y < p.row_hi)
         step_node_planes<M, T>(p, x, y, pl, sp_in, sp_out, moments);
 }
 
@@ -91,7 +92,7 @@ __global__ void __launch_bounds__(256) step_kernel_flat(const LbParams p, const 
     const int y = idx / p.nx, x = idx - y * p.nx;
     if (__all_sync(0xffffffffu, valid && inner_node(p, x, y)))
         step_node_planes<M, T, true>(p, x, y, pl, sp_in, sp_out, moments);
-    else if (valid)
+    else if (valid && y >= p.row_lo && y < p.row_hi)
         step_node_planes<M, T>(p, x, y, pl, sp_in, sp_out, moments);
 }
 
@@ -390,10 +391,14 @@ __global__ void init_kernel(const LbParams p, const float *__restrict__ fields, 
     // f = f^eq(phi, u); h = h^eq(u, p) - F_i / 2 (moments then return the inputs)
     float f[M][5], h[9];
     const float usq = usq_of(ux, uy);
+    const float uF = fmaf(ux, Fx, __fmul_rn(uy, Fy));
     scalar_equilibrium<M>(phid, phi, ux, uy, f);
 #pragma unroll
-    for (int i = 0; i < 9; ++i)
-        h[i] = fluid_equilibrium(i, prd, ux, uy, usq) - 0.5f * kA9(i) * (kC9x(i) * Fx + kC9y(i) * Fy);
+    for (int i = 0; i < 9; ++i) {
+        float Fi = kA9(i) * (kC9x(i) * Fx + kC9y(i) * Fy);
+        if (p.varphi != 0.f) Fi = fmaf(p.varphi, force2_dir(i, ux, uy, Fx, Fy, uF), Fi);
+        h[i] = fluid_equilibrium(i, prd, ux, uy, usq) - 0.5f * Fi;
+    }
     NodeOut<M> o;
     collide<M>(p, f, h, prx, 0.f, true, o);
     store_node<M, T>(out, P, o0, f, h);
@@ -500,24 +505,75 @@ __device__ __forceinline__ void pull_node_mr(const LbParams &p, int x, int y, co
     }
 }
 
-// Store of one node for 16-bit storage: deviations of the post-collision
-// populations from this node's new equilibrium, and its moments in FP32.
+// Encoding of one node for 16-bit storage, conservative.  The deviations of the
+// post-collision populations from this node's equilibrium are rounded to 16 bits;
+// a receiver rebuilds each population as the rounded deviation plus the
+// equilibrium of the moments stored beside it.  Rounding alone would change the
+// scalar mass sum_i f*_i, the fluid momentum sum_i c_i h*_i and sum_{i!=0} h*_i
+// (the pressure sum of Eq. sum-p) that leave the node by the residuals e_i =
+// rounded - exact, a rounding-level source of mass and a body force that never
+// averages out at a steady state.  The residuals are therefore folded into the
+// FP32 moments that are stored and rebuilt from: with phi_s = phi - sum_i e_i,
+// u_s = u - sum_i c_i e_i and p_s chosen so that sum_{i!=0} h^eq_i(p_s, u_s)
+// absorbs the pressure residual, the rebuilt populations carry exactly (to FP32
+// rounding) the mass, momentum and pressure sum of the collision's output
+// (sum_i W_i (1 + 3 c_i.u) = 1, sum_i c_i h^eq_i(p, u) = u and
+// sum_{i!=0} h^eq_i(p, u) = kC p' + kQ u.u in these variables).  The scalar
+// deviations are taken from the equilibrium at u_s, the velocity the receivers
+// rebuild with, so the shift of u leaves the scalar fluxes alone.  The stored
+// moments differ from the collision's by the rounding residuals.
+template <int M, typename T>
+__device__ __forceinline__ void encode_node_mr(const float (&f)[M][5], const float (&h)[9], const NodeOut<M> &o,
+                                               T (&fq)[M][5], T (&hq)[9], float (&mom)[M + 3]) {
+    float rx = 0.f, ry = 0.f, rp = 0.f;
+#pragma unroll
+    for (int i = 0; i < 9; ++i) {
+        const float d = h[i] - href_dir(i, o.pr, o.ux, o.uy);
+        hq[i] = Store<T>::encode(d);
+        if (i != 0) {
+            const float e = Store<T>::decode(hq[i]) - d;  // exact (Sterbenz)
+            rx += kC9x(i) * e;
+            ry += kC9y(i) * e;
+            rp += e;
+        }
+    }
+    const float us = o.ux - rx, vs = o.uy - ry;
+    mom[M] = us;
+    mom[M + 1] = vs;
+    mom[M + 2] = o.pr + __fmul_rn(fmaf(kQ, usq_of(o.ux, o.uy) - usq_of(us, vs), -rp), kInvC);
+    // scalar deviations from the equilibrium at the stored velocity: the receivers
+    // rebuild with u_s, so taking it here keeps the shift of u out of the scalar fluxes
+    float feq[M][5];
+    scalar_equilibrium<M>(o.phi, o.phi, us, vs, feq);
+#pragma unroll
+    for (int a = 0; a < M; ++a) {
+        float r = 0.f;
+#pragma unroll
+        for (int i = 0; i < 5; ++i) {
+            const float d = f[a][i] - feq[a][i];
+            fq[a][i] = Store<T>::encode(d);
+            r += Store<T>::decode(fq[a][i]) - d;
+        }
+        mom[a] = o.phi[a] - r;
+    }
+}
+
+// Store of one node for 16-bit storage: the encoded deviations and the stored
+// moments of encode_node_mr.
 template <int M, typename T>
 __device__ __forceinline__ void store_node_mr(int o0, const Planes<T> &pl, const MomentPlanes &mp,
                                               const float (&f)[M][5], const float (&h)[9], const NodeOut<M> &o) {
-    float feq[M][5];
-    scalar_equilibrium<M>(o.phi, o.phi, o.ux, o.uy, feq);
+    T fq[M][5], hq[9];
+    float mom[M + 3];
+    encode_node_mr<M, T>(f, h, o, fq, hq, mom);
 #pragma unroll
-    for (int i = 0; i < 9; ++i) Store<T>::store(pl.out[i] + o0, h[i] - href_dir(i, o.pr, o.ux, o.uy));
+    for (int i = 0; i < 9; ++i) pl.out[i][o0] = hq[i];
 #pragma unroll
     for (int a = 0; a < M; ++a)
 #pragma unroll
-        for (int i = 0; i < 5; ++i) Store<T>::store(pl.out[9 + 5 * a + i] + o0, f[a][i] - feq[a][i]);
+        for (int i = 0; i < 5; ++i) pl.out[9 + 5 * a + i][o0] = fq[a][i];
 #pragma unroll
-    for (int a = 0; a < M; ++a) mp.out[a][o0] = o.phi[a];
-    mp.out[M][o0] = o.ux;
-    mp.out[M + 1][o0] = o.uy;
-    mp.out[M + 2][o0] = o.pr;
+    for (int k = 0; k < M + 3; ++k) mp.out[k][o0] = mom[k];
 }
 
 // One node of the 16-bit step.
@@ -644,21 +700,28 @@ __global__ void init_kernel_mr(const LbParams p, const float *__restrict__ field
     for (int a = 0; a < M; ++a) fm = fmaf(p.beta[a], phi[a], fm);
     const float Fx = p.g[0] * fm, Fy = p.g[1] * fm;
     float f[M][5], h[9];
+    const float uF = fmaf(ux, Fx, __fmul_rn(uy, Fy));
     scalar_equilibrium<M>(phi, phi, ux, uy, f);
 #pragma unroll
-    for (int i = 0; i < 9; ++i) h[i] = heq_dir(i, pr, ux, uy) - 0.5f * kA9(i) * (kC9x(i) * Fx + kC9y(i) * Fy);
+    for (int i = 0; i < 9; ++i) {
+        float Fi = kA9(i) * (kC9x(i) * Fx + kC9y(i) * Fy);
+        if (p.varphi != 0.f) Fi = fmaf(p.varphi, force2_dir(i, ux, uy, Fx, Fy, uF), Fi);
+        h[i] = heq_dir(i, pr, ux, uy) - 0.5f * Fi;
+    }
     NodeOut<M> o;
     collide<M>(p, f, h, 0.f, 0.f, true, o);
-    float feq[M][5];
-    scalar_equilibrium<M>(o.phi, o.phi, o.ux, o.uy, feq);
+    T fq[M][5], hq[9];
+    float mom[M + 3];
+    encode_node_mr<M, T>(f, h, o, fq, hq, mom);
 #pragma unroll
-    for (int i = 0; i < 9; ++i) Store<T>::store(out + i * P + o0, h[i] - href_dir(i, o.pr, o.ux, o.uy));
+    for (int i = 0; i < 9; ++i) out[i * P + o0] = hq[i];
 #pragma unroll
     for (int a = 0; a < M; ++a)
 #pragma unroll
-        for (int i = 0; i < 5; ++i) Store<T>::store(out + (9 + 5 * a + i) * P + o0, f[a][i] - feq[a][i]);
+        for (int i = 0; i < 5; ++i) out[(9 + 5 * a + i) * P + o0] = fq[a][i];
     if (M >= 2 && p.skind == 2) sprev[o0] = o.s1;
-    write_moments<M>(mout, P, o0, o);
+#pragma unroll
+    for (int k = 0; k < M + 3; ++k) mout[k * P + o0] = mom[k];
 }
 
 template <int M, typename T>

@@ -96,6 +96,22 @@ cudaError_t run(const float *nw, const float *od, int nx, int ny, int pitch, lon
 
 }  // namespace
 
+cudaError_t preload_reduce_kernels() {
+    // cudaFuncGetAttributes makes the runtime load each kernel's code now (under
+    // lazy module loading it would otherwise load, and may allocate, at the first
+    // launch)
+    cudaFuncAttributes a;
+    const void *fns[] = {(const void *)partial_kernel<1>, (const void *)partial_kernel<2>,
+                         (const void *)partial_kernel<3>, (const void *)partial_kernel<4>,
+                         (const void *)final_kernel<1>,   (const void *)final_kernel<2>,
+                         (const void *)final_kernel<3>,   (const void *)final_kernel<4>};
+    for (const void *f : fns) {
+        cudaError_t e = cudaFuncGetAttributes(&a, f);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
 cudaError_t launch_reduce(const float *mom_new, const float *mom_old, int nx, int ny, int pitch,
                           long long plane, int m, double *partials, double *out, cudaStream_t s) {
     static_assert(kMaxQ == 17, "reduction slots");

@@ -430,6 +430,235 @@ __global__ void __launch_bounds__(kThreads) conv3x3_wgrad_kernel(const __nv_bflo
 }
 
 // ---------------------------------------------------------------------------
+// 3x3 convolution, weight gradient, on the tcgen05 tensor cores with a
+// deterministic split over the pixels:
+//   dW[co][t][ci] = sum_p dY[p][co] X[p + d(t)][ci].
+// GEMM: M = 9 Cin rows m = t Cin + ci (tile 128), N = Cout (one tile, <= 256),
+// K = pixels in stages of 64, split over blockIdx.y into `splits` contiguous
+// pixel ranges.  Both operands are channel-contiguous in memory (NHWC) while the
+// MMA reads K-major tiles, so each thread stages an 8 x 8 block -- 8 rows (8
+// consecutive channels) x 8 pixels -- with eight 16-byte loads, transposes it in
+// registers and writes eight 16-byte K-major rows.  Each split writes its FP32
+// partial tile to the workspace; wgrad_reduce_kernel then adds the splits in a
+// fixed order (no atomics: the result is the same bits on every run).
+// ---------------------------------------------------------------------------
+// 8 x 8 BF16 transpose: in[k] holds channels 0..7 of pixel k; out[c] holds
+// pixels 0..7 of channel c.
+__device__ __forceinline__ void transpose8x8(const uint4 (&in)[8], uint4 (&out)[8]) {
+    const __nv_bfloat16 *e = reinterpret_cast<const __nv_bfloat16 *>(in);
+    __nv_bfloat16 *o = reinterpret_cast<__nv_bfloat16 *>(out);
+#pragma unroll
+    for (int c = 0; c < 8; ++c)
+#pragma unroll
+        for (int k = 0; k < 8; ++k) o[c * 8 + k] = e[k * 8 + c];
+}
+
+template <int BN>
+__global__ void __launch_bounds__(kTcThreads) conv3x3_wgrad_tc_kernel(const __nv_bfloat16 *__restrict__ x,
+                                                                      const __nv_bfloat16 *__restrict__ dy,
+                                                                      float *__restrict__ part, int N, int H, int Wd,
+                                                                      int Cin, int Cout, long long pix_per_split) {
+    constexpr int kCols = BN < 32 ? 32 : BN;
+    constexpr uint32_t kABytes = kTM * kTK * 2, kBBytes = BN * kTK * 2;
+    extern __shared__ __align__(128) unsigned char tc_smem[];
+    unsigned char *A = tc_smem;
+    unsigned char *B = tc_smem + 2 * kABytes;
+    __shared__ __align__(8) uint64_t mbar[2];
+    __shared__ uint32_t tmem_slot;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const long long P = (long long)N * H * Wd;
+    const int M = 9 * Cin, m0 = blockIdx.x * kTM, n0 = blockIdx.z * BN;
+    const long long pbeg = (long long)blockIdx.y * pix_per_split;
+    const long long pend = pbeg + pix_per_split < P ? pbeg + pix_per_split : P;
+    const int nst = (int)((pend - pbeg + kTK - 1) / kTK);
+
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_slot)),
+                     "r"(kCols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    if (tid == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&mbar[0])) : "memory");
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&mbar[1])) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = tmem_slot;
+
+    // this thread's A block: rows mg*8..+7 (one tap, 8 consecutive channels), pixels kg*8..+7
+    const int mg = tid >> 3, kg = tid & 7;
+    const int ma = m0 + mg * 8;
+    const bool arow_ok = ma < M;  // M is a multiple of 8 (Cin % 16 == 0)
+    const int tap = arow_ok ? ma / Cin : 0, ci = arow_ok ? ma - tap * Cin : 0;
+    const int ddy = tap / 3 - 1, ddx = tap % 3 - 1;
+    constexpr uint32_t idesc = mma_idesc(kTM, BN);
+    bool ok = true;
+    int last = -1;
+    for (int s = 0; s < nst && ok; ++s) {
+        const int buf = s & 1;
+        if (s >= 2) ok = mbar_wait(smem_u32(&mbar[buf]), (uint32_t)(((s - 2) >> 1) & 1));
+        if (!ok) break;
+        unsigned char *As = A + buf * kABytes, *Bs = B + buf * kBBytes;
+        const long long pk = pbeg + (long long)s * kTK + kg * 8;
+        // A: X at the tap-shifted pixels, 8 channels each (zero outside the image or range)
+        {
+            uint4 v[8], t[8];
+#pragma unroll
+            for (int k = 0; k < 8; ++k) {
+                v[k] = make_uint4(0, 0, 0, 0);
+                const long long p = pk + k;
+                if (arow_ok && p < pend) {
+                    const int n = (int)(p / ((long long)H * Wd));
+                    const int rem = (int)(p - (long long)n * H * Wd);
+                    const int yy = rem / Wd + ddy, xx = rem % Wd + ddx;
+                    if (yy >= 0 && yy < H && xx >= 0 && xx < Wd)
+                        v[k] = *reinterpret_cast<const uint4 *>(x + (((long long)n * H + yy) * Wd + xx) * Cin + ci);
+                }
+            }
+            transpose8x8(v, t);
+#pragma unroll
+            for (int c = 0; c < 8; ++c) *reinterpret_cast<uint4 *>(As + cm_offset(mg * 8 + c, kg * 8, kTM)) = t[c];
+        }
+        // B: dY rows of the same pixels, 8 output channels per block
+        for (int e = tid; e < (BN / 8) * 8; e += kTcThreads) {
+            const int ng = e >> 3, kb = e & 7;
+            const long long pb = pbeg + (long long)s * kTK + kb * 8;
+            uint4 v[8], t[8];
+#pragma unroll
+            for (int k = 0; k < 8; ++k) {
+                v[k] = make_uint4(0, 0, 0, 0);
+                if (pb + k < pend) v[k] = *reinterpret_cast<const uint4 *>(dy + (pb + k) * Cout + n0 + ng * 8);
+            }
+            transpose8x8(v, t);
+#pragma unroll
+            for (int c = 0; c < 8; ++c) *reinterpret_cast<uint4 *>(Bs + cm_offset(ng * 8 + c, kb * 8, BN)) = t[c];
+        }
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        __syncthreads();
+        if (tid == 0) {
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const uint32_t a0 = smem_u32(As), b0 = smem_u32(Bs);
+#pragma unroll
+            for (int j = 0; j < kTK / 16; ++j) {
+                const uint64_t ad = smem_desc(a0 + 2 * j * (kTM / 8) * 128, (kTM / 8) * 128, 128);
+                const uint64_t bd = smem_desc(b0 + 2 * j * (BN / 8) * 128, (BN / 8) * 128, 128);
+                const uint32_t acc = (s > 0 || j > 0) ? 1u : 0u;
+                asm volatile(
+                    "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+                    " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(tmem),
+                    "l"(ad), "l"(bd), "r"(idesc), "r"(acc)
+                    : "memory");
+            }
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                             smem_u32(&mbar[buf]))
+                         : "memory");
+        }
+        last = s;
+    }
+    if (last >= 0) ok = mbar_wait(smem_u32(&mbar[last & 1]), (uint32_t)((last >> 1) & 1)) && ok;
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    if (ok) {
+        // TMEM lane = tile row m; this split's partial tile into part[split][m][co]
+        // (a split without pixels writes zeros)
+        const int m = m0 + warp * 32 + lane;
+        float *row = part + ((long long)blockIdx.y * M + m) * Cout + n0;
+#pragma unroll
+        for (int c = 0; c < BN; c += 8) {
+            uint32_t r[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+            if (nst > 0) {
+                asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+                             : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+                               "=r"(r[7])
+                             : "r"(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c));
+                asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+            }
+            if (m < M) {
+                float4 *d = reinterpret_cast<float4 *>(row + c);
+                d[0] = make_float4(__uint_as_float(r[0]), __uint_as_float(r[1]), __uint_as_float(r[2]),
+                                   __uint_as_float(r[3]));
+                d[1] = make_float4(__uint_as_float(r[4]), __uint_as_float(r[5]), __uint_as_float(r[6]),
+                                   __uint_as_float(r[7]));
+            }
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kCols) : "memory");
+}
+
+// dW[co][m] += sum_{split = 0..splits-1} part[split][m][co], in that order.
+__global__ void wgrad_reduce_kernel(const float *__restrict__ part, float *__restrict__ dw, int M, int Cout,
+                                    int splits) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;  // i = co * M + m
+    if (i >= (long long)M * Cout) return;
+    const int co = (int)(i / M), m = (int)(i - (long long)co * M);
+    float acc = 0.f;
+    for (int z = 0; z < splits; ++z) acc += part[((long long)z * M + m) * Cout + co];
+    dw[i] += acc;
+}
+
+// Bias gradient with a fixed summation order: db[c] += sum_p dY[p][c], one block of
+// 256 threads per 8 channels, each thread a strided run of pixels, a tree in shared memory.
+__global__ void bias_grad_det_kernel(const __nv_bfloat16 *__restrict__ dy, float *__restrict__ db, long long P, int C) {
+    const int c0 = blockIdx.x * 8;
+    float s[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    for (long long p = threadIdx.x; p < P; p += blockDim.x) {
+        const uint4 v = *reinterpret_cast<const uint4 *>(dy + p * C + c0);
+        const __nv_bfloat16 *e = reinterpret_cast<const __nv_bfloat16 *>(&v);
+#pragma unroll
+        for (int q = 0; q < 8; ++q) s[q] += __bfloat162float(e[q]);
+    }
+    __shared__ float red[8][256];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) red[q][threadIdx.x] = s[q];
+    __syncthreads();
+    for (int st = blockDim.x / 2; st > 0; st >>= 1) {
+        if ((int)threadIdx.x < st)
+#pragma unroll
+            for (int q = 0; q < 8; ++q) red[q][threadIdx.x] += red[q][threadIdx.x + st];
+        __syncthreads();
+    }
+    if (threadIdx.x < 8) db[c0 + threadIdx.x] += red[threadIdx.x][0];
+}
+
+// The weight gradient's tiling: output-channel tile BN (the largest of 256, 128,
+// 64, 32 that divides Cout), pixel splits for about two CTAs per SM in all with at
+// least 16 stages of 64 pixels each, and the pixels per split (a multiple of 64;
+// no split is empty).
+struct WgradPlan {
+    int bn, splits;
+    long long per;
+};
+WgradPlan wgrad_plan(long long P, int Cin, int Cout) {
+    WgradPlan w;
+    w.bn = Cout % 256 == 0 ? 256 : (Cout % 128 == 0 ? 128 : (Cout % 64 == 0 ? 64 : 32));
+    const long long tiles = (long long)((9 * Cin + kTM - 1) / kTM) * (Cout / w.bn);
+    long long s = (304 + tiles - 1) / tiles;
+    const long long cap = (P + 16 * kTK - 1) / (16 * kTK);
+    if (s > cap) s = cap;
+    if (s < 1) s = 1;
+    w.per = ((P + s - 1) / s + kTK - 1) / kTK * kTK;
+    w.splits = (int)((P + w.per - 1) / w.per);
+    return w;
+}
+
+template <int BN>
+cudaError_t launch_wgrad_tc(const __nv_bfloat16 *x, const __nv_bfloat16 *dy, float *part, int N, int H, int W,
+                            int Cin, int Cout, const WgradPlan &w, cudaStream_t s) {
+    const size_t smem = 2 * (size_t)(kTM * kTK * 2) + 2 * (size_t)(BN * kTK * 2);
+    cudaError_t e = cudaFuncSetAttribute(conv3x3_wgrad_tc_kernel<BN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess) return e;
+    dim3 grid((unsigned)((9 * Cin + kTM - 1) / kTM), (unsigned)w.splits, (unsigned)(Cout / BN));
+    conv3x3_wgrad_tc_kernel<BN><<<grid, kTcThreads, smem, s>>>(x, dy, part, N, H, W, Cin, Cout, w.per);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
 // Small layers (one thread per element unless stated).
 // ---------------------------------------------------------------------------
 __global__ void bias_grad_kernel(const __nv_bfloat16 *__restrict__ dy, float *__restrict__ db, long long P, int C) {
@@ -675,19 +904,47 @@ cdf_nn_status cdf_nn_conv3x3_bwd_data(const void *dy, const void *w, void *dx, i
     return launched();
 }
 
+long long cdf_nn_conv3x3_bwd_weight_workspace(int N, int H, int W, int Cin, int Cout) {
+    if (N < 1 || H < 1 || W < 1 || Cin < 16 || Cin % 16 || Cout < 32 || Cout % 32) return -1;
+    const WgradPlan w = wgrad_plan((long long)N * H * W, Cin, Cout);
+    return (long long)w.splits * 9 * Cin * Cout * (long long)sizeof(float);
+}
+
 cdf_nn_status cdf_nn_conv3x3_bwd_weight(const void *x, const void *dy, float *dw, float *db, int N, int H, int W,
-                                        int Cin, int Cout, void *stream) {
+                                        int Cin, int Cout, void *workspace, long long workspace_bytes, void *stream) {
     if (!x || !dy || !dw || N < 1 || H < 1 || W < 1 || Cin % 16 || Cout % 32)
         return nn_fail("conv3x3_bwd_weight: bad arguments (Cin % 16, Cout % 32)");
     const long long P = (long long)N * H * W;
-    const long long per = 4096;
-    dim3 grid((unsigned)((Cout + kWBM - 1) / kWBM), 9 * (Cin / 16), (unsigned)((P + per - 1) / per));
     auto s = static_cast<cudaStream_t>(stream);
-    conv3x3_wgrad_kernel<<<grid, kThreads, 0, s>>>(static_cast<const __nv_bfloat16 *>(x),
-                                                   static_cast<const __nv_bfloat16 *>(dy), dw, N, H, W, Cin, Cout, per);
-    if (db) {
-        dim3 g2(Cout / 8, (unsigned)((P + 256 * 64 - 1) / (256 * 64)));
-        bias_grad_kernel<<<g2, 256, 0, s>>>(static_cast<const __nv_bfloat16 *>(dy), db, P, Cout);
+    const auto *xb = static_cast<const __nv_bfloat16 *>(x);
+    const auto *dyb = static_cast<const __nv_bfloat16 *>(dy);
+    if (g_use_tc) {
+        const long long need = cdf_nn_conv3x3_bwd_weight_workspace(N, H, W, Cin, Cout);
+        if (!workspace || workspace_bytes < need)
+            return nn_fail("conv3x3_bwd_weight: the workspace is missing or smaller than "
+                           "cdf_nn_conv3x3_bwd_weight_workspace()");
+        const WgradPlan w = wgrad_plan(P, Cin, Cout);
+        float *part = static_cast<float *>(workspace);
+        cudaError_t e;
+        switch (w.bn) {
+            case 256: e = launch_wgrad_tc<256>(xb, dyb, part, N, H, W, Cin, Cout, w, s); break;
+            case 128: e = launch_wgrad_tc<128>(xb, dyb, part, N, H, W, Cin, Cout, w, s); break;
+            case 64: e = launch_wgrad_tc<64>(xb, dyb, part, N, H, W, Cin, Cout, w, s); break;
+            default: e = launch_wgrad_tc<32>(xb, dyb, part, N, H, W, Cin, Cout, w, s); break;
+        }
+        if (e != cudaSuccess) { cudaGetLastError(); return nn_fail(cudaGetErrorString(e)); }
+        const long long n = 9LL * Cin * Cout;
+        wgrad_reduce_kernel<<<blocks_for(n), 256, 0, s>>>(part, dw, 9 * Cin, Cout, w.splits);
+        if (db) bias_grad_det_kernel<<<Cout / 8, 256, 0, s>>>(dyb, db, P, Cout);
+    } else {
+        // the warp-level MMA path: split-K partial sums added atomically (order-dependent)
+        const long long per = 4096;
+        dim3 grid((unsigned)((Cout + kWBM - 1) / kWBM), 9 * (Cin / 16), (unsigned)((P + per - 1) / per));
+        conv3x3_wgrad_kernel<<<grid, kThreads, 0, s>>>(xb, dyb, dw, N, H, W, Cin, Cout, per);
+        if (db) {
+            dim3 g2(Cout / 8, (unsigned)((P + 256 * 64 - 1) / (256 * 64)));
+            bias_grad_kernel<<<g2, 256, 0, s>>>(dyb, db, P, Cout);
+        }
     }
     return launched();
 }

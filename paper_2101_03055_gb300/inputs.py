@@ -25,6 +25,8 @@ spacing inside the wall):
     (Sec. 3.2): T = C = 1 on the west wall, 0 on the east wall, adiabatic top
     and bottom, no slip everywhere, D = alpha [[1, Df], [Sr/Le, 1/Le]],
     F = g (T + N C) along y.
+  * `chemotaxis_plume_regularised` -- the Sec. 3.1.2 example: regularised
+    cut-off, periodic sides, large Sc, n0 = 1 / 0.5 across a perturbed interface.
   * `chemotaxis_steady_strip` -- the x-homogeneous steady chemotaxis test of
     Sec. 3.1.1 on a periodic strip.
   * `fourier_box` -- periodic box with uniform flow and a single Fourier mode in
@@ -201,6 +203,33 @@ def chemotaxis_plume(nx: int = 512, ny: int = 256, seed: int = 0, chi: float = 0
                    chi=chi, c_star=c_star, skind="consumption", k=k, g=(0.0, -1.0),
                    beta=np.array([g, 0.0]), west=side, east=wall_side(m), south=wall_side(m),
                    north=top, phi0=phi0, steps=steps)
+
+
+def chemotaxis_plume_regularised(nx: int = 512, ny: int = 256, alpha: float = 5.0, beta: float = 5.0,
+                                 delta: float = 0.25, gamma: float = 418.0, Sc: float = 7700.0, nu: float = 0.5,
+                                 c_star: float = 0.3, steps: int = 200_000) -> Problem:
+    """The example of Sec. 3.1.2: alpha = 5, beta = 5, delta = 0.25, gamma = 418,
+    Sc = 7700, the regularised cut-off r(c) = (1 + (c - c*)/sqrt((c - c*)^2 + eps^2))/2
+    with eps = dx (= 1/H), periodic sides, no-flux no-slip bottom, free-slip top with
+    c = 1; n0 = 1 above y = 0.501 - 0.01 sin((x - 0.5) pi), 0.5 below, c0 = 1, u0 = 0
+    (x, y scaled by H).  Lattice: nu fixes D_n = nu / Sc (the paper's large Sc
+    forces a small D_n, as its dt = 1e-8 does), D_c = delta D_n, chi = alpha D_n,
+    k = beta D_n / H^2, g = Sc gamma D_n^2 / H^3 (the mapping of chemotaxis_plume)."""
+    m = 2
+    H = float(ny)
+    Dn = nu / Sc
+    k = beta * Dn / H ** 2
+    g = Sc * gamma * Dn ** 2 / H ** 3
+    x = (np.arange(nx) + 0.5) / H
+    y = (np.arange(ny) + 0.5) / H
+    X, Y = np.meshgrid(x, y)
+    n0 = np.where(Y > 0.501 - 0.01 * np.sin((X - 0.5) * np.pi), 1.0, 0.5)
+    phi0 = np.stack([n0, np.ones((ny, nx))])
+    top = wall_side(m, FREESLIP, [NOFLUX, DIRICHLET], [0.0, 1.0])
+    return Problem("chemotaxis_plume_regularised", nx, ny, m, np.diag([Dn, delta * Dn]), nu, dkind="chemotaxis",
+                   chi=alpha * Dn, c_star=c_star, eps=1.0 / H, r_regularised=True, skind="consumption", k=k,
+                   g=(0.0, -1.0), beta=np.array([g, 0.0]), west=periodic_side(m), east=periodic_side(m),
+                   south=wall_side(m), north=top, phi0=phi0, steps=steps)
 
 
 def chemotaxis_plume_sweep(count: int = 256, seed: int = 0, wmin: int = 128, wmax: int = 512,

@@ -47,7 +47,7 @@ class cdf_source(ctypes.Structure):
 
 class cdf_force(ctypes.Structure):
     _fields_ = [("g", ctypes.c_double * 2), ("beta", ctypes.c_double * MAX_M),
-                ("phi_ref", ctypes.c_double * MAX_M), ("F0", ctypes.c_double)]
+                ("phi_ref", ctypes.c_double * MAX_M), ("F0", ctypes.c_double), ("varphi", ctypes.c_double)]
 
 
 class cdf_side(ctypes.Structure):
@@ -66,7 +66,8 @@ class cdf_options(ctypes.Structure):
                 ("wait_timeout_s", ctypes.c_double), ("test_stall_tile", ctypes.c_int),
                 ("prescribed_velocity", ctypes.c_int), ("temporal", ctypes.c_int),
                 ("temporal_block_x", ctypes.c_int), ("temporal_block_y", ctypes.c_int),
-                ("temporal_tile_y", ctypes.c_int)]
+                ("temporal_tile_y", ctypes.c_int), ("halo_rows", ctypes.c_int), ("origin_y", ctypes.c_int),
+                ("ny_global", ctypes.c_int)]
 
 
 class cdf_info(ctypes.Structure):
@@ -144,6 +145,23 @@ SIGNATURES = {
     "cdf_lb_last_error": (ctypes.c_char_p, []),
     "cdf_moment_sums_static": (ctypes.c_int, [_FP, _FP, ctypes.c_int, ctypes.c_int, ctypes.c_int, _FP,
                                               ctypes.c_void_p]),
+    "cdf_lb_halo_pack": (ctypes.c_int, [_H, ctypes.c_int, _FP]),
+    "cdf_lb_halo_unpack": (ctypes.c_int, [_H, ctypes.c_int, _FP]),
+    "cdf_lb_snapshot": (ctypes.c_int, [_H]),
+    "cdf_lb_change_sums": (ctypes.c_int, [_H, _DP]),
+    "cdf_split_create": (ctypes.c_int, [ctypes.POINTER(cdf_grid), ctypes.c_int, ctypes.POINTER(cdf_diffusion),
+                                        ctypes.c_double, ctypes.POINTER(cdf_source), ctypes.POINTER(cdf_force),
+                                        ctypes.POINTER(cdf_boundaries), ctypes.POINTER(cdf_options), ctypes.c_int,
+                                        ctypes.POINTER(ctypes.c_void_p)]),
+    "cdf_split_init_moments": (ctypes.c_int, [_H, _DP, _DP, _DP]),
+    "cdf_split_step": (ctypes.c_int, [_H, ctypes.c_longlong]),
+    "cdf_split_moments": (ctypes.c_int, [_H, _DP]),
+    "cdf_split_mass": (ctypes.c_int, [_H, _DP]),
+    "cdf_split_run_to_steady": (ctypes.c_int, [_H, ctypes.c_double, ctypes.c_longlong, ctypes.c_longlong,
+                                               ctypes.POINTER(ctypes.c_longlong), _DP]),
+    "cdf_split_slab": (ctypes.c_int, [_H, ctypes.c_int, ctypes.POINTER(ctypes.c_void_p),
+                                      ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]),
+    "cdf_split_destroy": (None, [_H]),
     "cdf_batch_create": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(cdf_grid), ctypes.c_int,
                                         ctypes.POINTER(cdf_diffusion), _DP, ctypes.POINTER(cdf_source),
                                         ctypes.POINTER(cdf_force), ctypes.POINTER(cdf_boundaries), _DP, _DP,
@@ -277,6 +295,64 @@ def cdf_moment_sums_static(dev_fields: int, dev_fields_old: int, nx: int, ny: in
                                          nx, ny, m, ctypes.c_void_p(dev_out or None), ctypes.c_void_p(stream or None))
 
 
+def cdf_lb_halo_pack(h, side: int, dev_buf: int):
+    _check(load().cdf_lb_halo_pack(h, int(side), ctypes.c_void_p(dev_buf)))
+
+
+def cdf_lb_halo_unpack(h, side: int, dev_buf: int):
+    _check(load().cdf_lb_halo_unpack(h, int(side), ctypes.c_void_p(dev_buf)))
+
+
+def cdf_lb_snapshot(h):
+    _check(load().cdf_lb_snapshot(h))
+
+
+def cdf_lb_change_sums(h, out: np.ndarray):
+    _check(load().cdf_lb_change_sums(h, _dptr(out)))
+
+
+def cdf_split_create(grid, m, diffusion, nu, source, force, boundaries, options, nslabs):
+    h = ctypes.c_void_p()
+    _check(load().cdf_split_create(ctypes.byref(grid), m, ctypes.byref(diffusion), nu, ctypes.byref(source),
+                                   ctypes.byref(force), ctypes.byref(boundaries), ctypes.byref(options), int(nslabs),
+                                   ctypes.byref(h)))
+    return h
+
+
+def cdf_split_init_moments(h, phi, u, p=None):
+    _check(load().cdf_split_init_moments(h, _dptr(phi), _dptr(u), None if p is None else _dptr(p)))
+
+
+def cdf_split_step(h, n: int):
+    _check(load().cdf_split_step(h, int(n)))
+
+
+def cdf_split_moments(h, out: np.ndarray):
+    _check(load().cdf_split_moments(h, _dptr(out)))
+
+
+def cdf_split_mass(h, out: np.ndarray):
+    _check(load().cdf_split_mass(h, _dptr(out)))
+
+
+def cdf_split_run_to_steady(h, tol, check_every, max_steps):
+    steps = ctypes.c_longlong(0)
+    res = ctypes.c_double(0.0)
+    st = load().cdf_split_run_to_steady(h, tol, int(check_every), int(max_steps), ctypes.byref(steps),
+                                        ctypes.byref(res))
+    return st, steps.value, res.value
+
+
+def cdf_split_slab(h, k: int):
+    slab, y0, rows = ctypes.c_void_p(), ctypes.c_int(), ctypes.c_int()
+    _check(load().cdf_split_slab(h, int(k), ctypes.byref(slab), ctypes.byref(y0), ctypes.byref(rows)))
+    return slab, y0.value, rows.value
+
+
+def cdf_split_destroy(h):
+    load().cdf_split_destroy(h)
+
+
 # ---- problem description -> C structs ------------------------------------------------
 def structs_from_problem(pb: Problem, storage: str = "fp32", stream: int = 0, block=None, phi_ref=None,
                          p_ref_grad=None, resident: int = 0, wait_timeout_s: float = 0.0, test_stall_tile: int = 0,
@@ -297,6 +373,7 @@ def structs_from_problem(pb: Problem, storage: str = "fp32", stream: int = 0, bl
     frc = cdf_force()
     frc.g[0], frc.g[1] = float(pb.g[0]), float(pb.g[1])
     frc.F0 = pb.F0
+    frc.varphi = float(getattr(pb, "varphi", 0.0))
     for a in range(m):
         src.S[a] = float(pb.S[a])
         frc.beta[a] = float(pb.beta[a])
@@ -438,6 +515,58 @@ class Solver:
     @property
     def t(self) -> int:
         return self.info().t
+
+
+class SplitSolver:
+    """One lattice split into `nslabs` slabs along y on the current device, with
+    the halo exchange after every step (cdf_split_*); same results as Solver."""
+
+    def __init__(self, pb: Problem, nslabs: int, stream: int = 0, block=None, init: bool = True):
+        self.pb = pb
+        self.m, self.nx, self.ny = pb.m, pb.nx, pb.ny
+        grid, dif, src, frc, bc, opt = structs_from_problem(pb, "fp32", stream, block)
+        self.h = cdf_split_create(grid, pb.m, dif, pb.nu, src, frc, bc, opt, nslabs)
+        self.nslabs = nslabs
+        if init:
+            self.init_moments(pb.phi0, pb.u0, pb.p0)
+
+    def close(self):
+        if getattr(self, "h", None):
+            cdf_split_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def init_moments(self, phi, u, p=None):
+        cdf_split_init_moments(self.h, np.ascontiguousarray(phi, np.float64), np.ascontiguousarray(u, np.float64),
+                               None if p is None else np.ascontiguousarray(p, np.float64))
+
+    def step(self, n: int = 1):
+        cdf_split_step(self.h, n)
+
+    def moments(self) -> np.ndarray:
+        out = np.empty((self.m + 3, self.ny, self.nx))
+        cdf_split_moments(self.h, out)
+        return out
+
+    def mass(self) -> np.ndarray:
+        out = np.empty(self.m)
+        cdf_split_mass(self.h, out)
+        return out
+
+    def run_to_steady(self, tol: float, check_every: int = 1000, max_steps: int = 10 ** 7):
+        st, steps, res = cdf_split_run_to_steady(self.h, tol, check_every, max_steps)
+        if st not in (CDF_OK, CDF_ENOTCONVERGED):
+            _check(st)
+        return st == CDF_OK, steps, res
+
+    def slabs(self):
+        """[(y0, rows)] of the slabs."""
+        return [cdf_split_slab(self.h, k)[1:] for k in range(self.nslabs)]
 
 
 # ---- batched solver -------------------------------------------------------------------

@@ -24,7 +24,8 @@ from . import lib
 NN_SIGNATURES = {
     "cdf_nn_conv3x3_fwd": [ctypes.c_void_p] * 4 + [ctypes.c_int] * 6 + [ctypes.c_void_p],
     "cdf_nn_conv3x3_bwd_data": [ctypes.c_void_p] * 3 + [ctypes.c_int] * 5 + [ctypes.c_void_p],
-    "cdf_nn_conv3x3_bwd_weight": [ctypes.c_void_p] * 4 + [ctypes.c_int] * 5 + [ctypes.c_void_p],
+    "cdf_nn_conv3x3_bwd_weight": [ctypes.c_void_p] * 4 + [ctypes.c_int] * 5 + [ctypes.c_void_p, ctypes.c_longlong,
+                                                                              ctypes.c_void_p],
     "cdf_nn_relu_bwd": [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_longlong, ctypes.c_void_p],
     "cdf_nn_avgpool2_fwd": [ctypes.c_void_p] * 2 + [ctypes.c_int] * 4 + [ctypes.c_void_p],
     "cdf_nn_avgpool2_bwd": [ctypes.c_void_p] * 2 + [ctypes.c_int] * 4 + [ctypes.c_void_p],
@@ -38,7 +39,9 @@ NN_SIGNATURES = {
                                                                                          ctypes.c_void_p],
     "cdf_nn_set_tensor_path": [ctypes.c_int],
     "cdf_nn_error_flag": [ctypes.POINTER(ctypes.c_int)],
+    "cdf_nn_conv3x3_bwd_weight_workspace": [ctypes.c_int] * 5,
 }
+NN_RESTYPES = {"cdf_nn_conv3x3_bwd_weight_workspace": ctypes.c_longlong}
 _nn = None
 
 
@@ -49,7 +52,7 @@ def nn_lib():
         for name, args in NN_SIGNATURES.items():
             fn = getattr(L, name)
             fn.argtypes = args
-            fn.restype = ctypes.c_int
+            fn.restype = NN_RESTYPES.get(name, ctypes.c_int)
         L.cdf_nn_last_error.restype = ctypes.c_char_p
         _nn = L
     return _nn
@@ -101,10 +104,22 @@ def conv3x3_bwd_data(dy, w, Cin):
     return dx
 
 
+_workspace = {}
+
+
 def conv3x3_bwd_weight(x, dy, dw, db):
+    """Accumulates the weight and bias gradients; the split partial sums go to a
+    device workspace kept per device (grown to the largest shape seen)."""
+    import torch
     N, H, W, Cin = x.shape
     Cout = dy.shape[3]
-    _call("cdf_nn_conv3x3_bwd_weight", _p(x), _p(dy), _p(dw), _p(db), N, H, W, Cin, Cout, _stream())
+    need = int(nn_lib().cdf_nn_conv3x3_bwd_weight_workspace(N, H, W, Cin, Cout))
+    ws = _workspace.get(x.device)
+    if ws is None or ws.numel() * 4 < need:
+        ws = torch.empty((max(need, 4) + 3) // 4, dtype=torch.float32, device=x.device)
+        _workspace[x.device] = ws
+    _call("cdf_nn_conv3x3_bwd_weight", _p(x), _p(dy), _p(dw), _p(db), N, H, W, Cin, Cout, _p(ws),
+          ws.numel() * 4, _stream())
 
 
 def relu_bwd(d, y):
@@ -455,6 +470,52 @@ def warm_start_comparison(net: UNet, prms, n: int, eps_list=(1e-3, 1e-4), ref_st
         first, taken, last = _steps_to_reference(b, inits, refs, eps_list, check_every, max_steps)
         torch.cuda.synchronize()
         out[name] = dict(first=first, seconds=time.perf_counter() - t0, steps=taken, last_distance=last)
+    b.close()
+    return out
+
+
+def upsample_prediction(pred: np.ndarray, n: int) -> np.ndarray:
+    """Bilinear resampling of predictions [N, m, m, 4] on an m x m cell-centred grid to
+    n x n (the fields are dimensionless, so a network trained on one lattice size gives
+    the others their steady state up to its discretisation error)."""
+    import torch
+    import torch.nn.functional as Fn
+    t = torch.as_tensor(np.ascontiguousarray(pred.transpose(0, 3, 1, 2)), dtype=torch.float32)
+    up = Fn.interpolate(t, size=(n, n), mode="bilinear", align_corners=False)
+    return up.numpy().transpose(0, 2, 3, 1)
+
+
+def time_to_steady(net: UNet, prms, n: int, n_net: int = 64, tol: float = 1e-5, check_every: int = 10_000,
+                   max_steps: int = 4_000_000, velocity: str = "zero"):
+    """Lattice steps and GPU seconds to the stop test of Sec. 3.1.1 (the residual R of
+    cdf_lb_run_to_steady over `check_every` steps below `tol`) for n x n cavities of
+    the parameters `prms`, from rest and from the network's prediction (made on the
+    n_net x n_net lattice the network was trained on and resampled to n x n; the
+    fluid at rest by default, see moments_from_prediction).  Both starts run the
+    cases together in one batched solver.  Returns per start the steps at which each
+    case first met the test (-1: not within max_steps) and the seconds of the run."""
+    import time
+    import torch
+    x = torch.as_tensor(input_planes(n_net, prms)).cuda().to(torch.bfloat16)
+    pred = predict(net, x).float().cpu().numpy()
+    if n != n_net:
+        pred = upsample_prediction(pred, n)
+    pbs = [cavity(n, prm) for prm in prms]
+    f64 = lambda a: np.ascontiguousarray(a, np.float64)  # noqa: E731
+    starts = {"cold": [(f64(pb.phi0), f64(pb.u0), f64(pb.p0)) for pb in pbs], "warm": []}
+    for k, pb in enumerate(pbs):
+        M = moments_from_prediction(pred[k], pb, velocity)
+        starts["warm"].append((f64(M[:2]), f64(M[2:4]), f64(M[4])))
+    b = lib.BatchSolver(pbs, tile=(64, 4), mode=0, init=False)
+    out = {}
+    for name, inits in starts.items():
+        for k, (phi, u, p) in enumerate(inits):
+            lib.cdf_batch_init_moments(b.h, k, phi, u, p)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        taken, R, first = b.run_to_steady(tol, check_every, max_steps)
+        torch.cuda.synchronize()
+        out[name] = {"first": first, "seconds": time.perf_counter() - t0, "steps": taken, "R": R}
     b.close()
     return out
 

@@ -60,7 +60,8 @@ def test_conv_forward(S, path, N, H, W, Cin, Cout):
 
 
 @pytest.mark.parametrize("N,H,W,Cin,Cout", [(2, 9, 13, 16, 32), (1, 8, 8, 64, 64), (2, 5, 7, 96, 32),
-                                            (1, 4, 4, 384, 128), (2, 24, 20, 128, 64)])
+                                            (1, 4, 4, 384, 128), (2, 24, 20, 128, 64), (1, 16, 12, 128, 256),
+                                            (2, 64, 64, 32, 32), (1, 40, 40, 64, 512)])
 def test_conv_backward(S, path, N, H, W, Cin, Cout):
     sur, torch = S
     r = np.random.default_rng(N * 7 + Cin)
@@ -75,6 +76,24 @@ def test_conv_backward(S, path, N, H, W, Cin, Cout):
     dwr, dbr = R.conv3x3_bwd_weight(xr, dyr)
     assert rel(dw.cpu().numpy(), dwr) < 1e-5
     assert rel(db.cpu().numpy(), dbr) < 1e-5
+
+
+def test_weight_gradient_is_deterministic(S):
+    """The tensor-core weight gradient adds its pixel splits in a fixed order: two
+    calls on the same inputs give the same bits (the warp-level path adds atomically)."""
+    sur, torch = S
+    sur.set_tensor_path(True)
+    r = np.random.default_rng(3)
+    x, _ = bf(torch, r.normal(size=(4, 48, 40, 64)))
+    dy, _ = bf(torch, r.normal(size=(4, 48, 40, 128)))
+    outs = []
+    for _ in range(2):
+        dw = torch.zeros((128, 3, 3, 64), dtype=torch.float32, device="cuda")
+        db = torch.zeros(128, dtype=torch.float32, device="cuda")
+        sur.conv3x3_bwd_weight(x, dy, dw, db)
+        outs.append((dw.cpu().numpy(), db.cpu().numpy()))
+    assert np.array_equal(outs[0][0], outs[1][0]) and np.array_equal(outs[0][1], outs[1][1])
+    assert sur.tensor_error_flag() == 0
 
 
 def test_small_layers(S):

@@ -5,7 +5,7 @@ against sits to the FP64 one.
    the GPU and in the FP64 oracle, both from rest: the steady states agree to
    relative L2 <= 1e-4 in T, C, u_x and u_y with FP32 populations (so "within 1e-4
    of the long-run FP32 state" is within ~1e-4 of the FP64 steady state) and to
-   1e-3 with FP16/BF16 populations.
+   1e-3 with FP16/BF16 populations (one case with a measured floor, see below).
 2. A U-Net trained by this package's BF16 kernels on solver-generated steady
    states of 32^2 cavities starts held-out cases closer to their steady states
    and reaches relative L2 1e-4 in fewer lattice steps than a start from rest.
@@ -44,29 +44,40 @@ def fp64_steady(oracle_mod):
     return pb, cur, o.t
 
 
-@pytest.mark.parametrize("storage,tol,tol_u", [("fp32", 1e-4, 1e-4), ("fp16", 1e-3, 2e-2), ("bf16", 1e-3, 2e-1)])
-def test_gpu_steady_state_matches_fp64_oracle(cdf, fp64_steady, storage, tol, tol_u):
-    """The GPU run to its steady state against the FP64 steady state (relative L2): FP32
-    populations 1e-4 in T, C and u (measured 6.5e-7, 9.9e-7, 8.7e-6); 16-bit
-    populations 1e-3 in T and C (FP16 4.1e-5, BF16 4.6e-4), while their velocity misses
-    1e-3 at steady state (FP16 3.7e-3, BF16 7.1e-2, the vertical component worst: the
-    rounding of the stored non-equilibrium parts, largest in the thin vertical
-    boundary layers, acts on the slowly relaxing flow for 1e6 steps), so the velocity
-    is held to the bound tol_u and reported."""
+# (storage, temporal, bound on T and C, bound on u).  BF16 with two steps per
+# launch carries its measured velocity floor instead of 1e-3 (reading R24).
+STEADY_BOUNDS = [("fp32", 0, 1e-4, 1e-4), ("fp16", -1, 1e-3, 1e-3), ("bf16", -1, 1e-3, 1e-3),
+                 ("fp16", 1, 1e-3, 1e-3), ("bf16", 1, 1e-3, 1.6e-3)]
+
+
+@pytest.mark.parametrize("storage,temporal,tol,tol_u", STEADY_BOUNDS)
+def test_gpu_steady_state_matches_fp64_oracle(cdf, fp64_steady, storage, temporal, tol, tol_u):
+    """The GPU run to its steady state against the FP64 steady state (relative L2).
+    FP32 populations: 1e-4 in T, C and u (measured 6.8e-7, 1.1e-6, 8.7e-6).  16-bit
+    populations with the conservative encoding, one step per launch: 1e-3 in T, C
+    and u (measured FP16 2.0e-5, 5.0e-5, 5.7e-5; BF16 2.4e-4, 3.2e-4, 3.6e-4).  With
+    two steps per launch the state settles into a fixed point of the rounded update,
+    whose rounding error is one fixed pattern acting on the flow for the whole run
+    (one step per launch keeps jittering, and its rounding errors average out): FP16
+    stays within 1e-3 (5.8e-5, 7.1e-5, 1.5e-4), BF16 (unit roundoff 2^-9) leaves the
+    velocity 1.45e-3 from the FP64 steady state (T 7.2e-4, C 9.5e-4), which that case
+    asserts as its measured floor (1.6e-3)."""
     pb, ref, t_ref = fp64_steady
-    s = cdf.Solver(pb, storage=storage)
+    s = cdf.Solver(pb, storage=storage, temporal=temporal)
+    if temporal:
+        assert s.info().temporal == (1 if temporal == 1 else 0)
     ok, steps, R = s.run_to_steady(2e-7, 2000, 1_000_000)
     if storage == "fp32":
         assert ok or R < 5e-6, R
     # 16-bit storage: the rounding of every stored population leaves the state
-    # jittering around the steady state (change over 2000 steps ~1e-4), so the
-    # run goes the full million steps and the state there is compared
+    # jittering around the steady state, so the run goes the full million steps
+    # and the state there is compared
     M = s.moments()
     err = rel_fields(M, ref)
     # as in the parity tests, the velocity is compared as one vector field
     err_u = float(np.linalg.norm(M[2:4] - ref[2:4]) / np.linalg.norm(ref[2:4]))
-    print(f"{storage} steady (R={R:.1e}, {steps} steps) vs FP64 steady ({t_ref} steps): rel L2 T, C = {err[:2]}, "
-          f"u = {err_u:.3e} (u_x {err[2]:.2e}, u_y {err[3]:.2e})")
+    print(f"{storage} temporal={temporal} steady (R={R:.1e}, {steps} steps) vs FP64 steady ({t_ref} steps): "
+          f"rel L2 T, C = {err[:2]}, u = {err_u:.3e} (u_x {err[2]:.2e}, u_y {err[3]:.2e})")
     assert max(err[0], err[1]) < tol
     assert err_u < tol_u
 

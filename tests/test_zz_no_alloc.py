@@ -5,8 +5,10 @@ plug-ins whose host owns all device memory through its own pool, processes
 under a fixed memory quota).  cdf_moment_sums_static gives them the FP64
 moment sums of cdf_lb_mass with its scratch in a static device array.  This
 test calls it through the C ABI twice in a row, on two different states, and
-checks each result against the existing entry point cdf_lb_mass.  It lives in a
-file of its own that pytest collects last.
+checks each result against the existing entry point cdf_lb_mass, and that the
+second call leaves the device's free memory unchanged (the first call may load
+kernel code; that is the set-up the header asks callers to do at start-up).  It
+lives in a file of its own that pytest collects last.
 """
 import numpy as np
 import pytest
@@ -26,9 +28,13 @@ def test_static_sums_match_existing_entry_point_twice(cdf):
     for call in range(2):
         s.step(40 + 30 * call)
         s.moments_device(fields)
+        torch.cuda.synchronize()
+        free0 = torch.cuda.mem_get_info()[0]
         st = cdf.cdf_moment_sums_static(fields.data_ptr(), 0, pb.nx, pb.ny, m, out.data_ptr(), 0)
         assert st == cdf.CDF_OK, cdf.cdf_lb_last_error()
         torch.cuda.synchronize()
+        if call == 1:  # after the set-up of the first call nothing is allocated
+            assert torch.cuda.mem_get_info()[0] == free0
         got = out.cpu().numpy()
         np.testing.assert_allclose(got[:m], s.mass(), rtol=1e-12)  # same FP64 sums
         M = s.moments()
