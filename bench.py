@@ -1,34 +1,40 @@
 """Benchmark of the fused lattice Boltzmann step (MLUPS and HBM roofline fraction).
 
-Workload (default): the chemotaxis-plume configuration, 512 x 256 lattice,
-m = 2 (bacteria n, oxygen c), FP32 populations, no-slip side and bottom walls,
-free-slip top with c = 1, chemotactic cross term D_01 = -chi n r(c) with the
-step cut-off, consumption S_c = -k n r(c), buoyancy -g n, n0 = 1 + 0.01 N(0, 1).
-One benchmark step = `--lb-steps` lattice time steps (by default about 0.1 s
-of work: 20000 for this lattice) of the whole hot path; L2 is flushed (a
-256 MiB write) between benchmark steps.
+Workload (default): the batched parameter sweep, 256 chemotaxis-plume instances
+of uneven size (W ~ U{128..512}, H ~ U{64..256}, 13.2 M nodes in all), each with
+its own chi, oxygen diffusivity and gravity scale; m = 2 (bacteria n, oxygen c),
+FP32 populations, no-slip side and bottom walls, free-slip top with c = 1,
+chemotactic cross term D_01 = -chi n r(c) with the step cut-off, consumption
+S_c = -k n r(c), buoyancy -g n, n0 = 1 + 0.01 N(0, 1).  The state (2.6 GB) is far
+above L2, so the step is an HBM measurement.  One benchmark step = `--lb-steps`
+lattice time steps of every instance (by default about 0.1 s of work); L2 is
+flushed (a 256 MiB write) between benchmark steps.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--workload NAME]
 
-Under torchrun each rank advances its own independent instance (seed = rank):
+With N = 1 the same JSON line also carries `extra`: the single 512 x 256 plume
+(state in L2; its roofline is an effective figure, not an HBM one) and the
+1024 x 1024 double-diffusive cavity, each timed in the same run.
+
+Under torchrun each rank advances its own independent sweep (seed = rank):
 weak scaling with no data-path collective; the barrier and the max-over-ranks
 timing are the only collectives.  Rank 0 prints one JSON line.
 
 value   -- whole-job MLUPS from CUDA events on the library's stream over the
            timed region (inputs resident in HBM).
 e2e     -- the same metric through the C ABI with host buffers: every step
-           uploads the initial moments from host memory (cdf_lb_init_moments),
-           advances, and reads the moments back (cdf_lb_moments).
-roofline -- the step kernel: algorithmic bytes per launch (bytes per lattice
-           update x nodes) / average launch time, against the measured HBM
-           copy bandwidth.
-cpu_baseline -- the FP64 oracle on a bounded sample of the same workload on
-           the host cores (rank 0, N = 1 only).
-copy_pass -- context for the roofline: one pass of a plain device copy (torch's
-           copy kernel, 32 copies per CUDA graph, two buffers used in turn) of
-           as many bytes as one lattice step reads and writes; the time floor of
-           any one-pass-per-step kernel at this size, also when the state is
-           L2-resident.
+           uploads the initial moments from host memory, advances, and reads
+           the moments back.
+roofline -- the dominant kernel: the bytes it must move per launch (the state
+           read once and written once: bytes per lattice update x nodes, per
+           launch whatever the number of time steps the launch performs) over
+           its average launch time, against the measured HBM copy bandwidth.
+           A two-step launch moves those bytes once per two updates.
+cpu_baseline -- the FP64 oracle as it stands on a bounded sample of the same
+           workload on the host cores, with all cores (OpenMP over nodes and
+           rows) and with one thread (rank 0, N = 1 only).
+copy_pass -- context for the roofline: one pass of a plain device copy of as
+           many bytes as one lattice step reads and writes.
 """
 from __future__ import annotations
 
@@ -55,6 +61,8 @@ L2_FLUSH_BYTES = 256 << 20
 def workload(name: str, rank: int):
     if name == "chemotaxis_plume_512x256":
         return I.chemotaxis_plume(512, 256, seed=rank, chi=0.5)
+    if name == "chemotaxis_plume_regularised_512x256":
+        return I.chemotaxis_plume_regularised(512, 256)
     if name == "ddc_cavity_1024":
         return I.ddc_cavity(1024, Df=0.5, Sr=0.5)
     if name == "periodic_4096":
@@ -82,6 +90,9 @@ def describe(name: str) -> str:
     return {
         "chemotaxis_plume_512x256": "chemotaxis-fluid plume 512x256, m=2 (n, c), FP32, walls + free-slip top, "
                                     "chi=0.5 step cut-off, consumption, buoyancy; n0 = 1 + 0.01 N(0,1)",
+        "chemotaxis_plume_regularised_512x256": "chemotaxis-fluid plume of Sec. 3.1.2, 512x256: alpha=5, beta=5, "
+                                                "delta=0.25, gamma=418, Sc=7700, regularised cut-off (eps = dx), "
+                                                "periodic sides, n0 = 1 / 0.5 across a perturbed interface",
         "ddc_cavity_1024": "double-diffusive cavity 1024x1024 with Soret/Dufour (Df=Sr=0.5), Ra=1e5, Pr=0.7, Le=2, N=1",
         "periodic_4096": "periodic 4096x4096 cross-diffusion box (roofline grid)",
         "periodic_2048": "periodic 2048x2048 cross-diffusion box (profiling grid above L2)",
@@ -95,7 +106,8 @@ def describe(name: str) -> str:
         "cde_cellular_2048": "Case 1 cellular flow at 2048x2048 (profiling size above L2)",
         "batched_plume_sweep_64": "64 chemotaxis-plume instances of the 256-instance sweep (profiling size)",
         "batched_plume_sweep_256": "256 chemotaxis-plume instances, W~U{128..512} x H~U{64..256} (13.2 M nodes), "
-                                   "per-instance chi, D_c, gravity; one persistent launch per 32 steps",
+                                   "per-instance chi, D_c, gravity; execution mode (persistent kernel or graph of per-instance "
+                                   "chains of one- or two-step launches) and tiles picked by the autotuner",
     }[name]
 
 
@@ -120,10 +132,10 @@ def kernel_source_hash(files=KERNEL_SOURCES_2D) -> str:
     return h.hexdigest()[:16]
 
 
-def recorded_traffic(workload_name: str, kernel: str):
-    """DRAM bytes per launch of the dominant kernel from the committed ncu summary
-    (profiles/step_kernel_traffic.json), if it was taken on the current kernel
-    source for this workload and kernel; else None."""
+def recorded_profile(workload_name: str, kernel: str):
+    """The dominant kernel's ncu record for this workload (DRAM bytes per launch,
+    issue-active fraction) from profiles/step_kernel_traffic.json, if it was taken
+    on the current kernel source and for this kernel; else None."""
     path = os.path.join(ROOT, "profiles", "step_kernel_traffic.json")
     if not os.path.exists(path):
         return None
@@ -133,7 +145,7 @@ def recorded_traffic(workload_name: str, kernel: str):
     files = KERNEL_SOURCES_3D if "3d" in workload_name else KERNEL_SOURCES_2D
     if not e or e.get("kernel_hash") != kernel_source_hash(files) or not kernel.startswith(e.get("kernel", "?")):
         return None
-    return float(e["dram_bytes_per_launch"])
+    return e
 
 
 class ClockSampler:
@@ -219,6 +231,10 @@ class _Single:
         """Lattice steps per kernel launch inside step(n)."""
         return min(n, RESIDENT_MAX_STEPS) if self.resident else (2 if self.pair and n >= 2 else 1)
 
+    def updates_per_pass(self, n):
+        """Lattice updates per read + write of the state in global memory."""
+        return self.steps_per_launch(n)
+
     def launches(self, n):
         """Kernels of this package launched by step(n)."""
         if self.resident:
@@ -264,6 +280,9 @@ class _Single3D:
     def steps_per_launch(self, n):
         return 1
 
+    def updates_per_pass(self, n):
+        return 1
+
     def launches(self, n):
         return n
 
@@ -276,11 +295,11 @@ class _Single3D:
 
 
 class _Batch:
-    def __init__(self, lib, pbs, storage):
+    def __init__(self, lib, pbs, storage, mode=None, tile=None):
         if storage != "fp32":
             raise SystemExit("the batched solver stores FP32 populations")
         self.lib, self.pbs = lib, pbs
-        self.s = lib.BatchSolver(pbs)
+        self.s = lib.BatchSolver(pbs, mode=mode or 0, tile=tile) if tile else lib.BatchSolver(pbs)
         info = self.s.info()
         self.nodes, self.bytes_per_lup, self.storage = info.nodes, info.bytes_per_lup, 0
         self.block = [info.tile_x, info.tile_y]
@@ -306,6 +325,11 @@ class _Batch:
         one or two lattice steps of one instance, counted here per whole sweep step)."""
         return {1: 1, 2: 2 if n >= 2 else 1}.get(self.mode, min(n, self.spl))
 
+    def updates_per_pass(self, n):
+        """Updates per read + write of the state: the persistent kernel passes over
+        global memory every step; chains of two-step launches once per two steps."""
+        return 2 if (self.mode == 2 and n >= 2) else 1
+
     def launches(self, n):
         if self.mode == 1:
             return n * self.count
@@ -328,6 +352,105 @@ class _Batch:
             self.lib.cdf_batch_moments(self.s.h, k, out)
             nbytes += 2 * (pb.m + 3) * pb.nodes * 4
         return nbytes
+
+
+class _Slab:
+    """One rank's slab of a single lattice split along y (paper_2101_03055_gb300.slab):
+    one step per launch and a halo exchange with the neighbouring ranks (NCCL
+    send/recv of the crossing rows) after every step.  `nodes` counts the whole
+    lattice: the job advances one lattice together (strong scaling)."""
+
+    def __init__(self, lib, pb, storage, rank, world):
+        if storage != "fp32":
+            raise SystemExit("a split lattice stores FP32 populations")
+        import torch
+        from paper_2101_03055_gb300 import slab
+        self.lib, self.pb = lib, pb
+        self.s = slab.SlabSolver(pb, rank, world)
+        info = lib.cdf_lb_get_info(self.s.h)
+        self.nodes, self.bytes_per_lup, self.storage = pb.nodes, info.bytes_per_lup, 0
+        self.block = [info.block_x, info.block_y]
+        self.m = pb.m
+        self.local_nodes = pb.nx * self.s.plan.rows
+        self.kernel = (f"step_kernel_flat<{pb.m},float>" if info.block_y == 0 else f"step_kernel<{pb.m},float>") + \
+            f" (slab of {self.s.plan.rows} of {pb.ny} rows, halo exchange after every step)"
+        self._stream = torch.cuda.current_stream().cuda_stream
+
+    stream = property(lambda self: self._stream)
+
+    def step(self, n):
+        self.s.step(n)
+
+    def steps_per_launch(self, n):
+        return 1
+
+    def updates_per_pass(self, n):
+        return 1
+
+    def launches(self, n):
+        return n
+
+    def e2e_step(self, n):
+        from paper_2101_03055_gb300 import slab
+        pb, p = self.pb, self.s.plan
+        rows = lambda f: slab.local_rows(f, p, pb.ny)  # noqa: E731
+        self.lib.cdf_lb_init_moments(self.s.h, rows(pb.phi0), rows(pb.u0), None if pb.p0 is None else rows(pb.p0))
+        self.s.exchange()
+        self.s.step(n)
+        self.s.moments()
+        return 2 * (pb.m + 3) * pb.nx * p.lny * 4
+
+
+def conv_line(N, H, W, Cin, Cout, reps, device, peak_tflops, peak_gbs):
+    """The surrogate's 3x3 convolution (forward, bias + ReLU; tcgen05 path) on one
+    layer shape: TFLOP/s from CUDA events over `reps` back-to-back launches, against
+    the measured BF16 tensor peak, and the bytes it moves (input, weights, output)
+    against the HBM copy bandwidth."""
+    import torch
+    from paper_2101_03055_gb300 import surrogate as sur
+    g = torch.Generator(device="cpu").manual_seed(N * 131 + Cin)
+    x = torch.randn((N, H, W, Cin), generator=g).to(device=device, dtype=torch.bfloat16)
+    w = (torch.randn((Cout, 3, 3, Cin), generator=g) / (3 * Cin ** 0.5)).to(device=device, dtype=torch.bfloat16)
+    b = torch.zeros(Cout, dtype=torch.float32, device=device)
+    y = torch.empty((N, H, W, Cout), dtype=torch.bfloat16, device=device)
+    sur.set_tensor_path(True)
+
+    def run():
+        sur._call("cdf_nn_conv3x3_fwd", sur._p(x), sur._p(w), sur._p(b), sur._p(y), N, H, W, Cin, Cout, 1,
+                  sur._stream())
+    for _ in range(3):
+        run()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(reps):
+        run()
+    e1.record()
+    torch.cuda.synchronize()
+    us = e0.elapsed_time(e1) * 1e3 / reps
+    flops = 2.0 * N * H * W * 9 * Cin * Cout
+    nbytes = 2.0 * N * H * W * (Cin + Cout) + 2.0 * 9 * Cin * Cout
+    tf = flops / us / 1e6
+    return {"description": f"3x3 convolution forward (bias + ReLU), N={N} {H}x{W}, {Cin}->{Cout} channels, BF16 "
+                           f"operands, FP32 accumulation in tensor memory",
+            "value": tf, "unit": "TFLOP/s", "launch_us": us, "flops_per_launch": flops,
+            "kernel": f"conv3x3_tc_kernel<false,{Cout if Cout <= 128 else 128}>", "gpu_launches": reps,
+            "roofline": {"bound": "tensor" if flops / nbytes > peak_tflops * 1e12 / (peak_gbs * 1e9) else "hbm",
+                         "achieved": tf, "peak": peak_tflops, "unit": "TFLOP/s", "frac": tf / peak_tflops,
+                         "traffic": None, "peak_source": "measured BF16 GEMM burst (MEASURED_PEAKS.json bf16_tflops)",
+                         "bytes_per_launch": nbytes, "hbm_gbs": nbytes / us / 1e3,
+                         "hbm_frac": nbytes / us / 1e3 / peak_gbs}}
+
+
+def measured_tensor_peak():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as fh:
+            return float(json.load(fh)["bf16_tflops"])
+    return 1900.0
+
+
+CONV_SHAPES = {"unet_conv3x3_256x256x32": (16, 256, 256, 32, 32), "unet_conv3x3_32x32x256": (16, 32, 32, 256, 256)}
 
 
 def copy_pass(nbytes: int, device) -> dict:
@@ -408,53 +531,171 @@ def _dims(pb) -> str:
     return f"{pb.nx}x{pb.ny}x{pb.nz}" if isinstance(pb, I.Problem3D) else f"{pb.nx}x{pb.ny}"
 
 
-def cpu_baseline(pb, budget_s: float = 15.0):
-    """The FP64 oracle as it stands, single-threaded, on a bounded sample: the
-    same lattice advanced for as many steps as fit in about `budget_s`."""
-    o = _oracle_sim(pb)
+def _oracle_threads(pb, n: int) -> int:
+    if isinstance(pb, I.Problem3D):
+        return 1  # the 3-D oracle runs one thread
+    import oracle
+    return oracle.set_threads(n)
+
+
+def _time_oracle(pbs, budget_s: float):
+    """Steps of the oracle on the problems `pbs` (round robin, about budget_s of
+    work); returns (lattice updates, seconds, steps per problem)."""
+    sims = [_oracle_sim(pb) for pb in pbs]
     t0 = time.perf_counter()
-    o.step(2)
-    per = (time.perf_counter() - t0) / 2
-    n = max(2, int(budget_s / max(per, 1e-9)))
+    for o in sims:
+        o.step(1)
+    per = time.perf_counter() - t0
+    n = max(1, int(budget_s / max(per, 1e-9)))
     t0 = time.perf_counter()
-    o.step(n)
+    for o in sims:
+        o.step(n)
     dt = time.perf_counter() - t0
-    return {"value": pb.nodes * n / dt / 1e6, "unit": "MLUPS", "cores": 1, "kind": "oracle",
-            "sample": f"{n} time steps of the {_dims(pb)} lattice (FP64, one thread, "
-                      f"{pb.nodes * n / 1e6:.1f} M lattice updates, {dt:.1f} s)"}
+    return sum(pb.nodes for pb in pbs) * n, dt, n
+
+
+def _sample(wl):
+    """The oracle's sample of a workload: a batched sweep's first eight instances."""
+    return wl[:8] if isinstance(wl, list) else [wl]
+
+
+def cpu_baseline(wl, budget_s: float = 10.0):
+    """The FP64 oracle as it stands on a bounded sample of the workload: with all
+    host cores (OpenMP over the node and row loops; same results) and with one
+    thread, each for about `budget_s`."""
+    pbs = _sample(wl)
+    dims = ", ".join(_dims(pb) for pb in pbs[:3]) + (", ..." if len(pbs) > 3 else "")
+    cores = _oracle_threads(pbs[0], 0)
+    lups, dt, n = _time_oracle(pbs, budget_s)
+    _oracle_threads(pbs[0], 1)
+    lups1, dt1, n1 = _time_oracle(pbs, budget_s)
+    return {"value": lups / dt / 1e6, "unit": "MLUPS", "cores": cores, "kind": "oracle",
+            "nproc": os.cpu_count(),
+            "sample": f"{n} time steps of {len(pbs)} lattice(s) ({dims}; FP64, {cores} threads, "
+                      f"{lups / 1e6:.1f} M lattice updates, {dt:.1f} s)",
+            "single_thread": {"value": lups1 / dt1 / 1e6, "unit": "MLUPS", "cores": 1,
+                              "sample": f"{n1} time steps of the same lattices ({lups1 / 1e6:.1f} M lattice "
+                                        f"updates, {dt1:.1f} s)"}}
 
 
 def run_reference(args, world, rank):
-    """Reference arm: the FP64 CPU oracle on the host cores, same metric and workload."""
+    """Reference arm: the FP64 CPU oracle on all host cores, same metric and workload
+    (a batched sweep: a sample of its instances)."""
     if rank != 0:
         return
     wl = workload(args.workload, 0)
-    pb = wl[0] if isinstance(wl, list) else wl  # a batched sweep: its first instance as the sample
-    o = _oracle_sim(pb)
+    pbs = _sample(wl)
+    cores = _oracle_threads(pbs[0], 0)
+    sims = [_oracle_sim(pb) for pb in pbs]
     per_step_budget = 4.0
     t0 = time.perf_counter()
-    o.step(1)
+    for o in sims:
+        o.step(1)
     per = time.perf_counter() - t0
     n = max(1, int(per_step_budget / max(per, 1e-9)))
     for _ in range(args.warmup):
-        o.step(1)
+        for o in sims:
+            o.step(1)
     t0 = time.perf_counter()
     for _ in range(args.steps):
-        o.step(n)
+        for o in sims:
+            o.step(n)
     dt = time.perf_counter() - t0
-    value = pb.nodes * n * args.steps / dt / 1e6
+    nodes = sum(pb.nodes for pb in pbs)
+    value = nodes * n * args.steps / dt / 1e6
+    dims = ", ".join(_dims(pb) for pb in pbs[:3]) + (", ..." if len(pbs) > 3 else "")
     line = {
         "impl": "reference", "metric": "MLUPS (lattice updates per second, millions)", "value": value,
         "unit": "MLUPS", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": args.workload, "description": describe(args.workload),
-                   "nx": pb.nx, "ny": pb.ny, "m": pb.m, "lb_steps_per_step": n},
-        "cpu_baseline": {"value": value, "unit": "MLUPS", "cores": 1, "kind": "oracle",
-                         "sample": f"{n} time steps of the {_dims(pb)} lattice per benchmark step"},
+                   "sample_lattices": len(pbs), "sample_nodes": nodes, "m": pbs[0].m, "lb_steps_per_step": n},
+        "cpu_baseline": {"value": value, "unit": "MLUPS", "cores": cores, "kind": "oracle",
+                         "sample": f"{n} time steps of {len(pbs)} lattice(s) ({dims}) per benchmark step, "
+                                   f"FP64, {cores} threads"},
         "e2e": {"value": value, "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
+
+
+def make_runner(lib, name, rank, args, fixed=True):
+    """The solver of workload `name` (the options of the command line apply to the
+    main workload only: fixed = True)."""
+    wl = workload(name, rank)
+    if isinstance(wl, list):
+        if fixed and args.batch_tile:
+            tile = tuple(int(v) for v in args.batch_tile.split(","))
+            return _Batch(lib, wl, args.storage, args.batch_mode, tile)
+        return _Batch(lib, wl, args.storage if fixed else "fp32")
+    if isinstance(wl, I.Problem3D):
+        return _Single3D(lib, wl, args.storage if fixed else "fp32")
+    if not fixed:
+        return _Single(lib, wl, "fp32")
+    block = tuple(int(v) for v in args.block.split(",")) if args.block else None
+    tshape = tuple(int(v) for v in args.temporal_shape.split(",")) if args.temporal_shape else None
+    return _Single(lib, wl, args.storage, args.resident, block, args.temporal, tshape)
+
+
+def default_lb_steps(nodes: int) -> int:
+    """About 0.1 s of lattice updates at ~30 GLUPS, a multiple of 32, at most 20000."""
+    return int(min(20000, max(32, 3e9 / nodes)) // 32 * 32)
+
+
+def time_runner(runner, S, K, W, flush, device, world):
+    """K timed benchmark steps of S lattice steps (after W untimed ones), L2 flushed
+    between them; returns the max over ranks of the summed event times (ms)."""
+    import torch
+    lib_stream = torch.cuda.ExternalStream(runner.stream, device=device)
+    for _ in range(W):
+        runner.step(S)
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
+    barrier(world)
+    torch.cuda.synchronize()
+    for k in range(K):
+        flush.zero_()  # evict L2 between benchmark steps
+        torch.cuda.synchronize()
+        ev[k][0].record(lib_stream)
+        runner.step(S)
+        ev[k][1].record(lib_stream)
+    torch.cuda.synchronize()
+    barrier(world)
+    kernel_ms = sum(a.elapsed_time(b) for a, b in ev)
+    return all_max(kernel_ms, world, device)
+
+
+L2_BYTES = 126e6  # GB300 L2, less a margin
+
+
+def roofline_of(runner, name, S, K, t_ms, peak, peak_kind):
+    """The dominant kernel's roofline: bytes it must move per launch (state read and
+    written once) over its launch time, against the measured copy bandwidth."""
+    nodes = getattr(runner, "local_nodes", runner.nodes)  # a slab's kernel moves its own rows
+    upp = runner.updates_per_pass(S)
+    state_bytes = runner.bytes_per_lup * nodes
+    pass_s = t_ms * 1e-3 / (S * K) * upp  # time of one pass over the state
+    achieved = state_bytes / pass_s / 1e9
+    l2 = state_bytes < L2_BYTES  # the buffer read and the buffer written both fit in L2
+    rec = recorded_profile(name, runner.kernel)
+    r = {"bound": "effective (L2-resident)" if l2 else "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+         "frac": achieved / peak, "traffic": None if rec is None else rec["dram_bytes_per_launch"],
+         "peak_source": f"{peak_kind} copy bandwidth (MEASURED_PEAKS.json hbm_gbs)",
+         "bytes_per_launch": state_bytes, "bytes_per_lup": runner.bytes_per_lup,
+         "lattice_updates_per_pass": upp, "kernel": runner.kernel,
+         "launch_us": pass_s * 1e6 / max(1, runner.steps_per_launch(S) // upp),
+         "lattice_steps_per_launch": runner.steps_per_launch(S)}
+    if l2:
+        r["l2_resident"] = True
+        r["note"] = ("the state stays in the 129 MB L2 inside a benchmark step: achieved is the algorithmic "
+                     "bytes over the launch time, an effective figure, not HBM traffic")
+    if rec is not None and "issue_active" in rec:
+        r["limiter"] = "instruction issue"
+        r["issue_active"] = rec["issue_active"]
+    return r
+
+
+EXTRA_WORKLOADS = ("chemotaxis_plume_512x256", "ddc_cavity_1024", "chemotaxis_plume_regularised_512x256")
 
 
 def main():
@@ -463,7 +704,7 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="chemotaxis_plume_512x256")
+    ap.add_argument("--workload", default="batched_plume_sweep_256")
     ap.add_argument("--lb-steps", type=int, default=None,
                     help="lattice time steps per benchmark step (default: about 0.1 s of work, a multiple "
                          "of 32, at most 20000)")
@@ -477,7 +718,15 @@ def main():
                          "default: autotuned")
     ap.add_argument("--block", default=None,
                     help="CTA shape 'X,Y' of the single-lattice step (Y = 0: flat launch); default: autotuned")
+    ap.add_argument("--split", default="none", choices=["none", "slab"],
+                    help="slab: one single lattice split along y over the ranks, halo exchange through NCCL "
+                         "after every step (strong scaling); none: every rank its own instance (weak scaling)")
+    ap.add_argument("--batch-mode", type=int, default=0, choices=[0, 1, 2],
+                    help="with --batch-tile: the batched solver's mode (0 persistent, 1 chains, 2 two-step chains)")
+    ap.add_argument("--batch-tile", default=None,
+                    help="'X,Y': tile (mode 0) or CTA shape (modes 1, 2) of the batched solver; default: autotuned")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extra", action="store_true", help="skip the extra workloads of the N = 1 line")
     ap.add_argument("--e2e-steps", type=int, default=3)
     args = ap.parse_args()
     world, rank, local = dist_setup()
@@ -496,44 +745,31 @@ def main():
 
     from paper_2101_03055_gb300 import build, lib
     build.build()
-    wl = workload(args.workload, rank)
-    if isinstance(wl, list):
-        runner = _Batch(lib, wl, args.storage)
-    elif isinstance(wl, I.Problem3D):
-        runner = _Single3D(lib, wl, args.storage)
+    if args.workload in CONV_SHAPES:  # one convolution layer of the surrogate, alone (profiling)
+        peak, _ = measured_peaks()
+        line = conv_line(*CONV_SHAPES[args.workload], max(1, args.steps), device, measured_tensor_peak(), peak)
+        line.update({"metric": "TFLOP/s of the 3x3 convolution", "n_gpus": 1, "steps": args.steps,
+                     "config": {"workload": args.workload}, "dtype": "bf16", "data": "synthetic"})
+        print(json.dumps(line), flush=True)
+        return
+    if args.split == "slab":
+        wl = workload(args.workload, 0)  # one lattice for the whole job
+        if not isinstance(wl, I.Problem):
+            raise SystemExit("--split slab needs a single 2-D lattice workload")
+        runner = _Slab(lib, wl, args.storage, rank, world)
     else:
-        block = tuple(int(v) for v in args.block.split(",")) if args.block else None
-        tshape = tuple(int(v) for v in args.temporal_shape.split(",")) if args.temporal_shape else None
-        runner = _Single(lib, wl, args.storage, args.resident, block, args.temporal, tshape)
+        runner = make_runner(lib, args.workload, rank, args)
     nodes = runner.nodes
-    S = args.lb_steps
-    if S is None:  # about 0.1 s of lattice updates at ~30 GLUPS per benchmark step
-        S = int(min(20000, max(32, 3e9 / nodes)) // 32 * 32)
+    S = args.lb_steps if args.lb_steps is not None else default_lb_steps(nodes)
     K, W = args.steps, args.warmup
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=device)
-    lib_stream = torch.cuda.ExternalStream(runner.stream, device=device)
 
-    for _ in range(W):
-        runner.step(S)
-    torch.cuda.synchronize()
-
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
-    barrier(world)
-    torch.cuda.synchronize()
     with ClockSampler(local) as clk:
         wall0 = time.perf_counter()
-        for k in range(K):
-            flush.zero_()  # evict L2 between benchmark steps
-            torch.cuda.synchronize()
-            ev[k][0].record(lib_stream)
-            runner.step(S)
-            ev[k][1].record(lib_stream)
-        torch.cuda.synchronize()
+        t_ms = time_runner(runner, S, K, W, flush, device, world)
         wall = time.perf_counter() - wall0
-    barrier(world)
-    kernel_ms = sum(a.elapsed_time(b) for a, b in ev)
-    t_ms = all_max(kernel_ms, world, device)
-    value = job_mlups(nodes, S, K, world, t_ms)
+    strong = args.split == "slab"
+    value = job_mlups(nodes, S, K, 1 if strong else world, t_ms)
 
     # e2e: host moments in, S steps through the C ABI, host moments out
     E = max(1, args.e2e_steps)
@@ -546,16 +782,34 @@ def main():
         moved = runner.e2e_step(S)
     torch.cuda.synchronize()
     e2e_s = all_max(time.perf_counter() - t0, world, device)
-    e2e_value = world * nodes * S * E / e2e_s / 1e6
+    e2e_value = (1 if strong else world) * nodes * S * E / e2e_s / 1e6
     stage_bytes = moved // 2
 
     cp = copy_pass(int(runner.bytes_per_lup * nodes), device)
     peak, peak_kind = measured_peaks()
-    spl = runner.steps_per_launch(S)
-    bytes_per_launch = runner.bytes_per_lup * nodes * spl
-    launch_s = t_ms * 1e-3 / (S * K) * spl
-    achieved = bytes_per_launch / launch_s / 1e9
-    traffic = recorded_traffic(args.workload, runner.kernel)
+    roof = roofline_of(runner, args.workload, S, K, t_ms, peak, peak_kind)
+    launches = runner.launches(S) * K
+    state_bytes = nodes * runner.bytes_per_lup / 2
+    block, m, storage = runner.block, runner.m, runner.storage
+
+    extra = {}
+    if world == 1 and not strong and not args.no_extra and args.workload not in EXTRA_WORKLOADS:
+        del runner
+        torch.cuda.synchronize()
+        for name in EXTRA_WORKLOADS:
+            r = make_runner(lib, name, rank, args, fixed=False)
+            Sx, Kx = default_lb_steps(r.nodes), min(K, 5)
+            with ClockSampler(local) as clk_x:
+                tx = time_runner(r, Sx, Kx, max(3, min(W, 3)), flush, device, 1)
+            extra[name] = {
+                "description": describe(name), "value": job_mlups(r.nodes, Sx, Kx, 1, tx), "unit": "MLUPS",
+                "ms_per_step": tx / Kx, "steps": Kx, "lb_steps_per_step": Sx, "nodes": r.nodes,
+                "gpu_launches": r.launches(Sx) * Kx, "clocks": clk_x.summary(),
+                "roofline": roofline_of(r, name, Sx, Kx, tx, peak, peak_kind)}
+            del r
+            torch.cuda.synchronize()
+        for name, shape in CONV_SHAPES.items():
+            extra[name] = conv_line(*shape, 50, device, measured_tensor_peak(), peak)
 
     if rank != 0:
         if world > 1:
@@ -565,31 +819,30 @@ def main():
     line = {
         "metric": "MLUPS (lattice updates per second, millions)",
         "value": value, "unit": "MLUPS", "n_gpus": world, "steps": K, "warmup": W,
-        "ms_per_step": t_ms / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "ms_per_step": t_ms / K, "higher_is_better": True, "scaling": "strong" if strong else "weak",
+        "vs_baseline": None,
         "dtype": "f32",
         "data": "synthetic",
         "config": {"workload": args.workload, "description": describe(args.workload), "nodes": nodes,
-                   "storage": {0: "f32", 1: "f16", 2: "bf16"}[runner.storage] + " populations (arithmetic in f32)",
-                   "m": runner.m, "lb_steps_per_step": S, "block": runner.block,
+                   "storage": {0: "f32", 1: "f16", 2: "bf16"}[storage] + " populations (arithmetic in f32)",
+                   "m": m, "lb_steps_per_step": S, "block": block,
                    "l2": "flushed between benchmark steps (256 MiB write); the state is L2-resident "
-                         "within a step" if nodes * runner.bytes_per_lup < 120e6 else
+                         "within a step" if 2 * state_bytes < L2_BYTES else
                          "flushed between benchmark steps; working set larger than L2",
-                   "parallelism": f"replicas x{world} (independent instances, seed = rank)"},
+                   "parallelism": (f"slabs x{world} (one lattice split along y, halo exchange after every step)"
+                                   if strong else f"replicas x{world} (independent instances, seed = rank)")},
         "e2e": {"value": e2e_value, "unit": "MLUPS", "h2d_bytes_per_step": stage_bytes,
                 "d2h_bytes_per_step": stage_bytes, "steps": E},
-        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": achieved / peak, "traffic": traffic,
-                     "peak_source": f"{peak_kind} copy bandwidth (MEASURED_PEAKS.json hbm_gbs)",
-                     "bytes_per_lup": runner.bytes_per_lup, "kernel": runner.kernel,
-                     "launch_us": launch_s * 1e6, "lattice_steps_per_launch": spl},
+        "roofline": roof,
         "copy_pass": cp,
-        "gpu_launches": runner.launches(S) * K,
+        "gpu_launches": launches,
         "clocks": clk.summary(),
         "wall_s": wall,
     }
+    if extra:
+        line["extra"] = extra
     if world == 1 and not args.no_cpu_baseline:
-        wl0 = workload(args.workload, 0)
-        line["cpu_baseline"] = cpu_baseline(wl0[0] if isinstance(wl0, list) else wl0)
+        line["cpu_baseline"] = cpu_baseline(workload(args.workload, 0))
     print(json.dumps(line), flush=True)
     if world > 1:
         import torch.distributed as dist
