@@ -61,6 +61,8 @@ L2_FLUSH_BYTES = 256 << 20
 def workload(name: str, rank: int):
     if name == "chemotaxis_plume_512x256":
         return I.chemotaxis_plume(512, 256, seed=rank, chi=0.5)
+    if name == "chemotaxis_plume_2048x1024":
+        return I.chemotaxis_plume(2048, 1024, seed=rank, chi=0.5)
     if name == "chemotaxis_plume_regularised_512x256":
         return I.chemotaxis_plume_regularised(512, 256)
     if name == "ddc_cavity_1024":
@@ -90,6 +92,8 @@ def describe(name: str) -> str:
     return {
         "chemotaxis_plume_512x256": "chemotaxis-fluid plume 512x256, m=2 (n, c), FP32, walls + free-slip top, "
                                     "chi=0.5 step cut-off, consumption, buoyancy; n0 = 1 + 0.01 N(0,1)",
+        "chemotaxis_plume_2048x1024": "chemotaxis-fluid plume 2048x1024 (the sweep's closures on one lattice above "
+                                      "L2, for profiling the sweep's kernel)",
         "chemotaxis_plume_regularised_512x256": "chemotaxis-fluid plume of Sec. 3.1.2, 512x256: alpha=5, beta=5, "
                                                 "delta=0.25, gamma=418, Sc=7700, regularised cut-off (eps = dx), "
                                                 "periodic sides, n0 = 1 / 0.5 across a perturbed interface",
@@ -413,28 +417,34 @@ def conv_line(N, H, W, Cin, Cout, reps, device, peak_tflops, peak_gbs):
     w = (torch.randn((Cout, 3, 3, Cin), generator=g) / (3 * Cin ** 0.5)).to(device=device, dtype=torch.bfloat16)
     b = torch.zeros(Cout, dtype=torch.float32, device=device)
     y = torch.empty((N, H, W, Cout), dtype=torch.bfloat16, device=device)
-    sur.set_tensor_path(True)
-
     def run():
         sur._call("cdf_nn_conv3x3_fwd", sur._p(x), sur._p(w), sur._p(b), sur._p(y), N, H, W, Cin, Cout, 1,
                   sur._stream())
-    for _ in range(3):
-        run()
-    torch.cuda.synchronize()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record()
-    for _ in range(reps):
-        run()
-    e1.record()
-    torch.cuda.synchronize()
-    us = e0.elapsed_time(e1) * 1e3 / reps
+
+    def timed(path):
+        sur.set_tensor_path(path)
+        for _ in range(3):
+            run()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            run()
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) * 1e3 / reps
+    us_sync = timed(2)  # the same MMAs with synchronously staged tiles, for comparison
+    us = timed(1)
     flops = 2.0 * N * H * W * 9 * Cin * Cout
     nbytes = 2.0 * N * H * W * (Cin + Cout) + 2.0 * 9 * Cin * Cout
     tf = flops / us / 1e6
     return {"description": f"3x3 convolution forward (bias + ReLU), N={N} {H}x{W}, {Cin}->{Cout} channels, BF16 "
                            f"operands, FP32 accumulation in tensor memory",
             "value": tf, "unit": "TFLOP/s", "launch_us": us, "flops_per_launch": flops,
-            "kernel": f"conv3x3_tc_kernel<false,{Cout if Cout <= 128 else 128}>", "gpu_launches": reps,
+            "kernel": (f"conv3x3_tc_pipe_kernel<false,{Cout if Cout <= 128 else 128}>" if Cin >= 128 else
+                       f"conv3x3_tc_kernel<false,{Cout if Cout <= 128 else 128}>"), "gpu_launches": 2 * reps,
+            "synchronous_staging": {"kernel": f"conv3x3_tc_kernel<false,{Cout if Cout <= 128 else 128}>",
+                                    "launch_us": us_sync, "value": flops / us_sync / 1e6},
             "roofline": {"bound": "tensor" if flops / nbytes > peak_tflops * 1e12 / (peak_gbs * 1e9) else "hbm",
                          "achieved": tf, "peak": peak_tflops, "unit": "TFLOP/s", "frac": tf / peak_tflops,
                          "traffic": None, "peak_source": "measured BF16 GEMM burst (MEASURED_PEAKS.json bf16_tflops)",
@@ -448,6 +458,36 @@ def measured_tensor_peak():
         with open(path) as fh:
             return float(json.load(fh)["bf16_tflops"])
     return 1900.0
+
+
+def time_to_steady_line(n=256, cases=8, tol=1e-5, check_every=10_000, max_steps=3_000_000):
+    """The surrogate's warm start against the start from rest on n x n double-diffusive
+    cavities (held-out parameter draws, seed 1): lattice steps and GPU seconds until the
+    stop test of Sec. 3.1.1 (R over check_every steps) drops below tol, both starts run
+    as one batched solve each.  The network is the committed one trained on 64^2
+    steady states; its prediction is resampled to n x n.  None when no trained
+    weights are present."""
+    from paper_2101_03055_gb300 import surrogate as S
+    path = S.default_model_path()
+    if not os.path.exists(path):
+        return None
+    net = S.UNet(seed=0)
+    net.load_state(dict(np.load(path)))
+    prms = S.draw_parameters(cases, 1)
+    res = S.time_to_steady(net, prms, n, 64, tol=tol, check_every=check_every, max_steps=max_steps)
+    c, w = res["cold"]["first"], res["warm"]["first"]
+    both = (c > 0) & (w > 0)
+    med = lambda a: float(np.median(a)) if len(a) else None  # noqa: E731
+    return {"description": f"{cases} held-out {n}x{n} double-diffusive cavities (Ra logU[1e4, 1e6], Nc U[-2, 2], "
+                           f"Le U[1, 10], Sr, Df U[0, 0.5], Pr 0.7): steps until R < {tol:g} over {check_every} "
+                           f"steps, from rest and from the U-Net prediction (trained on 64^2 steady states, "
+                           f"resampled; fluid at rest, hydrostatic p)",
+            "cases_reached_both": int(both.sum()), "cold_steps": c.tolist(), "warm_steps": w.tolist(),
+            "median_cold_steps": med(c[both]), "median_warm_steps": med(w[both]),
+            "median_ratio_warm_over_cold": med(w[both] / c[both]),
+            "cold_gpu_s": res["cold"]["seconds"], "warm_gpu_s": res["warm"]["seconds"],
+            "ratio_gpu_s": res["warm"]["seconds"] / res["cold"]["seconds"],
+            "max_steps": max_steps}
 
 
 CONV_SHAPES = {"unet_conv3x3_256x256x32": (16, 256, 256, 32, 32), "unet_conv3x3_32x32x256": (16, 32, 32, 256, 256)}
@@ -785,14 +825,15 @@ def main():
     e2e_value = (1 if strong else world) * nodes * S * E / e2e_s / 1e6
     stage_bytes = moved // 2
 
-    cp = copy_pass(int(runner.bytes_per_lup * nodes), device)
+    # context for an L2-resident state: the time of a plain device copy of one step's bytes
+    cp = copy_pass(int(runner.bytes_per_lup * nodes), device) if runner.bytes_per_lup * nodes < L2_BYTES else None
     peak, peak_kind = measured_peaks()
     roof = roofline_of(runner, args.workload, S, K, t_ms, peak, peak_kind)
     launches = runner.launches(S) * K
     state_bytes = nodes * runner.bytes_per_lup / 2
     block, m, storage = runner.block, runner.m, runner.storage
 
-    extra = {}
+    extra, tts = {}, None
     if world == 1 and not strong and not args.no_extra and args.workload not in EXTRA_WORKLOADS:
         del runner
         torch.cuda.synchronize()
@@ -810,6 +851,7 @@ def main():
             torch.cuda.synchronize()
         for name, shape in CONV_SHAPES.items():
             extra[name] = conv_line(*shape, 50, device, measured_tensor_peak(), peak)
+        tts = time_to_steady_line()
 
     if rank != 0:
         if world > 1:
@@ -834,13 +876,15 @@ def main():
         "e2e": {"value": e2e_value, "unit": "MLUPS", "h2d_bytes_per_step": stage_bytes,
                 "d2h_bytes_per_step": stage_bytes, "steps": E},
         "roofline": roof,
-        "copy_pass": cp,
+        **({"copy_pass": cp} if cp else {}),
         "gpu_launches": launches,
         "clocks": clk.summary(),
         "wall_s": wall,
     }
     if extra:
         line["extra"] = extra
+    if world == 1 and not strong and not args.no_extra and tts is not None:
+        line["time_to_steady"] = tts
     if world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(workload(args.workload, 0))
     print(json.dumps(line), flush=True)

@@ -238,6 +238,21 @@ cdf_status cdf_lb_moments_device(cdf_lb *h, float *dev_out);
  * the device (mass check of Eq. CDE). sums has m entries (host). */
 cdf_status cdf_lb_mass(cdf_lb *h, double *sums);
 
+/* Heat and mass transfer through a wall of the double-diffusive cavity (Sec. 3.2,
+ * the local Nusselt and Sherwood numbers and their averages over the wall), with
+ * T = phi_0 and C = phi_1 of the current moments and lengths scaled by the lattice
+ * width (dx = 1 / nx).  The wall derivative is the second-order one-sided (upwind)
+ * difference through the wall value and the first two nodes, which sit half a
+ * spacing and one and a half spacings from the half-way wall:
+ * q'(wall) = (9 q_1 - q_2 - 8 q_wall) / (3 dx), taken along +x on either wall.
+ * out[0] = mean_y Nu(y) = -mean_y (dT/dx + D_CT dC/dx), out[1] = mean_y Sh(y) =
+ * -mean_y (S_TC dT/dx + dC/dx): the flux in +x (out of a hot west wall, into a
+ * cold east wall; the paper prints the derivatives without the sign).  side: 0 west,
+ * 1 east; T_wall, C_wall: that wall's values.  FP64 sums on the device; out has 2
+ * host doubles.  Needs m >= 2 and nx >= 2. */
+cdf_status cdf_lb_wall_transfer(cdf_lb *h, int side, double D_CT, double S_TC, double T_wall, double C_wall,
+                                double *out);
+
 /* Post-collision populations of the current time as FP64 on the host:
  * f [m][5][ny][nx] (D2Q5 order of Eq. D2Q5), hf [9][ny][nx] (Eq. D2Q9 order),
  * s_now [m][ny][nx] = S(phi) of the current time (zeros unless CONSUMPTION).

@@ -31,9 +31,11 @@ struct BatchInst {
 
 // Grid-wide barrier for a co-resident (cooperative) grid.  bar[0] counts
 // arrivals, bar[1] is the generation.  Every wait is bounded: after timeout_ns
-// (or an iteration cap) the block sets *err and the whole grid gives up.
-// Returns false when the barrier failed.
-__device__ bool grid_barrier(unsigned *bar, unsigned expected, unsigned long long timeout_ns, int *err) {
+// (or an iteration cap) the block sets err[0] and the whole grid gives up; the
+// first block to give up records the step, the arrivals it saw and the time it
+// waited (err[1..3], microseconds) for the host's message.  Returns false when
+// the barrier failed.
+__device__ bool grid_barrier(unsigned *bar, unsigned expected, unsigned long long timeout_ns, int *err, int step) {
     __shared__ int ok;
     __syncthreads();
     if (threadIdx.x == 0 && threadIdx.y == 0) {
@@ -54,7 +56,11 @@ __device__ bool grid_barrier(unsigned *bar, unsigned expected, unsigned long lon
             while (*vgen == gen) {
                 if (*verr) { ok = 0; break; }
                 if (++it > cap || ((it & 63ull) == 0 && dev::global_ns() - t0 > timeout_ns)) {
-                    atomicExch(err, 1);
+                    if (atomicCAS(err, 0, 1) == 0) {
+                        err[1] = step;
+                        err[2] = (int)*(volatile unsigned *)bar;
+                        err[3] = (int)min((dev::global_ns() - t0) / 1000ull, 2000000000ull);
+                    }
                     ok = 0;
                     break;
                 }
@@ -111,7 +117,7 @@ __global__ void __launch_bounds__(256, 4) batch_kernel(const BatchInst *__restri
                 dev::step_node<M, float, true>(sp, x, y, in + s_off[0], out + s_off[0], sprev + s_off[1],
                                                sprev + s_off[1], mom ? mom + s_off[2] : nullptr);
         }
-        if (s + 1 < nsteps && !grid_barrier(bar, expected, timeout_ns, err)) return;
+        if (s + 1 < nsteps && !grid_barrier(bar, expected, timeout_ns, err, s)) return;
     }
 }
 
@@ -251,7 +257,7 @@ cdf_status setup_tiles(cdf_batch *b, dim3 tile) {
 }
 
 cdf_status launch_batch(cdf_batch *b, int nsteps, bool moments_last) {
-    BCK(cudaMemsetAsync(b->d_err, 0, sizeof(int), b->s));
+    BCK(cudaMemsetAsync(b->d_err, 0, 4 * sizeof(int), b->s));
     BCK(cudaMemsetAsync(b->d_bar, 0, 2 * sizeof(unsigned), b->s));
     unsigned expected = (unsigned)b->grid_blocks + (unsigned)b->extra_arrivals;
     int parity = b->cur, ml = moments_last ? 1 : 0;
@@ -265,7 +271,7 @@ cdf_status launch_batch(cdf_batch *b, int nsteps, bool moments_last) {
         default: kern = (const void *)batch_kernel<4>; break;
     }
     BCK(cudaLaunchCooperativeKernel(kern, dim3(b->grid_blocks), b->tile, args, 0, b->s));
-    BCK(cudaMemcpyAsync(b->h_err, b->d_err, sizeof(int), cudaMemcpyDeviceToHost, b->s));
+    BCK(cudaMemcpyAsync(b->h_err, b->d_err, 4 * sizeof(int), cudaMemcpyDeviceToHost, b->s));
     if (nsteps & 1) b->cur ^= 1;
     b->t += nsteps;
     return CDF_OK;
@@ -357,7 +363,14 @@ bool chain_pair_fits(const cdf_batch *b, dim3 blk, int th) {
 }
 
 cdf_status check_err(cdf_batch *b) {
-    if (*b->h_err) return bfail(CDF_ETIMEOUT, "grid barrier wait timed out; the batch state is undefined");
+    if (*b->h_err) {
+        char m[256];
+        std::snprintf(m, sizeof m,
+                      "grid barrier wait timed out after step %d of a launch (%d of %d blocks had arrived, waited %d "
+                      "us); the batch state is undefined",
+                      b->h_err[1], b->h_err[2], b->grid_blocks + b->extra_arrivals, b->h_err[3]);
+        return bfail(CDF_ETIMEOUT, m);
+    }
     return CDF_OK;
 }
 
@@ -513,14 +526,15 @@ cdf_status cdf_batch_create(int count, const cdf_grid *grids, int m, const cdf_d
               cudaMalloc(&b->dense, b->stage_floats * 4) == cudaSuccess &&
               cudaMalloc(&b->d_inst, count * sizeof(BatchInst)) == cudaSuccess &&
               cudaMalloc(&b->d_bar, 2 * sizeof(unsigned)) == cudaSuccess &&
-              cudaMalloc(&b->d_err, sizeof(int)) == cudaSuccess &&
-              cudaMallocHost(&b->h_err, sizeof(int)) == cudaSuccess &&
+              cudaMalloc(&b->d_err, 4 * sizeof(int)) == cudaSuccess &&
+              cudaMallocHost(&b->h_err, 4 * sizeof(int)) == cudaSuccess &&
               cudaMallocHost(&b->host_stage, b->stage_floats * 4) == cudaSuccess;
     if (!ok) {
         cudaGetLastError();
         brelease(b);
         return bfail(CDF_ENOMEM, "device allocation failed");
     }
+    std::memset(b->h_err, 0, 4 * sizeof(int));  // read after every step call, also in the chain modes
     if (cudaStreamCreateWithFlags(&b->s, cudaStreamNonBlocking) != cudaSuccess ||
         cudaEventCreateWithFlags(&b->ev_in, cudaEventDisableTiming) != cudaSuccess ||
         cudaEventCreateWithFlags(&b->ev_out, cudaEventDisableTiming) != cudaSuccess ||

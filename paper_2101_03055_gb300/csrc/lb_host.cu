@@ -1063,6 +1063,27 @@ cdf_status cdf_lb_change_sums(cdf_lb *h, double *sums) {
     return leave(h);
 }
 
+cdf_status cdf_lb_wall_transfer(cdf_lb *h, int side, double D_CT, double S_TC, double T_wall, double C_wall,
+                                double *out) {
+    g_err[0] = 0;
+    if (!h || !out) return fail(CDF_EINVAL, "NULL argument");
+    if (side != 0 && side != 1) return fail(CDF_EINVAL, "side must be 0 (west) or 1 (east)");
+    if (h->m < 2 || h->nx < 2) return fail(CDF_EINVAL, "needs m >= 2 (T, C) and nx >= 2");
+    if (h->P.case1) return fail(CDF_EINVAL, "the wall transfer needs the full model's moments");
+    if (!h->initialised) return fail(CDF_EINVAL, "state not initialised");
+    DeviceGuard g(h->device);
+    cdf_status st = enter(h);
+    if (st != CDF_OK) return st;
+    const long long off = (long long)h->P.row_lo * h->pitch;
+    CK(launch_wall_transfer(current_moments(h) + off, h->nx, h->P.row_hi - h->P.row_lo, h->pitch, h->plane, side,
+                            D_CT, S_TC, T_wall, C_wall, h->red, h->s));
+    CK(cudaMemcpyAsync(h->red_host, h->red, 2 * sizeof(double), cudaMemcpyDeviceToHost, h->s));
+    if ((st = sync(h)) != CDF_OK) return st;
+    out[0] = h->red_host[0];
+    out[1] = h->red_host[1];
+    return leave(h);
+}
+
 cdf_status cdf_lb_populations(cdf_lb *h, double *f, double *hf, double *s_now) {
     g_err[0] = 0;
     if (!h) return fail(CDF_EINVAL, "NULL handle");

@@ -153,6 +153,10 @@ constexpr int kReduceBlocks = 304;  // 2 x 152 SMs
 int reduce_quantities(int m);
 cudaError_t launch_reduce(const float *mom_new, const float *mom_old, int nx, int ny, int pitch,
                           long long plane, int m, double *partials, double *out, cudaStream_t s);
+// Average Nusselt and Sherwood numbers on the west (east = 0) or east wall of a
+// moment stack (T = plane 0, C = plane 1), FP64, into out[0..1] (device).
+cudaError_t launch_wall_transfer(const float *mom, int nx, int ny, int pitch, long long plane, int east, double D_CT,
+                                 double S_TC, double T_wall, double C_wall, double *out, cudaStream_t s);
 // Loads the code of every reduction kernel on the current device now instead of
 // at its first launch.
 cudaError_t preload_reduce_kernels();

@@ -96,6 +96,43 @@ cudaError_t run(const float *nw, const float *od, int nx, int ny, int pitch, lon
 
 }  // namespace
 
+// Wall heat and mass transfer of the double-diffusive cavity (Sec. 3.2): per row y
+// the x-derivative of T = phi_0 and C = phi_1 at the wall by the one-sided quadratic
+// through the wall value and the first two nodes (half a spacing and one and a half
+// spacings from the half-way wall), q'(wall) = (9 q_1 - q_2 - 8 q_w) / (3 dx) with dx
+// = 1 / nx (lengths scaled by the cavity width), taken in +x on either wall; then
+// Nu(y) = -(dT/dx + D_CT dC/dx), Sh(y) = -(S_TC dT/dx + dC/dx) (the flux in +x: out of
+// the hot west wall, into the cold east wall) and their row means, in FP64 with a
+// fixed summation order (one block, a strided run of rows per thread, a tree).
+__global__ void __launch_bounds__(kThreads) wall_transfer_kernel(const float *__restrict__ mom, int nx, int ny,
+                                                                 int pitch, long long plane, int east, double D_CT,
+                                                                 double S_TC, double T_wall, double C_wall,
+                                                                 double *__restrict__ out) {
+    double acc[2] = {0.0, 0.0};
+    const double dx = 1.0 / nx;
+    for (int y = threadIdx.x; y < ny; y += blockDim.x) {
+        const long long r = (long long)y * pitch;
+        const int i1 = east ? nx - 1 : 0, i2 = east ? nx - 2 : 1;
+        const double sgn = east ? -1.0 : 1.0;  // d/dx of the quadratic, pointing in +x
+        const double T1 = mom[r + i1], T2 = mom[r + i2], C1 = mom[plane + r + i1], C2 = mom[plane + r + i2];
+        const double dT = sgn * (9.0 * T1 - T2 - 8.0 * T_wall) / (3.0 * dx);
+        const double dC = sgn * (9.0 * C1 - C2 - 8.0 * C_wall) / (3.0 * dx);
+        acc[0] += -(dT + D_CT * dC);
+        acc[1] += -(S_TC * dT + dC);
+    }
+    block_sum<2>(acc);
+    if (threadIdx.x == 0) {
+        out[0] = acc[0] / ny;
+        out[1] = acc[1] / ny;
+    }
+}
+
+cudaError_t launch_wall_transfer(const float *mom, int nx, int ny, int pitch, long long plane, int east, double D_CT,
+                                 double S_TC, double T_wall, double C_wall, double *out, cudaStream_t s) {
+    wall_transfer_kernel<<<1, kThreads, 0, s>>>(mom, nx, ny, pitch, plane, east, D_CT, S_TC, T_wall, C_wall, out);
+    return cudaGetLastError();
+}
+
 cudaError_t preload_reduce_kernels() {
     // cudaFuncGetAttributes makes the runtime load each kernel's code now (under
     // lazy module loading it would otherwise load, and may allocate, at the first

@@ -9,6 +9,7 @@
 #include <cuda_runtime.h>
 #include <mma.h>
 
+#include <algorithm>
 #include <cstdint>
 
 #include "../../include/cdf_nn.h"
@@ -326,6 +327,451 @@ __global__ void __launch_bounds__(kTcThreads) conv3x3_tc_kernel(const __nv_bfloa
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kCols) : "memory");
 }
 
+// ---------------------------------------------------------------------------
+// The same convolution with its operand tiles copied by cp.async: three stage
+// buffers, the copies of stage s + 2 in flight while the tensor core works on
+// stage s.  Each thread copies its A row (8 x 16 bytes of the im2col row, zero
+// fill outside the image: a copy of 0 source bytes writes zeros) and, for the
+// forward pass, 16-byte runs of the weights straight into the K-major
+// core-matrix layout; the backward-data weights are a gather of single elements
+// and are staged with ordinary loads.  A buffer is refilled only after the MMAs
+// that read it have completed (its mbarrier).  Same stage layout, descriptors,
+// MMAs, bounded waits and epilogue as conv3x3_tc_kernel.
+// ---------------------------------------------------------------------------
+constexpr int kStages = 3;
+
+__device__ __forceinline__ void cp_async16(void *smem, const void *gmem, int src_bytes) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(smem_u32(smem)), "l"(gmem), "r"(src_bytes)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+
+template <bool kBwdData, int BN>
+__global__ void __launch_bounds__(kTcThreads) conv3x3_tc_pipe_kernel(const __nv_bfloat16 *__restrict__ in,
+                                                                     const __nv_bfloat16 *__restrict__ w,
+                                                                     const float *__restrict__ bias,
+                                                                     __nv_bfloat16 *__restrict__ out, int N, int H,
+                                                                     int Wd, int Cin_g, int Cout_g, int relu) {
+    constexpr int kCols = BN < 32 ? 32 : BN;
+    constexpr uint32_t kABytes = kTM * kTK * 2, kBBytes = BN * kTK * 2;
+    extern __shared__ __align__(128) unsigned char tc_smem[];
+    unsigned char *A = tc_smem;                    // kStages x kABytes
+    unsigned char *B = tc_smem + kStages * kABytes;  // kStages x kBBytes
+    __shared__ __align__(8) uint64_t mbar[kStages];
+    __shared__ uint32_t tmem_slot;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const long long P = (long long)N * H * Wd;
+    const long long p0 = (long long)blockIdx.x * kTM;
+    const int n0 = blockIdx.y * BN;
+    const int Cin_w = kBwdData ? Cout_g : Cin_g;
+    const int K = 9 * Cin_g, nst = (K + kTK - 1) / kTK;
+
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_slot)),
+                     "r"(kCols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    if (tid == 0) {
+#pragma unroll
+        for (int b = 0; b < kStages; ++b)
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&mbar[b])) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = tmem_slot;
+
+    const long long pa = p0 + tid;
+    int an = 0, ay = 0, ax = 0;
+    if (pa < P) {
+        an = (int)(pa / ((long long)H * Wd));
+        const int rem = (int)(pa - (long long)an * H * Wd);
+        ay = rem / Wd;
+        ax = rem - ay * Wd;
+    }
+    // copies of stage s into its buffer
+    auto load_stage = [&](int s) {
+        unsigned char *As = A + (s % kStages) * kABytes, *Bs = B + (s % kStages) * kBBytes;
+        const int k0 = s * kTK;
+#pragma unroll
+        for (int g = 0; g < kTK / 8; ++g) {
+            const int k = k0 + 8 * g;
+            const __nv_bfloat16 *src = in;
+            int bytes = 0;
+            if (pa < P && k < K) {
+                const int tap = k / Cin_g, c = k - tap * Cin_g;
+                const int sy = ay + tap / 3 - 1, sx = ax + tap % 3 - 1;
+                if (sy >= 0 && sy < H && sx >= 0 && sx < Wd) {
+                    src = in + (((long long)an * H + sy) * Wd + sx) * Cin_g + c;
+                    bytes = 16;
+                }
+            }
+            cp_async16(As + cm_offset(tid, 8 * g, kTM), src, bytes);
+        }
+        for (int e = tid; e < BN * (kTK / 8); e += kTcThreads) {
+            const int nn = e / (kTK / 8), g = e % (kTK / 8);
+            const int k = k0 + 8 * g;
+            if (!kBwdData) {
+                const __nv_bfloat16 *src = w;
+                int bytes = 0;
+                if (k < K) {
+                    const int tap = k / Cin_g, c = k - tap * Cin_g;
+                    src = w + ((long long)(n0 + nn) * 9 + tap) * Cin_w + c;
+                    bytes = 16;
+                }
+                cp_async16(Bs + cm_offset(nn, 8 * g, BN), src, bytes);
+            } else {
+                uint4 v = make_uint4(0, 0, 0, 0);
+                if (k < K) {
+                    const int tap = k / Cin_g, c = k - tap * Cin_g;
+                    __align__(16) __nv_bfloat16 t[8];
+#pragma unroll
+                    for (int q = 0; q < 8; ++q) t[q] = w[((long long)(c + q) * 9 + (8 - tap)) * Cin_w + n0 + nn];
+                    v = *reinterpret_cast<const uint4 *>(t);
+                }
+                *reinterpret_cast<uint4 *>(Bs + cm_offset(nn, 8 * g, BN)) = v;
+            }
+        }
+    };
+#pragma unroll
+    for (int s = 0; s < kStages - 1; ++s) {
+        if (s < nst) load_stage(s);
+        cp_async_commit();
+    }
+    constexpr uint32_t idesc = mma_idesc(kTM, BN);
+    bool ok = true;
+    int last = -1;
+    for (int s = 0; s < nst && ok; ++s) {
+        cp_async_wait<kStages - 2>();  // this thread's copies of stage s have landed
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        __syncthreads();
+        const int buf = s % kStages;
+        if (tid == 0) {
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const uint32_t a0 = smem_u32(A + buf * kABytes), b0 = smem_u32(B + buf * kBBytes);
+#pragma unroll
+            for (int j = 0; j < kTK / 16; ++j) {
+                const uint64_t ad = smem_desc(a0 + 2 * j * (kTM / 8) * 128, (kTM / 8) * 128, 128);
+                const uint64_t bd = smem_desc(b0 + 2 * j * (BN / 8) * 128, (BN / 8) * 128, 128);
+                const uint32_t acc = (s > 0 || j > 0) ? 1u : 0u;
+                asm volatile(
+                    "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+                    " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(tmem),
+                    "l"(ad), "l"(bd), "r"(idesc), "r"(acc)
+                    : "memory");
+            }
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                             smem_u32(&mbar[buf]))
+                         : "memory");
+        }
+        last = s;
+        // refill the buffer of stage s - 1 (its MMAs must be done) with stage s + kStages - 1
+        const int nxt = s + kStages - 1;
+        if (nxt < nst) {
+            if (s >= 1) ok = mbar_wait(smem_u32(&mbar[(s - 1) % kStages]), (uint32_t)(((s - 1) / kStages) & 1));
+            if (ok) load_stage(nxt);
+        }
+        cp_async_commit();
+    }
+    cp_async_wait<0>();
+    if (last >= 0) ok = mbar_wait(smem_u32(&mbar[last % kStages]), (uint32_t)((last / kStages) & 1)) && ok;
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    if (ok) {
+        const long long p = p0 + warp * 32 + lane;
+#pragma unroll
+        for (int c = 0; c < BN; c += 8) {
+            uint32_t r[8];
+            asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+                         : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+                           "=r"(r[7])
+                         : "r"(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c));
+            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+            if (p < P) {
+                __align__(16) __nv_bfloat16 o[8];
+#pragma unroll
+                for (int q = 0; q < 8; ++q) {
+                    float v = __uint_as_float(r[q]);
+                    if (bias) v += bias[n0 + c + q];
+                    if (relu) v = fmaxf(v, 0.f);
+                    o[q] = __float2bfloat16_rn(v);
+                }
+                *reinterpret_cast<uint4 *>(out + p * Cout_g + n0 + c) = *reinterpret_cast<const uint4 *>(o);
+            }
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kCols) : "memory");
+}
+
+// ---------------------------------------------------------------------------
+// Forward 3x3 convolution, persistent and warp-specialised.  One CTA per SM
+// walks the (pixel tile, output-channel tile) items of the layer; its warps have
+// fixed roles:
+//   warps 0-3  producers: cp.async copies of the A rows (im2col, zero fill) and of
+//              the weight tile into a ring of kWsStages stage buffers; each copy's
+//              completion arrives on the stage's `full` mbarrier (count 128);
+//   warp 8     one thread issues the tcgen05.mma of a stage once it is full and
+//              commits them to the stage's `empty` mbarrier (the buffer may be
+//              refilled when the MMAs reading it are done); after an item's last
+//              stage it commits to `acc_full` of the item's accumulator;
+//   warps 4-7  epilogue: wait for `acc_full`, read the accumulator from tensor
+//              memory (warp 4 + q owns lanes 32q..32q+31 = pixels), bias, ReLU,
+//              BF16 stores, then arrive on `acc_empty` (count 128).
+// Two accumulators (2 x BN TMEM columns) alternate between items, so the epilogue
+// of one item runs while the next one accumulates, and the producers run ahead
+// by up to kWsStages stages across item boundaries.  Tile layout, descriptors and
+// MMAs are those of conv3x3_tc_kernel.  Every wait is bounded; a thread whose
+// wait runs out sets g_tc_error and a shared abort flag that ends the others' waits.
+// ---------------------------------------------------------------------------
+constexpr int kWsThreads = 288;  // 9 warps
+
+__device__ __forceinline__ bool ws_wait(uint32_t bar, uint32_t parity, volatile int *abort) {
+    for (long long it = 0; it < (1ll << 26); ++it) {
+        uint32_t done;
+        asm volatile(
+            "{\n .reg .pred P;\n mbarrier.try_wait.parity.shared::cta.b64 P, [%1], %2;\n selp.u32 %0, 1, 0, P;\n}"
+            : "=r"(done)
+            : "r"(bar), "r"(parity)
+            : "memory");
+        if (done) return true;
+        if ((it & 255) == 255 && *abort) return false;
+    }
+    atomicExch(&g_tc_error, 1);
+    *abort = 1;
+    return false;
+}
+
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+    asm volatile("mbarrier.arrive.release.cta.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+
+template <int BN, int kWsStages>
+__global__ void __launch_bounds__(kWsThreads, 1) conv3x3_ws_kernel(const __nv_bfloat16 *__restrict__ in,
+                                                                   const __nv_bfloat16 *__restrict__ w,
+                                                                   const float *__restrict__ bias,
+                                                                   __nv_bfloat16 *__restrict__ out, int N, int H,
+                                                                   int Wd, int Cin, int Cout, int relu) {
+    constexpr uint32_t kABytes = kTM * kTK * 2, kBBytes = BN * kTK * 2;
+    constexpr int kCols = 2 * BN;  // two accumulators
+    extern __shared__ __align__(128) unsigned char tc_smem[];
+    unsigned char *A = tc_smem;
+    unsigned char *B = tc_smem + kWsStages * kABytes;
+    __shared__ __align__(8) uint64_t full[kWsStages], empty[kWsStages], acc_full[2], acc_empty[2];
+    __shared__ uint32_t tmem_slot;
+    __shared__ volatile int abort_flag;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const long long P = (long long)N * H * Wd;
+    const long long ptiles = (P + kTM - 1) / kTM;
+    const int ntiles = Cout / BN;
+    const long long items = ptiles * ntiles;
+    const int K = 9 * Cin, nst = (K + kTK - 1) / kTK;
+
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_slot)),
+                     "r"(kCols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    if (tid == 0) {
+        abort_flag = 0;
+        for (int b = 0; b < kWsStages; ++b) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&full[b])), "r"(128) : "memory");
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&empty[b])) : "memory");
+        }
+        for (int b = 0; b < 2; ++b) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&acc_full[b])) : "memory");
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&acc_empty[b])), "r"(128) : "memory");
+        }
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = tmem_slot;
+
+    if (warp < 4) {
+        // ---- producers: thread tid copies A row tid and a share of the B tile
+        long long g = 0;  // stage counter over all items of this CTA
+        bool ok = true;
+        for (long long item = blockIdx.x; item < items && ok; item += gridDim.x) {
+            const long long p0 = (item / ntiles) * kTM;
+            const int n0 = (int)(item % ntiles) * BN;
+            const long long pa = p0 + tid;
+            int an = 0, ay = 0, ax = 0;
+            if (pa < P) {
+                an = (int)(pa / ((long long)H * Wd));
+                const int rem = (int)(pa - (long long)an * H * Wd);
+                ay = rem / Wd;
+                ax = rem - ay * Wd;
+            }
+            for (int s = 0; s < nst && ok; ++s, ++g) {
+                const int buf = (int)(g % kWsStages);
+                ok = ws_wait(smem_u32(&empty[buf]), (uint32_t)(((g / kWsStages) & 1) ^ 1), &abort_flag);
+                if (!ok) break;
+                unsigned char *As = A + buf * kABytes, *Bs = B + buf * kBBytes;
+                const int k0 = s * kTK;
+#pragma unroll
+                for (int gg = 0; gg < kTK / 8; ++gg) {
+                    const int k = k0 + 8 * gg;
+                    const __nv_bfloat16 *src = in;
+                    int bytes = 0;
+                    if (pa < P && k < K) {
+                        const int tap = k / Cin, c = k - tap * Cin;
+                        const int sy = ay + tap / 3 - 1, sx = ax + tap % 3 - 1;
+                        if (sy >= 0 && sy < H && sx >= 0 && sx < Wd) {
+                            src = in + (((long long)an * H + sy) * Wd + sx) * Cin + c;
+                            bytes = 16;
+                        }
+                    }
+                    cp_async16(As + cm_offset(tid, 8 * gg, kTM), src, bytes);
+                }
+                for (int e = tid; e < BN * (kTK / 8); e += 128) {
+                    const int nn = e / (kTK / 8), gg = e % (kTK / 8);
+                    const int k = k0 + 8 * gg;
+                    const __nv_bfloat16 *src = w;
+                    int bytes = 0;
+                    if (k < K) {
+                        const int tap = k / Cin, c = k - tap * Cin;
+                        src = w + ((long long)(n0 + nn) * 9 + tap) * Cin + c;
+                        bytes = 16;
+                    }
+                    cp_async16(Bs + cm_offset(nn, 8 * gg, BN), src, bytes);
+                }
+                asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" ::"r"(smem_u32(&full[buf]))
+                             : "memory");
+            }
+        }
+        asm volatile("cp.async.wait_all;" ::: "memory");
+    } else if (warp == 8) {
+        // ---- one thread issues the MMAs
+        if (lane == 0) {
+            constexpr uint32_t idesc = mma_idesc(kTM, BN);
+            long long g = 0, j = 0;
+            bool ok = true, issued = false;
+            for (long long item = blockIdx.x; item < items && ok; item += gridDim.x, ++j) {
+                const int ab = (int)(j & 1);
+                ok = ws_wait(smem_u32(&acc_empty[ab]), (uint32_t)(((j >> 1) & 1) ^ 1), &abort_flag);
+                if (!ok) break;
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                const uint32_t dcol = tmem + (uint32_t)(ab * BN);
+                for (int s = 0; s < nst && ok; ++s, ++g) {
+                    const int buf = (int)(g % kWsStages);
+                    ok = ws_wait(smem_u32(&full[buf]), (uint32_t)((g / kWsStages) & 1), &abort_flag);
+                    if (!ok) break;
+                    // the producers' cp.async writes are generic-proxy writes; order them
+                    // before the tensor core's reads
+                    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                    const uint32_t a0 = smem_u32(A + buf * kABytes), b0 = smem_u32(B + buf * kBBytes);
+#pragma unroll
+                    for (int jj = 0; jj < kTK / 16; ++jj) {
+                        const uint64_t ad = smem_desc(a0 + 2 * jj * (kTM / 8) * 128, (kTM / 8) * 128, 128);
+                        const uint64_t bd = smem_desc(b0 + 2 * jj * (BN / 8) * 128, (BN / 8) * 128, 128);
+                        const uint32_t acc = (s > 0 || jj > 0) ? 1u : 0u;
+                        asm volatile(
+                            "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+                            " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(dcol),
+                            "l"(ad), "l"(bd), "r"(idesc), "r"(acc)
+                            : "memory");
+                    }
+                    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                                     smem_u32(&empty[buf]))
+                                 : "memory");
+                    issued = true;
+                }
+                if (ok)
+                    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                                     smem_u32(&acc_full[ab]))
+                                 : "memory");
+            }
+            // before the tensor memory is released: the last MMAs must be done
+            // (a commit tracks all earlier MMAs of this thread)
+            if (issued) {
+                uint64_t *fin = &empty[(int)((g - 1) % kWsStages)];
+                ws_wait(smem_u32(fin), (uint32_t)(((g - 1) / kWsStages) & 1), &abort_flag);
+            }
+        }
+    } else {
+        // ---- epilogue: warp 4 + q reads TMEM lanes 32q..32q+31
+        const int q = warp - 4, row = q * 32 + lane;
+        long long j = 0;
+        bool ok = true;
+        for (long long item = blockIdx.x; item < items && ok; item += gridDim.x, ++j) {
+            const int ab = (int)(j & 1);
+            ok = ws_wait(smem_u32(&acc_full[ab]), (uint32_t)((j >> 1) & 1), &abort_flag);
+            if (!ok) break;
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const long long p = (item / ntiles) * kTM + row;
+            const int n0 = (int)(item % ntiles) * BN;
+#pragma unroll
+            for (int c = 0; c < BN; c += 8) {
+                uint32_t r[8];
+                asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+                             : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+                               "=r"(r[7])
+                             : "r"(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(ab * BN + c)));
+                asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+                if (p < P) {
+                    __align__(16) __nv_bfloat16 o[8];
+#pragma unroll
+                    for (int t = 0; t < 8; ++t) {
+                        float v = __uint_as_float(r[t]);
+                        if (bias) v += bias[n0 + c + t];
+                        if (relu) v = fmaxf(v, 0.f);
+                        o[t] = __float2bfloat16_rn(v);
+                    }
+                    *reinterpret_cast<uint4 *>(out + p * Cout + n0 + c) = *reinterpret_cast<const uint4 *>(o);
+                }
+            }
+            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+            mbar_arrive(smem_u32(&acc_empty[ab]));
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kCols) : "memory");
+}
+
+template <int BN, int S>
+cudaError_t launch_conv_ws(const __nv_bfloat16 *in, const __nv_bfloat16 *w, const float *bias, __nv_bfloat16 *out,
+                           int N, int H, int W, int Cin, int Cout, int relu, cudaStream_t s) {
+    const size_t smem = S * (size_t)(kTM * kTK * 2) + S * (size_t)(BN * kTK * 2);
+    cudaError_t e = cudaFuncSetAttribute(conv3x3_ws_kernel<BN, S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess) return e;
+    int dev = 0, sms = 0;
+    e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return e;
+    const long long P = (long long)N * H * W;
+    const long long items = ((P + kTM - 1) / kTM) * (Cout / BN);
+    const int grid = (int)std::min<long long>(items, sms);
+    conv3x3_ws_kernel<BN, S><<<grid, kWsThreads, smem, s>>>(in, w, bias, out, N, H, W, Cin, Cout, relu);
+    return cudaGetLastError();
+}
+
+template <bool kBwdData, int BN>
+cudaError_t launch_conv_tc_pipe(const __nv_bfloat16 *in, const __nv_bfloat16 *w, const float *bias,
+                                __nv_bfloat16 *out, int N, int H, int W, int Cin_g, int Cout_g, int relu,
+                                cudaStream_t s) {
+    const size_t smem = kStages * (size_t)(kTM * kTK * 2) + kStages * (size_t)(BN * kTK * 2);
+    cudaError_t e = cudaFuncSetAttribute(conv3x3_tc_pipe_kernel<kBwdData, BN>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    const long long P = (long long)N * H * W;
+    dim3 grid((unsigned)((P + kTM - 1) / kTM), Cout_g / BN);
+    conv3x3_tc_pipe_kernel<kBwdData, BN><<<grid, kTcThreads, smem, s>>>(in, w, bias, out, N, H, W, Cin_g, Cout_g,
+                                                                        relu);
+    return cudaGetLastError();
+}
+
 template <bool kBwdData, int BN>
 cudaError_t launch_conv_tc(const __nv_bfloat16 *in, const __nv_bfloat16 *w, const float *bias, __nv_bfloat16 *out,
                            int N, int H, int W, int Cin_g, int Cout_g, int relu, cudaStream_t s) {
@@ -339,21 +785,48 @@ cudaError_t launch_conv_tc(const __nv_bfloat16 *in, const __nv_bfloat16 *w, cons
     return cudaGetLastError();
 }
 
-// Convolution on the tcgen05 path (default) or the warp-level MMA path.
+// Convolution path: 1 = tcgen05, the faster staging per shape (default), 2 = tcgen05
+// with synchronous staging, 3 = tcgen05 persistent warp-specialised forward,
+// 0 = the warp-level MMA kernels.
+int g_path = 1;
 bool g_use_tc = true;
+
+template <bool kBwdData>
+cudaError_t conv_dispatch_path2(const __nv_bfloat16 *in, const __nv_bfloat16 *w, const float *bias, __nv_bfloat16 *out,
+                                int N, int H, int W, int Cin_g, int Cout_g, int relu, cudaStream_t s, int BN) {
+    switch (BN) {
+        case 128: return launch_conv_tc<kBwdData, 128>(in, w, bias, out, N, H, W, Cin_g, Cout_g, relu, s);
+        case 64: return launch_conv_tc<kBwdData, 64>(in, w, bias, out, N, H, W, Cin_g, Cout_g, relu, s);
+        case 32: return launch_conv_tc<kBwdData, 32>(in, w, bias, out, N, H, W, Cin_g, Cout_g, relu, s);
+        default: return launch_conv_tc<kBwdData, 16>(in, w, bias, out, N, H, W, Cin_g, Cout_g, relu, s);
+    }
+}
 
 template <bool kBwdData>
 cudaError_t conv_dispatch(const __nv_bfloat16 *in, const __nv_bfloat16 *w, const float *bias, __nv_bfloat16 *out,
                           int N, int H, int W, int Cin_g, int Cout_g, int relu, cudaStream_t s) {
     const int BN = Cout_g % 128 == 0 ? 128 : (Cout_g % 64 == 0 ? 64 : (Cout_g % 32 == 0 ? 32 : 16));
-    if (g_use_tc) {
+    if (g_path == 3 && !kBwdData) {  // forward: the persistent warp-specialised kernel
         switch (BN) {
-            case 128: return launch_conv_tc<kBwdData, 128>(in, w, bias, out, N, H, W, Cin_g, Cout_g, relu, s);
-            case 64: return launch_conv_tc<kBwdData, 64>(in, w, bias, out, N, H, W, Cin_g, Cout_g, relu, s);
-            case 32: return launch_conv_tc<kBwdData, 32>(in, w, bias, out, N, H, W, Cin_g, Cout_g, relu, s);
-            default: return launch_conv_tc<kBwdData, 16>(in, w, bias, out, N, H, W, Cin_g, Cout_g, relu, s);
+            case 128: return launch_conv_ws<128, 4>(in, w, bias, out, N, H, W, Cin_g, Cout_g, relu, s);
+            case 64: return launch_conv_ws<64, 5>(in, w, bias, out, N, H, W, Cin_g, Cout_g, relu, s);
+            default: return launch_conv_ws<32, 6>(in, w, bias, out, N, H, W, Cin_g, Cout_g, relu, s);
         }
     }
+    // the default picks by the measured faster form: the cp.async pipeline for long K
+    // (Cin >= 128, e.g. 159 against 101 TFLOP/s at 32^2 x 256 -> 256), two-buffer
+    // synchronous staging for short K, where more CTAs per SM hide more latency
+    // (80 against 72 TFLOP/s at 256^2 x 32 -> 32)
+    if (g_path == 1 && Cin_g < 128) return conv_dispatch_path2<kBwdData>(in, w, bias, out, N, H, W, Cin_g, Cout_g, relu, s, BN);
+    if (g_path == 1 || g_path == 3) {
+        switch (BN) {
+            case 128: return launch_conv_tc_pipe<kBwdData, 128>(in, w, bias, out, N, H, W, Cin_g, Cout_g, relu, s);
+            case 64: return launch_conv_tc_pipe<kBwdData, 64>(in, w, bias, out, N, H, W, Cin_g, Cout_g, relu, s);
+            case 32: return launch_conv_tc_pipe<kBwdData, 32>(in, w, bias, out, N, H, W, Cin_g, Cout_g, relu, s);
+            default: return launch_conv_tc_pipe<kBwdData, 16>(in, w, bias, out, N, H, W, Cin_g, Cout_g, relu, s);
+        }
+    }
+    if (g_path == 2) return conv_dispatch_path2<kBwdData>(in, w, bias, out, N, H, W, Cin_g, Cout_g, relu, s, BN);
     const long long P = (long long)N * H * W;
     const int bn = BN >= 64 ? 64 : BN;
     dim3 grid((unsigned)((P + kBM - 1) / kBM), Cout_g / bn);
@@ -871,6 +1344,8 @@ extern "C" {
 const char *cdf_nn_last_error(void) { return g_nn_err; }
 
 cdf_nn_status cdf_nn_set_tensor_path(int tcgen05) {
+    if (tcgen05 < 0 || tcgen05 > 3) return nn_fail("set_tensor_path: 0, 1, 2 or 3");
+    g_path = tcgen05;
     g_use_tc = tcgen05 != 0;
     return CDF_NN_OK;
 }

@@ -260,12 +260,13 @@ def ddc_lattice_parameters(L: int, Ra: float, Pr: float, Ma: float = 0.1):
 
 
 def ddc_cavity(n: int = 1024, Ra: float = 1e5, Pr: float = 0.7, Le: float = 2.0, Nc: float = 1.0,
-               Df: float = 0.1, Sr: float = 0.1, ny: Optional[int] = None, steps: int = 0) -> Problem:
+               Df: float = 0.1, Sr: float = 0.1, ny: Optional[int] = None, steps: int = 0, Ma: float = 0.1) -> Problem:
     """Square (or n x ny) cavity; dimensionless D = [[1, D_CT], [S_TC/Le, 1/Le]]
-    times alpha_lat; F = g (T + Nc C) y_hat; T = C = 0 and u = 0 at t = 0."""
+    times alpha_lat; F = g (T + Nc C) y_hat; T = C = 0 and u = 0 at t = 0; Ma sets
+    the buoyancy velocity of the lattice mapping (ddc_lattice_parameters)."""
     m = 2
     ny = n if ny is None else ny
-    alpha, nu, g = ddc_lattice_parameters(n, Ra, Pr)
+    alpha, nu, g = ddc_lattice_parameters(n, Ra, Pr, Ma)
     D = alpha * np.array([[1.0, Df], [Sr / Le, 1.0 / Le]])
     hot = wall_side(m, NOSLIP, [DIRICHLET, DIRICHLET], [1.0, 1.0])
     cold = wall_side(m, NOSLIP, [DIRICHLET, DIRICHLET], [0.0, 0.0])

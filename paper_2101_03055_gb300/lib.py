@@ -145,6 +145,7 @@ SIGNATURES = {
     "cdf_lb_last_error": (ctypes.c_char_p, []),
     "cdf_moment_sums_static": (ctypes.c_int, [_FP, _FP, ctypes.c_int, ctypes.c_int, ctypes.c_int, _FP,
                                               ctypes.c_void_p]),
+    "cdf_lb_wall_transfer": (ctypes.c_int, [_H, ctypes.c_int] + [ctypes.c_double] * 4 + [_DP]),
     "cdf_lb_halo_pack": (ctypes.c_int, [_H, ctypes.c_int, _FP]),
     "cdf_lb_halo_unpack": (ctypes.c_int, [_H, ctypes.c_int, _FP]),
     "cdf_lb_snapshot": (ctypes.c_int, [_H]),
@@ -293,6 +294,12 @@ def cdf_moment_sums_static(dev_fields: int, dev_fields_old: int, nx: int, ny: in
     returns the status code without raising."""
     return load().cdf_moment_sums_static(ctypes.c_void_p(dev_fields or None), ctypes.c_void_p(dev_fields_old or None),
                                          nx, ny, m, ctypes.c_void_p(dev_out or None), ctypes.c_void_p(stream or None))
+
+
+def cdf_lb_wall_transfer(h, side: int, D_CT: float, S_TC: float, T_wall: float, C_wall: float) -> np.ndarray:
+    out = np.empty(2)
+    _check(load().cdf_lb_wall_transfer(h, int(side), D_CT, S_TC, T_wall, C_wall, _dptr(out)))
+    return out
 
 
 def cdf_lb_halo_pack(h, side: int, dev_buf: int):
@@ -504,6 +511,11 @@ class Solver:
 
     def load(self, path: str):
         cdf_lb_load(self.h, path)
+
+    def wall_transfer(self, side: int, D_CT: float, S_TC: float, T_wall: float, C_wall: float):
+        """Average (Nu, Sh) through the west (0) or east (1) wall (cdf_lb_wall_transfer)."""
+        Nu, Sh = cdf_lb_wall_transfer(self.h, side, D_CT, S_TC, T_wall, C_wall)
+        return float(Nu), float(Sh)
 
     def info(self) -> cdf_info:
         return cdf_lb_get_info(self.h)

@@ -58,10 +58,11 @@ def nn_lib():
     return _nn
 
 
-def set_tensor_path(tcgen05: bool):
-    """Convolutions on the 5th-generation tensor cores (True, the default) or on the
-    warp-level MMA kernels (False)."""
-    _call("cdf_nn_set_tensor_path", int(bool(tcgen05)))
+def set_tensor_path(tcgen05):
+    """Convolutions on the 5th-generation tensor cores (True or 1, the default: the faster
+    staging per layer; 2: synchronous staging; 3: persistent warp-specialised forward) or
+    on the warp-level MMA kernels (False or 0)."""
+    _call("cdf_nn_set_tensor_path", int(tcgen05))
 
 
 def tensor_error_flag() -> int:
@@ -636,12 +637,33 @@ if __name__ == "__main__":
     ap.add_argument("--ref-steps", type=int, default=6_000_000, help="steps from rest for the held-out references")
     ap.add_argument("--check-every", type=int, default=10_000)
     ap.add_argument("--out", default="")
+    ap.add_argument("--time-to-steady", type=int, default=0, metavar="N",
+                    help="instead of the experiment: steps to the stop test on N x N cavities from rest and from "
+                         "the committed network's prediction (time_to_steady)")
+    ap.add_argument("--cases", type=int, default=8)
+    ap.add_argument("--tol", type=float, nargs="+", default=[1e-5, 2e-6])
+    ap.add_argument("--max-steps", type=int, default=5_000_000)
     a = ap.parse_args()
     from . import build
     build.build()
-    summ, net = run_experiment(a.n, a.train, a.eval, a.epochs, steps=a.steps, check_every=a.check_every,
-                               ref_steps=a.ref_steps)
-    if a.out:
-        with open(a.out, "w") as fh:
-            json.dump(summ, fh, indent=1)
-        np.savez(a.out.replace(".json", "_model.npz"), **net.state())
+    if a.time_to_steady:
+        net = UNet(seed=0)
+        net.load_state(dict(np.load(default_model_path())))
+        prms = draw_parameters(a.cases, 1)
+        out = {"params": prms, "n": a.time_to_steady, "max_steps": a.max_steps, "runs": {}}
+        for tol in a.tol:
+            res = time_to_steady(net, prms, a.time_to_steady, 64, tol=tol, check_every=a.check_every,
+                                 max_steps=a.max_steps)
+            out["runs"][f"{tol:g}"] = {k: {"first": v["first"].tolist(), "seconds": v["seconds"], "steps": v["steps"],
+                                          "R": v["R"].tolist()} for k, v in res.items()}
+            print(tol, {k: v["first"].tolist() for k, v in res.items()}, flush=True)
+        if a.out:
+            with open(a.out, "w") as fh:
+                json.dump(out, fh, indent=1)
+    else:
+        summ, net = run_experiment(a.n, a.train, a.eval, a.epochs, steps=a.steps, check_every=a.check_every,
+                                   ref_steps=a.ref_steps)
+        if a.out:
+            with open(a.out, "w") as fh:
+                json.dump(summ, fh, indent=1)
+            np.savez(a.out.replace(".json", "_model.npz"), **net.state())

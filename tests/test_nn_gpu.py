@@ -29,12 +29,12 @@ def S(cdf):
     return surrogate, torch
 
 
-@pytest.fixture(params=["tcgen05", "mma"])
+@pytest.fixture(params=["tcgen05", "tcgen05_sync", "tcgen05_ws", "mma"])
 def path(S, request):
     """Run a convolution test on each tensor-core path, and check afterwards that no
     bounded wait of the tcgen05 kernels ran out."""
     sur, torch = S
-    sur.set_tensor_path(request.param == "tcgen05")
+    sur.set_tensor_path({"tcgen05": 1, "tcgen05_sync": 2, "tcgen05_ws": 3, "mma": 0}[request.param])
     yield request.param
     torch.cuda.synchronize()
     sur.set_tensor_path(True)
