@@ -452,6 +452,44 @@ def conv_line(N, H, W, Cin, Cout, reps, device, peak_tflops, peak_gbs):
                          "hbm_frac": nbytes / us / 1e3 / peak_gbs}}
 
 
+def wgrad_line(N, H, W, Cin, Cout, reps, device, peak_tflops, peak_gbs):
+    """The surrogate's 3x3 convolution weight and bias gradient (tcgen05 path: pixel
+    splits into a workspace, then a fixed-order sum) on one layer shape: TFLOP/s of
+    the whole call (its three launches) from CUDA events over `reps` calls, against
+    the measured BF16 tensor peak."""
+    import torch
+    from paper_2101_03055_gb300 import surrogate as sur
+    g = torch.Generator(device="cpu").manual_seed(N * 137 + Cout)
+    x = torch.randn((N, H, W, Cin), generator=g).to(device=device, dtype=torch.bfloat16)
+    dy = torch.randn((N, H, W, Cout), generator=g).to(device=device, dtype=torch.bfloat16)
+    dw = torch.zeros((Cout, 3, 3, Cin), dtype=torch.float32, device=device)
+    db = torch.zeros(Cout, dtype=torch.float32, device=device)
+    sur.set_tensor_path(1)
+    for _ in range(3):
+        sur.conv3x3_bwd_weight(x, dy, dw, db)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(reps):
+        sur.conv3x3_bwd_weight(x, dy, dw, db)
+    e1.record()
+    torch.cuda.synchronize()
+    us = e0.elapsed_time(e1) * 1e3 / reps
+    flops = 2.0 * N * H * W * 9 * Cin * Cout
+    nbytes = 2.0 * N * H * W * (Cin + Cout) + 4.0 * 9 * Cin * Cout
+    tf = flops / us / 1e6
+    bn = 256 if Cout % 256 == 0 else (128 if Cout % 128 == 0 else (64 if Cout % 64 == 0 else 32))
+    return {"description": f"3x3 convolution weight + bias gradient, N={N} {H}x{W}, {Cin}->{Cout} channels, BF16 "
+                           f"operands, FP32 accumulation in tensor memory, pixel splits summed in a fixed order",
+            "value": tf, "unit": "TFLOP/s", "launch_us": us, "flops_per_launch": flops,
+            "kernel": f"conv3x3_wgrad_tc_kernel<{bn}>", "gpu_launches": 3 * reps,
+            "roofline": {"bound": "tensor" if flops / nbytes > peak_tflops * 1e12 / (peak_gbs * 1e9) else "hbm",
+                         "achieved": tf, "peak": peak_tflops, "unit": "TFLOP/s", "frac": tf / peak_tflops,
+                         "traffic": None, "peak_source": "measured BF16 GEMM burst (MEASURED_PEAKS.json bf16_tflops)",
+                         "bytes_per_launch": nbytes, "hbm_gbs": nbytes / us / 1e3,
+                         "hbm_frac": nbytes / us / 1e3 / peak_gbs}}
+
+
 def measured_tensor_peak():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(path):
@@ -491,6 +529,8 @@ def time_to_steady_line(n=256, cases=8, tol=1e-5, check_every=10_000, max_steps=
 
 
 CONV_SHAPES = {"unet_conv3x3_256x256x32": (16, 256, 256, 32, 32), "unet_conv3x3_32x32x256": (16, 32, 32, 256, 256)}
+WGRAD_SHAPES = {"unet_wgrad3x3_256x256x32": (16, 256, 256, 32, 32),
+                "unet_wgrad3x3_32x32x256": (16, 32, 32, 256, 256)}
 
 
 def copy_pass(nbytes: int, device) -> dict:
@@ -792,6 +832,13 @@ def main():
                      "config": {"workload": args.workload}, "dtype": "bf16", "data": "synthetic"})
         print(json.dumps(line), flush=True)
         return
+    if args.workload in WGRAD_SHAPES:  # the weight gradient of one convolution layer, alone (profiling)
+        peak, _ = measured_peaks()
+        line = wgrad_line(*WGRAD_SHAPES[args.workload], max(1, args.steps), device, measured_tensor_peak(), peak)
+        line.update({"metric": "TFLOP/s of the 3x3 convolution weight gradient", "n_gpus": 1, "steps": args.steps,
+                     "config": {"workload": args.workload}, "dtype": "bf16", "data": "synthetic"})
+        print(json.dumps(line), flush=True)
+        return
     if args.split == "slab":
         wl = workload(args.workload, 0)  # one lattice for the whole job
         if not isinstance(wl, I.Problem):
@@ -851,6 +898,8 @@ def main():
             torch.cuda.synchronize()
         for name, shape in CONV_SHAPES.items():
             extra[name] = conv_line(*shape, 50, device, measured_tensor_peak(), peak)
+        for name, shape in WGRAD_SHAPES.items():
+            extra[name] = wgrad_line(*shape, 50, device, measured_tensor_peak(), peak)
         tts = time_to_steady_line()
 
     if rank != 0:

@@ -51,7 +51,9 @@ typedef enum {
     CDF_ENOTCONVERGED = 4, /* run_to_steady reached max_steps above tol */
     CDF_EUNSTABLE = 5,     /* a NaN or Inf appeared in the fields */
     CDF_ETIMEOUT = 6,      /* a bounded device-side wait ran out */
-    CDF_EIO = 7            /* checkpoint file could not be read or written */
+    CDF_EIO = 7,           /* checkpoint file could not be read or written */
+    CDF_ECHECK = 8         /* checks build only: a step kernel met an out-of-range offset, or a
+                              canary pad around a device buffer was overwritten */
 } cdf_status;
 
 /* Population storage.  Every mode stores each population as its deviation from
@@ -427,6 +429,30 @@ void cdf_lb_destroy(cdf_lb *h);
 /* Message of the calling thread's last error ("" if none).  Valid until the
  * thread's next call into the library. */
 const char *cdf_lb_last_error(void);
+
+/* ---- checks build --------------------------------------------------------------
+ * The library can be built a second time with -DCDF_CHECKS (libcdflb_checks.so)
+ * for tests; it computes the same bits as the normal build.  Its step kernels
+ * (2-D single lattice, one and two steps per launch, FP32 and 16-bit storage,
+ * Case 1, the tile-resident and the batched persistent step) test every
+ * population, moment and shared-memory offset against its buffer before the
+ * access; an offset outside is recorded (first one wins) and replaced by an
+ * in-range one, so the launch completes and never leaves its buffers.  Every
+ * device buffer of a lattice and of a batch lies between two 64 KiB canary pads.
+ * cdf_lb_step, cdf_lb_run_to_steady and cdf_batch_step wait for their stream and
+ * return CDF_ECHECK (message: the access site and offset, or the damaged pad)
+ * when either detector fired. */
+
+/* 1 in a checks build, 0 in a normal one. */
+int cdf_checks_enabled(void);
+
+/* Self-test of a checks build's detectors (CDF_EINVAL in a normal build):
+ *   which = 0: one kernel on a 64-float buffer asks for offsets 64..95 through the
+ *              offset check (it reads and writes offset 0 instead);
+ *   which = 1: the host writes one byte of the pad behind a 256-byte buffer.
+ * Returns CDF_ECHECK when the detector caught it (the expected result), CDF_OK
+ * when it did not; the detector's state is reset either way. */
+cdf_status cdf_checks_selftest(int which);
 
 #ifdef __cplusplus
 }

@@ -3,6 +3,11 @@
 Each translation unit is compiled in parallel; the shared library is linked
 only when a source or header is newer than it.  No CMake, no torch extension
 machinery: the library is plain C ABI and loads with ctypes.
+
+build(checks=True) builds the checks library libcdflb_checks.so instead (the
+same sources with -DCDF_CHECKS: offset checks in the step kernels, canary pads
+around device buffers; see include/cdf_lb.h), which the binding loads when the
+environment sets CDF_CHECKS=1.
 """
 from __future__ import annotations
 
@@ -17,10 +22,11 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 OBJ = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libcdflb.so")
+LIB_CHECKS = os.path.join(PKG, "libcdflb_checks.so")
 HEADERS = [os.path.join(ROOT, "include", "cdf_lb.h"), os.path.join(ROOT, "include", "cdf_lb3d.h"),
            os.path.join(ROOT, "include", "cdf_nn.h"), os.path.join(CSRC, "lb_internal.h"), os.path.join(CSRC, "lb_device.cuh")]
 SOURCES = ["lb_kernels.cu", "lb_reduce.cu", "lb_host.cu", "lb_static.cu", "lb_batch.cu", "lb_resident.cu", "lb_split.cu",
-           "lb3d.cu", "nn_kernels.cu"]
+           "lb_checks.cu", "lb3d.cu", "nn_kernels.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-Wall",
          "--expt-relaxed-constexpr"]
@@ -40,8 +46,8 @@ def _stale(target: str, deps) -> bool:
     return any(os.path.getmtime(d) > t for d in deps)
 
 
-def _compile(src: str, extra) -> str:
-    obj = os.path.join(OBJ, os.path.splitext(src)[0] + ".o")
+def _compile(src: str, extra, objdir: str = OBJ) -> str:
+    obj = os.path.join(objdir, os.path.splitext(src)[0] + ".o")
     path = os.path.join(CSRC, src)
     if _stale(obj, [path] + HEADERS):
         cmd = [nvcc(), *ARCH, *FLAGS, *extra, "-c", path, "-o", obj + ".tmp"]
@@ -52,20 +58,22 @@ def _compile(src: str, extra) -> str:
     return obj
 
 
-def build(verbose: bool = False, extra=()) -> str:
-    os.makedirs(OBJ, exist_ok=True)
+def build(verbose: bool = False, extra=(), checks: bool = False) -> str:
+    objdir, lib = (OBJ + "_checks", LIB_CHECKS) if checks else (OBJ, LIB)
+    flags = list(extra) + (["-DCDF_CHECKS"] if checks else [])
+    os.makedirs(objdir, exist_ok=True)
     with cf.ThreadPoolExecutor(max_workers=len(SOURCES)) as ex:
-        objs = list(ex.map(lambda s: _compile(s, list(extra)), SOURCES))
-    if _stale(LIB, objs):
-        tmp = LIB + f".tmp{os.getpid()}"
+        objs = list(ex.map(lambda s: _compile(s, flags, objdir), SOURCES))
+    if _stale(lib, objs):
+        tmp = lib + f".tmp{os.getpid()}"
         cmd = [nvcc(), *ARCH, "-shared", "-o", tmp, *objs, "-lcudart"]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError(f"link failed:\n{r.stderr}")
-        os.replace(tmp, LIB)
+        os.replace(tmp, lib)
     if verbose:
-        print(f"built {LIB}")
-    return LIB
+        print(f"built {lib}")
+    return lib
 
 
 def ptxas_report() -> str:

@@ -197,16 +197,16 @@ void brelease(cdf_batch *b) {
     for (cudaStream_t ps : b->pool) cudaStreamDestroy(ps);
     for (cudaEvent_t e : b->ev_join) cudaEventDestroy(e);
     if (b->ev_fork) cudaEventDestroy(b->ev_fork);
-    cudaFree(b->buf[0]);
-    cudaFree(b->buf[1]);
-    cudaFree(b->sprev);
-    cudaFree(b->sprev2);
-    cudaFree(b->mom);
-    cudaFree(b->mom_prev);
+    dev_free(b->buf[0]);
+    dev_free(b->buf[1]);
+    dev_free(b->sprev);
+    dev_free(b->sprev2);
+    dev_free(b->mom);
+    dev_free(b->mom_prev);
     cudaFree(b->partials);
     cudaFree(b->red);
     if (b->red_host) cudaFreeHost(b->red_host);
-    cudaFree(b->dense);
+    dev_free(b->dense);
     cudaFree(b->d_inst);
     cudaFree(b->d_tile_inst);
     cudaFree(b->d_bar);
@@ -514,16 +514,16 @@ cdf_status cdf_batch_create(int count, const cdf_grid *grids, int m, const cdf_d
     b->extra_arrivals = opt->test_unreachable_barrier ? 1 : 0;
     b->user = static_cast<cudaStream_t>(opt->cuda_stream);
     if (cudaGetDevice(&b->device) != cudaSuccess) { delete b; return bfail(CDF_ECUDA, "no CUDA device"); }
-    bool ok = cudaMalloc(&b->buf[0], b->pop_total * 4) == cudaSuccess &&
-              cudaMalloc(&b->buf[1], b->pop_total * 4) == cudaSuccess &&
-              cudaMalloc(&b->sprev, b->sp_total * 4) == cudaSuccess &&
-              cudaMalloc(&b->sprev2, b->sp_total * 4) == cudaSuccess &&
-              cudaMalloc(&b->mom, b->mom_total * 4) == cudaSuccess &&
-              cudaMalloc(&b->mom_prev, b->mom_total * 4) == cudaSuccess &&
+    bool ok = dev_alloc((void **)&b->buf[0], b->pop_total * 4) == cudaSuccess &&
+              dev_alloc((void **)&b->buf[1], b->pop_total * 4) == cudaSuccess &&
+              dev_alloc((void **)&b->sprev, b->sp_total * 4) == cudaSuccess &&
+              dev_alloc((void **)&b->sprev2, b->sp_total * 4) == cudaSuccess &&
+              dev_alloc((void **)&b->mom, b->mom_total * 4) == cudaSuccess &&
+              dev_alloc((void **)&b->mom_prev, b->mom_total * 4) == cudaSuccess &&
               cudaMalloc(&b->partials, (size_t)reduce_quantities(m) * kReduceBlocks * sizeof(double)) == cudaSuccess &&
               cudaMalloc(&b->red, (size_t)count * reduce_quantities(m) * sizeof(double)) == cudaSuccess &&
               cudaMallocHost(&b->red_host, (size_t)count * reduce_quantities(m) * sizeof(double)) == cudaSuccess &&
-              cudaMalloc(&b->dense, b->stage_floats * 4) == cudaSuccess &&
+              dev_alloc((void **)&b->dense, b->stage_floats * 4) == cudaSuccess &&
               cudaMalloc(&b->d_inst, count * sizeof(BatchInst)) == cudaSuccess &&
               cudaMalloc(&b->d_bar, 2 * sizeof(unsigned)) == cudaSuccess &&
               cudaMalloc(&b->d_err, 4 * sizeof(int)) == cudaSuccess &&
@@ -618,6 +618,7 @@ cdf_status cdf_batch_step(cdf_batch *b, long long n) {
     BCK(cudaStreamSynchronize(b->s));  // the barrier's error flag is read on the host
     cdf_status st = check_err(b);
     if (st != CDF_OK) return st;
+    if ((st = checks_verify(b->s)) != CDF_OK) return st;  // no-op unless built with -DCDF_CHECKS
     BCK(cudaEventRecord(b->ev_out, b->s));
     BCK(cudaStreamWaitEvent(b->user, b->ev_out, 0));
     return CDF_OK;

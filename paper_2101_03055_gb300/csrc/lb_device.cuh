@@ -56,6 +56,31 @@ __device__ __forceinline__ void pdl_wait_and_release() {
     asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
 }
 
+// ---- offset checks (checks builds) -------------------------------------------------
+// CDF_CHK(p, off, lim, site) is `off` itself in a normal build.  With
+// -DCDF_CHECKS it first tests 0 <= off < lim: an offset outside is recorded in
+// the word p.check -- bit 63, the access site in bits 48..62, the offset's low
+// 48 bits -- unless an earlier one is there already, and replaced by 0, so the
+// access that follows stays inside its buffer and the launch completes.  Sites:
+// 1 population load, 2 a node's store offset, 3 shared-memory store,
+// 4 shared-memory load, 5 moment-plane load (16-bit storage), 6 batched-step
+// load, 7 tile-resident global load, 8 tile-resident shared-memory offset.
+#ifdef CDF_CHECKS
+__device__ __forceinline__ long long checked_offset(unsigned long long *word, long long off, long long lim,
+                                                    int site) {
+    if (off >= 0 && off < lim) return off;
+    if (word)
+        atomicCAS(word, 0ull,
+                  (1ull << 63) | ((unsigned long long)(site & 0x7fff) << 48) |
+                      ((unsigned long long)off & 0xffffffffffffull));
+    return 0;
+}
+#define CDF_CHK(p, off, lim, site) \
+    ((decltype(off))::cdflb::dev::checked_offset((p).check, (long long)(off), (long long)(lim), (site)))
+#else
+#define CDF_CHK(p, off, lim, site) (off)
+#endif
+
 // ---- storage types ---------------------------------------------------------------
 // Populations are stored as deviations from a reference state (below) in FP32,
 // FP16 or BF16; every collision is computed in FP32.
@@ -541,8 +566,10 @@ __device__ __forceinline__ void step_node(const LbParams &p, int x, int y, const
     const long long P = p.plane;
     const int pitch = p.pitch;
     const auto mk = [pitch](int sx, int sy) { return sy * pitch + sx; };
-    const auto ld = [in, P](int plane, int off) { return load_pop<T, kL2>(in + plane * P + off); };
-    const int o0 = y * pitch + x;
+    const auto ld = [in, P, &p](int plane, int off) {
+        return load_pop<T, kL2>(in + plane * P + CDF_CHK(p, off, P, 6));
+    };
+    const int o0 = CDF_CHK(p, y * pitch + x, P, 2);
     const bool consume = (M >= 2 && p.skind == 2);
     const float sp1 = consume ? (kL2 ? __ldca(sp_in + o0) : sp_in[o0]) : 0.f;
     float h[9], f[M][5];
@@ -562,8 +589,10 @@ __device__ __forceinline__ void step_node_planes(const LbParams &p, int x, int y
                                                  const float *sp_in, float *sp_out, float *__restrict__ moments) {
     const int pitch = p.pitch;
     const auto mk = [pitch](int sx, int sy) { return sy * pitch + sx; };
-    const auto ld = [&pl](int plane, int off) { return Store<T>::load(pl.in[plane] + off); };
-    const int o0 = y * pitch + x;
+    const auto ld = [&pl, &p](int plane, int off) {
+        return Store<T>::load(pl.in[plane] + CDF_CHK(p, off, p.plane, 1));
+    };
+    const int o0 = CDF_CHK(p, y * pitch + x, p.plane, 2);
     const bool consume = (M >= 2 && p.skind == 2);
     const float sp1 = consume ? sp_in[o0] : 0.f;
     float h[9], f[M][5];

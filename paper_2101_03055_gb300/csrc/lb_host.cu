@@ -159,16 +159,16 @@ void release(cdf_lb *h) {
         for (auto &row : size)
             for (auto &ge : row)
                 if (ge) cudaGraphExecDestroy(ge);
-    cudaFree(h->buf[0]);
-    cudaFree(h->buf[1]);
-    cudaFree(h->sprev_pp[0]);
-    cudaFree(h->sprev_pp[1]);
-    cudaFree(h->vel);
-    cudaFree(h->mom);
-    cudaFree(h->mom_prev);
-    cudaFree(h->mom_pp[0]);
-    cudaFree(h->mom_pp[1]);
-    cudaFree(h->dense);
+    dev_free(h->buf[0]);
+    dev_free(h->buf[1]);
+    dev_free(h->sprev_pp[0]);
+    dev_free(h->sprev_pp[1]);
+    dev_free(h->vel);
+    dev_free(h->mom);
+    dev_free(h->mom_prev);
+    dev_free(h->mom_pp[0]);
+    dev_free(h->mom_pp[1]);
+    dev_free(h->dense);
     cudaFree(h->counters);
     cudaFree(h->d_err);
     if (h->h_err) cudaFreeHost(h->h_err);
@@ -690,6 +690,7 @@ cdf_status cdflb::build_params(const cdf_grid *grid, int m, const cdf_diffusion 
     P.yc = 0.5f * (float)(grid->ny - 1);
     P.row_lo = 0;
     P.row_hi = grid->ny;
+    P.check = check_word();
     P.rho0 = (float)rho0;
     P.periodic_x = bc->west.kind == CDF_BC_PERIODIC;
     P.periodic_y = bc->south.kind == CDF_BC_PERIODIC;
@@ -799,7 +800,7 @@ cdf_status cdf_lb_create(const cdf_grid *grid, int m, const cdf_diffusion *dif, 
     const size_t esz = elem_size(h->storage);
     const size_t pop_bytes = (size_t)h->planes * h->plane * esz;
     const size_t n = (size_t)h->nx * h->ny;
-    auto alloc = [&](void **p, size_t bytes) -> bool { return cudaMalloc(p, bytes) == cudaSuccess; };
+    auto alloc = [&](void **p, size_t bytes) -> bool { return dev_alloc(p, bytes) == cudaSuccess; };
     bool ok = alloc(&h->buf[0], pop_bytes) && alloc(&h->buf[1], pop_bytes) &&
               alloc((void **)&h->sprev_pp[0], (size_t)h->plane * 4) &&
               alloc((void **)&h->sprev_pp[1], (size_t)h->plane * 4) &&
@@ -916,6 +917,7 @@ cdf_status cdf_lb_step(cdf_lb *h, long long n) {
     cdf_status st = enter(h);
     if (st != CDF_OK) return st;
     if ((st = run_steps(h, n)) != CDF_OK) return st;
+    if ((st = checks_verify(h->s)) != CDF_OK) return st;  // no-op unless built with -DCDF_CHECKS
     return leave(h);
 }
 
@@ -950,6 +952,7 @@ cdf_status cdf_lb_run_to_steady(cdf_lb *h, double tol, long long check_every, lo
     }
     if (steps_taken) *steps_taken = taken;
     if (residual) *residual = R;
+    if ((st = checks_verify(h->s)) != CDF_OK) return st;  // no-op unless built with -DCDF_CHECKS
     if ((st = leave(h)) != CDF_OK) return st;
     if (result == CDF_EUNSTABLE) return fail(CDF_EUNSTABLE, "non-finite moments after %lld steps", taken);
     if (result == CDF_ENOTCONVERGED)

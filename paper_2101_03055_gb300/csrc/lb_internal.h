@@ -58,6 +58,10 @@ struct LbParams {
     // neighbouring slab's post-collision populations and are written by the halo
     // exchange instead.
     int row_lo, row_hi;
+    // Checks builds (-DCDF_CHECKS): the device word that records the first
+    // out-of-range offset a step kernel met (see CDF_CHK in lb_device.cuh);
+    // unused (nullptr) in a normal build.
+    unsigned long long *check;
 };
 
 enum Storage { kFP32 = 0, kFP16 = 1, kBF16 = 2 };
@@ -168,5 +172,22 @@ cdf_status build_params(const cdf_grid *grid, int m, const cdf_diffusion *dif, d
 
 // Sets the calling thread's cdf_lb_last_error() message and returns `status`.
 cdf_status report_error(cdf_status status, const char *msg);
+
+// ---- checks builds (lb_checks.cu) ----------------------------------------------
+// A library built with -DCDF_CHECKS tests the offsets of the step kernels'
+// accesses before it makes them (CDF_CHK) and surrounds every device buffer of
+// a lattice with canary pads.  dev_alloc / dev_free are cudaMalloc / cudaFree
+// in a normal build; there check_word() is nullptr and checks_verify returns
+// CDF_OK without touching the stream.  In a checks build checks_verify waits for
+// the stream, then returns CDF_ECHECK (and resets what it found) when the word
+// holds an offset or a pad of a live buffer lost its pattern.
+unsigned long long *check_word();
+cudaError_t dev_alloc(void **p, size_t bytes);
+void dev_free(void *p);
+#ifdef CDF_CHECKS
+cdf_status checks_verify(cudaStream_t s);
+#else
+inline cdf_status checks_verify(cudaStream_t) { return CDF_OK; }
+#endif
 
 }  // namespace cdflb

@@ -136,7 +136,7 @@ __global__ void __launch_bounds__(step2_max_threads(M)) step2_kernel(const LbPar
     // ---- step 1: R1 from global memory into shared memory
     {
         const auto mk = [pitch](int sx, int sy) { return sy * pitch + sx; };
-        const auto ld = [&pl](int plane, int off) { return __ldg(pl.in[plane] + off); };
+        const auto ld = [&pl, &p, P](int plane, int off) { return __ldg(pl.in[plane] + CDF_CHK(p, off, P, 1)); };
         for (int ly = threadIdx.y; ly < H1; ly += blockDim.y) {
             const int yu = Y0 - 1 + ly;
             const bool ok = colv && yu <= min(Y0 + TH, ny) && (p.periodic_y || (yu >= 0 && yu < ny));
@@ -150,7 +150,7 @@ __global__ void __launch_bounds__(step2_max_threads(M)) step2_kernel(const LbPar
                 if (!ok) continue;
                 pull_node<M, false>(p, gx, gy, mk, ld, f, h);
             }
-            const int o0 = gy * pitch + gx, l0 = ly * W1 + lx;
+            const int o0 = CDF_CHK(p, gy * pitch + gx, P, 2), l0 = CDF_CHK(p, ly * W1 + lx, SP, 3);
             NodeOut<M> o;
             collide<M>(p, f, h, pref_at(p, gx, gy), consume ? sp_in[o0] : 0.f, false, o);
 #pragma unroll
@@ -165,7 +165,7 @@ __global__ void __launch_bounds__(step2_max_threads(M)) step2_kernel(const LbPar
     __syncthreads();
 
     // ---- step 2: the tile from shared memory into global memory
-    const auto lds = [SP](int plane, int off) { return sm[plane * SP + off]; };
+    const auto lds = [SP, &p](int plane, int off) { return sm[plane * SP + CDF_CHK(p, off, SP, 4)]; };
     // interior nodes pull from x - c_i without wrapping
     const auto mk_in = [W1, X0, Y0](int sx, int sy) { return (sy - Y0 + 1) * W1 + (sx - X0 + 1); };
     // general nodes: wrapped source coordinates back into R1
@@ -187,9 +187,9 @@ __global__ void __launch_bounds__(step2_max_threads(M)) step2_kernel(const LbPar
             if (!ok) continue;
             pull_node<M, false>(p, x, y, mk_gen, lds, f, h);
         }
-        const int o0 = y * pitch + x;
+        const int o0 = CDF_CHK(p, y * pitch + x, P, 2);
         NodeOut<M> o;
-        collide<M>(p, f, h, pref_at(p, x, y), consume ? sm[NP * SP + ly * W1 + lx] : 0.f, false, o);
+        collide<M>(p, f, h, pref_at(p, x, y), consume ? sm[NP * SP + CDF_CHK(p, ly * W1 + lx, SP, 4)] : 0.f, false, o);
 #pragma unroll
         for (int i = 0; i < 9; ++i) pl.out[i][o0] = h[i];
 #pragma unroll
@@ -216,10 +216,10 @@ __global__ void __launch_bounds__(256) step_kernel_case1(const LbParams p, const
     const long long P = p.plane;
     const int pitch = p.pitch;
     const auto mk = [pitch](int sx, int sy) { return sy * pitch + sx; };
-    const auto ld = [in, P](int plane, int off) { return __ldg(in + plane * P + off); };
-    const int o0 = y * pitch + x;
-    float f[M][5];
+    const auto ld = [in, P, &p](int plane, int off) { return __ldg(in + plane * P + CDF_CHK(p, off, P, 1)); };
     if (x >= p.nx || y >= p.ny) return;
+    const int o0 = CDF_CHK(p, y * pitch + x, P, 2);
+    float f[M][5];
     pull_scalars<M, false>(p, x, y, mk, ld, f);
     const float *vel = p.vel;
     const float ux = __ldg(vel + o0), uy = __ldg(vel + P + o0);
@@ -267,7 +267,7 @@ __global__ void __launch_bounds__(step2_max_threads(M)) step2_kernel_case1(const
     // ---- step 1: R1 from global memory into shared memory
     {
         const auto mk = [pitch](int sx, int sy) { return sy * pitch + sx; };
-        const auto ld = [&pl](int plane, int off) { return __ldg(pl.in[plane] + off); };
+        const auto ld = [&pl, &p, P](int plane, int off) { return __ldg(pl.in[plane] + CDF_CHK(p, off, P, 1)); };
         for (int ly = threadIdx.y; ly < H1; ly += blockDim.y) {
             const int yu = Y0 - 1 + ly;
             const bool ok = colv && yu <= min(Y0 + TH, ny) && (p.periodic_y || (yu >= 0 && yu < ny));
@@ -275,7 +275,7 @@ __global__ void __launch_bounds__(step2_max_threads(M)) step2_kernel_case1(const
             if (!ok) continue;
             float f[M][5];
             pull_scalars<M, false>(p, gx, gy, mk, ld, f);
-            const int o0 = gy * pitch + gx, l0 = ly * W1 + lx;
+            const int o0 = CDF_CHK(p, gy * pitch + gx, P, 2), l0 = CDF_CHK(p, ly * W1 + lx, SP, 3);
             const float ux = __ldg(p.vel + o0), uy = __ldg(p.vel + P + o0);
             float php[M];
 #pragma unroll
@@ -294,7 +294,7 @@ __global__ void __launch_bounds__(step2_max_threads(M)) step2_kernel_case1(const
     __syncthreads();
 
     // ---- step 2: the tile from shared memory into global memory
-    const auto lds = [SP](int plane, int off) { return sm[(plane - 9) * SP + off]; };
+    const auto lds = [SP, &p](int plane, int off) { return sm[(plane - 9) * SP + CDF_CHK(p, off, SP, 4)]; };
     const auto mk_gen = [W1, H1, X0, Y0, nx, ny](int sx, int sy) {
         int a = sx - X0 + 1, b = sy - Y0 + 1;
         a = a < 0 ? a + nx : (a >= W1 ? a - nx : a);
@@ -306,7 +306,7 @@ __global__ void __launch_bounds__(step2_max_threads(M)) step2_kernel_case1(const
         if (!(lx >= 1 && lx <= TW && x < nx && y < ny)) continue;
         float f[M][5];
         pull_scalars<M, false>(p, x, y, mk_gen, lds, f);
-        const int o0 = y * pitch + x, l0 = ly * W1 + lx;
+        const int o0 = CDF_CHK(p, y * pitch + x, P, 2), l0 = CDF_CHK(p, ly * W1 + lx, SP, 4);
         const float ux = __ldg(p.vel + o0), uy = __ldg(p.vel + P + o0);
         float php[M];
 #pragma unroll
@@ -475,17 +475,19 @@ __device__ __forceinline__ void pull_node_mr(const LbParams &p, int x, int y, co
     float hu[9], hv[9], hp[9], hphi[9][M];
 #pragma unroll
     for (int i = 0; i < 9; ++i) {
-        h[i] = Store<T>::load(pl.in[t.hplane[i]] + t.hpos[i]);
-        hu[i] = __ldg(mp.in[M] + t.hpos[i]);
-        hv[i] = __ldg(mp.in[M + 1] + t.hpos[i]);
-        hp[i] = __ldg(mp.in[M + 2] + t.hpos[i]);
+        const int src = CDF_CHK(p, t.hpos[i], p.plane, 5);
+        h[i] = Store<T>::load(pl.in[t.hplane[i]] + src);
+        hu[i] = __ldg(mp.in[M] + src);
+        hv[i] = __ldg(mp.in[M + 1] + src);
+        hp[i] = __ldg(mp.in[M + 2] + src);
 #pragma unroll
-        for (int a = 0; a < M; ++a) hphi[i][a] = __ldg(mp.in[a] + t.hpos[i]);
+        for (int a = 0; a < M; ++a) hphi[i][a] = __ldg(mp.in[a] + src);
     }
 #pragma unroll
     for (int i = 0; i < 5; ++i)
 #pragma unroll
-        for (int a = 0; a < M; ++a) f[a][i] = Store<T>::load(pl.in[9 + 5 * a + t.splane[i]] + t.spos[i]);
+        for (int a = 0; a < M; ++a)
+            f[a][i] = Store<T>::load(pl.in[9 + 5 * a + t.splane[i]] + CDF_CHK(p, t.spos[i], p.plane, 1));
 
     // ---- rebuild the pre-collision populations
 #pragma unroll
@@ -580,7 +582,7 @@ __device__ __forceinline__ void store_node_mr(int o0, const Planes<T> &pl, const
 template <int M, typename T, bool kInterior>
 __device__ __forceinline__ void step_node_mr(const LbParams &p, int x, int y, const Planes<T> &pl,
                                              const MomentPlanes &mp, const float *sp_in, float *sp_out) {
-    const int o0 = y * p.pitch + x;
+    const int o0 = CDF_CHK(p, y * p.pitch + x, p.plane, 2);
     float f[M][5], h[9];
     pull_node_mr<M, T, kInterior>(p, x, y, pl, mp, f, h);
     const bool consume = (M >= 2 && p.skind == 2);
@@ -627,7 +629,7 @@ __global__ void __launch_bounds__(step2_mr_max_threads(M), (M <= 2 ? 3 : 1)) ste
             if (!ok) continue;
             pull_node_mr<M, T, false>(p, gx, gy, pl, mp, f, h);
         }
-        const int o0 = gy * pitch + gx, l0 = ly * W1 + lx;
+        const int o0 = CDF_CHK(p, gy * pitch + gx, p.plane, 2), l0 = CDF_CHK(p, ly * W1 + lx, SP, 3);
         NodeOut<M> o;
         collide<M>(p, f, h, 0.f, consume ? sp_in[o0] : 0.f, false, o);
 #pragma unroll
@@ -641,7 +643,7 @@ __global__ void __launch_bounds__(step2_mr_max_threads(M), (M <= 2 ? 3 : 1)) ste
     __syncthreads();
 
     // ---- step 2: the tile from shared memory into 16-bit deviations and moments
-    const auto lds = [SP](int plane, int off) { return sm[plane * SP + off]; };
+    const auto lds = [SP, &p](int plane, int off) { return sm[plane * SP + CDF_CHK(p, off, SP, 4)]; };
     const auto mk_in = [W1, X0, Y0](int sx, int sy) { return (sy - Y0 + 1) * W1 + (sx - X0 + 1); };
     const auto mk_gen = [W1, H1, X0, Y0, nx, ny](int sx, int sy) {
         int a = sx - X0 + 1, b = sy - Y0 + 1;
@@ -661,9 +663,9 @@ __global__ void __launch_bounds__(step2_mr_max_threads(M), (M <= 2 ? 3 : 1)) ste
             if (!ok) continue;
             pull_node<M, false>(p, x, y, mk_gen, lds, f, h);
         }
-        const int o0 = y * pitch + x;
+        const int o0 = CDF_CHK(p, y * pitch + x, p.plane, 2);
         NodeOut<M> o;
-        collide<M>(p, f, h, 0.f, consume ? sm[NP * SP + ly * W1 + lx] : 0.f, false, o);
+        collide<M>(p, f, h, 0.f, consume ? sm[NP * SP + CDF_CHK(p, ly * W1 + lx, SP, 4)] : 0.f, false, o);
         store_node_mr<M, T>(o0, pl, mp, f, h, o);
         if (consume) sp_out[o0] = o.s1;
     }

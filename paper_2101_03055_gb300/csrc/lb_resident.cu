@@ -84,28 +84,28 @@ __device__ __forceinline__ void resident_node(const LbParams &p, int x, int y, i
     float f[M][5], h[9];
     if (kInterior) {
         const auto mk = [tw, X0, Y0](int sx, int sy) { return (sy - Y0) * tw + (sx - X0); };
-        const auto ld = [A, TS](int plane, int off) { return A[plane * TS + off]; };
+        const auto ld = [A, TS, &p](int plane, int off) { return A[plane * TS + CDF_CHK(p, off, TS, 8)]; };
         pull_node<M, true>(p, x, y, mk, ld, f, h);
     } else {
         const auto mk = [](int sx, int sy) { return make_int2(sx, sy); };
         const auto ld = [=](int plane, int2 c) {
             const int lx = c.x - X0, ly = c.y - Y0;
             return ((unsigned)lx < (unsigned)w && (unsigned)ly < (unsigned)hgt)
-                       ? A[plane * TS + ly * tw + lx]
-                       : __ldcg(in + plane * P + (long long)c.y * pitch + c.x);
+                       ? A[plane * TS + CDF_CHK(p, ly * tw + lx, TS, 8)]
+                       : __ldcg(in + plane * P + CDF_CHK(p, (long long)c.y * pitch + c.x, P, 7));
         };
         pull_node<M, false>(p, x, y, mk, ld, f, h);
     }
     NodeOut<M> o;
     collide<M>(p, f, h, pref_at(p, x, y), sp1, false, o);
-    const int l0 = (y - Y0) * tw + (x - X0);
+    const int l0 = CDF_CHK(p, (y - Y0) * tw + (x - X0), TS, 8);
 #pragma unroll
     for (int i = 0; i < 9; ++i) B[i * TS + l0] = h[i];
 #pragma unroll
     for (int a = 0; a < M; ++a)
 #pragma unroll
         for (int i = 0; i < 5; ++i) B[(9 + 5 * a + i) * TS + l0] = f[a][i];
-    const int o0 = y * pitch + x;
+    const int o0 = CDF_CHK(p, y * pitch + x, P, 2);
     if (to_global) store_node<M, float>(out, P, o0, f, h);
     if (M >= 2 && p.skind == 2) {
         sp1 = o.s1;
@@ -170,7 +170,7 @@ __global__ void __launch_bounds__(kResidentThreads, 1)
     {
         const float *in = parity0 ? buf1 : buf0;
         if (has_node) {
-            const int o0 = y * p.pitch + x, l0 = ly * g.tw + lx;
+            const int o0 = CDF_CHK(p, y * p.pitch + x, P, 2), l0 = CDF_CHK(p, ly * g.tw + lx, TS, 8);
 #pragma unroll
             for (int k = 0; k < NP; ++k) sm[k * TS + l0] = in[k * P + o0];
             if (consume) sp1 = sp_in[o0];

@@ -16,18 +16,23 @@ import numpy as np
 from .inputs import Problem
 
 _PKG = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_PKG, "libcdflb.so")
+# CDF_CHECKS=1 in the environment selects the checks build (built by
+# build.build(checks=True)): offset checks in the step kernels and canary pads
+# around the device buffers, same results.
+CHECKS = os.environ.get("CDF_CHECKS", "0") not in ("", "0")
+LIB_PATH = os.path.join(_PKG, "libcdflb_checks.so" if CHECKS else "libcdflb.so")
 MAX_M = 4
 
-CDF_OK, CDF_EINVAL, CDF_ENOMEM, CDF_ECUDA, CDF_ENOTCONVERGED, CDF_EUNSTABLE, CDF_ETIMEOUT, CDF_EIO = range(8)
+(CDF_OK, CDF_EINVAL, CDF_ENOMEM, CDF_ECUDA, CDF_ENOTCONVERGED, CDF_EUNSTABLE, CDF_ETIMEOUT, CDF_EIO,
+ CDF_ECHECK) = range(9)
 STATUS_NAMES = ["CDF_OK", "CDF_EINVAL", "CDF_ENOMEM", "CDF_ECUDA", "CDF_ENOTCONVERGED",
-                "CDF_EUNSTABLE", "CDF_ETIMEOUT", "CDF_EIO"]
+                "CDF_EUNSTABLE", "CDF_ETIMEOUT", "CDF_EIO", "CDF_ECHECK"]
 STORAGE = {"fp32": 0, "fp16": 1, "bf16": 2}
 
 
 class CdfError(RuntimeError):
     def __init__(self, status, msg):
-        super().__init__(f"{STATUS_NAMES[status] if 0 <= status < 8 else status}: {msg}")
+        super().__init__(f"{STATUS_NAMES[status] if 0 <= status < len(STATUS_NAMES) else status}: {msg}")
         self.status = status
 
 
@@ -189,6 +194,8 @@ SIGNATURES = {
     "cdf_lb3d_get_info": (ctypes.c_int, [_H, ctypes.POINTER(cdf_info3)]),
     "cdf_lb3d_stream": (ctypes.c_void_p, [_H]),
     "cdf_lb3d_destroy": (None, [_H]),
+    "cdf_checks_enabled": (ctypes.c_int, []),
+    "cdf_checks_selftest": (ctypes.c_int, [ctypes.c_int]),
 }
 
 
@@ -197,7 +204,8 @@ def load(path: str = LIB_PATH):
     global _lib
     if _lib is None:
         if not os.path.exists(path):
-            raise RuntimeError(f"libcdflb not built: {path} is missing (run paper_2101_03055_gb300.build.build())")
+            how = "build(checks=True)" if path.endswith("_checks.so") else "build()"
+            raise RuntimeError(f"libcdflb not built: {path} is missing (run paper_2101_03055_gb300.build.{how})")
         lib = ctypes.CDLL(path)
         for name, (res, args) in SIGNATURES.items():
             fn = getattr(lib, name)
@@ -286,6 +294,16 @@ def cdf_lb_destroy(h):
 
 def cdf_lb_last_error() -> str:
     return load().cdf_lb_last_error().decode()
+
+
+def cdf_checks_enabled() -> bool:
+    return bool(load().cdf_checks_enabled())
+
+
+def cdf_checks_selftest(which: int) -> int:
+    """The checks build's detector self-test: CDF_ECHECK when it caught the planted
+    access (0: an offset beyond a device buffer; 1: a byte of a canary pad)."""
+    return int(load().cdf_checks_selftest(int(which)))
 
 
 def cdf_moment_sums_static(dev_fields: int, dev_fields_old: int, nx: int, ny: int, m: int, dev_out: int,
