@@ -91,11 +91,12 @@ cudaError_t dev_alloc(void **p, size_t bytes) {
 
 void dev_free(void *p) {
     if (!p) return;
+    bool padded;
     {
         std::lock_guard<std::mutex> lock(g_mu);
-        g_live.erase(p);
+        padded = g_live.erase(p) == 1;
     }
-    cudaFree(base_of(p));
+    cudaFree(padded ? base_of(p) : p);  // a buffer that dev_alloc did not make has no pads
 }
 
 cdf_status checks_verify(cudaStream_t s) {

@@ -172,8 +172,8 @@ void release(cdf_lb *h) {
     cudaFree(h->counters);
     cudaFree(h->d_err);
     if (h->h_err) cudaFreeHost(h->h_err);
-    cudaFree(h->partials);
-    cudaFree(h->red);
+    dev_free(h->partials);
+    dev_free(h->red);
     if (h->red_host) cudaFreeHost(h->red_host);
     if (h->host_stage) cudaFreeHost(h->host_stage);
     if (h->ev_in) cudaEventDestroy(h->ev_in);
