@@ -112,15 +112,21 @@ __global__ void __launch_bounds__(256) step_kernel_flat(const LbParams p, const 
 // periodic y axis (a wrapped source must not land twice in R1).  S_1 is read
 // from sp_in and written to sp_out, which must be different planes: the halo
 // of one CTA is the tile of another.
-template <int M>
-__global__ void __launch_bounds__(step2_max_threads(M)) step2_kernel(const LbParams p, int TH, const Planes<float> pl,
-                                                                     const float *sp_in, float *sp_out,
-                                                                     float *__restrict__ moments) {
+// FW, FY, FT != 0: a copy for one CTA shape FW x FY and tile height FT (the
+// launch must match; blockDim and the TH argument are then not read).  With the
+// shape known, the shared-memory plane stride is a constant, every
+// shared-memory access is a register plus an immediate offset and the row
+// loops unroll; the node update is the same, so are the bits.
+template <int M, int FW = 0, int FY = 0, int FT = 0>
+__global__ void __launch_bounds__(FW ? FW * FY : step2_max_threads(M), FW ? step2_max_threads(M) / (FW * FY) : 1)
+    step2_kernel(const LbParams p, int TH, const Planes<float> pl, const float *sp_in, float *sp_out,
+                 float *__restrict__ moments) {
     constexpr int NP = 9 + 5 * M;
     extern __shared__ float sm[];
     pdl_wait_and_release();
-    const int W1 = blockDim.x, H1 = TH + 2, SP = W1 * H1, TW = W1 - 2;
-    const int X0 = blockIdx.x * TW, Y0 = blockIdx.y * TH;
+    const int W1 = FW ? FW : (int)blockDim.x, BY = FY ? FY : (int)blockDim.y, THv = FT ? FT : TH;
+    const int H1 = THv + 2, SP = W1 * H1, TW = W1 - 2;
+    const int X0 = blockIdx.x * TW, Y0 = blockIdx.y * THv;
     const long long P = p.plane;
     const int pitch = p.pitch, nx = p.nx, ny = p.ny;
     const bool consume = M >= 2 && p.skind == 2;
@@ -137,9 +143,10 @@ __global__ void __launch_bounds__(step2_max_threads(M)) step2_kernel(const LbPar
     {
         const auto mk = [pitch](int sx, int sy) { return sy * pitch + sx; };
         const auto ld = [&pl, &p, P](int plane, int off) { return __ldg(pl.in[plane] + CDF_CHK(p, off, P, 1)); };
-        for (int ly = threadIdx.y; ly < H1; ly += blockDim.y) {
+#pragma unroll
+        for (int ly = threadIdx.y; ly < H1; ly += BY) {
             const int yu = Y0 - 1 + ly;
-            const bool ok = colv && yu <= min(Y0 + TH, ny) && (p.periodic_y || (yu >= 0 && yu < ny));
+            const bool ok = colv && yu <= min(Y0 + THv, ny) && (p.periodic_y || (yu >= 0 && yu < ny));
             const int gy = yu < 0 ? yu + ny : (yu >= ny ? yu - ny : yu);
             const bool general = ok && !inner_node(p, gx, gy);
             float h[9], f[M][5];
@@ -175,7 +182,8 @@ __global__ void __launch_bounds__(step2_max_threads(M)) step2_kernel(const LbPar
         b = b < 0 ? b + ny : (b >= H1 ? b - ny : b);
         return b * W1 + a;
     };
-    for (int ly = 1 + threadIdx.y; ly <= TH; ly += blockDim.y) {
+#pragma unroll
+    for (int ly = 1 + threadIdx.y; ly <= THv; ly += BY) {
         const int x = xu, y = Y0 - 1 + ly;
         const bool ok = lx >= 1 && lx <= TW && x < nx && y < ny;
         const bool general = ok && !inner_node(p, x, y);
@@ -600,14 +608,16 @@ __device__ __forceinline__ void step_node_mr(const LbParams &p, int x, int y, co
 // collides and stores deviations and moments.  Per two steps the populations
 // are rounded to 16 bits once, so the results differ from two one-step
 // launches by that saved rounding (both are held to the FP64 oracle).
-template <int M, typename T>
+// FW, FY, FT != 0: a copy for one CTA shape and tile height, as for step2_kernel.
+template <int M, typename T, int FW = 0, int FY = 0, int FT = 0>
 __global__ void __launch_bounds__(step2_mr_max_threads(M), (M <= 2 ? 3 : 1)) step2_kernel_mr(
     const LbParams p, int TH, const Planes<T> pl, const MomentPlanes mp, const float *sp_in, float *sp_out) {
     constexpr int NP = 9 + 5 * M;
     extern __shared__ float sm[];
     pdl_wait_and_release();
-    const int W1 = blockDim.x, H1 = TH + 2, SP = W1 * H1, TW = W1 - 2;
-    const int X0 = blockIdx.x * TW, Y0 = blockIdx.y * TH;
+    const int W1 = FW ? FW : (int)blockDim.x, BY = FY ? FY : (int)blockDim.y, THv = FT ? FT : TH;
+    const int H1 = THv + 2, SP = W1 * H1, TW = W1 - 2;
+    const int X0 = blockIdx.x * TW, Y0 = blockIdx.y * THv;
     const int pitch = p.pitch, nx = p.nx, ny = p.ny;
     const bool consume = M >= 2 && p.skind == 2;
     const int lx = threadIdx.x;
@@ -616,9 +626,10 @@ __global__ void __launch_bounds__(step2_mr_max_threads(M), (M <= 2 ? 3 : 1)) ste
     const int gx = xu < 0 ? xu + nx : (xu >= nx ? xu - nx : xu);
 
     // ---- step 1: R1 from the stored deviations into shared memory (FP32)
-    for (int ly = threadIdx.y; ly < H1; ly += blockDim.y) {
+#pragma unroll
+    for (int ly = threadIdx.y; ly < H1; ly += BY) {
         const int yu = Y0 - 1 + ly;
-        const bool ok = colv && yu <= min(Y0 + TH, ny) && (p.periodic_y || (yu >= 0 && yu < ny));
+        const bool ok = colv && yu <= min(Y0 + THv, ny) && (p.periodic_y || (yu >= 0 && yu < ny));
         const int gy = yu < 0 ? yu + ny : (yu >= ny ? yu - ny : yu);
         const bool general = ok && !inner_node(p, gx, gy);
         float h[9], f[M][5];
@@ -651,7 +662,8 @@ __global__ void __launch_bounds__(step2_mr_max_threads(M), (M <= 2 ? 3 : 1)) ste
         b = b < 0 ? b + ny : (b >= H1 ? b - ny : b);
         return b * W1 + a;
     };
-    for (int ly = 1 + threadIdx.y; ly <= TH; ly += blockDim.y) {
+#pragma unroll
+    for (int ly = 1 + threadIdx.y; ly <= THv; ly += BY) {
         const int x = xu, y = Y0 - 1 + ly;
         const bool ok = lx >= 1 && lx <= TW && x < nx && y < ny;
         const bool general = ok && !inner_node(p, x, y);
@@ -911,6 +923,9 @@ cudaError_t launch_step2(const LbParams &p, const float *in, float *out, const f
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
     if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+    // the shape that the autotuners pick for large lattices and for the batched
+    // sweep has its own copy of the kernel (constant shared-memory strides)
+    const bool fixed = !p.case1 && block.x == 32 && block.y == 8 && th == 14;
     switch (p.m) {
 #define CDF_STEP2_CASE(MM)                                                                               \
     case MM:                                                                                             \
@@ -918,14 +933,21 @@ cudaError_t launch_step2(const LbParams &p, const float *in, float *out, const f
             e = cudaFuncSetAttribute(step2_kernel<MM>, cudaFuncAttributeMaxDynamicSharedMemorySize,      \
                                      kStep2MaxSmem);                                                     \
             if (e == cudaSuccess)                                                                        \
+                e = cudaFuncSetAttribute(step2_kernel<MM, 32, 8, 14>,                                    \
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, kStep2MaxSmem);    \
+            if (e == cudaSuccess)                                                                        \
                 e = cudaFuncSetAttribute(step2_kernel_case1<MM>,                                         \
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, kStep2MaxSmem);    \
             if (e != cudaSuccess) return e;                                                              \
             attr_set[dev][MM].store(true);                                                               \
         }                                                                                                \
-        e = p.case1 ? launch_pdl_smem(step2_kernel_case1<MM>, grid, block, smem, s, p, th, pl, sp_in, sp_out,   \
-                                      moments)                                                           \
-                    : launch_pdl_smem(step2_kernel<MM>, grid, block, smem, s, p, th, pl, sp_in, sp_out, moments); \
+        if (p.case1)                                                                                     \
+            e = launch_pdl_smem(step2_kernel_case1<MM>, grid, block, smem, s, p, th, pl, sp_in, sp_out, moments); \
+        else if (fixed)                                                                                  \
+            e = launch_pdl_smem(step2_kernel<MM, 32, 8, 14>, grid, block, smem, s, p, th, pl, sp_in, sp_out,     \
+                                moments);                                                                \
+        else                                                                                             \
+            e = launch_pdl_smem(step2_kernel<MM>, grid, block, smem, s, p, th, pl, sp_in, sp_out, moments);   \
         break;
         CDF_STEP2_CASE(1)
         CDF_STEP2_CASE(2)
@@ -951,16 +973,22 @@ cudaError_t step2_mr_dispatch(const LbParams &p, const void *in, const float *mi
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
     if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+    const bool fixed = block.x == 32 && block.y == 8 && th == 14;  // the shape with its own copy
     switch (p.m) {
 #define CDF_STEP2MR_CASE(MM)                                                                             \
     case MM:                                                                                             \
         if (!attr_set[dev][MM].load()) {                                                                 \
             e = cudaFuncSetAttribute(step2_kernel_mr<MM, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
                                      kStep2MaxSmem);                                                     \
+            if (e == cudaSuccess)                                                                        \
+                e = cudaFuncSetAttribute(step2_kernel_mr<MM, T, 32, 8, 14>,                              \
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, kStep2MaxSmem);    \
             if (e != cudaSuccess) return e;                                                              \
             attr_set[dev][MM].store(true);                                                               \
         }                                                                                                \
-        e = launch_pdl_smem(step2_kernel_mr<MM, T>, grid, block, smem, s, p, th, pl, mp, sp_in, sp_out);  \
+        e = fixed ? launch_pdl_smem(step2_kernel_mr<MM, T, 32, 8, 14>, grid, block, smem, s, p, th, pl, mp, sp_in, \
+                                    sp_out)                                                              \
+                  : launch_pdl_smem(step2_kernel_mr<MM, T>, grid, block, smem, s, p, th, pl, mp, sp_in, sp_out); \
         break;
         CDF_STEP2MR_CASE(1)
         CDF_STEP2MR_CASE(2)

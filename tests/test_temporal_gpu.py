@@ -52,7 +52,8 @@ def test_two_step_launch_equals_one_step_kernel_bitwise(cdf, pb):
     assert_same(a, b)
 
 
-@pytest.mark.parametrize("shape", [(32, 8, 6), (32, 16, 30), (32, 17, 32), (64, 8, 14), (32, 32, 30), (64, 5, 9)])
+@pytest.mark.parametrize("shape", [(32, 8, 6), (32, 16, 30), (32, 17, 32), (64, 8, 14), (32, 32, 30), (64, 5, 9),
+                                   (32, 8, 14)])
 def test_tile_shapes_bitwise(cdf, shape):
     """CTA shapes with one, two and uneven passes of thread rows, halo regions of
     32 and 64 nodes, tiles that do not divide the lattice."""
@@ -76,6 +77,21 @@ def test_boundaries_bitwise_and_oracle(cdf, oracle_mod, xcase, ycase):
     o = oracle_mod.OracleSim(pb)
     o.step(60)
     assert_parity(a, o, 2)
+
+
+@pytest.mark.parametrize("m", [1, 2, 3, 4])
+@pytest.mark.parametrize("xcase,ycase", [("periodic", "periodic"), ("mixed", "freeslip_dirichlet"),
+                                         ("noslip_noflux", "periodic"), ("freeslip_dirichlet", "mixed")])
+def test_fixed_shape_copy_bitwise(cdf, m, xcase, ycase):
+    """The copy of the two-step kernel compiled for CTAs of 32 x 8 and tiles of
+    30 x 14 (the autotuners' shape for large lattices and for the batched sweep;
+    constant shared-memory strides) against one step per launch, on side pairs
+    whose halo wraps or meets walls and corners, m = 1 .. 4."""
+    pb = _rand_problem(71, 45, m, 20 + m, xcase, ycase)
+    a, b = pair(cdf, pb, (32, 8, 14))
+    a.step(29)
+    b.step(29)
+    assert_same(a, b)
 
 
 @pytest.mark.parametrize("nx,ny,m", [(1, 1, 2), (9, 1, 2), (2, 30, 2), (130, 3, 2), (29, 19, 1), (29, 19, 3),
@@ -174,3 +190,21 @@ def test_16bit_two_step_scalar_counts(cdf, oracle_mod, m):
     o = oracle_mod.OracleSim(pb)
     o.step(40)
     assert_parity(a, o, m, tol=TOL16, populations=False)
+
+
+@pytest.mark.parametrize("storage", ["fp16", "bf16"])
+@pytest.mark.parametrize("m,xcase,ycase", [(2, "periodic", "periodic"), (2, "mixed", "freeslip_dirichlet"),
+                                           (1, "noslip_noflux", "periodic"), (3, "freeslip_dirichlet", "mixed"),
+                                           (4, "periodic", "noslip_noflux")])
+def test_16bit_two_step_fixed_copy_bitwise(cdf, storage, m, xcase, ycase):
+    """A node's two steps do not depend on the tile it is computed in (a halo node
+    is recomputed by each CTA with the same arithmetic), so the copy of the 16-bit
+    two-step kernel compiled for CTAs of 32 x 8 and tiles of 30 x 14 must give the
+    bits of the general kernel run with another shape."""
+    pb = _rand_problem(71, 45, m, 30 + m, xcase, ycase)
+    a = cdf.Solver(pb, storage=storage, temporal=1, resident=-1, temporal_shape=(32, 8, 14))
+    b = cdf.Solver(pb, storage=storage, temporal=1, resident=-1, temporal_shape=(32, 16, 14))
+    for n in (2, 31):
+        a.step(n)
+        b.step(n)
+    assert_same(a, b)
