@@ -454,8 +454,8 @@ def conv_line(N, H, W, Cin, Cout, reps, device, peak_tflops, peak_gbs):
 
 def wgrad_line(N, H, W, Cin, Cout, reps, device, peak_tflops, peak_gbs):
     """The surrogate's 3x3 convolution weight and bias gradient (tcgen05 path: pixel
-    splits into a workspace, then a fixed-order sum) on one layer shape: TFLOP/s of
-    the whole call (its three launches) from CUDA events over `reps` calls, against
+    splits into a workspace, then fixed-order sums) on one layer shape: TFLOP/s of
+    the whole call (its four launches) from CUDA events over `reps` calls, against
     the measured BF16 tensor peak."""
     import torch
     from paper_2101_03055_gb300 import surrogate as sur
@@ -482,7 +482,7 @@ def wgrad_line(N, H, W, Cin, Cout, reps, device, peak_tflops, peak_gbs):
     return {"description": f"3x3 convolution weight + bias gradient, N={N} {H}x{W}, {Cin}->{Cout} channels, BF16 "
                            f"operands, FP32 accumulation in tensor memory, pixel splits summed in a fixed order",
             "value": tf, "unit": "TFLOP/s", "launch_us": us, "flops_per_launch": flops,
-            "kernel": f"conv3x3_wgrad_tc_kernel<{bn}>", "gpu_launches": 3 * reps,
+            "kernel": f"conv3x3_wgrad_tc_kernel<{bn}>", "gpu_launches": 4 * reps,
             "roofline": {"bound": "tensor" if flops / nbytes > peak_tflops * 1e12 / (peak_gbs * 1e9) else "hbm",
                          "achieved": tf, "peak": peak_tflops, "unit": "TFLOP/s", "frac": tf / peak_tflops,
                          "traffic": None, "peak_source": "measured BF16 GEMM burst (MEASURED_PEAKS.json bf16_tflops)",

@@ -35,10 +35,11 @@ cdf_nn_status cdf_nn_conv3x3_bwd_data(const void *dy, const void *w, void *dx, i
                                       void *stream);
 /* dw[co][t][ci] += sum_p dy[p][co] x[p + d(t)][ci] and db[co] += sum_p dy[p][co]
  * (FP32, accumulated: zero them first).  db may be NULL.  On the tensor-core path
- * the pixels are split over the GPU, each split's partial sums go to `workspace`
- * (device memory of at least cdf_nn_conv3x3_bwd_weight_workspace() bytes, owned by
- * the caller, contents overwritten) and are added in a fixed order: the result is
- * the same bits on every run.  The warp-level MMA path adds its partial sums
+ * the pixels are split over the GPU for dw and, separately, for db; each split's
+ * partial sums go to `workspace` (device memory of at least
+ * cdf_nn_conv3x3_bwd_weight_workspace() bytes, owned by the caller, contents
+ * overwritten) and are added in a fixed order: the result is the same bits on
+ * every run.  The warp-level MMA path adds its partial sums
  * atomically (order-dependent) and ignores the workspace. */
 cdf_nn_status cdf_nn_conv3x3_bwd_weight(const void *x, const void *dy, float *dw, float *db, int N, int H, int W,
                                         int Cin, int Cout, void *workspace, long long workspace_bytes, void *stream);

@@ -1074,12 +1074,17 @@ __global__ void wgrad_reduce_kernel(const float *__restrict__ part, float *__res
     dw[i] += acc;
 }
 
-// Bias gradient with a fixed summation order: db[c] += sum_p dY[p][c], one block of
-// 256 threads per 8 channels, each thread a strided run of pixels, a tree in shared memory.
-__global__ void bias_grad_det_kernel(const __nv_bfloat16 *__restrict__ dy, float *__restrict__ db, long long P, int C) {
+// Bias gradient with a fixed summation order, db[c] += sum_p dY[p][c], in two
+// passes: bias_partial_kernel gives each block of 256 threads 8 channels and one
+// run of `per` pixels (each thread a strided part of the run, then a tree in
+// shared memory) and writes its sums to part[split][c]; bias_sum_kernel adds the
+// splits in order.
+__global__ void bias_partial_kernel(const __nv_bfloat16 *__restrict__ dy, float *__restrict__ part, long long P,
+                                    int C, long long per) {
     const int c0 = blockIdx.x * 8;
+    const long long p0 = (long long)blockIdx.y * per, p1 = min(P, p0 + per);
     float s[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-    for (long long p = threadIdx.x; p < P; p += blockDim.x) {
+    for (long long p = p0 + threadIdx.x; p < p1; p += blockDim.x) {
         const uint4 v = *reinterpret_cast<const uint4 *>(dy + p * C + c0);
         const __nv_bfloat16 *e = reinterpret_cast<const __nv_bfloat16 *>(&v);
 #pragma unroll
@@ -1095,7 +1100,25 @@ __global__ void bias_grad_det_kernel(const __nv_bfloat16 *__restrict__ dy, float
             for (int q = 0; q < 8; ++q) red[q][threadIdx.x] += red[q][threadIdx.x + st];
         __syncthreads();
     }
-    if (threadIdx.x < 8) db[c0 + threadIdx.x] += red[threadIdx.x][0];
+    if (threadIdx.x < 8) part[(long long)blockIdx.y * C + c0 + threadIdx.x] = red[threadIdx.x][0];
+}
+
+__global__ void bias_sum_kernel(const float *__restrict__ part, float *__restrict__ db, int C, int splits) {
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= C) return;
+    float acc = 0.f;
+    for (int z = 0; z < splits; ++z) acc += part[(long long)z * C + c];
+    db[c] += acc;
+}
+
+// Pixel splits of the bias gradient: about two blocks per SM over the C / 8
+// channel groups, at least 2048 pixels a split.
+long long bias_splits(long long P, int C) {
+    const long long groups = C / 8;
+    long long s = (304 + groups - 1) / groups;
+    const long long cap = (P + 2047) / 2048;
+    if (s > cap) s = cap;
+    return s < 1 ? 1 : s;
 }
 
 // The weight gradient's tiling: output-channel tile BN (the largest of 256, 128,
@@ -1381,8 +1404,9 @@ cdf_nn_status cdf_nn_conv3x3_bwd_data(const void *dy, const void *w, void *dx, i
 
 long long cdf_nn_conv3x3_bwd_weight_workspace(int N, int H, int W, int Cin, int Cout) {
     if (N < 1 || H < 1 || W < 1 || Cin < 16 || Cin % 16 || Cout < 32 || Cout % 32) return -1;
-    const WgradPlan w = wgrad_plan((long long)N * H * W, Cin, Cout);
-    return (long long)w.splits * 9 * Cin * Cout * (long long)sizeof(float);
+    const long long P = (long long)N * H * W;
+    const WgradPlan w = wgrad_plan(P, Cin, Cout);
+    return ((long long)w.splits * 9 * Cin * Cout + bias_splits(P, Cout) * Cout) * (long long)sizeof(float);
 }
 
 cdf_nn_status cdf_nn_conv3x3_bwd_weight(const void *x, const void *dy, float *dw, float *db, int N, int H, int W,
@@ -1410,7 +1434,12 @@ cdf_nn_status cdf_nn_conv3x3_bwd_weight(const void *x, const void *dy, float *dw
         if (e != cudaSuccess) { cudaGetLastError(); return nn_fail(cudaGetErrorString(e)); }
         const long long n = 9LL * Cin * Cout;
         wgrad_reduce_kernel<<<blocks_for(n), 256, 0, s>>>(part, dw, 9 * Cin, Cout, w.splits);
-        if (db) bias_grad_det_kernel<<<Cout / 8, 256, 0, s>>>(dyb, db, P, Cout);
+        if (db) {
+            float *bpart = part + (long long)w.splits * 9 * Cin * Cout;  // after the weight partials
+            const long long bs = bias_splits(P, Cout), per = (P + bs - 1) / bs;
+            bias_partial_kernel<<<dim3(Cout / 8, (unsigned)bs), 256, 0, s>>>(dyb, bpart, P, Cout, per);
+            bias_sum_kernel<<<(Cout + 127) / 128, 128, 0, s>>>(bpart, db, Cout, (int)bs);
+        }
     } else {
         // the warp-level MMA path: split-K partial sums added atomically (order-dependent)
         const long long per = 4096;

@@ -61,7 +61,7 @@ def test_conv_forward(S, path, N, H, W, Cin, Cout):
 
 @pytest.mark.parametrize("N,H,W,Cin,Cout", [(2, 9, 13, 16, 32), (1, 8, 8, 64, 64), (2, 5, 7, 96, 32),
                                             (1, 4, 4, 384, 128), (2, 24, 20, 128, 64), (1, 16, 12, 128, 256),
-                                            (2, 64, 64, 32, 32), (1, 40, 40, 64, 512)])
+                                            (2, 64, 64, 32, 32), (1, 40, 40, 64, 512), (2, 96, 96, 32, 32)])
 def test_conv_backward(S, path, N, H, W, Cin, Cout):
     sur, torch = S
     r = np.random.default_rng(N * 7 + Cin)
