@@ -203,7 +203,7 @@ def test_16bit_two_step_fixed_copy_bitwise(cdf, storage, m, xcase, ycase):
     bits of the general kernel run with another shape."""
     pb = _rand_problem(71, 45, m, 30 + m, xcase, ycase)
     a = cdf.Solver(pb, storage=storage, temporal=1, resident=-1, temporal_shape=(32, 8, 14))
-    b = cdf.Solver(pb, storage=storage, temporal=1, resident=-1, temporal_shape=(32, 16, 14))
+    b = cdf.Solver(pb, storage=storage, temporal=1, resident=-1, temporal_shape=(32, 4, 14))
     for n in (2, 31):
         a.step(n)
         b.step(n)
