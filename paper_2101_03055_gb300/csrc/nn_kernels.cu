@@ -926,21 +926,25 @@ __device__ __forceinline__ void transpose8x8(const uint4 (&in)[8], uint4 (&out)[
         for (int k = 0; k < 8; ++k) o[c * 8 + k] = e[k * 8 + c];
 }
 
-template <int BN>
+template <int BN, int MT>
 __global__ void __launch_bounds__(kTcThreads) conv3x3_wgrad_tc_kernel(const __nv_bfloat16 *__restrict__ x,
                                                                       const __nv_bfloat16 *__restrict__ dy,
                                                                       float *__restrict__ part, int N, int H, int Wd,
                                                                       int Cin, int Cout, long long pix_per_split) {
-    constexpr int kCols = BN < 32 ? 32 : BN;
+    // MT accumulators of 128 x BN in tensor memory, columns mt * BN (a power of two >= 32 allocated)
+    constexpr int kNeed = MT * BN;
+    constexpr int kCols = kNeed <= 32 ? 32 : (kNeed <= 64 ? 64 : (kNeed <= 128 ? 128 : (kNeed <= 256 ? 256 : 512)));
     constexpr uint32_t kABytes = kTM * kTK * 2, kBBytes = BN * kTK * 2;
     extern __shared__ __align__(128) unsigned char tc_smem[];
-    unsigned char *A = tc_smem;
-    unsigned char *B = tc_smem + 2 * kABytes;
+    unsigned char *A = tc_smem;                     // [2 stages][MT tiles][kABytes]
+    unsigned char *B = tc_smem + 2 * MT * kABytes;  // [2 stages][kBBytes]
     __shared__ __align__(8) uint64_t mbar[2];
     __shared__ uint32_t tmem_slot;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const long long P = (long long)N * H * Wd;
-    const int M = 9 * Cin, m0 = blockIdx.x * kTM, n0 = blockIdx.z * BN;
+    const int M = 9 * Cin, mtiles = (M + kTM - 1) / kTM;
+    const int t0 = blockIdx.x * MT, n0 = blockIdx.z * BN;
+    const int nt = mtiles - t0 < MT ? mtiles - t0 : MT;  // M tiles of this CTA (>= 1)
     const long long pbeg = (long long)blockIdx.y * pix_per_split;
     const long long pend = pbeg + pix_per_split < P ? pbeg + pix_per_split : P;
     const int nst = (int)((pend - pbeg + kTK - 1) / kTK);
@@ -961,12 +965,21 @@ __global__ void __launch_bounds__(kTcThreads) conv3x3_wgrad_tc_kernel(const __nv
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const uint32_t tmem = tmem_slot;
 
-    // this thread's A block: rows mg*8..+7 (one tap, 8 consecutive channels), pixels kg*8..+7
+    // this thread's A block in each M tile: rows (t0 + mt) * 128 + mg * 8 .. + 7 (one tap, eight
+    // consecutive channels), pixels kg * 8 .. + 7 of the stage
     const int mg = tid >> 3, kg = tid & 7;
-    const int ma = m0 + mg * 8;
-    const bool arow_ok = ma < M;  // M is a multiple of 8 (Cin % 16 == 0)
-    const int tap = arow_ok ? ma / Cin : 0, ci = arow_ok ? ma - tap * Cin : 0;
-    const int ddy = tap / 3 - 1, ddx = tap % 3 - 1;
+    int ddy[MT], ddx[MT], cib[MT];
+    bool rok[MT];
+#pragma unroll
+    for (int mt = 0; mt < MT; ++mt) {
+        const int ma = (t0 + mt) * kTM + mg * 8;
+        rok[mt] = mt < nt && ma < M;  // M is a multiple of 8 (Cin % 16 == 0)
+        const int tap = rok[mt] ? ma / Cin : 0;
+        cib[mt] = rok[mt] ? ma - tap * Cin : 0;
+        ddy[mt] = tap / 3 - 1;
+        ddx[mt] = tap % 3 - 1;
+    }
+    const long long hw = (long long)H * Wd;
     constexpr uint32_t idesc = mma_idesc(kTM, BN);
     bool ok = true;
     int last = -1;
@@ -974,29 +987,48 @@ __global__ void __launch_bounds__(kTcThreads) conv3x3_wgrad_tc_kernel(const __nv
         const int buf = s & 1;
         if (s >= 2) ok = mbar_wait(smem_u32(&mbar[buf]), (uint32_t)(((s - 2) >> 1) & 1));
         if (!ok) break;
-        unsigned char *As = A + buf * kABytes, *Bs = B + buf * kBBytes;
+        unsigned char *Bs = B + buf * kBBytes;
         const long long pk = pbeg + (long long)s * kTK + kg * 8;
-        // A: X at the tap-shifted pixels, 8 channels each (zero outside the image or range)
+        // image coordinates of this thread's eight pixels (one division per stage, then a walk)
+        int pn[8], py[8], px[8];
         {
+            int n = (int)(pk / hw);
+            const int rem = (int)(pk - (long long)n * hw);
+            int yy = rem / Wd, xx = rem - (rem / Wd) * Wd;
+#pragma unroll
+            for (int k = 0; k < 8; ++k) {
+                pn[k] = n;
+                py[k] = yy;
+                px[k] = xx;
+                if (++xx == Wd) {
+                    xx = 0;
+                    if (++yy == H) {
+                        yy = 0;
+                        ++n;
+                    }
+                }
+            }
+        }
+        // A: X at the tap-shifted pixels, 8 channels each (zero outside the image, the range or M)
+#pragma unroll
+        for (int mt = 0; mt < MT; ++mt) {
+            if (mt >= nt) break;
             uint4 v[8], t[8];
 #pragma unroll
             for (int k = 0; k < 8; ++k) {
                 v[k] = make_uint4(0, 0, 0, 0);
-                const long long p = pk + k;
-                if (arow_ok && p < pend) {
-                    const int n = (int)(p / ((long long)H * Wd));
-                    const int rem = (int)(p - (long long)n * H * Wd);
-                    const int yy = rem / Wd + ddy, xx = rem % Wd + ddx;
-                    if (yy >= 0 && yy < H && xx >= 0 && xx < Wd)
-                        v[k] = *reinterpret_cast<const uint4 *>(x + (((long long)n * H + yy) * Wd + xx) * Cin + ci);
-                }
+                const int yy = py[k] + ddy[mt], xx = px[k] + ddx[mt];
+                if (rok[mt] && pk + k < pend && yy >= 0 && yy < H && xx >= 0 && xx < Wd)
+                    v[k] = *reinterpret_cast<const uint4 *>(x + (((long long)pn[k] * H + yy) * Wd + xx) * Cin + cib[mt]);
             }
             transpose8x8(v, t);
+            unsigned char *As = A + (buf * MT + mt) * kABytes;
 #pragma unroll
             for (int c = 0; c < 8; ++c) *reinterpret_cast<uint4 *>(As + cm_offset(mg * 8 + c, kg * 8, kTM)) = t[c];
         }
-        // B: dY rows of the same pixels, 8 output channels per block
-        for (int e = tid; e < (BN / 8) * 8; e += kTcThreads) {
+        // B: dY rows of the same pixels, 8 output channels per block, spread from the last thread
+        // down (the first threads carry the most A work when the last M tile is partial)
+        for (int e = kTcThreads - 1 - tid; e < (BN / 8) * 8; e += kTcThreads) {
             const int ng = e >> 3, kb = e & 7;
             const long long pb = pbeg + (long long)s * kTK + kb * 8;
             uint4 v[8], t[8];
@@ -1013,17 +1045,22 @@ __global__ void __launch_bounds__(kTcThreads) conv3x3_wgrad_tc_kernel(const __nv
         __syncthreads();
         if (tid == 0) {
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            const uint32_t a0 = smem_u32(As), b0 = smem_u32(Bs);
+            const uint32_t b0 = smem_u32(Bs);
 #pragma unroll
-            for (int j = 0; j < kTK / 16; ++j) {
-                const uint64_t ad = smem_desc(a0 + 2 * j * (kTM / 8) * 128, (kTM / 8) * 128, 128);
-                const uint64_t bd = smem_desc(b0 + 2 * j * (BN / 8) * 128, (BN / 8) * 128, 128);
-                const uint32_t acc = (s > 0 || j > 0) ? 1u : 0u;
-                asm volatile(
-                    "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-                    " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(tmem),
-                    "l"(ad), "l"(bd), "r"(idesc), "r"(acc)
-                    : "memory");
+            for (int mt = 0; mt < MT; ++mt) {
+                if (mt >= nt) break;
+                const uint32_t a0 = smem_u32(A + (buf * MT + mt) * kABytes);
+#pragma unroll
+                for (int j = 0; j < kTK / 16; ++j) {
+                    const uint64_t ad = smem_desc(a0 + 2 * j * (kTM / 8) * 128, (kTM / 8) * 128, 128);
+                    const uint64_t bd = smem_desc(b0 + 2 * j * (BN / 8) * 128, (BN / 8) * 128, 128);
+                    const uint32_t acc = (s > 0 || j > 0) ? 1u : 0u;
+                    asm volatile(
+                        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+                        " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(tmem + (uint32_t)(mt * BN)),
+                        "l"(ad), "l"(bd), "r"(idesc), "r"(acc)
+                        : "memory");
+                }
             }
             asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
                              smem_u32(&mbar[buf]))
@@ -1034,26 +1071,30 @@ __global__ void __launch_bounds__(kTcThreads) conv3x3_wgrad_tc_kernel(const __nv
     if (last >= 0) ok = mbar_wait(smem_u32(&mbar[last & 1]), (uint32_t)((last >> 1) & 1)) && ok;
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     if (ok) {
-        // TMEM lane = tile row m; this split's partial tile into part[split][m][co]
+        // TMEM lane = tile row; each tile's partial sums into part[split][m][co]
         // (a split without pixels writes zeros)
-        const int m = m0 + warp * 32 + lane;
-        float *row = part + ((long long)blockIdx.y * M + m) * Cout + n0;
 #pragma unroll
-        for (int c = 0; c < BN; c += 8) {
-            uint32_t r[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-            if (nst > 0) {
-                asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
-                             : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
-                               "=r"(r[7])
-                             : "r"(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c));
-                asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-            }
-            if (m < M) {
-                float4 *d = reinterpret_cast<float4 *>(row + c);
-                d[0] = make_float4(__uint_as_float(r[0]), __uint_as_float(r[1]), __uint_as_float(r[2]),
-                                   __uint_as_float(r[3]));
-                d[1] = make_float4(__uint_as_float(r[4]), __uint_as_float(r[5]), __uint_as_float(r[6]),
-                                   __uint_as_float(r[7]));
+        for (int mt = 0; mt < MT; ++mt) {
+            if (mt >= nt) break;
+            const int m = (t0 + mt) * kTM + warp * 32 + lane;
+            float *row = part + ((long long)blockIdx.y * M + m) * Cout + n0;
+#pragma unroll
+            for (int c = 0; c < BN; c += 8) {
+                uint32_t r[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+                if (nst > 0) {
+                    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+                                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]),
+                                   "=r"(r[6]), "=r"(r[7])
+                                 : "r"(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(mt * BN + c)));
+                    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+                }
+                if (m < M) {
+                    float4 *d = reinterpret_cast<float4 *>(row + c);
+                    d[0] = make_float4(__uint_as_float(r[0]), __uint_as_float(r[1]), __uint_as_float(r[2]),
+                                       __uint_as_float(r[3]));
+                    d[1] = make_float4(__uint_as_float(r[4]), __uint_as_float(r[5]), __uint_as_float(r[6]),
+                                       __uint_as_float(r[7]));
+                }
             }
         }
     }
@@ -1122,17 +1163,23 @@ long long bias_splits(long long P, int C) {
 }
 
 // The weight gradient's tiling: output-channel tile BN (the largest of 256, 128,
-// 64, 32 that divides Cout), pixel splits for about two CTAs per SM in all with at
+// 64, 32 that divides Cout); MT of the 128-row M tiles per CTA, which share each
+// staged tile of dY (at most 256 tensor-memory columns, MT * BN, and three tiles),
+// spread evenly over gx CTAs; pixel splits for about two CTAs per SM in all with at
 // least 16 stages of 64 pixels each, and the pixels per split (a multiple of 64;
 // no split is empty).
 struct WgradPlan {
-    int bn, splits;
+    int bn, mt, gx, splits;
     long long per;
 };
 WgradPlan wgrad_plan(long long P, int Cin, int Cout) {
     WgradPlan w;
     w.bn = Cout % 256 == 0 ? 256 : (Cout % 128 == 0 ? 128 : (Cout % 64 == 0 ? 64 : 32));
-    const long long tiles = (long long)((9 * Cin + kTM - 1) / kTM) * (Cout / w.bn);
+    const int mtiles = (9 * Cin + kTM - 1) / kTM;
+    const int mtmax = w.bn >= 256 ? 1 : (w.bn >= 128 ? 2 : 3);
+    w.gx = (mtiles + mtmax - 1) / mtmax;
+    w.mt = (mtiles + w.gx - 1) / w.gx;
+    const long long tiles = (long long)w.gx * (Cout / w.bn);
     long long s = (304 + tiles - 1) / tiles;
     const long long cap = (P + 16 * kTK - 1) / (16 * kTK);
     if (s > cap) s = cap;
@@ -1142,15 +1189,15 @@ WgradPlan wgrad_plan(long long P, int Cin, int Cout) {
     return w;
 }
 
-template <int BN>
+template <int BN, int MT>
 cudaError_t launch_wgrad_tc(const __nv_bfloat16 *x, const __nv_bfloat16 *dy, float *part, int N, int H, int W,
                             int Cin, int Cout, const WgradPlan &w, cudaStream_t s) {
-    const size_t smem = 2 * (size_t)(kTM * kTK * 2) + 2 * (size_t)(BN * kTK * 2);
-    cudaError_t e = cudaFuncSetAttribute(conv3x3_wgrad_tc_kernel<BN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem);
+    const size_t smem = 2 * MT * (size_t)(kTM * kTK * 2) + 2 * (size_t)(BN * kTK * 2);
+    cudaError_t e = cudaFuncSetAttribute(conv3x3_wgrad_tc_kernel<BN, MT>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    dim3 grid((unsigned)((9 * Cin + kTM - 1) / kTM), (unsigned)w.splits, (unsigned)(Cout / BN));
-    conv3x3_wgrad_tc_kernel<BN><<<grid, kTcThreads, smem, s>>>(x, dy, part, N, H, W, Cin, Cout, w.per);
+    dim3 grid((unsigned)w.gx, (unsigned)w.splits, (unsigned)(Cout / BN));
+    conv3x3_wgrad_tc_kernel<BN, MT><<<grid, kTcThreads, smem, s>>>(x, dy, part, N, H, W, Cin, Cout, w.per);
     return cudaGetLastError();
 }
 
@@ -1425,11 +1472,15 @@ cdf_nn_status cdf_nn_conv3x3_bwd_weight(const void *x, const void *dy, float *dw
         const WgradPlan w = wgrad_plan(P, Cin, Cout);
         float *part = static_cast<float *>(workspace);
         cudaError_t e;
-        switch (w.bn) {
-            case 256: e = launch_wgrad_tc<256>(xb, dyb, part, N, H, W, Cin, Cout, w, s); break;
-            case 128: e = launch_wgrad_tc<128>(xb, dyb, part, N, H, W, Cin, Cout, w, s); break;
-            case 64: e = launch_wgrad_tc<64>(xb, dyb, part, N, H, W, Cin, Cout, w, s); break;
-            default: e = launch_wgrad_tc<32>(xb, dyb, part, N, H, W, Cin, Cout, w, s); break;
+        // M = 9 Cin >= 144 spans at least two tiles, so MT = 1 occurs only with BN = 256
+        switch (w.bn * 4 + w.mt) {
+            case 256 * 4 + 1: e = launch_wgrad_tc<256, 1>(xb, dyb, part, N, H, W, Cin, Cout, w, s); break;
+            case 128 * 4 + 2: e = launch_wgrad_tc<128, 2>(xb, dyb, part, N, H, W, Cin, Cout, w, s); break;
+            case 64 * 4 + 2: e = launch_wgrad_tc<64, 2>(xb, dyb, part, N, H, W, Cin, Cout, w, s); break;
+            case 64 * 4 + 3: e = launch_wgrad_tc<64, 3>(xb, dyb, part, N, H, W, Cin, Cout, w, s); break;
+            case 32 * 4 + 2: e = launch_wgrad_tc<32, 2>(xb, dyb, part, N, H, W, Cin, Cout, w, s); break;
+            case 32 * 4 + 3: e = launch_wgrad_tc<32, 3>(xb, dyb, part, N, H, W, Cin, Cout, w, s); break;
+            default: return nn_fail("conv3x3_bwd_weight: no kernel for this tiling");
         }
         if (e != cudaSuccess) { cudaGetLastError(); return nn_fail(cudaGetErrorString(e)); }
         const long long n = 9LL * Cin * Cout;
