@@ -385,6 +385,16 @@ cdf_status cdf_batch_init_moments(cdf_batch *b, int k, const double *phi, const 
 cdf_status cdf_batch_step(cdf_batch *b, long long n);
 /* Moments of instance k at the current time into a host FP64 stack [m+3][ny][nx]. */
 cdf_status cdf_batch_moments(cdf_batch *b, int k, double *host_out);
+/* Device forms of the two calls above, without host staging or conversion:
+ * instance k from / into a device FP32 stack [m+3][ny][nx] (phi_0..phi_{m-1}, u_x,
+ * u_y, p; the layout of cdf_lb_init_moments_device), or, for k = -1, every
+ * instance from / into one buffer of such stacks back to back in instance order
+ * (instance k at float offset sum_{j<k} (m+3) nx_j ny_j).  Ordered on the batch's
+ * stream and returning after the launches (the buffer may be reused once that
+ * stream has reached this call); CDF_EINVAL for a NULL pointer or k outside
+ * [-1, count). */
+cdf_status cdf_batch_init_moments_device(cdf_batch *b, int k, const float *dev_fields);
+cdf_status cdf_batch_moments_device(cdf_batch *b, int k, float *dev_out);
 /* Keep a copy of every instance's current moments; cdf_batch_residuals then gives,
  * per instance, the stop-test residual R of cdf_lb_run_to_steady between that copy
  * and the current moments (FP64 sums; +Inf where a field is not finite).

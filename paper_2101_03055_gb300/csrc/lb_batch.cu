@@ -624,6 +624,52 @@ cdf_status cdf_batch_step(cdf_batch *b, long long n) {
     return CDF_OK;
 }
 
+// Instances [k0, k1) of a device call: one instance, or all of them for k = -1.
+static bool batch_range(const cdf_batch *b, int k, int *k0, int *k1) {
+    if (k == -1) {
+        *k0 = 0;
+        *k1 = b->count;
+        return true;
+    }
+    if (k < 0 || k >= b->count) return false;
+    *k0 = k;
+    *k1 = k + 1;
+    return true;
+}
+
+cdf_status cdf_batch_init_moments_device(cdf_batch *b, int k, const float *dev_fields) {
+    int k0, k1;
+    if (!b || !dev_fields || !batch_range(b, k, &k0, &k1)) return bfail(CDF_EINVAL, "bad argument");
+    BCK(cudaEventRecord(b->ev_in, b->user));
+    BCK(cudaStreamWaitEvent(b->s, b->ev_in, 0));
+    const float *src = dev_fields;
+    for (int j = k0; j < k1; ++j) {
+        const LbParams &P = b->params[j];
+        BCK(launch_init(P, kFP32, src, P.nx, b->buf[b->cur] + b->pop_off[j], sprev_of(b, b->cur) + b->sp_off[j],
+                        b->mom + b->mom_off[j], b->s));
+        src += (size_t)(b->m + 3) * P.nx * P.ny;
+    }
+    BCK(cudaEventRecord(b->ev_out, b->s));
+    BCK(cudaStreamWaitEvent(b->user, b->ev_out, 0));
+    return CDF_OK;
+}
+
+cdf_status cdf_batch_moments_device(cdf_batch *b, int k, float *dev_out) {
+    int k0, k1;
+    if (!b || !dev_out || !batch_range(b, k, &k0, &k1)) return bfail(CDF_EINVAL, "bad argument");
+    BCK(cudaEventRecord(b->ev_in, b->user));
+    BCK(cudaStreamWaitEvent(b->s, b->ev_in, 0));
+    float *dst = dev_out;
+    for (int j = k0; j < k1; ++j) {
+        const LbParams &P = b->params[j];
+        BCK(launch_pack_moments(P, b->mom + b->mom_off[j], dst, b->s));
+        dst += (size_t)(b->m + 3) * P.nx * P.ny;
+    }
+    BCK(cudaEventRecord(b->ev_out, b->s));
+    BCK(cudaStreamWaitEvent(b->user, b->ev_out, 0));
+    return CDF_OK;
+}
+
 cdf_status cdf_batch_moments(cdf_batch *b, int k, double *host_out) {
     if (!b || !host_out || k < 0 || k >= b->count) return bfail(CDF_EINVAL, "bad argument");
     const LbParams &P = b->params[k];

@@ -175,6 +175,8 @@ SIGNATURES = {
     "cdf_batch_init_moments": (ctypes.c_int, [_H, ctypes.c_int, _DP, _DP, _DP]),
     "cdf_batch_step": (ctypes.c_int, [_H, ctypes.c_longlong]),
     "cdf_batch_moments": (ctypes.c_int, [_H, ctypes.c_int, _DP]),
+    "cdf_batch_init_moments_device": (ctypes.c_int, [_H, ctypes.c_int, _FP]),
+    "cdf_batch_moments_device": (ctypes.c_int, [_H, ctypes.c_int, _FP]),
     "cdf_batch_get_info": (ctypes.c_int, [_H, ctypes.POINTER(cdf_batch_info)]),
     "cdf_batch_snapshot": (ctypes.c_int, [_H]),
     "cdf_batch_residuals": (ctypes.c_int, [_H, _DP]),
@@ -620,6 +622,14 @@ def cdf_batch_moments(h, k, out):
     _check(load().cdf_batch_moments(h, k, _dptr(out)))
 
 
+def cdf_batch_init_moments_device(h, k: int, dev_ptr: int):
+    _check(load().cdf_batch_init_moments_device(h, int(k), ctypes.c_void_p(dev_ptr)))
+
+
+def cdf_batch_moments_device(h, k: int, dev_ptr: int):
+    _check(load().cdf_batch_moments_device(h, int(k), ctypes.c_void_p(dev_ptr)))
+
+
 def cdf_batch_snapshot(h):
     _check(load().cdf_batch_snapshot(h))
 
@@ -701,6 +711,28 @@ class BatchSolver:
         out = np.empty((self.m + 3, pb.ny, pb.nx))
         cdf_batch_moments(self.h, k, out)
         return out
+
+    def stack_floats(self, k: int = -1) -> int:
+        """FP32 values of instance k's moment stack [m+3][ny][nx], or of all stacks
+        back to back for k = -1 (the layout of the device moment calls)."""
+        pbs = self.problems if k == -1 else [self.problems[k]]
+        return sum((self.m + 3) * pb.nx * pb.ny for pb in pbs)
+
+    def _check_device_buffer(self, t, k):
+        import torch
+        if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == torch.float32 and t.is_contiguous()
+                and t.numel() == self.stack_floats(k)):
+            raise ValueError(f"expected a contiguous CUDA float32 tensor of {self.stack_floats(k)} values")
+
+    def init_moments_device(self, fields, k: int = -1):
+        """Initial state from device FP32 moment stacks (cdf_batch_init_moments_device)."""
+        self._check_device_buffer(fields, k)
+        cdf_batch_init_moments_device(self.h, k, fields.data_ptr())
+
+    def moments_device(self, out, k: int = -1):
+        """Current moments into device FP32 stacks (cdf_batch_moments_device)."""
+        self._check_device_buffer(out, k)
+        cdf_batch_moments_device(self.h, k, out.data_ptr())
 
     def info(self) -> cdf_batch_info:
         return cdf_batch_get_info(self.h)

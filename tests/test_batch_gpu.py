@@ -76,3 +76,48 @@ def test_batch_autotuned_full_sweep_runs(cdf):
         s = cdf.Solver(pbs[k])
         s.step(40)
         np.testing.assert_array_equal(M, s.moments())
+
+
+def test_batch_device_moment_calls_match_the_host_calls(cdf):
+    """cdf_batch_init_moments_device / cdf_batch_moments_device, per instance and for
+    all instances back to back (k = -1), give the bits of the host FP64 calls (which
+    round the same values to FP32), before and after steps; bad arguments are refused."""
+    import torch
+    pbs = small_sweep(4, seed=8)
+    m = pbs[0].m
+
+    def stack(pb):
+        return np.concatenate([pb.phi0.reshape(m, pb.ny, pb.nx), pb.u0.reshape(2, pb.ny, pb.nx),
+                               pb.p0.reshape(1, pb.ny, pb.nx)]).astype(np.float32)
+
+    host = cdf.BatchSolver(pbs, mode=2, tile=(32, 8))
+    dev = cdf.BatchSolver(pbs, mode=2, tile=(32, 8), init=False)
+    fields = torch.from_numpy(np.concatenate([stack(pb).ravel() for pb in pbs])).cuda()
+    dev.init_moments_device(fields)
+    out = torch.empty(dev.stack_floats(), dtype=torch.float32, device="cuda")
+    for steps in (0, 23):
+        host.step(steps)
+        dev.step(steps)
+        dev.moments_device(out)
+        got, off = out.cpu().numpy(), 0
+        for k, pb in enumerate(pbs):
+            n = (m + 3) * pb.nx * pb.ny
+            want = host.moments(k)
+            assert np.array_equal(got[off:off + n].reshape(want.shape).astype(np.float64), want)
+            one = torch.empty(n, dtype=torch.float32, device="cuda")
+            dev.moments_device(one, k)
+            assert np.array_equal(one.cpu().numpy(), got[off:off + n])
+            off += n
+    # one instance re-initialised alone from its own stack: it restarts like a fresh batch's,
+    # the others keep their state
+    k = 2
+    dev.init_moments_device(torch.from_numpy(stack(pbs[k]).ravel()).cuda(), k)
+    fresh = cdf.BatchSolver(pbs, mode=2, tile=(32, 8))
+    assert np.array_equal(dev.moments(k), fresh.moments(k))
+    for j in (0, 1, 3):
+        assert np.array_equal(dev.moments(j), host.moments(j))
+    for bad in (-2, len(pbs)):
+        with pytest.raises(cdf.CdfError):
+            cdf.cdf_batch_moments_device(dev.h, bad, out.data_ptr())
+    with pytest.raises(cdf.CdfError):
+        cdf.cdf_batch_init_moments_device(dev.h, 0, 0)
