@@ -241,10 +241,11 @@ class _Single:
         self.resident = bool(info.resident)
         self.pair = bool(info.temporal) and not self.resident
         if self.pair:
-            kname = (f"step2_kernel<{pb.m}>" if info.storage == 0 else
-                     f"step2_kernel_mr<{pb.m},{ {1: '__half', 2: '__nv_bfloat16'}[info.storage]}>")
+            kname = ((f"step2_kernel_x2<{pb.m}>" if info.lanes == 2 else f"step2_kernel<{pb.m}>") if info.storage == 0
+                     else f"step2_kernel_mr<{pb.m},{ {1: '__half', 2: '__nv_bfloat16'}[info.storage]}>")
+            lanes = ", two nodes per thread on paired FP32 lanes" if info.lanes == 2 else ""
             self.kernel = (f"{kname} (two time steps per launch, CTAs of {info.block_x}x{info.block_y} "
-                           f"threads, output tiles {info.tile_x}x{info.tile_y})")
+                           f"threads, output tiles {info.tile_x}x{info.tile_y}{lanes})")
         elif self.resident:
             self.block = [info.tile_x, info.tile_y]
             self.kernel = (f"resident_kernel<{pb.m}> (tile-resident persistent step, {info.tiles} CTAs of "
@@ -339,7 +340,11 @@ class _Batch:
         if storage != "fp32":
             raise SystemExit("the batched solver stores FP32 populations")
         self.lib, self.pbs = lib, pbs
-        self.s = lib.BatchSolver(pbs, mode=mode or 0, tile=tile) if tile else lib.BatchSolver(pbs)
+        if tile:  # (x, y) or, for mode 2, (x, y, tile height, nodes per thread)
+            self.s = lib.BatchSolver(pbs, mode=mode or 0, tile=tile[:2], chain_tile_y=tile[2] if len(tile) > 2 else 0,
+                                     chain_lanes=tile[3] if len(tile) > 3 else 0)
+        else:
+            self.s = lib.BatchSolver(pbs)
         info = self.s.info()
         self.nodes, self.bytes_per_lup, self.storage = info.nodes, info.bytes_per_lup, 0
         self.block = [info.tile_x, info.tile_y]
@@ -350,7 +355,9 @@ class _Batch:
                            f"(graph of 32 steps over a 32-stream pool)")
         elif info.mode == 2:
             self.block = [info.chain_block_x, info.chain_block_y]
-            self.kernel = (f"step2_kernel<{self.m}> x {info.count} instance chains (two time steps per launch, "
+            name = "step2_kernel_x2" if info.chain_lanes == 2 else "step2_kernel"
+            lanes = "two nodes per thread on paired FP32 lanes, " if info.chain_lanes == 2 else ""
+            self.kernel = (f"{name}<{self.m}> x {info.count} instance chains (two time steps per launch, {lanes}"
                            f"CTAs of {info.chain_block_x}x{info.chain_block_y}, output tiles "
                            f"{info.chain_block_x - 2}x{info.chain_tile_y}; graph of 32 steps over a 32-stream pool)")
         else:
@@ -540,8 +547,8 @@ def measured_tensor_peak():
 def time_to_steady_line(n=256, cases=8, tol=1e-5, check_every=10_000, max_steps=3_000_000):
     """The surrogate's warm start against the start from rest on n x n double-diffusive
     cavities (held-out parameter draws, seed 1): lattice steps and GPU seconds until the
-    stop test of Sec. 3.1.1 (R over check_every steps) drops below tol, both starts run
-    as one batched solve each.  The network is the committed one trained on 64^2
+    stop test of Sec. 3.1.1 (R over check_every steps) drops below tol, each case and
+    start on its own single-lattice solver.  The network is the committed one trained on 64^2
     steady states; its prediction is resampled to n x n.  None when no trained
     weights are present."""
     from paper_2101_03055_gb300 import surrogate as S
@@ -562,8 +569,11 @@ def time_to_steady_line(n=256, cases=8, tol=1e-5, check_every=10_000, max_steps=
             "cases_reached_both": int(both.sum()), "cold_steps": c.tolist(), "warm_steps": w.tolist(),
             "median_cold_steps": med(c[both]), "median_warm_steps": med(w[both]),
             "median_ratio_warm_over_cold": med(w[both] / c[both]),
-            "cold_gpu_s": res["cold"]["seconds"], "warm_gpu_s": res["warm"]["seconds"],
-            "ratio_gpu_s": res["warm"]["seconds"] / res["cold"]["seconds"],
+            "cold_s": res["cold"]["seconds"].round(3).tolist(), "warm_s": res["warm"]["seconds"].round(3).tolist(),
+            "median_cold_s": med(res["cold"]["seconds"][both]), "median_warm_s": med(res["warm"]["seconds"][both]),
+            "median_ratio_s_warm_over_cold": med(res["warm"]["seconds"][both] / res["cold"]["seconds"][both]),
+            "timing": "wall clock around each case's cdf_lb_run_to_steady on its own single-lattice solver "
+                      "(device synchronised on both sides)",
             "max_steps": max_steps}
 
 
@@ -843,7 +853,8 @@ def main():
     ap.add_argument("--batch-mode", type=int, default=0, choices=[0, 1, 2],
                     help="with --batch-tile: the batched solver's mode (0 persistent, 1 chains, 2 two-step chains)")
     ap.add_argument("--batch-tile", default=None,
-                    help="'X,Y': tile (mode 0) or CTA shape (modes 1, 2) of the batched solver; default: autotuned")
+                    help="'X,Y': tile (mode 0) or CTA shape (modes 1, 2) of the batched solver, 'X,Y,TH,LANES' in "
+                         "mode 2 (tile height, nodes per thread); default: autotuned")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extra", action="store_true", help="skip the extra workloads of the N = 1 line")
     ap.add_argument("--e2e-steps", type=int, default=3)

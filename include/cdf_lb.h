@@ -177,6 +177,21 @@ typedef struct {
                                           the halo row below row 0 of a periodic axis); 0 otherwise */
     int ny_global;                     /* slab: rows of the whole lattice, whose pressure reference the
                                           slab keeps; 0 = ny (and 0 for a whole lattice) */
+    int temporal_lanes;                /* with a given two-step kernel shape: nodes each thread
+                                          updates.  2 = the paired-lane kernel (two nodes of a column
+                                          collide together on paired FP32 instructions; FP32 storage,
+                                          m <= 2, full model, block 32 x 8, tile_y 14 or 30); bitwise
+                                          the same as one node per thread.  0 or 1 = one node per
+                                          thread.  The autotuner does not time it: it executes 28 %
+                                          fewer instructions but needs 126 registers a thread, and at
+                                          half the occupancy it measured 20-27 % slower on GB300. */
+    int block_lanes;                   /* with a given flat launch (block_x > 0, block_y = 0): nodes
+                                          each thread updates.  2 = the paired-lane flat kernel (nodes
+                                          t and t + half of the row order collide together on paired
+                                          FP32 instructions; FP32 storage, m <= 2, full model); bitwise
+                                          the same as one node per thread.  0 or 1 = one.  Not timed by
+                                          the autotuner (measured 12 % slower on the 512 x 256 plume,
+                                          for the reason given at temporal_lanes). */
 } cdf_options;
 
 /* Facts about a handle (for benchmarks and tests). */
@@ -192,6 +207,8 @@ typedef struct {
     long long t;                       /* time steps taken since initialisation */
     int temporal;                      /* 1 if two steps run per launch; block_x/y is then that
                                           kernel's CTA shape and tile_x/y its output tile */
+    int lanes;                         /* nodes each thread of the step kernel in use updates (1 or 2:
+                                          the paired-lane kernels of block_lanes / temporal_lanes) */
 } cdf_info;
 
 typedef struct cdf_lb cdf_lb;
@@ -358,6 +375,9 @@ typedef struct {
                                     with tile_x = 0 the autotuner measures all three and picks */
     int chain_tile_y;            /* mode 2 with tile_x > 0: output tile height of the two-step
                                     kernel (0 = 14) */
+    int chain_lanes;             /* mode 2 with tile_x > 0: nodes per thread of the two-step
+                                    kernel (2: the paired-lane kernel of cdf_options.temporal_lanes,
+                                    tile 32 x 8, chain_tile_y 14 or 30; 0 or 1: one) */
 } cdf_batch_options;
 typedef struct {
     int count, m;
@@ -369,6 +389,7 @@ typedef struct {
                                     2 chains of two-step launches */
     int chain_block_x, chain_block_y;
     int chain_tile_y;            /* mode 2: output tile height of the two-step kernel */
+    int chain_lanes;             /* modes 1, 2: nodes per thread of the chains' kernel (1 or 2) */
 } cdf_batch_info;
 
 /* Create `count` lattices; every array argument has `count` entries (phi_ref:

@@ -353,8 +353,10 @@ cdf_status run_chains(cdf_batch *b, int nsteps, bool moments_last) {
     return CDF_OK;
 }
 
-// Can step2_kernel with CTA blk and tile height th run every instance?
+// Can step2_kernel with CTA blk and tile height th run every instance?  blk.z
+// == 2: the paired-lane kernel (m <= 2, CTAs of 32 x 8, tile heights 14 and 30).
 bool chain_pair_fits(const cdf_batch *b, dim3 blk, int th) {
+    if (blk.z == 2 && (b->m > 2 || blk.x != 32 || blk.y != 8 || (th != 14 && th != 30))) return false;
     if (blk.x % 32 != 0 || (int)(blk.x * blk.y) > step2_max_threads(b->m) || th < 1) return false;
     if (step2_smem_bytes(b->m, blk, th) > (size_t)kStep2MaxSmem) return false;
     for (const LbParams &p : b->params)
@@ -374,7 +376,13 @@ cdf_status check_err(cdf_batch *b) {
     return CDF_OK;
 }
 
-using ModeChoice = std::pair<int, dim3>;  // (mode, tile or chain block)
+// (mode, tile or chain block, tile height of mode 2); a chain block with z == 2
+// names the paired-lane two-step kernel
+struct ModeChoice {
+    int mode;
+    dim3 shape;
+    int th;
+};
 std::map<TuneKey, ModeChoice> g_bmode;
 
 cdf_status bautotune(cdf_batch *b) {
@@ -382,23 +390,21 @@ cdf_status bautotune(cdf_batch *b) {
     {
         std::lock_guard<std::mutex> lk(g_btune_mu);
         auto it = g_bmode.find(key);
-        if (it != g_bmode.end() && (it->second.first != 2 || chain_pair_fits(b, dim3(it->second.second.x,
-                                                                                         it->second.second.y),
-                                                                              (int)it->second.second.z))) {
-            b->mode = it->second.first;
+        if (it != g_bmode.end() && (it->second.mode != 2 || chain_pair_fits(b, it->second.shape, it->second.th))) {
+            b->mode = it->second.mode;
             if (b->mode >= 1) {
-                set_chain_block(b, dim3(it->second.second.x, it->second.second.y));
-                b->chain_th = (int)it->second.second.z;
+                set_chain_block(b, it->second.shape);
+                b->chain_th = it->second.th;
                 return setup_tiles(b, dim3(64, 4));
             }
-            return setup_tiles(b, it->second.second);
+            return setup_tiles(b, it->second.shape);
         }
     }
     cudaEvent_t e0, e1;
     BCK(cudaEventCreate(&e0));
     BCK(cudaEventCreate(&e1));
     float best = 1e30f;
-    ModeChoice choice{0, dim3(64, 4)};
+    ModeChoice choice{0, dim3(64, 4), 0};
     const int steps = b->nodes > (1 << 22) ? 4 : 16;
     auto time_it = [&](auto &&run, int nsteps) -> float {
         if (run(nsteps) != CDF_OK) return -1.f;  // warm-up (and graph capture)
@@ -418,7 +424,7 @@ cdf_status bautotune(cdf_batch *b) {
         float ms = time_it([&](int n) { return launch_batch(b, n, false); }, steps);
         if (ms < 0) return bfail(CDF_ECUDA, "autotuning the persistent kernel failed");
         ms *= (float)kChainGraphSteps / steps;  // per 32 steps, comparable with the chains
-        if (ms < best) { best = ms; choice = {0, c}; }
+        if (ms < best) { best = ms; choice = {0, c, 0}; }
     }
     const dim3 blocks[] = {dim3(128, 1), dim3(128, 2), dim3(256, 1), dim3(64, 4), dim3(32, 8), dim3(128, 0),
                            dim3(256, 0)};  // y == 0: flat launch
@@ -427,18 +433,20 @@ cdf_status bautotune(cdf_batch *b) {
         set_chain_block(b, c);
         float ms = time_it([&](int n) { return run_chains(b, n, false); }, kChainGraphSteps);
         if (ms < 0) return bfail(CDF_ECUDA, "autotuning the kernel chains failed");
-        if (ms < best) { best = ms; choice = {1, c}; }
+        if (ms < best) { best = ms; choice = {1, c, 0}; }
     }
-    // chains of two-step launches: CTA shape (x, y) and tile height z
-    const dim3 pairs[] = {dim3(32, 8, 14), dim3(32, 8, 6), dim3(32, 16, 14), dim3(64, 8, 14), dim3(32, 16, 30)};
+    // chains of two-step launches: CTA shape and tile height (the paired-lane
+    // kernel, chain_lanes = 2, measured slower on GB300 and is not timed here)
+    const std::pair<dim3, int> pairs[] = {{dim3(32, 8), 14}, {dim3(32, 8), 6}, {dim3(32, 16), 14},
+                                          {dim3(64, 8), 14}, {dim3(32, 16), 30}};
     b->mode = 2;
-    for (const dim3 &c : pairs) {
-        if (!chain_pair_fits(b, dim3(c.x, c.y), (int)c.z)) continue;
-        set_chain_block(b, dim3(c.x, c.y));
-        b->chain_th = (int)c.z;
+    for (const auto &c : pairs) {
+        if (!chain_pair_fits(b, c.first, c.second)) continue;
+        set_chain_block(b, c.first);
+        b->chain_th = c.second;
         float ms = time_it([&](int n) { return run_chains(b, n, false); }, kChainGraphSteps);
         if (ms < 0) return bfail(CDF_ECUDA, "autotuning the two-step kernel chains failed");
-        if (ms < best) { best = ms; choice = {2, c}; }
+        if (ms < best) { best = ms; choice = {2, c.first, c.second}; }
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
@@ -448,13 +456,13 @@ cdf_status bautotune(cdf_batch *b) {
         std::lock_guard<std::mutex> lk(g_btune_mu);
         g_bmode[key] = choice;
     }
-    b->mode = choice.first;
+    b->mode = choice.mode;
     if (b->mode >= 1) {
-        set_chain_block(b, dim3(choice.second.x, choice.second.y));
-        b->chain_th = (int)choice.second.z;
+        set_chain_block(b, choice.shape);
+        b->chain_th = choice.th;
         return setup_tiles(b, dim3(64, 4));
     }
-    return setup_tiles(b, choice.second);
+    return setup_tiles(b, choice.shape);
 }
 
 }  // namespace
@@ -556,7 +564,12 @@ cdf_status cdf_batch_create(int count, const cdf_grid *grids, int m, const cdf_d
         return bfail(CDF_ECUDA, "stream pool set-up failed");
     }
     b->mode = opt->mode;
-    if (opt->mode >= 1 && opt->tile_x > 0) set_chain_block(b, dim3(opt->tile_x, opt->tile_y));
+    if (opt->chain_lanes < 0 || opt->chain_lanes > 2 || (opt->chain_lanes == 2 && !(opt->mode == 2 && opt->tile_x > 0))) {
+        brelease(b);
+        return bfail(CDF_EINVAL, "chain_lanes: 0, 1, or 2 with mode 2 and a given tile");
+    }
+    if (opt->mode >= 1 && opt->tile_x > 0)
+        set_chain_block(b, dim3(opt->tile_x, opt->tile_y, opt->mode == 2 && opt->chain_lanes == 2 ? 2 : 1));
     if (opt->mode == 2 && opt->tile_x > 0) {
         b->chain_th = opt->chain_tile_y > 0 ? opt->chain_tile_y : 14;
         if (!chain_pair_fits(b, b->chain_block, b->chain_th)) {
@@ -698,6 +711,7 @@ cdf_status cdf_batch_get_info(const cdf_batch *b, cdf_batch_info *out) {
     out->chain_block_x = (int)b->chain_block.x;
     out->chain_block_y = (int)b->chain_block.y;
     out->chain_tile_y = b->mode == 2 ? b->chain_th : 0;
+    out->chain_lanes = b->mode >= 1 ? (int)b->chain_block.z : 1;
     out->t = b->t;
     return CDF_OK;
 }

@@ -6,6 +6,7 @@
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
+#include <type_traits>
 #include <utility>
 
 #include "lb_internal.h"
@@ -128,18 +129,96 @@ __device__ __forceinline__ float pref_at(const LbParams &p, int x, int y) {
     return fmaf(p.gref[0], (float)x - p.xc, __fmul_rn(p.gref[1], (float)y - p.yc));
 }
 
-__device__ __forceinline__ float cutoff(const LbParams &p, float c) {
-    // r(c): step (Sec. 3.1.3) or regularised (Sec. 3.1.2)
-    if (p.r_regularised) {
-        float d = c - p.c_star;
-        return 0.5f * fmaf(d, rsqrtf(fmaf(d, d, p.eps2)), 1.f);
-    }
-    return c >= p.c_star ? 1.f : 0.f;
+// ---- paired FP32 lanes -----------------------------------------------------------
+// F2 carries one FP32 value of each of two nodes.  Its arithmetic is the paired
+// FP32 instructions of sm_100 and later (__ffma2_rn, __fadd2_rn, __fmul2_rn):
+// one instruction for both lanes, each lane rounded exactly as the scalar
+// fmaf / __fadd_rn / __fmul_rn rounds it.  a - b is fma(b, -1, a) and -a is
+// a * -1, both exact.  The node update below is written once for a value type
+// V, float or F2, so a kernel that updates two nodes per thread with V = F2
+// gives every node the bits of the scalar update with half of its arithmetic
+// instructions (the loads, stores and pull table stay per node).
+struct F2 {
+    float2 v;
+};
+template <class T>
+struct IsF2 {
+    static constexpr bool value = false;
+};
+template <>
+struct IsF2<F2> {
+    static constexpr bool value = true;
+};
+template <class A, class B, class C = float>
+using IfF2 = typename std::enable_if<IsF2<A>::value || IsF2<B>::value || IsF2<C>::value, F2>::type;
+
+__device__ __forceinline__ float2 as2(float a) { return make_float2(a, a); }
+__device__ __forceinline__ float2 as2(F2 a) { return a.v; }
+template <class V>
+__device__ __forceinline__ V splat(float a) {
+    if constexpr (IsF2<V>::value) return F2{make_float2(a, a)};
+    else return a;
+}
+__device__ __forceinline__ F2 pack2(float a, float b) { return F2{make_float2(a, b)}; }
+__device__ __forceinline__ float lane(float a, int) { return a; }
+__device__ __forceinline__ float lane(F2 a, int k) { return k ? a.v.y : a.v.x; }
+
+// vfma / vmul: fmaf / __fmul_rn for float, their paired forms for F2 (a float
+// operand is used in both lanes)
+__device__ __forceinline__ float vfma(float a, float b, float c) { return fmaf(a, b, c); }
+__device__ __forceinline__ float vmul(float a, float b) { return __fmul_rn(a, b); }
+template <class A, class B, class C>
+__device__ __forceinline__ IfF2<A, B, C> vfma(A a, B b, C c) {
+    return F2{__ffma2_rn(as2(a), as2(b), as2(c))};
+}
+template <class A, class B>
+__device__ __forceinline__ IfF2<A, B> vmul(A a, B b) {
+    return F2{__fmul2_rn(as2(a), as2(b))};
+}
+template <class A, class B>
+__device__ __forceinline__ IfF2<A, B> operator*(A a, B b) {
+    return F2{__fmul2_rn(as2(a), as2(b))};
+}
+template <class A, class B>
+__device__ __forceinline__ IfF2<A, B> operator+(A a, B b) {
+    return F2{__fadd2_rn(as2(a), as2(b))};
+}
+template <class A, class B>
+__device__ __forceinline__ IfF2<A, B> operator-(A a, B b) {
+    return F2{__ffma2_rn(as2(b), make_float2(-1.f, -1.f), as2(a))};
+}
+__device__ __forceinline__ F2 operator-(F2 a) { return F2{__fmul2_rn(a.v, make_float2(-1.f, -1.f))}; }
+// per lane: 1 / a, 1 / sqrt(a), and the step a >= t ? 1 : 0
+__device__ __forceinline__ float vrcp(float a) { return 1.f / a; }
+__device__ __forceinline__ F2 vrcp(F2 a) { return pack2(1.f / a.v.x, 1.f / a.v.y); }
+__device__ __forceinline__ float vrsqrt(float a) { return rsqrtf(a); }
+__device__ __forceinline__ F2 vrsqrt(F2 a) { return pack2(rsqrtf(a.v.x), rsqrtf(a.v.y)); }
+__device__ __forceinline__ float vstep(float a, float t) { return a >= t ? 1.f : 0.f; }
+__device__ __forceinline__ F2 vstep(F2 a, float t) { return pack2(vstep(a.v.x, t), vstep(a.v.y, t)); }
+
+// c_i . (ax, ay) for a lattice direction (components 0 or +-1, at least one
+// nonzero), without multiplications by the components.
+template <class V>
+__device__ __forceinline__ V cdot(int cx, int cy, V ax, V ay) {
+    if (cx == 0) return cy > 0 ? ay : -ay;
+    if (cy == 0) return cx > 0 ? ax : -ax;
+    if (cx > 0) return cy > 0 ? ax + ay : ax - ay;
+    return cy > 0 ? ay - ax : -(ax + ay);
 }
 
-template <int M>
+template <class V>
+__device__ __forceinline__ V cutoff(const LbParams &p, V c) {
+    // r(c): step (Sec. 3.1.3) or regularised (Sec. 3.1.2)
+    if (p.r_regularised) {
+        const V d = c - p.c_star;
+        return 0.5f * vfma(d, vrsqrt(vfma(d, d, p.eps2)), 1.f);
+    }
+    return vstep(c, p.c_star);
+}
+
+template <int M, class V = float>
 struct NodeOut {
-    float phi[M], ux, uy, pr, s1;
+    V phi[M], ux, uy, pr, s1;
 };
 
 // Scalar equilibrium deviation, Eq. feq-phi with lambda = I, vartheta = 0:
@@ -148,17 +227,17 @@ struct NodeOut {
 // One moving direction j = 1..4 of the scalar equilibrium deviation
 // W_j (phi' + 3 phi c_j.u); shared by the collision and by the pull of the
 // 16-bit storage so both evaluate it bit for bit the same way.
-__device__ __forceinline__ float feq_dir(int j, float phid, float t3phi, float ux, float uy) {
-    const float cu = (j == 1) ? ux : (j == 2) ? uy : (j == 3) ? -ux : -uy;
-    return __fmul_rn(kW5, fmaf(t3phi, cu, phid));
+template <class V>
+__device__ __forceinline__ V feq_dir(int j, V phid, V t3phi, V ux, V uy) {
+    return vmul(kW5, vfma(t3phi, cdot(kC5x(j), kC5y(j), ux, uy), phid));
 }
 
-template <int M>
-__device__ __forceinline__ void scalar_equilibrium(const float (&phid)[M], const float (&phi)[M], float ux,
-                                                   float uy, float (&feq)[M][5]) {
+template <int M, class V>
+__device__ __forceinline__ void scalar_equilibrium(const V (&phid)[M], const V (&phi)[M], V ux, V uy,
+                                                   V (&feq)[M][5]) {
 #pragma unroll
     for (int b = 0; b < M; ++b) {
-        const float t = 3.f * phi[b];
+        const V t = 3.f * phi[b];
 #pragma unroll
         for (int j = 1; j < 5; ++j) feq[b][j] = feq_dir(j, phid[b], t, ux, uy);
         feq[b][0] = phid[b] - ((feq[b][1] + feq[b][3]) + (feq[b][2] + feq[b][4]));
@@ -169,45 +248,48 @@ __device__ __forceinline__ void scalar_equilibrium(const float (&phid)[M], const
 // compiled in different contexts; every multiply-add whose FMA contraction the
 // compiler could decide differently in each context is written out (fmaf,
 // __fmul_rn), so all kernels round identically and agree bit for bit.
-__device__ __forceinline__ float usq_of(float ux, float uy) { return fmaf(ux, ux, __fmul_rn(uy, uy)); }
+template <class V>
+__device__ __forceinline__ V usq_of(V ux, V uy) { return vfma(ux, ux, vmul(uy, uy)); }
 
 // Fluid equilibrium deviation (Eq. heq): h^eq_i(p, u) - h^eq_i(p_ref, 0)
 //   = kA_i (p' + c_i.u + 1.5 (c_i.u)^2 - 0.5 u.u)  (i != 0),  -kC p' - kQ u.u  (i = 0).
-__device__ __forceinline__ float fluid_equilibrium(int i, float prd, float ux, float uy, float usq) {
-    if (i == 0) return fmaf(-kC, prd, __fmul_rn(-kQ, usq));
-    const float cu = kC9x(i) * ux + kC9y(i) * uy;
-    return __fmul_rn(kA9(i), (prd + cu) + fmaf(__fmul_rn(1.5f, cu), cu, __fmul_rn(-0.5f, usq)));
+template <class V>
+__device__ __forceinline__ V fluid_equilibrium(int i, V prd, V ux, V uy, V usq) {
+    if (i == 0) return vfma(-kC, prd, vmul(-kQ, usq));
+    const V cu = cdot(kC9x(i), kC9y(i), ux, uy);
+    return vmul(kA9(i), (prd + cu) + vfma(vmul(1.5f, cu), cu, vmul(-0.5f, usq)));
 }
 
 // The second-order part of Eq. force per unit varphi, W_i (uF + Fu):(c_i c_i -
 // cs^2 I) / (2 cs^4): 3 W_i (3 (c_i.u)(c_i.F) - u.F) for i != 0 and, so that the
 // nine sum to zero with the exact-identity weights, -(3 - kC) u.F for i = 0.
-__device__ __forceinline__ float force2_dir(int i, float ux, float uy, float Fx, float Fy, float uF) {
-    if (i == 0) return __fmul_rn(-(3.f - kC), uF);
-    const float cu = kC9x(i) * ux + kC9y(i) * uy, cF = kC9x(i) * Fx + kC9y(i) * Fy;
-    return __fmul_rn(kA9(i), fmaf(__fmul_rn(3.f, cu), cF, -uF));
+template <class V>
+__device__ __forceinline__ V force2_dir(int i, V ux, V uy, V Fx, V Fy, V uF) {
+    if (i == 0) return vmul(-(3.f - kC), uF);
+    const V cu = cdot(kC9x(i), kC9y(i), ux, uy), cF = cdot(kC9x(i), kC9y(i), Fx, Fy);
+    return vmul(kA9(i), vfma(vmul(3.f, cu), cF, -uF));
 }
 
 // Scalar moments of one node (Eq. sum-phi) and the closures of Sec. 3 that
 // depend on them: the cut-off r(phi_1), the source S(phi) and S(t - 1).
 // sp1: S_1(t-1) of the consumption closure; `first` uses S(t-1) = S(t).
-template <int M>
+template <int M, class V = float>
 struct ScalarState {
-    float phid[M], phi[M], S[M], Sp[M], r;
+    V phid[M], phi[M], S[M], Sp[M], r;
 };
-template <int M>
-__device__ __forceinline__ void scalar_closures(const LbParams &p, const float (&f)[M][5], float sp1, bool first,
-                                                ScalarState<M> &s) {
+template <int M, class V>
+__device__ __forceinline__ void scalar_closures(const LbParams &p, const V (&f)[M][5], V sp1, bool first,
+                                                ScalarState<M, V> &s) {
 #pragma unroll
     for (int a = 0; a < M; ++a) {
         s.phid[a] = ((f[a][0] + f[a][1]) + (f[a][2] + f[a][3])) + f[a][4];
         s.phi[a] = p.phi_ref[a] + s.phid[a];
     }
-    s.r = 0.f;
+    s.r = splat<V>(0.f);
     if (M >= 2 && (p.chemotaxis || p.skind == 2)) s.r = cutoff(p, s.phi[M >= 2 ? 1 : 0]);
 #pragma unroll
     for (int a = 0; a < M; ++a) {
-        s.S[a] = (p.skind == 1) ? p.S[a] : 0.f;
+        s.S[a] = splat<V>((p.skind == 1) ? p.S[a] : 0.f);
         s.Sp[a] = s.S[a];
     }
     if (M >= 2 && p.skind == 2) {
@@ -218,27 +300,30 @@ __device__ __forceinline__ void scalar_closures(const LbParams &p, const float (
 
 // Eq. omega-D.  Constant D: omega from the host.  Chemotaxis: omega^-1 =
 // B + delta e_0 e_1^T with delta = -3 chi phi_0 r, inverted by Sherman-Morrison.
-template <int M>
-__device__ __forceinline__ void relaxation_matrix(const LbParams &p, const ScalarState<M> &s, float (&om)[M][M]) {
+template <int M, class V>
+__device__ __forceinline__ void relaxation_matrix(const LbParams &p, const ScalarState<M, V> &s, V (&om)[M][M]) {
 #pragma unroll
     for (int a = 0; a < M; ++a)
 #pragma unroll
-        for (int b = 0; b < M; ++b) om[a][b] = p.omega[a * M + b];
+        for (int b = 0; b < M; ++b) om[a][b] = splat<V>(p.omega[a * M + b]);
     if (M >= 2 && p.chemotaxis) {
-        const float delta = -p.chi3 * s.phi[0] * s.r;
+        const V delta = -p.chi3 * s.phi[0] * s.r;
         // 1 / (1 + delta omega_10); omega_10 = 0 (a diagonal constant part, as in
         // the benchmark closures) makes it exactly 1, so the quotient is skipped
         // by a branch that is uniform over the launch
-        const float o10 = om[M >= 2 ? 1 : 0][0];
-        float den = 1.f;
-        if (o10 != 0.f) den = 1.f / fmaf(delta, o10, 1.f);
+        const float o10 = p.omega[(M >= 2 ? 1 : 0) * M];
+        V den = splat<V>(1.f);
+        if (o10 != 0.f) den = vrcp(vfma(delta, o10, 1.f));
         float col0[M], row1[M];
 #pragma unroll
-        for (int a = 0; a < M; ++a) { col0[a] = om[a][0]; row1[a] = om[M >= 2 ? 1 : 0][a]; }
+        for (int a = 0; a < M; ++a) {
+            col0[a] = p.omega[a * M];
+            row1[a] = p.omega[(M >= 2 ? 1 : 0) * M + a];
+        }
 #pragma unroll
         for (int a = 0; a < M; ++a)
 #pragma unroll
-            for (int b = 0; b < M; ++b) om[a][b] = fmaf(-__fmul_rn(__fmul_rn(delta, den), col0[a]), row1[b], om[a][b]);
+            for (int b = 0; b < M; ++b) om[a][b] = vfma(-vmul(vmul(delta, den), col0[a]), row1[b], om[a][b]);
     }
 }
 
@@ -246,23 +331,23 @@ __device__ __forceinline__ void relaxation_matrix(const LbParams &p, const Scala
 // (f_i,b - f^eq_i,b) + W_i S_a + (W_i S_a - W_i S_a(t-1)) / 2 + G_i,a with the
 // auxiliary source G_i,a = 3 W_i c_i . J_a (J from Eq. Gi, or from the time
 // difference of phi u in Case 1 of Sec. 2.1).
-template <int M>
-__device__ __forceinline__ void scalar_collide(float (&f)[M][5], const ScalarState<M> &s, float ux, float uy,
-                                               const float (&om)[M][M], const float (&Jx)[M], const float (&Jy)[M]) {
-    float feq[M][5];
+template <int M, class V>
+__device__ __forceinline__ void scalar_collide(V (&f)[M][5], const ScalarState<M, V> &s, V ux, V uy,
+                                               const V (&om)[M][M], const V (&Jx)[M], const V (&Jy)[M]) {
+    V feq[M][5];
     scalar_equilibrium<M>(s.phid, s.phi, ux, uy, feq);
 #pragma unroll
     for (int i = 0; i < 5; ++i) {
-        float neq[M];
+        V neq[M];
 #pragma unroll
         for (int b = 0; b < M; ++b) neq[b] = f[b][i] - feq[b][i];
 #pragma unroll
         for (int a = 0; a < M; ++a) {
-            float coll = 0.f;
+            V coll = splat<V>(0.f);
 #pragma unroll
-            for (int b = 0; b < M; ++b) coll = fmaf(om[a][b], neq[b], coll);
-            const float G = (i == 0) ? 0.f : __fmul_rn(3.f * kW5, kC5x(i) * Jx[a] + kC5y(i) * Jy[a]);
-            f[a][i] = (f[a][i] - coll) + fmaf(kWs(i), fmaf(1.5f, s.S[a], __fmul_rn(-0.5f, s.Sp[a])), G);
+            for (int b = 0; b < M; ++b) coll = vfma(om[a][b], neq[b], coll);
+            const V G = (i == 0) ? splat<V>(0.f) : vmul(3.f * kW5, cdot(kC5x(i), kC5y(i), Jx[a], Jy[a]));
+            f[a][i] = (f[a][i] - coll) + vfma(kWs(i), vfma(1.5f, s.S[a], vmul(-0.5f, s.Sp[a])), G);
         }
     }
 }
@@ -270,44 +355,44 @@ __device__ __forceinline__ void scalar_collide(float (&f)[M][5], const ScalarSta
 // Collision of one node (Eqs. evolution12, evolution3) in deviation variables.
 // f, h: pre-collision deviations, overwritten by the post-collision ones.  prx:
 // p_ref at the node.  sp1: S_1(t-1) of the consumption closure; `first` uses
-// S(t-1) = S(t) (initialisation).
-template <int M>
-__device__ __forceinline__ void collide(const LbParams &p, float (&f)[M][5], float (&h)[9], float prx,
-                                        float sp1, bool first, NodeOut<M> &o) {
-    ScalarState<M> s;
+// S(t-1) = S(t) (initialisation).  V = F2: two nodes, one per lane.
+template <int M, class V>
+__device__ __forceinline__ void collide(const LbParams &p, V (&f)[M][5], V (&h)[9], V prx, V sp1, bool first,
+                                        NodeOut<M, V> &o) {
+    ScalarState<M, V> s;
     scalar_closures<M>(p, f, sp1, first, s);
-    float fm = p.Fbase;
+    V fm = splat<V>(p.Fbase);
 #pragma unroll
-    for (int a = 0; a < M; ++a) fm = fmaf(p.beta[a], s.phi[a], fm);
-    const float Fx = p.g[0] * fm, Fy = p.g[1] * fm;
+    for (int a = 0; a < M; ++a) fm = vfma(p.beta[a], s.phi[a], fm);
+    const V Fx = p.g[0] * fm, Fy = p.g[1] * fm;
 
     // Eq. sum-u and Eq. sum-p (varphi = 0):
     // p = cs^2/(1 - W0) [sum_{i!=0} h_i - W0 u.u / (2 cs^2)] = (sum_{i!=0} h_i - kQ u.u) / kC,
     // taken as a product with fl(1 / kC) (one rounding more than the quotient)
-    const float jx = (h[1] - h[3]) + (h[5] - h[6]) + (h[8] - h[7]);
-    const float jy = (h[2] - h[4]) + (h[5] - h[8]) + (h[6] - h[7]);
-    const float ux = fmaf(0.5f, Fx, jx), uy = fmaf(0.5f, Fy, jy);
-    const float usq = usq_of(ux, uy);
-    const float snr = ((h[1] + h[2]) + (h[3] + h[4])) + ((h[5] + h[6]) + (h[7] + h[8]));
-    float prd = __fmul_rn(fmaf(-kQ, usq, snr), kInvC);
+    const V jx = (h[1] - h[3]) + (h[5] - h[6]) + (h[8] - h[7]);
+    const V jy = (h[2] - h[4]) + (h[5] - h[8]) + (h[6] - h[7]);
+    const V ux = vfma(0.5f, Fx, jx), uy = vfma(0.5f, Fy, jy);
+    const V usq = usq_of(ux, uy);
+    const V snr = ((h[1] + h[2]) + (h[3] + h[4])) + ((h[5] + h[6]) + (h[7] + h[8]));
+    V prd = vmul(vfma(-kQ, usq, snr), kInvC);
     // varphi != 0 (a branch uniform over the launch): the appendix's pressure,
     // p = (sum_{i!=0} h_i - kQ u.u - varphi (1/omega - 1/2) (W_0/cs^2) u.F) / kC
-    const float uF = fmaf(ux, Fx, __fmul_rn(uy, Fy));
-    if (p.varphi != 0.f) prd = __fmul_rn(fmaf(-p.varphi_p, uF, fmaf(-kQ, usq, snr)), kInvC);
+    const V uF = vfma(ux, Fx, vmul(uy, Fy));
+    if (p.varphi != 0.f) prd = vmul(vfma(-p.varphi_p, uF, vfma(-kQ, usq, snr)), kInvC);
 
-    float om[M][M];
+    V om[M][M];
     relaxation_matrix<M>(p, s, om);
 
     // Eq. Gi: G_{i,a} = 3 W_i c_i . J_a,  J_a = sum_b (delta_ab - omega_ab / 2)(u S_b + phi_b F)
-    float Jx[M], Jy[M];
+    V Jx[M], Jy[M];
 #pragma unroll
     for (int a = 0; a < M; ++a) {
-        float jxa = 0.f, jya = 0.f;
+        V jxa = splat<V>(0.f), jya = splat<V>(0.f);
 #pragma unroll
         for (int b = 0; b < M; ++b) {
-            const float c = fmaf(-0.5f, om[a][b], a == b ? 1.f : 0.f);
-            jxa = fmaf(c, fmaf(ux, s.S[b], s.phi[b] * Fx), jxa);
-            jya = fmaf(c, fmaf(uy, s.S[b], s.phi[b] * Fy), jya);
+            const V c = vfma(-0.5f, om[a][b], a == b ? 1.f : 0.f);
+            jxa = vfma(c, vfma(ux, s.S[b], s.phi[b] * Fx), jxa);
+            jya = vfma(c, vfma(uy, s.S[b], s.phi[b] * Fy), jya);
         }
         Jx[a] = jxa;
         Jy[a] = jya;
@@ -319,17 +404,17 @@ __device__ __forceinline__ void collide(const LbParams &p, float (&f)[M][5], flo
     const float wf = p.omega_f, fw = 1.f - 0.5f * wf;
 #pragma unroll
     for (int i = 0; i < 9; ++i) {
-        const float heq = fluid_equilibrium(i, prd, ux, uy, usq);
-        float Fi = kA9(i) * (kC9x(i) * Fx + kC9y(i) * Fy);
-        if (p.varphi != 0.f) Fi = fmaf(p.varphi, force2_dir(i, ux, uy, Fx, Fy, uF), Fi);
-        h[i] = fmaf(fw, Fi, fmaf(-wf, h[i] - heq, h[i]));
+        const V heq = fluid_equilibrium(i, prd, ux, uy, usq);
+        V Fi = (i == 0) ? splat<V>(0.f) : kA9(i) * cdot(kC9x(i), kC9y(i), Fx, Fy);
+        if (p.varphi != 0.f) Fi = vfma(p.varphi, force2_dir(i, ux, uy, Fx, Fy, uF), Fi);
+        h[i] = vfma(fw, Fi, vfma(-wf, h[i] - heq, h[i]));
     }
 #pragma unroll
     for (int a = 0; a < M; ++a) o.phi[a] = s.phi[a];
     o.ux = ux;
     o.uy = uy;
     o.pr = prx + prd;
-    o.s1 = (M >= 2) ? s.S[M >= 2 ? 1 : 0] : 0.f;
+    o.s1 = (M >= 2) ? s.S[M >= 2 ? 1 : 0] : splat<V>(0.f);
 }
 
 // Case 1 of Sec. 2.1: the convection cross-diffusion equations in a prescribed

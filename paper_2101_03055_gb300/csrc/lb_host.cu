@@ -420,7 +420,11 @@ cdf_status autotune(cdf_lb *h) {
 }
 
 // Can step2_kernel run this lattice with CTA shape b and tile height th?
+// b.z == 2: the paired-lane kernel (step2_kernel_x2: FP32, m <= 2, full model,
+// CTAs of 32 x 8, tile heights 14 and 30).
 bool pair_fits(const cdf_lb *h, dim3 b, int th) {
+    if (b.z == 2 && (h->mr || h->P.case1 || h->m > 2 || b.x != 32 || b.y != 8 || (th != 14 && th != 30)))
+        return false;
     const int max_threads = h->mr ? step2_mr_max_threads(h->m) : step2_max_threads(h->m);
     if (b.x % 32 != 0 || b.x < 32 || (int)(b.x * b.y) > max_threads || th < 1) return false;
     if (step2_smem_bytes(h->m, b, th) > (size_t)kStep2MaxSmem) return false;
@@ -446,7 +450,7 @@ cdf_status setup_pair(cdf_lb *h, const cdf_options *opt) {
     // steps per launch are asked for explicitly
     if (opt->temporal == -1 || opt->resident == 1 || (opt->block_x > 0 && opt->temporal == 0)) return CDF_OK;
     if (opt->temporal_block_x > 0) {  // a given shape
-        const dim3 b(opt->temporal_block_x, opt->temporal_block_y, 1);
+        const dim3 b(opt->temporal_block_x, opt->temporal_block_y, opt->temporal_lanes == 2 ? 2 : 1);
         if (!pair_fits(h, b, opt->temporal_tile_y))
             return fail(CDF_EINVAL, "the two-step kernel shape %d x %d, tile height %d, cannot run this lattice",
                         opt->temporal_block_x, opt->temporal_block_y, opt->temporal_tile_y);
@@ -484,7 +488,8 @@ cdf_status setup_pair(cdf_lb *h, const cdf_options *opt) {
                     const dim3 b(w, by, 1);
                     if (!pair_fits(h, b, th)) continue;
                     bool dup = false;
-                    for (auto &c : cands) dup = dup || (c.first.x == b.x && c.first.y == b.y && c.second == th);
+                    for (auto &c : cands)
+                        dup = dup || (c.first.x == b.x && c.first.y == b.y && c.first.z == b.z && c.second == th);
                     if (!dup) cands.push_back({b, th});
                 }
     }
@@ -734,6 +739,9 @@ cdf_status cdf_lb_create(const cdf_grid *grid, int m, const cdf_diffusion *dif, 
         return fail(CDF_EINVAL, "the prescribed-velocity mode has no force: set g = 0");
     if (!(opt->rho0 > 0.0)) return fail(CDF_EINVAL, "rho0 must be positive");
     if (opt->temporal < -1 || opt->temporal > 1) return fail(CDF_EINVAL, "temporal must be -1, 0 or 1");
+    if (opt->temporal_lanes < 0 || opt->temporal_lanes > 2) return fail(CDF_EINVAL, "temporal_lanes must be 0, 1 or 2");
+    if (opt->temporal_lanes == 2 && opt->temporal_block_x == 0)
+        return fail(CDF_EINVAL, "temporal_lanes = 2 goes with a given two-step kernel shape (32 x 8, tile_y 14 or 30)");
     if (opt->temporal_block_x != 0 || opt->temporal_block_y != 0 || opt->temporal_tile_y != 0) {
         if (opt->temporal != 1) return fail(CDF_EINVAL, "a two-step kernel shape needs temporal = 1");
         if ((opt->temporal_block_x != 32 && opt->temporal_block_x != 64) || opt->temporal_block_y < 1 ||
@@ -769,6 +777,10 @@ cdf_status cdf_lb_create(const cdf_grid *grid, int m, const cdf_diffusion *dif, 
         if (opt->block_y == 0 && opt->storage != CDF_FP32)
             return fail(CDF_EINVAL, "the flat launch (block_y = 0) exists for FP32 storage only");
     }
+    if (opt->block_lanes < 0 || opt->block_lanes > 2) return fail(CDF_EINVAL, "block_lanes must be 0, 1 or 2");
+    if (opt->block_lanes == 2 && (opt->block_x <= 0 || opt->block_y != 0 || opt->storage != CDF_FP32 ||
+                                  opt->prescribed_velocity || m > 2))
+        return fail(CDF_EINVAL, "block_lanes = 2: a given flat launch (block_y = 0), FP32 storage, full model, m <= 2");
 
     cdf_lb *h = new (std::nothrow) cdf_lb;
     if (!h) return fail(CDF_ENOMEM, "host allocation failed");
@@ -837,7 +849,7 @@ cdf_status cdf_lb_create(const cdf_grid *grid, int m, const cdf_diffusion *dif, 
         return fail(CDF_ECUDA, "memset failed");
     }
     if (opt->block_x > 0) {
-        h->block = dim3(opt->block_x, opt->block_y, 1);
+        h->block = dim3(opt->block_x, opt->block_y, opt->block_lanes == 2 ? 2 : 1);
     } else if ((st = autotune(h)) != CDF_OK) {
         release(h);
         return st;
@@ -1229,6 +1241,7 @@ cdf_status cdf_lb_get_info(const cdf_lb *h, cdf_info *out) {
         out->bytes_per_lup = 2.0 * 5 * h->m * 4.0 + 8.0 + 8.0 * h->m + 8.0 * h->sprev_planes;
     out->t = h->t;
     out->temporal = h->pair ? 1 : 0;
+    out->lanes = h->pair ? (int)h->pair_block.z : (h->resident ? 1 : (int)h->block.z);
     if (h->pair) {
         out->block_x = (int)h->pair_block.x;
         out->block_y = (int)h->pair_block.y;

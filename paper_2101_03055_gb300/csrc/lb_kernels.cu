@@ -96,6 +96,91 @@ __global__ void __launch_bounds__(256) step_kernel_flat(const LbParams p, const 
         step_node_planes<M, T>(p, x, y, pl, sp_in, sp_out, moments);
 }
 
+template <int M>
+__device__ __forceinline__ void pack_node(const float (&f0)[M][5], const float (&h0)[9], const float (&f1)[M][5],
+                                          const float (&h1)[9], F2 (&f)[M][5], F2 (&h)[9]) {
+#pragma unroll
+    for (int i = 0; i < 9; ++i) h[i] = pack2(h0[i], h1[i]);
+#pragma unroll
+    for (int a = 0; a < M; ++a)
+#pragma unroll
+        for (int i = 0; i < 5; ++i) f[a][i] = pack2(f0[a][i], f1[a][i]);
+}
+
+template <int M>
+__device__ __forceinline__ NodeOut<M> lane_out(const NodeOut<M, F2> &o, int k) {
+    NodeOut<M> r;
+#pragma unroll
+    for (int a = 0; a < M; ++a) r.phi[a] = lane(o.phi[a], k);
+    r.ux = lane(o.ux, k);
+    r.uy = lane(o.uy, k);
+    r.pr = lane(o.pr, k);
+    r.s1 = lane(o.s1, k);
+    return r;
+}
+
+// Flat launch with two nodes per thread (paired FP32 lanes): thread t updates
+// nodes t and t + half of the row-major order (half a multiple of 32, so the
+// second nodes of a warp are a whole warp's worth of the order too).  The two
+// nodes are pulled one after the other and collide together on paired FP32
+// lanes (collide<M, F2>): each lane runs the scalar update's operations in the
+// same order, so every node gets the bits of step_kernel_flat.  A lattice of
+// about one wave is bound by the instructions each SM issues for its share of
+// the nodes, which this halves for the arithmetic; where a lane has no node to
+// update (past the end, or a slab's halo row) it repeats the other lane's node
+// and its result is not stored.  FP32, m <= 2, full model.
+template <int M>
+__global__ void __launch_bounds__(256) step_kernel_flat_x2(const LbParams p, const Planes<float> pl,
+                                                           const float *sp_in, float *sp_out,
+                                                           float *__restrict__ moments, int half) {
+    constexpr unsigned kAll = 0xffffffffu;
+    pdl_wait_and_release();
+    const int n = p.nx * p.ny, nx = p.nx;
+    const int i0 = blockIdx.x * blockDim.x + threadIdx.x, i1 = i0 + half;
+    bool ok[2];
+    int xs[2], ys[2];
+    ys[0] = i0 / nx;
+    xs[0] = i0 - ys[0] * nx;
+    ys[1] = i1 / nx;
+    xs[1] = i1 - ys[1] * nx;
+#pragma unroll
+    for (int k = 0; k < 2; ++k) ok[k] = i0 < half && (k ? i1 : i0) < n && ys[k] >= p.row_lo && ys[k] < p.row_hi;
+    const int ka = ok[0] ? 0 : 1, kb = ok[1] ? 1 : 0;  // a lane without a node repeats the other's
+    const int xa = xs[ka], ya = ys[ka], xb = xs[kb], yb = ys[kb];
+    const bool any = ok[0] || ok[1];
+    const bool inta = __all_sync(kAll, any && inner_node(p, xa, ya));
+    const bool intb = __all_sync(kAll, any && inner_node(p, xb, yb));
+    if (!any) return;
+    const int pitch = p.pitch;
+    const auto mk = [pitch](int sx, int sy) { return sy * pitch + sx; };
+    const auto ld = [&pl, &p](int plane, int off) { return __ldg(pl.in[plane] + CDF_CHK(p, off, p.plane, 1)); };
+    float h0[9], f0[M][5], h1[9], f1[M][5];
+    if (inta) pull_node<M, true>(p, xa, ya, mk, ld, f0, h0);
+    else pull_node<M, false>(p, xa, ya, mk, ld, f0, h0);
+    if (intb) pull_node<M, true>(p, xb, yb, mk, ld, f1, h1);
+    else pull_node<M, false>(p, xb, yb, mk, ld, f1, h1);
+    const int oa = CDF_CHK(p, ya * pitch + xa, p.plane, 2), ob = CDF_CHK(p, yb * pitch + xb, p.plane, 2);
+    const bool consume = (M >= 2 && p.skind == 2);
+    F2 h[9], f[M][5];
+    pack_node<M>(f0, h0, f1, h1, f, h);
+    NodeOut<M, F2> o;
+    collide<M>(p, f, h, pack2(pref_at(p, xa, ya), pref_at(p, xb, yb)),
+               consume ? pack2(sp_in[oa], sp_in[ob]) : splat<F2>(0.f), false, o);
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+        if (!ok[k]) continue;
+        const int o0 = k ? ob : oa;
+#pragma unroll
+        for (int i = 0; i < 9; ++i) pl.out[i][o0] = lane(h[i], k);
+#pragma unroll
+        for (int a = 0; a < M; ++a)
+#pragma unroll
+            for (int i = 0; i < 5; ++i) pl.out[9 + 5 * a + i][o0] = lane(f[a][i], k);
+        if (consume) sp_out[o0] = lane(o.s1, k);
+        if (moments) write_moments<M>(moments, p.plane, o0, lane_out<M>(o, k));
+    }
+}
+
 // ---- two time steps per launch (temporal blocking), FP32 storage ----------------
 // A small lattice lives in L2 between steps, and a one-step launch is then
 // bound by one full pass over the state plus the launch gap.  Here a CTA of
@@ -206,6 +291,130 @@ __global__ void __launch_bounds__(FW ? FW * FY : step2_max_threads(M), FW ? step
             for (int i = 0; i < 5; ++i) pl.out[9 + 5 * a + i][o0] = f[a][i];
         if (consume) sp_out[o0] = o.s1;
         if (moments) write_moments<M>(moments, P, o0, o);
+    }
+}
+
+// ---- two time steps per launch, two nodes per thread (paired FP32 lanes) ---------
+// The tiling of step2_kernel for CTAs of 32 x 8 threads and output tiles of
+// 30 x FT (FT = 14 or 30), with every thread updating two nodes of its column
+// at once: rows ly and ly + 8 of R1 (step 1) or of the tile (step 2).  The two
+// nodes are pulled one after the other (pull table and loads per node) and
+// then collide together on paired FP32 lanes (collide<M, F2>), which halves the
+// arithmetic instructions of the node update.  Each lane performs the scalar
+// update's operations in the same order with the same rounding, so every node
+// gets the bits of step2_kernel and of step_kernel.  Where one of the two rows
+// has no node to update (outside the lattice, or past the tile), its lane
+// repeats the other row's node and its result is not stored.  256 threads,
+// two CTAs per SM (up to 128 registers a thread).
+template <int M, int FT>
+__global__ void __launch_bounds__(256, 2)
+    step2_kernel_x2(const LbParams p, int, const Planes<float> pl, const float *sp_in, float *sp_out,
+                    float *__restrict__ moments) {
+    constexpr int NP = 9 + 5 * M, W1 = 32, BY = 8, H1 = FT + 2, SP = W1 * H1, TW = W1 - 2;
+    static_assert(H1 % (2 * BY) == 0, "the rows of R1 fill whole paired passes");
+    constexpr unsigned kAll = 0xffffffffu;
+    extern __shared__ float sm[];
+    pdl_wait_and_release();
+    const int X0 = blockIdx.x * TW, Y0 = blockIdx.y * FT;
+    const long long P = p.plane;
+    const int pitch = p.pitch, nx = p.nx, ny = p.ny;
+    const bool consume = M >= 2 && p.skind == 2;
+    const int lx = threadIdx.x;
+    const int xu = X0 - 1 + lx;
+    const bool colv = xu <= min(X0 + TW, nx) && (p.periodic_x || (xu >= 0 && xu < nx));
+    const int gx = xu < 0 ? xu + nx : (xu >= nx ? xu - nx : xu);
+
+    // ---- step 1: R1 from global memory into shared memory, rows ly and ly + BY
+    {
+        const auto mk = [pitch](int sx, int sy) { return sy * pitch + sx; };
+        const auto ld = [&pl, &p, P](int plane, int off) { return __ldg(pl.in[plane] + CDF_CHK(p, off, P, 1)); };
+#pragma unroll
+        for (int ly = threadIdx.y; ly < H1; ly += 2 * BY) {
+            bool ok[2];
+            int gy[2];
+#pragma unroll
+            for (int k = 0; k < 2; ++k) {
+                const int yu = Y0 - 1 + ly + k * BY;
+                ok[k] = colv && yu <= min(Y0 + FT, ny) && (p.periodic_y || (yu >= 0 && yu < ny));
+                gy[k] = yu < 0 ? yu + ny : (yu >= ny ? yu - ny : yu);
+            }
+            const bool any = ok[0] || ok[1];
+            const int ya = ok[0] ? gy[0] : gy[1], yb = ok[1] ? gy[1] : gy[0];
+            // warp votes before any lane leaves the pass
+            const bool gena = __any_sync(kAll, any && !inner_node(p, gx, ya));
+            const bool genb = __any_sync(kAll, any && !inner_node(p, gx, yb));
+            if (!any) continue;
+            float h0[9], f0[M][5], h1[9], f1[M][5];
+            if (!gena) pull_node<M, true>(p, gx, ya, mk, ld, f0, h0);
+            else pull_node<M, false>(p, gx, ya, mk, ld, f0, h0);
+            if (!genb) pull_node<M, true>(p, gx, yb, mk, ld, f1, h1);
+            else pull_node<M, false>(p, gx, yb, mk, ld, f1, h1);
+            const int oa = CDF_CHK(p, ya * pitch + gx, P, 2), ob = CDF_CHK(p, yb * pitch + gx, P, 2);
+            F2 h[9], f[M][5];
+            pack_node<M>(f0, h0, f1, h1, f, h);
+            NodeOut<M, F2> o;
+            collide<M>(p, f, h, pack2(pref_at(p, gx, ya), pref_at(p, gx, yb)),
+                       consume ? pack2(sp_in[oa], sp_in[ob]) : splat<F2>(0.f), false, o);
+#pragma unroll
+            for (int k = 0; k < 2; ++k) {
+                if (!ok[k]) continue;
+                const int l0 = CDF_CHK(p, (ly + k * BY) * W1 + lx, SP, 3);
+#pragma unroll
+                for (int i = 0; i < 9; ++i) sm[i * SP + l0] = lane(h[i], k);
+#pragma unroll
+                for (int a = 0; a < M; ++a)
+#pragma unroll
+                    for (int i = 0; i < 5; ++i) sm[(9 + 5 * a + i) * SP + l0] = lane(f[a][i], k);
+                if (consume) sm[NP * SP + l0] = lane(o.s1, k);
+            }
+        }
+    }
+    __syncthreads();
+
+    // ---- step 2: the tile from shared memory into global memory, rows ly and ly + BY
+    const auto lds = [&p](int plane, int off) { return sm[plane * SP + CDF_CHK(p, off, SP, 4)]; };
+    const auto mk_in = [X0, Y0](int sx, int sy) { return (sy - Y0 + 1) * W1 + (sx - X0 + 1); };
+    const auto mk_gen = [X0, Y0, nx, ny](int sx, int sy) {
+        int a = sx - X0 + 1, b = sy - Y0 + 1;
+        a = a < 0 ? a + nx : (a >= W1 ? a - nx : a);
+        b = b < 0 ? b + ny : (b >= H1 ? b - ny : b);
+        return b * W1 + a;
+    };
+#pragma unroll
+    for (int ly = 1 + threadIdx.y; ly <= FT; ly += 2 * BY) {
+        const int x = xu, ya = Y0 - 1 + ly;
+        const bool oka = lx >= 1 && lx <= TW && x < nx && ya < ny;
+        const bool okb = oka && ly + BY <= FT && ya + BY < ny;
+        const int yb = okb ? ya + BY : ya;
+        const bool gena = __any_sync(kAll, oka && !inner_node(p, x, ya));
+        const bool genb = __any_sync(kAll, oka && !inner_node(p, x, yb));
+        if (!oka) continue;
+        float h0[9], f0[M][5], h1[9], f1[M][5];
+        if (!gena) pull_node<M, true>(p, x, ya, mk_in, lds, f0, h0);
+        else pull_node<M, false>(p, x, ya, mk_gen, lds, f0, h0);
+        if (!genb) pull_node<M, true>(p, x, yb, mk_in, lds, f1, h1);
+        else pull_node<M, false>(p, x, yb, mk_gen, lds, f1, h1);
+        const int la = ly * W1 + lx, lb = (yb - Y0 + 1) * W1 + lx;
+        F2 h[9], f[M][5];
+        pack_node<M>(f0, h0, f1, h1, f, h);
+        NodeOut<M, F2> o;
+        collide<M>(p, f, h, pack2(pref_at(p, x, ya), pref_at(p, x, yb)),
+                   consume ? pack2(sm[NP * SP + CDF_CHK(p, la, SP, 4)], sm[NP * SP + CDF_CHK(p, lb, SP, 4)])
+                           : splat<F2>(0.f),
+                   false, o);
+#pragma unroll
+        for (int k = 0; k < 2; ++k) {
+            if (k == 1 && !okb) continue;
+            const int o0 = CDF_CHK(p, (k ? yb : ya) * pitch + x, P, 2);
+#pragma unroll
+            for (int i = 0; i < 9; ++i) pl.out[i][o0] = lane(h[i], k);
+#pragma unroll
+            for (int a = 0; a < M; ++a)
+#pragma unroll
+                for (int i = 0; i < 5; ++i) pl.out[9 + 5 * a + i][o0] = lane(f[a][i], k);
+            if (consume) sp_out[o0] = lane(o.s1, k);
+            if (moments) write_moments<M>(moments, P, o0, lane_out<M>(o, k));
+        }
     }
 }
 
@@ -832,6 +1041,21 @@ cudaError_t step_dispatch(const LbParams &p, const void *in, void *out, const fl
         return cudaErrorInvalidValue;
     }
     const Planes<T> pl = planes_of(p, i, o);
+    if (block.y == 0 && block.z == 2) {  // flat launch, two nodes per thread (FP32, m <= 2)
+        if constexpr (std::is_same<T, float>::value) {
+            const long long n = (long long)p.nx * p.ny;
+            const int half = (int)(((n + 1) / 2 + 31) / 32 * 32);
+            dim3 fb(block.x), grid((unsigned)((half + block.x - 1) / block.x));
+            cudaError_t e = cudaSuccess;
+            switch (p.m) {
+                case 1: e = launch_pdl(step_kernel_flat_x2<1>, grid, fb, s, p, pl, sp_in, sp_out, mom, half); break;
+                case 2: e = launch_pdl(step_kernel_flat_x2<2>, grid, fb, s, p, pl, sp_in, sp_out, mom, half); break;
+                default: return cudaErrorInvalidValue;
+            }
+            return e != cudaSuccess ? e : cudaGetLastError();
+        }
+        return cudaErrorInvalidValue;
+    }
     if (block.y == 0) {  // flat launch
         const long long n = (long long)p.nx * p.ny;
         dim3 fb(block.x), grid((unsigned)((n + block.x - 1) / block.x));
@@ -917,6 +1141,11 @@ cudaError_t launch_step2(const LbParams &p, const float *in, float *out, const f
     const size_t smem = step2_smem_bytes(p.m, block, th);
     dim3 grid((p.nx + block.x - 3) / (block.x - 2), (p.ny + th - 1) / th);
     const Planes<float> pl = planes_of(p, in, out);
+    // block.z == 2 names the paired-lane kernel (two nodes per thread; CTAs of
+    // 32 x 8 threads, tile heights 14 and 30)
+    const bool x2 = block.z == 2;
+    if (x2 && (p.case1 || block.x != 32 || block.y != 8 || (th != 14 && th != 30))) return cudaErrorInvalidValue;
+    const dim3 threads(block.x, block.y, 1);
     // the opt-in to more than 48 KB of dynamic shared memory, once per device and m
     static std::atomic<bool> attr_set[64][kMaxM + 1];
     int dev = 0;
@@ -938,16 +1167,27 @@ cudaError_t launch_step2(const LbParams &p, const float *in, float *out, const f
             if (e == cudaSuccess)                                                                        \
                 e = cudaFuncSetAttribute(step2_kernel_case1<MM>,                                         \
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, kStep2MaxSmem);    \
+            if (e == cudaSuccess && MM <= 2)                                                             \
+                e = cudaFuncSetAttribute(step2_kernel_x2<(MM <= 2 ? MM : 2), 14>,                        \
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, kStep2MaxSmem);    \
+            if (e == cudaSuccess && MM <= 2)                                                             \
+                e = cudaFuncSetAttribute(step2_kernel_x2<(MM <= 2 ? MM : 2), 30>,                        \
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, kStep2MaxSmem);    \
             if (e != cudaSuccess) return e;                                                              \
             attr_set[dev][MM].store(true);                                                               \
         }                                                                                                \
         if (p.case1)                                                                                     \
-            e = launch_pdl_smem(step2_kernel_case1<MM>, grid, block, smem, s, p, th, pl, sp_in, sp_out, moments); \
+            e = launch_pdl_smem(step2_kernel_case1<MM>, grid, threads, smem, s, p, th, pl, sp_in, sp_out, moments); \
+        else if (x2)                                                                                     \
+            e = MM > 2 ? cudaErrorInvalidValue                                                           \
+                       : launch_pdl_smem(th == 14 ? step2_kernel_x2<(MM <= 2 ? MM : 2), 14>              \
+                                                  : step2_kernel_x2<(MM <= 2 ? MM : 2), 30>,             \
+                                         grid, threads, smem, s, p, th, pl, sp_in, sp_out, moments);     \
         else if (fixed)                                                                                  \
-            e = launch_pdl_smem(step2_kernel<MM, 32, 8, 14>, grid, block, smem, s, p, th, pl, sp_in, sp_out,     \
+            e = launch_pdl_smem(step2_kernel<MM, 32, 8, 14>, grid, threads, smem, s, p, th, pl, sp_in, sp_out,   \
                                 moments);                                                                \
         else                                                                                             \
-            e = launch_pdl_smem(step2_kernel<MM>, grid, block, smem, s, p, th, pl, sp_in, sp_out, moments);   \
+            e = launch_pdl_smem(step2_kernel<MM>, grid, threads, smem, s, p, th, pl, sp_in, sp_out, moments); \
         break;
         CDF_STEP2_CASE(1)
         CDF_STEP2_CASE(2)

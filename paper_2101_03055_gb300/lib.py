@@ -72,7 +72,7 @@ class cdf_options(ctypes.Structure):
                 ("prescribed_velocity", ctypes.c_int), ("temporal", ctypes.c_int),
                 ("temporal_block_x", ctypes.c_int), ("temporal_block_y", ctypes.c_int),
                 ("temporal_tile_y", ctypes.c_int), ("halo_rows", ctypes.c_int), ("origin_y", ctypes.c_int),
-                ("ny_global", ctypes.c_int)]
+                ("ny_global", ctypes.c_int), ("temporal_lanes", ctypes.c_int), ("block_lanes", ctypes.c_int)]
 
 
 class cdf_info(ctypes.Structure):
@@ -80,14 +80,15 @@ class cdf_info(ctypes.Structure):
                 ("storage", ctypes.c_int), ("planes", ctypes.c_int), ("sprev_planes", ctypes.c_int),
                 ("block_x", ctypes.c_int), ("block_y", ctypes.c_int), ("resident", ctypes.c_int),
                 ("tile_x", ctypes.c_int), ("tile_y", ctypes.c_int), ("tiles", ctypes.c_int),
-                ("bytes_per_lup", ctypes.c_double), ("t", ctypes.c_longlong), ("temporal", ctypes.c_int)]
+                ("bytes_per_lup", ctypes.c_double), ("t", ctypes.c_longlong), ("temporal", ctypes.c_int),
+                ("lanes", ctypes.c_int)]
 
 
 class cdf_batch_options(ctypes.Structure):
     _fields_ = [("storage", ctypes.c_int), ("rho0", ctypes.c_double), ("cuda_stream", ctypes.c_void_p),
                 ("tile_x", ctypes.c_int), ("tile_y", ctypes.c_int), ("steps_per_launch", ctypes.c_int),
                 ("barrier_timeout_s", ctypes.c_double), ("test_unreachable_barrier", ctypes.c_int),
-                ("mode", ctypes.c_int), ("chain_tile_y", ctypes.c_int)]
+                ("mode", ctypes.c_int), ("chain_tile_y", ctypes.c_int), ("chain_lanes", ctypes.c_int)]
 
 
 class cdf_batch_info(ctypes.Structure):
@@ -95,7 +96,8 @@ class cdf_batch_info(ctypes.Structure):
                 ("tiles", ctypes.c_longlong), ("tile_x", ctypes.c_int), ("tile_y", ctypes.c_int),
                 ("grid_blocks", ctypes.c_int), ("steps_per_launch", ctypes.c_int),
                 ("bytes_per_lup", ctypes.c_double), ("t", ctypes.c_longlong), ("mode", ctypes.c_int),
-                ("chain_block_x", ctypes.c_int), ("chain_block_y", ctypes.c_int), ("chain_tile_y", ctypes.c_int)]
+                ("chain_block_x", ctypes.c_int), ("chain_block_y", ctypes.c_int), ("chain_tile_y", ctypes.c_int),
+                ("chain_lanes", ctypes.c_int)]
 
 
 _DP = ctypes.POINTER(ctypes.c_double)
@@ -422,13 +424,18 @@ def structs_from_problem(pb: Problem, storage: str = "fp32", stream: int = 0, bl
         opt.phi_ref[a] = float(ref[a])
     grad = p_ref_grad if p_ref_grad is not None else default_p_ref_grad(pb)
     opt.p_ref_grad[0], opt.p_ref_grad[1] = float(grad[0]), float(grad[1])
-    if block is not None:
-        opt.block_x, opt.block_y = block
+    if block is not None:  # (block_x, block_y) or, for a flat launch, (block_x, 0, lanes)
+        opt.block_x, opt.block_y = block[0], block[1]
+        if len(block) > 2:
+            opt.block_lanes = block[2]
     opt.resident, opt.wait_timeout_s, opt.test_stall_tile = int(resident), float(wait_timeout_s), int(test_stall_tile)
     opt.prescribed_velocity = int(getattr(pb, "case1", False))
     opt.temporal = int(temporal)
-    if temporal_shape is not None:
-        opt.temporal_block_x, opt.temporal_block_y, opt.temporal_tile_y = (int(v) for v in temporal_shape)
+    if temporal_shape is not None:  # (block_x, block_y, tile_y) or (block_x, block_y, tile_y, lanes)
+        ts = [int(v) for v in temporal_shape]
+        opt.temporal_block_x, opt.temporal_block_y, opt.temporal_tile_y = ts[:3]
+        if len(ts) > 3:
+            opt.temporal_lanes = ts[3]
     return grid, dif, src, frc, bc, opt
 
 
@@ -462,7 +469,9 @@ class Solver:
         """resident: 0 = the autotuner decides whether the tile-resident step is
         used, 1 = always, -1 = never (cdf_options.resident).  temporal: the
         same choice for two steps per launch (cdf_options.temporal);
-        temporal_shape: (block_x, block_y, tile_y) of that kernel, or None."""
+        temporal_shape: (block_x, block_y, tile_y) of that kernel, or
+        (block_x, block_y, tile_y, lanes) with lanes = 2 for the paired-lane
+        kernel (cdf_options.temporal_lanes), or None."""
         self.pb = pb
         self.m, self.nx, self.ny = pb.m, pb.nx, pb.ny
         self.storage = storage
@@ -656,7 +665,8 @@ class BatchSolver:
     """Many lattices (same m and source kind, FP32) advanced by the persistent batched kernel."""
 
     def __init__(self, problems, stream: int = 0, tile=None, steps_per_launch: int = 0, barrier_timeout_s: float = 0.0,
-                 test_unreachable_barrier: bool = False, init: bool = True, mode: int = 0, chain_tile_y: int = 0):
+                 test_unreachable_barrier: bool = False, init: bool = True, mode: int = 0, chain_tile_y: int = 0,
+                 chain_lanes: int = 0):
         self.problems = list(problems)
         n = len(self.problems)
         m = self.problems[0].m
@@ -685,6 +695,7 @@ class BatchSolver:
         opt.test_unreachable_barrier = int(test_unreachable_barrier)
         opt.mode = mode
         opt.chain_tile_y = chain_tile_y
+        opt.chain_lanes = chain_lanes
         self.h = cdf_batch_create(n, grids, m, dif, nu, src, frc, bcs, phi_ref, grad, opt)
         self.m = m
         if init:

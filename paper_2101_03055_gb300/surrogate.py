@@ -492,9 +492,11 @@ def time_to_steady(net: UNet, prms, n: int, n_net: int = 64, tol: float = 1e-5, 
     cdf_lb_run_to_steady over `check_every` steps below `tol`) for n x n cavities of
     the parameters `prms`, from rest and from the network's prediction (made on the
     n_net x n_net lattice the network was trained on and resampled to n x n; the
-    fluid at rest by default, see moments_from_prediction).  Both starts run the
-    cases together in one batched solver.  Returns per start the steps at which each
-    case first met the test (-1: not within max_steps) and the seconds of the run."""
+    fluid at rest by default, see moments_from_prediction).  Each case and start runs
+    on its own single-lattice solver (the configuration the autotuner picks for
+    n x n), so the seconds are that case's own.  Returns per start the steps at which
+    each case met the test (-1: not within max_steps), the seconds of each run and
+    the last residuals."""
     import time
     import torch
     x = torch.as_tensor(input_planes(n_net, prms)).cuda().to(torch.bfloat16)
@@ -507,17 +509,22 @@ def time_to_steady(net: UNet, prms, n: int, n_net: int = 64, tol: float = 1e-5, 
     for k, pb in enumerate(pbs):
         M = moments_from_prediction(pred[k], pb, velocity)
         starts["warm"].append((f64(M[:2]), f64(M[2:4]), f64(M[4])))
-    b = lib.BatchSolver(pbs, tile=(64, 4), mode=0, init=False)
     out = {}
     for name, inits in starts.items():
+        first = np.full(len(pbs), -1, dtype=np.int64)
+        secs = np.zeros(len(pbs))
+        R = np.full(len(pbs), np.inf)
         for k, (phi, u, p) in enumerate(inits):
-            lib.cdf_batch_init_moments(b.h, k, phi, u, p)
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        taken, R, first = b.run_to_steady(tol, check_every, max_steps)
-        torch.cuda.synchronize()
-        out[name] = {"first": first, "seconds": time.perf_counter() - t0, "steps": taken, "R": R}
-    b.close()
+            s = lib.Solver(pbs[k], init=False)
+            s.init_moments(phi, u, p)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            ok, steps, R[k] = s.run_to_steady(tol, check_every, max_steps)
+            torch.cuda.synchronize()
+            secs[k] = time.perf_counter() - t0
+            first[k] = steps if ok else -1
+            s.close()
+        out[name] = {"first": first, "seconds": secs, "steps": int(max(first.max(), 0)), "R": R}
     return out
 
 
@@ -654,7 +661,8 @@ if __name__ == "__main__":
         for tol in a.tol:
             res = time_to_steady(net, prms, a.time_to_steady, 64, tol=tol, check_every=a.check_every,
                                  max_steps=a.max_steps)
-            out["runs"][f"{tol:g}"] = {k: {"first": v["first"].tolist(), "seconds": v["seconds"], "steps": v["steps"],
+            out["runs"][f"{tol:g}"] = {k: {"first": v["first"].tolist(), "seconds": v["seconds"].tolist(),
+                                          "steps": v["steps"],
                                           "R": v["R"].tolist()} for k, v in res.items()}
             print(tol, {k: v["first"].tolist() for k, v in res.items()}, flush=True)
         if a.out:
