@@ -82,6 +82,38 @@ __host__ __device__ constexpr int c19(int i, int d) {
 }
 __host__ __device__ constexpr int opp19(int i) { return i == 0 ? 0 : ((i & 1) ? i + 1 : i - 1); }
 __host__ __device__ constexpr float kB19(int i) { return i == 0 ? 0.f : (i <= 6 ? kB1 : kB2); }
+constexpr float kInvC3 = 0x1.000002p-1f;  // fl(1 / kC3): Eq. sum-p by one multiply
+
+// c . (a0, a1, a2) for a lattice direction whose components are 0 or +-1 (at most
+// two nonzero), without multiplications by the components.
+__device__ __forceinline__ float cdot3(int c0, int c1, int c2, float a0, float a1, float a2) {
+    const float t0 = c0 > 0 ? a0 : -a0, t1 = c1 > 0 ? a1 : -a1, t2 = c2 > 0 ? a2 : -a2;
+    if (c0 != 0) return c1 != 0 ? t0 + t1 : (c2 != 0 ? t0 + t2 : t0);
+    if (c1 != 0) return c2 != 0 ? t1 + t2 : t1;
+    return c2 != 0 ? t2 : 0.f;
+}
+__device__ __forceinline__ float c19dot(int i, const float (&a)[3]) {
+    return cdot3(c19(i, 0), c19(i, 1), c19(i, 2), a[0], a[1], a[2]);
+}
+__device__ __forceinline__ float c7dot(int i, const float (&a)[3]) {
+    return cdot3(c7(i, 0), c7(i, 1), c7(i, 2), a[0], a[1], a[2]);
+}
+
+// Fluid equilibrium deviation on D3Q19 (Eq. heq): for i != 0,
+// kB_i (q + 1.5 (c_i.u)^2) + kB_i c_i.u with q = p' - 0.5 u.u; the first term is even
+// in c_i, the second odd, so the odd directions i = 1, 3, .., 17 and their opposites
+// i + 1 share them (the collision forms them once per pair); -kC3 p' - kQ3 u.u for i = 0.
+__device__ __forceinline__ float heq3_even(int i, float q, const float (&u)[3]) {
+    const float cu = c19dot(i, u);
+    return __fmul_rn(kB19(i), fmaf(1.5f, __fmul_rn(cu, cu), q));
+}
+__device__ __forceinline__ float heq3_odd(int i, const float (&u)[3]) { return __fmul_rn(kB19(i), c19dot(i, u)); }
+__device__ __forceinline__ float fluid_eq3(int i, float prd, const float (&u)[3], float usq) {
+    if (i == 0) return fmaf(-kC3, prd, __fmul_rn(-kQ3, usq));
+    const int b = (i & 1) ? i : i - 1;
+    const float E = heq3_even(b, fmaf(-0.5f, usq, prd), u), O = heq3_odd(b, u);
+    return b == i ? E + O : E - O;
+}
 
 __device__ __forceinline__ float pref_at(const Lb3Params &p, int x, int y, int z) {
     return fmaf(p.gref[0], (float)x - p.xc,
@@ -143,7 +175,7 @@ __device__ __forceinline__ void collide3(const Lb3Params &p, float (&f)[M][7], f
     float snr = 0.f;
 #pragma unroll
     for (int i = 1; i < 19; ++i) snr += h[i];
-    const float prd = fmaf(-kQ3, usq, snr) / kC3;
+    const float prd = __fmul_rn(fmaf(-kQ3, usq, snr), kInvC3);
 
     // Eq. omega-D (cs_s^2 = 1/4): omega^-1 = B + delta e_0 e_1^T, delta = -4 chi phi_0 r
     float om[M][M];
@@ -182,10 +214,7 @@ __device__ __forceinline__ void collide3(const Lb3Params &p, float (&f)[M][7], f
         const float t = 4.f * phi[a];
         float mv = 0.f;
 #pragma unroll
-        for (int i = 1; i < 7; ++i) {
-            const float cu = (float)c7(i, 0) * u[0] + (float)c7(i, 1) * u[1] + (float)c7(i, 2) * u[2];
-            feq[a][i] = __fmul_rn(kW7, fmaf(t, cu, phid[a]));
-        }
+        for (int i = 1; i < 7; ++i) feq[a][i] = __fmul_rn(kW7, fmaf(t, c7dot(i, u), phid[a]));
         mv = ((feq[a][1] + feq[a][4]) + (feq[a][2] + feq[a][5])) + (feq[a][3] + feq[a][6]);
         feq[a][0] = phid[a] - mv;
     }
@@ -200,21 +229,22 @@ __device__ __forceinline__ void collide3(const Lb3Params &p, float (&f)[M][7], f
             float coll = 0.f;
 #pragma unroll
             for (int b = 0; b < M; ++b) coll = fmaf(om[a][b], neq[b], coll);
-            const float cJ = (float)c7(i, 0) * J[a][0] + (float)c7(i, 1) * J[a][1] + (float)c7(i, 2) * J[a][2];
-            const float G = (i == 0) ? 0.f : __fmul_rn(4.f * kW7, cJ);
+            const float G = (i == 0) ? 0.f : __fmul_rn(4.f * kW7, c7dot(i, J[a]));
             f[a][i] = (f[a][i] - coll) + fmaf(w, fmaf(1.5f, S[a], __fmul_rn(-0.5f, Sp[a])), G);
         }
     }
-    // Eq. evolution3 with Eq. force (varphi = 0) on D3Q19
+    // Eq. evolution3 with Eq. force (varphi = 0) on D3Q19: h*_i = h_i - wf (h_i - h^eq_i)
+    // + fw F_i (the non-equilibrium part first: a node at equilibrium stays there
+    // exactly).  h^eq and F_i = kB_i c_i.F split into parts even and odd in c_i, which a
+    // direction i (odd) and its opposite i + 1 share.
     const float wf = p.omega_f, fw = 1.f - 0.5f * wf;
+    h[0] = fmaf(-wf, h[0] - fluid_eq3(0, prd, u, usq), h[0]);
+    const float q = fmaf(-0.5f, usq, prd);
 #pragma unroll
-    for (int i = 0; i < 19; ++i) {
-        const float cu = (float)c19(i, 0) * u[0] + (float)c19(i, 1) * u[1] + (float)c19(i, 2) * u[2];
-        const float cF = (float)c19(i, 0) * F[0] + (float)c19(i, 1) * F[1] + (float)c19(i, 2) * F[2];
-        const float heq = (i == 0) ? fmaf(-kC3, prd, __fmul_rn(-kQ3, usq))
-                                   : __fmul_rn(kB19(i), (prd + cu) + fmaf(__fmul_rn(1.5f, cu), cu, __fmul_rn(-0.5f, usq)));
-        const float Fi = __fmul_rn(kB19(i), cF);
-        h[i] = fmaf(fw, Fi, fmaf(-wf, h[i] - heq, h[i]));
+    for (int i = 1; i < 19; i += 2) {
+        const float E = heq3_even(i, q, u), O = heq3_odd(i, u), Fo = __fmul_rn(kB19(i), c19dot(i, F));
+        h[i] = fmaf(fw, Fo, fmaf(-wf, h[i] - (E + O), h[i]));
+        h[i + 1] = fmaf(fw, -Fo, fmaf(-wf, h[i + 1] - (E - O), h[i + 1]));
     }
 #pragma unroll
     for (int a = 0; a < M; ++a) o.phi[a] = phi[a];
@@ -365,19 +395,14 @@ __global__ void init3d_kernel(const Lb3Params p, const float *__restrict__ field
     for (int a = 0; a < M; ++a) {
         const float t = 4.f * phi[a];
 #pragma unroll
-        for (int i = 1; i < 7; ++i) {
-            const float cu = (float)c7(i, 0) * u[0] + (float)c7(i, 1) * u[1] + (float)c7(i, 2) * u[2];
-            f[a][i] = __fmul_rn(kW7, fmaf(t, cu, phid[a]));
-        }
+        for (int i = 1; i < 7; ++i) f[a][i] = __fmul_rn(kW7, fmaf(t, c7dot(i, u), phid[a]));
         f[a][0] = phid[a] - (((f[a][1] + f[a][4]) + (f[a][2] + f[a][5])) + (f[a][3] + f[a][6]));
     }
 #pragma unroll
     for (int i = 0; i < 19; ++i) {
-        const float cu = (float)c19(i, 0) * u[0] + (float)c19(i, 1) * u[1] + (float)c19(i, 2) * u[2];
-        const float cF = ((float)c19(i, 0) * p.g[0] + (float)c19(i, 1) * p.g[1] + (float)c19(i, 2) * p.g[2]) * fm;
-        const float heq = (i == 0) ? fmaf(-kC3, prd, __fmul_rn(-kQ3, usq))
-                                   : __fmul_rn(kB19(i), (prd + cu) + fmaf(__fmul_rn(1.5f, cu), cu, __fmul_rn(-0.5f, usq)));
-        h[i] = heq - 0.5f * __fmul_rn(kB19(i), cF);
+        const float g[3] = {p.g[0], p.g[1], p.g[2]};
+        const float cF = c19dot(i, g) * fm;
+        h[i] = fluid_eq3(i, prd, u, usq) - 0.5f * __fmul_rn(kB19(i), cF);
     }
     Out3<M> o;
     collide3<M>(p, f, h, prx, 0.f, true, o);

@@ -94,17 +94,51 @@ template <> struct Store<float> {
 // moves them out of FP16's subnormal range: normal numbers then cover
 // |d| in [1.5e-8, 16].
 constexpr float kHalfScale = 4096.f, kHalfUnscale = 1.f / 4096.f;
+// Random bits for the stochastic rounding of the value pair (x, y) in slot k of a
+// node's encoding: the lowbias32 integer hash (C. Wellons' published constants) of
+// the two FP32 bit patterns and the slot.  The rounding is then a deterministic
+// function of the values (bitwise reproducible, independent of where the node
+// sits in the lattice), while its errors are uncorrelated between populations and
+// nodes and average to zero.
+__device__ __forceinline__ unsigned sr_bits(float x, float y, unsigned k) {
+    unsigned h = __float_as_uint(x) ^ (__float_as_uint(y) * 0x9E3779B1u) ^ (k * 0x85EBCA77u);
+    h ^= h >> 16;
+    h *= 0x7FEB352Du;
+    h ^= h >> 15;
+    h *= 0x846CA68Bu;
+    h ^= h >> 16;
+    return h;
+}
+// encode2: the pair (x, y) rounded stochastically to the 16-bit type with one
+// cvt.rs (sm_100 and later): each value goes to one of its two 16-bit neighbours
+// with the probabilities that make the expected rounded value the value itself,
+// so the rounding of the stored deviations acts as a zero-mean perturbation
+// instead of a fixed forcing at a steady state.
 template <> struct Store<__half> {
     __device__ static __half encode(float v) { return __float2half_rn(v * kHalfScale); }
     __device__ static float decode(__half q) { return __half2float(q) * kHalfUnscale; }
     __device__ static float load(const __half *p) { return decode(__ldg(p)); }
     __device__ static void store(__half *p, float v) { *p = encode(v); }
+    __device__ static void encode2(float x, float y, unsigned k, __half &qx, __half &qy) {
+        unsigned d;
+        asm("cvt.rs.f16x2.f32 %0, %1, %2, %3;"
+            : "=r"(d)
+            : "f"(y * kHalfScale), "f"(x * kHalfScale), "r"(sr_bits(x, y, k)));
+        qx = __ushort_as_half((unsigned short)(d & 0xffffu));
+        qy = __ushort_as_half((unsigned short)(d >> 16));
+    }
 };
 template <> struct Store<__nv_bfloat16> {
     __device__ static __nv_bfloat16 encode(float v) { return __float2bfloat16_rn(v); }
     __device__ static float decode(__nv_bfloat16 q) { return __bfloat162float(q); }
     __device__ static float load(const __nv_bfloat16 *p) { return decode(__ldg(p)); }
     __device__ static void store(__nv_bfloat16 *p, float v) { *p = encode(v); }
+    __device__ static void encode2(float x, float y, unsigned k, __nv_bfloat16 &qx, __nv_bfloat16 &qy) {
+        unsigned d;
+        asm("cvt.rs.bf16x2.f32 %0, %1, %2, %3;" : "=r"(d) : "f"(y), "f"(x), "r"(sr_bits(x, y, k)));
+        qx = __ushort_as_bfloat16((unsigned short)(d & 0xffffu));
+        qy = __ushort_as_bfloat16((unsigned short)(d >> 16));
+    }
 };
 
 // Population load of the step.  A kernel that runs one step per launch reads
@@ -252,12 +286,25 @@ template <class V>
 __device__ __forceinline__ V usq_of(V ux, V uy) { return vfma(ux, ux, vmul(uy, uy)); }
 
 // Fluid equilibrium deviation (Eq. heq): h^eq_i(p, u) - h^eq_i(p_ref, 0)
-//   = kA_i (p' + c_i.u + 1.5 (c_i.u)^2 - 0.5 u.u)  (i != 0),  -kC p' - kQ u.u  (i = 0).
+//   = kA_i (q + 1.5 (c_i.u)^2) + kA_i c_i.u,  q = p' - 0.5 u.u  (i != 0),   -kC p' - kQ u.u  (i = 0).
+// The first term is even in c_i, the second odd: heq_even / heq_odd give them for the
+// directions i = 1, 2, 5, 6, whose opposites 3, 4, 7, 8 take the odd part with the
+// other sign.  Every user (the collision, which forms them once per pair of
+// opposite directions, the initialisation and the 16-bit storage) evaluates them
+// with these functions, so all agree bit for bit.
+template <class V>
+__device__ __forceinline__ V heq_even(int i, V q, V ux, V uy) {
+    const V cu = cdot(kC9x(i), kC9y(i), ux, uy);
+    return vmul(kA9(i), vfma(1.5f, vmul(cu, cu), q));
+}
+template <class V>
+__device__ __forceinline__ V heq_odd(int i, V ux, V uy) { return vmul(kA9(i), cdot(kC9x(i), kC9y(i), ux, uy)); }
 template <class V>
 __device__ __forceinline__ V fluid_equilibrium(int i, V prd, V ux, V uy, V usq) {
     if (i == 0) return vfma(-kC, prd, vmul(-kQ, usq));
-    const V cu = cdot(kC9x(i), kC9y(i), ux, uy);
-    return vmul(kA9(i), (prd + cu) + vfma(vmul(1.5f, cu), cu, vmul(-0.5f, usq)));
+    const int b = (i == 3 || i == 4 || i == 7 || i == 8) ? i - 2 : i;  // the direction of the pair in 1, 2, 5, 6
+    const V E = heq_even(b, vfma(-0.5f, usq, prd), ux, uy), O = heq_odd(b, ux, uy);
+    return b == i ? E + O : E - O;
 }
 
 // The second-order part of Eq. force per unit varphi, W_i (uF + Fu):(c_i c_i -
@@ -330,7 +377,9 @@ __device__ __forceinline__ void relaxation_matrix(const LbParams &p, const Scala
 // Eq. evolution12 for the scalars of one node: f*_i,a = f_i,a - sum_b omega_ab
 // (f_i,b - f^eq_i,b) + W_i S_a + (W_i S_a - W_i S_a(t-1)) / 2 + G_i,a with the
 // auxiliary source G_i,a = 3 W_i c_i . J_a (J from Eq. Gi, or from the time
-// difference of phi u in Case 1 of Sec. 2.1).
+// difference of phi u in Case 1 of Sec. 2.1).  The non-equilibrium part f - f^eq
+// is formed first, so a node at equilibrium stays there exactly (no rounding-level
+// forcing of the conserved scalar mass).
 template <int M, class V>
 __device__ __forceinline__ void scalar_collide(V (&f)[M][5], const ScalarState<M, V> &s, V ux, V uy,
                                                const V (&om)[M][M], const V (&Jx)[M], const V (&Jy)[M]) {
@@ -400,14 +449,34 @@ __device__ __forceinline__ void collide(const LbParams &p, V (&f)[M][5], V (&h)[
     scalar_collide<M>(f, s, ux, uy, om, Jx, Jy);
 
     // Eq. evolution3 with Eq. force, weighted by (1 - omega_f / 2):
-    // F_i = 3 W_i c_i.F  +  varphi [3 W_i (3 (c_i.u)(c_i.F) - u.F)  (i != 0),  -(3 - kC) u.F  (i = 0)]
+    //   h*_i = h_i - wf (h_i - h^eq_i) + fw F_i,   fw = 1 - wf / 2,
+    //   F_i = 3 W_i c_i.F  +  varphi [3 W_i (3 (c_i.u)(c_i.F) - u.F)  (i != 0),  -(3 - kC) u.F  (i = 0)].
+    // The non-equilibrium part h - h^eq is formed first, so a node at equilibrium stays
+    // there exactly.  For i != 0, h^eq_i = kA_i (q + 1.5 (c_i.u)^2) + kA_i c_i.u with
+    // q = p' - u.u / 2 (Eq. heq), and the first-order force kA_i c_i.F is odd in c_i:
+    // a direction and its opposite share the even parts and take the odd parts with
+    // opposite signs, so each pair forms them once.
     const float wf = p.omega_f, fw = 1.f - 0.5f * wf;
+    {
+        V F0 = splat<V>(0.f);
+        if (p.varphi != 0.f) F0 = vmul(p.varphi, force2_dir(0, ux, uy, Fx, Fy, uF));
+        h[0] = vfma(fw, F0, vfma(-wf, h[0] - fluid_equilibrium(0, prd, ux, uy, usq), h[0]));
+    }
+    const V q = vfma(-0.5f, usq, prd);
 #pragma unroll
-    for (int i = 0; i < 9; ++i) {
-        const V heq = fluid_equilibrium(i, prd, ux, uy, usq);
-        V Fi = (i == 0) ? splat<V>(0.f) : kA9(i) * cdot(kC9x(i), kC9y(i), Fx, Fy);
-        if (p.varphi != 0.f) Fi = vfma(p.varphi, force2_dir(i, ux, uy, Fx, Fy, uF), Fi);
-        h[i] = vfma(fw, Fi, vfma(-wf, h[i] - heq, h[i]));
+    for (int k = 0; k < 4; ++k) {
+        const int i = k < 2 ? k + 1 : k + 3, o = i + 2;  // i = 1, 2, 5, 6 and their opposites 3, 4, 7, 8
+        const float kA = kA9(i);
+        const V cu = cdot(kC9x(i), kC9y(i), ux, uy), cF = cdot(kC9x(i), kC9y(i), Fx, Fy);
+        const V E = heq_even(i, q, ux, uy), O = heq_odd(i, ux, uy), Fo = vmul(kA, cF);
+        V Fi = Fo, Fopp = -Fo;
+        if (p.varphi != 0.f) {
+            const V f2 = vmul(kA, vfma(vmul(3.f, cu), cF, -uF));  // even in c_i
+            Fi = vfma(p.varphi, f2, Fo);
+            Fopp = vfma(p.varphi, f2, -Fo);
+        }
+        h[i] = vfma(fw, Fi, vfma(-wf, h[i] - (E + O), h[i]));
+        h[o] = vfma(fw, Fopp, vfma(-wf, h[o] - (E - O), h[o]));
     }
 #pragma unroll
     for (int a = 0; a < M; ++a) o.phi[a] = s.phi[a];

@@ -612,7 +612,7 @@ __global__ void init_kernel(const LbParams p, const float *__restrict__ fields, 
     scalar_equilibrium<M>(phid, phi, ux, uy, f);
 #pragma unroll
     for (int i = 0; i < 9; ++i) {
-        float Fi = kA9(i) * (kC9x(i) * Fx + kC9y(i) * Fy);
+        float Fi = (i == 0 ? 0.f : kA9(i) * cdot(kC9x(i), kC9y(i), Fx, Fy));
         if (p.varphi != 0.f) Fi = fmaf(p.varphi, force2_dir(i, ux, uy, Fx, Fy, uF), Fi);
         h[i] = fluid_equilibrium(i, prd, ux, uy, usq) - 0.5f * Fi;
     }
@@ -740,21 +740,31 @@ __device__ __forceinline__ void pull_node_mr(const LbParams &p, int x, int y, co
 // sum_{i!=0} h^eq_i(p, u) = kC p' + kQ u.u in these variables).  The scalar
 // deviations are taken from the equilibrium at u_s, the velocity the receivers
 // rebuild with, so the shift of u leaves the scalar fluxes alone.  The stored
-// moments differ from the collision's by the rounding residuals.
+// moments differ from the collision's by the rounding residuals.  The deviations
+// are rounded stochastically, two at a time (Store<T>::encode2): the distribution
+// functions' own rounding errors then average to zero, where round-to-nearest
+// would leave a steady state under a fixed rounding-level forcing of the
+// non-conserved moments.
 template <int M, typename T>
 __device__ __forceinline__ void encode_node_mr(const float (&f)[M][5], const float (&h)[9], const NodeOut<M> &o,
                                                T (&fq)[M][5], T (&hq)[9], float (&mom)[M + 3]) {
+    // fluid deviations, rounded stochastically in pairs (slots 0..4)
+    float dh[9];
+#pragma unroll
+    for (int i = 0; i < 9; ++i) dh[i] = h[i] - href_dir(i, o.pr, o.ux, o.uy);
+#pragma unroll
+    for (int i = 0; i < 8; i += 2) Store<T>::encode2(dh[i], dh[i + 1], i / 2, hq[i], hq[i + 1]);
+    {
+        T spare;
+        Store<T>::encode2(dh[8], 0.f, 4, hq[8], spare);
+    }
     float rx = 0.f, ry = 0.f, rp = 0.f;
 #pragma unroll
-    for (int i = 0; i < 9; ++i) {
-        const float d = h[i] - href_dir(i, o.pr, o.ux, o.uy);
-        hq[i] = Store<T>::encode(d);
-        if (i != 0) {
-            const float e = Store<T>::decode(hq[i]) - d;  // exact (Sterbenz)
-            rx += kC9x(i) * e;
-            ry += kC9y(i) * e;
-            rp += e;
-        }
+    for (int i = 1; i < 9; ++i) {
+        const float e = Store<T>::decode(hq[i]) - dh[i];  // exact (Sterbenz)
+        if (kC9x(i) != 0) rx = kC9x(i) > 0 ? rx + e : rx - e;
+        if (kC9y(i) != 0) ry = kC9y(i) > 0 ? ry + e : ry - e;
+        rp += e;
     }
     const float us = o.ux - rx, vs = o.uy - ry;
     mom[M] = us;
@@ -764,14 +774,20 @@ __device__ __forceinline__ void encode_node_mr(const float (&f)[M][5], const flo
     // rebuild with u_s, so taking it here keeps the shift of u out of the scalar fluxes
     float feq[M][5];
     scalar_equilibrium<M>(o.phi, o.phi, us, vs, feq);
+    float df[5 * M + 1];
+#pragma unroll
+    for (int n = 0; n < 5 * M; ++n) df[n] = f[n / 5][n % 5] - feq[n / 5][n % 5];
+    df[5 * M] = 0.f;
+    T q[5 * M + 1];
+#pragma unroll
+    for (int n = 0; n < 5 * M; n += 2) Store<T>::encode2(df[n], df[n + 1], 5 + n / 2, q[n], q[n + 1]);
 #pragma unroll
     for (int a = 0; a < M; ++a) {
         float r = 0.f;
 #pragma unroll
         for (int i = 0; i < 5; ++i) {
-            const float d = f[a][i] - feq[a][i];
-            fq[a][i] = Store<T>::encode(d);
-            r += Store<T>::decode(fq[a][i]) - d;
+            fq[a][i] = q[5 * a + i];
+            r += Store<T>::decode(fq[a][i]) - df[5 * a + i];
         }
         mom[a] = o.phi[a] - r;
     }
@@ -927,7 +943,7 @@ __global__ void init_kernel_mr(const LbParams p, const float *__restrict__ field
     scalar_equilibrium<M>(phi, phi, ux, uy, f);
 #pragma unroll
     for (int i = 0; i < 9; ++i) {
-        float Fi = kA9(i) * (kC9x(i) * Fx + kC9y(i) * Fy);
+        float Fi = (i == 0 ? 0.f : kA9(i) * cdot(kC9x(i), kC9y(i), Fx, Fy));
         if (p.varphi != 0.f) Fi = fmaf(p.varphi, force2_dir(i, ux, uy, Fx, Fy, uF), Fi);
         h[i] = heq_dir(i, pr, ux, uy) - 0.5f * Fi;
     }
