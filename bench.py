@@ -487,7 +487,9 @@ def conv_line(N, H, W, Cin, Cout, reps, device, peak_tflops, peak_gbs):
     return {"description": f"3x3 convolution forward (bias + ReLU), N={N} {H}x{W}, {Cin}->{Cout} channels, BF16 "
                            f"operands, FP32 accumulation in tensor memory",
             "value": tf, "unit": "TFLOP/s", "launch_us": us, "flops_per_launch": flops,
-            "kernel": (f"conv3x3_tc_pipe_kernel<false,{Cout if Cout <= 128 else 128}>" if Cin >= 128 else
+            "kernel": (f"conv3x3_slab_kernel<{min(Cout, 128 if Cin < 64 else 64)},{Cin // 8}> (no im2col copy, "
+                       f"persistent)" if W % 128 == 0 and Cin in (16, 32, 64) else
+                       f"conv3x3_tc_pipe_kernel<false,{Cout if Cout <= 128 else 128}>" if Cin >= 128 else
                        f"conv3x3_tc_kernel<false,{Cout if Cout <= 128 else 128}>"), "gpu_launches": 2 * reps,
             "synchronous_staging": {"kernel": f"conv3x3_tc_kernel<false,{Cout if Cout <= 128 else 128}>",
                                     "launch_us": us_sync, "value": flops / us_sync / 1e6},

@@ -73,16 +73,21 @@ cdf_nn_status cdf_nn_adam(float *w, const float *g, float *m, float *v, void *w_
 const char *cdf_nn_last_error(void);
 /* Tensor-core path of the convolutions above.  1 (the default): the 5th-generation
  * tensor cores (tcgen05.mma, accumulators in tensor memory) with the faster operand
- * staging for the layer's depth -- tiles copied by cp.async through three stage
- * buffers when the GEMM input has at least 128 channels, two buffers filled by
- * ordinary loads below that (more CTAs per SM hide more latency at short K);
+ * staging for the layer's depth -- for a forward pass whose image rows are whole
+ * 128-pixel tiles with 16, 32 or 64 input channels, the kernel without im2col copy
+ * (each tile's three input rows staged once; every tap's operand is the same rows
+ * seen through a shifted descriptor; persistent CTAs); otherwise tiles copied by
+ * cp.async through three stage buffers when the GEMM input has at least 128
+ * channels, two buffers filled by ordinary loads below that (more CTAs per SM hide
+ * more latency at short K); 4: the kernel without im2col copy where the shape
+ * allows it, else as 1;
  * 2: tcgen05 with the two-buffer staging for every layer; 3: the forward pass on a
  * persistent warp-specialised tcgen05 kernel (producer warps, one MMA thread, epilogue
  * warps, two accumulators; slower than 1 at the surrogate's layer shapes, where one
  * CTA per SM leaves too few warps to hide latency), the backward pass as in 1;
- * 0: the warp-level MMA kernels.  The weight gradient runs on tcgen05 for 1, 2 and 3.
+ * 0: the warp-level MMA kernels.  The weight gradient runs on tcgen05 for 1 to 4.
  * Process-wide; all give the same results up to the order of the FP32 accumulation
- * (1, 2 and 3: the same bits). */
+ * (1 to 4 issue the same MMAs in the same order: the same bits). */
 cdf_nn_status cdf_nn_set_tensor_path(int tcgen05);
 /* *out = 1 if a bounded wait of a tcgen05 convolution ever ran out (its output is
  * then undefined), else 0.  Synchronises with the device. */

@@ -757,6 +757,228 @@ cudaError_t launch_conv_ws(const __nv_bfloat16 *in, const __nv_bfloat16 *w, cons
     return cudaGetLastError();
 }
 
+// ---------------------------------------------------------------------------
+// Forward 3x3 convolution without an im2col copy, for images whose rows are a
+// whole number of 128-pixel tiles and Cin = 8 G (16, 32 or 64 channels).  An
+// output tile is 128 consecutive pixels of one image row.  For each tile the CTA
+// stages the three input rows that the tile reads, 130 pixels each (one pixel of
+// zero padding on either side), once in shared memory, laid out
+// [ky][channel group g][pixel][8 channels]: 8 consecutive pixels of one group form
+// one 128-byte core matrix.  The A operand of tap (ky, kx) and channels 16j..16j+15
+// is that slab seen from pixel kx: a K-major descriptor whose start address moves
+// 16 bytes per pixel, with 128 bytes between 8-pixel groups and 130 x 16 bytes
+// between the two channel groups of one MMA.  So every input element is staged
+// once per tile, where the im2col staging copies it nine times.  The weights of
+// all nine taps for the CTA's BN output channels are staged once per CTA,
+// [tap][g][co][8 channels].  The CTA is persistent over tiles: the slab of the
+// next tile is copied (cp.async, zero fill outside the image) while the tensor
+// core works on the current one, and two accumulators in tensor memory let the
+// epilogue of one tile run while the next accumulates.  Every wait is bounded;
+// on a time-out the kernel sets g_tc_error, waits (bounded) for its own MMAs and
+// copies, frees its tensor memory and returns.
+// ---------------------------------------------------------------------------
+constexpr int kSlabW = kTM + 2;  // staged pixels per input row
+
+__host__ __device__ constexpr uint32_t slab_bytes(int G) {
+    return (uint32_t)((3 * G * kSlabW * 16 + 127) / 128 * 128);
+}
+
+template <int BN, int G>
+__global__ void __launch_bounds__(kTcThreads) conv3x3_slab_kernel(const __nv_bfloat16 *__restrict__ in,
+                                                                  const __nv_bfloat16 *__restrict__ w,
+                                                                  const float *__restrict__ bias,
+                                                                  __nv_bfloat16 *__restrict__ out, int N, int H,
+                                                                  int Wd, int Cout, int relu) {
+    constexpr int Cin = 8 * G;
+    constexpr int kAcc = BN < 32 ? 32 : BN;  // TMEM columns of one accumulator
+    constexpr int kCols = 2 * kAcc;
+    constexpr uint32_t kSlab = slab_bytes(G);
+    extern __shared__ __align__(128) unsigned char sl_smem[];
+    unsigned char *const Wsm = sl_smem + 2 * kSlab;
+    __shared__ __align__(8) uint64_t mbar[2];
+    __shared__ uint32_t tmem_slot;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int n0 = blockIdx.y * BN;
+    const int tiles_x = Wd / kTM;
+    const long long ntiles = (long long)N * H * tiles_x;
+
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_slot)),
+                     "r"(kCols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    if (tid == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&mbar[0])) : "memory");
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&mbar[1])) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = tmem_slot;
+
+    // weights: W[n0 + co][t][8g .. 8g + 7] -> Wsm[(t G + g) BN + co]
+    for (int e = tid; e < 9 * G * BN; e += kTcThreads) {
+        const int g = e % G, co = (e / G) % BN, t = e / (G * BN);
+        cp_async16(Wsm + ((t * G + g) * BN + co) * 16, w + ((long long)(n0 + co) * 9 + t) * Cin + 8 * g, 16);
+    }
+    // the three input rows of a tile, channel group fastest (coalesced reads)
+    const auto stage = [&](long long tile, unsigned char *dst) {
+        const int tx = (int)(tile % tiles_x);
+        const long long ry = tile / tiles_x;
+        const int y = (int)(ry % H), n = (int)(ry / H), x0 = tx * kTM;
+        for (int e = tid; e < 3 * G * kSlabW; e += kTcThreads) {
+            const int g = e % G, px = (e / G) % kSlabW, ky = e / (G * kSlabW);
+            const int sy = y + ky - 1, sx = x0 + px - 1;
+            const bool inside = sy >= 0 && sy < H && sx >= 0 && sx < Wd;
+            const __nv_bfloat16 *src = inside ? in + (((long long)n * H + sy) * Wd + sx) * Cin + 8 * g : in;
+            cp_async16(dst + ((ky * G + g) * kSlabW + px) * 16, src, inside ? 16 : 0);
+        }
+    };
+    const auto epilogue = [&](long long tile, int acc) {
+        const int tx = (int)(tile % tiles_x);
+        const long long row = tile / tiles_x;  // n H + y
+        const long long p = row * Wd + tx * kTM + warp * 32 + lane;
+#pragma unroll
+        for (int c = 0; c < BN; c += 8) {
+            uint32_t r[8];
+            asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+                         : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+                           "=r"(r[7])
+                         : "r"(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(acc * kAcc + c)));
+            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+            __align__(16) __nv_bfloat16 o[8];
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+                float v = __uint_as_float(r[q]);
+                if (bias) v += bias[n0 + c + q];
+                if (relu) v = fmaxf(v, 0.f);
+                o[q] = __float2bfloat16_rn(v);
+            }
+            *reinterpret_cast<uint4 *>(out + p * Cout + n0 + c) = *reinterpret_cast<const uint4 *>(o);
+        }
+    };
+
+    constexpr uint32_t idesc = mma_idesc(kTM, BN);
+    long long tile = blockIdx.x;
+    if (tile < ntiles) stage(tile, sl_smem);
+    cp_async_commit();  // the weights and the first slab
+    bool ok = true;
+    int i = 0;
+    long long prev = -1;
+    for (; tile < ntiles; tile += gridDim.x, ++i) {
+        const int b = i & 1;
+        cp_async_wait<0>();
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        __syncthreads();
+        if (tid == 0) {
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const uint32_t a0 = smem_u32(sl_smem + b * kSlab), w0 = smem_u32(Wsm);
+            int k = 0;
+#pragma unroll
+            for (int t = 0; t < 9; ++t) {
+                const int ky = t / 3, kx = t % 3;
+#pragma unroll
+                for (int j = 0; j < G / 2; ++j, ++k) {
+                    const uint64_t ad = smem_desc(a0 + (uint32_t)(((ky * G + 2 * j) * kSlabW + kx) * 16), kSlabW * 16, 128);
+                    const uint64_t bd = smem_desc(w0 + (uint32_t)((t * G + 2 * j) * BN * 16), BN * 16, 128);
+                    const uint32_t accum = k > 0 ? 1u : 0u;
+                    asm volatile(
+                        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+                        " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(tmem + (uint32_t)(b * kAcc)),
+                        "l"(ad), "l"(bd), "r"(idesc), "r"(accum)
+                        : "memory");
+                }
+            }
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                             smem_u32(&mbar[b]))
+                         : "memory");
+        }
+        // the previous tile's MMAs: done -> its slab buffer and accumulator are free
+        if (i > 0) {
+            const bool mine = ok && mbar_wait(smem_u32(&mbar[b ^ 1]), (uint32_t)(((i - 1) >> 1) & 1));
+            ok = __syncthreads_and(mine) != 0;  // one decision for the whole CTA
+        }
+        const long long next = tile + gridDim.x;
+        if (ok && next < ntiles) stage(next, sl_smem + (b ^ 1) * kSlab);
+        cp_async_commit();
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        if (ok && i > 0) epilogue(prev, b ^ 1);
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        prev = tile;
+        if (!ok) {
+            ++i;
+            break;
+        }
+    }
+    // the last tile (its commit tracks every earlier MMA of the issuing thread;
+    // waited for also after a time-out, before the tensor memory is freed)
+    if (i > 0) {
+        const bool done = mbar_wait(smem_u32(&mbar[(i - 1) & 1]), (uint32_t)(((i - 1) >> 1) & 1));
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        if (ok && done) epilogue(prev, (i - 1) & 1);
+    }
+    cp_async_wait<0>();
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kCols) : "memory");
+}
+
+template <int BN, int G>
+cudaError_t launch_conv_slab(const __nv_bfloat16 *in, const __nv_bfloat16 *w, const float *bias, __nv_bfloat16 *out,
+                             int N, int H, int W, int Cout, int relu, cudaStream_t s) {
+    const size_t smem = 2 * (size_t)slab_bytes(G) + 9 * (size_t)G * BN * 16;
+    cudaError_t e = cudaFuncSetAttribute(conv3x3_slab_kernel<BN, G>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    // the whole unified L1 / shared memory as shared memory, so that several CTAs fit on an SM
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(conv3x3_slab_kernel<BN, G>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                 (int)cudaSharedmemCarveoutMaxShared);
+    if (e != cudaSuccess) return e;
+    int dev = 0, sms = 0, per_sm = 0, smem_sm = 0;
+    e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+    if (e == cudaSuccess)
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, conv3x3_slab_kernel<BN, G>, kTcThreads, smem);
+    if (e != cudaSuccess) return e;
+    // CTAs per SM: the occupancy query, the shared memory (1 KB reserved a CTA) and the
+    // tensor memory (512 columns per SM, two accumulators a CTA), whichever is least
+    per_sm = std::max(per_sm, (int)(smem_sm / (smem + 1024)));
+    per_sm = std::max(1, std::min({per_sm, (int)(smem_sm / (smem + 1024)), 512 / (2 * (BN < 32 ? 32 : BN))}));
+    const long long tiles = (long long)N * H * (W / kTM);
+    const int gx = (int)std::max<long long>(1, std::min<long long>(tiles, (long long)sms * per_sm / (Cout / BN)));
+    dim3 grid(gx, Cout / BN);
+    conv3x3_slab_kernel<BN, G><<<grid, kTcThreads, smem, s>>>(in, w, bias, out, N, H, W, Cout, relu);
+    return cudaGetLastError();
+}
+
+// The slab kernel's shapes: forward, rows of whole 128-pixel tiles, Cin 16, 32 or 64.
+bool slab_shape(int W, int Cin_g, int Cout_g) {
+    return W % kTM == 0 && (Cin_g == 16 || Cin_g == 32 || Cin_g == 64) && Cout_g % 16 == 0;
+}
+
+cudaError_t conv_dispatch_slab(const __nv_bfloat16 *in, const __nv_bfloat16 *w, const float *bias, __nv_bfloat16 *out,
+                               int N, int H, int W, int Cin_g, int Cout_g, int relu, cudaStream_t s) {
+    // (for 64 input channels at most 64 output channels a CTA: the staged weights of
+    // 128 would not fit beside the two slabs)
+    int BN = Cout_g % 128 == 0 ? 128 : (Cout_g % 64 == 0 ? 64 : (Cout_g % 32 == 0 ? 32 : 16));
+    if (Cin_g == 64 && BN > 64) BN = 64;
+#define CDF_SLAB(G, WIDE)                                                                               \
+    switch (BN) {                                                                                       \
+        case 128: return launch_conv_slab<WIDE, G>(in, w, bias, out, N, H, W, Cout_g, relu, s);         \
+        case 64: return launch_conv_slab<64, G>(in, w, bias, out, N, H, W, Cout_g, relu, s);            \
+        case 32: return launch_conv_slab<32, G>(in, w, bias, out, N, H, W, Cout_g, relu, s);            \
+        default: return launch_conv_slab<16, G>(in, w, bias, out, N, H, W, Cout_g, relu, s);            \
+    }
+    if (Cin_g == 16) CDF_SLAB(2, 128)
+    if (Cin_g == 32) CDF_SLAB(4, 128)
+    CDF_SLAB(8, 64)  // BN is at most 64 here
+#undef CDF_SLAB
+}
+
 template <bool kBwdData, int BN>
 cudaError_t launch_conv_tc_pipe(const __nv_bfloat16 *in, const __nv_bfloat16 *w, const float *bias,
                                 __nv_bfloat16 *out, int N, int H, int W, int Cin_g, int Cout_g, int relu,
@@ -787,7 +1009,8 @@ cudaError_t launch_conv_tc(const __nv_bfloat16 *in, const __nv_bfloat16 *w, cons
 
 // Convolution path: 1 = tcgen05, the faster staging per shape (default), 2 = tcgen05
 // with synchronous staging, 3 = tcgen05 persistent warp-specialised forward,
-// 0 = the warp-level MMA kernels.
+// 4 = the forward without im2col copy (conv3x3_slab_kernel) where the shape allows it,
+// else as 1, 0 = the warp-level MMA kernels.
 int g_path = 1;
 bool g_use_tc = true;
 
@@ -806,6 +1029,8 @@ template <bool kBwdData>
 cudaError_t conv_dispatch(const __nv_bfloat16 *in, const __nv_bfloat16 *w, const float *bias, __nv_bfloat16 *out,
                           int N, int H, int W, int Cin_g, int Cout_g, int relu, cudaStream_t s) {
     const int BN = Cout_g % 128 == 0 ? 128 : (Cout_g % 64 == 0 ? 64 : (Cout_g % 32 == 0 ? 32 : 16));
+    if ((g_path == 1 || g_path == 4) && !kBwdData && slab_shape(W, Cin_g, Cout_g))
+        return conv_dispatch_slab(in, w, bias, out, N, H, W, Cin_g, Cout_g, relu, s);
     if (g_path == 3 && !kBwdData) {  // forward: the persistent warp-specialised kernel
         switch (BN) {
             case 128: return launch_conv_ws<128, 4>(in, w, bias, out, N, H, W, Cin_g, Cout_g, relu, s);
@@ -817,8 +1042,9 @@ cudaError_t conv_dispatch(const __nv_bfloat16 *in, const __nv_bfloat16 *w, const
     // (Cin >= 128, e.g. 159 against 101 TFLOP/s at 32^2 x 256 -> 256), two-buffer
     // synchronous staging for short K, where more CTAs per SM hide more latency
     // (80 against 72 TFLOP/s at 256^2 x 32 -> 32)
-    if (g_path == 1 && Cin_g < 128) return conv_dispatch_path2<kBwdData>(in, w, bias, out, N, H, W, Cin_g, Cout_g, relu, s, BN);
-    if (g_path == 1 || g_path == 3) {
+    if ((g_path == 1 || g_path == 4) && Cin_g < 128)
+        return conv_dispatch_path2<kBwdData>(in, w, bias, out, N, H, W, Cin_g, Cout_g, relu, s, BN);
+    if (g_path == 1 || g_path == 3 || g_path == 4) {
         switch (BN) {
             case 128: return launch_conv_tc_pipe<kBwdData, 128>(in, w, bias, out, N, H, W, Cin_g, Cout_g, relu, s);
             case 64: return launch_conv_tc_pipe<kBwdData, 64>(in, w, bias, out, N, H, W, Cin_g, Cout_g, relu, s);
@@ -1414,7 +1640,7 @@ extern "C" {
 const char *cdf_nn_last_error(void) { return g_nn_err; }
 
 cdf_nn_status cdf_nn_set_tensor_path(int tcgen05) {
-    if (tcgen05 < 0 || tcgen05 > 3) return nn_fail("set_tensor_path: 0, 1, 2 or 3");
+    if (tcgen05 < 0 || tcgen05 > 4) return nn_fail("set_tensor_path: 0, 1, 2, 3 or 4");
     g_path = tcgen05;
     g_use_tc = tcgen05 != 0;
     return CDF_NN_OK;

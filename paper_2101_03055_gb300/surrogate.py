@@ -60,8 +60,9 @@ def nn_lib():
 
 def set_tensor_path(tcgen05):
     """Convolutions on the 5th-generation tensor cores (True or 1, the default: the faster
-    staging per layer; 2: synchronous staging; 3: persistent warp-specialised forward) or
-    on the warp-level MMA kernels (False or 0)."""
+    staging per layer; 2: synchronous staging; 3: persistent warp-specialised forward;
+    4: the forward without im2col copy where the shape allows it) or on the warp-level
+    MMA kernels (False or 0)."""
     _call("cdf_nn_set_tensor_path", int(tcgen05))
 
 

@@ -29,12 +29,12 @@ def S(cdf):
     return surrogate, torch
 
 
-@pytest.fixture(params=["tcgen05", "tcgen05_sync", "tcgen05_ws", "mma"])
+@pytest.fixture(params=["tcgen05", "tcgen05_sync", "tcgen05_ws", "tcgen05_slab", "mma"])
 def path(S, request):
     """Run a convolution test on each tensor-core path, and check afterwards that no
     bounded wait of the tcgen05 kernels ran out."""
     sur, torch = S
-    sur.set_tensor_path({"tcgen05": 1, "tcgen05_sync": 2, "tcgen05_ws": 3, "mma": 0}[request.param])
+    sur.set_tensor_path({"tcgen05": 1, "tcgen05_sync": 2, "tcgen05_ws": 3, "tcgen05_slab": 4, "mma": 0}[request.param])
     yield request.param
     torch.cuda.synchronize()
     sur.set_tensor_path(True)
@@ -47,7 +47,13 @@ def bf(torch, a):
 
 
 @pytest.mark.parametrize("N,H,W,Cin,Cout", [(2, 9, 13, 16, 32), (1, 8, 8, 32, 64), (2, 5, 7, 96, 32),
-                                            (1, 4, 4, 384, 128), (2, 24, 20, 64, 128)])
+                                            (1, 4, 4, 384, 128), (2, 24, 20, 64, 128),
+                                            # rows of whole 128-pixel tiles: the forward without im2col
+                                            # copy (paths 1 and 4), Cin 16 / 32 / 64, every output tile
+                                            # width, tiles at the image's top and bottom rows
+                                            (2, 3, 256, 16, 32), (1, 4, 128, 32, 32), (1, 2, 128, 32, 96),
+                                            (1, 3, 256, 32, 128), (2, 3, 128, 64, 64), (1, 2, 128, 64, 128),
+                                            (1, 1, 128, 16, 64)])
 def test_conv_forward(S, path, N, H, W, Cin, Cout):
     sur, torch = S
     r = np.random.default_rng(N * 1000 + Cin)
@@ -175,3 +181,25 @@ def test_training_reduces_loss(S):
     net = sur.UNet(base=32, levels=4, seed=0)
     hist = sur.train(net, x, y, epochs=40, batch=16, lr=2e-3)
     assert hist[-1] < 0.2 * hist[0]
+
+
+@pytest.mark.parametrize("N,H,W,Cin,Cout", [(2, 3, 256, 16, 32), (1, 4, 128, 32, 64), (1, 3, 128, 64, 128)])
+def test_conv_forward_without_im2col_same_bits(S, N, H, W, Cin, Cout):
+    """The forward kernel without im2col copy (path 4) issues the same MMAs in the same
+    K order as the staged kernels (tap by tap, 16 channels at a time), so its output
+    equals the synchronous-staging kernel's (path 2) bit for bit."""
+    sur, torch = S
+    r = np.random.default_rng(7 * Cin + W)
+    x, _ = bf(torch, r.normal(size=(N, H, W, Cin)))
+    w, _ = bf(torch, r.normal(size=(Cout, 3, 3, Cin)) / math.sqrt(9 * Cin))
+    b = torch.as_tensor(r.normal(size=Cout).astype(np.float32)).cuda()
+    try:
+        out = {}
+        for p in (2, 4):
+            sur.set_tensor_path(p)
+            out[p] = sur.conv3x3_fwd(x, w, b, True).cpu()
+        torch.cuda.synchronize()
+        assert torch.equal(out[2], out[4])
+    finally:
+        sur.set_tensor_path(True)
+    assert sur.tensor_error_flag() == 0
