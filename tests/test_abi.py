@@ -90,7 +90,8 @@ def _create_status(pb, **kw):
 
 
 @pytest.mark.parametrize("case", ["nu", "m0", "m5", "grid", "D", "chemo_m1", "storage", "rho0", "block",
-                                  "periodic_mismatch", "dirichlet_on_periodic", "eps"])
+                                  "periodic_mismatch", "dirichlet_on_periodic", "eps", "temporal_lanes",
+                                  "lanes_without_shape", "block_lanes", "block_lanes_not_flat", "block_lanes_m3"])
 def test_create_rejects_invalid_parameters(L, case):
     pb = I.cross_diffusion_taylor_green(16, 16)
     if case == "nu":
@@ -105,13 +106,21 @@ def test_create_rejects_invalid_parameters(L, case):
         pb = pb.replace(west=I.Side("periodic", "noslip", ["dirichlet", "noflux"], [1.0, 0.0]))
     kw = {"m0": {"m": 0}, "m5": {"m": 5}, "grid": {"grid__nx": 0}, "storage": {"opt__storage": 7},
           "rho0": {"opt__rho0": 0.0}, "block": {"opt__block_x": 48, "opt__block_y": 2},
-          "eps": {"dif__r_regularised": 1, "dif__eps": 0.0}}.get(case, {})
+          "eps": {"dif__r_regularised": 1, "dif__eps": 0.0},
+          # nodes per thread of the paired-lane kernels: 0, 1 or 2, and 2 only with a given shape
+          "temporal_lanes": {"opt__temporal_lanes": 3},
+          "lanes_without_shape": {"opt__temporal_lanes": 2},
+          "block_lanes": {"opt__block_x": 128, "opt__block_y": 0, "opt__block_lanes": 3},
+          "block_lanes_not_flat": {"opt__block_x": 128, "opt__block_y": 1, "opt__block_lanes": 2},
+          "block_lanes_m3": {"m": 3, "opt__block_x": 128, "opt__block_y": 0, "opt__block_lanes": 2}}.get(case, {})
     if case == "nu":
         kw["nu"] = 0.0
     st, h, msg = _create_status(pb, **kw)
     assert st == lib.CDF_EINVAL, (case, st, msg)
     assert h is None
     assert msg
+    if "lanes" in case:  # refused for that reason, before any device call
+        assert "lanes" in msg, msg
 
 
 def test_null_arguments(L):
