@@ -465,7 +465,7 @@ __device__ __forceinline__ void collide(const LbParams &p, V (&f)[M][5], V (&h)[
     const V q = vfma(-0.5f, usq, prd);
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
-        const int i = k < 2 ? k + 1 : k + 3, o = i + 2;  // i = 1, 2, 5, 6 and their opposites 3, 4, 7, 8
+        const int i = k < 2 ? k + 1 : k + 3, io = i + 2;  // i = 1, 2, 5, 6 and their opposites io = 3, 4, 7, 8
         const float kA = kA9(i);
         const V cu = cdot(kC9x(i), kC9y(i), ux, uy), cF = cdot(kC9x(i), kC9y(i), Fx, Fy);
         const V E = heq_even(i, q, ux, uy), O = heq_odd(i, ux, uy), Fo = vmul(kA, cF);
@@ -476,7 +476,7 @@ __device__ __forceinline__ void collide(const LbParams &p, V (&f)[M][5], V (&h)[
             Fopp = vfma(p.varphi, f2, -Fo);
         }
         h[i] = vfma(fw, Fi, vfma(-wf, h[i] - (E + O), h[i]));
-        h[o] = vfma(fw, Fopp, vfma(-wf, h[o] - (E - O), h[o]));
+        h[io] = vfma(fw, Fopp, vfma(-wf, h[io] - (E - O), h[io]));
     }
 #pragma unroll
     for (int a = 0; a < M; ++a) o.phi[a] = s.phi[a];
